@@ -1,0 +1,278 @@
+/*
+ * b3t: a task-DAG executor for one B300 GPU (sm_103a).
+ *
+ * The programming model is the one of Section 2 of the paper (Courtes,
+ * "C Language Extensions for Hybrid CPU/GPU Programming with StarPU"):
+ *   - a task is declared with its implementation, its number of buffer
+ *     parameters and one access mode per buffer (read-only, write-only or
+ *     read-write), like the paper's codelet structure;
+ *   - buffers are registered before tasks use them;
+ *   - invoking a task is asynchronous: it only adds the task to the
+ *     scheduler's queue; the access modes together with the order of the
+ *     invocations determine the dependency graph;
+ *   - a wait joins every pending task.
+ * Here every task has exactly one implementation, a CUDA device function
+ * run by a persistent kernel; there is no CPU implementation and no
+ * fallback.
+ *
+ * Conventions for every function below:
+ *   - Return value: 0 on success, a negative errno value on failure (the
+ *     generated task body of Section 3.2 turns a non-zero error into
+ *     strerror(-err); this library never aborts, the caller decides).
+ *     b3t_strerror() gives a message.
+ *   - Pointers passed as buffers are DEVICE pointers, owned by the caller
+ *     (for instance torch tensors).  The caller keeps them alive and
+ *     unmodified by other work until the tasks using them have completed
+ *     (b3t_task_wait, b3t_data_acquire or b3t_data_unregister): the
+ *     ownership rule behind the paper's warning about registering automatic
+ *     variables (Section 3.4).
+ *   - The library owns handles, codelets, task records and its own device
+ *     scratch (task table, dependency counters, ready queue, status word).
+ *   - A context is not thread-safe; use one context per host thread.
+ *   - All calls are non-blocking except b3t_task_wait, b3t_data_acquire,
+ *     b3t_data_unregister, b3t_tiles_unregister and b3t_shutdown.
+ */
+#ifndef B3T_H
+#define B3T_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define B3T_API __attribute__((visibility("default")))
+#else
+#define B3T_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct b3t_ctx b3t_ctx;
+typedef int32_t b3t_handle;
+typedef int32_t b3t_codelet;
+typedef int32_t b3t_graph;
+
+/* Access modes.  Section 3.2: the generated invocation passes a read-write
+ * buffer with mode value 3; read and write are the two bits of it. */
+enum { B3T_R = 1, B3T_W = 2, B3T_RW = 3 };
+
+/* Task implementations.  Each kind fixes its buffers (in order), their
+ * modes, their element types and the scalar argument blob; b3t_task_decl
+ * checks a declaration against it (Section 3.2: a signature mismatch between
+ * a task and its implementation is diagnosed).  Tiles are b x b, contiguous,
+ * column-major inside the tile (element (r, c) at r + c*b), registered with
+ * ld = b, b a multiple of 64 (128 for the mixed-precision kinds).
+ *
+ *  kind            buffers (mode, type)                       scalars
+ *  B3T_NOOP        0..4 buffers of any mode                   none
+ *  B3T_SCAL_F32    x (RW, f32 vector, 16-byte aligned)        float f
+ *                  x[i] <- fl32(x[i] * f)   (Section 2 example)
+ *  B3T_POTRF       A_kk (RW, f64 tile)                        int32 col0
+ *                  lower Cholesky in place; a pivot <= 0 or NaN makes the
+ *                  wait return -EDOM with info = col0 + 1-based column
+ *  B3T_TRSM        L_kk (R), A_ik (RW)  f64 tiles             none
+ *                  A_ik <- A_ik L_kk^{-T}
+ *  B3T_SYRK        A_ik (R), A_ii (RW)  f64 tiles             none
+ *                  A_ii <- A_ii - A_ik A_ik^T (lower triangle only)
+ *  B3T_GEMM        A_ik (R), A_jk (R), A_ij (RW)  f64 tiles   none
+ *                  A_ij <- A_ij - A_ik A_jk^T
+ *  Mixed precision: W tiles binary32, L tiles f64, Q tiles quantised
+ *  (fmt = B3T_FMT_BF16 or B3T_FMT_E4M3, layout below):
+ *  B3T_POTRF_MX    W_kk (R, f32), L_kk (W, f64)               int32 col0
+ *                  L_kk = chol(fp64(W_kk)); strict upper part of L_kk = 0
+ *  B3T_TRSM_MX     L_kk (R), W_ik (R, f32), L_ik (W, f64)     none
+ *                  L_ik = fp64(W_ik) L_kk^{-T}
+ *  B3T_QUANT       L_ik (R, f64), Q_ik (W)                    int32 fmt
+ *                  Q_ik = round_fmt(fl32(L_ik / 2^e)), e the tile's scale
+ *                  exponent (0 for bf16; for E4M3 the smallest e with
+ *                  max|L_ik| <= 448 * 2^e)
+ *  B3T_SYRK_MX     Q_ik (R), W_ii (RW, f32)                   int32 fmt
+ *                  W_ii <- fl32(W_ii - 2^(2e) Q_ik Q_ik^T), lower triangle
+ *  B3T_GEMM_MX     Q_ik (R), Q_jk (R), W_ij (RW, f32)         int32 fmt
+ *                  W_ij <- fl32(W_ij - 2^(ei+ej) Q_ik Q_jk^T)
+ *  The products of the MX updates are exact and are accumulated in binary32
+ *  on the tensor cores (tcgen05).
+ */
+enum b3t_kind {
+    B3T_NOOP = 0,
+    B3T_SCAL_F32 = 1,
+    B3T_POTRF = 2,
+    B3T_TRSM = 3,
+    B3T_SYRK = 4,
+    B3T_GEMM = 5,
+    B3T_POTRF_MX = 6,
+    B3T_TRSM_MX = 7,
+    B3T_SYRK_MX = 8,
+    B3T_GEMM_MX = 9,
+    B3T_QUANT = 10
+};
+
+/* Low-precision formats of the Q tiles. */
+enum b3t_fmt { B3T_FMT_BF16 = 0, B3T_FMT_E4M3 = 1 };
+
+/* Quantised tile layout (Q tiles).  A b x b tile is cut into 16 KiB chunks
+ * of 128 rows x 128 bytes of K (64 bf16 or 128 E4M3 columns); with
+ * nk = b * esize / 128, chunk (rb, kb) covers rows 128*rb.. and starts at byte
+ * (rb * nk + kb) * 16384.  Inside a chunk, row r occupies bytes r*128.. and its
+ * 16-byte group g (columns ascending) is stored at group position g ^ (r % 8).
+ * After the b*b*esize data bytes: int32 scale exponent e, padded to 16 bytes.
+ * b3t_q_bytes() gives the total size (0 for invalid arguments). */
+B3T_API size_t b3t_q_bytes(int b, int fmt);
+
+typedef struct b3t_config {
+    int64_t timeout_ns;     /* bound on any device-side wait; 0 = 10 s */
+    int32_t ctas_per_sm;    /* persistent CTAs per SM; 0 = automatic */
+    int32_t prio_levels;    /* ready-queue priority levels 1..8; 0 = 8 */
+    int32_t debug_checks;   /* 1: kernels bounds-check task ids and items */
+    int32_t reserved[3];
+} b3t_config;
+
+/* Create a context bound to the current CUDA device and to `cuda_stream`
+ * (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream; NULL = the
+ * legacy default stream).  cfg may be NULL.  -ENODEV without a CUDA device,
+ * -ENOMEM when host or device memory runs out. */
+B3T_API int b3t_init(b3t_ctx **ctx, const b3t_config *cfg, void *cuda_stream);
+
+/* Wait for all pending work, release every library-owned resource and the
+ * context.  Registered buffers stay the caller's. */
+B3T_API int b3t_shutdown(b3t_ctx *ctx);
+
+/* Declare a task (the codelet of Section 2): its name (for debugging, like
+ * the codelet's name field), its implementation kind, the number of buffer
+ * parameters, their modes and the size of its scalar blob.  -EINVAL if the
+ * declaration does not match the kind's signature (Section 3.2). */
+B3T_API int b3t_task_decl(b3t_ctx *ctx, const char *name, int kind, int nbuffers,
+                          const uint8_t *modes, size_t scalar_bytes, b3t_codelet *out);
+
+/* Register a device buffer (Section 2: buffers passed to tasks must be
+ * registered first): nelems elements of elemsize bytes starting at
+ * dev_ptr; ld = 0 for a vector, ld = b for a b x b tile.  The same address
+ * may not be registered twice (-EEXIST).  -EINVAL on a null pointer or zero
+ * size. */
+B3T_API int b3t_data_register(b3t_ctx *ctx, void *dev_ptr, size_t nelems,
+                              size_t elemsize, int64_t ld, b3t_handle *out);
+
+/* Handle of a registered pointer (Section 3.2: the generated task body looks
+ * the pointer up and reports an unregistered pointer).  -ENOENT if none. */
+B3T_API int b3t_data_lookup(b3t_ctx *ctx, const void *dev_ptr, b3t_handle *out);
+
+/* Split a registered buffer into nparts consecutive parts of part_nelems
+ * elements each (the filters of Section 5.1).  Each part gets a handle of
+ * its own; a task that names the parent accesses every part.  The parent
+ * may not be partitioned twice (-EEXIST), nor while pending tasks name it
+ * (-EBUSY); nparts * part_nelems must fit in it (-EINVAL). */
+B3T_API int b3t_data_partition(b3t_ctx *ctx, b3t_handle parent, int32_t nparts,
+                               size_t part_nelems, b3t_handle *parts_out);
+
+/* Submit one task (asynchronous, Section 3.3): handles in the codelet's
+ * buffer order, with the modes the caller uses them in (NULL = the
+ * declaration's; otherwise they must equal it: -EINVAL), and the scalar
+ * blob.  Dependencies on earlier submissions are derived here from the
+ * access modes: read-after-write, write-after-read and write-after-write,
+ * per buffer, in submission order.  -ENOENT for an unregistered handle;
+ * -EINVAL for buffers whose size, alignment or type does not fit the kind.
+ * The task runs at the next b3t_task_flush / b3t_task_wait. */
+B3T_API int b3t_task_submit(b3t_ctx *ctx, b3t_codelet cl, const b3t_handle *handles,
+                            const uint8_t *modes, int nbuffers, const void *scalars,
+                            size_t scalar_bytes);
+
+/* Same, naming the buffers by device pointer; each pointer is looked up like
+ * the generated task body of Section 3.2 does (-ENOENT: "attempt to use
+ * unregistered pointer"). */
+B3T_API int b3t_task_submit_ptrs(b3t_ctx *ctx, b3t_codelet cl, void *const *ptrs,
+                                 int nbuffers, const void *scalars, size_t scalar_bytes);
+
+/* Launch every pending task as one persistent-kernel run on the context's
+ * stream and return without waiting.  Tasks submitted later depend on the
+ * flushed ones through stream order. */
+B3T_API int b3t_task_flush(b3t_ctx *ctx);
+
+/* Flush, then wait for every submitted task (Section 2: wait for all;
+ * Section 3.3: the wait pragma) and read the device status words of the
+ * launches since the last wait.  timeout_ns bounds the host wait (0 = no
+ * bound; -ETIMEDOUT when it expires with work still running).  Returns
+ * -ETIMEDOUT if a device-side wait ran past the context's timeout, -EDOM if
+ * a POTRF met a non-positive pivot (see b3t_last_error), -EIO on a CUDA
+ * error. */
+B3T_API int b3t_task_wait(b3t_ctx *ctx, int64_t timeout_ns);
+
+/* Make a buffer safe for host-side use (Section 3.4, acquire pragma): waits
+ * for the tasks that write it (mode R) or also read it (mode W / RW). */
+B3T_API int b3t_data_acquire(b3t_ctx *ctx, b3t_handle h, uint8_t mode);
+
+/* Wait for the tasks using the buffer, then forget the handle (Section 2).
+ * Unregistering a partitioned parent unregisters its parts. */
+B3T_API int b3t_data_unregister(b3t_ctx *ctx, b3t_handle h);
+
+/* Detail of the last device-side failure: the task id (in submission order
+ * within its launch) and the POTRF info (1-based global column), or -1. */
+B3T_API int b3t_last_error(b3t_ctx *ctx, int32_t *task_id, int32_t *info);
+
+/* Static message for a return code of this library. */
+B3T_API const char *b3t_strerror(int err);
+
+/* Repeated DAGs.  Between capture_begin and capture_end, submissions are
+ * recorded instead of launched; capture_end builds the task table and the
+ * dependency graph once, uploads them, and captures the launch (counter
+ * reset + persistent kernel) into a CUDA graph.  replay launches it on the
+ * context's stream without waiting; b3t_task_wait joins it.  The graph names
+ * the same buffers every time; their contents are whatever they hold at
+ * replay.  -EBUSY if tasks are pending at capture_begin. */
+B3T_API int b3t_graph_capture_begin(b3t_ctx *ctx);
+B3T_API int b3t_graph_capture_end(b3t_ctx *ctx, b3t_graph *out);
+B3T_API int b3t_graph_replay(b3t_ctx *ctx, b3t_graph g);
+B3T_API int b3t_graph_destroy(b3t_ctx *ctx, b3t_graph g);
+
+/* Introspection of the pending (not yet flushed) batch, for tests and
+ * tools: number of tasks and derived edges, and the edges themselves as
+ * (pred, succ) pairs of task indices in submission order (pred < succ).
+ * Writes at most cap pairs. */
+B3T_API int b3t_dag_stats(b3t_ctx *ctx, int64_t *ntasks, int64_t *nedges);
+B3T_API int b3t_dag_edges(b3t_ctx *ctx, int32_t *pred, int32_t *succ, int64_t cap,
+                          int64_t *count);
+
+/* Launch statistics of the last launch (flush or replay): tasks, work
+ * items, persistent CTAs, and the device time of the persistent kernel (or
+ * of the replayed graph) in ns, measured with CUDA events on the context's
+ * stream; valid after b3t_task_wait, -1 otherwise. */
+B3T_API int b3t_last_launch(b3t_ctx *ctx, int64_t *ntasks, int64_t *nitems,
+                            int32_t *nctas, int64_t *kernel_ns);
+
+/* Add one phantom dependency to a pending task so that its counter never
+ * reaches zero: the launch then ends through the device-side timeout
+ * (-ETIMEDOUT), never by hanging.  For failure-detection tests. */
+B3T_API int b3t_debug_block_task(b3t_ctx *ctx, int64_t task_index);
+
+/* ---------------------------------------------------------------------
+ * Tiled Cholesky helpers, built on the calls above.  Tiles are passed as an
+ * array of T(T+1)/2 device pointers to b x b column-major tiles in packed
+ * column order: tile (i, j), i >= j, at index j*T - j(j-1)/2 + (i - j).
+ * Every tile is registered as its own buffer (the workaround Section 5.1
+ * gives for partitioned matrices; already registered tiles are reused) and
+ * the right-looking task order is submitted:
+ *   for k: POTRF(A_kk); for i>k: TRSM(A_kk, A_ik);
+ *          for i>k: SYRK(A_ik, A_ii); for k<j<i: GEMM(A_ik, A_jk, A_ij)
+ * col0 is added to POTRF info values (global column of the first tile).
+ * Several submissions before one wait run in one launch (batching). */
+B3T_API int b3t_cholesky_submit(b3t_ctx *ctx, double *const *tiles, int32_t T, int32_t b,
+                                int32_t col0);
+
+/* Mixed precision, right-looking:
+ *   for k: POTRF_MX(W_kk, L_kk);
+ *          for i>k: TRSM_MX(L_kk, W_ik, L_ik), QUANT(L_ik, Q_ik);
+ *          for i>k: SYRK_MX(Q_ik, W_ii); for k<j<i: GEMM_MX(Q_ik, Q_jk, W_ij)
+ * W tiles (binary32, caller-initialised, e.g. to fl32(A)), L tiles (f64) and
+ * Q tiles (b3t_q_bytes(b, fmt) bytes each; the diagonal ones are unused)
+ * receive the results. */
+B3T_API int b3t_cholesky_mx_submit(b3t_ctx *ctx, float *const *W, double *const *L,
+                                   void *const *Q, int32_t T, int32_t b, int32_t fmt,
+                                   int32_t col0);
+
+/* Wait, then unregister the T(T+1)/2 tiles given (any registered set). */
+B3T_API int b3t_tiles_unregister(b3t_ctx *ctx, void *const *tiles, int32_t T);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* B3T_H */

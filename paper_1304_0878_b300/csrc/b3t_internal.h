@@ -1,0 +1,108 @@
+// Internal layout shared by the host runtime (runtime.cpp) and the device
+// executor (executor.cu).  Not part of the public ABI.
+#pragma once
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __CUDACC__
+#define B3T_HD __host__ __device__
+#else
+#define B3T_HD
+#endif
+
+namespace b3t {
+
+constexpr int kMaxBuffers = 4;
+constexpr int kMaxLevels = 8;
+constexpr int kThreads = 256;            // threads per persistent CTA
+
+// Work-item decomposition of each kind (the host computes nitems, the
+// device maps item -> sub-block with the same constants).
+constexpr int64_t kScalChunk = 1 << 16;  // f32 elements per SCAL item
+constexpr int kGemmBlk = 64;             // f64 GEMM / SYRK item: 64 x 64 of C
+constexpr int kTrsmRows = 32;            // f64 TRSM item: 32 rows of A_ik
+constexpr int kMxBlk = 128;              // MX GEMM / SYRK item: 128 x 128 of C
+
+enum : int32_t {
+    kNoop = 0, kScalF32 = 1, kPotrf = 2, kTrsm = 3, kSyrk = 4, kGemm = 5,
+    kPotrfMx = 6, kTrsmMx = 7, kSyrkMx = 8, kGemmMx = 9, kQuant = 10,
+    kNumKinds = 11
+};
+
+// One task as the device sees it: 64 bytes.
+struct alignas(16) TaskRec {
+    uint64_t buf[kMaxBuffers];   // device pointers, in the codelet's order
+    int64_t n;                   // vector length (SCAL) or tile size b
+    int32_t kind;
+    int32_t nitems;              // work items the task is split into
+    int32_t succ_off;            // first successor in the CSR array
+    int32_t nsucc;
+    int32_t aux;                 // POTRF: global column offset; MX: format
+    uint32_t scal;               // SCAL: float factor bits
+};
+static_assert(sizeof(TaskRec) == 64, "TaskRec is 64 bytes");
+
+// Device status + queue control block (one per launch arena).
+struct alignas(128) Ctl {
+    int32_t error;               // sticky: 0 or a positive errno
+    int32_t err_task;            // task id that set it
+    int32_t err_info;            // POTRF info (1-based global column)
+    int32_t err_where;           // where it was raised (diagnostics)
+    unsigned long long retired;  // tasks retired in this launch
+    int32_t pad0[26];
+    // per-level ring heads / tails, each on its own 128-byte line
+    struct alignas(128) Level {
+        unsigned long long head;
+        unsigned long long tail;
+        int32_t pad[28];
+    } lvl[kMaxLevels];
+};
+
+struct LaunchParams {
+    const TaskRec *tasks;
+    const int32_t *succ;         // CSR successor lists
+    const int32_t *level;        // ready-queue level of each task
+    int32_t *counters;           // remaining predecessors per task
+    int32_t *done_items;         // finished items per task
+    unsigned long long *slots;   // ready rings, all levels back to back
+    Ctl *ctl;
+    unsigned long long ring_off[kMaxLevels];   // first slot of each level
+    unsigned long long ring_cap[kMaxLevels];
+    int64_t ntasks;
+    int32_t nlevels;
+    int32_t has_mx;              // launch holds tcgen05 work: allocate TMEM
+    int64_t timeout_ns;
+    int32_t debug;
+    int32_t pad;
+};
+
+// Init-kernel parameters: reset counters, rings and status for a launch.
+struct InitParams {
+    const int32_t *indeg;        // initial counters
+    int32_t *counters;
+    int32_t *done_items;
+    unsigned long long *slots;
+    unsigned long long nslots;
+    const unsigned long long *roots;      // root items, per level back to back
+    unsigned long long root_off[kMaxLevels];
+    unsigned long long root_cnt[kMaxLevels];
+    Ctl *ctl;
+    int64_t ntasks;
+    int32_t nlevels;
+};
+
+constexpr unsigned long long kEmpty = ~0ull;
+
+B3T_HD inline unsigned long long pack_item(int64_t task, int32_t item) {
+    return ((unsigned long long)task << 32) | (uint32_t)item;
+}
+
+}  // namespace b3t
+
+// Launch entry points implemented in executor.cu.
+extern "C" {
+int b3t_internal_launch(const b3t::InitParams *ip, const b3t::LaunchParams *lp,
+                        int nctas, size_t smem, void *stream, void *ev_start, void *ev_stop);
+int b3t_internal_occupancy(int *ctas_per_sm, size_t smem, int *num_sms);
+size_t b3t_internal_smem_bytes(int has_mx);
+}

@@ -1,0 +1,354 @@
+// Device executor: one persistent kernel runs a whole task graph.
+//
+// Section 2 of the paper: the runtime learns the task graph from the access
+// modes and the invocation order, and schedules tasks as their inputs become
+// ready.  Here that schedule runs on the GPU itself:
+//   * every CTA of a grid sized to full residency loops: claim a work item from
+//     the device-resident ready queue, run the task body on it, and count the
+//     item done;
+//   * the CTA that finishes the last item of a task retires it: one warp
+//     decrements the dependency counters of its successors (one lane per
+//     successor, atomics issued by the whole warp) and pushes every successor
+//     whose counter reached zero, all of its work items at once;
+//   * the ready queue has up to kMaxLevels levels (upward-rank buckets, the
+//     scheduling hint of Section 5.3); a claim takes the oldest item of the
+//     highest non-empty level, found with one warp-wide scan;
+//   * every wait is bounded by %globaltimer: an idle CTA that sees no work for
+//     longer than the launch's timeout sets ETIMEDOUT in the status word and
+//     the whole grid exits; nothing spins forever.
+#include <cuda_runtime.h>
+#include <cerrno>
+
+#include "b3t_internal.h"
+#include "mx.cuh"
+#include "tiles_fp64.cuh"
+
+namespace b3t {
+
+constexpr size_t kSmemData = 100 * 1024;   // dynamic shared memory per CTA
+
+__device__ __forceinline__ unsigned long long ld_acq(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_rlx(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_rel(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ int ld_rlx_i32(const int *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void set_error(Ctl *ctl, int err, int task, int info, int where) {
+    if (atomicCAS(&ctl->error, 0, err) == 0) {
+        ctl->err_task = task;
+        ctl->err_info = info;
+        ctl->err_where = where;
+        __threadfence();
+    }
+}
+
+// ------------------------------------------------------------- SCAL
+// x[i] <- fl32(x[i] * f) over one chunk, 128-bit loads and stores.
+__device__ __forceinline__ void scal_item(const TaskRec &t, int item) {
+    float *x = (float *)t.buf[0];
+    const float f = __uint_as_float(t.scal);
+    const int64_t start = (int64_t)item * kScalChunk;
+    const int64_t end = min(t.n, start + kScalChunk);
+    const int64_t nv = (end - start) >> 2;
+    float4 *v = reinterpret_cast<float4 *>(x + start);
+    constexpr int U = 8;
+    const int tid = threadIdx.x;
+    for (int64_t i0 = tid; i0 < nv; i0 += (int64_t)kThreads * U) {
+        float4 r[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = i0 + (int64_t)u * kThreads;
+            if (i < nv) r[u] = __ldcg(v + i);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = i0 + (int64_t)u * kThreads;
+            if (i < nv) {
+                float4 a = r[u];
+                a.x = __fmul_rn(a.x, f); a.y = __fmul_rn(a.y, f);
+                a.z = __fmul_rn(a.z, f); a.w = __fmul_rn(a.w, f);
+                __stcg(v + i, a);
+            }
+        }
+    }
+    const int64_t tail = (end - start) & 3;
+    if (tid < tail) {
+        float *p = x + start + nv * 4 + tid;
+        *p = __fmul_rn(*p, f);
+    }
+}
+
+// POTRF_MX: L_kk = chol(fp64(W_kk)), strict upper part of L_kk zeroed.
+__device__ __forceinline__ int potrf_mx_item(const TaskRec &t, double *smem, int *s_info) {
+    const float *Wt = (const float *)t.buf[0];
+    double *L = (double *)t.buf[1];
+    const int b = (int)t.n;
+    for (size_t e = threadIdx.x; e < (size_t)b * b; e += kThreads) {
+        const int r = (int)(e % b), c = (int)(e / b);
+        L[e] = r >= c ? (double)Wt[e] : 0.0;
+    }
+    __syncthreads();
+    return potrf_tile(L, b, smem, s_info);
+}
+
+// ------------------------------------------------------------- queue
+// Warp 0 claims one work item.  Returns the packed item, or kEmpty when the
+// launch is over (all tasks retired, an error was raised, or the wait timed
+// out: the last two leave the reason in ctl).
+__device__ __forceinline__ unsigned long long claim(const LaunchParams &p) {
+    const int lane = threadIdx.x & 31;
+    Ctl *ctl = p.ctl;
+    const uint64_t t0 = gtimer();
+    uint32_t backoff = 0;
+    for (uint32_t spin = 0;; ++spin) {
+        int err = 0;
+        if (lane == 0) err = ld_rlx_i32(&ctl->error);
+        err = __shfl_sync(0xffffffffu, err, 0);
+        if (err) return kEmpty;
+        unsigned long long h = 0, tl = 0;
+        const bool mine = lane < p.nlevels;
+        if (mine) {
+            h = ld_rlx(&ctl->lvl[lane].head);
+            tl = ld_rlx(&ctl->lvl[lane].tail);
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, mine && h < tl);
+        if (mask) {
+            const int lv = 31 - __clz(mask);
+            const unsigned long long hv = __shfl_sync(0xffffffffu, h, lv);
+            unsigned long long item = kEmpty;
+            int got = 0;
+            if (lane == 0 && atomicCAS(&ctl->lvl[lv].head, hv, hv + 1) == hv) {
+                got = 1;
+                if (p.debug && hv >= p.ring_cap[lv]) {
+                    set_error(ctl, EPROTO, -1, -1, 3);
+                    got = 2;
+                } else {
+                    unsigned long long *slot = p.slots + p.ring_off[lv] + hv;
+                    // the producer reserves a slot before it fills it
+                    item = ld_acq(slot);
+                    const uint64_t ts = gtimer();
+                    for (uint32_t n = 0; item == kEmpty; ++n) {
+                        __nanosleep(32);
+                        item = ld_acq(slot);
+                        if ((n & 63) == 63 && (int64_t)(gtimer() - ts) > p.timeout_ns) {
+                            set_error(ctl, ETIMEDOUT, -1, -1, 2);
+                            got = 2;
+                            break;
+                        }
+                    }
+                }
+            }
+            got = __shfl_sync(0xffffffffu, got, 0);
+            if (got == 1) return __shfl_sync(0xffffffffu, item, 0);
+            if (got == 2) return kEmpty;
+            continue;
+        }
+        unsigned long long r = 0;
+        if (lane == 0) r = ld_acq(&ctl->retired);
+        r = __shfl_sync(0xffffffffu, r, 0);
+        if ((int64_t)r >= p.ntasks) return kEmpty;
+        if ((spin & 15) == 15 && (int64_t)(gtimer() - t0) > p.timeout_ns) {
+            if (lane == 0) set_error(ctl, ETIMEDOUT, -1, -1, 1);
+            return kEmpty;
+        }
+        __nanosleep(backoff);
+        backoff = backoff < 256 ? backoff + 32 : 256;
+    }
+}
+
+// Warp 0 retires task t: successors' counters, pushes, retired count.
+__device__ __forceinline__ void retire(const LaunchParams &p, int64_t t, const TaskRec &rec) {
+    const int lane = threadIdx.x & 31;
+    __threadfence();
+    for (int base = 0; base < rec.nsucc; base += 32) {
+        const int k = base + lane;
+        if (k < rec.nsucc) {
+            const int s = p.succ[rec.succ_off + k];
+            const int prev = atomicSub(&p.counters[s], 1);
+            if (prev == 1) {
+                const int lv = p.level[s];
+                const int n = p.tasks[s].nitems;
+                const unsigned long long pos = atomicAdd(&p.ctl->lvl[lv].tail, (unsigned long long)n);
+                if (p.debug && pos + n > p.ring_cap[lv]) {
+                    set_error(p.ctl, EPROTO, s, -1, 4);
+                } else {
+                    unsigned long long *slot = p.slots + p.ring_off[lv] + pos;
+                    for (int i = 0; i < n; ++i) st_rel(slot + i, pack_item(s, i));
+                }
+            }
+        }
+    }
+    __syncwarp();
+    if (lane == 0) {
+        __threadfence();
+        atomicAdd(&p.ctl->retired, 1ull);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 2) exec_kernel(const LaunchParams p) {
+    extern __shared__ __align__(1024) unsigned char dsmem[];
+    // align the dynamic area to 1024 bytes (128-byte swizzled operands)
+    unsigned char *smem = (unsigned char *)(((uintptr_t)dsmem + 1023) & ~(uintptr_t)1023);
+    __shared__ unsigned long long s_item;
+    __shared__ int s_flag, s_info, s_fail, s_e;
+    __shared__ __align__(8) uint64_t s_bars[2 * kMxStages + 1];
+    __shared__ uint32_t s_tmem;
+    __shared__ double s_red[kThreads / 32];
+    const int tid = threadIdx.x, warp = tid >> 5;
+
+    MxState mx;
+    mx.full = s_bars;
+    mx.empty = s_bars + kMxStages;
+    mx.done = s_bars + 2 * kMxStages;
+    mx.stage = smem;
+    mx.fills = 0;
+    mx.items = 0;
+    mx.tmem = 0;
+    if (p.has_mx) {
+        if (tid == 0) {
+            for (int i = 0; i < 2 * kMxStages + 1; ++i) mbar_init(&s_bars[i], 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        if (warp == 0) tmem_alloc(&s_tmem, kTmemCols);
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        mx.tmem = s_tmem;
+    }
+
+    for (;;) {
+        if (warp == 0) {
+            const unsigned long long it = claim(p);
+            if ((tid & 31) == 0) s_item = it;
+        }
+        __syncthreads();
+        const unsigned long long item = s_item;
+        if (item == kEmpty) break;
+        __threadfence();   // acquire side for every thread of the CTA
+        const int64_t t = (int64_t)(item >> 32);
+        const int it = (int)(item & 0xffffffffu);
+        if (p.debug && (t >= p.ntasks || it >= p.tasks[t].nitems)) {
+            if (tid == 0) set_error(p.ctl, EPROTO, (int)t, -1, 5);
+            __syncthreads();
+            break;
+        }
+        const TaskRec rec = p.tasks[t];
+        int st = 0;
+        switch (rec.kind) {
+        case kScalF32: scal_item(rec, it); break;
+        case kPotrf: {
+            const int info = potrf_tile((double *)rec.buf[0], (int)rec.n, (double *)smem, &s_info);
+            if (info) st = rec.aux + info;
+            break;
+        }
+        case kTrsm: trsm_item(rec, it, (double *)smem); break;
+        case kSyrk: syrk_item(rec, it, (double *)smem); break;
+        case kGemm: gemm_item(rec, it, (double *)smem); break;
+        case kPotrfMx: {
+            const int info = potrf_mx_item(rec, (double *)smem, &s_info);
+            if (info) st = rec.aux + info;
+            break;
+        }
+        case kTrsmMx: trsm_mx_item(rec, it, (double *)smem); break;
+        case kQuant: quant_item(rec, s_red, &s_e); break;
+        case kSyrkMx:
+        case kGemmMx:
+            if (!p.has_mx) { st = -EPROTO; break; }
+            if (mx_update_item(rec, it, rec.kind == kSyrkMx, mx, p.timeout_ns, &s_fail)) st = -ETIMEDOUT;
+            break;
+        default: break;   // NOOP
+        }
+        __syncthreads();
+        if (tid == 0) {
+            if (st > 0) {
+                set_error(p.ctl, EDOM, (int)t, st, 0);   // not positive definite: no retire
+                s_flag = 0;
+            } else if (st < 0) {
+                set_error(p.ctl, -st, (int)t, -1, 6);
+                s_flag = 0;
+            } else {
+                __threadfence();
+                const int d = atomicAdd(&p.done_items[t], 1) + 1;
+                s_flag = (d == rec.nitems);
+            }
+        }
+        __syncthreads();
+        if (s_flag && warp == 0) retire(p, t, rec);
+    }
+
+    if (p.has_mx) {
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (warp == 0) tmem_dealloc(mx.tmem, kTmemCols);
+    }
+}
+
+__global__ void init_kernel(const InitParams ip, const LaunchParams lp) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = gid; i < ip.ntasks; i += stride) {
+        ip.counters[i] = ip.indeg[i];
+        ip.done_items[i] = 0;
+    }
+    for (int64_t i = gid; i < (int64_t)ip.nslots; i += stride) {
+        int l = 0;
+        while (l + 1 < ip.nlevels && (unsigned long long)i >= lp.ring_off[l + 1]) ++l;
+        const unsigned long long k = (unsigned long long)i - lp.ring_off[l];
+        ip.slots[i] = k < ip.root_cnt[l] ? ip.roots[ip.root_off[l] + k] : kEmpty;
+    }
+    if (gid == 0) {
+        for (int l = 0; l < kMaxLevels; ++l) {
+            ip.ctl->lvl[l].head = 0;
+            ip.ctl->lvl[l].tail = l < ip.nlevels ? ip.root_cnt[l] : 0;
+        }
+        ip.ctl->retired = 0;
+    }
+}
+
+}  // namespace b3t
+
+using namespace b3t;
+
+extern "C" size_t b3t_internal_smem_bytes(int has_mx) {
+    (void)has_mx;
+    return kSmemData + 1024;
+}
+
+extern "C" int b3t_internal_occupancy(int *ctas_per_sm, size_t smem, int *num_sms) {
+    if (cudaFuncSetAttribute(exec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return -EIO;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -EIO;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, exec_kernel, kThreads, smem) != cudaSuccess)
+        return -EIO;
+    return 0;
+}
+
+extern "C" int b3t_internal_launch(const InitParams *ip, const LaunchParams *lp, int nctas, size_t smem,
+                                   void *stream, void *ev_start, void *ev_stop) {
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t work = ip->ntasks > (int64_t)ip->nslots ? ip->ntasks : (int64_t)ip->nslots;
+    int ib = (int)((work + 255) / 256);
+    ib = ib < 1 ? 1 : (ib > 4096 ? 4096 : ib);
+    init_kernel<<<ib, 256, 0, s>>>(*ip, *lp);
+    if (ev_start) cudaEventRecord((cudaEvent_t)ev_start, s);
+    exec_kernel<<<nctas, kThreads, smem, s>>>(*lp);
+    if (ev_stop) cudaEventRecord((cudaEvent_t)ev_stop, s);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? 0 : -EIO;
+}

@@ -1,0 +1,324 @@
+// Mixed-precision tile bodies: quantisation of a panel tile and the
+// low-precision trailing update on the tcgen05 tensor cores.
+//
+// Q tile layout (written by QUANT, read by the updates): a b x b tile is cut
+// into 16 KiB chunks of 128 rows x 128 bytes of K; chunk (rb, kb) sits at
+// (rb * nk + kb) * 16 KiB with nk = b * esize / 128.  Inside a chunk row r
+// takes 128 bytes at r * 128 and its 16-byte group g is stored at group
+// position g ^ (r % 8): the 128-byte swizzled, K-major operand layout of the
+// tensor cores, so one bulk copy of a chunk into a 1024-byte aligned shared
+// buffer is directly an MMA operand.  After the data: int32 scale exponent e
+// (scale 2^e).
+//
+// Update item (SYRK_MX / GEMM_MX): a 128 x 128 block of the binary32 tile W,
+//   W <- fl32(W - 2^(ea+eb) * QA QB^T),
+// QA = rows 128*bi.. of the first operand, QB = rows 128*bj.. of the second.
+// One thread issues bulk copies (cp.async.bulk, completion on an mbarrier)
+// into a 3-stage ring and the MMAs (M = 128, N = 128, 4 per 128-byte K
+// chunk); the accumulator lives in tensor memory (128 columns) and all eight
+// warps read it back for the epilogue.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include "b3t_internal.h"
+
+namespace b3t {
+
+constexpr int kMxStages = 3;
+constexpr uint32_t kChunkBytes = 16384;
+constexpr uint32_t kTmemCols = 128;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred P1;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, P1;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false if the phase did not complete within limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int64_t limit_ns) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = gtimer();
+    for (uint32_t n = 0;; ++n) {
+        if (mbar_try(bar, parity)) return true;
+        if ((n & 255) == 255 && (int64_t)(gtimer() - t0) > limit_ns) return false;
+    }
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// tcgen05 shared-memory matrix descriptor: K-major operand, 128-byte swizzle,
+// 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);          // start address
+    d |= (uint64_t)1 << 16;                          // leading byte offset (unused here)
+    d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset
+    d |= (uint64_t)1 << 46;                          // descriptor version
+    d |= (uint64_t)2 << 61;                          // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: f32 accumulate, K-major A and B, M = 128, N = 128;
+// operand format 1 = bf16 (kind::f16) or 0 = E4M3 (kind::f8f6f4).
+__host__ __device__ constexpr uint32_t mx_idesc(uint32_t opfmt) {
+    return (1u << 4) | (opfmt << 7) | (opfmt << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_e4m3(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+        "[%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// Per-CTA state of the tensor-core pipeline, persistent across items.
+struct MxState {
+    uint64_t *full;       // [kMxStages]
+    uint64_t *empty;      // [kMxStages]
+    uint64_t *done;       // [1]
+    unsigned char *stage; // kMxStages x 32 KiB, 1024-aligned
+    uint32_t tmem;        // accumulator base address
+    uint32_t fills;       // stage fills issued so far (thread 0)
+    uint32_t items;       // items completed so far (all threads)
+};
+
+// Smallest e with amax <= 448 * 2^e (exact comparisons); 0 for amax = 0.
+__device__ __forceinline__ int e4m3_scale_exp(double amax) {
+    if (!(amax > 0.0)) return 0;
+    int e = ilogb(amax) - 8;
+    while (amax > ldexp(448.0, e)) ++e;
+    while (amax <= ldexp(448.0, e - 1)) --e;
+    return e;
+}
+
+__device__ __forceinline__ int q_esize(int fmt) { return fmt == 0 ? 2 : 1; }
+
+// QUANT: L (f64 tile) -> Q (layout above).  One work item per tile.
+__device__ __forceinline__ void quant_item(const TaskRec &t, double *red, int *s_e) {
+    const double *L = (const double *)t.buf[0];
+    unsigned char *Q = (unsigned char *)t.buf[1];
+    const int b = (int)t.n, fmt = t.aux, es = q_esize(fmt);
+    const int tid = threadIdx.x;
+    if (fmt == 1) {
+        double m = 0.0;
+        for (size_t i = tid; i < (size_t)b * b; i += kThreads) m = fmax(m, fabs(L[i]));
+        for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((tid & 31) == 0) red[tid >> 5] = m;
+        __syncthreads();
+        if (tid == 0) {
+            double a = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) a = fmax(a, red[w]);
+            *s_e = e4m3_scale_exp(a);
+        }
+    } else if (tid == 0) {
+        *s_e = 0;
+    }
+    __syncthreads();
+    const int e = *s_e;
+    const int G = 16 / es;                  // values per 16-byte group
+    const int cpc = 128 / es;               // K values per chunk
+    const int nk = b / cpc;
+    const size_t npairs = (size_t)b * (b / G);
+    for (size_t p = tid; p < npairs; p += kThreads) {
+        const int r = (int)(p % b), gg = (int)(p / b);
+        const int c0 = gg * G, kb = c0 / cpc, g = (c0 % cpc) / G;
+        const int rb = r >> 7, rr = r & 127;
+        uint32_t w[4];
+        if (fmt == 0) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float lo = (float)L[(size_t)r + (size_t)(c0 + 2 * j) * b];
+                const float hi = (float)L[(size_t)r + (size_t)(c0 + 2 * j + 1) * b];
+                __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+                w[j] = *reinterpret_cast<uint32_t *>(&h);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                uint32_t word = 0;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    float2 f;
+                    f.x = (float)ldexp(L[(size_t)r + (size_t)(c0 + 4 * j + 2 * h) * b], -e);
+                    f.y = (float)ldexp(L[(size_t)r + (size_t)(c0 + 4 * j + 2 * h + 1) * b], -e);
+                    const __nv_fp8x2_storage_t q = __nv_cvt_float2_to_fp8x2(f, __NV_SATFINITE, __NV_E4M3);
+                    word |= (uint32_t)q << (16 * h);
+                }
+                w[j] = word;
+            }
+        }
+        unsigned char *dst = Q + ((size_t)rb * nk + kb) * kChunkBytes + (size_t)rr * 128 + ((g ^ (rr & 7)) << 4);
+        *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    if (tid == 0) {
+        int *tr = (int *)(Q + (size_t)b * b * es);
+        tr[0] = e; tr[1] = 0; tr[2] = 0; tr[3] = 0;
+    }
+}
+
+// SYRK_MX (syrk = true, lower blocks only) / GEMM_MX update of one 128 x 128
+// block.  Returns 0, or ETIMEDOUT when a pipeline wait ran out.
+__device__ __forceinline__ int mx_update_item(const TaskRec &t, int item, bool syrk, MxState &st,
+                                              int64_t limit_ns, int *s_fail) {
+    const int b = (int)t.n, fmt = t.aux, es = q_esize(fmt);
+    const unsigned char *QA = (const unsigned char *)t.buf[0];
+    const unsigned char *QB = syrk ? QA : (const unsigned char *)t.buf[1];
+    float *W = (float *)(syrk ? t.buf[1] : t.buf[2]);
+    int bi, bj;
+    if (syrk) {
+        int i = (int)((sqrtf(8.0f * item + 1.0f) - 1.0f) * 0.5f);
+        while ((i + 1) * (i + 2) / 2 <= item) ++i;
+        while (i * (i + 1) / 2 > item) --i;
+        bi = i; bj = item - i * (i + 1) / 2;
+    } else {
+        const int m = b / kMxBlk;
+        bi = item / m; bj = item % m;
+    }
+    const int nk = b * es / 128;
+    const uint32_t idesc = mx_idesc(fmt == 0 ? 1u : 0u);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        *s_fail = 0;
+        // make generic-proxy writes of the producer tasks visible to the bulk copies
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        tc_fence_after();
+        uint32_t issued = 0;
+        const uint32_t G = st.fills;
+        bool fail = false;
+        for (int kk = 0; kk < nk && !fail; ++kk) {
+            while ((int)issued < nk && (int)issued < kk + kMxStages) {
+                const uint32_t g = G + issued, slot = g % kMxStages;
+                if (g >= (uint32_t)kMxStages && !mbar_wait(&st.empty[slot], ((g / kMxStages) - 1) & 1, limit_ns)) {
+                    fail = true;
+                    break;
+                }
+                unsigned char *sa = st.stage + slot * 2 * kChunkBytes;
+                mbar_expect_tx(&st.full[slot], 2 * kChunkBytes);
+                bulk_g2s(sa, QA + ((size_t)bi * nk + issued) * kChunkBytes, kChunkBytes, &st.full[slot]);
+                bulk_g2s(sa + kChunkBytes, QB + ((size_t)bj * nk + issued) * kChunkBytes, kChunkBytes,
+                         &st.full[slot]);
+                ++issued;
+            }
+            if (fail) break;
+            const uint32_t g = G + kk, slot = g % kMxStages;
+            if (!mbar_wait(&st.full[slot], (g / kMxStages) & 1, limit_ns)) { fail = true; break; }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(st.stage + slot * 2 * kChunkBytes);
+            const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + kChunkBytes);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                // advance 32 bytes of K per MMA inside the swizzle atom
+                if (fmt == 0) mma_bf16(st.tmem, ad + 2 * i, bd + 2 * i, idesc, (kk | i) ? 1u : 0u);
+                else mma_e4m3(st.tmem, ad + 2 * i, bd + 2 * i, idesc, (kk | i) ? 1u : 0u);
+            }
+            mma_commit(&st.empty[slot]);
+        }
+        if (fail) {
+            *s_fail = 1;
+            // let copies already issued land before shared memory is reused
+            for (uint32_t k2 = 0; k2 < issued; ++k2) {
+                const uint32_t g = G + k2;
+                mbar_wait(&st.full[g % kMxStages], (g / kMxStages) & 1, limit_ns);
+            }
+        }
+        st.fills = G + issued;
+        mma_commit(st.done);
+    }
+    __syncthreads();
+    const bool ok = mbar_wait(st.done, st.items & 1, limit_ns);
+    st.items++;
+    tc_fence_after();
+    if (*s_fail || !ok) return ETIMEDOUT;
+    // epilogue: warp w reads TMEM lanes 32*(w%4).. and columns 64*(w/4)..
+    const int warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, h = warp >> 2;
+    float s = 1.0f;
+    if (fmt == 1) {
+        const int ea = *(const int *)(QA + (size_t)b * b * es);
+        const int eb = *(const int *)(QB + (size_t)b * b * es);
+        s = ldexpf(1.0f, ea + eb);
+    }
+    const int gr = bi * kMxBlk + 32 * q + lane;
+#pragma unroll 1
+    for (int i = 0; i < 4; ++i) {
+        float v[16];
+        tmem_ld16(st.tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * 64 + 16 * i), v);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            const int gc = bj * kMxBlk + h * 64 + 16 * i + c;
+            if (!syrk || gr >= gc) {
+                float *p = W + (size_t)gr + (size_t)gc * b;
+                *p = fmaf(-s, v[c], *p);
+            }
+        }
+    }
+    tc_fence_before();
+    return 0;
+}
+
+}  // namespace b3t

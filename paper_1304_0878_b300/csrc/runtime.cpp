@@ -1,0 +1,932 @@
+// Host side of the b3t C ABI: handles, codelets, dependency derivation,
+// task-table build, launch, wait and graph capture.
+//
+// The model (Section 2 of the paper): tasks with declared implementations and
+// per-buffer access modes; registered buffers; asynchronous invocation; the
+// dependency graph follows from the access modes and the invocation order;
+// a wait joins everything.  Submissions accumulate in a pending batch; a
+// flush turns the batch into one task table + CSR successor graph and runs
+// it in one persistent-kernel launch on the context's stream.
+#include "b3t.h"
+#include "b3t_internal.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cerrno>
+#include <chrono>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+using namespace b3t;
+
+namespace {
+
+struct Handle {
+    void *ptr = nullptr;
+    size_t nelems = 0, elemsize = 0;
+    int64_t ld = 0;
+    bool alive = false;
+    int32_t parent = -1;
+    std::vector<int32_t> parts;
+    // dependency state of a leaf within the pending batch
+    int32_t last_writer = -1;
+    std::vector<int32_t> readers;
+    bool touched = false;
+};
+
+struct Codelet {
+    std::string name;
+    int kind = 0;
+    int nbuf = 0;
+    uint8_t modes[kMaxBuffers] = {0, 0, 0, 0};
+    size_t scalar_bytes = 0;
+};
+
+struct Pending {
+    TaskRec rec;
+    float cost;
+};
+
+// Device arena of one launch (task table, graph, counters, rings, status).
+struct Arena {
+    TaskRec *tasks = nullptr;  size_t cap_tasks = 0;
+    int32_t *succ = nullptr;   size_t cap_succ = 0;
+    int32_t *indeg = nullptr;  int32_t *counters = nullptr; int32_t *done = nullptr;
+    size_t cap_cnt = 0;
+    unsigned long long *slots = nullptr; size_t cap_slots = 0;
+    unsigned long long *roots = nullptr; size_t cap_roots = 0;
+    Ctl *ctl = nullptr;
+
+    void release() {
+        cudaFree(tasks); cudaFree(succ); cudaFree(indeg); cudaFree(counters);
+        cudaFree(done); cudaFree(slots); cudaFree(roots); cudaFree(ctl);
+        *this = Arena();
+    }
+};
+
+template <class T>
+int grow(T *&p, size_t &cap, size_t need) {
+    if (need <= cap && p) return 0;
+    size_t n = std::max<size_t>(need, std::max<size_t>(cap * 2, 64));
+    if (p) { cudaFree(p); p = nullptr; cap = 0; }
+    if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) { p = nullptr; return -ENOMEM; }
+    cap = n;
+    return 0;
+}
+
+struct GraphRec {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    Arena arena;
+    int64_t ntasks = 0, nitems = 0;
+    int nctas = 0;
+    bool alive = false;
+};
+
+// Signature of each kind: buffers, modes, element sizes, scalar blob size.
+struct KindSig {
+    int nbuf;
+    uint8_t modes[kMaxBuffers];
+    int elem[kMaxBuffers];     // element size in bytes; 1 = quantised tile
+    size_t scalar_bytes;
+    bool tile;
+};
+
+const KindSig kSigs[kNumKinds] = {
+    /* NOOP     */ {-1, {0, 0, 0, 0}, {0, 0, 0, 0}, 0, false},
+    /* SCAL_F32 */ {1, {B3T_RW}, {4}, 4, false},
+    /* POTRF    */ {1, {B3T_RW}, {8}, 4, true},
+    /* TRSM     */ {2, {B3T_R, B3T_RW}, {8, 8}, 0, true},
+    /* SYRK     */ {2, {B3T_R, B3T_RW}, {8, 8}, 0, true},
+    /* GEMM     */ {3, {B3T_R, B3T_R, B3T_RW}, {8, 8, 8}, 0, true},
+    /* POTRF_MX */ {2, {B3T_R, B3T_W}, {4, 8}, 4, true},
+    /* TRSM_MX  */ {3, {B3T_R, B3T_R, B3T_W}, {8, 4, 8}, 0, true},
+    /* SYRK_MX  */ {2, {B3T_R, B3T_RW}, {1, 4}, 4, true},
+    /* GEMM_MX  */ {3, {B3T_R, B3T_R, B3T_RW}, {1, 1, 4}, 4, true},
+    /* QUANT    */ {2, {B3T_R, B3T_W}, {8, 1}, 4, true},
+};
+
+const char *kKindNames[kNumKinds] = {"noop", "scal_f32", "potrf", "trsm", "syrk", "gemm",
+                                     "potrf_mx", "trsm_mx", "syrk_mx", "gemm_mx", "quant"};
+
+bool is_mx(int kind) { return kind == kSyrkMx || kind == kGemmMx; }
+bool has_fmt(int kind) { return kind == kSyrkMx || kind == kGemmMx || kind == kQuant; }
+
+int64_t items_of(int kind, int64_t n) {
+    switch (kind) {
+    case kScalF32: return std::max<int64_t>(1, (n + kScalChunk - 1) / kScalChunk);
+    case kPotrf: case kPotrfMx: case kQuant: case kNoop: return 1;
+    case kTrsm: case kTrsmMx: return n / kTrsmRows;
+    case kSyrk: { int64_t m = n / kGemmBlk; return m * (m + 1) / 2; }
+    case kGemm: { int64_t m = n / kGemmBlk; return m * m; }
+    case kSyrkMx: { int64_t m = n / kMxBlk; return m * (m + 1) / 2; }
+    case kGemmMx: { int64_t m = n / kMxBlk; return m * m; }
+    }
+    return 1;
+}
+
+// Rough device time of a task in ns on one CTA, only used to rank tasks by
+// their distance to the end of the graph (upward rank, the scheduling hint
+// Section 5.3 of the paper proposes).
+float cost_of(int kind, int64_t n) {
+    double b = (double)n;
+    const double fp64 = 3.7;   // flop / ns per CTA (FP64 DFMA, 2 CTAs / SM)
+    const double mx = 2000.0;  // flop / ns per CTA (tensor cores)
+    switch (kind) {
+    case kScalF32: return (float)(8.0 * b / 20.0);
+    case kPotrf: case kPotrfMx: return (float)(b * b * b / 3.0 / fp64);
+    case kTrsm: case kTrsmMx: return (float)(b * b * b / fp64);
+    case kSyrk: return (float)(b * b * b / fp64);
+    case kGemm: return (float)(2.0 * b * b * b / fp64);
+    case kSyrkMx: return (float)(b * b * b / mx + 4.0 * b * b / 20.0);
+    case kGemmMx: return (float)(2.0 * b * b * b / mx + 8.0 * b * b / 20.0);
+    case kQuant: return (float)(10.0 * b * b / 20.0);
+    }
+    return 1000.0f;
+}
+
+size_t q_bytes(int b, int fmt) {
+    size_t elems = (size_t)b * b;
+    return (fmt == B3T_FMT_BF16 ? elems * 2 : elems) + 16;
+}
+
+}  // namespace
+
+struct b3t_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    b3t_config cfg{};
+    std::vector<Handle> handles;
+    std::unordered_map<uintptr_t, int32_t> by_ptr;
+    std::vector<Codelet> codelets;
+    std::vector<Pending> tasks;
+    std::vector<std::pair<int32_t, int32_t>> edges;
+    std::vector<int32_t> extra_deps;        // phantom predecessors (tests)
+    std::vector<int32_t> touched;
+    bool capturing = false;
+    Arena arena;
+    // pinned staging for uploads, reused once the previous copy completed
+    void *staging = nullptr; size_t staging_cap = 0;
+    cudaEvent_t staging_done = nullptr;
+    // pinned mirrors of the status blocks of launches since the last wait
+    std::vector<Ctl *> mirrors;
+    std::vector<std::pair<Ctl *, Ctl *>> inflight;   // (device ctl, mirror)
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int64_t last_ntasks = 0, last_nitems = 0;
+    int last_nctas = 0;
+    bool last_timed = false;
+    int32_t err_task = -1, err_info = -1;
+    std::vector<GraphRec> graphs;
+    b3t_codelet kind_cl[kNumKinds];
+};
+
+namespace {
+
+int cuda_err(cudaError_t e) {
+    if (e == cudaSuccess) return 0;
+    if (e == cudaErrorMemoryAllocation) return -ENOMEM;
+    return -EIO;
+}
+
+void reset_dep_state(b3t_ctx *c) {
+    for (int32_t h : c->touched) {
+        Handle &H = c->handles[h];
+        H.last_writer = -1;
+        H.readers.clear();
+        H.touched = false;
+    }
+    c->touched.clear();
+}
+
+// Section 2: access modes + invocation order -> RAW / WAR / WAW edges.
+void derive(b3t_ctx *c, int32_t t, const int32_t *leaves, const uint8_t *modes, int n,
+            std::vector<int32_t> &preds) {
+    preds.clear();
+    for (int i = 0; i < n; ++i) {
+        Handle &H = c->handles[leaves[i]];
+        if (!H.touched) { H.touched = true; c->touched.push_back(leaves[i]); }
+        if (modes[i] & B3T_W) {
+            if (!H.readers.empty()) {
+                for (int32_t r : H.readers) if (r != t) preds.push_back(r);
+            } else if (H.last_writer >= 0 && H.last_writer != t) {
+                preds.push_back(H.last_writer);
+            }
+            H.last_writer = t;
+            H.readers.clear();
+        } else {
+            if (H.last_writer >= 0 && H.last_writer != t) preds.push_back(H.last_writer);
+            H.readers.push_back(t);
+        }
+    }
+    std::sort(preds.begin(), preds.end());
+    preds.erase(std::unique(preds.begin(), preds.end()), preds.end());
+}
+
+// Build the task table, CSR graph, ready rings and root lists of the pending
+// batch into arena `a` (uploaded through the pinned staging buffer on the
+// context's stream) and fill the launch parameters.
+int build_launch(b3t_ctx *c, Arena &a, InitParams &ip, LaunchParams &lp, int64_t &nitems_out,
+                 bool &has_mx) {
+    const int64_t nt = (int64_t)c->tasks.size();
+    const int64_t ne = (int64_t)c->edges.size();
+    const int L = c->cfg.prio_levels;
+    std::vector<int32_t> off(nt + 1, 0), indeg(nt, 0);
+    for (auto &e : c->edges) { off[e.first + 1]++; indeg[e.second]++; }
+    for (int64_t t = 0; t < nt; ++t) off[t + 1] += off[t];
+    const int64_t ne_pad = std::max<int64_t>(ne, 1);
+    // device layout of the succ buffer: [successors (ne_pad)] [level (nt)]
+    std::vector<int32_t> succ_lv(ne_pad + nt, 0);
+    {
+        std::vector<int32_t> pos(off.begin(), off.end() - 1);
+        for (auto &e : c->edges) succ_lv[pos[e.first]++] = e.second;
+    }
+    for (int64_t t = 0; t < nt && t < (int64_t)c->extra_deps.size(); ++t) indeg[t] += c->extra_deps[t];
+    // upward rank -> priority level (higher level = closer to the critical path)
+    std::vector<float> rank(nt, 0.f);
+    float maxr = 0.f;
+    for (int64_t t = nt - 1; t >= 0; --t) {
+        float m = 0.f;
+        for (int32_t k = off[t]; k < off[t + 1]; ++k) m = std::max(m, rank[succ_lv[k]]);
+        rank[t] = c->tasks[t].cost + m;
+        maxr = std::max(maxr, rank[t]);
+    }
+    unsigned long long cap[kMaxLevels] = {0}, rootcnt[kMaxLevels] = {0};
+    int64_t nitems = 0;
+    has_mx = false;
+    for (int64_t t = 0; t < nt; ++t) {
+        TaskRec &r = c->tasks[t].rec;
+        r.succ_off = off[t];
+        r.nsucc = off[t + 1] - off[t];
+        int lv = 0;
+        if (L > 1 && maxr > 0.f) lv = std::min(L - 1, (int)((double)L * rank[t] / (maxr * 1.000001)));
+        succ_lv[ne_pad + t] = lv;
+        cap[lv] += r.nitems;
+        if (indeg[t] == 0) rootcnt[lv] += r.nitems;
+        nitems += r.nitems;
+        if (is_mx(r.kind)) has_mx = true;
+    }
+    unsigned long long ringoff[kMaxLevels] = {0}, rootoff[kMaxLevels] = {0};
+    unsigned long long nslots = 0, nroots = 0;
+    for (int l = 0; l < L; ++l) {
+        ringoff[l] = nslots; nslots += cap[l];
+        rootoff[l] = nroots; nroots += rootcnt[l];
+    }
+    std::vector<unsigned long long> roots(std::max<unsigned long long>(nroots, 1), kEmpty);
+    {
+        unsigned long long fill[kMaxLevels];
+        for (int l = 0; l < L; ++l) fill[l] = rootoff[l];
+        for (int64_t t = 0; t < nt; ++t)
+            if (indeg[t] == 0) {
+                const int lv = succ_lv[ne_pad + t];
+                for (int32_t it = 0; it < c->tasks[t].rec.nitems; ++it) roots[fill[lv]++] = pack_item(t, it);
+            }
+    }
+    int rc;
+    if ((rc = grow(a.tasks, a.cap_tasks, nt))) return rc;
+    if ((rc = grow(a.succ, a.cap_succ, succ_lv.size()))) return rc;
+    if ((size_t)nt > a.cap_cnt || !a.indeg) {
+        size_t n = std::max<size_t>(nt, std::max<size_t>(a.cap_cnt * 2, 64));
+        cudaFree(a.indeg); cudaFree(a.counters); cudaFree(a.done);
+        a.indeg = a.counters = a.done = nullptr; a.cap_cnt = 0;
+        if (cudaMalloc(&a.indeg, n * 4) != cudaSuccess || cudaMalloc(&a.counters, n * 4) != cudaSuccess ||
+            cudaMalloc(&a.done, n * 4) != cudaSuccess)
+            return -ENOMEM;
+        a.cap_cnt = n;
+    }
+    if ((rc = grow(a.slots, a.cap_slots, std::max<unsigned long long>(nslots, 1)))) return rc;
+    if ((rc = grow(a.roots, a.cap_roots, roots.size()))) return rc;
+    if (!a.ctl) {
+        if (cudaMalloc(&a.ctl, sizeof(Ctl)) != cudaSuccess) return -ENOMEM;
+        if ((rc = cuda_err(cudaMemsetAsync(a.ctl, 0, sizeof(Ctl), c->stream)))) return rc;
+    }
+    // staging: tasks | succ_lv | indeg | roots
+    const size_t o_t = 0, o_s = o_t + nt * sizeof(TaskRec), o_i = o_s + succ_lv.size() * 4,
+                 o_r = (o_i + nt * 4 + 15) / 16 * 16, bytes = o_r + roots.size() * 8;
+    if (c->staging) cudaEventSynchronize(c->staging_done);
+    if (bytes > c->staging_cap) {
+        if (c->staging) cudaFreeHost(c->staging);
+        c->staging = nullptr;
+        const size_t cap2 = std::max(bytes, c->staging_cap * 2);
+        if (cudaMallocHost(&c->staging, cap2) != cudaSuccess) { c->staging_cap = 0; return -ENOMEM; }
+        c->staging_cap = cap2;
+    }
+    char *s = (char *)c->staging;
+    for (int64_t t = 0; t < nt; ++t) std::memcpy(s + o_t + t * sizeof(TaskRec), &c->tasks[t].rec, sizeof(TaskRec));
+    std::memcpy(s + o_s, succ_lv.data(), succ_lv.size() * 4);
+    std::memcpy(s + o_i, indeg.data(), nt * 4);
+    std::memcpy(s + o_r, roots.data(), roots.size() * 8);
+    cudaMemcpyAsync(a.tasks, s + o_t, nt * sizeof(TaskRec), cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(a.succ, s + o_s, succ_lv.size() * 4, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(a.indeg, s + o_i, nt * 4, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(a.roots, s + o_r, roots.size() * 8, cudaMemcpyHostToDevice, c->stream);
+    if ((rc = cuda_err(cudaEventRecord(c->staging_done, c->stream)))) return rc;
+
+    ip = InitParams{};
+    ip.indeg = a.indeg; ip.counters = a.counters; ip.done_items = a.done;
+    ip.slots = a.slots; ip.nslots = nslots; ip.roots = a.roots; ip.ctl = a.ctl;
+    ip.ntasks = nt; ip.nlevels = L;
+    lp = LaunchParams{};
+    lp.tasks = a.tasks; lp.succ = a.succ; lp.level = a.succ + ne_pad;
+    lp.counters = a.counters; lp.done_items = a.done;
+    lp.slots = a.slots; lp.ctl = a.ctl; lp.ntasks = nt; lp.nlevels = L;
+    lp.has_mx = has_mx ? 1 : 0;
+    lp.timeout_ns = c->cfg.timeout_ns;
+    lp.debug = c->cfg.debug_checks;
+    for (int l = 0; l < L; ++l) {
+        ip.root_off[l] = rootoff[l]; ip.root_cnt[l] = rootcnt[l];
+        lp.ring_off[l] = ringoff[l]; lp.ring_cap[l] = cap[l];
+    }
+    nitems_out = nitems;
+    return 0;
+}
+
+int grid_for(b3t_ctx *c, bool has_mx, int *nctas, size_t *smem) {
+    *smem = b3t_internal_smem_bytes(has_mx ? 1 : 0);
+    int per_sm = 0, sms = 0;
+    int rc = b3t_internal_occupancy(&per_sm, *smem, &sms);
+    if (rc) return rc;
+    if (c->cfg.ctas_per_sm > 0) per_sm = std::min(per_sm, c->cfg.ctas_per_sm);
+    if (per_sm < 1) return -EINVAL;
+    *nctas = per_sm * sms;
+    return 0;
+}
+
+void clear_batch(b3t_ctx *c) {
+    c->tasks.clear();
+    c->edges.clear();
+    c->extra_deps.clear();
+    reset_dep_state(c);
+}
+
+// Queue a device->host copy of a launch's status block into a pinned mirror.
+int track(b3t_ctx *c, Ctl *dev) {
+    if (c->inflight.size() == c->mirrors.size()) {
+        Ctl *m = nullptr;
+        if (cudaMallocHost(&m, sizeof(Ctl)) != cudaSuccess) return -ENOMEM;
+        std::memset(m, 0, sizeof(Ctl));
+        c->mirrors.push_back(m);
+    }
+    Ctl *m = c->mirrors[c->inflight.size()];
+    c->inflight.emplace_back(dev, m);
+    return cuda_err(cudaMemcpyAsync(m, dev, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+}
+
+int flush_impl(b3t_ctx *c) {
+    if (c->tasks.empty()) return 0;
+    InitParams ip; LaunchParams lp; int64_t nitems; bool has_mx;
+    int rc = build_launch(c, c->arena, ip, lp, nitems, has_mx);
+    if (rc) { clear_batch(c); return rc; }
+    int nctas; size_t smem;
+    if ((rc = grid_for(c, has_mx, &nctas, &smem))) { clear_batch(c); return rc; }
+    rc = b3t_internal_launch(&ip, &lp, nctas, smem, c->stream, c->ev0, c->ev1);
+    c->last_ntasks = (int64_t)c->tasks.size();
+    c->last_nitems = nitems;
+    c->last_nctas = nctas;
+    c->last_timed = true;
+    const int r2 = track(c, c->arena.ctl);
+    clear_batch(c);
+    return rc ? rc : r2;
+}
+
+int sync_stream(b3t_ctx *c, int64_t timeout_ns) {
+    if (timeout_ns <= 0) return cuda_err(cudaStreamSynchronize(c->stream));
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const cudaError_t e = cudaStreamQuery(c->stream);
+        if (e == cudaSuccess) return 0;
+        if (e != cudaErrorNotReady) return cuda_err(e);
+        const auto dt = std::chrono::duration_cast<std::chrono::nanoseconds>(
+                            std::chrono::steady_clock::now() - t0).count();
+        if (dt > timeout_ns) return -ETIMEDOUT;
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+// After a stream sync: the first error reported by any launch since the last
+// wait; sticky device errors are cleared for the launches that follow.
+int read_status(b3t_ctx *c) {
+    int first = 0;
+    static const int32_t zero[4] = {0, -1, -1, 0};
+    for (auto &f : c->inflight) {
+        Ctl &s = *f.second;
+        if (s.error) {
+            if (!first) {
+                first = -s.error;
+                c->err_task = s.err_task;
+                c->err_info = s.err_info;
+            }
+            cudaMemcpy(f.first, zero, sizeof(zero), cudaMemcpyHostToDevice);
+            s.error = 0;
+        }
+    }
+    c->inflight.clear();
+    return first;
+}
+
+int wait_impl(b3t_ctx *c, int64_t timeout_ns) {
+    int rc = flush_impl(c);
+    const int rs = sync_stream(c, timeout_ns);
+    if (rs) return rs;
+    const int st = read_status(c);
+    return rc ? rc : st;
+}
+
+int check_handle(b3t_ctx *c, b3t_handle h) {
+    if (h < 0 || h >= (int32_t)c->handles.size() || !c->handles[h].alive) return -ENOENT;
+    return 0;
+}
+
+int submit_impl(b3t_ctx *c, b3t_codelet cl, const b3t_handle *handles, const uint8_t *modes,
+                int nbuffers, const void *scalars, size_t scalar_bytes) {
+    if (!c || cl < 0 || cl >= (int32_t)c->codelets.size()) return -EINVAL;
+    const Codelet &C = c->codelets[cl];
+    if (nbuffers != C.nbuf || scalar_bytes != C.scalar_bytes) return -EINVAL;
+    if (scalar_bytes && !scalars) return -EINVAL;
+    if (nbuffers && !handles) return -EINVAL;
+    for (int i = 0; i < nbuffers; ++i) {
+        const int rc = check_handle(c, handles[i]);
+        if (rc) return rc;
+        if (modes && modes[i] != C.modes[i]) return -EINVAL;
+    }
+    const KindSig &S = kSigs[C.kind];
+    TaskRec r;
+    std::memset(&r, 0, sizeof(r));
+    r.kind = C.kind;
+    for (int i = 0; i < nbuffers; ++i) r.buf[i] = (uint64_t)(uintptr_t)c->handles[handles[i]].ptr;
+    if (C.kind == kScalF32) {
+        const Handle &H = c->handles[handles[0]];
+        if (H.elemsize != 4 || r.buf[0] % 16) return -EINVAL;   // 128-bit accesses
+        r.n = (int64_t)H.nelems;
+        std::memcpy(&r.scal, scalars, 4);
+    } else if (S.tile) {
+        const int64_t b = c->handles[handles[0]].ld;
+        if (scalar_bytes == 4) std::memcpy(&r.aux, scalars, 4);
+        const int fmt = has_fmt(C.kind) ? r.aux : 0;
+        if (fmt != B3T_FMT_BF16 && fmt != B3T_FMT_E4M3) return -EINVAL;
+        if (b <= 0 || b % kGemmBlk || b > 4096) return -EINVAL;
+        if (C.kind >= kPotrfMx && b % kMxBlk) return -EINVAL;
+        for (int i = 0; i < nbuffers; ++i) {
+            const Handle &H = c->handles[handles[i]];
+            if (H.ld != b || r.buf[i] % 16) return -EINVAL;
+            if (S.elem[i] == 1) {
+                if (H.elemsize != 1 || H.nelems != q_bytes((int)b, fmt)) return -EINVAL;
+            } else if (H.elemsize != (size_t)S.elem[i] || H.nelems < (size_t)(b * b)) {
+                return -EINVAL;
+            }
+        }
+        r.n = b;
+    }
+    r.nitems = (int32_t)items_of(C.kind, r.n);
+    const int32_t t = (int32_t)c->tasks.size();
+    // expand partitioned parents to their parts; OR the modes of repeats
+    std::vector<int32_t> leaves;
+    std::vector<uint8_t> lmodes;
+    for (int i = 0; i < nbuffers; ++i) {
+        const Handle &H = c->handles[handles[i]];
+        const uint8_t m = C.modes[i];
+        auto add = [&](int32_t leaf) {
+            for (size_t k = 0; k < leaves.size(); ++k)
+                if (leaves[k] == leaf) { lmodes[k] |= m; return; }
+            leaves.push_back(leaf);
+            lmodes.push_back(m);
+        };
+        if (H.parts.empty()) add(handles[i]);
+        else for (int32_t k : H.parts) add(k);
+    }
+    std::vector<int32_t> preds;
+    derive(c, t, leaves.data(), lmodes.data(), (int)leaves.size(), preds);
+    for (int32_t p : preds) c->edges.emplace_back(p, t);
+    Pending P;
+    P.rec = r;
+    P.cost = cost_of(C.kind, r.n);
+    c->tasks.push_back(P);
+    return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t b3t_q_bytes(int b, int fmt) {
+    if (b <= 0 || b % kMxBlk || (fmt != B3T_FMT_BF16 && fmt != B3T_FMT_E4M3)) return 0;
+    return q_bytes(b, fmt);
+}
+
+int b3t_init(b3t_ctx **out, const b3t_config *cfg, void *cuda_stream) {
+    if (!out) return -EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) { cudaGetLastError(); return -ENODEV; }
+    b3t_ctx *c = new (std::nothrow) b3t_ctx();
+    if (!c) return -ENOMEM;
+    if (cfg) c->cfg = *cfg;
+    if (c->cfg.timeout_ns <= 0) c->cfg.timeout_ns = 10'000'000'000LL;
+    if (c->cfg.prio_levels <= 0) c->cfg.prio_levels = kMaxLevels;
+    c->cfg.prio_levels = std::min(c->cfg.prio_levels, kMaxLevels);
+    for (int k = 0; k < kNumKinds; ++k) c->kind_cl[k] = -1;
+    cudaGetDevice(&c->device);
+    c->stream = (cudaStream_t)cuda_stream;
+    if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->staging_done, cudaEventDisableTiming) != cudaSuccess) {
+        delete c;
+        return -EIO;
+    }
+    *out = c;
+    return 0;
+}
+
+int b3t_shutdown(b3t_ctx *c) {
+    if (!c) return -EINVAL;
+    const int rc = wait_impl(c, 0);
+    for (auto &g : c->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.graph) cudaGraphDestroy(g.graph);
+        g.arena.release();
+    }
+    c->arena.release();
+    if (c->staging) cudaFreeHost(c->staging);
+    for (Ctl *m : c->mirrors) cudaFreeHost(m);
+    cudaEventDestroy(c->ev0);
+    cudaEventDestroy(c->ev1);
+    cudaEventDestroy(c->staging_done);
+    delete c;
+    return rc;
+}
+
+int b3t_task_decl(b3t_ctx *c, const char *name, int kind, int nbuffers, const uint8_t *modes,
+                  size_t scalar_bytes, b3t_codelet *out) {
+    if (!c || !out || kind < 0 || kind >= kNumKinds) return -EINVAL;
+    if (nbuffers < 0 || nbuffers > kMaxBuffers || (nbuffers && !modes)) return -EINVAL;
+    const KindSig &s = kSigs[kind];
+    if (kind == kNoop) {
+        if (scalar_bytes != 0) return -EINVAL;
+        for (int i = 0; i < nbuffers; ++i) if (modes[i] < 1 || modes[i] > 3) return -EINVAL;
+    } else {
+        if (nbuffers != s.nbuf || scalar_bytes != s.scalar_bytes) return -EINVAL;
+        for (int i = 0; i < nbuffers; ++i) if (modes[i] != s.modes[i]) return -EINVAL;
+    }
+    Codelet cl;
+    cl.name = name ? name : "";
+    cl.kind = kind;
+    cl.nbuf = nbuffers;
+    for (int i = 0; i < nbuffers; ++i) cl.modes[i] = modes[i];
+    cl.scalar_bytes = scalar_bytes;
+    c->codelets.push_back(cl);
+    *out = (b3t_codelet)(c->codelets.size() - 1);
+    return 0;
+}
+
+int b3t_data_register(b3t_ctx *c, void *p, size_t nelems, size_t elemsize, int64_t ld,
+                      b3t_handle *out) {
+    if (!c || !out || !p || nelems == 0 || elemsize == 0 || ld < 0) return -EINVAL;
+    if (c->by_ptr.count((uintptr_t)p)) return -EEXIST;
+    Handle H;
+    H.ptr = p; H.nelems = nelems; H.elemsize = elemsize; H.ld = ld; H.alive = true;
+    c->handles.push_back(std::move(H));
+    const int32_t h = (int32_t)(c->handles.size() - 1);
+    c->by_ptr[(uintptr_t)p] = h;
+    *out = h;
+    return 0;
+}
+
+int b3t_data_lookup(b3t_ctx *c, const void *p, b3t_handle *out) {
+    if (!c || !out) return -EINVAL;
+    auto it = c->by_ptr.find((uintptr_t)p);
+    if (it == c->by_ptr.end()) return -ENOENT;
+    *out = it->second;
+    return 0;
+}
+
+int b3t_data_partition(b3t_ctx *c, b3t_handle parent, int32_t nparts, size_t part_nelems,
+                       b3t_handle *parts_out) {
+    if (!c || !parts_out || nparts <= 0 || part_nelems == 0) return -EINVAL;
+    int rc = check_handle(c, parent);
+    if (rc) return rc;
+    if (!c->handles[parent].parts.empty() || c->handles[parent].parent >= 0) return -EEXIST;
+    if ((size_t)nparts * part_nelems > c->handles[parent].nelems) return -EINVAL;
+    if (c->handles[parent].touched) return -EBUSY;
+    const size_t es = c->handles[parent].elemsize;
+    std::vector<int32_t> kids;
+    for (int32_t i = 0; i < nparts; ++i) {
+        Handle H;
+        H.ptr = (char *)c->handles[parent].ptr + (size_t)i * part_nelems * es;
+        H.nelems = part_nelems; H.elemsize = es; H.ld = 0; H.alive = true; H.parent = parent;
+        c->handles.push_back(std::move(H));
+        const int32_t h = (int32_t)(c->handles.size() - 1);
+        if (i > 0) c->by_ptr[(uintptr_t)c->handles[h].ptr] = h;   // part 0 shares the parent's address
+        kids.push_back(h);
+        parts_out[i] = h;
+    }
+    c->handles[parent].parts = kids;
+    return 0;
+}
+
+int b3t_task_submit(b3t_ctx *c, b3t_codelet cl, const b3t_handle *handles, const uint8_t *modes,
+                    int nbuffers, const void *scalars, size_t scalar_bytes) {
+    return submit_impl(c, cl, handles, modes, nbuffers, scalars, scalar_bytes);
+}
+
+int b3t_task_submit_ptrs(b3t_ctx *c, b3t_codelet cl, void *const *ptrs, int nbuffers,
+                         const void *scalars, size_t scalar_bytes) {
+    if (!c || nbuffers < 0 || nbuffers > kMaxBuffers || (nbuffers && !ptrs)) return -EINVAL;
+    b3t_handle hs[kMaxBuffers];
+    for (int i = 0; i < nbuffers; ++i) {
+        const int rc = b3t_data_lookup(c, ptrs[i], &hs[i]);
+        if (rc) return rc;
+    }
+    return submit_impl(c, cl, hs, nullptr, nbuffers, scalars, scalar_bytes);
+}
+
+int b3t_task_flush(b3t_ctx *c) {
+    if (!c) return -EINVAL;
+    if (c->capturing) return 0;
+    return flush_impl(c);
+}
+
+int b3t_task_wait(b3t_ctx *c, int64_t timeout_ns) {
+    if (!c) return -EINVAL;
+    if (c->capturing) return -EBUSY;
+    return wait_impl(c, timeout_ns);
+}
+
+int b3t_data_acquire(b3t_ctx *c, b3t_handle h, uint8_t mode) {
+    if (!c || mode < 1 || mode > 3) return -EINVAL;
+    const int rc = check_handle(c, h);
+    if (rc) return rc;
+    if (c->capturing) return -EBUSY;
+    // joins every pending and in-flight task: a superset of the writers (and
+    // readers) of h, which is what acquire has to wait for
+    return wait_impl(c, 0);
+}
+
+int b3t_data_unregister(b3t_ctx *c, b3t_handle h) {
+    if (!c) return -EINVAL;
+    int rc = check_handle(c, h);
+    if (rc) return rc;
+    rc = c->capturing ? 0 : wait_impl(c, 0);
+    Handle &H = c->handles[h];
+    for (int32_t k : H.parts) {
+        auto it = c->by_ptr.find((uintptr_t)c->handles[k].ptr);
+        if (it != c->by_ptr.end() && it->second == k) c->by_ptr.erase(it);
+        c->handles[k].alive = false;
+    }
+    auto it = c->by_ptr.find((uintptr_t)H.ptr);
+    if (it != c->by_ptr.end() && it->second == h) c->by_ptr.erase(it);
+    H.alive = false;
+    H.parts.clear();
+    return rc;
+}
+
+int b3t_last_error(b3t_ctx *c, int32_t *task_id, int32_t *info) {
+    if (!c) return -EINVAL;
+    if (task_id) *task_id = c->err_task;
+    if (info) *info = c->err_info;
+    return 0;
+}
+
+const char *b3t_strerror(int err) {
+    switch (-err) {
+    case 0: return "success";
+    case EINVAL: return "invalid argument or task/implementation signature mismatch";
+    case ENOENT: return "attempt to use unregistered pointer or handle";
+    case ENOMEM: return "out of memory";
+    case ETIMEDOUT: return "timed out waiting for tasks";
+    case EDOM: return "matrix is not positive definite (see b3t_last_error)";
+    case EIO: return "CUDA error";
+    case EBUSY: return "operation not allowed while capturing or with pending tasks";
+    case EEXIST: return "already registered or partitioned";
+    case ENODEV: return "no CUDA device";
+    case EPROTO: return "internal consistency check failed on the device";
+    case ERANGE: return "iterative refinement did not converge";
+    }
+    return "unknown error";
+}
+
+int b3t_graph_capture_begin(b3t_ctx *c) {
+    if (!c) return -EINVAL;
+    if (c->capturing || !c->tasks.empty()) return -EBUSY;
+    c->capturing = true;
+    return 0;
+}
+
+int b3t_graph_capture_end(b3t_ctx *c, b3t_graph *out) {
+    if (!c || !out || !c->capturing) return -EINVAL;
+    c->capturing = false;
+    if (c->tasks.empty()) return -EINVAL;
+    GraphRec g;
+    InitParams ip; LaunchParams lp; int64_t nitems; bool has_mx;
+    int rc = build_launch(c, g.arena, ip, lp, nitems, has_mx);
+    if (!rc) rc = cuda_err(cudaStreamSynchronize(c->stream));
+    int nctas = 0; size_t smem = 0;
+    if (!rc) rc = grid_for(c, has_mx, &nctas, &smem);
+    if (rc) { clear_batch(c); g.arena.release(); return rc; }
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        clear_batch(c); g.arena.release(); return -EIO;
+    }
+    cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    rc = b3t_internal_launch(&ip, &lp, nctas, smem, cs, nullptr, nullptr);
+    const cudaError_t ec = cudaStreamEndCapture(cs, &g.graph);
+    cudaStreamDestroy(cs);
+    if (rc || ec != cudaSuccess || !g.graph) { clear_batch(c); g.arena.release(); return rc ? rc : -EIO; }
+    if (cudaGraphInstantiate(&g.exec, g.graph, 0) != cudaSuccess) {
+        cudaGraphDestroy(g.graph); clear_batch(c); g.arena.release(); return -EIO;
+    }
+    g.ntasks = (int64_t)c->tasks.size();
+    g.nitems = nitems;
+    g.nctas = nctas;
+    g.alive = true;
+    clear_batch(c);
+    c->graphs.push_back(g);
+    *out = (b3t_graph)(c->graphs.size() - 1);
+    return 0;
+}
+
+int b3t_graph_replay(b3t_ctx *c, b3t_graph gi) {
+    if (!c || gi < 0 || gi >= (int32_t)c->graphs.size() || !c->graphs[gi].alive) return -EINVAL;
+    if (c->capturing) return -EBUSY;
+    const int rc = flush_impl(c);
+    if (rc) return rc;
+    GraphRec &g = c->graphs[gi];
+    cudaEventRecord(c->ev0, c->stream);
+    const int rl = cuda_err(cudaGraphLaunch(g.exec, c->stream));
+    cudaEventRecord(c->ev1, c->stream);
+    const int r2 = track(c, g.arena.ctl);
+    c->last_ntasks = g.ntasks; c->last_nitems = g.nitems; c->last_nctas = g.nctas;
+    c->last_timed = true;
+    return rl ? rl : r2;
+}
+
+int b3t_graph_destroy(b3t_ctx *c, b3t_graph gi) {
+    if (!c || gi < 0 || gi >= (int32_t)c->graphs.size() || !c->graphs[gi].alive) return -EINVAL;
+    const int rc = wait_impl(c, 0);
+    GraphRec &g = c->graphs[gi];
+    cudaGraphExecDestroy(g.exec);
+    cudaGraphDestroy(g.graph);
+    g.arena.release();
+    g.alive = false;
+    return rc;
+}
+
+int b3t_dag_stats(b3t_ctx *c, int64_t *ntasks, int64_t *nedges) {
+    if (!c) return -EINVAL;
+    if (ntasks) *ntasks = (int64_t)c->tasks.size();
+    if (nedges) *nedges = (int64_t)c->edges.size();
+    return 0;
+}
+
+int b3t_dag_edges(b3t_ctx *c, int32_t *pred, int32_t *succ, int64_t cap, int64_t *count) {
+    if (!c) return -EINVAL;
+    const int64_t n = (int64_t)c->edges.size();
+    if (count) *count = n;
+    for (int64_t i = 0; i < n && i < cap; ++i) {
+        if (pred) pred[i] = c->edges[i].first;
+        if (succ) succ[i] = c->edges[i].second;
+    }
+    return 0;
+}
+
+int b3t_last_launch(b3t_ctx *c, int64_t *ntasks, int64_t *nitems, int32_t *nctas, int64_t *kernel_ns) {
+    if (!c) return -EINVAL;
+    if (ntasks) *ntasks = c->last_ntasks;
+    if (nitems) *nitems = c->last_nitems;
+    if (nctas) *nctas = c->last_nctas;
+    if (kernel_ns) {
+        *kernel_ns = -1;
+        float ms = 0.f;
+        if (c->last_timed && cudaEventQuery(c->ev1) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, c->ev0, c->ev1) == cudaSuccess)
+            *kernel_ns = (int64_t)((double)ms * 1e6);
+        cudaGetLastError();
+    }
+    return 0;
+}
+
+int b3t_debug_block_task(b3t_ctx *c, int64_t t) {
+    if (!c || t < 0 || t >= (int64_t)c->tasks.size()) return -EINVAL;
+    if (c->extra_deps.size() < c->tasks.size()) c->extra_deps.resize(c->tasks.size(), 0);
+    c->extra_deps[t] += 1;
+    return 0;
+}
+
+// ------------------------------------------------------------- Cholesky
+
+static int kind_codelet(b3t_ctx *c, int kind, b3t_codelet *cl) {
+    if (c->kind_cl[kind] >= 0) { *cl = c->kind_cl[kind]; return 0; }
+    const KindSig &s = kSigs[kind];
+    const int rc = b3t_task_decl(c, kKindNames[kind], kind, s.nbuf, s.modes, s.scalar_bytes, cl);
+    if (!rc) c->kind_cl[kind] = *cl;
+    return rc;
+}
+
+static int64_t tidx(int32_t i, int32_t j, int32_t T) {
+    return (int64_t)j * T - (int64_t)j * (j - 1) / 2 + (i - j);
+}
+
+static int reg_tiles(b3t_ctx *c, void *const *tiles, int64_t nt, size_t nelems, size_t es, int64_t ld,
+                     std::vector<b3t_handle> &h) {
+    h.resize(nt);
+    for (int64_t t = 0; t < nt; ++t) {
+        int rc = b3t_data_lookup(c, tiles[t], &h[t]);
+        if (rc == -ENOENT) rc = b3t_data_register(c, tiles[t], nelems, es, ld, &h[t]);
+        if (rc) return rc;
+        const Handle &H = c->handles[h[t]];
+        if (H.ld != ld || H.elemsize != es || H.nelems != nelems) return -EINVAL;
+    }
+    return 0;
+}
+
+int b3t_cholesky_submit(b3t_ctx *c, double *const *tiles, int32_t T, int32_t b, int32_t col0) {
+    if (!c || !tiles || T <= 0 || b <= 0 || b % kGemmBlk) return -EINVAL;
+    const int64_t nt = (int64_t)T * (T + 1) / 2;
+    std::vector<b3t_handle> h;
+    int rc = reg_tiles(c, (void *const *)tiles, nt, (size_t)b * b, 8, b, h);
+    if (rc) return rc;
+    b3t_codelet cp, ct, cs, cg;
+    if ((rc = kind_codelet(c, kPotrf, &cp)) || (rc = kind_codelet(c, kTrsm, &ct)) ||
+        (rc = kind_codelet(c, kSyrk, &cs)) || (rc = kind_codelet(c, kGemm, &cg)))
+        return rc;
+    for (int32_t k = 0; k < T; ++k) {
+        const int32_t c0 = col0 + k * b;
+        const b3t_handle hp[1] = {h[tidx(k, k, T)]};
+        if ((rc = submit_impl(c, cp, hp, nullptr, 1, &c0, 4))) return rc;
+        for (int32_t i = k + 1; i < T; ++i) {
+            const b3t_handle ht[2] = {h[tidx(k, k, T)], h[tidx(i, k, T)]};
+            if ((rc = submit_impl(c, ct, ht, nullptr, 2, nullptr, 0))) return rc;
+        }
+        for (int32_t i = k + 1; i < T; ++i) {
+            const b3t_handle hs[2] = {h[tidx(i, k, T)], h[tidx(i, i, T)]};
+            if ((rc = submit_impl(c, cs, hs, nullptr, 2, nullptr, 0))) return rc;
+            for (int32_t j = k + 1; j < i; ++j) {
+                const b3t_handle hg[3] = {h[tidx(i, k, T)], h[tidx(j, k, T)], h[tidx(i, j, T)]};
+                if ((rc = submit_impl(c, cg, hg, nullptr, 3, nullptr, 0))) return rc;
+            }
+        }
+    }
+    return 0;
+}
+
+int b3t_cholesky_mx_submit(b3t_ctx *c, float *const *W, double *const *L, void *const *Q,
+                           int32_t T, int32_t b, int32_t fmt, int32_t col0) {
+    if (!c || !W || !L || !Q || T <= 0 || b <= 0 || b % kMxBlk) return -EINVAL;
+    if (fmt != B3T_FMT_BF16 && fmt != B3T_FMT_E4M3) return -EINVAL;
+    const int64_t nt = (int64_t)T * (T + 1) / 2;
+    std::vector<b3t_handle> hw, hl, hq;
+    int rc = reg_tiles(c, (void *const *)W, nt, (size_t)b * b, 4, b, hw);
+    if (!rc) rc = reg_tiles(c, (void *const *)L, nt, (size_t)b * b, 8, b, hl);
+    if (rc) return rc;
+    hq.assign(nt, -1);
+    for (int32_t j = 0; j < T; ++j)
+        for (int32_t i = j + 1; i < T; ++i) {
+            const int64_t t = tidx(i, j, T);
+            rc = b3t_data_lookup(c, Q[t], &hq[t]);
+            if (rc == -ENOENT) rc = b3t_data_register(c, Q[t], q_bytes(b, fmt), 1, b, &hq[t]);
+            if (rc) return rc;
+        }
+    b3t_codelet cp, ct, cq, cs, cg;
+    if ((rc = kind_codelet(c, kPotrfMx, &cp)) || (rc = kind_codelet(c, kTrsmMx, &ct)) ||
+        (rc = kind_codelet(c, kQuant, &cq)) || (rc = kind_codelet(c, kSyrkMx, &cs)) ||
+        (rc = kind_codelet(c, kGemmMx, &cg)))
+        return rc;
+    for (int32_t k = 0; k < T; ++k) {
+        const int32_t c0 = col0 + k * b;
+        const b3t_handle hp[2] = {hw[tidx(k, k, T)], hl[tidx(k, k, T)]};
+        if ((rc = submit_impl(c, cp, hp, nullptr, 2, &c0, 4))) return rc;
+        for (int32_t i = k + 1; i < T; ++i) {
+            const b3t_handle ht[3] = {hl[tidx(k, k, T)], hw[tidx(i, k, T)], hl[tidx(i, k, T)]};
+            if ((rc = submit_impl(c, ct, ht, nullptr, 3, nullptr, 0))) return rc;
+            const b3t_handle hqq[2] = {hl[tidx(i, k, T)], hq[tidx(i, k, T)]};
+            if ((rc = submit_impl(c, cq, hqq, nullptr, 2, &fmt, 4))) return rc;
+        }
+        for (int32_t i = k + 1; i < T; ++i) {
+            const b3t_handle hs[2] = {hq[tidx(i, k, T)], hw[tidx(i, i, T)]};
+            if ((rc = submit_impl(c, cs, hs, nullptr, 2, &fmt, 4))) return rc;
+            for (int32_t j = k + 1; j < i; ++j) {
+                const b3t_handle hg[3] = {hq[tidx(i, k, T)], hq[tidx(j, k, T)], hw[tidx(i, j, T)]};
+                if ((rc = submit_impl(c, cg, hg, nullptr, 3, &fmt, 4))) return rc;
+            }
+        }
+    }
+    return 0;
+}
+
+int b3t_tiles_unregister(b3t_ctx *c, void *const *tiles, int32_t T) {
+    if (!c || !tiles || T <= 0) return -EINVAL;
+    int rc = c->capturing ? -EBUSY : wait_impl(c, 0);
+    const int64_t nt = (int64_t)T * (T + 1) / 2;
+    for (int64_t t = 0; t < nt; ++t) {
+        b3t_handle h;
+        if (tiles[t] && b3t_data_lookup(c, tiles[t], &h) == 0) {
+            Handle &H = c->handles[h];
+            c->by_ptr.erase((uintptr_t)H.ptr);
+            H.alive = false;
+        }
+    }
+    return rc;
+}
+
+}  // extern "C"

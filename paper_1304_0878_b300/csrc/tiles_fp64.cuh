@@ -1,0 +1,269 @@
+// FP64 tile task bodies for the persistent executor (256 threads per CTA).
+//
+// Tiles are b x b, column-major inside the tile: element (r, c) at r + c*b.
+// Only the lower triangle of diagonal tiles is read or written.
+//   POTRF : A_kk = L_kk L_kk^T            one work item per task
+//   TRSM  : A_ik <- A_ik L_kk^{-T}        items of kTrsmRows rows
+//   SYRK  : A_ii <- A_ii - A_ik A_ik^T    items of 64 x 64 lower blocks
+//   GEMM  : A_ij <- A_ij - A_ik A_jk^T    items of 64 x 64 blocks
+// FP64 on sm_103 is bound by the DFMA pipe (about two DFMA per clock per
+// SM), not by memory: the bodies stage operands through shared memory in
+// K-chunks and keep a small register tile per thread, which is enough to keep
+// that pipe busy.  Data written by other tasks of the same launch is read
+// with plain (coherent) loads, never through the read-only path.
+#pragma once
+#include "b3t_internal.h"
+
+namespace b3t {
+
+constexpr int kKc = 32;            // K chunk staged in shared memory
+
+// C(crow0.., ccol0..) (64 x 64 block) -= A(arow0.., :) * B(brow0.., :)^T, K = b.
+// lower_only: write only entries with global row >= global column.
+__device__ __forceinline__ void gemm64_f64(const double *A, int arow0, const double *B, int brow0,
+                                           double *C, int crow0, int ccol0, int b, bool lower_only,
+                                           double *smem) {
+    double *As = smem;                   // [kKc][64]
+    double *Bs = smem + kKc * 64;        // [kKc][64]
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int k0 = 0; k0 < b; k0 += kKc) {
+#pragma unroll
+        for (int q = 0; q < (kKc * 64) / kThreads; ++q) {
+            const int e = tid + q * kThreads;
+            const int r = e & 63, p = e >> 6;
+            As[p * 64 + r] = A[(size_t)(arow0 + r) + (size_t)(k0 + p) * b];
+            Bs[p * 64 + r] = B[(size_t)(brow0 + r) + (size_t)(k0 + p) * b];
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int p = 0; p < kKc; ++p) {
+            double a[4], bb[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[p * 64 + tx + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bb[j] = Bs[p * 64 + ty + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = crow0 + tx + 16 * i, c = ccol0 + ty + 16 * j;
+            if (!lower_only || r >= c) {
+                double *p = C + (size_t)r + (size_t)c * b;
+                *p = *p - acc[i][j];
+            }
+        }
+}
+
+__device__ __forceinline__ void gemm_item(const TaskRec &t, int item, double *smem) {
+    const int b = (int)t.n, m = b / kGemmBlk;
+    const int bi = item / m, bj = item % m;
+    gemm64_f64((const double *)t.buf[0], bi * 64, (const double *)t.buf[1], bj * 64,
+               (double *)t.buf[2], bi * 64, bj * 64, b, false, smem);
+}
+
+// item -> (bi, bj), bi >= bj, enumerating the lower block triangle row by row
+__device__ __forceinline__ void tri_index(int item, int &bi, int &bj) {
+    int i = (int)((sqrtf(8.0f * item + 1.0f) - 1.0f) * 0.5f);
+    while ((i + 1) * (i + 2) / 2 <= item) ++i;
+    while (i * (i + 1) / 2 > item) --i;
+    bi = i;
+    bj = item - i * (i + 1) / 2;
+}
+
+__device__ __forceinline__ void syrk_item(const TaskRec &t, int item, double *smem) {
+    const int b = (int)t.n;
+    int bi, bj;
+    tri_index(item, bi, bj);
+    const double *A = (const double *)t.buf[0];
+    gemm64_f64(A, bi * 64, A, bj * 64, (double *)t.buf[1], bi * 64, bj * 64, b, bi == bj, smem);
+}
+
+// X L^T = A for rows [r0, r0 + 32) of a b-wide tile.  Ain is the input
+// (f64, or f32 for the mixed-precision panel), X the f64 output (may alias
+// Ain when Tin is double).  L is the b x b lower factor.
+template <typename Tin>
+__device__ __forceinline__ void trsm_rows(const double *L, const Tin *Ain, double *X, int r0, int b,
+                                          double *smem) {
+    constexpr int RB = kTrsmRows;           // 32 rows
+    double *Lcb = smem;                     // [64][65]  Lcb[c*65 + q] = L(c0+c, c0+q)
+    double *Acc = Lcb + 64 * 65;            // [64][33]  Acc[c*33 + r]
+    double *Xs = Acc + 64 * 33;             // [kKc][33] Xs[p*33 + r] = X(r0+r, k0+p)
+    double *Ls = Xs + kKc * 33;             // [kKc][64] Ls[p*64 + c] = L(c0+c, k0+p)
+    const int tid = threadIdx.x;
+    const int tr = tid & 31, tw = tid >> 5;     // row, column group
+    for (int c0 = 0; c0 < b; c0 += 64) {
+        double acc[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            acc[j] = (double)Ain[(size_t)(r0 + tr) + (size_t)(c0 + tw + 8 * j) * b];
+        for (int k0 = 0; k0 < c0; k0 += kKc) {
+#pragma unroll
+            for (int q = 0; q < (RB * kKc) / kThreads; ++q) {
+                const int e = tid + q * kThreads;
+                const int r = e & 31, p = e >> 5;
+                Xs[p * 33 + r] = X[(size_t)(r0 + r) + (size_t)(k0 + p) * b];
+            }
+#pragma unroll
+            for (int q = 0; q < (64 * kKc) / kThreads; ++q) {
+                const int e = tid + q * kThreads;
+                const int c = e & 63, p = e >> 6;
+                Ls[p * 64 + c] = L[(size_t)(c0 + c) + (size_t)(k0 + p) * b];
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int p = 0; p < kKc; ++p) {
+                const double x = Xs[p * 33 + tr];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[j] = fma(-x, Ls[p * 64 + tw + 8 * j], acc[j]);
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) Acc[(tw + 8 * j) * 33 + tr] = acc[j];
+        for (int e = tid; e < 64 * 64; e += kThreads) {
+            const int c = e & 63, q = e >> 6;           // element (c0+c, c0+q)
+            if (c >= q) Lcb[c * 65 + q] = L[(size_t)(c0 + c) + (size_t)(c0 + q) * b];
+        }
+        __syncthreads();
+        // small triangular solve, right-looking over the 64 columns
+        for (int c = 0; c < 64; ++c) {
+            if (tid < RB) Acc[c * 33 + tid] = Acc[c * 33 + tid] / Lcb[c * 65 + c];
+            __syncthreads();
+            const int rem = 63 - c;
+            for (int e = tid; e < RB * rem; e += kThreads) {
+                const int r = e & 31, cc = c + 1 + (e >> 5);
+                Acc[cc * 33 + r] = fma(-Acc[c * 33 + r], Lcb[cc * 65 + c], Acc[cc * 33 + r]);
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            X[(size_t)(r0 + tr) + (size_t)(c0 + tw + 8 * j) * b] = Acc[(tw + 8 * j) * 33 + tr];
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ void trsm_item(const TaskRec &t, int item, double *smem) {
+    double *A = (double *)t.buf[1];
+    trsm_rows<double>((const double *)t.buf[0], A, A, item * kTrsmRows, (int)t.n, smem);
+}
+
+__device__ __forceinline__ void trsm_mx_item(const TaskRec &t, int item, double *smem) {
+    trsm_rows<float>((const double *)t.buf[0], (const float *)t.buf[1], (double *)t.buf[2],
+                     item * kTrsmRows, (int)t.n, smem);
+}
+
+// Cholesky of one b x b tile in place (lower), one CTA, left-looking over
+// panels of 32 columns.  Returns 0 or the 1-based column (within the tile)
+// of the first pivot that is <= 0 or NaN.
+__device__ __forceinline__ int potrf_tile(double *A, int b, double *smem, int *s_info) {
+    constexpr int PW = 32;
+    double *Dg = smem;                     // [32][33]  Dg[i*33 + k] = A(jb+i, jb+k)
+    double *Lr = Dg + PW * 33;             // [kKc][64] Lr[p*64 + r] = A(rr0+r, k0+p)
+    double *Lc = Lr + kKc * 64;            // [kKc][32] Lc[p*32 + c] = A(jb+c, k0+p)
+    const int tid = threadIdx.x;
+    if (tid == 0) *s_info = 0;
+    __syncthreads();
+    for (int jb = 0; jb < b; jb += PW) {
+        // (1) panel update: P = A(jb:, jb:jb+32) - A(jb:, :jb) A(jb:jb+32, :jb)^T
+        if (jb > 0) {
+            const int tr = tid & 63, tc = tid >> 6;    // 64 rows x (4 x 8) columns
+            for (int rr0 = jb; rr0 < b; rr0 += 64) {
+                double acc[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[j] = 0.0;
+                for (int k0 = 0; k0 < jb; k0 += kKc) {
+#pragma unroll
+                    for (int q = 0; q < (64 * kKc) / kThreads; ++q) {
+                        const int e = tid + q * kThreads;
+                        const int r = e & 63, p = e >> 6;
+                        const int gr = rr0 + r;
+                        Lr[p * 64 + r] = gr < b ? A[(size_t)gr + (size_t)(k0 + p) * b] : 0.0;
+                    }
+#pragma unroll
+                    for (int q = 0; q < (PW * kKc) / kThreads; ++q) {
+                        const int e = tid + q * kThreads;
+                        const int c = e & 31, p = e >> 5;
+                        Lc[p * 32 + c] = A[(size_t)(jb + c) + (size_t)(k0 + p) * b];
+                    }
+                    __syncthreads();
+#pragma unroll 8
+                    for (int p = 0; p < kKc; ++p) {
+                        const double x = Lr[p * 64 + tr];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) acc[j] = fma(x, Lc[p * 32 + tc + 4 * j], acc[j]);
+                    }
+                    __syncthreads();
+                }
+                const int gr = rr0 + tr;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int gc = jb + tc + 4 * j;
+                    if (gr < b && gr >= gc) {
+                        double *p = A + (size_t)gr + (size_t)gc * b;
+                        *p = *p - acc[j];
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        // (2) factor the 32 x 32 diagonal block in shared memory
+        for (int e = tid; e < PW * PW; e += kThreads) {
+            const int i = e & 31, k = e >> 5;
+            if (i >= k) Dg[i * 33 + k] = A[(size_t)(jb + i) + (size_t)(jb + k) * b];
+        }
+        __syncthreads();
+        for (int j = 0; j < PW; ++j) {
+            if (tid == 0) {
+                const double d = Dg[j * 33 + j];
+                if (!(d > 0.0)) *s_info = jb + j + 1;
+                else Dg[j * 33 + j] = sqrt(d);
+            }
+            __syncthreads();
+            if (*s_info) return *s_info;
+            if (tid > j && tid < PW) Dg[tid * 33 + j] = Dg[tid * 33 + j] / Dg[j * 33 + j];
+            __syncthreads();
+            for (int e = tid; e < PW * PW; e += kThreads) {
+                const int i = e & 31, k = e >> 5;
+                if (k > j && i >= k) Dg[i * 33 + k] = fma(-Dg[i * 33 + j], Dg[k * 33 + j], Dg[i * 33 + k]);
+            }
+            __syncthreads();
+        }
+        for (int e = tid; e < PW * PW; e += kThreads) {
+            const int i = e & 31, k = e >> 5;
+            if (i >= k) A[(size_t)(jb + i) + (size_t)(jb + k) * b] = Dg[i * 33 + k];
+        }
+        // (3) rows below the block: X Dg^T = P, one row per thread
+        for (int i = jb + PW + tid; i < b; i += kThreads) {
+            double x[PW];
+#pragma unroll
+            for (int c = 0; c < PW; ++c) x[c] = A[(size_t)i + (size_t)(jb + c) * b];
+#pragma unroll
+            for (int c = 0; c < PW; ++c) {
+                double s = x[c];
+#pragma unroll
+                for (int q = 0; q < c; ++q) s = fma(-x[q], Dg[c * 33 + q], s);
+                x[c] = s / Dg[c * 33 + c];
+            }
+#pragma unroll
+            for (int c = 0; c < PW; ++c) A[(size_t)i + (size_t)(jb + c) * b] = x[c];
+        }
+        __syncthreads();
+    }
+    return 0;
+}
+
+}  // namespace b3t
