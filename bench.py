@@ -1,0 +1,418 @@
+#!/usr/bin/env python
+"""Benchmark of the task-DAG executor on one B300 (or N replicas).
+
+Headline: plain FP64 tiled Cholesky, N = 32768, tile 512 (64 x 64 tiles,
+45,760 POTRF / TRSM / SYRK / GEMM tasks), A = B B^T / N + 0.1 I, seed 3,
+submitted in right-looking order with R / RW modes and run as ONE
+persistent-kernel launch per factorisation (the DAG is captured once into a
+CUDA graph and replayed).  Metric: TFLOP/s = (N^3/3 + N^2/2 + N/6) / time.
+
+Secondary (same JSON line, "secondary"): vector-scaling chains (n = 2^28
+binary32, 256 blocks x 8 chained RW tasks) in task-level GB/s, scheduler
+throughput in tasks/s on empty-bodied DAGs, and the small Cholesky
+(N = 1024, tile 128, 120 tasks) in ms.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the oracle (the sequential CPU executor) on the same
+workload, a bounded sample of it per step, on the host cores.
+Under torchrun every rank runs an independent replica (the DAG does not
+shard); rank 0 prints one JSON line with the max time over ranks.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAK_FP64_FLOP_PER_CLK_SM = 4      # two DFMA per clock per SM on sm_103
+NUM_SMS = 148
+SM_MAX_MHZ = 2032.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=32768)
+    p.add_argument("--b", type=int, default=512)
+    p.add_argument("--no-secondary", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    return p.parse_args()
+
+
+def cholesky_flops(N):
+    return float(N * (N + 1) * (2 * N + 1) // 6)
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region (every 200 ms)."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_sample(get_tile, T, b, seconds):
+    """The oracle on a bounded prefix of the submission order (1 core)."""
+    import oracle
+    from oracle import cholesky as och
+    oracle.build()
+    done, fl, sec = och.run_prefix(get_tile, T, b, seconds)
+    return {"value": fl / sec / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+            "sample": "first %d tasks (%.3g flop) of the N=%d, b=%d submission order in %.1f s"
+                      % (done, fl, T * b, b, sec)}
+
+
+def host_tile_getter(N, b, seed, shift):
+    """Tiles of A = B B^T/N + shift I formed on the host in FP64 (no GPU)."""
+    rng = np.random.default_rng(seed)
+    B = rng.standard_normal((N, N))
+
+    def get(i, j):
+        blk = B[i * b:(i + 1) * b] @ B[j * b:(j + 1) * b].T / N
+        if i == j:
+            blk[np.diag_indices(b)] += shift
+        return np.ascontiguousarray(blk.T)
+    return get
+
+
+def run_reference(args):
+    ws, rank, _ = dist()
+    if rank != 0:
+        return
+    N, b = args.n, args.b
+    T = N // b
+    get = None
+    try:
+        import torch
+        if torch.cuda.is_available():
+            import synth
+            A0 = synth.spd_tiles_device(N, b, 3, 0.1, "cuda")
+            from paper_1304_0878_b300.tiles import tile_index
+
+            def get(i, j):
+                return A0[tile_index(i, j, T)].cpu().numpy()
+    except ImportError:
+        pass
+    if get is None:
+        get = host_tile_getter(N, b, 3, 0.1)
+    per = max(2.0, min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup)))
+    vals = []
+    for s in range(args.warmup + args.steps):
+        r = oracle_sample(get, T, b, per)
+        if s >= args.warmup:
+            vals.append(r)
+    v = float(np.mean([r["value"] for r in vals]))
+    flops = cholesky_flops(N)
+    line = {"impl": "reference", "metric": "cholesky_fp64_tflops", "value": v, "unit": "TFLOP/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": flops / (v * 1e12) * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "tiled Cholesky FP64 N=%d tile %d (%d tasks)" % (N, b, len_tasks(T))},
+            "cpu_baseline": {**vals[-1], "value": v},
+            "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def len_tasks(T):
+    return T + T * (T - 1) + T * (T - 1) * (T - 2) // 6
+
+
+def sampled_residual(t, A0, N, b, nsamp=24, seed=0):
+    """max |(L L^T - A)_ij| / max |A_ij| over sampled lower (i, j): rows of L
+    gathered from the tiles, products formed on the device."""
+    import torch
+    from paper_1304_0878_b300.tiles import tile_index
+    T = N // b
+    rng = np.random.default_rng(seed)
+
+    def row(M, i):
+        I, r = divmod(i, b)
+        return torch.cat([M[tile_index(I, J, T), :, r] for J in range(I + 1)])
+
+    worst = 0.0
+    for _ in range(nsamp):
+        i = int(rng.integers(0, N))
+        j = int(rng.integers(0, i + 1))
+        li, lj = row(t, i)[: i + 1], row(t, j)[: j + 1]
+        m = min(i, j) + 1
+        v = float(torch.dot(li[:m], lj[:m]))
+        a = float(row(A0, i)[j])
+        worst = max(worst, abs(v - a))
+    return worst / float(A0.abs().max())
+
+
+def run_ours(args):
+    import torch
+    import synth
+    import paper_1304_0878_b300 as b3t
+    from paper_1304_0878_b300 import tiles as dt
+    import paper_1304_0878_b300.build as pb
+
+    ws, rank, local = dist()
+    pb.build()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    ctx = b3t.Context(stream=stream.cuda_stream, timeout_ns=120_000_000_000)
+    N, b = args.n, args.b
+    T = N // b
+    flops = cholesky_flops(N)
+
+    A0 = synth.spd_tiles_device(N, b, 3, 0.1, dev)
+    t = torch.empty_like(A0)
+    ptrs = dt.tile_ptrs(t)
+    ctx.graph_capture_begin()
+    ctx.cholesky_submit(ptrs, T, b)
+    g = ctx.graph_capture_end()
+
+    def step():
+        t.copy_(A0)
+        ctx.graph_replay(g)
+        ctx.task_wait()
+        return ctx.last_launch()["kernel_ns"]
+
+    for _ in range(args.warmup):
+        step()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    clocks = Clocks(torch.cuda.current_device())
+    barrier()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    kns = []
+    for _ in range(args.steps):
+        kns.append(step())
+    e1.record(stream)
+    barrier()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if ws > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    resid = sampled_residual(t, A0, N, b)
+    kernel_s = float(np.mean(kns)) / 1e9
+    achieved = flops / kernel_s / 1e12
+    peak = NUM_SMS * PEAK_FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+
+    # end to end through the public API: pinned host A in, L out, every step
+    e2e = None
+    if not args.no_e2e:
+        hA = torch.empty(A0.shape, dtype=A0.dtype, pin_memory=True)
+        hA.copy_(A0)
+        hL = torch.empty_like(hA, pin_memory=True)
+        ke = max(1, min(args.steps, 2))
+        torch.cuda.synchronize()
+        e2 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        for _ in range(ke):
+            t.copy_(hA, non_blocking=True)
+            ctx.graph_replay(g)
+            ctx.task_wait()
+            hL.copy_(t, non_blocking=True)
+        e3.record(stream)
+        torch.cuda.synchronize()
+        mse = e2.elapsed_time(e3) / ke
+        nbytes = A0.numel() * A0.element_size()
+        e2e = {"value": ws * flops / (mse / 1e3) / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "ms_per_step": mse}
+        del hA, hL
+
+    secondary = {}
+    if not args.no_secondary:
+        secondary = run_secondary(ctx, dev, stream)
+
+    cpu = None
+    if rank == 0 and args.cpu_seconds > 0:
+        from paper_1304_0878_b300.tiles import tile_index
+
+        def get(i, j):
+            return A0[tile_index(i, j, T)].cpu().numpy()
+        cpu = oracle_sample(get, T, b, args.cpu_seconds)
+
+    ctx.graph_destroy(g)
+    ctx.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": "cholesky_fp64_tflops", "value": ws * flops / (ms / 1e3) / 1e12, "unit": "TFLOP/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "tiled Cholesky FP64 N=%d tile %d (%d tasks, one persistent-kernel "
+                               "launch per factorisation, DAG captured once and replayed)"
+                               % (N, b, len_tasks(T)),
+                   "N": N, "tile": b, "tasks": len_tasks(T), "seed": 3, "shift": 0.1,
+                   "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "l2": "inputs (%.2f GB of tiles) larger than L2" % (A0.numel() * 8 / 1e9),
+                   "input_reset": "A tiles restored by a device copy inside each step"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "note": "FP64 DFMA pipe: 148 SMs x 4 flop/clk x 2032 MHz; achieved = "
+                             "N^3/3 flops / persistent-kernel time"},
+        "check": {"sampled_rel_residual": resid},
+        "clocks": ck,
+        "gpu_launches": 2 * args.steps,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "secondary": secondary,
+    }
+    print(json.dumps(line))
+
+
+def run_secondary(ctx, dev, stream):
+    """Vector chains (config 2), tasks/s on empty-bodied DAGs, small Cholesky."""
+    import torch
+    import synth
+    import paper_1304_0878_b300 as b3t
+    from paper_1304_0878_b300 import tiles as dt
+    out = {}
+    # vector-scaling chains: n = 2^28 f32, 256 blocks x 8 tasks
+    nb, nk, n = 256, 8, 1 << 20
+    x = torch.from_numpy(synth.vector_f32(nb * n, seed=1)).to(dev)
+    f = synth.chain_factors(nb, nk, seed=2)
+    hs = [ctx.data_register(x[i * n:(i + 1) * n].data_ptr(), n, 4) for i in range(nb)]
+    cl = ctx.task_decl("scale_vector", b3t.SCAL_F32, [b3t.RW], 4)
+    ctx.graph_capture_begin()
+    for k in range(nk):
+        for i in range(nb):
+            ctx.task_submit(cl, [hs[i]], b3t.pack_f32(float(f[i, k])))
+    g = ctx.graph_capture_end()
+    ts = []
+    for r in range(8):
+        ctx.graph_replay(g)
+        ctx.task_wait()
+        if r >= 3:
+            ts.append(ctx.last_launch()["kernel_ns"] / 1e9)
+    tbytes = 8.0 * nb * nk * n
+    out["vector_chains"] = {"workload": "n=2^28 f32, 256 blocks x 8 chained RW tasks (2048 tasks)",
+                            "ms": 1e3 * float(np.median(ts)), "task_level_GBps": tbytes / float(np.median(ts)) / 1e9,
+                            "task_bytes": tbytes}
+    ctx.graph_destroy(g)
+    for h in hs:
+        ctx.data_unregister(h)
+    del x
+    # scheduler throughput: 1000 chains x 100 empty tasks
+    y = torch.zeros(1000 * 64, device=dev)
+    hy = [ctx.data_register(y[i * 64:(i + 1) * 64].data_ptr(), 64, 4) for i in range(1000)]
+    cn = ctx.task_decl("noop", b3t.NOOP, [b3t.RW])
+    ctx.graph_capture_begin()
+    for k in range(100):
+        for h in hy:
+            ctx.task_submit(cn, [h])
+    g = ctx.graph_capture_end()
+    ts = []
+    for r in range(6):
+        ctx.graph_replay(g)
+        ctx.task_wait()
+        if r >= 2:
+            ts.append(ctx.last_launch()["kernel_ns"] / 1e9)
+    out["tasks_per_s"] = {"workload": "1000 chains x 100 empty tasks (100k tasks)",
+                          "value": 1e5 / float(np.median(ts))}
+    ctx.graph_destroy(g)
+    for h in hy:
+        ctx.data_unregister(h)
+    # small Cholesky, N = 1024, tile 128 (config 1): latency of one launch
+    N1, b1 = 1024, 128
+    A1 = dt.to_tiles(torch.from_numpy(synth.spd_host(N1, seed=0, shift=1.0)).to(dev), b1)
+    t1 = torch.empty_like(A1)
+    p1 = dt.tile_ptrs(t1)
+    ctx.graph_capture_begin()
+    ctx.cholesky_submit(p1, N1 // b1, b1)
+    g = ctx.graph_capture_end()
+    ts = []
+    for r in range(8):
+        t1.copy_(A1)
+        ctx.graph_replay(g)
+        ctx.task_wait()
+        if r >= 3:
+            ts.append(ctx.last_launch()["kernel_ns"] / 1e9)
+    out["cholesky_small"] = {"workload": "FP64 N=1024 tile 128 (120 tasks)",
+                             "ms": 1e3 * float(np.median(ts)),
+                             "TFLOPs": cholesky_flops(N1) / float(np.median(ts)) / 1e12}
+    ctx.graph_destroy(g)
+    ctx.tiles_unregister(p1, N1 // b1)
+    return out
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -125,13 +125,17 @@ typedef struct b3t_config {
     int32_t ctas_per_sm;    /* persistent CTAs per SM; 0 = automatic */
     int32_t prio_levels;    /* ready-queue priority levels 1..8; 0 = 8 */
     int32_t debug_checks;   /* 1: kernels bounds-check task ids and items */
-    int32_t reserved[3];
+    int32_t host_only;      /* 1: no CUDA device is touched; registration,
+                               submission and DAG inspection work, flush /
+                               wait / replay return -ENODEV (for tools and
+                               CPU-only tests of the dependency logic) */
+    int32_t reserved[2];
 } b3t_config;
 
 /* Create a context bound to the current CUDA device and to `cuda_stream`
  * (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream; NULL = the
- * legacy default stream).  cfg may be NULL.  -ENODEV without a CUDA device,
- * -ENOMEM when host or device memory runs out. */
+ * legacy default stream).  cfg may be NULL.  -ENODEV without a CUDA device
+ * (unless cfg->host_only), -ENOMEM when host or device memory runs out. */
 B3T_API int b3t_init(b3t_ctx **ctx, const b3t_config *cfg, void *cuda_stream);
 
 /* Wait for all pending work, release every library-owned resource and the

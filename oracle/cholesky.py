@@ -134,3 +134,36 @@ def task_flops(kind, b):
     SYRK b^2 (b + 1), GEMM 2 b^3."""
     return {POTRF: flops(b), TRSM: float(b) ** 3, SYRK: float(b) ** 2 * (b + 1),
             GEMM: 2.0 * b ** 3}[kind]
+
+
+def run_prefix(get_tile, T, b, budget_s):
+    """Run task_list(T) in submission order, each task at once, until
+    budget_s seconds have passed (a bounded sample of a factorisation too
+    large to run whole).  get_tile(i, j) returns the packed tile (b, b)
+    float64 array for (i, j), fetched lazily and then reused.  Returns
+    (tasks done, flops done, seconds)."""
+    import time
+    cache = {}
+
+    def tile(i, j):
+        if (i, j) not in cache:
+            cache[(i, j)] = np.ascontiguousarray(get_tile(i, j), dtype=np.float64)
+        return _F(cache[(i, j)])
+
+    done, fl = 0, 0.0
+    t0 = time.perf_counter()
+    for kind, acc in task_list(T):
+        v = [tile(i, j) for (i, j), _ in acc]
+        if kind == POTRF:
+            _t.potrf(v[0])
+        elif kind == TRSM:
+            _t.trsm(v[0], v[1])
+        elif kind == SYRK:
+            _t.syrk(v[0], v[1])
+        else:
+            _t.gemm(v[0], v[1], v[2])
+        done += 1
+        fl += task_flops(kind, b)
+        if time.perf_counter() - t0 > budget_s:
+            break
+    return done, fl, time.perf_counter() - t0

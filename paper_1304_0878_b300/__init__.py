@@ -1,0 +1,13 @@
+"""b3t: a task-DAG executor for one B300 GPU.
+
+The task-programming model of Courtes, "C Language Extensions for Hybrid
+CPU/GPU Programming with StarPU" (Section 2): tasks declared with their
+implementation and per-buffer access modes, registered buffers,
+asynchronous submission, dependencies derived from the access modes in
+submission order, and a wait.  The C-ABI library (include/b3t.h,
+libb3t.so) does all of it; this package only marshals arguments.
+"""
+from ._lib import (Context, B3TError, Config, lib, strerror, q_bytes, header_symbols,  # noqa: F401
+                   pack_f32, pack_i32, R, W, RW, NOOP, SCAL_F32, POTRF, TRSM, SYRK, GEMM,
+                   POTRF_MX, TRSM_MX, SYRK_MX, GEMM_MX, QUANT, FMT_BF16, FMT_E4M3)
+from . import tiles  # noqa: F401

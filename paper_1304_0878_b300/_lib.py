@@ -1,0 +1,255 @@
+"""ctypes binding of libb3t.so: argument marshalling only.
+
+Every function of include/b3t.h is reachable here under the same name
+without the ``b3t_`` prefix, as a method of :class:`Context`.  Every step of
+the task path (dependency derivation, task table build, scheduling, task
+bodies) runs in the library; nothing here computes.  A negative return code
+raises :class:`B3TError`.  The library must exist: there is no fallback.
+"""
+import ctypes
+import errno
+import os
+import re
+import struct
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libb3t.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "b3t.h")
+
+R, W, RW = 1, 2, 3
+NOOP, SCAL_F32, POTRF, TRSM, SYRK, GEMM = 0, 1, 2, 3, 4, 5
+POTRF_MX, TRSM_MX, SYRK_MX, GEMM_MX, QUANT = 6, 7, 8, 9, 10
+FMT_BF16, FMT_E4M3 = 0, 1
+
+
+class B3TError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (where, strerror(code), code))
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("timeout_ns", ctypes.c_int64), ("ctas_per_sm", ctypes.c_int32),
+                ("prio_levels", ctypes.c_int32), ("debug_checks", ctypes.c_int32),
+                ("host_only", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+
+
+_lib = None
+_i32, _i64, _vp, _sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_size_t
+_pi32, _pi64 = ctypes.POINTER(_i32), ctypes.POINTER(_i64)
+_pu8 = ctypes.POINTER(ctypes.c_uint8)
+
+_SIGS = {
+    "b3t_q_bytes": (_sz, [ctypes.c_int, ctypes.c_int]),
+    "b3t_init": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(Config), _vp]),
+    "b3t_shutdown": (ctypes.c_int, [_vp]),
+    "b3t_task_decl": (ctypes.c_int, [_vp, ctypes.c_char_p, ctypes.c_int, ctypes.c_int, _pu8, _sz, _pi32]),
+    "b3t_data_register": (ctypes.c_int, [_vp, _vp, _sz, _sz, _i64, _pi32]),
+    "b3t_data_lookup": (ctypes.c_int, [_vp, _vp, _pi32]),
+    "b3t_data_partition": (ctypes.c_int, [_vp, _i32, _i32, _sz, _pi32]),
+    "b3t_task_submit": (ctypes.c_int, [_vp, _i32, _pi32, _pu8, ctypes.c_int, _vp, _sz]),
+    "b3t_task_submit_ptrs": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(_vp), ctypes.c_int, _vp, _sz]),
+    "b3t_task_flush": (ctypes.c_int, [_vp]),
+    "b3t_task_wait": (ctypes.c_int, [_vp, _i64]),
+    "b3t_data_acquire": (ctypes.c_int, [_vp, _i32, ctypes.c_uint8]),
+    "b3t_data_unregister": (ctypes.c_int, [_vp, _i32]),
+    "b3t_last_error": (ctypes.c_int, [_vp, _pi32, _pi32]),
+    "b3t_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "b3t_graph_capture_begin": (ctypes.c_int, [_vp]),
+    "b3t_graph_capture_end": (ctypes.c_int, [_vp, _pi32]),
+    "b3t_graph_replay": (ctypes.c_int, [_vp, _i32]),
+    "b3t_graph_destroy": (ctypes.c_int, [_vp, _i32]),
+    "b3t_dag_stats": (ctypes.c_int, [_vp, _pi64, _pi64]),
+    "b3t_dag_edges": (ctypes.c_int, [_vp, _pi32, _pi32, _i64, _pi64]),
+    "b3t_last_launch": (ctypes.c_int, [_vp, _pi64, _pi64, _pi32, _pi64]),
+    "b3t_debug_block_task": (ctypes.c_int, [_vp, _i64]),
+    "b3t_cholesky_submit": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), _i32, _i32, _i32]),
+    "b3t_cholesky_mx_submit": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                              ctypes.POINTER(_vp), _i32, _i32, _i32, _i32]),
+    "b3t_tiles_unregister": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), _i32]),
+}
+
+
+def header_symbols():
+    """Names of every function include/b3t.h declares."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"B3T_API\s+[\w\s\*]*?\b(b3t_\w+)\s*\(", txt)))
+
+
+def lib():
+    """Load libb3t.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libb3t.so not built: run python -m paper_1304_0878_b300.build "
+                              "(there is no fallback path)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def strerror(code):
+    return lib().b3t_strerror(code).decode()
+
+
+def _check(rc, where):
+    if rc < 0:
+        raise B3TError(rc, where)
+    return rc
+
+
+def _ptrs(seq):
+    arr = (_vp * len(seq))()
+    for i, p in enumerate(seq):
+        arr[i] = int(p)
+    return arr
+
+
+def q_bytes(b, fmt):
+    return int(lib().b3t_q_bytes(b, fmt))
+
+
+class Context:
+    """One b3t context bound to a CUDA stream (a raw cudaStream_t value such
+    as ``torch.cuda.current_stream().cuda_stream``)."""
+
+    def __init__(self, stream=0, timeout_ns=0, ctas_per_sm=0, prio_levels=0, debug=False,
+                 host_only=False):
+        cfg = Config(timeout_ns, ctas_per_sm, prio_levels, 1 if debug else 0, 1 if host_only else 0)
+        h = _vp()
+        _check(lib().b3t_init(ctypes.byref(h), ctypes.byref(cfg), _vp(stream or 0)), "b3t_init")
+        self._h = h
+
+    def close(self):
+        if self._h:
+            h, self._h = self._h, None
+            _check(lib().b3t_shutdown(h), "b3t_shutdown")
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            if getattr(self, "_h", None):
+                lib().b3t_shutdown(self._h)
+        except Exception:
+            pass
+
+    # -- task model (Section 2 of the paper) ----------------------------------
+    def task_decl(self, name, kind, modes, scalar_bytes=0):
+        out = _i32()
+        m = (ctypes.c_uint8 * max(1, len(modes)))(*modes)
+        _check(lib().b3t_task_decl(self._h, name.encode(), kind, len(modes), m, scalar_bytes,
+                                   ctypes.byref(out)), "b3t_task_decl")
+        return out.value
+
+    def data_register(self, ptr, nelems, elemsize, ld=0):
+        out = _i32()
+        _check(lib().b3t_data_register(self._h, _vp(int(ptr)), nelems, elemsize, ld, ctypes.byref(out)),
+               "b3t_data_register")
+        return out.value
+
+    def data_lookup(self, ptr):
+        out = _i32()
+        _check(lib().b3t_data_lookup(self._h, _vp(int(ptr)), ctypes.byref(out)), "b3t_data_lookup")
+        return out.value
+
+    def data_partition(self, h, nparts, part_nelems):
+        out = (_i32 * nparts)()
+        _check(lib().b3t_data_partition(self._h, h, nparts, part_nelems, out), "b3t_data_partition")
+        return list(out)
+
+    def task_submit(self, cl, handles, scalars=b"", modes=None):
+        hs = (_i32 * max(1, len(handles)))(*handles)
+        ms = (ctypes.c_uint8 * len(modes))(*modes) if modes is not None else None
+        buf = ctypes.create_string_buffer(scalars, len(scalars)) if scalars else None
+        _check(lib().b3t_task_submit(self._h, cl, hs, ms, len(handles), buf, len(scalars)),
+               "b3t_task_submit")
+
+    def task_submit_ptrs(self, cl, ptrs, scalars=b""):
+        buf = ctypes.create_string_buffer(scalars, len(scalars)) if scalars else None
+        _check(lib().b3t_task_submit_ptrs(self._h, cl, _ptrs(ptrs), len(ptrs), buf, len(scalars)),
+               "b3t_task_submit_ptrs")
+
+    def task_flush(self):
+        _check(lib().b3t_task_flush(self._h), "b3t_task_flush")
+
+    def task_wait(self, timeout_ns=0):
+        _check(lib().b3t_task_wait(self._h, timeout_ns), "b3t_task_wait")
+
+    def data_acquire(self, h, mode=R):
+        _check(lib().b3t_data_acquire(self._h, h, mode), "b3t_data_acquire")
+
+    def data_unregister(self, h):
+        _check(lib().b3t_data_unregister(self._h, h), "b3t_data_unregister")
+
+    def last_error(self):
+        t, i = _i32(), _i32()
+        lib().b3t_last_error(self._h, ctypes.byref(t), ctypes.byref(i))
+        return t.value, i.value
+
+    # -- repeated DAGs ----------------------------------------------------------
+    def graph_capture_begin(self):
+        _check(lib().b3t_graph_capture_begin(self._h), "b3t_graph_capture_begin")
+
+    def graph_capture_end(self):
+        out = _i32()
+        _check(lib().b3t_graph_capture_end(self._h, ctypes.byref(out)), "b3t_graph_capture_end")
+        return out.value
+
+    def graph_replay(self, g):
+        _check(lib().b3t_graph_replay(self._h, g), "b3t_graph_replay")
+
+    def graph_destroy(self, g):
+        _check(lib().b3t_graph_destroy(self._h, g), "b3t_graph_destroy")
+
+    # -- introspection ----------------------------------------------------------
+    def dag_stats(self):
+        n, e = _i64(), _i64()
+        _check(lib().b3t_dag_stats(self._h, ctypes.byref(n), ctypes.byref(e)), "b3t_dag_stats")
+        return n.value, e.value
+
+    def dag_edges(self):
+        _, ne = self.dag_stats()
+        p, s, cnt = (_i32 * max(ne, 1))(), (_i32 * max(ne, 1))(), _i64()
+        _check(lib().b3t_dag_edges(self._h, p, s, ne, ctypes.byref(cnt)), "b3t_dag_edges")
+        return [(p[i], s[i]) for i in range(cnt.value)]
+
+    def last_launch(self):
+        nt, ni, nc, ns = _i64(), _i64(), _i32(), _i64()
+        _check(lib().b3t_last_launch(self._h, ctypes.byref(nt), ctypes.byref(ni), ctypes.byref(nc),
+                                     ctypes.byref(ns)), "b3t_last_launch")
+        return {"ntasks": nt.value, "nitems": ni.value, "nctas": nc.value, "kernel_ns": ns.value}
+
+    def debug_block_task(self, i):
+        _check(lib().b3t_debug_block_task(self._h, i), "b3t_debug_block_task")
+
+    # -- tiled Cholesky helpers -------------------------------------------------
+    def cholesky_submit(self, tile_ptrs, T, b, col0=0):
+        _check(lib().b3t_cholesky_submit(self._h, _ptrs(tile_ptrs), T, b, col0), "b3t_cholesky_submit")
+
+    def cholesky_mx_submit(self, W_ptrs, L_ptrs, Q_ptrs, T, b, fmt, col0=0):
+        _check(lib().b3t_cholesky_mx_submit(self._h, _ptrs(W_ptrs), _ptrs(L_ptrs), _ptrs(Q_ptrs),
+                                            T, b, fmt, col0), "b3t_cholesky_mx_submit")
+
+    def tiles_unregister(self, tile_ptrs, T):
+        _check(lib().b3t_tiles_unregister(self._h, _ptrs(tile_ptrs), T), "b3t_tiles_unregister")
+
+
+def pack_f32(x):
+    return struct.pack("<f", x)
+
+
+def pack_i32(x):
+    return struct.pack("<i", x)
+
+
+ENOENT, EINVAL, EEXIST, EBUSY = -errno.ENOENT, -errno.EINVAL, -errno.EEXIST, -errno.EBUSY
+ENODEV, ETIMEDOUT, EDOM, EIO = -errno.ENODEV, -errno.ETIMEDOUT, -errno.EDOM, -errno.EIO

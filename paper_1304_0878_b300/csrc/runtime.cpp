@@ -377,6 +377,7 @@ int track(b3t_ctx *c, Ctl *dev) {
 
 int flush_impl(b3t_ctx *c) {
     if (c->tasks.empty()) return 0;
+    if (c->cfg.host_only) { clear_batch(c); return -ENODEV; }
     InitParams ip; LaunchParams lp; int64_t nitems; bool has_mx;
     int rc = build_launch(c, c->arena, ip, lp, nitems, has_mx);
     if (rc) { clear_batch(c); return rc; }
@@ -429,6 +430,7 @@ int read_status(b3t_ctx *c) {
 
 int wait_impl(b3t_ctx *c, int64_t timeout_ns) {
     int rc = flush_impl(c);
+    if (c->cfg.host_only) return rc;
     const int rs = sync_stream(c, timeout_ns);
     if (rs) return rs;
     const int st = read_status(c);
@@ -519,8 +521,12 @@ size_t b3t_q_bytes(int b, int fmt) {
 int b3t_init(b3t_ctx **out, const b3t_config *cfg, void *cuda_stream) {
     if (!out) return -EINVAL;
     *out = nullptr;
+    const bool host_only = cfg && cfg->host_only;
     int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) { cudaGetLastError(); return -ENODEV; }
+    if (!host_only && (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)) {
+        cudaGetLastError();
+        return -ENODEV;
+    }
     b3t_ctx *c = new (std::nothrow) b3t_ctx();
     if (!c) return -ENOMEM;
     if (cfg) c->cfg = *cfg;
@@ -528,6 +534,7 @@ int b3t_init(b3t_ctx **out, const b3t_config *cfg, void *cuda_stream) {
     if (c->cfg.prio_levels <= 0) c->cfg.prio_levels = kMaxLevels;
     c->cfg.prio_levels = std::min(c->cfg.prio_levels, kMaxLevels);
     for (int k = 0; k < kNumKinds; ++k) c->kind_cl[k] = -1;
+    if (host_only) { *out = c; return 0; }
     cudaGetDevice(&c->device);
     c->stream = (cudaStream_t)cuda_stream;
     if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess ||
@@ -541,6 +548,7 @@ int b3t_init(b3t_ctx **out, const b3t_config *cfg, void *cuda_stream) {
 
 int b3t_shutdown(b3t_ctx *c) {
     if (!c) return -EINVAL;
+    if (c->cfg.host_only) { delete c; return 0; }
     const int rc = wait_impl(c, 0);
     for (auto &g : c->graphs) {
         if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -717,6 +725,7 @@ int b3t_graph_capture_end(b3t_ctx *c, b3t_graph *out) {
     if (!c || !out || !c->capturing) return -EINVAL;
     c->capturing = false;
     if (c->tasks.empty()) return -EINVAL;
+    if (c->cfg.host_only) { clear_batch(c); return -ENODEV; }
     GraphRec g;
     InitParams ip; LaunchParams lp; int64_t nitems; bool has_mx;
     int rc = build_launch(c, g.arena, ip, lp, nitems, has_mx);

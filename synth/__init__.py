@@ -9,8 +9,8 @@ Recipes (numpy PCG64 ``default_rng(seed)`` unless stated):
     factors f[blk][k] ~ U[0.5, 2) drawn block-major (blk outer, k inner),
     rounded to float32.
   * SPD matrices: A = B B^T / N + shift * I with B_ij ~ N(0, 1) (float64).
-    Division by N is exact for N a power of two.  Large N is formed on the
-    GPU with torch's FP64 matmul from a B drawn on the host in row blocks.
+    Division by N is exact for N a power of two.  Large N (spd_tiles_device)
+    is formed on the GPU in binary32 and widened to FP64.
   * integer SPD matrices: A = L0 L0^T with L0 lower triangular, small
     integer entries and a positive integer diagonal, formed in int64 (exact
     below 2^53), so every Cholesky step on it is exact.
@@ -51,29 +51,34 @@ def spd_host(N, seed=0, shift=1.0):
     return A
 
 
-def spd_tiles_device(N, b, seed, shift, device, dtype=None):
-    """Packed lower tiles (column-major inside a tile) of A = B B^T/N + shift I,
-    formed on `device` with torch FP64 matmul; B is drawn on the host row
-    block by row block from default_rng(seed) (the same stream as
-    spd_host).  Returns a torch tensor of shape (T(T+1)/2, b, b) where
-    out[t, c, r] = A[i*b + r, j*b + c] for tile t = (i, j) in column order."""
+def spd_tiles_device(N, b, seed, shift, device):
+    """Packed lower tiles (column-major inside a tile) of an SPD matrix
+    A = B B^T / N + shift I formed on `device`, for sizes too large to form on
+    the host: B ~ N(0, 1) is drawn in binary32 by torch's CUDA generator
+    seeded with `seed`, B B^T is formed by a binary32 matmul (no TF32) one
+    row block of tiles at a time, then widened to FP64, divided by N (exact)
+    and shifted.  The bytes returned are the input's definition.  Returns a
+    tensor of shape (T(T+1)/2, b, b) with out[t, c, r] = A[i*b + r, j*b + c]
+    for tile t = (i, j) in packed column order."""
     import torch
     assert N % b == 0
     T = N // b
-    rng = np.random.default_rng(seed)
-    Bd = torch.empty((N, N), dtype=torch.float64, device=device)
-    rows = max(b, (1 << 27) // N)   # ~1 GiB of host doubles per chunk
-    for s in range(0, N, rows):
-        m = min(rows, N - s)
-        Bd[s:s + m] = torch.from_numpy(rng.standard_normal((m, N))).to(device)
-    nt = T * (T + 1) // 2
-    out = torch.empty((nt, b, b), dtype=torch.float64, device=device)
-    for i in range(T):
-        blk = Bd[i * b:(i + 1) * b] @ Bd[:(i + 1) * b].T / N     # b x (i+1)b
-        for j in range(i + 1):
-            t = j * T - j * (j - 1) // 2 + (i - j)
-            out[t] = blk[:, j * b:(j + 1) * b].T
-    del Bd
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    B = torch.randn((N, N), generator=g, device=device, dtype=torch.float32)
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        nt = T * (T + 1) // 2
+        out = torch.empty((nt, b, b), dtype=torch.float64, device=device)
+        for i in range(T):
+            blk = (B[i * b:(i + 1) * b] @ B[:(i + 1) * b].T).double() / N   # b x (i+1)b
+            for j in range(i + 1):
+                t = j * T - j * (j - 1) // 2 + (i - j)
+                out[t] = blk[:, j * b:(j + 1) * b].T
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    del B
     idx = torch.arange(b, device=device)
     for k in range(T):
         t = k * T - k * (k - 1) // 2

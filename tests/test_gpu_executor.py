@@ -1,0 +1,227 @@
+"""Device executor against the oracle (GPU).  Every result is compared with
+the sequential oracle run on the same seeded inputs: bit-exact for the
+vector chains and integer-exact Cholesky, within a stated FP64 tolerance
+otherwise (the device sums in another order and with FMA)."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+import paper_1304_0878_b300 as b3t
+from paper_1304_0878_b300 import tiles as dt
+from oracle import cholesky as och, executor as oex, tiles as otl
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="no CUDA device")]
+R, W, RW = 1, 2, 3
+FP64_TOL = 1e-12     # max |L_gpu - L_orc| / max |L_orc|
+
+
+def run_chain_device(ctx, x, f, order="k"):
+    nb, nk = f.shape
+    n = x.size // nb
+    xd = torch.from_numpy(x.copy()).cuda()
+    blocks = [xd[i * n:(i + 1) * n] for i in range(nb)]
+    hs = [ctx.data_register(bl.data_ptr(), n, 4) for bl in blocks]
+    cl = ctx.task_decl("scale_vector", b3t.SCAL_F32, [RW], 4)
+    seq = [(k, i) for k in range(nk) for i in range(nb)] if order == "k" else \
+          [(k, i) for i in range(nb) for k in range(nk)]
+    for k, i in seq:
+        ctx.task_submit(cl, [hs[i]], b3t.pack_f32(float(f[i, k])))
+    ctx.task_wait()
+    for h in hs:
+        ctx.data_unregister(h)
+    return xd.cpu().numpy()
+
+
+def run_chain_oracle(x, f):
+    nb, nk = f.shape
+    n = x.size // nb
+    y = x.copy()
+    ex = oex.Executor()
+    cl = ex.task_decl("scale_vector", oex.scal_body, [RW])
+    hs = [ex.data_register(y[i * n:(i + 1) * n]) for i in range(nb)]
+    for k in range(nk):
+        for i in range(nb):
+            ex.task_submit(cl, [hs[i]], scalars=(f[i, k],))
+    return y
+
+
+@pytest.mark.parametrize("nb,n,order", [(16, (1 << 16) + 4, "k"), (8, 3 * (1 << 16) + 12, "b"),
+                                        (5, 1000, "k")])
+def test_scal_chains_bit_exact(orc, gctx, nb, n, order):
+    x = synth.vector_f32(nb * n, seed=1)
+    x[:7] = np.array([1e-38, -3e-39, 5e-45, 0.0, -0.0, 3e38, -1.0], dtype=np.float32)
+    f = synth.chain_factors(nb, 8, seed=2)
+    y = run_chain_device(gctx, x, f, order)
+    z = run_chain_oracle(x, f)
+    assert np.array_equal(y.view(np.uint32), z.view(np.uint32))
+
+
+def test_scal_full_size_config(orc, gctx):
+    # n = 2^28, 256 blocks x 8 chained tasks: compared element-wise against
+    # in-order binary32 multiplies on sampled blocks (the whole vector fits
+    # the oracle only slowly)
+    nb, nk, n = 256, 8, 1 << 20
+    x = synth.vector_f32(nb * n, seed=1)
+    f = synth.chain_factors(nb, nk, seed=2)
+    y = run_chain_device(gctx, x, f)
+    for i in [0, 1, 77, 128, 255]:
+        z = x[i * n:(i + 1) * n].copy()
+        for k in range(nk):
+            otl.scal_f32(z, f[i, k])
+        assert np.array_equal(y[i * n:(i + 1) * n].view(np.uint32), z.view(np.uint32))
+
+
+def factor_device(ctx, A, b, col0=0):
+    N = A.shape[0]
+    T = N // b
+    t = torch.from_numpy(och.to_tiles(A, b)).cuda()
+    ptrs = dt.tile_ptrs(t)
+    ctx.cholesky_submit(ptrs, T, b, col0)
+    ctx.task_wait()
+    ctx.tiles_unregister(ptrs, T)
+    return np.tril(och.from_tiles(t.cpu().numpy(), N, b))
+
+
+def factor_oracle(A, b):
+    N = A.shape[0]
+    t = och.to_tiles(A, b)
+    info = och.run(t, N // b, b)
+    assert info == 0
+    return np.tril(och.from_tiles(t, N, b))
+
+
+@pytest.mark.parametrize("N,b", [(256, 64), (512, 128), (576, 192), (1024, 256)])
+def test_cholesky_integer_exact(orc, gctx, N, b):
+    A, L0 = synth.integer_spd(N, seed=N + b)
+    L = factor_device(gctx, A, b)
+    assert np.array_equal(L, L0)
+
+
+def test_cholesky_config1_parity(orc, gctx):
+    # N = 1024, tile 128 (8 x 8 tiles, 120 tasks), A = B B^T / N + I, seed 0
+    A = synth.spd_host(1024, seed=0, shift=1.0)
+    L = factor_device(gctx, A, 128)
+    Lo = factor_oracle(A, 128)
+    assert np.max(np.abs(L - Lo)) / np.max(np.abs(Lo)) <= FP64_TOL
+    assert och.rel_residual(L, A) <= 1e-12
+    st = gctx.last_launch()
+    assert st["ntasks"] == 120
+
+
+@pytest.mark.parametrize("N,b", [(320, 64), (1536, 512)])
+def test_cholesky_other_tiles(orc, gctx, N, b):
+    A = synth.spd_host(N, seed=3, shift=0.1)
+    L = factor_device(gctx, A, b)
+    Lo = factor_oracle(A, b)
+    assert np.max(np.abs(L - Lo)) / np.max(np.abs(Lo)) <= FP64_TOL
+    assert och.rel_residual(L, A) <= 1e-12
+
+
+def test_cholesky_deterministic(orc, gctx):
+    A = synth.spd_host(768, seed=8, shift=1.0)
+    outs = [factor_device(gctx, A, 128) for _ in range(3)]
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
+
+
+def test_not_spd_reports_info(orc, gctx):
+    A = synth.spd_host(512, seed=4, shift=1.0)
+    A[300, 300] = -10.0
+    with pytest.raises(b3t.B3TError) as e:
+        factor_device(gctx, A, 128, col0=0)
+    assert e.value.code == b3t._lib.EDOM
+    task, info = gctx.last_error()
+    # the oracle stops at the same column
+    t = och.to_tiles(A, 128)
+    assert och.run(t, 4, 128) == info == 301
+    # the context stays usable
+    A2, L0 = synth.integer_spd(256, seed=1)
+    assert np.array_equal(factor_device(gctx, A2, 64), L0)
+
+
+def test_single_tasks_against_oracle(orc, gctx):
+    rng = np.random.default_rng(7)
+    b = 128
+    M = rng.standard_normal((b, b))
+    Lk = np.tril(M) + b * np.eye(b)
+    A = rng.standard_normal((b, b))
+    B = rng.standard_normal((b, b))
+    C = rng.standard_normal((b, b))
+    dev = {k: torch.from_numpy(np.ascontiguousarray(v.T)).cuda() for k, v in
+           dict(L=Lk, A=A, B=B, C=C, S=C.copy()).items()}
+    h = {k: gctx.data_register(v.data_ptr(), b * b, 8, b) for k, v in dev.items()}
+    ct = gctx.task_decl("trsm", b3t.TRSM, [R, RW])
+    cg = gctx.task_decl("gemm", b3t.GEMM, [R, R, RW])
+    cs = gctx.task_decl("syrk", b3t.SYRK, [R, RW])
+    gctx.task_submit(cg, [h["A"], h["B"], h["C"]])
+    gctx.task_submit(cs, [h["A"], h["S"]])
+    gctx.task_submit(ct, [h["L"], h["A"]])     # after GEMM / SYRK read A (WAR)
+    gctx.task_wait()
+    got = {k: v.cpu().numpy().T for k, v in dev.items()}
+    X = np.asfortranarray(A.copy()); otl.trsm(np.asfortranarray(Lk), X)
+    Cg = np.asfortranarray(C.copy()); otl.gemm(np.asfortranarray(A), np.asfortranarray(B), Cg)
+    Cs = np.asfortranarray(C.copy()); otl.syrk(np.asfortranarray(A), Cs)
+    assert np.max(np.abs(got["A"] - X)) <= 1e-13 * np.max(np.abs(X))
+    assert np.max(np.abs(got["C"] - Cg)) <= 1e-13 * np.max(np.abs(Cg))
+    assert np.max(np.abs(np.tril(got["S"]) - np.tril(Cs))) <= 1e-13 * np.max(np.abs(Cs))
+    assert np.array_equal(np.triu(got["S"], 1), np.triu(C, 1))   # upper untouched
+
+
+def test_graph_capture_replay(orc, gctx):
+    N, b = 512, 128
+    T = N // b
+    A = synth.spd_host(N, seed=11, shift=1.0)
+    At = torch.from_numpy(och.to_tiles(A, b)).cuda()
+    t = At.clone()
+    ptrs = dt.tile_ptrs(t)
+    gctx.graph_capture_begin()
+    gctx.cholesky_submit(ptrs, T, b)
+    g = gctx.graph_capture_end()
+    outs = []
+    for _ in range(3):
+        t.copy_(At)
+        gctx.graph_replay(g)
+        gctx.task_wait()
+        outs.append(np.tril(och.from_tiles(t.cpu().numpy(), N, b)))
+    ref = factor_device(gctx, A, b)
+    for o in outs:
+        assert np.array_equal(o, ref)
+    gctx.graph_destroy(g)
+
+
+def test_timeout_is_bounded_and_recoverable(orc):
+    # a task whose dependency counter never reaches zero: the launch must end
+    # through the device-side timeout, and the context must stay usable
+    c = b3t.Context(stream=torch.cuda.current_stream().cuda_stream, timeout_ns=50_000_000)
+    x = torch.ones(1 << 16, device="cuda")
+    h = c.data_register(x.data_ptr(), x.numel(), 4)
+    cl = c.task_decl("scale_vector", b3t.SCAL_F32, [RW], 4)
+    c.task_submit(cl, [h], b3t.pack_f32(2.0))
+    c.task_submit(cl, [h], b3t.pack_f32(2.0))
+    c.debug_block_task(1)
+    with pytest.raises(b3t.B3TError) as e:
+        c.task_wait()
+    assert e.value.code == b3t._lib.ETIMEDOUT
+    assert float(x[0]) == 2.0             # the first task ran, the second never
+    c.task_submit(cl, [h], b3t.pack_f32(3.0))
+    c.task_wait()
+    assert float(x[-1]) == 6.0
+    c.close()
+
+
+def test_noop_dags_and_partitions(orc, gctx):
+    # many tiny tasks: chains, fan-out / fan-in through a partitioned buffer
+    x = torch.zeros(1 << 12, device="cuda")
+    hp = gctx.data_register(x.data_ptr(), x.numel(), 4)
+    parts = gctx.data_partition(hp, 64, 64)
+    c1 = gctx.task_decl("touch", b3t.NOOP, [RW])
+    call = gctx.task_decl("all", b3t.NOOP, [R])
+    for rep in range(20):
+        for p in parts:
+            gctx.task_submit(c1, [p])
+        gctx.task_submit(call, [hp])
+    nt, ne = gctx.dag_stats()
+    assert nt == 20 * 65
+    gctx.task_wait()
+    assert gctx.last_launch()["ntasks"] == nt

@@ -1,0 +1,187 @@
+"""C-ABI library on the host (no GPU): it loads, exports every function of
+include/b3t.h, derives exactly the oracle's dependency edges, and reports
+the errors the paper's tooling diagnoses (Section 3.2) as return codes."""
+import subprocess
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+import paper_1304_0878_b300 as b3t
+from oracle import dag, cholesky as och
+
+R, W, RW = 1, 2, 3
+
+
+@pytest.fixture
+def ctx():
+    b3t.lib()
+    c = b3t.Context(host_only=True)
+    yield c
+    c.close()
+
+
+def fake_ptr(i):
+    return 0x10000000 + (i << 20)   # distinct, 16-byte aligned, never dereferenced
+
+
+def test_exports_every_header_symbol():
+    names = b3t.header_symbols()
+    assert len(names) >= 20
+    out = subprocess.check_output(["nm", "-D", "--defined-only", b3t._lib.LIB_PATH]).decode()
+    exported = {l.split()[-1] for l in out.splitlines() if l.strip()}
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    L = b3t.lib()
+    for n in names:
+        assert hasattr(L, n)
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="a CUDA device is present")
+def test_init_without_device_reports_enodev():
+    with pytest.raises(b3t.B3TError) as e:
+        b3t.Context()
+    assert e.value.code == b3t._lib.ENODEV
+
+
+def _submit_accesses(c, accesses, nhandles, parts=None):
+    hs = [c.data_register(fake_ptr(i), 64, 4) for i in range(nhandles)]
+    pmap = {}
+    for parent, nkids in (parts or {}).items():
+        pmap[parent] = c.data_partition(hs[parent], nkids, 64 // nkids)
+    cls = {}
+    for acc in accesses:
+        modes = tuple(m for _, m in acc)
+        if modes not in cls:
+            cls[modes] = c.task_decl("t", b3t.NOOP, list(modes))
+        c.task_submit(cls[modes], [hs[h] for h, _ in acc])
+    return hs, pmap
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_edges_match_oracle_random(ctx, seed):
+    n = 5 + seed % 20
+    nh = 2 + seed % 6
+    acc = synth.random_accesses(n, nhandles=nh, maxbuf=min(3, nh), seed=1000 + seed)
+    _submit_accesses(ctx, acc, nh)
+    assert sorted(ctx.dag_edges()) == dag.derive_edges(acc)
+
+
+def test_edges_match_oracle_with_partitions(ctx):
+    rng = np.random.default_rng(5)
+    hs = [ctx.data_register(fake_ptr(i), 64, 4) for i in range(3)]
+    kids = ctx.data_partition(hs[0], 4, 16)           # handle 0 -> 4 parts
+    # oracle names: parts 10..13 of parent 0; plain handles 1, 2
+    parts = {0: (10, 11, 12, 13)}
+    lib_of = {0: hs[0], 1: hs[1], 2: hs[2], 10: kids[0], 11: kids[1], 12: kids[2], 13: kids[3]}
+    acc = []
+    cls = {}
+    for _ in range(40):
+        k = int(rng.integers(1, 4))
+        names = rng.choice([0, 1, 2, 10, 11, 12, 13], size=k, replace=False)
+        a = [(int(h), int(rng.integers(1, 4))) for h in names]
+        modes = tuple(m for _, m in a)
+        if modes not in cls:
+            cls[modes] = ctx.task_decl("t", b3t.NOOP, list(modes))
+        ctx.task_submit(cls[modes], [lib_of[h] for h, _ in a])
+        acc.append(a)
+    assert sorted(ctx.dag_edges()) == dag.derive_edges(acc, parts)
+
+
+@pytest.mark.parametrize("T", [1, 2, 8, 64])
+def test_cholesky_submission_edges(ctx, T):
+    b = 128
+    ptrs = [fake_ptr(i) for i in range(och.ntiles(T))]
+    ctx.cholesky_submit(ptrs, T, b)
+    nt, ne = ctx.dag_stats()
+    acc = och.accesses(T)
+    assert nt == len(acc)
+    assert sorted(ctx.dag_edges()) == dag.derive_edges(acc)
+
+
+def test_mixed_submission_edges(ctx):
+    from oracle import mixed
+    T, b = 6, 128
+    nt = och.ntiles(T)
+    Wp = [fake_ptr(i) for i in range(nt)]
+    Lp = [fake_ptr(1000 + i) for i in range(nt)]
+    Qp = [fake_ptr(2000 + i) for i in range(nt)]
+    ctx.cholesky_mx_submit(Wp, Lp, Qp, T, b, b3t.FMT_BF16)
+    key = {}
+    acc = []
+    for kind, a in mixed.task_list(T):
+        acc.append([(key.setdefault(buf, len(key)), m) for buf, m in a])
+        if kind == mixed.TRSM_MX:
+            # the library submits QUANT(L_ik: R, Q_ik: W) right after TRSM_MX
+            (_, i, k) = a[2][0]
+            acc.append([(key.setdefault(("L", i, k), len(key)), R),
+                        (key.setdefault(("Q", i, k), len(key)), W)])
+    assert ctx.dag_stats()[0] == len(acc)
+    assert sorted(ctx.dag_edges()) == dag.derive_edges(acc)
+
+
+def test_chain_edges(ctx):
+    nb, nk = 256, 8
+    hs = [ctx.data_register(fake_ptr(i), 1 << 20, 4) for i in range(nb)]
+    cl = ctx.task_decl("scale_vector", b3t.SCAL_F32, [RW], 4)
+    for k in range(nk):
+        for i in range(nb):
+            ctx.task_submit(cl, [hs[i]], b3t.pack_f32(1.5))
+    assert ctx.dag_stats() == (2048, 1792)
+    acc = [[(i, RW)] for k in range(nk) for i in range(nb)]
+    assert sorted(ctx.dag_edges()) == dag.derive_edges(acc)
+
+
+def test_error_codes(ctx):
+    E = b3t._lib
+    h = ctx.data_register(fake_ptr(1), 1024, 4)
+    with pytest.raises(b3t.B3TError) as e:
+        ctx.data_register(fake_ptr(1), 1024, 4)
+    assert e.value.code == E.EEXIST
+    with pytest.raises(b3t.B3TError) as e:
+        ctx.data_lookup(fake_ptr(2))           # unregistered pointer
+    assert e.value.code == E.ENOENT
+    cl = ctx.task_decl("scale_vector", b3t.SCAL_F32, [RW], 4)
+    with pytest.raises(b3t.B3TError) as e:     # declaration vs kind signature
+        ctx.task_decl("bad", b3t.SCAL_F32, [R], 4)
+    assert e.value.code == E.EINVAL
+    with pytest.raises(b3t.B3TError) as e:     # wrong scalar blob
+        ctx.task_decl("bad", b3t.TRSM, [R, RW], 4)
+    assert e.value.code == E.EINVAL
+    with pytest.raises(b3t.B3TError) as e:     # mode used differs from declared
+        ctx.task_submit(cl, [h], b3t.pack_f32(2.0), modes=[R])
+    assert e.value.code == E.EINVAL
+    with pytest.raises(b3t.B3TError) as e:
+        ctx.task_submit(cl, [12345], b3t.pack_f32(2.0))
+    assert e.value.code == E.ENOENT
+    with pytest.raises(b3t.B3TError) as e:     # pointer form: lookup failure
+        ctx.task_submit_ptrs(cl, [fake_ptr(3)], b3t.pack_f32(2.0))
+    assert e.value.code == E.ENOENT
+    ctx.task_submit_ptrs(cl, [fake_ptr(1)], b3t.pack_f32(2.0))
+    # tile kinds check buffer shapes: f32 buffer where f64 tile is expected
+    t = ctx.data_register(fake_ptr(9), 128 * 128, 4, 128)
+    cp = ctx.task_decl("potrf", b3t.POTRF, [RW], 4)
+    with pytest.raises(b3t.B3TError) as e:
+        ctx.task_submit(cp, [t], b3t.pack_i32(0))
+    assert e.value.code == E.EINVAL
+    assert ctx.dag_stats()[0] == 1
+    with pytest.raises(b3t.B3TError) as e:     # no device in host-only mode
+        ctx.task_wait()
+    assert e.value.code == E.ENODEV
+    assert ctx.dag_stats() == (0, 0)
+    ctx.data_unregister(h)
+    with pytest.raises(b3t.B3TError) as e:
+        ctx.task_submit(cl, [h], b3t.pack_f32(2.0))
+    assert e.value.code == E.ENOENT
+
+
+def test_q_bytes():
+    assert b3t.q_bytes(512, b3t.FMT_BF16) == 512 * 512 * 2 + 16
+    assert b3t.q_bytes(256, b3t.FMT_E4M3) == 256 * 256 + 16
+    assert b3t.q_bytes(100, b3t.FMT_BF16) == 0
+
+
+def test_strerror():
+    assert "unregistered" in b3t.strerror(b3t._lib.ENOENT)
+    assert "positive definite" in b3t.strerror(b3t._lib.EDOM)
