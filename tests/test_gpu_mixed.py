@@ -1,0 +1,144 @@
+"""Mixed-precision tasks against the oracle (GPU): quantisation bit-exact
+(both sides round FP64 -> binary32 -> format the same way), tensor-core
+updates exact when every product and partial sum is representable, and
+within the binary32 accumulation bound otherwise."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+import paper_1304_0878_b300 as b3t
+from paper_1304_0878_b300 import tiles as dt
+from oracle import cholesky as och, mixed as omx, tiles as otl
+from qlayout import decode
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="no CUDA device")]
+R, W, RW = 1, 2, 3
+FMTS = {"bf16": b3t.FMT_BF16, "e4m3": b3t.FMT_E4M3}
+U32 = 2.0 ** -24
+
+
+def dev_tile(M, dtype=torch.float64):
+    """(r, c) matrix -> device tile (column-major)."""
+    return torch.from_numpy(np.ascontiguousarray(M.T)).to(dtype).cuda()
+
+
+def quantise_dev(ctx, Lm, fmt, b):
+    L = dev_tile(Lm)
+    Q = torch.zeros(b3t.q_bytes(b, FMTS[fmt]), dtype=torch.uint8, device="cuda")
+    hl = ctx.data_register(L.data_ptr(), b * b, 8, b)
+    hq = ctx.data_register(Q.data_ptr(), Q.numel(), 1, b)
+    cq = ctx.task_decl("quant", b3t.QUANT, [R, W], 4)
+    ctx.task_submit(cq, [hl, hq], b3t.pack_i32(FMTS[fmt]))
+    ctx.task_wait()
+    ctx.data_unregister(hl)
+    return Q, hq
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "e4m3"])
+@pytest.mark.parametrize("b", [128, 256])
+def test_quant_bit_exact(orc, gctx, fmt, b):
+    rng = np.random.default_rng(b)
+    Lm = rng.standard_normal((b, b)) * 10.0 ** rng.integers(-3, 3)
+    Lm[0, 0] = 1e-30
+    Q, hq = quantise_dev(gctx, Lm, fmt, b)
+    vals, e = decode(Q.cpu().numpy(), b, FMTS[fmt])
+    qo, eo = otl.quantise(Lm, fmt)
+    assert e == eo
+    assert np.array_equal(vals, qo)
+
+
+def mx_update_dev(ctx, QA_m, QB_m, W0, fmt, b, syrk):
+    """Run SYRK_MX / GEMM_MX with Q tiles produced by QUANT from exact
+    values (so the device operands equal the oracle's)."""
+    QA, ha = quantise_dev(ctx, QA_m, fmt, b)
+    if not syrk:
+        QB, hb = quantise_dev(ctx, QB_m, fmt, b)
+    Wd = dev_tile(W0, torch.float32)
+    hw = ctx.data_register(Wd.data_ptr(), b * b, 4, b)
+    if syrk:
+        cs = ctx.task_decl("syrk_mx", b3t.SYRK_MX, [R, RW], 4)
+        ctx.task_submit(cs, [ha, hw], b3t.pack_i32(FMTS[fmt]))
+    else:
+        cg = ctx.task_decl("gemm_mx", b3t.GEMM_MX, [R, R, RW], 4)
+        ctx.task_submit(cg, [ha, hb, hw], b3t.pack_i32(FMTS[fmt]))
+    ctx.task_wait()
+    for h in ([ha, hw] if syrk else [ha, hb, hw]):
+        ctx.data_unregister(h)
+    return Wd.cpu().numpy().T
+
+
+@pytest.mark.parametrize("fmt,lim", [("bf16", 32), ("e4m3", 8)])
+@pytest.mark.parametrize("syrk", [False, True])
+def test_mx_update_exact_on_integers(orc, gctx, fmt, lim, syrk):
+    b = 256
+    rng = np.random.default_rng(3)
+    A = rng.integers(-lim, lim + 1, (b, b)).astype(np.float64)
+    B = rng.integers(-lim, lim + 1, (b, b)).astype(np.float64)
+    W0 = rng.integers(-4096, 4096, (b, b)).astype(np.float32)
+    got = mx_update_dev(gctx, A, B, W0, fmt, b, syrk)
+    qa, ea = otl.quantise(A, fmt)
+    qb, eb = otl.quantise(A if syrk else B, fmt)
+    ref = np.asfortranarray(W0.copy())
+    otl.gemm_lowp(qa, qb, 2.0 ** (ea + eb), ref, lower=syrk)
+    if syrk:
+        assert np.array_equal(np.tril(got), np.tril(ref))
+        assert np.array_equal(np.triu(got, 1), np.triu(W0, 1))
+    else:
+        assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "e4m3"])
+def test_mx_update_within_fp32_bound(orc, gctx, fmt):
+    b = 384
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((b, b)) * 0.3
+    B = rng.standard_normal((b, b)) * 0.3
+    W0 = rng.standard_normal((b, b)).astype(np.float32)
+    got = mx_update_dev(gctx, A, B, W0, fmt, b, False)
+    qa, ea = otl.quantise(A, fmt)
+    qb, eb = otl.quantise(B, fmt)
+    s = 2.0 ** (ea + eb)
+    ref = np.asfortranarray(W0.copy())
+    otl.gemm_lowp(qa, qb, s, ref)
+    # binary32 accumulation of b products plus the final rounding
+    bound = (b + 2) * U32 * (s * otl.gemm_abs(qa, qb) + np.abs(W0)) + U32 * np.abs(ref)
+    assert np.all(np.abs(got - ref) <= bound)
+
+
+def factor_mx_dev(ctx, A, b, fmt):
+    N = A.shape[0]
+    T = N // b
+    At = torch.from_numpy(och.to_tiles(A, b)).cuda()
+    Wt = At.float()
+    Lt = torch.zeros_like(At)
+    Qt = dt.q_tiles(T, b, FMTS[fmt], "cuda")
+    wp, lp, qp = dt.tile_ptrs(Wt), dt.tile_ptrs(Lt), dt.tile_ptrs(Qt)
+    ctx.cholesky_mx_submit(wp, lp, qp, T, b, FMTS[fmt])
+    ctx.task_wait()
+    for p in (wp, lp, qp):
+        ctx.tiles_unregister(p, T)
+    return np.tril(och.from_tiles(Lt.cpu().numpy(), N, b))
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "e4m3"])
+@pytest.mark.parametrize("N,b", [(512, 128), (768, 256)])
+def test_mixed_factor_exact_on_integer_matrix(orc, gctx, fmt, N, b):
+    A, L0 = synth.integer_spd(N, seed=N + 7)
+    L = factor_mx_dev(gctx, A, b, fmt)
+    assert np.array_equal(L, L0)
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "e4m3"])
+def test_mixed_factor_matches_mixed_oracle(orc, gctx, fmt):
+    N, b = 1024, 128
+    A = synth.spd_host(N, seed=0, shift=1.0)
+    L = factor_mx_dev(gctx, A, b, fmt)
+    Lt, info = omx.factor(och.to_tiles(A, b), N // b, b, fmt)
+    Lo = np.tril(och.from_tiles(Lt, N, b))
+    r_dev, r_orc = och.rel_residual(L, A), och.rel_residual(Lo, A)
+    # same low-precision factor up to binary32 accumulation order
+    assert r_dev <= 2.0 * r_orc + 1e-6
+    tol = 1e-3 if fmt == "bf16" else 5e-2
+    assert np.max(np.abs(L - Lo)) / np.max(np.abs(Lo)) <= tol
