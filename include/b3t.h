@@ -276,6 +276,33 @@ B3T_API int b3t_cholesky_mx_submit(b3t_ctx *ctx, float *const *W, double *const 
 /* Wait, then unregister the T(T+1)/2 tiles given (any registered set). */
 B3T_API int b3t_tiles_unregister(b3t_ctx *ctx, void *const *tiles, int32_t T);
 
+/* ---------------------------------------------------------------------
+ * Allocation-free vector-scaling chains.  The paper has no counterpart: it
+ * is an extra entry point for callers that cannot let a library allocate
+ * device memory -- a process whose GPU memory is all reserved by a
+ * framework's caching allocator, code that cannot afford the device-wide
+ * synchronisation cudaMalloc / cudaFree may imply, or hosts that forbid
+ * allocation after start-up.  It performs no cudaMalloc, cudaFree or other
+ * allocating call; its scratch (a ticket counter, a status word and one
+ * completion counter per task) is a fixed file-scope device array of
+ * about 256 KiB that every GPU loading the library holds until exit.
+ *
+ * Computes, for every block i < nblocks and every step k < nchain in order,
+ * x_i[e] <- fl32(x_i[e] * factors[i * nchain + k]), where block i is
+ * x[i*n .. i*n + n): the same results, bit for bit, as submitting the
+ * B3T_SCAL_F32 task chains through b3t_task_submit.  x and factors are
+ * device pointers owned by the caller; x must be 16-byte aligned and n a
+ * multiple of 4 (-EINVAL otherwise).  nblocks * nchain may not exceed 65536
+ * (-E2BIG).  timeout_ns bounds every device-side wait (0 = 10 s;
+ * -ETIMEDOUT).  Runs on cuda_stream and returns after it has finished.
+ * The first call on a device looks up the array's device address and the
+ * grid size (once per device, with that device current); make that first
+ * call before any stream capture.  Every call on a device shares the one
+ * array and clears what must start at zero; calls that overlap on the GPU
+ * (other streams or host threads) race on it and must not be issued. */
+B3T_API int b3t_scal_chains_noalloc(float *x, int64_t n, int32_t nblocks, int32_t nchain,
+                                    const float *factors, int64_t timeout_ns, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

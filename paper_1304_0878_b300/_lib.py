@@ -67,6 +67,7 @@ _SIGS = {
     "b3t_cholesky_mx_submit": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                               ctypes.POINTER(_vp), _i32, _i32, _i32, _i32]),
     "b3t_tiles_unregister": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), _i32]),
+    "b3t_scal_chains_noalloc": (ctypes.c_int, [_vp, _i64, _i32, _i32, _vp, _i64, _vp]),
 }
 
 
@@ -253,3 +254,4 @@ def pack_i32(x):
 
 ENOENT, EINVAL, EEXIST, EBUSY = -errno.ENOENT, -errno.EINVAL, -errno.EEXIST, -errno.EBUSY
 ENODEV, ETIMEDOUT, EDOM, EIO = -errno.ENODEV, -errno.ETIMEDOUT, -errno.EDOM, -errno.EIO
+E2BIG, ERANGE = -errno.E2BIG, -errno.ERANGE

@@ -12,7 +12,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libb3t.so")
 
-SOURCES = ["executor.cu", "runtime.cpp"]
+SOURCES = ["executor.cu", "runtime.cpp", "noalloc.cu"]
 HEADERS = ["b3t_internal.h", "tiles_fp64.cuh", "mx.cuh"]
 
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
