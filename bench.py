@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--no-secondary", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--no-mixed", action="store_true")
+    p.add_argument("--nrhs", type=int, default=16)
     return p.parse_args()
 
 
@@ -293,9 +295,12 @@ def run_ours(args):
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "ms_per_step": mse}
         del hA, hL
 
+    nctas = ctx.last_launch()["nctas"]
     secondary = {}
     if not args.no_secondary:
         secondary = run_secondary(ctx, dev, stream)
+    if not args.no_mixed:
+        secondary["time_to_solution"] = run_time_to_solution(ctx, A0, t, g, N, b, dev, stream, args)
 
     cpu = None
     if rank == 0 and args.cpu_seconds > 0:
@@ -320,7 +325,8 @@ def run_ours(args):
                    "N": N, "tile": b, "tasks": len_tasks(T), "seed": 3, "shift": 0.1,
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "l2": "inputs (%.2f GB of tiles) larger than L2" % (A0.numel() * 8 / 1e9),
-                   "input_reset": "A tiles restored by a device copy inside each step"},
+                   "input_reset": "A tiles restored by a device copy inside each step",
+                   "persistent_ctas": nctas},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
                      "note": "FP64 DFMA pipe: 148 SMs x 4 flop/clk x 2032 MHz; achieved = "
@@ -335,6 +341,89 @@ def run_ours(args):
     print(json.dumps(line))
 
 
+def rhs_parts(N, b, nrhs, seed, dev):
+    """N(0,1) right-hand sides as T parts of b x nrhs (column-major)."""
+    import torch
+    import synth
+    B = synth.rhs(N, nrhs, seed=seed)
+    T = N // b
+    return torch.from_numpy(np.ascontiguousarray(B.reshape(T, b, nrhs).transpose(0, 2, 1))).to(dev)
+
+
+def run_time_to_solution(ctx, A0, t, g64, N, b, dev, stream, args):
+    """Config 4: 16 right-hand sides to backward error <= 1e-12.
+    FP64: FP64 factorisation (graph g64 on tiles t) + one FP64 solve step.
+    Mixed: binary32 working tiles, bf16 / E4M3 tensor-core updates, FP64
+    POTRF / TRSM, then iterative refinement (binary32 correction solves,
+    FP64 residual) until eta <= 1e-12.  Times are device-event wall times of
+    the whole solution, inputs resident."""
+    import torch
+    import paper_1304_0878_b300 as b3t
+    from paper_1304_0878_b300 import tiles as dt
+    T = N // b
+    nrhs = args.nrhs
+    Bd = rhs_parts(N, b, nrhs, 4, dev)
+    R = torch.zeros(b3t.ir_work_elems(T, b, nrhs), dtype=torch.float64, device=dev)
+    eta = torch.zeros(nrhs + 1, dtype=torch.float64, device=dev)
+    flops = cholesky_flops(N)
+    out = {"workload": "N=%d tile %d, %d right-hand sides N(0,1) seed 4, target eta <= 1e-12" % (N, b, nrhs)}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+    def solve(Lp, X, flags, max_iter):
+        return ctx.ir_solve(A0.data_ptr(), Lp, Bd.data_ptr(), X.data_ptr(), R.data_ptr(), eta.data_ptr(),
+                            T, b, nrhs, flags, 1e-12, max_iter)
+
+    # FP64 reference path
+    X64 = torch.zeros_like(Bd)
+    res = []
+    for rep in range(2):
+        t.copy_(A0)
+        ev[0].record(stream)
+        ctx.graph_replay(g64)
+        ctx.task_wait()
+        ev[1].record(stream)
+        rc, its, e = solve(dt.tile_ptrs(t), X64, 0, 1)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        res.append((ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), rc, its, e[nrhs]))
+    f_ms, s_ms, rc, its, e64 = res[-1]
+    out["fp64"] = {"ms": f_ms + s_ms, "factor_ms": f_ms, "solve_ms": s_ms, "eta": e64, "rc": rc,
+                   "effective_TFLOPs": flops / ((f_ms + s_ms) / 1e3) / 1e12}
+    # mixed precision + refinement
+    W = torch.empty(A0.shape, dtype=torch.float32, device=dev)
+    Lm = torch.zeros_like(A0)
+    for fmt, name in ((b3t.FMT_BF16, "bf16"), (b3t.FMT_E4M3, "e4m3")):
+        Q = dt.q_tiles(T, b, fmt, dev)
+        wp, lp, qp = dt.tile_ptrs(W), dt.tile_ptrs(Lm), dt.tile_ptrs(Q)
+        ctx.graph_capture_begin()
+        ctx.cholesky_mx_submit(wp, lp, qp, T, b, fmt)
+        gm = ctx.graph_capture_end()
+        Xm = torch.zeros_like(Bd)
+        res = []
+        for rep in range(3):
+            ev[0].record(stream)
+            W.copy_(A0)
+            ctx.graph_replay(gm)
+            ctx.task_wait()
+            ev[1].record(stream)
+            rc, its, e = solve(lp, Xm, b3t.VEC_F32, 30)
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            res.append((ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), rc, its, e[nrhs]))
+        f_ms, s_ms, rc, its, em = res[-1]
+        diff = float((Xm - X64).abs().max() / X64.abs().max())
+        out[name] = {"ms": f_ms + s_ms, "factor_ms": f_ms, "refine_ms": s_ms, "iterations": its, "eta": em,
+                     "converged": rc == 0, "max_rel_diff_vs_fp64_solution": diff,
+                     "effective_TFLOPs": flops / ((f_ms + s_ms) / 1e3) / 1e12,
+                     "speedup_vs_fp64": (out["fp64"]["ms"]) / (f_ms + s_ms)}
+        ctx.graph_destroy(gm)
+        ctx.tiles_unregister(qp, T)
+        del Q
+    ctx.tiles_unregister(dt.tile_ptrs(W), T)
+    ctx.tiles_unregister(dt.tile_ptrs(Lm), T)
+    return out
+
+
 def run_secondary(ctx, dev, stream):
     """Vector chains (config 2), tasks/s on empty-bodied DAGs, small Cholesky."""
     import torch
@@ -342,30 +431,34 @@ def run_secondary(ctx, dev, stream):
     import paper_1304_0878_b300 as b3t
     from paper_1304_0878_b300 import tiles as dt
     out = {}
-    # vector-scaling chains: n = 2^28 f32, 256 blocks x 8 tasks
+    # vector-scaling chains: n = 2^28 f32, 256 blocks x 8 tasks, under both
+    # ready-queue orders (upward rank = breadth first here; depth = each
+    # chain's next task first, its block still in L2)
     nb, nk, n = 256, 8, 1 << 20
     x = torch.from_numpy(synth.vector_f32(nb * n, seed=1)).to(dev)
     f = synth.chain_factors(nb, nk, seed=2)
-    hs = [ctx.data_register(x[i * n:(i + 1) * n].data_ptr(), n, 4) for i in range(nb)]
-    cl = ctx.task_decl("scale_vector", b3t.SCAL_F32, [b3t.RW], 4)
-    ctx.graph_capture_begin()
-    for k in range(nk):
-        for i in range(nb):
-            ctx.task_submit(cl, [hs[i]], b3t.pack_f32(float(f[i, k])))
-    g = ctx.graph_capture_end()
-    ts = []
-    for r in range(8):
-        ctx.graph_replay(g)
-        ctx.task_wait()
-        if r >= 3:
-            ts.append(ctx.last_launch()["kernel_ns"] / 1e9)
     tbytes = 8.0 * nb * nk * n
-    out["vector_chains"] = {"workload": "n=2^28 f32, 256 blocks x 8 chained RW tasks (2048 tasks)",
-                            "ms": 1e3 * float(np.median(ts)), "task_level_GBps": tbytes / float(np.median(ts)) / 1e9,
-                            "task_bytes": tbytes}
-    ctx.graph_destroy(g)
-    for h in hs:
-        ctx.data_unregister(h)
+    for name, pol in (("vector_chains", b3t.PRIO_UPWARD), ("vector_chains_depth_first", b3t.PRIO_DEPTH)):
+        c2 = b3t.Context(stream=stream.cuda_stream, timeout_ns=60_000_000_000, prio_policy=pol)
+        hs = [c2.data_register(x[i * n:(i + 1) * n].data_ptr(), n, 4) for i in range(nb)]
+        cl = c2.task_decl("scale_vector", b3t.SCAL_F32, [b3t.RW], 4)
+        c2.graph_capture_begin()
+        for k in range(nk):
+            for i in range(nb):
+                c2.task_submit(cl, [hs[i]], b3t.pack_f32(float(f[i, k])))
+        g = c2.graph_capture_end()
+        ts = []
+        for r in range(8):
+            c2.graph_replay(g)
+            c2.task_wait()
+            if r >= 3:
+                ts.append(c2.last_launch()["kernel_ns"] / 1e9)
+        med = float(np.median(ts))
+        out[name] = {"workload": "n=2^28 f32, 256 blocks x 8 chained RW tasks (2048 tasks)",
+                     "ms": 1e3 * med, "task_level_GBps": tbytes / med / 1e9, "task_bytes": tbytes,
+                     "hbm_frac_of_measured": tbytes / med / 1e9 / 6451.5}
+        c2.graph_destroy(g)
+        c2.close()
     del x
     # scheduler throughput: 1000 chains x 100 empty tasks
     y = torch.zeros(1000 * 64, device=dev)

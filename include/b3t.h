@@ -105,8 +105,39 @@ enum b3t_kind {
     B3T_TRSM_MX = 7,
     B3T_SYRK_MX = 8,
     B3T_GEMM_MX = 9,
-    B3T_QUANT = 10
+    B3T_QUANT = 10,
+    B3T_TRSV_L = 11,
+    B3T_GEMV_L = 12,
+    B3T_TRSV_LT = 13,
+    B3T_GEMV_LT = 14,
+    B3T_AXPY = 15,
+    B3T_RESID = 16,
+    B3T_NRM = 17
 };
+
+/* Vector kinds (solves and refinement).  A block vector with nrhs <= 32
+ * right-hand sides is split into T parts of b rows; part k holds Y_k(r, j) at
+ * j*b + r.  Scalars: struct b3t_vec_args below (20 bytes).
+ *  B3T_TRSV_L   L_kk (R, f64 tile), Y_k (RW)          Y_k <- L_kk^{-1} Y_k
+ *  B3T_GEMV_L   L_ik (R), Y_k (R), Y_i (RW)           Y_i <- Y_i - L_ik Y_k
+ *  B3T_TRSV_LT  L_kk (R), Y_k (RW)                    Y_k <- L_kk^{-T} Y_k
+ *  B3T_GEMV_LT  L_ki (R), Y_k (R), Y_i (RW)           Y_i <- Y_i - L_ki^T Y_k
+ *               (flags bit 0: compute in binary32, store FP64)
+ *  B3T_AXPY     X_i (RW), D_i (R)                     X_i <- X_i + D_i
+ *               (flags bit 1: X_i <- D_i)
+ *  B3T_RESID    A (R, all T(T+1)/2 packed f64 tiles as one buffer), X (R,
+ *               T parts), B (R, T parts), R_i (W, b3t_ir_work_elems / T
+ *               elements): R_i <- B_i - (A X)_i in FP64 with A symmetric and
+ *               only its lower tiles stored; after the b*nrhs values, R_i
+ *               holds per 32-row item max|r_j|, max|x_j| and the largest
+ *               row sum of |A| (flags bit 1: X taken as 0, R_i <- B_i)
+ *  B3T_NRM      R (R, all parts), B (R), eta (W, nrhs + 1 f64):
+ *               eta_j = max|r_j| / (||A||_inf max|x_j| + max|b_j|),
+ *               eta[nrhs] = max_j eta_j (normwise backward error) */
+typedef struct b3t_vec_args {
+    int32_t nrhs, flags, i, T, b;
+} b3t_vec_args;
+enum { B3T_VEC_F32 = 1, B3T_VEC_ASSIGN = 2 };
 
 /* Low-precision formats of the Q tiles. */
 enum b3t_fmt { B3T_FMT_BF16 = 0, B3T_FMT_E4M3 = 1 };
@@ -129,8 +160,15 @@ typedef struct b3t_config {
                                submission and DAG inspection work, flush /
                                wait / replay return -ENODEV (for tools and
                                CPU-only tests of the dependency logic) */
-    int32_t reserved[2];
+    int32_t prio_policy;    /* ready-queue order: B3T_PRIO_UPWARD (0, default):
+                               longest remaining path first (upward rank,
+                               Section 5.3); B3T_PRIO_DEPTH (1): deepest task
+                               first, so a successor runs right after its
+                               predecessor while the data is in L2 */
+    int32_t reserved[1];
 } b3t_config;
+
+enum { B3T_PRIO_UPWARD = 0, B3T_PRIO_DEPTH = 1 };
 
 /* Create a context bound to the current CUDA device and to `cuda_stream`
  * (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream; NULL = the
@@ -272,6 +310,32 @@ B3T_API int b3t_cholesky_submit(b3t_ctx *ctx, double *const *tiles, int32_t T, i
 B3T_API int b3t_cholesky_mx_submit(b3t_ctx *ctx, float *const *W, double *const *L,
                                    void *const *Q, int32_t T, int32_t b, int32_t fmt,
                                    int32_t col0);
+
+/* Solves with a tiled Cholesky factor: Y <- (L L^T)^{-1} Y, submitted as
+ * TRSV_L / GEMV_L tasks (forward, k ascending) then TRSV_LT / GEMV_LT tasks
+ * (backward, k descending).  L: T(T+1)/2 f64 tile pointers (packed order;
+ * only lower triangles read).  Y: device f64 block vector of T parts,
+ * part_stride elements apart (>= b*nrhs); registered and partitioned here if
+ * it is not already.  flags: B3T_VEC_F32 for binary32 arithmetic. */
+B3T_API int b3t_chol_solve_submit(b3t_ctx *ctx, double *const *L, double *Y, int32_t T, int32_t b,
+                                  int32_t nrhs, int64_t part_stride, int32_t flags);
+
+/* Elements (f64) of the residual work area b3t_ir_solve needs. */
+B3T_API size_t b3t_ir_work_elems(int32_t T, int32_t b, int32_t nrhs);
+
+/* Iterative refinement, each step a task graph run by the executor:
+ *   x_0 = 0, r_0 = b;  repeat  d = (L L^T)^{-1} r (solve tasks),
+ *   x += d (AXPY), r = b - A x in FP64 (RESID), eta (NRM)
+ * until eta <= tol (returns 0), max_iter steps (-ERANGE) or no progress
+ * (eta above 0.9 x its previous value: -ERANGE).  A_packed: the original
+ * matrix as T(T+1)/2 contiguous packed lower f64 tiles; L: factor tile
+ * pointers (any precision history, FP64 storage); B, X: T parts of b*nrhs
+ * f64; R: b3t_ir_work_elems f64; eta: nrhs + 1 f64 (device).  flags:
+ * B3T_VEC_F32 for binary32 correction solves.  iters and eta_out (nrhs + 1
+ * host doubles) report the result.  Blocks until done. */
+B3T_API int b3t_ir_solve(b3t_ctx *ctx, const double *A_packed, double *const *L, const double *B,
+                         double *X, double *R, double *eta, int32_t T, int32_t b, int32_t nrhs,
+                         int32_t flags, double tol, int32_t max_iter, int32_t *iters, double *eta_out);
 
 /* Wait, then unregister the T(T+1)/2 tiles given (any registered set). */
 B3T_API int b3t_tiles_unregister(b3t_ctx *ctx, void *const *tiles, int32_t T);

@@ -20,6 +20,9 @@ R, W, RW = 1, 2, 3
 NOOP, SCAL_F32, POTRF, TRSM, SYRK, GEMM = 0, 1, 2, 3, 4, 5
 POTRF_MX, TRSM_MX, SYRK_MX, GEMM_MX, QUANT = 6, 7, 8, 9, 10
 FMT_BF16, FMT_E4M3 = 0, 1
+PRIO_UPWARD, PRIO_DEPTH = 0, 1
+TRSV_L, GEMV_L, TRSV_LT, GEMV_LT, AXPY, RESID, NRM = 11, 12, 13, 14, 15, 16, 17
+VEC_F32, VEC_ASSIGN = 1, 2
 
 
 class B3TError(RuntimeError):
@@ -31,7 +34,8 @@ class B3TError(RuntimeError):
 class Config(ctypes.Structure):
     _fields_ = [("timeout_ns", ctypes.c_int64), ("ctas_per_sm", ctypes.c_int32),
                 ("prio_levels", ctypes.c_int32), ("debug_checks", ctypes.c_int32),
-                ("host_only", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("host_only", ctypes.c_int32), ("prio_policy", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 _lib = None
@@ -68,6 +72,10 @@ _SIGS = {
                                               ctypes.POINTER(_vp), _i32, _i32, _i32, _i32]),
     "b3t_tiles_unregister": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), _i32]),
     "b3t_scal_chains_noalloc": (ctypes.c_int, [_vp, _i64, _i32, _i32, _vp, _i64, _vp]),
+    "b3t_chol_solve_submit": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), _vp, _i32, _i32, _i32, _i64, _i32]),
+    "b3t_ir_work_elems": (_sz, [_i32, _i32, _i32]),
+    "b3t_ir_solve": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_vp), _vp, _vp, _vp, _vp, _i32, _i32, _i32,
+                                    _i32, ctypes.c_double, _i32, _pi32, ctypes.POINTER(ctypes.c_double)]),
 }
 
 
@@ -114,13 +122,22 @@ def q_bytes(b, fmt):
     return int(lib().b3t_q_bytes(b, fmt))
 
 
+def ir_work_elems(T, b, nrhs):
+    return int(lib().b3t_ir_work_elems(T, b, nrhs))
+
+
+def vec_args(nrhs, flags=0, i=0, T=1, b=64):
+    return struct.pack("<5i", nrhs, flags, i, T, b)
+
+
 class Context:
     """One b3t context bound to a CUDA stream (a raw cudaStream_t value such
     as ``torch.cuda.current_stream().cuda_stream``)."""
 
     def __init__(self, stream=0, timeout_ns=0, ctas_per_sm=0, prio_levels=0, debug=False,
-                 host_only=False):
-        cfg = Config(timeout_ns, ctas_per_sm, prio_levels, 1 if debug else 0, 1 if host_only else 0)
+                 host_only=False, prio_policy=0):
+        cfg = Config(timeout_ns, ctas_per_sm, prio_levels, 1 if debug else 0, 1 if host_only else 0,
+                     prio_policy)
         h = _vp()
         _check(lib().b3t_init(ctypes.byref(h), ctypes.byref(cfg), _vp(stream or 0)), "b3t_init")
         self._h = h
@@ -239,6 +256,23 @@ class Context:
     def cholesky_mx_submit(self, W_ptrs, L_ptrs, Q_ptrs, T, b, fmt, col0=0):
         _check(lib().b3t_cholesky_mx_submit(self._h, _ptrs(W_ptrs), _ptrs(L_ptrs), _ptrs(Q_ptrs),
                                             T, b, fmt, col0), "b3t_cholesky_mx_submit")
+
+    def chol_solve_submit(self, L_ptrs, Y_ptr, T, b, nrhs, part_stride, flags=0):
+        _check(lib().b3t_chol_solve_submit(self._h, _ptrs(L_ptrs), _vp(int(Y_ptr)), T, b, nrhs,
+                                           part_stride, flags), "b3t_chol_solve_submit")
+
+    def ir_solve(self, A_ptr, L_ptrs, B_ptr, X_ptr, R_ptr, eta_ptr, T, b, nrhs, flags=0, tol=1e-12,
+                 max_iter=30):
+        """Returns (return code, iterations, eta list); -ERANGE is returned,
+        not raised, so that a non-converged refinement can be reported."""
+        it = _i32(0)
+        eta = (ctypes.c_double * (nrhs + 1))()
+        rc = lib().b3t_ir_solve(self._h, _vp(int(A_ptr)), _ptrs(L_ptrs), _vp(int(B_ptr)), _vp(int(X_ptr)),
+                                _vp(int(R_ptr)), _vp(int(eta_ptr)), T, b, nrhs, flags, tol, max_iter,
+                                ctypes.byref(it), eta)
+        if rc < 0 and rc != ERANGE:
+            raise B3TError(rc, "b3t_ir_solve")
+        return rc, it.value, list(eta)
 
     def tiles_unregister(self, tile_ptrs, T):
         _check(lib().b3t_tiles_unregister(self._h, _ptrs(tile_ptrs), T), "b3t_tiles_unregister")

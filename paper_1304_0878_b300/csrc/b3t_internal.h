@@ -22,11 +22,31 @@ constexpr int64_t kScalChunk = 1 << 16;  // f32 elements per SCAL item
 constexpr int kGemmBlk = 64;             // f64 GEMM / SYRK item: 64 x 64 of C
 constexpr int kTrsmRows = 32;            // f64 TRSM item: 32 rows of A_ik
 constexpr int kMxBlk = 128;              // MX GEMM / SYRK item: 128 x 128 of C
+constexpr int kGemvRows = 64;            // GEMV item: 64 rows of the updated part
+constexpr int kResidRows = 32;           // RESID item: 32 rows of the residual part
+constexpr int kMaxRhs = 32;
+
+// Scalar blob of the vector kinds (TRSV / GEMV / AXPY / RESID / NRM).
+struct VecArgs {
+    int32_t nrhs;
+    int32_t flags;    // bit 0: binary32 arithmetic (solves); bit 1: AXPY assigns / RESID with x = 0
+    int32_t i;        // row block (RESID)
+    int32_t T;        // number of row blocks
+    int32_t b;        // rows per block (tile size)
+};
+constexpr int32_t kVecF32 = 1, kVecAssign = 2;
+
+// Elements of one part of the residual work area: b*nrhs values, then per
+// RESID item the maxima |r_j| and |x_j| and the largest row sum of |A|.
+B3T_HD constexpr int64_t resid_part_elems(int b, int nrhs) {
+    return (int64_t)b * nrhs + (int64_t)(b / kResidRows) * (2 * nrhs + 1);
+}
 
 enum : int32_t {
     kNoop = 0, kScalF32 = 1, kPotrf = 2, kTrsm = 3, kSyrk = 4, kGemm = 5,
     kPotrfMx = 6, kTrsmMx = 7, kSyrkMx = 8, kGemmMx = 9, kQuant = 10,
-    kNumKinds = 11
+    kTrsvL = 11, kGemvL = 12, kTrsvLT = 13, kGemvLT = 14, kAxpy = 15, kResid = 16, kNrm = 17,
+    kNumKinds = 18
 };
 
 // One task as the device sees it: 64 bytes.
@@ -64,7 +84,8 @@ struct LaunchParams {
     const int32_t *level;        // ready-queue level of each task
     int32_t *counters;           // remaining predecessors per task
     int32_t *done_items;         // finished items per task
-    unsigned long long *slots;   // ready rings, all levels back to back
+    int32_t *next_item;          // next item to hand out, per task
+    unsigned long long *slots;   // ready rings (one slot per task), levels back to back
     Ctl *ctl;
     unsigned long long ring_off[kMaxLevels];   // first slot of each level
     unsigned long long ring_cap[kMaxLevels];
@@ -81,9 +102,10 @@ struct InitParams {
     const int32_t *indeg;        // initial counters
     int32_t *counters;
     int32_t *done_items;
+    int32_t *next_item;
     unsigned long long *slots;
     unsigned long long nslots;
-    const unsigned long long *roots;      // root items, per level back to back
+    const unsigned long long *roots;      // root task slots, per level back to back
     unsigned long long root_off[kMaxLevels];
     unsigned long long root_cnt[kMaxLevels];
     Ctl *ctl;
@@ -93,8 +115,9 @@ struct InitParams {
 
 constexpr unsigned long long kEmpty = ~0ull;
 
-B3T_HD inline unsigned long long pack_item(int64_t task, int32_t item) {
-    return ((unsigned long long)task << 32) | (uint32_t)item;
+// A ready-ring slot names a task and carries its item count.
+B3T_HD inline unsigned long long pack_slot(int64_t task, int32_t nitems) {
+    return ((unsigned long long)task << 32) | (uint32_t)nitems;
 }
 
 }  // namespace b3t

@@ -9,10 +9,11 @@
 //   * the CTA that finishes the last item of a task retires it: one warp
 //     decrements the dependency counters of its successors (one lane per
 //     successor, atomics issued by the whole warp) and pushes every successor
-//     whose counter reached zero, all of its work items at once;
+//     whose counter reached zero into the ready queue (one slot per task);
 //   * the ready queue has up to kMaxLevels levels (upward-rank buckets, the
-//     scheduling hint of Section 5.3); a claim takes the oldest item of the
-//     highest non-empty level, found with one warp-wide scan;
+//     scheduling hint of Section 5.3, or depth from the sources); a claim
+//     takes the next item of the oldest task of the highest non-empty level,
+//     found with one warp-wide scan;
 //   * every wait is bounded by %globaltimer: an idle CTA that sees no work for
 //     longer than the launch's timeout sets ETIMEDOUT in the status word and
 //     the whole grid exits; nothing spins forever.
@@ -21,6 +22,7 @@
 
 #include "b3t_internal.h"
 #include "mx.cuh"
+#include "solve.cuh"
 #include "tiles_fp64.cuh"
 
 namespace b3t {
@@ -64,7 +66,7 @@ __device__ __forceinline__ void scal_item(const TaskRec &t, int item) {
     const int64_t end = min(t.n, start + kScalChunk);
     const int64_t nv = (end - start) >> 2;
     float4 *v = reinterpret_cast<float4 *>(x + start);
-    constexpr int U = 8;
+    constexpr int U = 16;
     const int tid = threadIdx.x;
     for (int64_t i0 = tid; i0 < nv; i0 += (int64_t)kThreads * U) {
         float4 r[U];
@@ -105,9 +107,14 @@ __device__ __forceinline__ int potrf_mx_item(const TaskRec &t, double *smem, int
 }
 
 // ------------------------------------------------------------- queue
-// Warp 0 claims one work item.  Returns the packed item, or kEmpty when the
-// launch is over (all tasks retired, an error was raised, or the wait timed
-// out: the last two leave the reason in ctl).
+// Each ready-ring slot names one task and its item count.  Warp 0 claims a
+// work item: one warp-wide scan finds the highest non-empty level; the task
+// at that level's head hands out its items through an atomicAdd on its
+// next_item counter, and whoever takes (or overshoots) the last item
+// advances the head with a CAS, so the head moves once per task, not once per
+// item.  Returns the packed (task, item), or kEmpty when the launch is over
+// (all tasks retired, an error was raised, or the wait timed out: the last
+// two leave the reason in ctl).
 __device__ __forceinline__ unsigned long long claim(const LaunchParams &p) {
     const int lane = threadIdx.x & 31;
     Ctl *ctl = p.ctl;
@@ -130,23 +137,32 @@ __device__ __forceinline__ unsigned long long claim(const LaunchParams &p) {
             const unsigned long long hv = __shfl_sync(0xffffffffu, h, lv);
             unsigned long long item = kEmpty;
             int got = 0;
-            if (lane == 0 && atomicCAS(&ctl->lvl[lv].head, hv, hv + 1) == hv) {
-                got = 1;
+            if (lane == 0) {
                 if (p.debug && hv >= p.ring_cap[lv]) {
                     set_error(ctl, EPROTO, -1, -1, 3);
                     got = 2;
                 } else {
                     unsigned long long *slot = p.slots + p.ring_off[lv] + hv;
-                    // the producer reserves a slot before it fills it
-                    item = ld_acq(slot);
+                    // a producer reserves the slot (tail) before it fills it
+                    unsigned long long v = ld_acq(slot);
                     const uint64_t ts = gtimer();
-                    for (uint32_t n = 0; item == kEmpty; ++n) {
+                    for (uint32_t n = 0; v == kEmpty; ++n) {
                         __nanosleep(32);
-                        item = ld_acq(slot);
+                        v = ld_acq(slot);
                         if ((n & 63) == 63 && (int64_t)(gtimer() - ts) > p.timeout_ns) {
                             set_error(ctl, ETIMEDOUT, -1, -1, 2);
                             got = 2;
                             break;
+                        }
+                    }
+                    if (!got) {
+                        const int64_t t = (int64_t)(v >> 32);
+                        const int n = (int)(v & 0xffffffffu);
+                        const int i = atomicAdd(&p.next_item[t], 1);
+                        if (i >= n - 1) atomicCAS(&ctl->lvl[lv].head, hv, hv + 1);
+                        if (i < n) {
+                            item = ((unsigned long long)t << 32) | (uint32_t)i;
+                            got = 1;
                         }
                     }
                 }
@@ -169,7 +185,8 @@ __device__ __forceinline__ unsigned long long claim(const LaunchParams &p) {
     }
 }
 
-// Warp 0 retires task t: successors' counters, pushes, retired count.
+// Warp 0 retires task t: successors' counters (one lane per successor),
+// one ready-ring slot per successor that became ready, retired count.
 __device__ __forceinline__ void retire(const LaunchParams &p, int64_t t, const TaskRec &rec) {
     const int lane = threadIdx.x & 31;
     __threadfence();
@@ -180,14 +197,9 @@ __device__ __forceinline__ void retire(const LaunchParams &p, int64_t t, const T
             const int prev = atomicSub(&p.counters[s], 1);
             if (prev == 1) {
                 const int lv = p.level[s];
-                const int n = p.tasks[s].nitems;
-                const unsigned long long pos = atomicAdd(&p.ctl->lvl[lv].tail, (unsigned long long)n);
-                if (p.debug && pos + n > p.ring_cap[lv]) {
-                    set_error(p.ctl, EPROTO, s, -1, 4);
-                } else {
-                    unsigned long long *slot = p.slots + p.ring_off[lv] + pos;
-                    for (int i = 0; i < n; ++i) st_rel(slot + i, pack_item(s, i));
-                }
+                const unsigned long long pos = atomicAdd(&p.ctl->lvl[lv].tail, 1ull);
+                if (p.debug && pos >= p.ring_cap[lv]) set_error(p.ctl, EPROTO, s, -1, 4);
+                else st_rel(p.slots + p.ring_off[lv] + pos, pack_slot(s, p.tasks[s].nitems));
             }
         }
     }
@@ -269,6 +281,25 @@ __global__ void __launch_bounds__(kThreads, 2) exec_kernel(const LaunchParams p)
             if (!p.has_mx) { st = -EPROTO; break; }
             if (mx_update_item(rec, it, rec.kind == kSyrkMx, mx, p.timeout_ns, &s_fail)) st = -ETIMEDOUT;
             break;
+        case kTrsvL:
+            if (vk_flags(rec) & kVecF32) trsv_l_item<float>(rec, it, smem);
+            else trsv_l_item<double>(rec, it, smem);
+            break;
+        case kTrsvLT:
+            if (vk_flags(rec) & kVecF32) trsv_lt_item<float>(rec, it, smem);
+            else trsv_lt_item<double>(rec, it, smem);
+            break;
+        case kGemvL:
+            if (vk_flags(rec) & kVecF32) gemv_item<float, false>(rec, it, smem);
+            else gemv_item<double, false>(rec, it, smem);
+            break;
+        case kGemvLT:
+            if (vk_flags(rec) & kVecF32) gemv_item<float, true>(rec, it, smem);
+            else gemv_item<double, true>(rec, it, smem);
+            break;
+        case kAxpy: axpy_item(rec); break;
+        case kResid: resid_item(rec, it, smem); break;
+        case kNrm: nrm_item(rec, smem); break;
         default: break;   // NOOP
         }
         __syncthreads();
@@ -303,6 +334,7 @@ __global__ void init_kernel(const InitParams ip, const LaunchParams lp) {
     for (int64_t i = gid; i < ip.ntasks; i += stride) {
         ip.counters[i] = ip.indeg[i];
         ip.done_items[i] = 0;
+        ip.next_item[i] = 0;
     }
     for (int64_t i = gid; i < (int64_t)ip.nslots; i += stride) {
         int l = 0;
@@ -329,7 +361,8 @@ extern "C" size_t b3t_internal_smem_bytes(int has_mx) {
 }
 
 extern "C" int b3t_internal_occupancy(int *ctas_per_sm, size_t smem, int *num_sms) {
-    if (cudaFuncSetAttribute(exec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(exec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(exec_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
         return -EIO;
     int dev = 0;
     cudaGetDevice(&dev);

@@ -56,6 +56,7 @@ struct Arena {
     TaskRec *tasks = nullptr;  size_t cap_tasks = 0;
     int32_t *succ = nullptr;   size_t cap_succ = 0;
     int32_t *indeg = nullptr;  int32_t *counters = nullptr; int32_t *done = nullptr;
+    int32_t *next = nullptr;
     size_t cap_cnt = 0;
     unsigned long long *slots = nullptr; size_t cap_slots = 0;
     unsigned long long *roots = nullptr; size_t cap_roots = 0;
@@ -63,7 +64,7 @@ struct Arena {
 
     void release() {
         cudaFree(tasks); cudaFree(succ); cudaFree(indeg); cudaFree(counters);
-        cudaFree(done); cudaFree(slots); cudaFree(roots); cudaFree(ctl);
+        cudaFree(done); cudaFree(next); cudaFree(slots); cudaFree(roots); cudaFree(ctl);
         *this = Arena();
     }
 };
@@ -108,10 +109,19 @@ const KindSig kSigs[kNumKinds] = {
     /* SYRK_MX  */ {2, {B3T_R, B3T_RW}, {1, 4}, 4, true},
     /* GEMM_MX  */ {3, {B3T_R, B3T_R, B3T_RW}, {1, 1, 4}, 4, true},
     /* QUANT    */ {2, {B3T_R, B3T_W}, {8, 1}, 4, true},
+    /* TRSV_L   */ {2, {B3T_R, B3T_RW}, {8, 8}, sizeof(VecArgs), false},
+    /* GEMV_L   */ {3, {B3T_R, B3T_R, B3T_RW}, {8, 8, 8}, sizeof(VecArgs), false},
+    /* TRSV_LT  */ {2, {B3T_R, B3T_RW}, {8, 8}, sizeof(VecArgs), false},
+    /* GEMV_LT  */ {3, {B3T_R, B3T_R, B3T_RW}, {8, 8, 8}, sizeof(VecArgs), false},
+    /* AXPY     */ {2, {B3T_RW, B3T_R}, {8, 8}, sizeof(VecArgs), false},
+    /* RESID    */ {4, {B3T_R, B3T_R, B3T_R, B3T_W}, {8, 8, 8, 8}, sizeof(VecArgs), false},
+    /* NRM      */ {3, {B3T_R, B3T_R, B3T_W}, {8, 8, 8}, sizeof(VecArgs), false},
 };
 
 const char *kKindNames[kNumKinds] = {"noop", "scal_f32", "potrf", "trsm", "syrk", "gemm",
-                                     "potrf_mx", "trsm_mx", "syrk_mx", "gemm_mx", "quant"};
+                                     "potrf_mx", "trsm_mx", "syrk_mx", "gemm_mx", "quant",
+                                     "trsv_l", "gemv_l", "trsv_lt", "gemv_lt", "axpy", "resid", "nrm"};
+bool is_vec(int kind) { return kind >= kTrsvL && kind <= kNrm; }
 
 bool is_mx(int kind) { return kind == kSyrkMx || kind == kGemmMx; }
 bool has_fmt(int kind) { return kind == kSyrkMx || kind == kGemmMx || kind == kQuant; }
@@ -125,6 +135,9 @@ int64_t items_of(int kind, int64_t n) {
     case kGemm: { int64_t m = n / kGemmBlk; return m * m; }
     case kSyrkMx: { int64_t m = n / kMxBlk; return m * (m + 1) / 2; }
     case kGemmMx: { int64_t m = n / kMxBlk; return m * m; }
+    case kGemvL: case kGemvLT: return n / kGemvRows;
+    case kResid: return n / kResidRows;
+    case kAxpy: case kNrm: return 1;
     }
     return 1;
 }
@@ -132,8 +145,9 @@ int64_t items_of(int kind, int64_t n) {
 // Rough device time of a task in ns on one CTA, only used to rank tasks by
 // their distance to the end of the graph (upward rank, the scheduling hint
 // Section 5.3 of the paper proposes).
-float cost_of(int kind, int64_t n) {
+float cost_of(int kind, int64_t n, int nrhs = 1, int T = 1, bool f32 = false) {
     double b = (double)n;
+    const double vec = f32 ? 60.0 : 3.7;
     const double fp64 = 3.7;   // flop / ns per CTA (FP64 DFMA, 2 CTAs / SM)
     const double mx = 2000.0;  // flop / ns per CTA (tensor cores)
     switch (kind) {
@@ -145,6 +159,11 @@ float cost_of(int kind, int64_t n) {
     case kSyrkMx: return (float)(b * b * b / mx + 4.0 * b * b / 20.0);
     case kGemmMx: return (float)(2.0 * b * b * b / mx + 8.0 * b * b / 20.0);
     case kQuant: return (float)(10.0 * b * b / 20.0);
+    case kTrsvL: case kTrsvLT: return (float)(b * b / vec + 32.0 * b / 32.0 * 20.0);
+    case kGemvL: case kGemvLT: return (float)(2.0 * b * b * nrhs / vec + 8.0 * b * b / 20.0);
+    case kAxpy: return (float)(b * nrhs / 10.0 + 1000.0);
+    case kResid: return (float)(2.0 * b * b * T * nrhs / 3.7);
+    case kNrm: return 5000.0f;
     }
     return 1000.0f;
 }
@@ -245,14 +264,25 @@ int build_launch(b3t_ctx *c, Arena &a, InitParams &ip, LaunchParams &lp, int64_t
         for (auto &e : c->edges) succ_lv[pos[e.first]++] = e.second;
     }
     for (int64_t t = 0; t < nt && t < (int64_t)c->extra_deps.size(); ++t) indeg[t] += c->extra_deps[t];
-    // upward rank -> priority level (higher level = closer to the critical path)
+    // priority level of each task (higher level = claimed first):
+    //   upward rank: longest cost-weighted path to the end of the graph,
+    //   bucketed linearly (Section 5.3's scheduling hint);
+    //   depth: longest path from a source, in tasks (successor first).
     std::vector<float> rank(nt, 0.f);
     float maxr = 0.f;
-    for (int64_t t = nt - 1; t >= 0; --t) {
-        float m = 0.f;
-        for (int32_t k = off[t]; k < off[t + 1]; ++k) m = std::max(m, rank[succ_lv[k]]);
-        rank[t] = c->tasks[t].cost + m;
-        maxr = std::max(maxr, rank[t]);
+    if (c->cfg.prio_policy == B3T_PRIO_DEPTH) {
+        for (int64_t t = 0; t < nt; ++t) {
+            for (int32_t k = off[t]; k < off[t + 1]; ++k)
+                rank[succ_lv[k]] = std::max(rank[succ_lv[k]], rank[t] + 1.f);
+            maxr = std::max(maxr, rank[t]);
+        }
+    } else {
+        for (int64_t t = nt - 1; t >= 0; --t) {
+            float m = 0.f;
+            for (int32_t k = off[t]; k < off[t + 1]; ++k) m = std::max(m, rank[succ_lv[k]]);
+            rank[t] = c->tasks[t].cost + m;
+            maxr = std::max(maxr, rank[t]);
+        }
     }
     unsigned long long cap[kMaxLevels] = {0}, rootcnt[kMaxLevels] = {0};
     int64_t nitems = 0;
@@ -262,10 +292,14 @@ int build_launch(b3t_ctx *c, Arena &a, InitParams &ip, LaunchParams &lp, int64_t
         r.succ_off = off[t];
         r.nsucc = off[t + 1] - off[t];
         int lv = 0;
-        if (L > 1 && maxr > 0.f) lv = std::min(L - 1, (int)((double)L * rank[t] / (maxr * 1.000001)));
+        if (L > 1 && maxr > 0.f) {
+            lv = c->cfg.prio_policy == B3T_PRIO_DEPTH
+                     ? std::min(L - 1, (int)rank[t])
+                     : std::min(L - 1, (int)((double)L * rank[t] / (maxr * 1.000001)));
+        }
         succ_lv[ne_pad + t] = lv;
-        cap[lv] += r.nitems;
-        if (indeg[t] == 0) rootcnt[lv] += r.nitems;
+        cap[lv] += 1;
+        if (indeg[t] == 0) rootcnt[lv] += 1;
         nitems += r.nitems;
         if (is_mx(r.kind)) has_mx = true;
     }
@@ -280,20 +314,17 @@ int build_launch(b3t_ctx *c, Arena &a, InitParams &ip, LaunchParams &lp, int64_t
         unsigned long long fill[kMaxLevels];
         for (int l = 0; l < L; ++l) fill[l] = rootoff[l];
         for (int64_t t = 0; t < nt; ++t)
-            if (indeg[t] == 0) {
-                const int lv = succ_lv[ne_pad + t];
-                for (int32_t it = 0; it < c->tasks[t].rec.nitems; ++it) roots[fill[lv]++] = pack_item(t, it);
-            }
+            if (indeg[t] == 0) roots[fill[succ_lv[ne_pad + t]]++] = pack_slot(t, c->tasks[t].rec.nitems);
     }
     int rc;
     if ((rc = grow(a.tasks, a.cap_tasks, nt))) return rc;
     if ((rc = grow(a.succ, a.cap_succ, succ_lv.size()))) return rc;
     if ((size_t)nt > a.cap_cnt || !a.indeg) {
         size_t n = std::max<size_t>(nt, std::max<size_t>(a.cap_cnt * 2, 64));
-        cudaFree(a.indeg); cudaFree(a.counters); cudaFree(a.done);
-        a.indeg = a.counters = a.done = nullptr; a.cap_cnt = 0;
+        cudaFree(a.indeg); cudaFree(a.counters); cudaFree(a.done); cudaFree(a.next);
+        a.indeg = a.counters = a.done = a.next = nullptr; a.cap_cnt = 0;
         if (cudaMalloc(&a.indeg, n * 4) != cudaSuccess || cudaMalloc(&a.counters, n * 4) != cudaSuccess ||
-            cudaMalloc(&a.done, n * 4) != cudaSuccess)
+            cudaMalloc(&a.done, n * 4) != cudaSuccess || cudaMalloc(&a.next, n * 4) != cudaSuccess)
             return -ENOMEM;
         a.cap_cnt = n;
     }
@@ -326,12 +357,12 @@ int build_launch(b3t_ctx *c, Arena &a, InitParams &ip, LaunchParams &lp, int64_t
     if ((rc = cuda_err(cudaEventRecord(c->staging_done, c->stream)))) return rc;
 
     ip = InitParams{};
-    ip.indeg = a.indeg; ip.counters = a.counters; ip.done_items = a.done;
+    ip.indeg = a.indeg; ip.counters = a.counters; ip.done_items = a.done; ip.next_item = a.next;
     ip.slots = a.slots; ip.nslots = nslots; ip.roots = a.roots; ip.ctl = a.ctl;
     ip.ntasks = nt; ip.nlevels = L;
     lp = LaunchParams{};
     lp.tasks = a.tasks; lp.succ = a.succ; lp.level = a.succ + ne_pad;
-    lp.counters = a.counters; lp.done_items = a.done;
+    lp.counters = a.counters; lp.done_items = a.done; lp.next_item = a.next;
     lp.slots = a.slots; lp.ctl = a.ctl; lp.ntasks = nt; lp.nlevels = L;
     lp.has_mx = has_mx ? 1 : 0;
     lp.timeout_ns = c->cfg.timeout_ns;
@@ -482,7 +513,44 @@ int submit_impl(b3t_ctx *c, b3t_codelet cl, const b3t_handle *handles, const uin
         }
         r.n = b;
     }
-    r.nitems = (int32_t)items_of(C.kind, r.n);
+    int vnrhs = 1, vT = 1;
+    bool vf32 = false;
+    if (is_vec(C.kind)) {
+        VecArgs v;
+        std::memcpy(&v, scalars, sizeof(v));
+        if (v.nrhs < 1 || v.nrhs > kMaxRhs || v.flags < 0 || v.flags > 3 || v.T < 1 || v.T > 65535 ||
+            v.i < 0 || v.i >= v.T || v.b < 64 || v.b > 4096 || v.b % 64)
+            return -EINVAL;
+        const size_t b = (size_t)v.b, blk = b * v.nrhs, T = (size_t)v.T;
+        auto need = [&](int i, size_t elems) {
+            const Handle &H = c->handles[handles[i]];
+            return H.elemsize == 8 && H.nelems >= elems && r.buf[i] % 8 == 0;
+        };
+        bool ok = true;
+        switch (C.kind) {
+        case kTrsvL: case kTrsvLT:
+            ok = c->handles[handles[0]].ld == (int64_t)b && need(0, b * b) && need(1, blk);
+            break;
+        case kGemvL: case kGemvLT:
+            ok = c->handles[handles[0]].ld == (int64_t)b && need(0, b * b) && need(1, blk) && need(2, blk);
+            break;
+        case kAxpy: ok = need(0, blk) && need(1, blk); break;
+        case kResid:
+            ok = need(0, T * (T + 1) / 2 * b * b) && need(1, T * blk) && need(2, T * blk) &&
+                 need(3, (size_t)resid_part_elems(v.b, v.nrhs));
+            break;
+        case kNrm:
+            ok = need(0, T * (size_t)resid_part_elems(v.b, v.nrhs)) && need(1, T * blk) &&
+                 need(2, (size_t)v.nrhs + 1);
+            break;
+        }
+        if (!ok) return -EINVAL;
+        r.n = v.b;
+        r.aux = v.i | (v.flags << 24);
+        r.scal = (uint32_t)v.T | ((uint32_t)v.nrhs << 16);
+        vnrhs = v.nrhs; vT = v.T; vf32 = v.flags & kVecF32;
+    }
+    r.nitems = (int32_t)(C.kind == kTrsvL || C.kind == kTrsvLT ? vnrhs : items_of(C.kind, r.n));
     const int32_t t = (int32_t)c->tasks.size();
     // expand partitioned parents to their parts; OR the modes of repeats
     std::vector<int32_t> leaves;
@@ -504,7 +572,7 @@ int submit_impl(b3t_ctx *c, b3t_codelet cl, const b3t_handle *handles, const uin
     for (int32_t p : preds) c->edges.emplace_back(p, t);
     Pending P;
     P.rec = r;
-    P.cost = cost_of(C.kind, r.n);
+    P.cost = cost_of(C.kind, r.n, vnrhs, vT, vf32);
     c->tasks.push_back(P);
     return 0;
 }
@@ -532,6 +600,7 @@ int b3t_init(b3t_ctx **out, const b3t_config *cfg, void *cuda_stream) {
     if (cfg) c->cfg = *cfg;
     if (c->cfg.timeout_ns <= 0) c->cfg.timeout_ns = 10'000'000'000LL;
     if (c->cfg.prio_levels <= 0) c->cfg.prio_levels = kMaxLevels;
+    if (c->cfg.prio_policy != B3T_PRIO_DEPTH) c->cfg.prio_policy = B3T_PRIO_UPWARD;
     c->cfg.prio_levels = std::min(c->cfg.prio_levels, kMaxLevels);
     for (int k = 0; k < kNumKinds; ++k) c->kind_cl[k] = -1;
     if (host_only) { *out = c; return 0; }
@@ -921,6 +990,138 @@ int b3t_cholesky_mx_submit(b3t_ctx *c, float *const *W, double *const *L, void *
         }
     }
     return 0;
+}
+
+// Register ptr as a vector of nparts parts of part_elems f64 (reusing an
+// existing registration of the same shape).
+static int reg_parted(b3t_ctx *c, void *ptr, int32_t nparts, size_t part_elems, b3t_handle *parent,
+                      std::vector<b3t_handle> &parts) {
+    int rc = b3t_data_lookup(c, ptr, parent);
+    if (rc == -ENOENT) rc = b3t_data_register(c, ptr, (size_t)nparts * part_elems, 8, 0, parent);
+    if (rc) return rc;
+    Handle &H = c->handles[*parent];
+    if (H.elemsize != 8) return -EINVAL;
+    if (H.parts.empty()) {
+        if (H.nelems < (size_t)nparts * part_elems) return -EINVAL;
+        parts.resize(nparts);
+        return b3t_data_partition(c, *parent, nparts, part_elems, parts.data());
+    }
+    if ((int32_t)H.parts.size() != nparts || c->handles[H.parts[0]].nelems != part_elems) return -EINVAL;
+    parts = H.parts;
+    return 0;
+}
+
+static int reg_vec(b3t_ctx *c, const void *ptr, size_t elems, b3t_handle *h) {
+    int rc = b3t_data_lookup(c, ptr, h);
+    if (rc == -ENOENT) rc = b3t_data_register(c, (void *)ptr, elems, 8, 0, h);
+    if (rc) return rc;
+    return c->handles[*h].nelems >= elems && c->handles[*h].elemsize == 8 ? 0 : -EINVAL;
+}
+
+static int submit_solve(b3t_ctx *c, const std::vector<b3t_handle> &hl, const std::vector<b3t_handle> &hy,
+                        int32_t T, int32_t b, int32_t nrhs, int32_t flags) {
+    b3t_codelet tl, gl, tlt, glt;
+    int rc;
+    if ((rc = kind_codelet(c, kTrsvL, &tl)) || (rc = kind_codelet(c, kGemvL, &gl)) ||
+        (rc = kind_codelet(c, kTrsvLT, &tlt)) || (rc = kind_codelet(c, kGemvLT, &glt)))
+        return rc;
+    VecArgs v{nrhs, flags & kVecF32, 0, T, b};
+    for (int32_t k = 0; k < T; ++k) {
+        const b3t_handle h2[2] = {hl[tidx(k, k, T)], hy[k]};
+        if ((rc = submit_impl(c, tl, h2, nullptr, 2, &v, sizeof(v)))) return rc;
+        for (int32_t i = k + 1; i < T; ++i) {
+            const b3t_handle h3[3] = {hl[tidx(i, k, T)], hy[k], hy[i]};
+            if ((rc = submit_impl(c, gl, h3, nullptr, 3, &v, sizeof(v)))) return rc;
+        }
+    }
+    for (int32_t k = T - 1; k >= 0; --k) {
+        const b3t_handle h2[2] = {hl[tidx(k, k, T)], hy[k]};
+        if ((rc = submit_impl(c, tlt, h2, nullptr, 2, &v, sizeof(v)))) return rc;
+        for (int32_t i = 0; i < k; ++i) {
+            const b3t_handle h3[3] = {hl[tidx(k, i, T)], hy[k], hy[i]};
+            if ((rc = submit_impl(c, glt, h3, nullptr, 3, &v, sizeof(v)))) return rc;
+        }
+    }
+    return 0;
+}
+
+int b3t_chol_solve_submit(b3t_ctx *c, double *const *L, double *Y, int32_t T, int32_t b, int32_t nrhs,
+                          int64_t part_stride, int32_t flags) {
+    if (!c || !L || !Y || T <= 0 || b <= 0 || b % 64 || nrhs < 1 || nrhs > kMaxRhs ||
+        part_stride < (int64_t)b * nrhs)
+        return -EINVAL;
+    std::vector<b3t_handle> hl, hy;
+    b3t_handle hp;
+    int rc = reg_tiles(c, (void *const *)L, (int64_t)T * (T + 1) / 2, (size_t)b * b, 8, b, hl);
+    if (!rc) rc = reg_parted(c, Y, T, (size_t)part_stride, &hp, hy);
+    if (!rc) rc = submit_solve(c, hl, hy, T, b, nrhs, flags);
+    return rc;
+}
+
+size_t b3t_ir_work_elems(int32_t T, int32_t b, int32_t nrhs) {
+    if (T <= 0 || b <= 0 || b % 64 || nrhs < 1 || nrhs > kMaxRhs) return 0;
+    return (size_t)T * (size_t)resid_part_elems(b, nrhs);
+}
+
+int b3t_ir_solve(b3t_ctx *c, const double *A, double *const *L, const double *B, double *X, double *R,
+                 double *eta, int32_t T, int32_t b, int32_t nrhs, int32_t flags, double tol, int32_t max_iter,
+                 int32_t *iters, double *eta_out) {
+    if (!c || !A || !L || !B || !X || !R || !eta || T <= 0 || b <= 0 || b % 64 || nrhs < 1 ||
+        nrhs > kMaxRhs || max_iter < 1 || c->capturing)
+        return -EINVAL;
+    if (c->cfg.host_only) return -ENODEV;
+    const int64_t nt = (int64_t)T * (T + 1) / 2;
+    const size_t blk = (size_t)b * nrhs, PR = (size_t)resid_part_elems(b, nrhs);
+    std::vector<b3t_handle> hl, hx, hr, hb;
+    b3t_handle ha, hxp, hrp, hbp, he;
+    int rc = reg_tiles(c, (void *const *)L, nt, (size_t)b * b, 8, b, hl);
+    if (!rc) rc = reg_vec(c, A, (size_t)nt * b * b, &ha);
+    if (!rc) rc = reg_parted(c, X, T, blk, &hxp, hx);
+    if (!rc) rc = reg_vec(c, B, (size_t)T * blk, &hbp);
+    if (!rc) rc = reg_parted(c, R, T, PR, &hrp, hr);
+    if (!rc) rc = reg_vec(c, eta, (size_t)nrhs + 1, &he);
+    if (rc) return rc;
+    (void)hb;
+    b3t_codelet cres, cax, cnrm;
+    if ((rc = kind_codelet(c, kResid, &cres)) || (rc = kind_codelet(c, kAxpy, &cax)) ||
+        (rc = kind_codelet(c, kNrm, &cnrm)))
+        return rc;
+    auto resid = [&](int32_t fl) -> int {
+        for (int32_t i = 0; i < T; ++i) {
+            VecArgs v{nrhs, fl, i, T, b};
+            const b3t_handle h4[4] = {ha, hxp, hbp, hr[i]};
+            const int r2 = submit_impl(c, cres, h4, nullptr, 4, &v, sizeof(v));
+            if (r2) return r2;
+        }
+        return 0;
+    };
+    if ((rc = resid(kVecAssign))) return rc;          // r_0 = b (x_0 = 0)
+    std::vector<double> host(nrhs + 1, 0.0);
+    double prev = 0.0;
+    for (int32_t it = 1; it <= max_iter; ++it) {
+        if ((rc = submit_solve(c, hl, hr, T, b, nrhs, flags))) return rc;
+        for (int32_t i = 0; i < T; ++i) {
+            VecArgs v{nrhs, it == 1 ? kVecAssign : 0, i, T, b};
+            const b3t_handle h2[2] = {hx[i], hr[i]};
+            if ((rc = submit_impl(c, cax, h2, nullptr, 2, &v, sizeof(v)))) return rc;
+        }
+        if ((rc = resid(0))) return rc;
+        VecArgs v{nrhs, 0, 0, T, b};
+        const b3t_handle h3[3] = {hrp, hbp, he};
+        if ((rc = submit_impl(c, cnrm, h3, nullptr, 3, &v, sizeof(v)))) return rc;
+        if ((rc = wait_impl(c, 0))) return rc;
+        if ((rc = cuda_err(cudaMemcpyAsync(host.data(), eta, (nrhs + 1) * sizeof(double),
+                                           cudaMemcpyDeviceToHost, c->stream))) ||
+            (rc = cuda_err(cudaStreamSynchronize(c->stream))))
+            return rc;
+        if (iters) *iters = it;
+        if (eta_out) std::memcpy(eta_out, host.data(), (nrhs + 1) * sizeof(double));
+        const double e = host[nrhs];
+        if (e <= tol) return 0;
+        if (it >= 2 && !(e < 0.9 * prev)) return -ERANGE;
+        prev = e;
+    }
+    return -ERANGE;
 }
 
 int b3t_tiles_unregister(b3t_ctx *c, void *const *tiles, int32_t T) {

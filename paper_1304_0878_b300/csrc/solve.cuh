@@ -1,0 +1,285 @@
+// Solve and refinement task bodies (256 threads per CTA).
+//
+// Vectors with nrhs right-hand sides are split into T row blocks ("parts")
+// of b rows; part k holds Y_k(r, j) at j*b + r (column-major b x nrhs).
+//   TRSV_L  : Y_k <- L_kk^{-1} Y_k            item = one right-hand side
+//   GEMV_L  : Y_i <- Y_i - L_ik Y_k           item = 64 rows of Y_i
+//   TRSV_LT : Y_k <- L_kk^{-T} Y_k            item = one right-hand side
+//   GEMV_LT : Y_i <- Y_i - L_ki^T Y_k         item = 64 rows of Y_i
+//   AXPY    : X_i <- X_i + D_i (or X_i = D_i) one item
+//   RESID   : R_i <- B_i - (A X)_i, FP64, with A symmetric and only its lower
+//             tiles stored; also per-item maxima |R|, |X_i| and the largest
+//             row sum of |A| (for the backward error)   item = 32 rows
+//   NRM     : eta_j = max|r_j| / (||A||_inf max|x_j| + max|b_j|), one item
+// The solve bodies compute in Tc (double, or float for refinement
+// corrections) and read / write FP64 storage.
+#pragma once
+#include "b3t_internal.h"
+
+namespace b3t {
+
+// record packing of the vector kinds: n = b, aux = i | flags << 24,
+// scal = T | nrhs << 16
+__device__ __forceinline__ int vk_nrhs(const TaskRec &t) { return (int)(t.scal >> 16); }
+__device__ __forceinline__ int vk_T(const TaskRec &t) { return (int)(t.scal & 0xffff); }
+__device__ __forceinline__ int vk_i(const TaskRec &t) { return t.aux & 0xffffff; }
+__device__ __forceinline__ int vk_flags(const TaskRec &t) { return (t.aux >> 24) & 0xff; }
+
+template <typename Tc>
+__device__ __forceinline__ void trsv_l_item(const TaskRec &t, int j, unsigned char *smem) {
+    const double *L = (const double *)t.buf[0];
+    double *y = (double *)t.buf[1] + (size_t)j * t.n;
+    const int b = (int)t.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    Tc *ys = (Tc *)smem;                 // [b]
+    Tc *red = ys + b;                    // [8][32]
+    Tc *Dg = red + 256;                  // [32][33]
+    for (int r = tid; r < b; r += kThreads) ys[r] = (Tc)y[r];
+    __syncthreads();
+    for (int R0 = 0; R0 < b; R0 += 32) {
+        Tc s = 0;
+        for (int q = warp; q < R0; q += 8) s += (Tc)L[(size_t)(R0 + lane) + (size_t)q * b] * ys[q];
+        red[warp * 32 + lane] = s;
+        for (int e = tid; e < 1024; e += kThreads) {
+            const int i = e & 31, k = e >> 5;
+            Dg[i * 33 + k] = i >= k ? (Tc)L[(size_t)(R0 + i) + (size_t)(R0 + k) * b] : (Tc)0;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            Tc v = ys[R0 + lane];
+            for (int g = 0; g < 8; ++g) v -= red[g * 32 + lane];
+            for (int c = 0; c < 32; ++c) {
+                if (lane == c) v = v / Dg[c * 33 + c];
+                const Tc xc = __shfl_sync(0xffffffffu, v, c);
+                if (lane > c) v -= Dg[lane * 33 + c] * xc;
+            }
+            ys[R0 + lane] = v;
+        }
+        __syncthreads();
+    }
+    for (int r = tid; r < b; r += kThreads) y[r] = (double)ys[r];
+}
+
+template <typename Tc>
+__device__ __forceinline__ void trsv_lt_item(const TaskRec &t, int j, unsigned char *smem) {
+    const double *L = (const double *)t.buf[0];
+    double *y = (double *)t.buf[1] + (size_t)j * t.n;
+    const int b = (int)t.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    Tc *ys = (Tc *)smem;                 // [b]
+    Tc *red = ys + b;                    // [32]
+    Tc *Dg = red + 256;                  // [32][33]
+    for (int r = tid; r < b; r += kThreads) ys[r] = (Tc)y[r];
+    __syncthreads();
+    for (int R0 = b - 32; R0 >= 0; R0 -= 32) {
+        // red[r] = sum_{q >= R0+32} L(q, R0+r) y_q  (column R0+r of L is contiguous)
+        for (int r = warp; r < 32; r += 8) {
+            Tc s = 0;
+            const double *col = L + (size_t)(R0 + r) * b;
+            for (int q = R0 + 32 + lane; q < b; q += 32) s += (Tc)col[q] * ys[q];
+            for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) red[r] = s;
+        }
+        for (int e = tid; e < 1024; e += kThreads) {
+            const int i = e & 31, k = e >> 5;
+            Dg[i * 33 + k] = i >= k ? (Tc)L[(size_t)(R0 + i) + (size_t)(R0 + k) * b] : (Tc)0;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            Tc v = ys[R0 + lane] - red[lane];
+            for (int c = 31; c >= 0; --c) {
+                if (lane == c) v = v / Dg[c * 33 + c];
+                const Tc xc = __shfl_sync(0xffffffffu, v, c);
+                if (lane < c) v -= Dg[c * 33 + lane] * xc;
+            }
+            ys[R0 + lane] = v;
+        }
+        __syncthreads();
+    }
+    for (int r = tid; r < b; r += kThreads) y[r] = (double)ys[r];
+}
+
+// Y_i(r0+r, j) -= sum_q M(r, q) Y_k(q, j), M = L_ik (trans = false) or
+// L_ki^T (trans = true), 64 rows per item.
+template <typename Tc, bool trans>
+__device__ __forceinline__ void gemv_item(const TaskRec &t, int item, unsigned char *smem) {
+    const double *L = (const double *)t.buf[0];
+    const double *Yk = (const double *)t.buf[1];
+    double *Yi = (double *)t.buf[2];
+    const int b = (int)t.n, nrhs = vk_nrhs(t), tid = threadIdx.x;
+    const int r = tid & 63, g = tid >> 6, r0 = item * 64;
+    Tc *Ys = (Tc *)smem;                 // [nrhs][64]
+    Tc *Lc = Ys + 64 * 32;               // [64][65] (trans only)
+    Tc acc[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) acc[m] = 0;
+    for (int q0 = 0; q0 < b; q0 += 64) {
+        for (int e = tid; e < 64 * nrhs; e += kThreads) {
+            const int q = e & 63, jj = e >> 6;
+            Ys[jj * 64 + q] = (Tc)Yk[(size_t)jj * b + q0 + q];
+        }
+        if (trans) {
+            for (int e = tid; e < 64 * 64; e += kThreads) {
+                const int q = e & 63, rr = e >> 6;
+                Lc[rr * 65 + q] = (Tc)L[(size_t)(q0 + q) + (size_t)(r0 + rr) * b];
+            }
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int q = 0; q < 64; ++q) {
+            const Tc a = trans ? Lc[r * 65 + q] : (Tc)L[(size_t)(r0 + r) + (size_t)(q0 + q) * b];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int jj = g + 4 * m;
+                if (jj < nrhs) acc[m] += a * Ys[jj * 64 + q];
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const int jj = g + 4 * m;
+        if (jj < nrhs) {
+            double *p = Yi + (size_t)jj * b + r0 + r;
+            *p = *p - (double)acc[m];
+        }
+    }
+}
+
+__device__ __forceinline__ void axpy_item(const TaskRec &t) {
+    double *X = (double *)t.buf[0];
+    const double *D = (const double *)t.buf[1];
+    const size_t n = (size_t)t.n * vk_nrhs(t);
+    const bool assign = vk_flags(t) & 2;
+    for (size_t e = threadIdx.x; e < n; e += kThreads) X[e] = assign ? D[e] : X[e] + D[e];
+}
+
+__device__ __forceinline__ int64_t ptile(int i, int j, int T) {
+    return (int64_t)j * T - (int64_t)j * (j - 1) / 2 + (i - j);
+}
+
+__device__ __forceinline__ void resid_item(const TaskRec &t, int item, unsigned char *smem) {
+    const double *A = (const double *)t.buf[0];
+    const double *X = (const double *)t.buf[1];
+    const double *B = (const double *)t.buf[2];
+    double *Ri = (double *)t.buf[3];
+    const int b = (int)t.n, nrhs = vk_nrhs(t), T = vk_T(t), i = vk_i(t);
+    const bool xzero = vk_flags(t) & 2;
+    const int tid = threadIdx.x, r = tid & 31, g = tid >> 5, r0 = item * 32, nit = b / 32;
+    double *As = (double *)smem;          // [64][33]
+    double *Xs = As + 64 * 33;            // [nrhs][64]
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    double rs = 0.0;
+    if (!xzero) {
+        for (int J = 0; J < T; ++J) {
+            const double *tile = A + (size_t)ptile(J > i ? J : i, J > i ? i : J, T) * b * b;
+            for (int c0 = 0; c0 < b; c0 += 64) {
+                for (int e = tid; e < 64 * nrhs; e += kThreads) {
+                    const int c = e & 63, jj = e >> 6;
+                    Xs[jj * 64 + c] = X[(size_t)J * b * nrhs + (size_t)jj * b + c0 + c];
+                }
+                for (int e = tid; e < 2048; e += kThreads) {
+                    int rr, c;
+                    size_t off;
+                    if (J < i) {            // tile (i, J): (r, c) at r + c*b
+                        rr = e & 31; c = e >> 5;
+                        off = (size_t)(r0 + rr) + (size_t)(c0 + c) * b;
+                    } else if (J > i) {     // tile (J, i): A(i.., J..) = tile(c, r)
+                        c = e & 63; rr = e >> 6;
+                        off = (size_t)(c0 + c) + (size_t)(r0 + rr) * b;
+                    } else {                // diagonal tile: lower part, mirrored
+                        rr = e & 31; c = e >> 5;
+                        const int R = r0 + rr, C = c0 + c;
+                        off = R >= C ? (size_t)R + (size_t)C * b : (size_t)C + (size_t)R * b;
+                    }
+                    As[c * 33 + rr] = tile[off];
+                }
+                __syncthreads();
+#pragma unroll 4
+                for (int c = 0; c < 64; ++c) {
+                    const double a = As[c * 33 + r];
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        const int jj = g + 8 * m;
+                        if (jj < nrhs) acc[m] = fma(a, Xs[jj * 64 + c], acc[m]);
+                    }
+                    rs += fabs(a);
+                }
+                __syncthreads();
+            }
+        }
+    }
+    double *Rn = Ri + (size_t)b * nrhs;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int jj = g + 8 * m;
+        if (jj < nrhs) {   // warp-uniform
+            const size_t o = (size_t)jj * b + r0 + r;
+            const double v = B[(size_t)i * b * nrhs + o] - acc[m];
+            Ri[o] = v;
+            double mr = fabs(v), mx = xzero ? 0.0 : fabs(X[(size_t)i * b * nrhs + o]);
+            for (int s = 16; s; s >>= 1) {
+                mr = fmax(mr, __shfl_xor_sync(0xffffffffu, mr, s));
+                mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, s));
+            }
+            if (r == 0) {
+                Rn[(size_t)item * nrhs + jj] = mr;
+                Rn[(size_t)nit * nrhs + (size_t)item * nrhs + jj] = mx;
+            }
+        }
+    }
+    if (g == 0) {
+        for (int s = 16; s; s >>= 1) rs = fmax(rs, __shfl_xor_sync(0xffffffffu, rs, s));
+        if (r == 0) Rn[(size_t)2 * nit * nrhs + item] = rs;
+    }
+}
+
+__device__ __forceinline__ void nrm_item(const TaskRec &t, unsigned char *smem) {
+    const double *R = (const double *)t.buf[0];
+    const double *B = (const double *)t.buf[1];
+    double *eta = (double *)t.buf[2];
+    const int b = (int)t.n, nrhs = vk_nrhs(t), T = vk_T(t), nit = b / 32;
+    const int64_t PR = resid_part_elems(b, nrhs);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double *sm = (double *)smem;          // [4][8][32]: rmax, xmax, bmax, anorm partials
+    double rm = 0.0, xm = 0.0, bm = 0.0, an = 0.0;
+    const int jj = lane;
+    if (jj < nrhs) {
+        for (int k = warp; k < T * nit; k += 8) {
+            const double *Rn = R + (size_t)(k / nit) * PR + (size_t)b * nrhs;
+            const int it = k % nit;
+            rm = fmax(rm, Rn[(size_t)it * nrhs + jj]);
+            xm = fmax(xm, Rn[(size_t)nit * nrhs + (size_t)it * nrhs + jj]);
+        }
+        for (int k = warp; k < T * b; k += 8) {
+            const int part = k / b, row = k % b;
+            bm = fmax(bm, fabs(B[(size_t)part * b * nrhs + (size_t)jj * b + row]));
+        }
+    }
+    for (int k = tid; k < T * nit; k += kThreads) {
+        const double *Rn = R + (size_t)(k / nit) * PR + (size_t)b * nrhs;
+        an = fmax(an, Rn[(size_t)2 * nit * nrhs + k % nit]);
+    }
+    sm[0 * 256 + warp * 32 + lane] = rm;
+    sm[1 * 256 + warp * 32 + lane] = xm;
+    sm[2 * 256 + warp * 32 + lane] = bm;
+    sm[3 * 256 + tid] = an;
+    __syncthreads();
+    if (tid == 0) {
+        double a = 0.0;
+        for (int k = 0; k < 256; ++k) a = fmax(a, sm[3 * 256 + k]);
+        double emax = 0.0;
+        for (int j = 0; j < nrhs; ++j) {
+            double r2 = 0.0, x2 = 0.0, b2 = 0.0;
+            for (int w = 0; w < 8; ++w) {
+                r2 = fmax(r2, sm[0 * 256 + w * 32 + j]);
+                x2 = fmax(x2, sm[1 * 256 + w * 32 + j]);
+                b2 = fmax(b2, sm[2 * 256 + w * 32 + j]);
+            }
+            const double e = r2 / (a * x2 + b2);
+            eta[j] = e;
+            emax = fmax(emax, e);
+        }
+        eta[nrhs] = emax;
+    }
+}
+
+}  // namespace b3t
