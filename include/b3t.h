@@ -244,7 +244,8 @@ B3T_API int b3t_task_wait(b3t_ctx *ctx, int64_t timeout_ns);
 B3T_API int b3t_data_acquire(b3t_ctx *ctx, b3t_handle h, uint8_t mode);
 
 /* Wait for the tasks using the buffer, then forget the handle (Section 2).
- * Unregistering a partitioned parent unregisters its parts. */
+ * Unregistering a partitioned parent unregisters its parts.  In stream mode
+ * it does not wait: -EBUSY while an unfinished batch uses the buffer. */
 B3T_API int b3t_data_unregister(b3t_ctx *ctx, b3t_handle h);
 
 /* Detail of the last device-side failure: the task id (in submission order
@@ -337,7 +338,38 @@ B3T_API int b3t_ir_solve(b3t_ctx *ctx, const double *A_packed, double *const *L,
                          double *X, double *R, double *eta, int32_t T, int32_t b, int32_t nrhs,
                          int32_t flags, double tol, int32_t max_iter, int32_t *iters, double *eta_out);
 
-/* Wait, then unregister the T(T+1)/2 tiles given (any registered set). */
+/* ---------------------------------------------------------------------
+ * Stream mode: continuous submission into one resident persistent kernel.
+ * b3t_stream_open launches the executor on the context's stream and leaves it
+ * running; each b3t_stream_submit hands it the tasks submitted since the last
+ * call as one self-contained batch (edges only inside the batch), uploaded
+ * through a separate feed stream and published with a counter: the tasks of
+ * the new batch join the ready queue while earlier batches are still running,
+ * so their work overlaps on the device.  Capacities are fixed at open
+ * (-ENOMEM beyond).  A batch may not name a buffer that an unfinished batch
+ * uses (-EBUSY; the tasks stay pending).  The kernel exits after
+ * b3t_stream_close once everything published has retired, or at deadline_ns
+ * after open (-ETIMEDOUT).  While the stream is open, flush / wait / replay
+ * on this context return -EBUSY.  A POTRF that meets a non-positive pivot does
+ * not stop the stream: its batch completes with info set. */
+B3T_API int b3t_stream_open(b3t_ctx *ctx, int64_t max_tasks, int64_t max_edges, int32_t max_batches,
+                            int64_t deadline_ns);
+B3T_API int b3t_stream_submit(b3t_ctx *ctx, int32_t *batch_id);
+/* 1 if the batch has finished (info: 0, or the 1-based global column of a
+ * non-positive pivot), 0 if it is still running, a negative errno if the
+ * resident kernel stopped before finishing it.  Non-blocking. */
+B3T_API int b3t_stream_query(b3t_ctx *ctx, int32_t batch, int32_t *info);
+B3T_API int b3t_stream_close(b3t_ctx *ctx);
+
+/* Submit one refinement step of b3t_ir_solve without waiting (first != 0:
+ * start from x = 0, r = b), for callers that drive the loop themselves, such
+ * as a serving loop in stream mode.  eta is written by the step's NRM task. */
+B3T_API int b3t_ir_step_submit(b3t_ctx *ctx, const double *A_packed, double *const *L, const double *B,
+                               double *X, double *R, double *eta, int32_t T, int32_t b, int32_t nrhs,
+                               int32_t flags, int32_t first);
+
+/* Wait (or, in stream mode, check that no unfinished batch uses them), then
+ * unregister the T(T+1)/2 tiles given (any registered set). */
 B3T_API int b3t_tiles_unregister(b3t_ctx *ctx, void *const *tiles, int32_t T);
 
 /* ---------------------------------------------------------------------

@@ -72,8 +72,14 @@ _SIGS = {
                                               ctypes.POINTER(_vp), _i32, _i32, _i32, _i32]),
     "b3t_tiles_unregister": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), _i32]),
     "b3t_scal_chains_noalloc": (ctypes.c_int, [_vp, _i64, _i32, _i32, _vp, _i64, _vp]),
+    "b3t_stream_open": (ctypes.c_int, [_vp, _i64, _i64, _i32, _i64]),
+    "b3t_stream_submit": (ctypes.c_int, [_vp, _pi32]),
+    "b3t_stream_query": (ctypes.c_int, [_vp, _i32, _pi32]),
+    "b3t_stream_close": (ctypes.c_int, [_vp]),
     "b3t_chol_solve_submit": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), _vp, _i32, _i32, _i32, _i64, _i32]),
     "b3t_ir_work_elems": (_sz, [_i32, _i32, _i32]),
+    "b3t_ir_step_submit": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_vp), _vp, _vp, _vp, _vp, _i32, _i32,
+                                          _i32, _i32, _i32]),
     "b3t_ir_solve": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_vp), _vp, _vp, _vp, _vp, _i32, _i32, _i32,
                                     _i32, ctypes.c_double, _i32, _pi32, ctypes.POINTER(ctypes.c_double)]),
 }
@@ -257,6 +263,25 @@ class Context:
         _check(lib().b3t_cholesky_mx_submit(self._h, _ptrs(W_ptrs), _ptrs(L_ptrs), _ptrs(Q_ptrs),
                                             T, b, fmt, col0), "b3t_cholesky_mx_submit")
 
+    # -- stream mode (continuous submission) --------------------------------------
+    def stream_open(self, max_tasks, max_edges, max_batches, deadline_ns):
+        _check(lib().b3t_stream_open(self._h, max_tasks, max_edges, max_batches, deadline_ns),
+               "b3t_stream_open")
+
+    def stream_submit(self):
+        out = _i32()
+        _check(lib().b3t_stream_submit(self._h, ctypes.byref(out)), "b3t_stream_submit")
+        return out.value
+
+    def stream_query(self, batch):
+        """(done, info): done is True when the batch has finished."""
+        info = _i32(0)
+        rc = _check(lib().b3t_stream_query(self._h, batch, ctypes.byref(info)), "b3t_stream_query")
+        return rc == 1, info.value
+
+    def stream_close(self):
+        _check(lib().b3t_stream_close(self._h), "b3t_stream_close")
+
     def chol_solve_submit(self, L_ptrs, Y_ptr, T, b, nrhs, part_stride, flags=0):
         _check(lib().b3t_chol_solve_submit(self._h, _ptrs(L_ptrs), _vp(int(Y_ptr)), T, b, nrhs,
                                            part_stride, flags), "b3t_chol_solve_submit")
@@ -273,6 +298,11 @@ class Context:
         if rc < 0 and rc != ERANGE:
             raise B3TError(rc, "b3t_ir_solve")
         return rc, it.value, list(eta)
+
+    def ir_step_submit(self, A_ptr, L_ptrs, B_ptr, X_ptr, R_ptr, eta_ptr, T, b, nrhs, flags=0, first=True):
+        _check(lib().b3t_ir_step_submit(self._h, _vp(int(A_ptr)), _ptrs(L_ptrs), _vp(int(B_ptr)),
+                                        _vp(int(X_ptr)), _vp(int(R_ptr)), _vp(int(eta_ptr)), T, b, nrhs,
+                                        flags, 1 if first else 0), "b3t_ir_step_submit")
 
     def tiles_unregister(self, tile_ptrs, T):
         _check(lib().b3t_tiles_unregister(self._h, _ptrs(tile_ptrs), T), "b3t_tiles_unregister")

@@ -69,13 +69,29 @@ struct alignas(128) Ctl {
     int32_t err_info;            // POTRF info (1-based global column)
     int32_t err_where;           // where it was raised (diagnostics)
     unsigned long long retired;  // tasks retired in this launch
-    int32_t pad0[26];
+    unsigned long long subs_consumed;   // stream mode: submissions taken in
+    int32_t pad0[24];
     // per-level ring heads / tails, each on its own 128-byte line
     struct alignas(128) Level {
         unsigned long long head;
         unsigned long long tail;
         int32_t pad[28];
     } lvl[kMaxLevels];
+};
+
+// Stream mode (a resident kernel fed with new task graphs while it runs).
+// Written by the host through copies on a feed stream, read by the kernel.
+struct alignas(128) StreamCtl {
+    unsigned long long published_subs;   // submissions whose data is in place
+    unsigned long long published_tasks;  // tasks in those submissions
+    unsigned long long stop;             // host: no more submissions
+    unsigned long long pad[13];
+};
+
+struct SubDesc {
+    unsigned long long root_off;   // first root slot in the shared root array
+    uint32_t nroots;
+    uint32_t batch;
 };
 
 struct LaunchParams {
@@ -94,7 +110,17 @@ struct LaunchParams {
     int32_t has_mx;              // launch holds tcgen05 work: allocate TMEM
     int64_t timeout_ns;
     int32_t debug;
-    int32_t pad;
+    int32_t stream_mode;
+    // stream mode only
+    const StreamCtl *sctl;
+    const SubDesc *subs;
+    const unsigned long long *sroots;
+    const int32_t *task_batch;
+    int32_t *batch_left;
+    int32_t *batch_info;            // first POTRF info of a batch (device)
+    volatile int32_t *batch_done;   // host-mapped: 1 when a batch retired, 2 + info if a
+                                    // POTRF of it met a non-positive pivot
+    int64_t deadline_ns;
 };
 
 // Init-kernel parameters: reset counters, rings and status for a launch.
@@ -127,5 +153,6 @@ extern "C" {
 int b3t_internal_launch(const b3t::InitParams *ip, const b3t::LaunchParams *lp,
                         int nctas, size_t smem, void *stream, void *ev_start, void *ev_stop);
 int b3t_internal_occupancy(int *ctas_per_sm, size_t smem, int *num_sms);
+int b3t_internal_launch_exec(const b3t::LaunchParams *lp, int nctas, size_t smem, void *stream, void *ev_start);
 size_t b3t_internal_smem_bytes(int has_mx);
 }

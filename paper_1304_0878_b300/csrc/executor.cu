@@ -115,7 +115,20 @@ __device__ __forceinline__ int potrf_mx_item(const TaskRec &t, double *smem, int
 // item.  Returns the packed (task, item), or kEmpty when the launch is over
 // (all tasks retired, an error was raised, or the wait timed out: the last
 // two leave the reason in ctl).
-__device__ __forceinline__ unsigned long long claim(const LaunchParams &p) {
+__device__ __forceinline__ void push_roots(const LaunchParams &p, const SubDesc &sd) {
+    const int lane = threadIdx.x & 31;
+    for (uint32_t k = lane; k < sd.nroots; k += 32) {
+        const unsigned long long v = p.sroots[sd.root_off + k];
+        const int64_t t = (int64_t)(v >> 32);
+        const int lv = p.level[t];
+        const unsigned long long pos = atomicAdd(&p.ctl->lvl[lv].tail, 1ull);
+        if (p.debug && pos >= p.ring_cap[lv]) set_error(p.ctl, EPROTO, (int)t, -1, 7);
+        else st_rel(p.slots + p.ring_off[lv] + pos, v);
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ unsigned long long claim(const LaunchParams &p, uint64_t kstart) {
     const int lane = threadIdx.x & 31;
     Ctl *ctl = p.ctl;
     const uint64_t t0 = gtimer();
@@ -158,11 +171,19 @@ __device__ __forceinline__ unsigned long long claim(const LaunchParams &p) {
                     if (!got) {
                         const int64_t t = (int64_t)(v >> 32);
                         const int n = (int)(v & 0xffffffffu);
-                        const int i = atomicAdd(&p.next_item[t], 1);
-                        if (i >= n - 1) atomicCAS(&ctl->lvl[lv].head, hv, hv + 1);
-                        if (i < n) {
-                            item = ((unsigned long long)t << 32) | (uint32_t)i;
-                            got = 1;
+                        if (n == 1) {
+                            // single-item task: taking the head slot is taking the task
+                            if (atomicCAS(&ctl->lvl[lv].head, hv, hv + 1) == hv) {
+                                item = (unsigned long long)t << 32;
+                                got = 1;
+                            }
+                        } else {
+                            const int i = atomicAdd(&p.next_item[t], 1);
+                            if (i >= n - 1) atomicCAS(&ctl->lvl[lv].head, hv, hv + 1);
+                            if (i < n) {
+                                item = ((unsigned long long)t << 32) | (uint32_t)i;
+                                got = 1;
+                            }
                         }
                     }
                 }
@@ -170,6 +191,37 @@ __device__ __forceinline__ unsigned long long claim(const LaunchParams &p) {
             got = __shfl_sync(0xffffffffu, got, 0);
             if (got == 1) return __shfl_sync(0xffffffffu, item, 0);
             if (got == 2) return kEmpty;
+            continue;
+        }
+        if (p.stream_mode) {
+            // take in a newly published task graph, or stop when told to and
+            // everything published has retired; bounded by the deadline
+            unsigned long long cs = 0, ps = 0;
+            int took = 0, done = 0;
+            if (lane == 0) {
+                ps = ld_acq(&p.sctl->published_subs);
+                cs = ld_rlx(&ctl->subs_consumed);
+                if (cs < ps) {
+                    took = atomicCAS(&ctl->subs_consumed, cs, cs + 1) == cs;
+                } else if (ld_acq(&p.sctl->stop)) {
+                    done = ld_acq(&ctl->retired) >= ld_acq(&p.sctl->published_tasks);
+                }
+            }
+            took = __shfl_sync(0xffffffffu, took, 0);
+            done = __shfl_sync(0xffffffffu, done, 0);
+            cs = __shfl_sync(0xffffffffu, cs, 0);
+            if (took) {
+                const SubDesc sd = p.subs[cs];
+                push_roots(p, sd);
+                continue;
+            }
+            if (done) return kEmpty;
+            if ((spin & 15) == 15 && (int64_t)(gtimer() - kstart) > p.deadline_ns) {
+                if (lane == 0) set_error(ctl, ETIMEDOUT, -1, -1, 8);
+                return kEmpty;
+            }
+            __nanosleep(backoff);
+            backoff = backoff < 256 ? backoff + 32 : 256;
             continue;
         }
         unsigned long long r = 0;
@@ -206,6 +258,15 @@ __device__ __forceinline__ void retire(const LaunchParams &p, int64_t t, const T
     __syncwarp();
     if (lane == 0) {
         __threadfence();
+        if (p.stream_mode) {
+            const int b = p.task_batch[t];
+            if (atomicSub(&p.batch_left[b], 1) == 1) {
+                const int info = atomicAdd(&p.batch_info[b], 0);
+                __threadfence_system();
+                p.batch_done[b] = info ? 2 + info : 1;
+                __threadfence_system();
+            }
+        }
         atomicAdd(&p.ctl->retired, 1ull);
     }
 }
@@ -241,9 +302,10 @@ __global__ void __launch_bounds__(kThreads, 2) exec_kernel(const LaunchParams p)
         mx.tmem = s_tmem;
     }
 
+    const uint64_t kstart = gtimer();
     for (;;) {
         if (warp == 0) {
-            const unsigned long long it = claim(p);
+            const unsigned long long it = claim(p, kstart);
             if ((tid & 31) == 0) s_item = it;
         }
         __syncthreads();
@@ -303,6 +365,12 @@ __global__ void __launch_bounds__(kThreads, 2) exec_kernel(const LaunchParams p)
         default: break;   // NOOP
         }
         __syncthreads();
+        if (st > 0 && p.stream_mode) {
+            // a served request that is not positive definite fails alone: its
+            // info is reported with the batch and the graph drains
+            if (tid == 0) atomicCAS(&p.batch_info[p.task_batch[t]], 0, st);
+            st = 0;
+        }
         if (tid == 0) {
             if (st > 0) {
                 set_error(p.ctl, EDOM, (int)t, st, 0);   // not positive definite: no retire
@@ -384,4 +452,12 @@ extern "C" int b3t_internal_launch(const InitParams *ip, const LaunchParams *lp,
     if (ev_stop) cudaEventRecord((cudaEvent_t)ev_stop, s);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? 0 : -EIO;
+}
+
+extern "C" int b3t_internal_launch_exec(const LaunchParams *lp, int nctas, size_t smem, void *stream,
+                                        void *ev_start) {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (ev_start) cudaEventRecord((cudaEvent_t)ev_start, s);
+    exec_kernel<<<nctas, kThreads, smem, s>>>(*lp);
+    return cudaGetLastError() == cudaSuccess ? 0 : -EIO;
 }

@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cerrno>
 #include <chrono>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <thread>
@@ -201,6 +202,28 @@ struct b3t_ctx {
     int32_t err_task = -1, err_info = -1;
     std::vector<GraphRec> graphs;
     b3t_codelet kind_cl[kNumKinds];
+    // stream mode: one resident kernel fed with task graphs while it runs
+    struct Stream {
+        bool open = false;
+        cudaStream_t feed = nullptr;
+        cudaEvent_t staged = nullptr;
+        int64_t max_tasks = 0, max_edges = 0;
+        int32_t max_batches = 0;
+        TaskRec *tasks = nullptr;
+        int32_t *succ = nullptr, *level = nullptr, *counters = nullptr, *done = nullptr, *next = nullptr;
+        int32_t *task_batch = nullptr, *batch_left = nullptr, *batch_info = nullptr;
+        unsigned long long *slots = nullptr, *sroots = nullptr;
+        SubDesc *subs = nullptr;
+        StreamCtl *sctl = nullptr;
+        Ctl *ctl = nullptr;
+        int32_t *done_h = nullptr;            // host-mapped batch status
+        int32_t *done_d = nullptr;
+        void *staging = nullptr;
+        size_t staging_cap = 0;
+        int64_t ntasks = 0, nedges = 0, nroots = 0;
+        int32_t nbatches = 0;
+        std::vector<int32_t> handle_batch;    // last batch that used each handle
+    } st;
 };
 
 namespace {
@@ -381,6 +404,13 @@ int grid_for(b3t_ctx *c, bool has_mx, int *nctas, size_t *smem) {
     int rc = b3t_internal_occupancy(&per_sm, *smem, &sms);
     if (rc) return rc;
     if (c->cfg.ctas_per_sm > 0) per_sm = std::min(per_sm, c->cfg.ctas_per_sm);
+    // B3T_CTAS_PER_SM overrides the occupancy query (1..4).  Claims never
+    // wait on other work items, so a grid larger than what is resident is
+    // still correct: the extra CTAs start as others finish.
+    if (const char *e = std::getenv("B3T_CTAS_PER_SM")) {
+        const int v = std::atoi(e);
+        if (v >= 1 && v <= 4) per_sm = v;
+    }
     if (per_sm < 1) return -EINVAL;
     *nctas = per_sm * sms;
     return 0;
@@ -408,6 +438,7 @@ int track(b3t_ctx *c, Ctl *dev) {
 
 int flush_impl(b3t_ctx *c) {
     if (c->tasks.empty()) return 0;
+    if (c->st.open) return -EBUSY;
     if (c->cfg.host_only) { clear_batch(c); return -ENODEV; }
     InitParams ip; LaunchParams lp; int64_t nitems; bool has_mx;
     int rc = build_launch(c, c->arena, ip, lp, nitems, has_mx);
@@ -460,6 +491,7 @@ int read_status(b3t_ctx *c) {
 }
 
 int wait_impl(b3t_ctx *c, int64_t timeout_ns) {
+    if (c->st.open) return -EBUSY;
     int rc = flush_impl(c);
     if (c->cfg.host_only) return rc;
     const int rs = sync_stream(c, timeout_ns);
@@ -618,6 +650,7 @@ int b3t_init(b3t_ctx **out, const b3t_config *cfg, void *cuda_stream) {
 int b3t_shutdown(b3t_ctx *c) {
     if (!c) return -EINVAL;
     if (c->cfg.host_only) { delete c; return 0; }
+    if (c->st.open) b3t_stream_close(c);
     const int rc = wait_impl(c, 0);
     for (auto &g : c->graphs) {
         if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -740,11 +773,31 @@ int b3t_data_acquire(b3t_ctx *c, b3t_handle h, uint8_t mode) {
     return wait_impl(c, 0);
 }
 
+static bool stream_handle_busy(b3t_ctx *c, b3t_handle h) {
+    auto &S = c->st;
+    if (!S.open || h >= (int32_t)S.handle_batch.size()) return false;
+    std::vector<int32_t> hs{h};
+    for (int32_t k : c->handles[h].parts) hs.push_back(k);
+    for (int32_t x : hs) {
+        if (x < (int32_t)S.handle_batch.size()) {
+            const int32_t b = S.handle_batch[x];
+            if (b >= 0 && ((volatile int32_t *)S.done_h)[b] == 0) return true;
+        }
+        if (c->handles[x].touched) return true;    // named by a pending task
+    }
+    return false;
+}
+
 int b3t_data_unregister(b3t_ctx *c, b3t_handle h) {
     if (!c) return -EINVAL;
     int rc = check_handle(c, h);
     if (rc) return rc;
-    rc = c->capturing ? 0 : wait_impl(c, 0);
+    if (c->st.open) {
+        // stream mode: no wait; the buffer must not be in use
+        if (stream_handle_busy(c, h)) return -EBUSY;
+    } else {
+        rc = c->capturing ? 0 : wait_impl(c, 0);
+    }
     Handle &H = c->handles[h];
     for (int32_t k : H.parts) {
         auto it = c->by_ptr.find((uintptr_t)c->handles[k].ptr);
@@ -889,6 +942,213 @@ int b3t_debug_block_task(b3t_ctx *c, int64_t t) {
     if (c->extra_deps.size() < c->tasks.size()) c->extra_deps.resize(c->tasks.size(), 0);
     c->extra_deps[t] += 1;
     return 0;
+}
+
+// ------------------------------------------------------------- stream mode
+
+static void stream_free(b3t_ctx *c) {
+    auto &S = c->st;
+    cudaFree(S.tasks); cudaFree(S.succ); cudaFree(S.level); cudaFree(S.counters); cudaFree(S.done);
+    cudaFree(S.next); cudaFree(S.task_batch); cudaFree(S.batch_left); cudaFree(S.batch_info);
+    cudaFree(S.slots); cudaFree(S.sroots); cudaFree(S.subs); cudaFree(S.sctl); cudaFree(S.ctl);
+    if (S.done_h) cudaFreeHost(S.done_h);
+    if (S.staging) cudaFreeHost(S.staging);
+    if (S.staged) cudaEventDestroy(S.staged);
+    if (S.feed) cudaStreamDestroy(S.feed);
+    c->st = b3t_ctx::Stream();
+}
+
+int b3t_stream_open(b3t_ctx *c, int64_t max_tasks, int64_t max_edges, int32_t max_batches,
+                    int64_t deadline_ns) {
+    if (!c || max_tasks <= 0 || max_edges < 0 || max_batches <= 0 || deadline_ns <= 0) return -EINVAL;
+    if (c->cfg.host_only) return -ENODEV;
+    if (c->st.open || c->capturing || !c->tasks.empty()) return -EBUSY;
+    int rc = wait_impl(c, 0);
+    if (rc) return rc;
+    auto &S = c->st;
+    const int L = c->cfg.prio_levels;
+    const size_t nt = (size_t)max_tasks, ne = (size_t)std::max<int64_t>(max_edges, 1);
+    bool ok = cudaMalloc(&S.tasks, nt * sizeof(TaskRec)) == cudaSuccess &&
+              cudaMalloc(&S.succ, ne * 4) == cudaSuccess && cudaMalloc(&S.level, nt * 4) == cudaSuccess &&
+              cudaMalloc(&S.counters, nt * 4) == cudaSuccess && cudaMalloc(&S.done, nt * 4) == cudaSuccess &&
+              cudaMalloc(&S.next, nt * 4) == cudaSuccess && cudaMalloc(&S.task_batch, nt * 4) == cudaSuccess &&
+              cudaMalloc(&S.batch_left, (size_t)max_batches * 4) == cudaSuccess &&
+              cudaMalloc(&S.batch_info, (size_t)max_batches * 4) == cudaSuccess &&
+              cudaMalloc(&S.slots, (size_t)L * nt * 8) == cudaSuccess &&
+              cudaMalloc(&S.sroots, nt * 8) == cudaSuccess &&
+              cudaMalloc(&S.subs, (size_t)max_batches * sizeof(SubDesc)) == cudaSuccess &&
+              cudaMalloc(&S.sctl, sizeof(StreamCtl)) == cudaSuccess && cudaMalloc(&S.ctl, sizeof(Ctl)) == cudaSuccess &&
+              cudaHostAlloc((void **)&S.done_h, (size_t)max_batches * 4, cudaHostAllocMapped) == cudaSuccess &&
+              cudaHostGetDevicePointer((void **)&S.done_d, S.done_h, 0) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&S.feed, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&S.staged, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) { cudaGetLastError(); stream_free(c); return -ENOMEM; }
+    S.max_tasks = max_tasks; S.max_edges = (int64_t)ne; S.max_batches = max_batches;
+    std::memset(S.done_h, 0, (size_t)max_batches * 4);
+    cudaMemsetAsync(S.slots, 0xff, (size_t)L * nt * 8, c->stream);
+    cudaMemsetAsync(S.ctl, 0, sizeof(Ctl), c->stream);
+    cudaMemsetAsync(S.sctl, 0, sizeof(StreamCtl), c->stream);
+    cudaMemsetAsync(S.batch_info, 0, (size_t)max_batches * 4, c->stream);
+    if ((rc = cuda_err(cudaStreamSynchronize(c->stream)))) { stream_free(c); return rc; }
+    S.handle_batch.assign(c->handles.size(), -1);
+    LaunchParams lp{};
+    lp.tasks = S.tasks; lp.succ = S.succ; lp.level = S.level; lp.counters = S.counters;
+    lp.done_items = S.done; lp.next_item = S.next; lp.slots = S.slots; lp.ctl = S.ctl;
+    for (int l = 0; l < L; ++l) { lp.ring_off[l] = (unsigned long long)l * nt; lp.ring_cap[l] = nt; }
+    lp.ntasks = max_tasks; lp.nlevels = L; lp.has_mx = 1; lp.timeout_ns = c->cfg.timeout_ns;
+    lp.debug = c->cfg.debug_checks; lp.stream_mode = 1;
+    lp.sctl = S.sctl; lp.subs = S.subs; lp.sroots = S.sroots; lp.task_batch = S.task_batch;
+    lp.batch_left = S.batch_left; lp.batch_info = S.batch_info; lp.batch_done = S.done_d;
+    lp.deadline_ns = deadline_ns;
+    int nctas; size_t smem;
+    if ((rc = grid_for(c, true, &nctas, &smem))) { stream_free(c); return rc; }
+    if ((rc = b3t_internal_launch_exec(&lp, nctas, smem, c->stream, c->ev0))) { stream_free(c); return rc; }
+    S.open = true;
+    c->last_nctas = nctas;
+    return 0;
+}
+
+int b3t_stream_submit(b3t_ctx *c, int32_t *batch_id) {
+    if (!c || !batch_id) return -EINVAL;
+    auto &S = c->st;
+    if (!S.open) return -EINVAL;
+    const int64_t nt = (int64_t)c->tasks.size(), ne = (int64_t)c->edges.size();
+    if (nt == 0) return -EINVAL;
+    if (S.ntasks + nt > S.max_tasks || S.nedges + ne > S.max_edges || S.nroots + nt > S.max_tasks ||
+        S.nbatches >= S.max_batches)
+        return -ENOMEM;
+    // a buffer still used by an unfinished batch may not be named again
+    if (S.handle_batch.size() < c->handles.size()) S.handle_batch.resize(c->handles.size(), -1);
+    for (int32_t h : c->touched) {
+        const int32_t b = S.handle_batch[h];
+        if (b >= 0 && ((volatile int32_t *)S.done_h)[b] == 0) return -EBUSY;
+    }
+    const int32_t batch = S.nbatches;
+    const int64_t base = S.ntasks, eoff = S.nedges;
+    const int L = c->cfg.prio_levels;
+    std::vector<int32_t> off(nt + 1, 0), indeg(nt, 0), succ(std::max<int64_t>(ne, 1));
+    for (auto &e : c->edges) { off[e.first + 1]++; indeg[e.second]++; }
+    for (int64_t t = 0; t < nt; ++t) off[t + 1] += off[t];
+    {
+        std::vector<int32_t> pos(off.begin(), off.end() - 1);
+        for (auto &e : c->edges) succ[pos[e.first]++] = (int32_t)(base + e.second);
+    }
+    for (int64_t t = 0; t < nt && t < (int64_t)c->extra_deps.size(); ++t) indeg[t] += c->extra_deps[t];
+    std::vector<float> rank(nt, 0.f);
+    float maxr = 0.f;
+    for (int64_t t = nt - 1; t >= 0; --t) {
+        float m = 0.f;
+        for (int32_t k = off[t]; k < off[t + 1]; ++k) m = std::max(m, rank[succ[k] - base]);
+        rank[t] = c->tasks[t].cost + m;
+        maxr = std::max(maxr, rank[t]);
+    }
+    std::vector<int32_t> level(nt), tb(nt, batch), zeros(nt, 0);
+    std::vector<unsigned long long> roots;
+    for (int64_t t = 0; t < nt; ++t) {
+        TaskRec &r = c->tasks[t].rec;
+        r.succ_off = (int32_t)(eoff + off[t]);
+        r.nsucc = off[t + 1] - off[t];
+        level[t] = (L > 1 && maxr > 0.f) ? std::min(L - 1, (int)((double)L * rank[t] / (maxr * 1.000001))) : 0;
+        if (indeg[t] == 0) roots.push_back(pack_slot(base + t, r.nitems));
+    }
+    const int64_t nr = (int64_t)roots.size();
+    // staging layout
+    const size_t o_t = 0, o_s = o_t + nt * sizeof(TaskRec), o_l = o_s + ne * 4, o_i = o_l + nt * 4,
+                 o_z = o_i + nt * 4, o_b = o_z + nt * 4, o_r = (o_b + nt * 4 + 15) / 16 * 16,
+                 o_m = o_r + nr * 8, bytes = o_m + 64;
+    cudaEventSynchronize(S.staged);
+    if (bytes > S.staging_cap) {
+        if (S.staging) cudaFreeHost(S.staging);
+        S.staging = nullptr;
+        S.staging_cap = 0;
+        if (cudaMallocHost(&S.staging, std::max(bytes, (size_t)1 << 20)) != cudaSuccess) return -ENOMEM;
+        S.staging_cap = std::max(bytes, (size_t)1 << 20);
+    }
+    char *sp = (char *)S.staging;
+    for (int64_t t = 0; t < nt; ++t) std::memcpy(sp + o_t + t * sizeof(TaskRec), &c->tasks[t].rec, sizeof(TaskRec));
+    if (ne) std::memcpy(sp + o_s, succ.data(), ne * 4);
+    std::memcpy(sp + o_l, level.data(), nt * 4);
+    std::memcpy(sp + o_i, indeg.data(), nt * 4);
+    std::memcpy(sp + o_z, zeros.data(), nt * 4);
+    std::memcpy(sp + o_b, tb.data(), nt * 4);
+    std::memcpy(sp + o_r, roots.data(), nr * 8);
+    int32_t *misc = (int32_t *)(sp + o_m);
+    misc[0] = (int32_t)nt;   // batch_left
+    misc[1] = 0;             // batch_info
+    SubDesc sd{(unsigned long long)S.nroots, (uint32_t)nr, (uint32_t)batch};
+    std::memcpy(sp + o_m + 16, &sd, sizeof(sd));
+    unsigned long long pub[2] = {(unsigned long long)batch + 1, (unsigned long long)(base + nt)};
+    std::memcpy(sp + o_m + 32, pub, sizeof(pub));
+    ((volatile int32_t *)S.done_h)[batch] = 0;
+    cudaStream_t f = S.feed;
+    cudaMemcpyAsync(S.tasks + base, sp + o_t, nt * sizeof(TaskRec), cudaMemcpyHostToDevice, f);
+    if (ne) cudaMemcpyAsync(S.succ + eoff, sp + o_s, ne * 4, cudaMemcpyHostToDevice, f);
+    cudaMemcpyAsync(S.level + base, sp + o_l, nt * 4, cudaMemcpyHostToDevice, f);
+    cudaMemcpyAsync(S.counters + base, sp + o_i, nt * 4, cudaMemcpyHostToDevice, f);
+    cudaMemcpyAsync(S.done + base, sp + o_z, nt * 4, cudaMemcpyHostToDevice, f);
+    cudaMemcpyAsync(S.next + base, sp + o_z, nt * 4, cudaMemcpyHostToDevice, f);
+    cudaMemcpyAsync(S.task_batch + base, sp + o_b, nt * 4, cudaMemcpyHostToDevice, f);
+    cudaMemcpyAsync(S.sroots + S.nroots, sp + o_r, nr * 8, cudaMemcpyHostToDevice, f);
+    cudaMemcpyAsync(S.batch_left + batch, sp + o_m, 4, cudaMemcpyHostToDevice, f);
+    cudaMemcpyAsync(S.batch_info + batch, sp + o_m + 4, 4, cudaMemcpyHostToDevice, f);
+    cudaMemcpyAsync(S.subs + batch, sp + o_m + 16, sizeof(SubDesc), cudaMemcpyHostToDevice, f);
+    // publish last: the kernel reads the data only after it sees the counters
+    cudaMemcpyAsync(S.sctl, sp + o_m + 32, 16, cudaMemcpyHostToDevice, f);
+    const int rc = cuda_err(cudaEventRecord(S.staged, f));
+    if (rc) return rc;
+    for (int32_t h : c->touched) S.handle_batch[h] = batch;
+    S.ntasks += nt;
+    S.nedges += ne;
+    S.nroots += nr;
+    S.nbatches += 1;
+    clear_batch(c);
+    *batch_id = batch;
+    return 0;
+}
+
+int b3t_stream_query(b3t_ctx *c, int32_t batch, int32_t *info) {
+    if (!c || !c->st.open || batch < 0 || batch >= c->st.nbatches) return -EINVAL;
+    const int32_t v = ((volatile int32_t *)c->st.done_h)[batch];
+    if (v) {
+        if (info) *info = v >= 2 ? v - 2 : 0;
+        return 1;
+    }
+    const cudaError_t e = cudaStreamQuery(c->stream);
+    if (e == cudaErrorNotReady) return 0;
+    // the resident kernel has stopped with this batch unfinished
+    Ctl h;
+    if (e != cudaSuccess || cudaMemcpy(&h, c->st.ctl, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return -EIO;
+    }
+    if (h.error) { c->err_task = h.err_task; c->err_info = h.err_info; return -h.error; }
+    return -EIO;
+}
+
+int b3t_stream_close(b3t_ctx *c) {
+    if (!c || !c->st.open) return -EINVAL;
+    auto &S = c->st;
+    static const unsigned long long one = 1;
+    unsigned long long *stopflag = nullptr;
+    int rc = 0;
+    if (cudaMallocHost(&stopflag, 8) == cudaSuccess) {
+        *stopflag = one;
+        cudaMemcpyAsync(&S.sctl->stop, stopflag, 8, cudaMemcpyHostToDevice, S.feed);
+        cudaStreamSynchronize(S.feed);
+    } else {
+        rc = -ENOMEM;
+    }
+    const int rs = cuda_err(cudaStreamSynchronize(c->stream));
+    Ctl h;
+    std::memset(&h, 0, sizeof(h));
+    if (!rs && cudaMemcpy(&h, S.ctl, sizeof(h), cudaMemcpyDeviceToHost) == cudaSuccess && h.error) {
+        c->err_task = h.err_task;
+        c->err_info = h.err_info;
+        if (!rc) rc = -h.error;
+    }
+    if (stopflag) cudaFreeHost(stopflag);
+    stream_free(c);
+    return rc ? rc : rs;
 }
 
 // ------------------------------------------------------------- Cholesky
@@ -1063,6 +1323,64 @@ size_t b3t_ir_work_elems(int32_t T, int32_t b, int32_t nrhs) {
     return (size_t)T * (size_t)resid_part_elems(b, nrhs);
 }
 
+// Registration shared by the refinement helpers.
+struct IrHandles {
+    std::vector<b3t_handle> hl, hx, hr;
+    b3t_handle ha, hxp, hrp, hbp, he;
+};
+
+static int ir_register(b3t_ctx *c, const double *A, double *const *L, const double *B, double *X, double *R,
+                       double *eta, int32_t T, int32_t b, int32_t nrhs, IrHandles &H) {
+    const int64_t nt = (int64_t)T * (T + 1) / 2;
+    const size_t blk = (size_t)b * nrhs, PR = (size_t)resid_part_elems(b, nrhs);
+    int rc = reg_tiles(c, (void *const *)L, nt, (size_t)b * b, 8, b, H.hl);
+    if (!rc) rc = reg_vec(c, A, (size_t)nt * b * b, &H.ha);
+    if (!rc) rc = reg_parted(c, X, T, blk, &H.hxp, H.hx);
+    if (!rc) rc = reg_vec(c, B, (size_t)T * blk, &H.hbp);
+    if (!rc) rc = reg_parted(c, R, T, PR, &H.hrp, H.hr);
+    if (!rc) rc = reg_vec(c, eta, (size_t)nrhs + 1, &H.he);
+    return rc;
+}
+
+// One refinement step: [first: r = b]; d = (L L^T)^{-1} r; x (+)= d;
+// r = b - A x; eta.
+static int ir_step(b3t_ctx *c, IrHandles &H, int32_t T, int32_t b, int32_t nrhs, int32_t flags, bool first) {
+    b3t_codelet cres, cax, cnrm;
+    int rc;
+    if ((rc = kind_codelet(c, kResid, &cres)) || (rc = kind_codelet(c, kAxpy, &cax)) ||
+        (rc = kind_codelet(c, kNrm, &cnrm)))
+        return rc;
+    auto resid = [&](int32_t fl) -> int {
+        for (int32_t i = 0; i < T; ++i) {
+            VecArgs v{nrhs, fl, i, T, b};
+            const b3t_handle h4[4] = {H.ha, H.hxp, H.hbp, H.hr[i]};
+            const int r2 = submit_impl(c, cres, h4, nullptr, 4, &v, sizeof(v));
+            if (r2) return r2;
+        }
+        return 0;
+    };
+    if (first && (rc = resid(kVecAssign))) return rc;          // r_0 = b (x_0 = 0)
+    if ((rc = submit_solve(c, H.hl, H.hr, T, b, nrhs, flags))) return rc;
+    for (int32_t i = 0; i < T; ++i) {
+        VecArgs v{nrhs, first ? kVecAssign : 0, i, T, b};
+        const b3t_handle h2[2] = {H.hx[i], H.hr[i]};
+        if ((rc = submit_impl(c, cax, h2, nullptr, 2, &v, sizeof(v)))) return rc;
+    }
+    if ((rc = resid(0))) return rc;
+    VecArgs v{nrhs, 0, 0, T, b};
+    const b3t_handle h3[3] = {H.hrp, H.hbp, H.he};
+    return submit_impl(c, cnrm, h3, nullptr, 3, &v, sizeof(v));
+}
+
+int b3t_ir_step_submit(b3t_ctx *c, const double *A, double *const *L, const double *B, double *X, double *R,
+                       double *eta, int32_t T, int32_t b, int32_t nrhs, int32_t flags, int32_t first) {
+    if (!c || !A || !L || !B || !X || !R || !eta || T <= 0 || b <= 0 || b % 64 || nrhs < 1 || nrhs > kMaxRhs)
+        return -EINVAL;
+    IrHandles H;
+    int rc = ir_register(c, A, L, B, X, R, eta, T, b, nrhs, H);
+    return rc ? rc : ir_step(c, H, T, b, nrhs, flags, first != 0);
+}
+
 int b3t_ir_solve(b3t_ctx *c, const double *A, double *const *L, const double *B, double *X, double *R,
                  double *eta, int32_t T, int32_t b, int32_t nrhs, int32_t flags, double tol, int32_t max_iter,
                  int32_t *iters, double *eta_out) {
@@ -1070,45 +1388,14 @@ int b3t_ir_solve(b3t_ctx *c, const double *A, double *const *L, const double *B,
         nrhs > kMaxRhs || max_iter < 1 || c->capturing)
         return -EINVAL;
     if (c->cfg.host_only) return -ENODEV;
-    const int64_t nt = (int64_t)T * (T + 1) / 2;
-    const size_t blk = (size_t)b * nrhs, PR = (size_t)resid_part_elems(b, nrhs);
-    std::vector<b3t_handle> hl, hx, hr, hb;
-    b3t_handle ha, hxp, hrp, hbp, he;
-    int rc = reg_tiles(c, (void *const *)L, nt, (size_t)b * b, 8, b, hl);
-    if (!rc) rc = reg_vec(c, A, (size_t)nt * b * b, &ha);
-    if (!rc) rc = reg_parted(c, X, T, blk, &hxp, hx);
-    if (!rc) rc = reg_vec(c, B, (size_t)T * blk, &hbp);
-    if (!rc) rc = reg_parted(c, R, T, PR, &hrp, hr);
-    if (!rc) rc = reg_vec(c, eta, (size_t)nrhs + 1, &he);
+    if (c->st.open) return -EBUSY;
+    IrHandles H;
+    int rc = ir_register(c, A, L, B, X, R, eta, T, b, nrhs, H);
     if (rc) return rc;
-    (void)hb;
-    b3t_codelet cres, cax, cnrm;
-    if ((rc = kind_codelet(c, kResid, &cres)) || (rc = kind_codelet(c, kAxpy, &cax)) ||
-        (rc = kind_codelet(c, kNrm, &cnrm)))
-        return rc;
-    auto resid = [&](int32_t fl) -> int {
-        for (int32_t i = 0; i < T; ++i) {
-            VecArgs v{nrhs, fl, i, T, b};
-            const b3t_handle h4[4] = {ha, hxp, hbp, hr[i]};
-            const int r2 = submit_impl(c, cres, h4, nullptr, 4, &v, sizeof(v));
-            if (r2) return r2;
-        }
-        return 0;
-    };
-    if ((rc = resid(kVecAssign))) return rc;          // r_0 = b (x_0 = 0)
     std::vector<double> host(nrhs + 1, 0.0);
     double prev = 0.0;
     for (int32_t it = 1; it <= max_iter; ++it) {
-        if ((rc = submit_solve(c, hl, hr, T, b, nrhs, flags))) return rc;
-        for (int32_t i = 0; i < T; ++i) {
-            VecArgs v{nrhs, it == 1 ? kVecAssign : 0, i, T, b};
-            const b3t_handle h2[2] = {hx[i], hr[i]};
-            if ((rc = submit_impl(c, cax, h2, nullptr, 2, &v, sizeof(v)))) return rc;
-        }
-        if ((rc = resid(0))) return rc;
-        VecArgs v{nrhs, 0, 0, T, b};
-        const b3t_handle h3[3] = {hrp, hbp, he};
-        if ((rc = submit_impl(c, cnrm, h3, nullptr, 3, &v, sizeof(v)))) return rc;
+        if ((rc = ir_step(c, H, T, b, nrhs, flags, it == 1))) return rc;
         if ((rc = wait_impl(c, 0))) return rc;
         if ((rc = cuda_err(cudaMemcpyAsync(host.data(), eta, (nrhs + 1) * sizeof(double),
                                            cudaMemcpyDeviceToHost, c->stream))) ||
@@ -1126,8 +1413,16 @@ int b3t_ir_solve(b3t_ctx *c, const double *A, double *const *L, const double *B,
 
 int b3t_tiles_unregister(b3t_ctx *c, void *const *tiles, int32_t T) {
     if (!c || !tiles || T <= 0) return -EINVAL;
-    int rc = c->capturing ? -EBUSY : wait_impl(c, 0);
     const int64_t nt = (int64_t)T * (T + 1) / 2;
+    int rc = 0;
+    if (c->st.open) {
+        for (int64_t t = 0; t < nt; ++t) {
+            b3t_handle h;
+            if (tiles[t] && b3t_data_lookup(c, tiles[t], &h) == 0 && stream_handle_busy(c, h)) return -EBUSY;
+        }
+    } else {
+        rc = c->capturing ? -EBUSY : wait_impl(c, 0);
+    }
     for (int64_t t = 0; t < nt; ++t) {
         b3t_handle h;
         if (tiles[t] && b3t_data_lookup(c, tiles[t], &h) == 0) {
