@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-mixed", action="store_true")
     p.add_argument("--nrhs", type=int, default=16)
+    p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--serve-requests", type=int, default=96)
     return p.parse_args()
 
 
@@ -301,6 +303,10 @@ def run_ours(args):
         secondary = run_secondary(ctx, dev, stream)
     if not args.no_mixed:
         secondary["time_to_solution"] = run_time_to_solution(ctx, A0, t, g, N, b, dev, stream, args)
+    if not args.no_serve:
+        del A0, t
+        torch.cuda.empty_cache()
+        secondary["serving"] = run_serving(dev, args)
 
     cpu = None
     if rank == 0 and args.cpu_seconds > 0:
@@ -421,6 +427,30 @@ def run_time_to_solution(ctx, A0, t, g64, N, b, dev, stream, args):
         del Q
     ctx.tiles_unregister(dt.tile_ptrs(W), T)
     ctx.tiles_unregister(dt.tile_ptrs(Lm), T)
+    return out
+
+
+def run_serving(dev, args):
+    """Config 5 (bounded sample): the first requests of the seed-5 stream
+    (Poisson 2000/s, N log-uniform in [256, 8192], 1..32 right-hand sides),
+    served with continuous batching (one resident executor) and, for
+    comparison, one at a time (plain per-request path)."""
+    import torch
+    import paper_1304_0878_b300 as b3t
+    from paper_1304_0878_b300 import serve as sv
+    out = {"workload": "first %d requests of 100k Poisson 2000/s, N log-uniform [256, 8192], "
+                       "1-32 rhs, A = B B^T/N + I per request (seed 5)" % args.serve_requests}
+    for prec in ("fp64", "bf16"):
+        sstream = torch.cuda.Stream(device=dev)
+        ctx = b3t.Context(stream=sstream.cuda_stream, timeout_ns=60_000_000_000)
+        reqs = sv.make_requests(args.serve_requests, 2000.0, 5, prec=prec)
+        cont = sv.serve(ctx, reqs, prec=prec, budget_bytes=64 << 30, max_inflight=48, time_limit=300.0)
+        ctx.close()
+        ctx2 = b3t.Context(stream=torch.cuda.current_stream(dev).cuda_stream, timeout_ns=60_000_000_000)
+        reqs2 = sv.make_requests(args.serve_requests, 2000.0, 5, prec=prec)
+        plain = sv.serve_plain(ctx2, reqs2, prec=prec, time_limit=300.0)
+        ctx2.close()
+        out[prec] = {"continuous": cont, "plain": plain}
     return out
 
 

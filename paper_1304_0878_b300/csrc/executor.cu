@@ -27,7 +27,10 @@
 
 namespace b3t {
 
-constexpr size_t kSmemData = 100 * 1024;   // dynamic shared memory per CTA
+// dynamic shared memory per CTA: tensor-core stages need 96 KB; without them
+// the largest body (FP64 TRSM) needs 75 KB, which leaves room for two CTAs
+constexpr size_t kSmemData = 100 * 1024;
+constexpr size_t kSmemDataNoMx = 76 * 1024;
 
 __device__ __forceinline__ unsigned long long ld_acq(const unsigned long long *p) {
     unsigned long long v;
@@ -424,12 +427,12 @@ __global__ void init_kernel(const InitParams ip, const LaunchParams lp) {
 using namespace b3t;
 
 extern "C" size_t b3t_internal_smem_bytes(int has_mx) {
-    (void)has_mx;
-    return kSmemData + 1024;
+    return (has_mx ? kSmemData : kSmemDataNoMx) + 1024;
 }
 
 extern "C" int b3t_internal_occupancy(int *ctas_per_sm, size_t smem, int *num_sms) {
-    if (cudaFuncSetAttribute(exec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+    if (cudaFuncSetAttribute(exec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kSmemData + 1024)) != cudaSuccess ||
         cudaFuncSetAttribute(exec_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
         return -EIO;
     int dev = 0;

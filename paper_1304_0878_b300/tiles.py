@@ -49,3 +49,33 @@ def q_tiles(T, b, fmt, device):
     """Byte buffer for the quantised panel tiles: (nt, q_bytes) uint8."""
     from ._lib import q_bytes
     return torch.empty((ntiles(T), q_bytes(b, fmt)), dtype=torch.uint8, device=device)
+
+
+_gather_cache = {}
+
+
+def packed_index(T, device):
+    """(rows, cols) index tensors of the packed lower tiles in column order."""
+    key = (T, str(device))
+    if key not in _gather_cache:
+        ii, jj = [], []
+        for j in range(T):
+            for i in range(j, T):
+                ii.append(i)
+                jj.append(j)
+        _gather_cache[key] = (torch.tensor(ii, device=device), torch.tensor(jj, device=device))
+    return _gather_cache[key]
+
+
+def pack_lower(C, b):
+    """Dense (N, N) tensor -> packed lower tiles in one gather (N % b == 0):
+    out[t, c, r] = C[i*b + r, j*b + c] for tile t = (i, j)."""
+    N = C.shape[0]
+    T = N // b
+    v = C.view(T, b, T, b).permute(0, 2, 3, 1)       # [I, J, c, r]
+    ii, jj = packed_index(T, C.device)
+    return v[ii, jj].contiguous()
+
+
+def pad_size(N, b):
+    return (N + b - 1) // b * b

@@ -1,0 +1,59 @@
+"""Serving with continuous batching (GPU): every request completes with an
+FP64-level backward error, and each request's solution computed in the mix
+(stream mode, overlapping with other requests) is bit-for-bit the solution
+of the same request served alone (one request at a time)."""
+import copy
+
+import numpy as np
+import pytest
+import torch
+
+import paper_1304_0878_b300 as b3t
+from paper_1304_0878_b300 import serve as sv
+from paper_1304_0878_b300 import batch as bt
+import synth
+from oracle import cholesky as och
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="no CUDA device")]
+
+
+def requests(n, rate, prec, nmax=1536):
+    return sv.make_requests(n, rate, seed=5, nmin=200, nmax=nmax, rmax=8, prec=prec)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-14), ("bf16", 1e-12)])
+def test_serve_mix_equals_alone(orc, prec, tol):
+    reqs = requests(10, 400.0, prec)
+    side = torch.cuda.Stream()
+    ctx = b3t.Context(stream=side.cuda_stream, timeout_ns=20_000_000_000)
+    st = sv.serve(ctx, reqs, prec=prec, budget_bytes=2 << 30, max_inflight=6, time_limit=120.0,
+                  max_tasks=1 << 20, max_edges=1 << 22, keep_x=True)
+    ctx.close()
+    assert st["requests"] == 10 and st["failed"] == 0
+    assert all(r.eta <= tol for r in reqs)
+    alone = [copy.copy(r) for r in requests(10, 1e9, prec)]     # same requests, served one by one
+    c2 = b3t.Context(stream=torch.cuda.current_stream().cuda_stream, timeout_ns=20_000_000_000)
+    sv.serve_plain(c2, alone, prec=prec, keep_x=True)
+    c2.close()
+    for r, a in zip(reqs, alone):
+        assert r.N == a.N and r.iters == a.iters
+        assert torch.equal(r.x, a.x)
+
+
+def test_batch_uneven_sizes_one_launch(orc):
+    # many uneven factorisations in one launch, tile sizes from the tuner,
+    # ragged sizes padded with identity: each equals its own factorisation
+    sizes = [300, 1000, 513, 2048, 77, 1500]
+    mats = [synth.spd_host(N, seed=N, shift=1.0) for N in sizes]
+    ctx = b3t.Context(stream=torch.cuda.current_stream().cuda_stream, timeout_ns=20_000_000_000)
+    out = bt.cholesky_many(ctx, [torch.from_numpy(A).cuda() for A in mats])
+    ctx.close()
+    for A, (t, N, Np, b) in zip(mats, out):
+        L = np.tril(och.from_tiles(t.cpu().numpy(), Np, b))
+        assert np.array_equal(L[N:, N:], np.eye(Np - N))      # identity padding
+        assert np.all(L[N:, :N] == 0)
+        Lo, info = och.dense_potrf(A)
+        Lo = np.tril(Lo)
+        assert info == 0
+        assert np.max(np.abs(L[:N, :N] - Lo)) / np.max(np.abs(Lo)) <= 1e-12

@@ -18,8 +18,16 @@ pytestmark = [pytest.mark.gpu,
 RW = 3
 
 
+_streams = []
+
+
 def new_ctx(timeout_ns=20_000_000_000):
-    return b3t.Context(stream=torch.cuda.current_stream().cuda_stream, timeout_ns=timeout_ns)
+    # stream mode keeps a kernel resident on the context's stream for the
+    # whole session: give it a stream of its own, so that torch's own work
+    # (allocations, copies) on the current stream does not queue behind it
+    s = torch.cuda.Stream()
+    _streams.append(s)
+    return b3t.Context(stream=s.cuda_stream, timeout_ns=timeout_ns)
 
 
 def wait_batches(ctx, ids, limit_s=60.0):
@@ -37,7 +45,7 @@ def wait_batches(ctx, ids, limit_s=60.0):
 
 
 def factor_alone(A, b):
-    ctx = new_ctx()
+    ctx = b3t.Context(stream=torch.cuda.current_stream().cuda_stream, timeout_ns=20_000_000_000)
     t = torch.from_numpy(och.to_tiles(A, b)).cuda()
     p = dt.tile_ptrs(t)
     ctx.cholesky_submit(p, A.shape[0] // b, b)
