@@ -112,8 +112,31 @@ enum b3t_kind {
     B3T_GEMV_LT = 14,
     B3T_AXPY = 15,
     B3T_RESID = 16,
-    B3T_NRM = 17
+    B3T_NRM = 17,
+    B3T_POTRF_D = 18,
+    B3T_PANEL_TRSM = 19,
+    B3T_PANEL_UPD = 20,
+    B3T_CVT = 21
 };
+
+/* Diagonal tile split into column panels.  A b x b diagonal tile partitioned
+ * (b3t_data_partition, the filters of Section 5.1) into np = b / pw column
+ * panels of b x pw (pw = 64 or 128; panel kk is columns kk*pw.. of the tile,
+ * leading dimension b) is factored by a small DAG instead of one POTRF, so
+ * that several CTAs work on it:
+ *   for kk: POTRF_D(P_kk); PANEL_TRSM(P_kk) (kk < np-1);
+ *           for jj > kk: PANEL_UPD(P_kk, P_jj)
+ *  B3T_POTRF_D     P_kk (RW)       Cholesky of the pw x pw block at row kk*pw
+ *  B3T_PANEL_TRSM  P_kk (RW)       rows below it: X <- X L_d^{-T}
+ *  B3T_PANEL_UPD   P_kk (R), P_jj (RW)
+ *                  P_jj(r, :) -= P_kk(r, :) P_kk(jj*pw.., :)^T for rows
+ *                  r >= jj*pw (lower part on the diagonal block)
+ *  Scalars: struct b3t_panel_args; col0 offsets POTRF info like B3T_POTRF.
+ *  B3T_CVT         W_kk (R, f32 tile), L_kk (W, f64 tile): L = fp64(W) on the
+ *                  lower triangle, 0 above; no scalars. */
+typedef struct b3t_panel_args {
+    int32_t b, pw, kk, jj, col0;
+} b3t_panel_args;
 
 /* Vector kinds (solves and refinement).  A block vector with nrhs <= 32
  * right-hand sides is split into T parts of b rows; part k holds Y_k(r, j) at
@@ -129,7 +152,7 @@ enum b3t_kind {
  *               T parts), B (R, T parts), R_i (W, b3t_ir_work_elems / T
  *               elements): R_i <- B_i - (A X)_i in FP64 with A symmetric and
  *               only its lower tiles stored; after the b*nrhs values, R_i
- *               holds per 32-row item max|r_j|, max|x_j| and the largest
+ *               holds per 64-row item max|r_j|, max|x_j| and the largest
  *               row sum of |A| (flags bit 1: X taken as 0, R_i <- B_i)
  *  B3T_NRM      R (R, all parts), B (R), eta (W, nrhs + 1 f64):
  *               eta_j = max|r_j| / (||A||_inf max|x_j| + max|b_j|),

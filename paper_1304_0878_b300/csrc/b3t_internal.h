@@ -23,7 +23,7 @@ constexpr int kGemmBlk = 64;             // f64 GEMM / SYRK item: 64 x 64 of C
 constexpr int kTrsmRows = 32;            // f64 TRSM item: 32 rows of A_ik
 constexpr int kMxBlk = 128;              // MX GEMM / SYRK item: 128 x 128 of C
 constexpr int kGemvRows = 64;            // GEMV item: 64 rows of the updated part
-constexpr int kResidRows = 32;           // RESID item: 32 rows of the residual part
+constexpr int kResidRows = 64;           // RESID item: 64 rows of the residual part
 constexpr int kMaxRhs = 32;
 
 // Scalar blob of the vector kinds (TRSV / GEMV / AXPY / RESID / NRM).
@@ -36,6 +36,11 @@ struct VecArgs {
 };
 constexpr int32_t kVecF32 = 1, kVecAssign = 2;
 
+struct PanelArgs {
+    int32_t b, pw, kk, jj, col0;
+};
+constexpr int kPanelWidth = 128;          // panel width used by the Cholesky helpers
+
 // Elements of one part of the residual work area: b*nrhs values, then per
 // RESID item the maxima |r_j| and |x_j| and the largest row sum of |A|.
 B3T_HD constexpr int64_t resid_part_elems(int b, int nrhs) {
@@ -46,7 +51,8 @@ enum : int32_t {
     kNoop = 0, kScalF32 = 1, kPotrf = 2, kTrsm = 3, kSyrk = 4, kGemm = 5,
     kPotrfMx = 6, kTrsmMx = 7, kSyrkMx = 8, kGemmMx = 9, kQuant = 10,
     kTrsvL = 11, kGemvL = 12, kTrsvLT = 13, kGemvLT = 14, kAxpy = 15, kResid = 16, kNrm = 17,
-    kNumKinds = 18
+    kPotrfD = 18, kPanelTrsm = 19, kPanelUpd = 20, kCvt = 21,
+    kNumKinds = 22
 };
 
 // One task as the device sees it: 64 bytes.

@@ -109,6 +109,17 @@ __device__ __forceinline__ int potrf_mx_item(const TaskRec &t, double *smem, int
     return potrf_tile(L, b, smem, s_info);
 }
 
+// CVT: L_kk = fp64(W_kk) on the lower triangle, 0 above.
+__device__ __forceinline__ void cvt_item(const TaskRec &t) {
+    const float *Wt = (const float *)t.buf[0];
+    double *L = (double *)t.buf[1];
+    const int b = (int)t.n;
+    for (size_t e = threadIdx.x; e < (size_t)b * b; e += kThreads) {
+        const int r = (int)(e % b), c = (int)(e / b);
+        L[e] = r >= c ? (double)Wt[e] : 0.0;
+    }
+}
+
 // ------------------------------------------------------------- queue
 // Each ready-ring slot names one task and its item count.  Warp 0 claims a
 // work item: one warp-wide scan finds the highest non-empty level; the task
@@ -340,6 +351,14 @@ __global__ void __launch_bounds__(kThreads, 2) exec_kernel(const LaunchParams p)
             break;
         }
         case kTrsmMx: trsm_mx_item(rec, it, (double *)smem); break;
+        case kPotrfD: {
+            const int info = potrf_d_item(rec, (double *)smem, &s_info);
+            if (info) st = rec.aux + info;
+            break;
+        }
+        case kPanelTrsm: panel_trsm_item(rec, it, (double *)smem); break;
+        case kPanelUpd: panel_upd_item(rec, it, (double *)smem); break;
+        case kCvt: cvt_item(rec); break;
         case kQuant: quant_item(rec, s_red, &s_e); break;
         case kSyrkMx:
         case kGemmMx:

@@ -117,11 +117,17 @@ const KindSig kSigs[kNumKinds] = {
     /* AXPY     */ {2, {B3T_RW, B3T_R}, {8, 8}, sizeof(VecArgs), false},
     /* RESID    */ {4, {B3T_R, B3T_R, B3T_R, B3T_W}, {8, 8, 8, 8}, sizeof(VecArgs), false},
     /* NRM      */ {3, {B3T_R, B3T_R, B3T_W}, {8, 8, 8}, sizeof(VecArgs), false},
+    /* POTRF_D  */ {1, {B3T_RW}, {8}, sizeof(PanelArgs), false},
+    /* PANEL_TR */ {1, {B3T_RW}, {8}, sizeof(PanelArgs), false},
+    /* PANEL_UP */ {2, {B3T_R, B3T_RW}, {8, 8}, sizeof(PanelArgs), false},
+    /* CVT      */ {2, {B3T_R, B3T_W}, {4, 8}, 0, true},
 };
 
 const char *kKindNames[kNumKinds] = {"noop", "scal_f32", "potrf", "trsm", "syrk", "gemm",
                                      "potrf_mx", "trsm_mx", "syrk_mx", "gemm_mx", "quant",
-                                     "trsv_l", "gemv_l", "trsv_lt", "gemv_lt", "axpy", "resid", "nrm"};
+                                     "trsv_l", "gemv_l", "trsv_lt", "gemv_lt", "axpy", "resid", "nrm",
+                                     "potrf_d", "panel_trsm", "panel_upd", "cvt"};
+bool is_panel(int kind) { return kind >= kPotrfD && kind <= kPanelUpd; }
 bool is_vec(int kind) { return kind >= kTrsvL && kind <= kNrm; }
 
 bool is_mx(int kind) { return kind == kSyrkMx || kind == kGemmMx; }
@@ -130,7 +136,7 @@ bool has_fmt(int kind) { return kind == kSyrkMx || kind == kGemmMx || kind == kQ
 int64_t items_of(int kind, int64_t n) {
     switch (kind) {
     case kScalF32: return std::max<int64_t>(1, (n + kScalChunk - 1) / kScalChunk);
-    case kPotrf: case kPotrfMx: case kQuant: case kNoop: return 1;
+    case kPotrf: case kPotrfMx: case kQuant: case kNoop: case kCvt: return 1;
     case kTrsm: case kTrsmMx: return n / kTrsmRows;
     case kSyrk: { int64_t m = n / kGemmBlk; return m * (m + 1) / 2; }
     case kGemm: { int64_t m = n / kGemmBlk; return m * m; }
@@ -165,6 +171,7 @@ float cost_of(int kind, int64_t n, int nrhs = 1, int T = 1, bool f32 = false) {
     case kAxpy: return (float)(b * nrhs / 10.0 + 1000.0);
     case kResid: return (float)(2.0 * b * b * T * nrhs / 3.7);
     case kNrm: return 5000.0f;
+    case kCvt: return (float)(12.0 * b * b / 20.0);
     }
     return 1000.0f;
 }
@@ -545,6 +552,35 @@ int submit_impl(b3t_ctx *c, b3t_codelet cl, const b3t_handle *handles, const uin
         }
         r.n = b;
     }
+    float pcost = -1.f;
+    if (is_panel(C.kind)) {
+        PanelArgs a;
+        std::memcpy(&a, scalars, sizeof(a));
+        const int np = a.pw > 0 ? a.b / a.pw : 0;
+        bool ok = (a.pw == 64 || a.pw == 128) && a.b >= a.pw && a.b <= 4096 && a.b % a.pw == 0 &&
+                  a.kk >= 0 && a.kk < np && a.col0 >= 0;
+        if (C.kind == kPanelTrsm) ok = ok && a.kk < np - 1;
+        if (C.kind == kPanelUpd) ok = ok && a.jj > a.kk && a.jj < np;
+        for (int i = 0; ok && i < nbuffers; ++i) {
+            const Handle &H = c->handles[handles[i]];
+            ok = H.elemsize == 8 && H.nelems >= (size_t)a.b * a.pw && r.buf[i] % 16 == 0;
+        }
+        if (!ok) return -EINVAL;
+        r.n = a.b;
+        r.aux = a.col0;
+        r.scal = (uint32_t)a.kk | ((uint32_t)a.jj << 8) | ((uint32_t)a.pw << 16);
+        const double bb = a.b, pw = a.pw;
+        if (C.kind == kPotrfD) { r.nitems = 1; pcost = (float)(pw * pw * pw / 3.0 / 3.7 + 20000.0); }
+        if (C.kind == kPanelTrsm) {
+            r.nitems = (a.b - (a.kk + 1) * a.pw) / kTrsmRows;
+            pcost = (float)(kTrsmRows * pw * pw / 3.7 + 5000.0);
+        }
+        if (C.kind == kPanelUpd) {
+            r.nitems = ((a.b - a.jj * a.pw) / 64) * (a.pw / 64);
+            pcost = (float)(2.0 * 64 * 64 * pw / 3.7 + 5000.0);
+        }
+        (void)bb;
+    }
     int vnrhs = 1, vT = 1;
     bool vf32 = false;
     if (is_vec(C.kind)) {
@@ -582,7 +618,8 @@ int submit_impl(b3t_ctx *c, b3t_codelet cl, const b3t_handle *handles, const uin
         r.scal = (uint32_t)v.T | ((uint32_t)v.nrhs << 16);
         vnrhs = v.nrhs; vT = v.T; vf32 = v.flags & kVecF32;
     }
-    r.nitems = (int32_t)(C.kind == kTrsvL || C.kind == kTrsvLT ? vnrhs : items_of(C.kind, r.n));
+    if (!is_panel(C.kind))
+        r.nitems = (int32_t)(C.kind == kTrsvL || C.kind == kTrsvLT ? vnrhs : items_of(C.kind, r.n));
     const int32_t t = (int32_t)c->tasks.size();
     // expand partitioned parents to their parts; OR the modes of repeats
     std::vector<int32_t> leaves;
@@ -604,7 +641,7 @@ int submit_impl(b3t_ctx *c, b3t_codelet cl, const b3t_handle *handles, const uin
     for (int32_t p : preds) c->edges.emplace_back(p, t);
     Pending P;
     P.rec = r;
-    P.cost = cost_of(C.kind, r.n, vnrhs, vT, vf32);
+    P.cost = pcost >= 0.f ? pcost : cost_of(C.kind, r.n, vnrhs, vT, vf32);
     c->tasks.push_back(P);
     return 0;
 }
@@ -1178,6 +1215,44 @@ static int reg_tiles(b3t_ctx *c, void *const *tiles, int64_t nt, size_t nelems, 
     return 0;
 }
 
+// Partition a diagonal tile handle into b / pw column panels (reuse an
+// existing partition of the same shape).
+static int panel_parts(b3t_ctx *c, b3t_handle h, int32_t b, int32_t pw, std::vector<b3t_handle> &parts) {
+    Handle &H = c->handles[h];
+    const int32_t np = b / pw;
+    if (!H.parts.empty()) {
+        if ((int32_t)H.parts.size() != np || c->handles[H.parts[0]].nelems != (size_t)b * pw) return -EINVAL;
+        parts = H.parts;
+        return 0;
+    }
+    parts.resize(np);
+    return b3t_data_partition(c, h, np, (size_t)b * pw, parts.data());
+}
+
+// POTRF of one diagonal tile as the panel DAG on its partition parts.
+static int submit_panel_potrf(b3t_ctx *c, const std::vector<b3t_handle> &P, int32_t b, int32_t pw,
+                              int32_t col0) {
+    b3t_codelet cd, ct, cu;
+    int rc;
+    if ((rc = kind_codelet(c, kPotrfD, &cd)) || (rc = kind_codelet(c, kPanelTrsm, &ct)) ||
+        (rc = kind_codelet(c, kPanelUpd, &cu)))
+        return rc;
+    const int32_t np = b / pw;
+    for (int32_t kk = 0; kk < np; ++kk) {
+        PanelArgs a{b, pw, kk, 0, col0};
+        if ((rc = submit_impl(c, cd, &P[kk], nullptr, 1, &a, sizeof(a)))) return rc;
+        if (kk < np - 1 && (rc = submit_impl(c, ct, &P[kk], nullptr, 1, &a, sizeof(a)))) return rc;
+        for (int32_t jj = kk + 1; jj < np; ++jj) {
+            PanelArgs u{b, pw, kk, jj, col0};
+            const b3t_handle h2[2] = {P[kk], P[jj]};
+            if ((rc = submit_impl(c, cu, h2, nullptr, 2, &u, sizeof(u)))) return rc;
+        }
+    }
+    return 0;
+}
+
+static bool use_panels(int32_t b) { return b >= 2 * kPanelWidth && b % kPanelWidth == 0; }
+
 int b3t_cholesky_submit(b3t_ctx *c, double *const *tiles, int32_t T, int32_t b, int32_t col0) {
     if (!c || !tiles || T <= 0 || b <= 0 || b % kGemmBlk) return -EINVAL;
     const int64_t nt = (int64_t)T * (T + 1) / 2;
@@ -1188,10 +1263,18 @@ int b3t_cholesky_submit(b3t_ctx *c, double *const *tiles, int32_t T, int32_t b, 
     if ((rc = kind_codelet(c, kPotrf, &cp)) || (rc = kind_codelet(c, kTrsm, &ct)) ||
         (rc = kind_codelet(c, kSyrk, &cs)) || (rc = kind_codelet(c, kGemm, &cg)))
         return rc;
+    const bool panels = use_panels(b);
+    std::vector<std::vector<b3t_handle>> dparts(panels ? T : 0);
+    for (int32_t k = 0; panels && k < T; ++k)
+        if ((rc = panel_parts(c, h[tidx(k, k, T)], b, kPanelWidth, dparts[k]))) return rc;
     for (int32_t k = 0; k < T; ++k) {
         const int32_t c0 = col0 + k * b;
         const b3t_handle hp[1] = {h[tidx(k, k, T)]};
-        if ((rc = submit_impl(c, cp, hp, nullptr, 1, &c0, 4))) return rc;
+        if (panels) {
+            if ((rc = submit_panel_potrf(c, dparts[k], b, kPanelWidth, c0))) return rc;
+        } else if ((rc = submit_impl(c, cp, hp, nullptr, 1, &c0, 4))) {
+            return rc;
+        }
         for (int32_t i = k + 1; i < T; ++i) {
             const b3t_handle ht[2] = {h[tidx(k, k, T)], h[tidx(i, k, T)]};
             if ((rc = submit_impl(c, ct, ht, nullptr, 2, nullptr, 0))) return rc;
@@ -1225,15 +1308,24 @@ int b3t_cholesky_mx_submit(b3t_ctx *c, float *const *W, double *const *L, void *
             if (rc == -ENOENT) rc = b3t_data_register(c, Q[t], q_bytes(b, fmt), 1, b, &hq[t]);
             if (rc) return rc;
         }
-    b3t_codelet cp, ct, cq, cs, cg;
+    b3t_codelet cp, ct, cq, cs, cg, cc;
     if ((rc = kind_codelet(c, kPotrfMx, &cp)) || (rc = kind_codelet(c, kTrsmMx, &ct)) ||
         (rc = kind_codelet(c, kQuant, &cq)) || (rc = kind_codelet(c, kSyrkMx, &cs)) ||
-        (rc = kind_codelet(c, kGemmMx, &cg)))
+        (rc = kind_codelet(c, kGemmMx, &cg)) || (rc = kind_codelet(c, kCvt, &cc)))
         return rc;
+    const bool panels = use_panels(b);
+    std::vector<std::vector<b3t_handle>> dparts(panels ? T : 0);
+    for (int32_t k = 0; panels && k < T; ++k)
+        if ((rc = panel_parts(c, hl[tidx(k, k, T)], b, kPanelWidth, dparts[k]))) return rc;
     for (int32_t k = 0; k < T; ++k) {
         const int32_t c0 = col0 + k * b;
         const b3t_handle hp[2] = {hw[tidx(k, k, T)], hl[tidx(k, k, T)]};
-        if ((rc = submit_impl(c, cp, hp, nullptr, 2, &c0, 4))) return rc;
+        if (panels) {
+            if ((rc = submit_impl(c, cc, hp, nullptr, 2, nullptr, 0))) return rc;
+            if ((rc = submit_panel_potrf(c, dparts[k], b, kPanelWidth, c0))) return rc;
+        } else if ((rc = submit_impl(c, cp, hp, nullptr, 2, &c0, 4))) {
+            return rc;
+        }
         for (int32_t i = k + 1; i < T; ++i) {
             const b3t_handle ht[3] = {hl[tidx(k, k, T)], hw[tidx(i, k, T)], hl[tidx(i, k, T)]};
             if ((rc = submit_impl(c, ct, ht, nullptr, 3, nullptr, 0))) return rc;

@@ -9,7 +9,7 @@
 //   AXPY    : X_i <- X_i + D_i (or X_i = D_i) one item
 //   RESID   : R_i <- B_i - (A X)_i, FP64, with A symmetric and only its lower
 //             tiles stored; also per-item maxima |R|, |X_i| and the largest
-//             row sum of |A| (for the backward error)   item = 32 rows
+//             row sum of |A| (for the backward error)   item = 64 rows
 //   NRM     : eta_j = max|r_j| / (||A||_inf max|x_j| + max|b_j|), one item
 // The solve bodies compute in Tc (double, or float for refinement
 // corrections) and read / write FP64 storage.
@@ -163,10 +163,13 @@ __device__ __forceinline__ void resid_item(const TaskRec &t, int item, unsigned 
     double *Ri = (double *)t.buf[3];
     const int b = (int)t.n, nrhs = vk_nrhs(t), T = vk_T(t), i = vk_i(t);
     const bool xzero = vk_flags(t) & 2;
-    const int tid = threadIdx.x, r = tid & 31, g = tid >> 5, r0 = item * 32, nit = b / 32;
-    double *As = (double *)smem;          // [64][33]
-    double *Xs = As + 64 * 33;            // [nrhs][64]
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    constexpr int RR = kResidRows;          // 64 rows per item
+    const int tid = threadIdx.x, r = tid & (RR - 1), g = tid / RR, r0 = item * RR, nit = b / RR;
+    double *As = (double *)smem;            // [64 columns][65]: As[c*65 + r]
+    double *Xs = As + 64 * 65;              // [nrhs][64]
+    double acc[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) acc[m] = 0.0;
     double rs = 0.0;
     if (!xzero) {
         for (int J = 0; J < T; ++J) {
@@ -176,29 +179,29 @@ __device__ __forceinline__ void resid_item(const TaskRec &t, int item, unsigned 
                     const int c = e & 63, jj = e >> 6;
                     Xs[jj * 64 + c] = X[(size_t)J * b * nrhs + (size_t)jj * b + c0 + c];
                 }
-                for (int e = tid; e < 2048; e += kThreads) {
+                for (int e = tid; e < 64 * RR; e += kThreads) {
                     int rr, c;
                     size_t off;
                     if (J < i) {            // tile (i, J): (r, c) at r + c*b
-                        rr = e & 31; c = e >> 5;
+                        rr = e & 63; c = e >> 6;
                         off = (size_t)(r0 + rr) + (size_t)(c0 + c) * b;
                     } else if (J > i) {     // tile (J, i): A(i.., J..) = tile(c, r)
                         c = e & 63; rr = e >> 6;
                         off = (size_t)(c0 + c) + (size_t)(r0 + rr) * b;
                     } else {                // diagonal tile: lower part, mirrored
-                        rr = e & 31; c = e >> 5;
+                        rr = e & 63; c = e >> 6;
                         const int R = r0 + rr, C = c0 + c;
                         off = R >= C ? (size_t)R + (size_t)C * b : (size_t)C + (size_t)R * b;
                     }
-                    As[c * 33 + rr] = tile[off];
+                    As[c * 65 + rr] = tile[off];
                 }
                 __syncthreads();
-#pragma unroll 4
+#pragma unroll 2
                 for (int c = 0; c < 64; ++c) {
-                    const double a = As[c * 33 + r];
+                    const double a = As[c * 65 + r];
 #pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        const int jj = g + 8 * m;
+                    for (int m = 0; m < 8; ++m) {
+                        const int jj = g + 4 * m;
                         if (jj < nrhs) acc[m] = fma(a, Xs[jj * 64 + c], acc[m]);
                     }
                     rs += fabs(a);
@@ -207,28 +210,36 @@ __device__ __forceinline__ void resid_item(const TaskRec &t, int item, unsigned 
             }
         }
     }
-    double *Rn = Ri + (size_t)b * nrhs;
+    // residual, then per-column maxima of |r| and |x| and the largest |A| row sum
+    double *Ra = As;                        // reuse: [nrhs][64] |r|, then [nrhs][64] |x|
+    double *Xa = As + 64 * kMaxRhs;
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-        const int jj = g + 8 * m;
-        if (jj < nrhs) {   // warp-uniform
+    for (int m = 0; m < 8; ++m) {
+        const int jj = g + 4 * m;
+        if (jj < nrhs) {
             const size_t o = (size_t)jj * b + r0 + r;
             const double v = B[(size_t)i * b * nrhs + o] - acc[m];
             Ri[o] = v;
-            double mr = fabs(v), mx = xzero ? 0.0 : fabs(X[(size_t)i * b * nrhs + o]);
-            for (int s = 16; s; s >>= 1) {
-                mr = fmax(mr, __shfl_xor_sync(0xffffffffu, mr, s));
-                mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, s));
-            }
-            if (r == 0) {
-                Rn[(size_t)item * nrhs + jj] = mr;
-                Rn[(size_t)nit * nrhs + (size_t)item * nrhs + jj] = mx;
-            }
+            Ra[jj * 64 + r] = fabs(v);
+            Xa[jj * 64 + r] = xzero ? 0.0 : fabs(X[(size_t)i * b * nrhs + o]);
         }
     }
-    if (g == 0) {
-        for (int s = 16; s; s >>= 1) rs = fmax(rs, __shfl_xor_sync(0xffffffffu, rs, s));
-        if (r == 0) Rn[(size_t)2 * nit * nrhs + item] = rs;
+    double *Rs = Xa + 64 * kMaxRhs;         // [64] row sums
+    if (g == 0) Rs[r] = rs;
+    __syncthreads();
+    double *Rn = Ri + (size_t)b * nrhs;
+    if (tid < nrhs) {
+        double mr = 0.0, mx = 0.0;
+        for (int k = 0; k < RR; ++k) {
+            mr = fmax(mr, Ra[tid * 64 + k]);
+            mx = fmax(mx, Xa[tid * 64 + k]);
+        }
+        Rn[(size_t)item * nrhs + tid] = mr;
+        Rn[(size_t)nit * nrhs + (size_t)item * nrhs + tid] = mx;
+    } else if (tid == 32) {
+        double m = 0.0;
+        for (int k = 0; k < RR; ++k) m = fmax(m, Rs[k]);
+        Rn[(size_t)2 * nit * nrhs + item] = m;
     }
 }
 
@@ -236,7 +247,7 @@ __device__ __forceinline__ void nrm_item(const TaskRec &t, unsigned char *smem) 
     const double *R = (const double *)t.buf[0];
     const double *B = (const double *)t.buf[1];
     double *eta = (double *)t.buf[2];
-    const int b = (int)t.n, nrhs = vk_nrhs(t), T = vk_T(t), nit = b / 32;
+    const int b = (int)t.n, nrhs = vk_nrhs(t), T = vk_T(t), nit = b / kResidRows;
     const int64_t PR = resid_part_elems(b, nrhs);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double *sm = (double *)smem;          // [4][8][32]: rmax, xmax, bmax, anorm partials

@@ -18,11 +18,13 @@ namespace b3t {
 
 constexpr int kKc = 32;            // K chunk staged in shared memory
 
-// C(crow0.., ccol0..) (64 x 64 block) -= A(arow0.., :) * B(brow0.., :)^T, K = b.
-// lower_only: write only entries with global row >= global column.
+// C(crow0.., ccol0..) (64 x 64 block) -= A(arow0.., 0..K) * B(brow0.., 0..K)^T,
+// all column-major with leading dimension ld.  lower_only: write only the
+// entries with row - lower_shift >= column.
 __device__ __forceinline__ void gemm64_f64(const double *A, int arow0, const double *B, int brow0,
-                                           double *C, int crow0, int ccol0, int b, bool lower_only,
-                                           double *smem) {
+                                           double *C, int crow0, int ccol0, int K, int ld, bool lower_only,
+                                           int lower_shift, double *smem) {
+    const int b = ld;
     double *As = smem;                   // [kKc][64]
     double *Bs = smem + kKc * 64;        // [kKc][64]
     const int tid = threadIdx.x;
@@ -32,7 +34,7 @@ __device__ __forceinline__ void gemm64_f64(const double *A, int arow0, const dou
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-    for (int k0 = 0; k0 < b; k0 += kKc) {
+    for (int k0 = 0; k0 < K; k0 += kKc) {
 #pragma unroll
         for (int q = 0; q < (kKc * 64) / kThreads; ++q) {
             const int e = tid + q * kThreads;
@@ -60,7 +62,7 @@ __device__ __forceinline__ void gemm64_f64(const double *A, int arow0, const dou
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int r = crow0 + tx + 16 * i, c = ccol0 + ty + 16 * j;
-            if (!lower_only || r >= c) {
+            if (!lower_only || r - lower_shift >= c) {
                 double *p = C + (size_t)r + (size_t)c * b;
                 *p = *p - acc[i][j];
             }
@@ -71,7 +73,7 @@ __device__ __forceinline__ void gemm_item(const TaskRec &t, int item, double *sm
     const int b = (int)t.n, m = b / kGemmBlk;
     const int bi = item / m, bj = item % m;
     gemm64_f64((const double *)t.buf[0], bi * 64, (const double *)t.buf[1], bj * 64,
-               (double *)t.buf[2], bi * 64, bj * 64, b, false, smem);
+               (double *)t.buf[2], bi * 64, bj * 64, b, b, false, 0, smem);
 }
 
 // item -> (bi, bj), bi >= bj, enumerating the lower block triangle row by row
@@ -88,15 +90,17 @@ __device__ __forceinline__ void syrk_item(const TaskRec &t, int item, double *sm
     int bi, bj;
     tri_index(item, bi, bj);
     const double *A = (const double *)t.buf[0];
-    gemm64_f64(A, bi * 64, A, bj * 64, (double *)t.buf[1], bi * 64, bj * 64, b, bi == bj, smem);
+    gemm64_f64(A, bi * 64, A, bj * 64, (double *)t.buf[1], bi * 64, bj * 64, b, b, bi == bj, 0, smem);
 }
 
-// X L^T = A for rows [r0, r0 + 32) of a b-wide tile.  Ain is the input
-// (f64, or f32 for the mixed-precision panel), X the f64 output (may alias
-// Ain when Tin is double).  L is the b x b lower factor.
+// X L^T = A for rows [r0, r0 + 32) of an n-wide block (n a multiple of 64).
+// Ain is the input (f64, or f32 for the mixed-precision panel), X the f64
+// output (may alias Ain when Tin is double), L the n x n lower factor; all
+// column-major with leading dimension ld.
 template <typename Tin>
-__device__ __forceinline__ void trsm_rows(const double *L, const Tin *Ain, double *X, int r0, int b,
+__device__ __forceinline__ void trsm_rows(const double *L, const Tin *Ain, double *X, int r0, int n, int ld,
                                           double *smem) {
+    const int b = ld;
     constexpr int RB = kTrsmRows;           // 32 rows
     double *Lcb = smem;                     // [64][65]  Lcb[c*65 + q] = L(c0+c, c0+q)
     double *Acc = Lcb + 64 * 65;            // [64][33]  Acc[c*33 + r]
@@ -104,7 +108,7 @@ __device__ __forceinline__ void trsm_rows(const double *L, const Tin *Ain, doubl
     double *Ls = Xs + kKc * 33;             // [kKc][64] Ls[p*64 + c] = L(c0+c, k0+p)
     const int tid = threadIdx.x;
     const int tr = tid & 31, tw = tid >> 5;     // row, column group
-    for (int c0 = 0; c0 < b; c0 += 64) {
+    for (int c0 = 0; c0 < n; c0 += 64) {
         double acc[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j)
@@ -158,18 +162,19 @@ __device__ __forceinline__ void trsm_rows(const double *L, const Tin *Ain, doubl
 
 __device__ __forceinline__ void trsm_item(const TaskRec &t, int item, double *smem) {
     double *A = (double *)t.buf[1];
-    trsm_rows<double>((const double *)t.buf[0], A, A, item * kTrsmRows, (int)t.n, smem);
+    trsm_rows<double>((const double *)t.buf[0], A, A, item * kTrsmRows, (int)t.n, (int)t.n, smem);
 }
 
 __device__ __forceinline__ void trsm_mx_item(const TaskRec &t, int item, double *smem) {
     trsm_rows<float>((const double *)t.buf[0], (const float *)t.buf[1], (double *)t.buf[2],
-                     item * kTrsmRows, (int)t.n, smem);
+                     item * kTrsmRows, (int)t.n, (int)t.n, smem);
 }
 
-// Cholesky of one b x b tile in place (lower), one CTA, left-looking over
-// panels of 32 columns.  Returns 0 or the 1-based column (within the tile)
-// of the first pivot that is <= 0 or NaN.
-__device__ __forceinline__ int potrf_tile(double *A, int b, double *smem, int *s_info) {
+// Cholesky of one n x n block in place (lower, leading dimension ld), one
+// CTA, left-looking over panels of 32 columns.  Returns 0 or the 1-based
+// column (within the block) of the first pivot that is <= 0 or NaN.
+__device__ __forceinline__ int potrf_block(double *A, int n, int ld, double *smem, int *s_info) {
+    const int b = n;
     constexpr int PW = 32;
     double *Dg = smem;                     // [32][33]  Dg[i*33 + k] = A(jb+i, jb+k)
     double *Lr = Dg + PW * 33;             // [kKc][64] Lr[p*64 + r] = A(rr0+r, k0+p)
@@ -191,13 +196,13 @@ __device__ __forceinline__ int potrf_tile(double *A, int b, double *smem, int *s
                         const int e = tid + q * kThreads;
                         const int r = e & 63, p = e >> 6;
                         const int gr = rr0 + r;
-                        Lr[p * 64 + r] = gr < b ? A[(size_t)gr + (size_t)(k0 + p) * b] : 0.0;
+                        Lr[p * 64 + r] = gr < b ? A[(size_t)gr + (size_t)(k0 + p) * ld] : 0.0;
                     }
 #pragma unroll
                     for (int q = 0; q < (PW * kKc) / kThreads; ++q) {
                         const int e = tid + q * kThreads;
                         const int c = e & 31, p = e >> 5;
-                        Lc[p * 32 + c] = A[(size_t)(jb + c) + (size_t)(k0 + p) * b];
+                        Lc[p * 32 + c] = A[(size_t)(jb + c) + (size_t)(k0 + p) * ld];
                     }
                     __syncthreads();
 #pragma unroll 8
@@ -213,7 +218,7 @@ __device__ __forceinline__ int potrf_tile(double *A, int b, double *smem, int *s
                 for (int j = 0; j < 8; ++j) {
                     const int gc = jb + tc + 4 * j;
                     if (gr < b && gr >= gc) {
-                        double *p = A + (size_t)gr + (size_t)gc * b;
+                        double *p = A + (size_t)gr + (size_t)gc * ld;
                         *p = *p - acc[j];
                     }
                 }
@@ -223,7 +228,7 @@ __device__ __forceinline__ int potrf_tile(double *A, int b, double *smem, int *s
         // (2) factor the 32 x 32 diagonal block in shared memory
         for (int e = tid; e < PW * PW; e += kThreads) {
             const int i = e & 31, k = e >> 5;
-            if (i >= k) Dg[i * 33 + k] = A[(size_t)(jb + i) + (size_t)(jb + k) * b];
+            if (i >= k) Dg[i * 33 + k] = A[(size_t)(jb + i) + (size_t)(jb + k) * ld];
         }
         __syncthreads();
         for (int j = 0; j < PW; ++j) {
@@ -244,13 +249,13 @@ __device__ __forceinline__ int potrf_tile(double *A, int b, double *smem, int *s
         }
         for (int e = tid; e < PW * PW; e += kThreads) {
             const int i = e & 31, k = e >> 5;
-            if (i >= k) A[(size_t)(jb + i) + (size_t)(jb + k) * b] = Dg[i * 33 + k];
+            if (i >= k) A[(size_t)(jb + i) + (size_t)(jb + k) * ld] = Dg[i * 33 + k];
         }
         // (3) rows below the block: X Dg^T = P, one row per thread
         for (int i = jb + PW + tid; i < b; i += kThreads) {
             double x[PW];
 #pragma unroll
-            for (int c = 0; c < PW; ++c) x[c] = A[(size_t)i + (size_t)(jb + c) * b];
+            for (int c = 0; c < PW; ++c) x[c] = A[(size_t)i + (size_t)(jb + c) * ld];
 #pragma unroll
             for (int c = 0; c < PW; ++c) {
                 double s = x[c];
@@ -259,11 +264,49 @@ __device__ __forceinline__ int potrf_tile(double *A, int b, double *smem, int *s
                 x[c] = s / Dg[c * 33 + c];
             }
 #pragma unroll
-            for (int c = 0; c < PW; ++c) A[(size_t)i + (size_t)(jb + c) * b] = x[c];
+            for (int c = 0; c < PW; ++c) A[(size_t)i + (size_t)(jb + c) * ld] = x[c];
         }
         __syncthreads();
     }
     return 0;
+}
+
+__device__ __forceinline__ int potrf_tile(double *A, int b, double *smem, int *s_info) {
+    return potrf_block(A, b, b, smem, s_info);
+}
+
+// ---- diagonal tile split into column panels (partition parts of the tile)
+// record: buf[0] = panel kk (and buf[1] = panel jj for updates), n = b,
+// aux = global column offset of the tile (POTRF info), scal = kk | jj << 8 | pw << 16
+__device__ __forceinline__ int pn_kk(const TaskRec &t) { return (int)(t.scal & 0xff); }
+__device__ __forceinline__ int pn_jj(const TaskRec &t) { return (int)((t.scal >> 8) & 0xff); }
+__device__ __forceinline__ int pn_pw(const TaskRec &t) { return (int)(t.scal >> 16); }
+
+// POTRF of the diagonal block of panel kk (rows kk*pw.., pw x pw)
+__device__ __forceinline__ int potrf_d_item(const TaskRec &t, double *smem, int *s_info) {
+    const int b = (int)t.n, kk = pn_kk(t), pw = pn_pw(t);
+    double *P = (double *)t.buf[0];
+    const int info = potrf_block(P + (size_t)kk * pw, pw, b, smem, s_info);
+    return info ? kk * pw + info : 0;
+}
+
+// rows below the diagonal block of panel kk: X L_d^T = P, 32 rows per item
+__device__ __forceinline__ void panel_trsm_item(const TaskRec &t, int item, double *smem) {
+    const int b = (int)t.n, kk = pn_kk(t), pw = pn_pw(t);
+    double *P = (double *)t.buf[0];
+    trsm_rows<double>(P + (size_t)kk * pw, P, P, (kk + 1) * pw + item * kTrsmRows, pw, b, smem);
+}
+
+// panel jj -= panel kk(rows jj*pw.., :) panel kk(jj*pw..jj*pw+pw, :)^T, rows
+// from jj*pw (lower part on the diagonal block); 64 x 64 blocks per item
+__device__ __forceinline__ void panel_upd_item(const TaskRec &t, int item, double *smem) {
+    const int b = (int)t.n, jj = pn_jj(t), pw = pn_pw(t);
+    const double *Pk = (const double *)t.buf[0];
+    double *Pj = (double *)t.buf[1];
+    const int nc = pw / 64;
+    const int bi = item / nc, bj = item % nc;
+    const int row0 = jj * pw + bi * 64;
+    gemm64_f64(Pk, row0, Pk, jj * pw + bj * 64, Pj, row0, bj * 64, pw, b, bi * 64 < pw, jj * pw, smem);
 }
 
 }  // namespace b3t

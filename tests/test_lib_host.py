@@ -185,3 +185,31 @@ def test_q_bytes():
 def test_strerror():
     assert "unregistered" in b3t.strerror(b3t._lib.ENOENT)
     assert "positive definite" in b3t.strerror(b3t._lib.EDOM)
+
+
+@pytest.mark.parametrize("T,b", [(1, 256), (3, 512), (4, 256)])
+def test_cholesky_panel_dag_edges(ctx, T, b):
+    # b >= 256: each diagonal tile is partitioned into b/128 column panels
+    # and POTRF becomes POTRF_D / PANEL_TRSM / PANEL_UPD tasks on the parts
+    ptrs = [fake_ptr(i) for i in range(och.ntiles(T))]
+    ctx.cholesky_submit(ptrs, T, b)
+    np_ = b // 128
+    parts = {och.tile_index(k, k, T): tuple(("P", k, kk) for kk in range(np_)) for k in range(T)}
+    acc = []
+    for k in range(T):
+        P = parts[och.tile_index(k, k, T)]
+        for kk in range(np_):
+            acc.append([(P[kk], RW)])
+            if kk < np_ - 1:
+                acc.append([(P[kk], RW)])
+            for jj in range(kk + 1, np_):
+                acc.append([(P[kk], R), (P[jj], RW)])
+        for i in range(k + 1, T):
+            acc.append([(och.tile_index(k, k, T), R), (och.tile_index(i, k, T), RW)])
+        for i in range(k + 1, T):
+            acc.append([(och.tile_index(i, k, T), R), (och.tile_index(i, i, T), RW)])
+            for j in range(k + 1, i):
+                acc.append([(och.tile_index(i, k, T), R), (och.tile_index(j, k, T), R),
+                            (och.tile_index(i, j, T), RW)])
+    assert ctx.dag_stats()[0] == len(acc)
+    assert sorted(ctx.dag_edges()) == dag.derive_edges(acc, parts)
