@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--nrhs", type=int, default=16)
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--serve-requests", type=int, default=96)
+    p.add_argument("--case", default=None, choices=["mx_gemm_bf16", "mx_gemm_e4m3", "scal", "resid"],
+                   help="run a DAG of one task kind only (profiling case) and print its timing")
     return p.parse_args()
 
 
@@ -546,9 +548,85 @@ def run_secondary(ctx, dev, stream):
     return out
 
 
+def run_case(args):
+    """Single-kind DAGs sized for a short profiler capture (inputs > L2)."""
+    import torch
+    import synth
+    import paper_1304_0878_b300 as b3t
+    from paper_1304_0878_b300 import tiles as dt
+    import paper_1304_0878_b300.build as pb
+    pb.build()
+    dev = torch.device("cuda", 0)
+    ctx = b3t.Context(stream=torch.cuda.current_stream().cuda_stream, timeout_ns=60_000_000_000)
+    b = 512
+    if args.case.startswith("mx_gemm"):
+        # 64 independent GEMM_MX updates W_i -= Q_a Q_b^T (b = 512): 64 x 2 b^3 flop
+        fmt = b3t.FMT_BF16 if args.case.endswith("bf16") else b3t.FMT_E4M3
+        nW = 64
+        L = torch.randn((8, b, b), dtype=torch.float64, device=dev) * 0.1
+        Q = torch.empty((8, b3t.q_bytes(b, fmt)), dtype=torch.uint8, device=dev)
+        W = torch.randn((nW, b, b), dtype=torch.float32, device=dev)
+        hl = [ctx.data_register(p, b * b, 8, b) for p in dt.tile_ptrs(L)]
+        hq = [ctx.data_register(p, Q.shape[1], 1, b) for p in dt.tile_ptrs(Q)]
+        hw = [ctx.data_register(p, b * b, 4, b) for p in dt.tile_ptrs(W)]
+        cq = ctx.task_decl("quant", b3t.QUANT, [1, 2], 4)
+        for i in range(8):
+            ctx.task_submit(cq, [hl[i], hq[i]], b3t.pack_i32(fmt))
+        ctx.task_wait()
+        cg = ctx.task_decl("gemm_mx", b3t.GEMM_MX, [1, 1, 3], 4)
+        ctx.graph_capture_begin()
+        for i in range(nW):
+            ctx.task_submit(cg, [hq[i % 8], hq[(i * 3 + 1) % 8], hw[i]], b3t.pack_i32(fmt))
+        g = ctx.graph_capture_end()
+        work, unit = nW * 2.0 * b ** 3, "TFLOP/s"
+    elif args.case == "scal":
+        n, nb, nk = 1 << 20, 256, 8
+        x = torch.from_numpy(synth.vector_f32(nb * n, seed=1)).to(dev)
+        hs = [ctx.data_register(x[i * n:(i + 1) * n].data_ptr(), n, 4) for i in range(nb)]
+        cl = ctx.task_decl("scale_vector", b3t.SCAL_F32, [3], 4)
+        ctx.graph_capture_begin()
+        for k in range(nk):
+            for h in hs:
+                ctx.task_submit(cl, [h], b3t.pack_f32(1.0000001))
+        g = ctx.graph_capture_end()
+        work, unit = 8.0 * n * nb * nk, "GB/s"
+    else:  # resid: one refinement residual over N = 16384, 16 rhs (FP64)
+        N, nrhs = 16384, 16
+        T = N // b
+        A = synth.spd_tiles_device(N, b, 3, 0.1, dev)
+        X = torch.randn((T, nrhs, b), dtype=torch.float64, device=dev)
+        B = torch.randn((T, nrhs, b), dtype=torch.float64, device=dev)
+        R = torch.zeros(b3t.ir_work_elems(T, b, nrhs), dtype=torch.float64, device=dev)
+        ha = ctx.data_register(A.data_ptr(), A.numel(), 8)
+        hx = ctx.data_register(X.data_ptr(), X.numel(), 8)
+        hb = ctx.data_register(B.data_ptr(), B.numel(), 8)
+        hr = ctx.data_register(R.data_ptr(), R.numel(), 8)
+        pr = ctx.data_partition(hr, T, R.numel() // T)
+        cr = ctx.task_decl("resid", b3t.RESID, [1, 1, 1, 2], 20)
+        ctx.graph_capture_begin()
+        for i in range(T):
+            ctx.task_submit(cr, [ha, hx, hb, pr[i]], b3t.vec_args(nrhs, 0, i, T, b))
+        g = ctx.graph_capture_end()
+        work, unit = 2.0 * N * N * nrhs, "TFLOP/s"
+    ts = []
+    for r in range(args.warmup + args.steps):
+        ctx.graph_replay(g)
+        ctx.task_wait()
+        if r >= args.warmup:
+            ts.append(ctx.last_launch()["kernel_ns"] / 1e9)
+    med = float(np.median(ts))
+    scale = 1e12 if unit == "TFLOP/s" else 1e9
+    print(json.dumps({"case": args.case, "kernel_ms": med * 1e3, "value": work / med / scale, "unit": unit,
+                      "nctas": ctx.last_launch()["nctas"]}))
+    ctx.graph_destroy(g)
+    ctx.close()
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.case:
+        run_case(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)

@@ -369,7 +369,10 @@ B3T_API int b3t_ir_solve(b3t_ctx *ctx, const double *A_packed, double *const *L,
  * through a separate feed stream and published with a counter: the tasks of
  * the new batch join the ready queue while earlier batches are still running,
  * so their work overlaps on the device.  Capacities are fixed at open
- * (-ENOMEM beyond).  A batch may not name a buffer that an unfinished batch
+ * (-ENOMEM beyond; a batch whose upload exceeds 64 MiB: -E2BIG).  While the
+ * stream is open the caller must not make calls that synchronise the whole
+ * device (cudaDeviceSynchronize, cudaFree, cudaFreeHost, ...): they would wait
+ * for the resident kernel.  A batch may not name a buffer that an unfinished batch
  * uses (-EBUSY; the tasks stay pending).  The kernel exits after
  * b3t_stream_close once everything published has retired, or at deadline_ns
  * after open (-ETIMEDOUT).  While the stream is open, flush / wait / replay

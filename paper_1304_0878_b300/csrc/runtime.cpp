@@ -983,6 +983,8 @@ int b3t_debug_block_task(b3t_ctx *c, int64_t t) {
 
 // ------------------------------------------------------------- stream mode
 
+constexpr size_t kStreamStaging = (size_t)64 << 20;   // pinned upload buffer of a stream
+
 static void stream_free(b3t_ctx *c) {
     auto &S = c->st;
     cudaFree(S.tasks); cudaFree(S.succ); cudaFree(S.level); cudaFree(S.counters); cudaFree(S.done);
@@ -1018,8 +1020,10 @@ int b3t_stream_open(b3t_ctx *c, int64_t max_tasks, int64_t max_edges, int32_t ma
               cudaHostAlloc((void **)&S.done_h, (size_t)max_batches * 4, cudaHostAllocMapped) == cudaSuccess &&
               cudaHostGetDevicePointer((void **)&S.done_d, S.done_h, 0) == cudaSuccess &&
               cudaStreamCreateWithFlags(&S.feed, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaEventCreateWithFlags(&S.staged, cudaEventDisableTiming) == cudaSuccess;
+              cudaEventCreateWithFlags(&S.staged, cudaEventDisableTiming) == cudaSuccess &&
+              cudaMallocHost(&S.staging, kStreamStaging) == cudaSuccess;
     if (!ok) { cudaGetLastError(); stream_free(c); return -ENOMEM; }
+    S.staging_cap = kStreamStaging;
     S.max_tasks = max_tasks; S.max_edges = (int64_t)ne; S.max_batches = max_batches;
     std::memset(S.done_h, 0, (size_t)max_batches * 4);
     cudaMemsetAsync(S.slots, 0xff, (size_t)L * nt * 8, c->stream);
@@ -1093,14 +1097,11 @@ int b3t_stream_submit(b3t_ctx *c, int32_t *batch_id) {
     const size_t o_t = 0, o_s = o_t + nt * sizeof(TaskRec), o_l = o_s + ne * 4, o_i = o_l + nt * 4,
                  o_z = o_i + nt * 4, o_b = o_z + nt * 4, o_r = (o_b + nt * 4 + 15) / 16 * 16,
                  o_m = o_r + nr * 8, bytes = o_m + 64;
+    // the staging buffer is fixed for the life of the stream: freeing pinned
+    // memory implies a device-wide synchronisation, which would wait for the
+    // resident kernel itself
+    if (bytes > S.staging_cap) return -E2BIG;
     cudaEventSynchronize(S.staged);
-    if (bytes > S.staging_cap) {
-        if (S.staging) cudaFreeHost(S.staging);
-        S.staging = nullptr;
-        S.staging_cap = 0;
-        if (cudaMallocHost(&S.staging, std::max(bytes, (size_t)1 << 20)) != cudaSuccess) return -ENOMEM;
-        S.staging_cap = std::max(bytes, (size_t)1 << 20);
-    }
     char *sp = (char *)S.staging;
     for (int64_t t = 0; t < nt; ++t) std::memcpy(sp + o_t + t * sizeof(TaskRec), &c->tasks[t].rec, sizeof(TaskRec));
     if (ne) std::memcpy(sp + o_s, succ.data(), ne * 4);
@@ -1165,16 +1166,12 @@ int b3t_stream_query(b3t_ctx *c, int32_t batch, int32_t *info) {
 int b3t_stream_close(b3t_ctx *c) {
     if (!c || !c->st.open) return -EINVAL;
     auto &S = c->st;
-    static const unsigned long long one = 1;
-    unsigned long long *stopflag = nullptr;
     int rc = 0;
-    if (cudaMallocHost(&stopflag, 8) == cudaSuccess) {
-        *stopflag = one;
-        cudaMemcpyAsync(&S.sctl->stop, stopflag, 8, cudaMemcpyHostToDevice, S.feed);
-        cudaStreamSynchronize(S.feed);
-    } else {
-        rc = -ENOMEM;
-    }
+    cudaEventSynchronize(S.staged);
+    unsigned long long *stopflag = (unsigned long long *)S.staging;
+    *stopflag = 1;
+    cudaMemcpyAsync(&S.sctl->stop, stopflag, 8, cudaMemcpyHostToDevice, S.feed);
+    cudaStreamSynchronize(S.feed);
     const int rs = cuda_err(cudaStreamSynchronize(c->stream));
     Ctl h;
     std::memset(&h, 0, sizeof(h));
@@ -1183,7 +1180,6 @@ int b3t_stream_close(b3t_ctx *c) {
         c->err_info = h.err_info;
         if (!rc) rc = -h.error;
     }
-    if (stopflag) cudaFreeHost(stopflag);
     stream_free(c);
     return rc ? rc : rs;
 }

@@ -176,13 +176,14 @@ def serve(ctx, reqs, prec="fp64", budget_bytes=48 << 30, max_inflight=64, tol=1e
     (generation and read-backs use other streams)."""
     gen_stream = torch.cuda.Stream(device=device)
     side = torch.cuda.Stream(device=device)
+    host = torch.empty(64, dtype=torch.float64, pin_memory=True)
     nb = sum(1 for _ in reqs) * (max_iter + 1) + 16
+    # from here until stream_close nothing may synchronise the whole device
     ctx.stream_open(max_tasks, max_edges, nb, int(time_limit * 1e9))
     pending = list(reqs)            # not yet arrived (arrival order)
     queue, gen, run, done = [], [], [], []
     used = 0
     t0 = time.perf_counter()
-    host = torch.empty(64, dtype=torch.float64, pin_memory=True)
     pi = 0
     try:
         while len(done) < len(reqs):
