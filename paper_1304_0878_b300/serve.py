@@ -168,6 +168,29 @@ def _stats(reqs, t_first, t_last, prec, mode):
     }
 
 
+def warm_up(prec, device, gen_stream, side, host, reserve_bytes):
+    """Initialise, before the resident kernel starts, everything that is set up
+    lazily on first use and may synchronise the whole device: cuBLAS handles
+    and workspaces of the generation stream, the random generator, and the
+    caching allocator's pools (one large reservation, freed into torch's
+    cache so that later allocations on that stream reuse it)."""
+    r = Request(-1, 0.0, 300, 2, 1)
+    r.b = tune.choose_tile(r.N, prec)
+    r.Np = dt.pad_size(r.N, r.b)
+    r.T = r.Np // r.b
+    generate(r, prec, device, gen_stream)
+    gen_stream.synchronize()
+    with torch.cuda.stream(side):
+        host[:3].copy_(r.bufs["eta"][:3], non_blocking=True)
+    side.synchronize()
+    with torch.cuda.stream(gen_stream):
+        free = torch.cuda.mem_get_info(device)[0]
+        pool = torch.empty(int(min(reserve_bytes, 0.8 * free)), dtype=torch.uint8, device=device)
+        del pool
+    r.bufs = None
+    torch.cuda.synchronize(device)
+
+
 def serve(ctx, reqs, prec="fp64", budget_bytes=48 << 30, max_inflight=64, tol=1e-12, max_iter=30,
           device="cuda", time_limit=600.0, max_tasks=1 << 22, max_edges=1 << 24, keep_x=False):
     """Continuous batching with the resident executor.  Arrival times in
@@ -177,6 +200,7 @@ def serve(ctx, reqs, prec="fp64", budget_bytes=48 << 30, max_inflight=64, tol=1e
     gen_stream = torch.cuda.Stream(device=device)
     side = torch.cuda.Stream(device=device)
     host = torch.empty(64, dtype=torch.float64, pin_memory=True)
+    warm_up(prec, device, gen_stream, side, host, budget_bytes)
     nb = sum(1 for _ in reqs) * (max_iter + 1) + 16
     # from here until stream_close nothing may synchronise the whole device
     ctx.stream_open(max_tasks, max_edges, nb, int(time_limit * 1e9))
