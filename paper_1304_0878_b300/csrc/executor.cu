@@ -96,88 +96,6 @@ __device__ __forceinline__ void scal_item(const TaskRec &t, int item) {
     }
 }
 
-// SCAL through bulk copies: 16 KiB chunks of the item stream through a ring of
-// kScalStages shared-memory stages (cp.async.bulk global -> shared, multiply
-// in place, cp.async.bulk shared -> global).  Thread 0 issues the copies; the
-// ring keeps up to kScalStages - 1 loads in flight while a chunk is scaled
-// and stored.  Ragged tails (< 4 floats) are handled with plain loads.
-constexpr int kScalStages = 4;
-constexpr uint32_t kScalChunkBytes = 16384;
-
-struct ScalRing {
-    uint64_t *full;        // [kScalStages] mbarriers
-    unsigned char *stage;  // kScalStages x 16 KiB
-    uint32_t fills;        // chunks loaded so far by this CTA (all threads keep a copy)
-};
-
-__device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t bytes) {
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
-                 "r"(smem_u32(src)), "r"(bytes)
-                 : "memory");
-    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-}
-
-__device__ __forceinline__ int scal_item_bulk(const TaskRec &t, int item, ScalRing &ring, int64_t limit_ns) {
-    float *x = (float *)t.buf[0];
-    const float f = __uint_as_float(t.scal);
-    const int64_t start = (int64_t)item * kScalChunk;
-    const int64_t end = min(t.n, start + kScalChunk);
-    const int64_t nvec = (end - start) & ~(int64_t)3;          // floats moved by bulk copies
-    const uint32_t bytes = (uint32_t)(nvec * 4);
-    const int nch = (int)((bytes + kScalChunkBytes - 1) / kScalChunkBytes);
-    const int tid = threadIdx.x;
-    char *gx = (char *)(x + start);
-    const uint32_t G = ring.fills;
-    __shared__ int s_bad;
-    if (tid == 0) {
-        s_bad = 0;
-        asm volatile("fence.proxy.async.global;" ::: "memory");
-        for (int c = 0; c < nch && c < kScalStages; ++c) {
-            const uint32_t s = (G + c) % kScalStages;
-            const uint32_t nb = min(kScalChunkBytes, bytes - (uint32_t)c * kScalChunkBytes);
-            mbar_expect_tx(&ring.full[s], nb);
-            bulk_g2s(ring.stage + s * kScalChunkBytes, gx + (size_t)c * kScalChunkBytes, nb, &ring.full[s]);
-        }
-    }
-    for (int c = 0; c < nch; ++c) {
-        const uint32_t g = G + c, s = g % kScalStages;
-        const uint32_t nb = min(kScalChunkBytes, bytes - (uint32_t)c * kScalChunkBytes);
-        if (!mbar_wait(&ring.full[s], (g / kScalStages) & 1, limit_ns)) s_bad = 1;
-        float4 *v = reinterpret_cast<float4 *>(ring.stage + s * kScalChunkBytes);
-        for (uint32_t i = tid; i < nb / 16; i += kThreads) {
-            float4 a = v[i];
-            a.x = __fmul_rn(a.x, f); a.y = __fmul_rn(a.y, f);
-            a.z = __fmul_rn(a.z, f); a.w = __fmul_rn(a.w, f);
-            v[i] = a;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            bulk_s2g(gx + (size_t)c * kScalChunkBytes, ring.stage + s * kScalChunkBytes, nb);
-            if (c + kScalStages < nch) {
-                // the stage is refilled once this store has read it
-                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-                const uint32_t nb2 = min(kScalChunkBytes, bytes - (uint32_t)(c + kScalStages) * kScalChunkBytes);
-                mbar_expect_tx(&ring.full[s], nb2);
-                bulk_g2s(ring.stage + s * kScalChunkBytes, gx + (size_t)(c + kScalStages) * kScalChunkBytes, nb2,
-                         &ring.full[s]);
-            }
-        }
-    }
-    ring.fills = G + nch;
-    const int64_t tail = (end - start) - nvec;
-    if (tid < tail) {
-        float *p = x + start + nvec + tid;
-        *p = __fmul_rn(*p, f);
-    }
-    if (tid == 0) {
-        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-        asm volatile("fence.proxy.async.global;" ::: "memory");
-    }
-    __syncthreads();
-    return s_bad ? ETIMEDOUT : 0;
-}
-
 // POTRF_MX: L_kk = chol(fp64(W_kk)), strict upper part of L_kk zeroed.
 __device__ __forceinline__ int potrf_mx_item(const TaskRec &t, double *smem, int *s_info) {
     const float *Wt = (const float *)t.buf[0];
@@ -376,7 +294,6 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
     __shared__ unsigned long long s_item;
     __shared__ int s_flag, s_info, s_fail, s_e;
     __shared__ __align__(8) uint64_t s_bars[2 * kMxStages + 1];
-    __shared__ __align__(8) uint64_t s_sbars[kScalStages];
     __shared__ uint32_t s_tmem;
     __shared__ double s_red[kThreads / 32];
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -389,15 +306,6 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
     mx.fills = 0;
     mx.items = 0;
     mx.tmem = 0;
-    ScalRing ring;
-    ring.full = s_sbars;
-    ring.stage = smem;
-    ring.fills = 0;
-    if (tid == 0) {
-        for (int i = 0; i < kScalStages; ++i) mbar_init(&s_sbars[i], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
     if (p.has_mx) {
         if (tid == 0) {
             for (int i = 0; i < 2 * kMxStages + 1; ++i) mbar_init(&s_bars[i], 1);
@@ -430,9 +338,7 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
         const TaskRec rec = p.tasks[t];
         int st = 0;
         switch (rec.kind) {
-        case kScalF32:
-            if (scal_item_bulk(rec, it, ring, p.timeout_ns)) st = -ETIMEDOUT;
-            break;
+        case kScalF32: scal_item(rec, it); break;
         case kPotrf: {
             const int info = potrf_tile((double *)rec.buf[0], (int)rec.n, (double *)smem, &s_info);
             if (info) st = rec.aux + info;
