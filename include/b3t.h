@@ -188,7 +188,9 @@ typedef struct b3t_config {
                                Section 5.3); B3T_PRIO_DEPTH (1): deepest task
                                first, so a successor runs right after its
                                predecessor while the data is in L2 */
-    int32_t reserved[1];
+    int32_t stream_free_sms; /* stream mode: SMs the resident kernel leaves
+                               free for other work issued meanwhile (input
+                               generation, copies); 0 = 8 */
 } b3t_config;
 
 enum { B3T_PRIO_UPWARD = 0, B3T_PRIO_DEPTH = 1 };
@@ -372,7 +374,8 @@ B3T_API int b3t_ir_solve(b3t_ctx *ctx, const double *A_packed, double *const *L,
  * (-ENOMEM beyond; a batch whose upload exceeds 64 MiB: -E2BIG).  While the
  * stream is open the caller must not make calls that synchronise the whole
  * device (cudaDeviceSynchronize, cudaFree, cudaFreeHost, ...): they would wait
- * for the resident kernel.  A batch may not name a buffer that an unfinished batch
+ * for the resident kernel.  The resident kernel leaves stream_free_sms SMs
+ * (b3t_config) free so that other kernels issued meanwhile can run.  A batch may not name a buffer that an unfinished batch
  * uses (-EBUSY; the tasks stay pending).  The kernel exits after
  * b3t_stream_close once everything published has retired, or at deadline_ns
  * after open (-ETIMEDOUT).  While the stream is open, flush / wait / replay

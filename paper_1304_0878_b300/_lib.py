@@ -35,7 +35,7 @@ class Config(ctypes.Structure):
     _fields_ = [("timeout_ns", ctypes.c_int64), ("ctas_per_sm", ctypes.c_int32),
                 ("prio_levels", ctypes.c_int32), ("debug_checks", ctypes.c_int32),
                 ("host_only", ctypes.c_int32), ("prio_policy", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 1)]
+                ("stream_free_sms", ctypes.c_int32)]
 
 
 _lib = None

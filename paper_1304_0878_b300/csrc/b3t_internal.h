@@ -158,7 +158,7 @@ B3T_HD inline unsigned long long pack_slot(int64_t task, int32_t nitems) {
 extern "C" {
 int b3t_internal_launch(const b3t::InitParams *ip, const b3t::LaunchParams *lp,
                         int nctas, size_t smem, void *stream, void *ev_start, void *ev_stop);
-int b3t_internal_occupancy(int *ctas_per_sm, size_t smem, int *num_sms);
+int b3t_internal_occupancy(int *ctas_per_sm, size_t smem, int *num_sms, int has_mx);
 int b3t_internal_launch_exec(const b3t::LaunchParams *lp, int nctas, size_t smem, void *stream, void *ev_start);
 size_t b3t_internal_smem_bytes(int has_mx);
 }

@@ -285,8 +285,12 @@ __device__ __forceinline__ void retire(const LaunchParams &p, int64_t t, const T
     }
 }
 
-// 120 registers (not 128) so that two 256-thread CTAs fit the register file of
-// an SM together with their shared memory.
+// Two variants: kMx = true carries the tcgen05 tensor-memory path (launches
+// with SYRK_MX / GEMM_MX tasks, and stream mode); a kernel that allocates
+// tensor memory runs one CTA per SM.  kMx = false leaves it out, so that two
+// CTAs per SM fit (120 registers keep two 256-thread CTAs in the register
+// file).
+template <bool kMx>
 __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
     extern __shared__ __align__(1024) unsigned char dsmem[];
     // align the dynamic area to 1024 bytes (128-byte swizzled operands)
@@ -306,7 +310,7 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
     mx.fills = 0;
     mx.items = 0;
     mx.tmem = 0;
-    if (p.has_mx) {
+    if (kMx && p.has_mx) {
         if (tid == 0) {
             for (int i = 0; i < 2 * kMxStages + 1; ++i) mbar_init(&s_bars[i], 1);
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -364,8 +368,12 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
         case kQuant: quant_item(rec, s_red, &s_e); break;
         case kSyrkMx:
         case kGemmMx:
-            if (!p.has_mx) { st = -EPROTO; break; }
-            if (mx_update_item(rec, it, rec.kind == kSyrkMx, mx, p.timeout_ns, &s_fail)) st = -ETIMEDOUT;
+            if constexpr (kMx) {
+                if (!p.has_mx) { st = -EPROTO; break; }
+                if (mx_update_item(rec, it, rec.kind == kSyrkMx, mx, p.timeout_ns, &s_fail)) st = -ETIMEDOUT;
+            } else {
+                st = -EPROTO;
+            }
             break;
         case kTrsvL:
             if (vk_flags(rec) & kVecF32) trsv_l_item<float>(rec, it, smem);
@@ -412,7 +420,7 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
         if (s_flag && warp == 0) retire(p, t, rec);
     }
 
-    if (p.has_mx) {
+    if (kMx && p.has_mx) {
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
@@ -451,17 +459,24 @@ extern "C" size_t b3t_internal_smem_bytes(int has_mx) {
     return (has_mx ? kSmemData : kSmemDataNoMx) + 1024;
 }
 
-extern "C" int b3t_internal_occupancy(int *ctas_per_sm, size_t smem, int *num_sms) {
-    if (cudaFuncSetAttribute(exec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <bool kMx>
+static int occupancy_of(int *ctas_per_sm, size_t smem) {
+    if (cudaFuncSetAttribute(exec_kernel<kMx>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kSmemData + 1024)) != cudaSuccess ||
-        cudaFuncSetAttribute(exec_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
+        cudaFuncSetAttribute(exec_kernel<kMx>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) !=
+            cudaSuccess)
         return -EIO;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, exec_kernel<kMx>, kThreads, smem) ==
+                   cudaSuccess
+               ? 0
+               : -EIO;
+}
+
+extern "C" int b3t_internal_occupancy(int *ctas_per_sm, size_t smem, int *num_sms, int has_mx) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -EIO;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, exec_kernel, kThreads, smem) != cudaSuccess)
-        return -EIO;
-    return 0;
+    return has_mx ? occupancy_of<true>(ctas_per_sm, smem) : occupancy_of<false>(ctas_per_sm, smem);
 }
 
 extern "C" int b3t_internal_launch(const InitParams *ip, const LaunchParams *lp, int nctas, size_t smem,
@@ -472,7 +487,8 @@ extern "C" int b3t_internal_launch(const InitParams *ip, const LaunchParams *lp,
     ib = ib < 1 ? 1 : (ib > 4096 ? 4096 : ib);
     init_kernel<<<ib, 256, 0, s>>>(*ip, *lp);
     if (ev_start) cudaEventRecord((cudaEvent_t)ev_start, s);
-    exec_kernel<<<nctas, kThreads, smem, s>>>(*lp);
+    if (lp->has_mx) exec_kernel<true><<<nctas, kThreads, smem, s>>>(*lp);
+    else exec_kernel<false><<<nctas, kThreads, smem, s>>>(*lp);
     if (ev_stop) cudaEventRecord((cudaEvent_t)ev_stop, s);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? 0 : -EIO;
@@ -482,6 +498,7 @@ extern "C" int b3t_internal_launch_exec(const LaunchParams *lp, int nctas, size_
                                         void *ev_start) {
     cudaStream_t s = (cudaStream_t)stream;
     if (ev_start) cudaEventRecord((cudaEvent_t)ev_start, s);
-    exec_kernel<<<nctas, kThreads, smem, s>>>(*lp);
+    if (lp->has_mx) exec_kernel<true><<<nctas, kThreads, smem, s>>>(*lp);
+    else exec_kernel<false><<<nctas, kThreads, smem, s>>>(*lp);
     return cudaGetLastError() == cudaSuccess ? 0 : -EIO;
 }

@@ -405,10 +405,10 @@ int build_launch(b3t_ctx *c, Arena &a, InitParams &ip, LaunchParams &lp, int64_t
     return 0;
 }
 
-int grid_for(b3t_ctx *c, bool has_mx, int *nctas, size_t *smem) {
+int grid_for(b3t_ctx *c, bool has_mx, int *nctas, size_t *smem, int free_sms = 0) {
     *smem = b3t_internal_smem_bytes(has_mx ? 1 : 0);
     int per_sm = 0, sms = 0;
-    int rc = b3t_internal_occupancy(&per_sm, *smem, &sms);
+    int rc = b3t_internal_occupancy(&per_sm, *smem, &sms, has_mx ? 1 : 0);
     if (rc) return rc;
     if (c->cfg.ctas_per_sm > 0) per_sm = std::min(per_sm, c->cfg.ctas_per_sm);
     // B3T_CTAS_PER_SM overrides the occupancy query (1..4).  Claims never
@@ -419,7 +419,7 @@ int grid_for(b3t_ctx *c, bool has_mx, int *nctas, size_t *smem) {
         if (v >= 1 && v <= 4) per_sm = v;
     }
     if (per_sm < 1) return -EINVAL;
-    *nctas = per_sm * sms;
+    *nctas = per_sm * std::max(1, sms - free_sms);
     return 0;
 }
 
@@ -984,6 +984,7 @@ int b3t_debug_block_task(b3t_ctx *c, int64_t t) {
 // ------------------------------------------------------------- stream mode
 
 constexpr size_t kStreamStaging = (size_t)64 << 20;   // pinned upload buffer of a stream
+constexpr int kStreamFreeSms = 8;                      // SMs a resident stream kernel leaves free
 
 static void stream_free(b3t_ctx *c) {
     auto &S = c->st;
@@ -1041,8 +1042,12 @@ int b3t_stream_open(b3t_ctx *c, int64_t max_tasks, int64_t max_edges, int32_t ma
     lp.sctl = S.sctl; lp.subs = S.subs; lp.sroots = S.sroots; lp.task_batch = S.task_batch;
     lp.batch_left = S.batch_left; lp.batch_info = S.batch_info; lp.batch_done = S.done_d;
     lp.deadline_ns = deadline_ns;
+    // leave SMs free for work issued while the kernel is resident (input
+    // generation, copies): a kernel that needs a whole SM's shared memory
+    // could not start otherwise, and whoever waits for it would stall
+    const int free_sms = c->cfg.stream_free_sms > 0 ? c->cfg.stream_free_sms : kStreamFreeSms;
     int nctas; size_t smem;
-    if ((rc = grid_for(c, true, &nctas, &smem))) { stream_free(c); return rc; }
+    if ((rc = grid_for(c, true, &nctas, &smem, free_sms))) { stream_free(c); return rc; }
     if ((rc = b3t_internal_launch_exec(&lp, nctas, smem, c->stream, c->ev0))) { stream_free(c); return rc; }
     S.open = true;
     c->last_nctas = nctas;
