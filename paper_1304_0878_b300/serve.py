@@ -17,6 +17,12 @@ measured from arrival to the completion of the last stage.
 
 `serve_plain` is the per-request path for comparison: one request at a time,
 one launch per stage, no overlap.
+
+Request inputs (the matrix and right-hand sides, as a client would send
+them) are built on the device before serving starts (`prepare`, timed
+separately): that step uses library GEMMs, which may be persistent kernels
+that need the whole GPU and so cannot run next to the resident executor.
+Admission then only allocates the working buffers and copies into them.
 """
 import math
 import time
@@ -45,7 +51,8 @@ def footprint(Np, nrhs, b, prec):
 
 class Request:
     __slots__ = ("rid", "arrival", "N", "nrhs", "seed", "b", "Np", "T", "state", "bufs", "ptrs",
-                 "batch", "gen_ev", "t_admit", "t_ready", "t_done", "iters", "eta", "info", "bytes", "x")
+                 "batch", "gen_ev", "t_admit", "t_ready", "t_done", "iters", "eta", "info", "bytes", "x",
+                 "inputs")
 
     def __init__(self, rid, arrival, N, nrhs, seed):
         self.rid, self.arrival, self.N, self.nrhs, self.seed = rid, arrival, int(N), int(nrhs), int(seed)
@@ -56,11 +63,13 @@ class Request:
         self.batch = -1
 
 
-def generate(req, prec, device, stream):
-    """Build request `req` on the device (on `stream`): A = B B^T / N + I with
-    B ~ N(0, 1) binary32 from torch's CUDA generator seeded with req.seed,
-    padded to diag(A, I), packed lower FP64 tiles; rhs N(0, 1) in parts."""
-    import paper_1304_0878_b300 as b3t
+def make_inputs(req, device, stream):
+    """Request inputs on the device: A = B B^T / N + I with B ~ N(0, 1)
+    binary32 from torch's CUDA generator seeded with req.seed (binary32
+    product, TF32 off), padded to diag(A, I), as packed lower FP64 tiles; the
+    right-hand sides N(0, 1) as T parts of b x nrhs.  Built before serving
+    starts: library GEMMs may be persistent kernels that need the whole GPU,
+    so they must not run next to the resident executor."""
     N, b, Np, T, nrhs = req.N, req.b, req.Np, req.T, req.nrhs
     with torch.cuda.stream(stream):
         g = torch.Generator(device=device)
@@ -81,6 +90,17 @@ def generate(req, prec, device, stream):
         flat = torch.zeros((nrhs, Np), dtype=torch.float64, device=device)
         flat[:, :N] = rv
         rhs = flat.view(nrhs, T, b).permute(1, 0, 2).contiguous()     # T parts of b x nrhs
+        del B, C
+    req.inputs = (A, rhs)
+
+
+def generate(req, prec, device, stream):
+    """Admission: the request's working buffers, filled from its inputs with
+    elementwise copies on `stream` (safe next to the resident executor)."""
+    import paper_1304_0878_b300 as b3t
+    T, b, nrhs = req.T, req.b, req.nrhs
+    A, rhs = req.inputs
+    with torch.cuda.stream(stream):
         X = torch.zeros_like(rhs)
         R = torch.zeros(b3t.ir_work_elems(T, b, nrhs), dtype=torch.float64, device=device)
         eta = torch.zeros(nrhs + 1, dtype=torch.float64, device=device)
@@ -92,12 +112,21 @@ def generate(req, prec, device, stream):
             bufs["W"] = A.float()
             bufs["L"] = torch.empty_like(A)
             bufs["Q"] = dt.q_tiles(T, b, fmt, device)
-        del B, C
         ev = torch.cuda.Event()
         ev.record(stream)
     req.bufs = bufs
     req.gen_ev = ev
     req.ptrs = {k: dt.tile_ptrs(v) for k, v in bufs.items() if k in ("F", "W", "L", "Q")}
+
+
+def prepare(reqs, device="cuda"):
+    """Build every request's inputs (before serving); returns seconds."""
+    t0 = time.perf_counter()
+    s = torch.cuda.current_stream(device)
+    for r in reqs:
+        make_inputs(r, device, s)
+    torch.cuda.synchronize(device)
+    return time.perf_counter() - t0
 
 
 def submit_stage(ctx, req, prec, first, tol):
@@ -136,6 +165,7 @@ def release(ctx, req, keep_x=False, stream=None):
             pass
     req.bufs = None
     req.ptrs = None
+    req.inputs = None
 
 
 def make_requests(n, rate, seed, nmin=256, nmax=8192, rmax=32, prec="fp64"):
@@ -178,6 +208,7 @@ def warm_up(prec, device, gen_stream, side, host, reserve_bytes):
     r.b = tune.choose_tile(r.N, prec)
     r.Np = dt.pad_size(r.N, r.b)
     r.T = r.Np // r.b
+    make_inputs(r, device, gen_stream)
     generate(r, prec, device, gen_stream)
     gen_stream.synchronize()
     with torch.cuda.stream(side):
@@ -194,9 +225,10 @@ def warm_up(prec, device, gen_stream, side, host, reserve_bytes):
 def serve(ctx, reqs, prec="fp64", budget_bytes=48 << 30, max_inflight=64, tol=1e-12, max_iter=30,
           device="cuda", time_limit=600.0, max_tasks=1 << 22, max_edges=1 << 24, keep_x=False):
     """Continuous batching with the resident executor.  Arrival times in
-    `reqs` are seconds from the start of the run.  `ctx` must be bound to a
-    stream of its own: the resident kernel occupies it for the whole run
-    (generation and read-backs use other streams)."""
+    `reqs` are seconds from the start of the run; the requests' inputs must
+    have been built (prepare).  `ctx` must be bound to a stream of its own:
+    the resident kernel occupies it for the whole run (admission copies and
+    read-backs use other streams)."""
     gen_stream = torch.cuda.Stream(device=device)
     side = torch.cuda.Stream(device=device)
     host = torch.empty(64, dtype=torch.float64, pin_memory=True)
@@ -265,8 +297,8 @@ def serve_plain(ctx, reqs, prec="fp64", tol=1e-12, max_iter=30, device="cuda", t
     per stage, nothing overlapped."""
     stream = torch.cuda.current_stream(device)
     done = []
-    t0 = time.perf_counter()
     host = torch.empty(64, dtype=torch.float64, pin_memory=True)
+    t0 = time.perf_counter()
     for r in reqs:
         now = time.perf_counter() - t0
         if now > time_limit:

@@ -25,6 +25,7 @@ def requests(n, rate, prec, nmax=1536):
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-14), ("bf16", 1e-12)])
 def test_serve_mix_equals_alone(orc, prec, tol):
     reqs = requests(10, 400.0, prec)
+    sv.prepare(reqs)
     side = torch.cuda.Stream()
     ctx = b3t.Context(stream=side.cuda_stream, timeout_ns=20_000_000_000)
     st = sv.serve(ctx, reqs, prec=prec, budget_bytes=2 << 30, max_inflight=6, time_limit=120.0,
@@ -33,6 +34,7 @@ def test_serve_mix_equals_alone(orc, prec, tol):
     assert st["requests"] == 10 and st["failed"] == 0
     assert all(r.eta <= tol for r in reqs)
     alone = [copy.copy(r) for r in requests(10, 1e9, prec)]     # same requests, served one by one
+    sv.prepare(alone)
     c2 = b3t.Context(stream=torch.cuda.current_stream().cuda_stream, timeout_ns=20_000_000_000)
     sv.serve_plain(c2, alone, prec=prec, keep_x=True)
     c2.close()
