@@ -313,6 +313,14 @@ def run_ours(args):
         del hA, hL
 
     nctas = ctx.last_launch()["nctas"]
+    cpu = None
+    if rank == 0 and args.cpu_seconds > 0:
+        from paper_1304_0878_b300.tiles import tile_index
+
+        def get(i, j):
+            return A0[tile_index(i, j, T)].cpu().numpy()
+        cpu = oracle_sample(get, T, b, args.cpu_seconds)
+
     secondary = {}
     if not args.no_secondary:
         secondary = run_secondary(ctx, dev, stream)
@@ -322,14 +330,6 @@ def run_ours(args):
         del A0, t
         torch.cuda.empty_cache()
         secondary["serving"] = run_serving(dev, args)
-
-    cpu = None
-    if rank == 0 and args.cpu_seconds > 0:
-        from paper_1304_0878_b300.tiles import tile_index
-
-        def get(i, j):
-            return A0[tile_index(i, j, T)].cpu().numpy()
-        cpu = oracle_sample(get, T, b, args.cpu_seconds)
 
     ctx.graph_destroy(g)
     ctx.close()
