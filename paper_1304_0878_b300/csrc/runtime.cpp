@@ -825,16 +825,9 @@ static bool stream_handle_busy(b3t_ctx *c, b3t_handle h) {
     return false;
 }
 
-int b3t_data_unregister(b3t_ctx *c, b3t_handle h) {
-    if (!c) return -EINVAL;
-    int rc = check_handle(c, h);
-    if (rc) return rc;
-    if (c->st.open) {
-        // stream mode: no wait; the buffer must not be in use
-        if (stream_handle_busy(c, h)) return -EBUSY;
-    } else {
-        rc = c->capturing ? 0 : wait_impl(c, 0);
-    }
+// Forget a handle and its partition parts (parts 1.. are looked up by their
+// own addresses, so they leave the address map too).
+static void drop_handle(b3t_ctx *c, b3t_handle h) {
     Handle &H = c->handles[h];
     for (int32_t k : H.parts) {
         auto it = c->by_ptr.find((uintptr_t)c->handles[k].ptr);
@@ -845,6 +838,19 @@ int b3t_data_unregister(b3t_ctx *c, b3t_handle h) {
     if (it != c->by_ptr.end() && it->second == h) c->by_ptr.erase(it);
     H.alive = false;
     H.parts.clear();
+}
+
+int b3t_data_unregister(b3t_ctx *c, b3t_handle h) {
+    if (!c) return -EINVAL;
+    int rc = check_handle(c, h);
+    if (rc) return rc;
+    if (c->st.open) {
+        // stream mode: no wait; the buffer must not be in use
+        if (stream_handle_busy(c, h)) return -EBUSY;
+    } else {
+        rc = c->capturing ? 0 : wait_impl(c, 0);
+    }
+    drop_handle(c, h);
     return rc;
 }
 
@@ -1518,11 +1524,7 @@ int b3t_tiles_unregister(b3t_ctx *c, void *const *tiles, int32_t T) {
     }
     for (int64_t t = 0; t < nt; ++t) {
         b3t_handle h;
-        if (tiles[t] && b3t_data_lookup(c, tiles[t], &h) == 0) {
-            Handle &H = c->handles[h];
-            c->by_ptr.erase((uintptr_t)H.ptr);
-            H.alive = false;
-        }
+        if (tiles[t] && b3t_data_lookup(c, tiles[t], &h) == 0) drop_handle(c, h);
     }
     return rc;
 }

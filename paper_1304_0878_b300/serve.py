@@ -168,13 +168,15 @@ def release(ctx, req, keep_x=False, stream=None):
     req.inputs = None
 
 
-def make_requests(n, rate, seed, nmin=256, nmax=8192, rmax=32, prec="fp64"):
+def make_requests(n, rate, seed, nmin=256, nmax=8192, rmax=32, prec="fp64", tile=None):
+    """n requests (Poisson arrivals at `rate` per second); the tile size is
+    the tuner's choice for each N unless `tile` fixes it."""
     import synth
     arr, Ns, nrhs, seeds = synth.serve_requests(n, rate=rate, seed=seed, nmin=nmin, nmax=nmax, rmax=rmax)
     out = []
     for i in range(n):
         r = Request(i, float(arr[i]), Ns[i], nrhs[i], seeds[i] % (2 ** 62))
-        r.b = tune.choose_tile(r.N, prec)
+        r.b = tile or tune.choose_tile(r.N, prec)
         r.Np = dt.pad_size(r.N, r.b)
         r.T = r.Np // r.b
         r.bytes = footprint(r.Np, r.nrhs, r.b, prec)

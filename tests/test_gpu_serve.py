@@ -18,22 +18,27 @@ pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not torch.cuda.is_available(), reason="no CUDA device")]
 
 
-def requests(n, rate, prec, nmax=1536):
-    return sv.make_requests(n, rate, seed=5, nmin=200, nmax=nmax, rmax=8, prec=prec)
+def requests(n, rate, prec, nmin=200, nmax=1536):
+    tile = 256 if nmin > 2048 else None
+    return sv.make_requests(n, rate, seed=5, nmin=nmin, nmax=nmax, rmax=8, prec=prec, tile=tile)
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-14), ("bf16", 1e-12)])
-def test_serve_mix_equals_alone(orc, prec, tol):
-    reqs = requests(10, 400.0, prec)
+# the large cases use tiles of 256 (diagonal tiles split into column panels)
+# and, with two requests in flight, reuse freed buffers' addresses
+@pytest.mark.parametrize("prec,tol,n,nmin,nmax,inflight", [
+    ("fp64", 1e-14, 10, 200, 1536, 6), ("bf16", 1e-12, 10, 200, 1536, 6),
+    ("fp64", 1e-14, 6, 2100, 3500, 2), ("bf16", 1e-12, 6, 2100, 3500, 2)])
+def test_serve_mix_equals_alone(orc, prec, tol, n, nmin, nmax, inflight):
+    reqs = requests(n, 400.0, prec, nmin, nmax)
     sv.prepare(reqs)
     side = torch.cuda.Stream()
     ctx = b3t.Context(stream=side.cuda_stream, timeout_ns=20_000_000_000)
-    st = sv.serve(ctx, reqs, prec=prec, budget_bytes=2 << 30, max_inflight=6, time_limit=120.0,
+    st = sv.serve(ctx, reqs, prec=prec, budget_bytes=2 << 30, max_inflight=inflight, time_limit=120.0,
                   max_tasks=1 << 20, max_edges=1 << 22, keep_x=True)
     ctx.close()
-    assert st["requests"] == 10 and st["failed"] == 0
+    assert st["requests"] == n and st["failed"] == 0
     assert all(r.eta <= tol for r in reqs)
-    alone = [copy.copy(r) for r in requests(10, 1e9, prec)]     # same requests, served one by one
+    alone = [copy.copy(r) for r in requests(n, 1e9, prec, nmin, nmax)]     # same requests, served one by one
     sv.prepare(alone)
     c2 = b3t.Context(stream=torch.cuda.current_stream().cuda_stream, timeout_ns=20_000_000_000)
     sv.serve_plain(c2, alone, prec=prec, keep_x=True)

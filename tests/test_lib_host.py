@@ -213,3 +213,17 @@ def test_cholesky_panel_dag_edges(ctx, T, b):
                             (och.tile_index(i, j, T), RW)])
     assert ctx.dag_stats()[0] == len(acc)
     assert sorted(ctx.dag_edges()) == dag.derive_edges(acc, parts)
+
+
+def test_tiles_unregister_forgets_panel_parts(ctx):
+    # a diagonal tile of b = 256 is split into two 128-column panels whose
+    # second part is looked up by its own address; after the tiles are
+    # unregistered a new buffer at that address must register afresh
+    p = fake_ptr(0)
+    ctx.cholesky_submit([p], 1, 256)
+    with pytest.raises(b3t.B3TError) as e:      # host-only: the wait drops the batch, reports no device
+        ctx.tiles_unregister([p], 1)
+    assert e.value.code == b3t._lib.ENODEV
+    part1 = p + 256 * 128 * 8
+    ctx.cholesky_submit([part1], 1, 128)
+    assert ctx.dag_stats()[0] == 1
