@@ -249,6 +249,7 @@ def run_ours(args):
     flops = cholesky_flops(N)
 
     A0 = synth.spd_tiles_device(N, b, 3, 0.1, dev)
+    a_bytes = A0.numel() * A0.element_size()
     t = torch.empty_like(A0)
     ptrs = dt.tile_ptrs(t)
     ctx.graph_capture_begin()
@@ -345,7 +346,7 @@ def run_ours(args):
                                % (N, b, len_tasks(T)),
                    "N": N, "tile": b, "tasks": len_tasks(T), "seed": 3, "shift": 0.1,
                    "parallelism": "replicas" if ws > 1 else "single GPU",
-                   "l2": "inputs (%.2f GB of tiles) larger than L2" % (A0.numel() * 8 / 1e9),
+                   "l2": "inputs (%.2f GB of tiles) larger than L2" % (a_bytes / 1e9),
                    "input_reset": "A tiles restored by a device copy inside each step",
                    "persistent_ctas": nctas},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
