@@ -61,7 +61,16 @@ __device__ __forceinline__ void set_error(Ctl *ctl, int err, int task, int info,
 }
 
 // ------------------------------------------------------------- SCAL
-// x[i] <- fl32(x[i] * f) over one chunk, 128-bit loads and stores.
+// x[i] <- fl32(x[i] * f) over one chunk, 128-bit loads and stores.  Each
+// thread walks batches of U float4 at a stride of the CTA; two register
+// batches alternate, so the loads of the next batch are in flight while the
+// current one is scaled and stored.
+__device__ __forceinline__ float4 mul4(float4 a, float f) {
+    a.x = __fmul_rn(a.x, f); a.y = __fmul_rn(a.y, f);
+    a.z = __fmul_rn(a.z, f); a.w = __fmul_rn(a.w, f);
+    return a;
+}
+
 __device__ __forceinline__ void scal_item(const TaskRec &t, int item) {
     float *x = (float *)t.buf[0];
     const float f = __uint_as_float(t.scal);
@@ -69,26 +78,34 @@ __device__ __forceinline__ void scal_item(const TaskRec &t, int item) {
     const int64_t end = min(t.n, start + kScalChunk);
     const int64_t nv = (end - start) >> 2;
     float4 *v = reinterpret_cast<float4 *>(x + start);
-    constexpr int U = 16;
+    constexpr int U = 8;
+    constexpr int64_t B = (int64_t)kThreads * U;   // float4 per batch
     const int tid = threadIdx.x;
-    for (int64_t i0 = tid; i0 < nv; i0 += (int64_t)kThreads * U) {
-        float4 r[U];
+    const int64_t nfull = nv / B;
+    float4 a[U], b[U];
+    int64_t j = 0;
+    if (nfull > 0) {
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t i = i0 + (int64_t)u * kThreads;
-            if (i < nv) r[u] = __ldcg(v + i);
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t i = i0 + (int64_t)u * kThreads;
-            if (i < nv) {
-                float4 a = r[u];
-                a.x = __fmul_rn(a.x, f); a.y = __fmul_rn(a.y, f);
-                a.z = __fmul_rn(a.z, f); a.w = __fmul_rn(a.w, f);
-                __stcg(v + i, a);
-            }
-        }
+        for (int u = 0; u < U; ++u) a[u] = __ldcg(v + tid + u * kThreads);
     }
+    for (; j + 2 <= nfull; j += 2) {
+        const int64_t o0 = j * B + tid, o1 = o0 + B;
+#pragma unroll
+        for (int u = 0; u < U; ++u) b[u] = __ldcg(v + o1 + u * kThreads);
+#pragma unroll
+        for (int u = 0; u < U; ++u) __stcg(v + o0 + u * kThreads, mul4(a[u], f));
+        if (j + 2 < nfull) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) a[u] = __ldcg(v + o1 + B + u * kThreads);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) __stcg(v + o1 + u * kThreads, mul4(b[u], f));
+    }
+    if (j < nfull) {   // an odd batch count leaves the last batch in a
+#pragma unroll
+        for (int u = 0; u < U; ++u) __stcg(v + j * B + tid + u * kThreads, mul4(a[u], f));
+    }
+    for (int64_t i = nfull * B + tid; i < nv; i += kThreads) __stcg(v + i, mul4(__ldcg(v + i), f));
     const int64_t tail = (end - start) & 3;
     if (tid < tail) {
         float *p = x + start + nv * 4 + tid;
@@ -148,16 +165,19 @@ __device__ __forceinline__ unsigned long long claim(const LaunchParams &p, uint6
     const uint64_t t0 = gtimer();
     uint32_t backoff = 0;
     for (uint32_t spin = 0;; ++spin) {
+        // one round trip: lanes < nlevels read their level's head and tail,
+        // lane 31 the sticky error word
         int err = 0;
-        if (lane == 0) err = ld_rlx_i32(&ctl->error);
-        err = __shfl_sync(0xffffffffu, err, 0);
-        if (err) return kEmpty;
         unsigned long long h = 0, tl = 0;
         const bool mine = lane < p.nlevels;
         if (mine) {
             h = ld_rlx(&ctl->lvl[lane].head);
             tl = ld_rlx(&ctl->lvl[lane].tail);
+        } else if (lane == 31) {
+            err = ld_rlx_i32(&ctl->error);
         }
+        err = __shfl_sync(0xffffffffu, err, 31);
+        if (err) return kEmpty;
         const unsigned mask = __ballot_sync(0xffffffffu, mine && h < tl);
         if (mask) {
             const int lv = 31 - __clz(mask);
@@ -323,10 +343,28 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
     }
 
     const uint64_t kstart = gtimer();
+    __shared__ TaskRec s_rec;
+    // warp 0: the task of the previous item while it may have items left
+    int64_t ft = -1;
+    int fn = 0;
     for (;;) {
         if (warp == 0) {
-            const unsigned long long it = claim(p, kstart);
-            if ((tid & 31) == 0) s_item = it;
+            const int lane = tid & 31;
+            unsigned long long it = kEmpty;
+            if (ft >= 0) {
+                // stay on the task: take its next item without a queue scan
+                // (a scan that later finds the task exhausted moves the head)
+                int j = 0;
+                if (lane == 0) j = atomicAdd(&p.next_item[ft], 1);
+                j = __shfl_sync(0xffffffffu, j, 0);
+                if (j < fn) it = ((unsigned long long)ft << 32) | (uint32_t)j;
+            }
+            const bool same = it != kEmpty;
+            if (!same) it = claim(p, kstart);
+            const int64_t t = (int64_t)(it >> 32);
+            if (!same && it != kEmpty && (!p.debug || t < p.ntasks) && lane < 4)
+                reinterpret_cast<uint4 *>(&s_rec)[lane] = __ldcg(reinterpret_cast<const uint4 *>(p.tasks + t) + lane);
+            if (lane == 0) s_item = it;
         }
         __syncthreads();
         const unsigned long long item = s_item;
@@ -334,12 +372,12 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
         __threadfence();   // acquire side for every thread of the CTA
         const int64_t t = (int64_t)(item >> 32);
         const int it = (int)(item & 0xffffffffu);
-        if (p.debug && (t >= p.ntasks || it >= p.tasks[t].nitems)) {
+        if (p.debug && (t >= p.ntasks || it >= s_rec.nitems)) {
             if (tid == 0) set_error(p.ctl, EPROTO, (int)t, -1, 5);
             __syncthreads();
             break;
         }
-        const TaskRec rec = p.tasks[t];
+        const TaskRec rec = s_rec;
         int st = 0;
         switch (rec.kind) {
         case kScalF32: scal_item(rec, it); break;
@@ -417,7 +455,13 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
             }
         }
         __syncthreads();
-        if (s_flag && warp == 0) retire(p, t, rec);
+        if (warp == 0) {
+            if (s_flag) retire(p, t, rec);
+            // a multi-item task that has not finished may still hold items
+            const int more = __shfl_sync(0xffffffffu, st == 0 && !s_flag && rec.nitems > 1, 0);
+            ft = more ? t : -1;
+            fn = rec.nitems;
+        }
     }
 
     if (kMx && p.has_mx) {
