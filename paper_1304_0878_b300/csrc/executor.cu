@@ -13,7 +13,12 @@
 //   * the ready queue has up to kMaxLevels levels (upward-rank buckets, the
 //     scheduling hint of Section 5.3, or depth from the sources); a claim
 //     takes the next item of the oldest task of the highest non-empty level,
-//     found with one warp-wide scan;
+//     found with one warp-wide scan; a CTA that finishes an item of a task
+//     with several items asks for the task's next item in the same round trip
+//     as its done count, so it scans the queue only once the task runs dry;
+//   * SCAL items stream through a ring of shared-memory stages with bulk
+//     copies (cp.async.bulk and mbarriers) in the variant without tensor
+//     memory, through double-buffered registers in the other;
 //   * every wait is bounded by %globaltimer: an idle CTA that sees no work for
 //     longer than the launch's timeout sets ETIMEDOUT in the status word and
 //     the whole grid exits; nothing spins forever.
@@ -111,6 +116,91 @@ __device__ __forceinline__ void scal_item(const TaskRec &t, int item) {
         float *p = x + start + nv * 4 + tid;
         *p = __fmul_rn(*p, f);
     }
+}
+
+// SCAL through bulk copies: 16 KiB chunks stream through a ring of 4 shared
+// memory stages (global -> shared with an mbarrier, multiply in place,
+// shared -> global).  Thread 0 issues every copy.  Every wait is bounded;
+// the first that gives up stops the item (no further copies) after the
+// fills already issued are drained, again with a bound.  Returns 0 or the
+// 1-based chunk whose wait gave up.
+constexpr int kSbStages = 4;
+constexpr uint32_t kSbBytes = 16384;
+
+__device__ __forceinline__ void bulk_s2g_commit(void *dst, const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ int scal_item_bulk(const TaskRec &t, int item, uint64_t *full, unsigned char *stage,
+                                              uint32_t &fills, int64_t limit_ns) {
+    float *x = (float *)t.buf[0];
+    const float f = __uint_as_float(t.scal);
+    const int64_t start = (int64_t)item * kScalChunk;
+    const int64_t end = min(t.n, start + kScalChunk);
+    const int64_t nvec = (end - start) & ~(int64_t)3;
+    const uint32_t bytes = (uint32_t)(nvec * 4);
+    const int nch = (int)((bytes + kSbBytes - 1) / kSbBytes);
+    const int tid = threadIdx.x;
+    char *gx = (char *)(x + start);
+    const uint32_t G = fills;
+    if (tid == 0) {
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        for (int c = 0; c < nch && c < kSbStages; ++c) {
+            const uint32_t s = (G + c) % kSbStages;
+            const uint32_t nb = min(kSbBytes, bytes - (uint32_t)c * kSbBytes);
+            mbar_expect_tx(&full[s], nb);
+            bulk_g2s(stage + s * kSbBytes, gx + (size_t)c * kSbBytes, nb, &full[s]);
+        }
+    }
+    int issued = min(nch, kSbStages);
+    int failed = 0, c = 0;
+    for (; c < nch; ++c) {
+        const uint32_t g = G + c, s = g % kSbStages;
+        const uint32_t nb = min(kSbBytes, bytes - (uint32_t)c * kSbBytes);
+        const bool ok = mbar_wait(&full[s], (g / kSbStages) & 1, limit_ns);
+        if (ok) {
+            float4 *v = reinterpret_cast<float4 *>(stage + s * kSbBytes);
+            for (uint32_t i = tid; i < nb / 16; i += kThreads) v[i] = mul4(v[i], f);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+        if (__syncthreads_or(!ok)) {
+            failed = c + 1;
+            break;
+        }
+        if (tid == 0) {
+            bulk_s2g_commit(gx + (size_t)c * kSbBytes, stage + s * kSbBytes, nb);
+            if (c + kSbStages < nch) {
+                // the stage is refilled once the store has read it
+                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                const int cn = c + kSbStages;
+                const uint32_t nb2 = min(kSbBytes, bytes - (uint32_t)cn * kSbBytes);
+                mbar_expect_tx(&full[s], nb2);
+                bulk_g2s(stage + s * kSbBytes, gx + (size_t)cn * kSbBytes, nb2, &full[s]);
+            }
+        }
+        if (c + kSbStages < nch) ++issued;
+    }
+    if (failed) {
+        for (int d = c; d < issued; ++d) {
+            const uint32_t g = G + d;
+            mbar_wait(&full[g % kSbStages], (g / kSbStages) & 1, limit_ns);
+        }
+    }
+    fills = G + issued;
+    const int64_t tail = (end - start) - nvec;
+    if (!failed && tid < tail) {
+        float *p = x + start + nvec + tid;
+        *p = __fmul_rn(*p, f);
+    }
+    if (tid == 0) {
+        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+    }
+    __syncthreads();
+    return failed;
 }
 
 // POTRF_MX: L_kk = chol(fp64(W_kk)), strict upper part of L_kk zeroed.
@@ -316,7 +406,7 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
     // align the dynamic area to 1024 bytes (128-byte swizzled operands)
     unsigned char *smem = (unsigned char *)(((uintptr_t)dsmem + 1023) & ~(uintptr_t)1023);
     __shared__ unsigned long long s_item;
-    __shared__ int s_flag, s_info, s_fail, s_e;
+    __shared__ int s_info, s_fail, s_e;
     __shared__ __align__(8) uint64_t s_bars[2 * kMxStages + 1];
     __shared__ uint32_t s_tmem;
     __shared__ double s_red[kThreads / 32];
@@ -342,25 +432,25 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
         mx.tmem = s_tmem;
     }
 
+    // SCAL bulk-copy ring (the variant without the tensor-memory path)
+    __shared__ __align__(8) uint64_t s_sbar[kSbStages];
+    uint32_t sfills = 0;
+    if (!kMx) {
+        if (tid == 0) {
+            for (int i = 0; i < kSbStages; ++i) mbar_init(&s_sbar[i], 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+    }
     const uint64_t kstart = gtimer();
     __shared__ TaskRec s_rec;
-    // warp 0: the task of the previous item while it may have items left
-    int64_t ft = -1;
-    int fn = 0;
+    // warp 0: an item of the previous task taken when that item finished
+    unsigned long long fi = kEmpty;
     for (;;) {
         if (warp == 0) {
             const int lane = tid & 31;
-            unsigned long long it = kEmpty;
-            if (ft >= 0) {
-                // stay on the task: take its next item without a queue scan
-                // (a scan that later finds the task exhausted moves the head)
-                int j = 0;
-                if (lane == 0) j = atomicAdd(&p.next_item[ft], 1);
-                j = __shfl_sync(0xffffffffu, j, 0);
-                if (j < fn) it = ((unsigned long long)ft << 32) | (uint32_t)j;
-            }
-            const bool same = it != kEmpty;
-            if (!same) it = claim(p, kstart);
+            const bool same = fi != kEmpty;
+            const unsigned long long it = same ? fi : claim(p, kstart);
             const int64_t t = (int64_t)(it >> 32);
             if (!same && it != kEmpty && (!p.debug || t < p.ntasks) && lane < 4)
                 reinterpret_cast<uint4 *>(&s_rec)[lane] = __ldcg(reinterpret_cast<const uint4 *>(p.tasks + t) + lane);
@@ -380,7 +470,19 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
         const TaskRec rec = s_rec;
         int st = 0;
         switch (rec.kind) {
-        case kScalF32: scal_item(rec, it); break;
+        case kScalF32:
+            if constexpr (!kMx) {
+                // each wait of the ring gives up after 50 ms (a 16 KiB copy
+                // takes microseconds) and the launch reports ETIMEDOUT
+                const int fc = scal_item_bulk(rec, it, s_sbar, smem, sfills, min(p.timeout_ns, (int64_t)50000000));
+                if (fc) {
+                    if (tid == 0) set_error(p.ctl, ETIMEDOUT, (int)t, fc, 20);
+                    st = -ETIMEDOUT;
+                }
+            } else {
+                scal_item(rec, it);
+            }
+            break;
         case kPotrf: {
             const int info = potrf_tile((double *)rec.buf[0], (int)rec.n, (double *)smem, &s_info);
             if (info) st = rec.aux + info;
@@ -434,33 +536,35 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
         case kNrm: nrm_item(rec, smem); break;
         default: break;   // NOOP
         }
-        __syncthreads();
-        if (st > 0 && p.stream_mode) {
-            // a served request that is not positive definite fails alone: its
-            // info is reported with the batch and the graph drains
-            if (tid == 0) atomicCAS(&p.batch_info[p.task_batch[t]], 0, st);
-            st = 0;
-        }
-        if (tid == 0) {
-            if (st > 0) {
-                set_error(p.ctl, EDOM, (int)t, st, 0);   // not positive definite: no retire
-                s_flag = 0;
-            } else if (st < 0) {
-                set_error(p.ctl, -st, (int)t, -1, 6);
-                s_flag = 0;
-            } else {
-                __threadfence();
-                const int d = atomicAdd(&p.done_items[t], 1) + 1;
-                s_flag = (d == rec.nitems);
-            }
-        }
-        __syncthreads();
+        __syncthreads();   // every thread is done with the item
         if (warp == 0) {
-            if (s_flag) retire(p, t, rec);
-            // a multi-item task that has not finished may still hold items
-            const int more = __shfl_sync(0xffffffffu, st == 0 && !s_flag && rec.nitems > 1, 0);
-            ft = more ? t : -1;
-            fn = rec.nitems;
+            // warp 0 alone finishes the item; the other warps go on to the
+            // barrier at the top of the loop
+            int flag = 0, nj = -1;
+            if (tid == 0) {
+                if (st > 0 && p.stream_mode) {
+                    // a served request that is not positive definite fails
+                    // alone: its info is reported with the batch, the graph drains
+                    atomicCAS(&p.batch_info[p.task_batch[t]], 0, st);
+                    st = 0;
+                }
+                if (st > 0) {
+                    set_error(p.ctl, EDOM, (int)t, st, 0);   // not positive definite: no retire
+                } else if (st < 0) {
+                    set_error(p.ctl, -st, (int)t, -1, 6);
+                } else {
+                    __threadfence();
+                    // the next item of the same task is asked for together
+                    // with the done count (the two round trips overlap)
+                    if (rec.nitems > 1) nj = atomicAdd(&p.next_item[t], 1);
+                    const int d = atomicAdd(&p.done_items[t], 1) + 1;
+                    flag = d == rec.nitems;
+                }
+            }
+            flag = __shfl_sync(0xffffffffu, flag, 0);
+            nj = __shfl_sync(0xffffffffu, nj, 0);
+            if (flag) retire(p, t, rec);
+            fi = (nj >= 0 && nj < rec.nitems) ? (((unsigned long long)t << 32) | (uint32_t)nj) : kEmpty;
         }
     }
 
