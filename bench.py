@@ -35,6 +35,17 @@ sys.path.insert(0, ROOT)
 PEAK_FP64_FLOP_PER_CLK_SM = 4      # two DFMA per clock per SM on sm_103
 NUM_SMS = 148
 SM_MAX_MHZ = 2032.0
+FALLBACK_HBM_GBS = 6400.0           # one earlier copy measurement on a B300
+
+
+def hbm_peak():
+    """Measured copy bandwidth of the B300s (GB/s) and its source."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
 
 
 def parse():
@@ -505,7 +516,8 @@ def run_secondary(ctx, dev, stream):
         med = float(np.median(ts))
         out[name] = {"workload": "n=2^28 f32, 256 blocks x 8 chained RW tasks (2048 tasks)",
                      "ms": 1e3 * med, "task_level_GBps": tbytes / med / 1e9, "task_bytes": tbytes,
-                     "hbm_frac_of_measured": tbytes / med / 1e9 / 6451.5}
+                     "hbm_frac": tbytes / med / 1e9 / hbm_peak()[0], "hbm_peak_GBps": hbm_peak()[0],
+                     "hbm_peak_source": hbm_peak()[1]}
         c2.graph_destroy(g)
         c2.close()
     del x

@@ -552,11 +552,13 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
                     set_error(p.ctl, EDOM, (int)t, st, 0);   // not positive definite: no retire
                 } else if (st < 0) {
                     set_error(p.ctl, -st, (int)t, -1, 6);
+                } else if (rec.nitems == 1) {
+                    flag = 1;   // the only item: retire (which fences) at once
                 } else {
                     __threadfence();
                     // the next item of the same task is asked for together
                     // with the done count (the two round trips overlap)
-                    if (rec.nitems > 1) nj = atomicAdd(&p.next_item[t], 1);
+                    nj = atomicAdd(&p.next_item[t], 1);
                     const int d = atomicAdd(&p.done_items[t], 1) + 1;
                     flag = d == rec.nitems;
                 }
