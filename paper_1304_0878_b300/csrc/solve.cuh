@@ -98,9 +98,11 @@ __device__ __forceinline__ void trsv_lt_item(const TaskRec &t, int j, unsigned c
 }
 
 // Y_i(r0+r, j) -= sum_q M(r, q) Y_k(q, j), M = L_ik (trans = false) or
-// L_ki^T (trans = true), 64 rows per item.
-template <typename Tc, bool trans>
-__device__ __forceinline__ void gemv_item(const TaskRec &t, int item, unsigned char *smem) {
+// L_ki^T (trans = true), 64 rows per item.  Thread (r, g) owns row r and the
+// right-hand sides g, g + 4, ...: NM of them, NM the smallest power of two
+// that covers nrhs (so no multiply-add is issued for an absent column).
+template <typename Tc, bool trans, int NM>
+__device__ __forceinline__ void gemv_body(const TaskRec &t, int item, unsigned char *smem) {
     const double *L = (const double *)t.buf[0];
     const double *Yk = (const double *)t.buf[1];
     double *Yi = (double *)t.buf[2];
@@ -108,9 +110,9 @@ __device__ __forceinline__ void gemv_item(const TaskRec &t, int item, unsigned c
     const int r = tid & 63, g = tid >> 6, r0 = item * 64;
     Tc *Ys = (Tc *)smem;                 // [nrhs][64]
     Tc *Lc = Ys + 64 * 32;               // [64][65] (trans only)
-    Tc acc[8];
+    Tc acc[NM];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) acc[m] = 0;
+    for (int m = 0; m < NM; ++m) acc[m] = 0;
     for (int q0 = 0; q0 < b; q0 += 64) {
         for (int e = tid; e < 64 * nrhs; e += kThreads) {
             const int q = e & 63, jj = e >> 6;
@@ -127,21 +129,30 @@ __device__ __forceinline__ void gemv_item(const TaskRec &t, int item, unsigned c
         for (int q = 0; q < 64; ++q) {
             const Tc a = trans ? Lc[r * 65 + q] : (Tc)L[(size_t)(r0 + r) + (size_t)(q0 + q) * b];
 #pragma unroll
-            for (int m = 0; m < 8; ++m) {
+            for (int m = 0; m < NM; ++m) {
                 const int jj = g + 4 * m;
-                if (jj < nrhs) acc[m] += a * Ys[jj * 64 + q];
+                if (NM == 1 || jj < nrhs) acc[m] += a * Ys[jj * 64 + q];
             }
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
+    for (int m = 0; m < NM; ++m) {
         const int jj = g + 4 * m;
         if (jj < nrhs) {
             double *p = Yi + (size_t)jj * b + r0 + r;
             *p = *p - (double)acc[m];
         }
     }
+}
+
+template <typename Tc, bool trans>
+__device__ __forceinline__ void gemv_item(const TaskRec &t, int item, unsigned char *smem) {
+    const int nm = (vk_nrhs(t) + 3) / 4;
+    if (nm <= 1) gemv_body<Tc, trans, 1>(t, item, smem);
+    else if (nm <= 2) gemv_body<Tc, trans, 2>(t, item, smem);
+    else if (nm <= 4) gemv_body<Tc, trans, 4>(t, item, smem);
+    else gemv_body<Tc, trans, 8>(t, item, smem);
 }
 
 __device__ __forceinline__ void axpy_item(const TaskRec &t) {
@@ -156,7 +167,12 @@ __device__ __forceinline__ int64_t ptile(int i, int j, int T) {
     return (int64_t)j * T - (int64_t)j * (j - 1) / 2 + (i - j);
 }
 
-__device__ __forceinline__ void resid_item(const TaskRec &t, int item, unsigned char *smem) {
+// Thread (r, g) accumulates row r0 + r of A X for the right-hand sides
+// g, g + 4, ... (NM of them, the smallest power of two covering nrhs: no
+// multiply-add is issued for an absent column), and the threads of g = 0
+// also the row sum of |A| (one FP64 add per element of A, not four).
+template <int NM>
+__device__ __forceinline__ void resid_body(const TaskRec &t, int item, unsigned char *smem) {
     const double *A = (const double *)t.buf[0];
     const double *X = (const double *)t.buf[1];
     const double *B = (const double *)t.buf[2];
@@ -167,9 +183,9 @@ __device__ __forceinline__ void resid_item(const TaskRec &t, int item, unsigned 
     const int tid = threadIdx.x, r = tid & (RR - 1), g = tid / RR, r0 = item * RR, nit = b / RR;
     double *As = (double *)smem;            // [64 columns][65]: As[c*65 + r]
     double *Xs = As + 64 * 65;              // [nrhs][64]
-    double acc[8];
+    double acc[NM];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) acc[m] = 0.0;
+    for (int m = 0; m < NM; ++m) acc[m] = 0.0;
     double rs = 0.0;
     if (!xzero) {
         for (int J = 0; J < T; ++J) {
@@ -196,15 +212,27 @@ __device__ __forceinline__ void resid_item(const TaskRec &t, int item, unsigned 
                     As[c * 65 + rr] = tile[off];
                 }
                 __syncthreads();
+                if (g == 0) {
 #pragma unroll 2
-                for (int c = 0; c < 64; ++c) {
-                    const double a = As[c * 65 + r];
+                    for (int c = 0; c < 64; ++c) {
+                        const double a = As[c * 65 + r];
 #pragma unroll
-                    for (int m = 0; m < 8; ++m) {
-                        const int jj = g + 4 * m;
-                        if (jj < nrhs) acc[m] = fma(a, Xs[jj * 64 + c], acc[m]);
+                        for (int m = 0; m < NM; ++m) {
+                            const int jj = 4 * m;
+                            if (jj < nrhs) acc[m] = fma(a, Xs[jj * 64 + c], acc[m]);
+                        }
+                        rs += fabs(a);
                     }
-                    rs += fabs(a);
+                } else {
+#pragma unroll 2
+                    for (int c = 0; c < 64; ++c) {
+                        const double a = As[c * 65 + r];
+#pragma unroll
+                        for (int m = 0; m < NM; ++m) {
+                            const int jj = g + 4 * m;
+                            if (jj < nrhs) acc[m] = fma(a, Xs[jj * 64 + c], acc[m]);
+                        }
+                    }
                 }
                 __syncthreads();
             }
@@ -214,7 +242,7 @@ __device__ __forceinline__ void resid_item(const TaskRec &t, int item, unsigned 
     double *Ra = As;                        // reuse: [nrhs][64] |r|, then [nrhs][64] |x|
     double *Xa = As + 64 * kMaxRhs;
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
+    for (int m = 0; m < NM; ++m) {
         const int jj = g + 4 * m;
         if (jj < nrhs) {
             const size_t o = (size_t)jj * b + r0 + r;
@@ -241,6 +269,14 @@ __device__ __forceinline__ void resid_item(const TaskRec &t, int item, unsigned 
         for (int k = 0; k < RR; ++k) m = fmax(m, Rs[k]);
         Rn[(size_t)2 * nit * nrhs + item] = m;
     }
+}
+
+__device__ __forceinline__ void resid_item(const TaskRec &t, int item, unsigned char *smem) {
+    const int nm = (vk_nrhs(t) + 3) / 4;
+    if (nm <= 1) resid_body<1>(t, item, smem);
+    else if (nm <= 2) resid_body<2>(t, item, smem);
+    else if (nm <= 4) resid_body<4>(t, item, smem);
+    else resid_body<8>(t, item, smem);
 }
 
 __device__ __forceinline__ void nrm_item(const TaskRec &t, unsigned char *smem) {
