@@ -63,7 +63,8 @@ def parse():
     p.add_argument("--nrhs", type=int, default=16)
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--serve-requests", type=int, default=96)
-    p.add_argument("--case", default=None, choices=["mx_gemm_bf16", "mx_gemm_e4m3", "scal", "resid"],
+    p.add_argument("--case", default=None, choices=["mx_gemm_bf16", "mx_gemm_e4m3", "scal", "resid", "solve_f32",
+                                                    "solve_f64"],
                    help="run a DAG of one task kind only (profiling case) and print its timing")
     return p.parse_args()
 
@@ -606,6 +607,23 @@ def run_case(args):
                 ctx.task_submit(cl, [h], b3t.pack_f32(1.0000001))
         g = ctx.graph_capture_end()
         work, unit = 8.0 * n * nb * nk, "GB/s"
+    elif args.case.startswith("solve"):
+        # forward + backward solve with a tiled factor, N = 16384, 16 rhs
+        N, nrhs = 16384, 16
+        T = N // b
+        L = synth.spd_tiles_device(N, b, 3, 0.1, dev)
+        ctx.graph_capture_begin()
+        ctx.cholesky_submit(dt.tile_ptrs(L), T, b)
+        gl = ctx.graph_capture_end()
+        ctx.graph_replay(gl)
+        ctx.task_wait()
+        ctx.graph_destroy(gl)
+        Y = torch.randn((T, nrhs, b), dtype=torch.float64, device=dev)
+        flags = b3t.VEC_F32 if args.case.endswith("f32") else 0
+        ctx.graph_capture_begin()
+        ctx.chol_solve_submit(dt.tile_ptrs(L), Y.data_ptr(), T, b, nrhs, b * nrhs, flags)
+        g = ctx.graph_capture_end()
+        work, unit = 2.0 * N * N * nrhs, "TFLOP/s"
     else:  # resid: one refinement residual over N = 16384, 16 rhs (FP64)
         N, nrhs = 16384, 16
         T = N // b

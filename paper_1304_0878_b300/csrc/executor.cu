@@ -255,19 +255,19 @@ __device__ __forceinline__ unsigned long long claim(const LaunchParams &p, uint6
     const uint64_t t0 = gtimer();
     uint32_t backoff = 0;
     for (uint32_t spin = 0;; ++spin) {
-        // one round trip: lanes < nlevels read their level's head and tail,
-        // lane 31 the sticky error word
+        // the sticky error word first (reading it in the same round trip as
+        // the level heads measured slower: it shares a line with the retire
+        // counter every retirement increments)
         int err = 0;
+        if (lane == 0) err = ld_rlx_i32(&ctl->error);
+        err = __shfl_sync(0xffffffffu, err, 0);
+        if (err) return kEmpty;
         unsigned long long h = 0, tl = 0;
         const bool mine = lane < p.nlevels;
         if (mine) {
             h = ld_rlx(&ctl->lvl[lane].head);
             tl = ld_rlx(&ctl->lvl[lane].tail);
-        } else if (lane == 31) {
-            err = ld_rlx_i32(&ctl->error);
         }
-        err = __shfl_sync(0xffffffffu, err, 31);
-        if (err) return kEmpty;
         const unsigned mask = __ballot_sync(0xffffffffu, mine && h < tl);
         if (mask) {
             const int lv = 31 - __clz(mask);

@@ -37,6 +37,7 @@ __device__ __forceinline__ void trsv_l_item(const TaskRec &t, int j, unsigned ch
     __syncthreads();
     for (int R0 = 0; R0 < b; R0 += 32) {
         Tc s = 0;
+#pragma unroll 8
         for (int q = warp; q < R0; q += 8) s += (Tc)L[(size_t)(R0 + lane) + (size_t)q * b] * ys[q];
         red[warp * 32 + lane] = s;
         for (int e = tid; e < 1024; e += kThreads) {
@@ -74,6 +75,7 @@ __device__ __forceinline__ void trsv_lt_item(const TaskRec &t, int j, unsigned c
         for (int r = warp; r < 32; r += 8) {
             Tc s = 0;
             const double *col = L + (size_t)(R0 + r) * b;
+#pragma unroll 8
             for (int q = R0 + 32 + lane; q < b; q += 32) s += (Tc)col[q] * ys[q];
             for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
             if (lane == 0) red[r] = s;
@@ -109,7 +111,7 @@ __device__ __forceinline__ void gemv_body(const TaskRec &t, int item, unsigned c
     const int b = (int)t.n, nrhs = vk_nrhs(t), tid = threadIdx.x;
     const int r = tid & 63, g = tid >> 6, r0 = item * 64;
     Tc *Ys = (Tc *)smem;                 // [nrhs][64]
-    Tc *Lc = Ys + 64 * 32;               // [64][65] (trans only)
+    Tc *Lc = Ys + 64 * 32;               // [64][65]: Lc[r*65 + q] = M(r0 + r, q0 + q)
     Tc acc[NM];
 #pragma unroll
     for (int m = 0; m < NM; ++m) acc[m] = 0;
@@ -118,16 +120,23 @@ __device__ __forceinline__ void gemv_body(const TaskRec &t, int item, unsigned c
             const int q = e & 63, jj = e >> 6;
             Ys[jj * 64 + q] = (Tc)Yk[(size_t)jj * b + q0 + q];
         }
+        // the 64 x 64 block of M in shared memory: 16 independent coalesced
+        // loads per thread, so the block arrives in about one memory latency
         if (trans) {
             for (int e = tid; e < 64 * 64; e += kThreads) {
                 const int q = e & 63, rr = e >> 6;
                 Lc[rr * 65 + q] = (Tc)L[(size_t)(q0 + q) + (size_t)(r0 + rr) * b];
             }
+        } else {
+            for (int e = tid; e < 64 * 64; e += kThreads) {
+                const int rr = e & 63, q = e >> 6;
+                Lc[rr * 65 + q] = (Tc)L[(size_t)(r0 + rr) + (size_t)(q0 + q) * b];
+            }
         }
         __syncthreads();
 #pragma unroll 4
         for (int q = 0; q < 64; ++q) {
-            const Tc a = trans ? Lc[r * 65 + q] : (Tc)L[(size_t)(r0 + r) + (size_t)(q0 + q) * b];
+            const Tc a = Lc[r * 65 + q];
 #pragma unroll
             for (int m = 0; m < NM; ++m) {
                 const int jj = g + 4 * m;
