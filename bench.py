@@ -608,7 +608,8 @@ def run_case(args):
         g = ctx.graph_capture_end()
         work, unit = 8.0 * n * nb * nk, "GB/s"
     elif args.case.startswith("solve"):
-        # forward + backward solve with a tiled factor, N = 16384, 16 rhs
+        # forward + backward solve with a tiled factor and its inverted
+        # diagonal tiles (the refinement's solve), N = 16384, 16 rhs
         N, nrhs = 16384, 16
         T = N // b
         L = synth.spd_tiles_device(N, b, 3, 0.1, dev)
@@ -619,9 +620,14 @@ def run_case(args):
         ctx.task_wait()
         ctx.graph_destroy(gl)
         Y = torch.randn((T, nrhs, b), dtype=torch.float64, device=dev)
+        Z = torch.zeros_like(Y)
+        U = torch.empty((T, b, b), dtype=torch.float64, device=dev)
+        ctx.chol_inv_submit(dt.tile_ptrs(L), dt.tile_ptrs(U), T, b)     # once per factor, not timed
+        ctx.task_wait()
         flags = b3t.VEC_F32 if args.case.endswith("f32") else 0
         ctx.graph_capture_begin()
-        ctx.chol_solve_submit(dt.tile_ptrs(L), Y.data_ptr(), T, b, nrhs, b * nrhs, flags)
+        ctx.chol_solve_inv_submit(dt.tile_ptrs(L), dt.tile_ptrs(U), Y.data_ptr(), Z.data_ptr(), T, b, nrhs,
+                                  b * nrhs, flags)
         g = ctx.graph_capture_end()
         work, unit = 2.0 * N * N * nrhs, "TFLOP/s"
     else:  # resid: one refinement residual over N = 16384, 16 rhs (FP64)

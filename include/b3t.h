@@ -116,7 +116,8 @@ enum b3t_kind {
     B3T_POTRF_D = 18,
     B3T_PANEL_TRSM = 19,
     B3T_PANEL_UPD = 20,
-    B3T_CVT = 21
+    B3T_CVT = 21,
+    B3T_TRTRI = 22
 };
 
 /* Diagonal tile split into column panels.  A b x b diagonal tile partitioned
@@ -133,7 +134,13 @@ enum b3t_kind {
  *                  r >= jj*pw (lower part on the diagonal block)
  *  Scalars: struct b3t_panel_args; col0 offsets POTRF info like B3T_POTRF.
  *  B3T_CVT         W_kk (R, f32 tile), L_kk (W, f64 tile): L = fp64(W) on the
- *                  lower triangle, 0 above; no scalars. */
+ *                  lower triangle, 0 above; no scalars.
+ *  B3T_TRTRI       L_kk (R, f64 tile), U_k (W, f64 tile): U_k = L_kk^{-T}
+ *                  (upper triangular; 0 below the diagonal), computed in FP64
+ *                  by substitution against the identity; no scalars.  The
+ *                  solves of the refinement use it so that every diagonal
+ *                  step is a triangular multiply (Section 2's tasks over
+ *                  registered buffers; the inverse is this build's choice). */
 typedef struct b3t_panel_args {
     int32_t b, pw, kk, jj, col0;
 } b3t_panel_args;
@@ -145,7 +152,9 @@ typedef struct b3t_panel_args {
  *  B3T_GEMV_L   L_ik (R), Y_k (R), Y_i (RW)           Y_i <- Y_i - L_ik Y_k
  *  B3T_TRSV_LT  L_kk (R), Y_k (RW)                    Y_k <- L_kk^{-T} Y_k
  *  B3T_GEMV_LT  L_ki (R), Y_k (R), Y_i (RW)           Y_i <- Y_i - L_ki^T Y_k
- *               (flags bit 0: compute in binary32, store FP64)
+ *               (flags bit 0: compute in binary32, store FP64; bit 1:
+ *               assign Y_i <- M Y_k instead of subtracting; bit 2 / bit 3:
+ *               M is lower / upper triangular, so zero blocks are skipped)
  *  B3T_AXPY     X_i (RW), D_i (R)                     X_i <- X_i + D_i
  *               (flags bit 1: X_i <- D_i)
  *  B3T_RESID    A (R, all T(T+1)/2 packed f64 tiles as one buffer), X (R,
@@ -160,7 +169,7 @@ typedef struct b3t_panel_args {
 typedef struct b3t_vec_args {
     int32_t nrhs, flags, i, T, b;
 } b3t_vec_args;
-enum { B3T_VEC_F32 = 1, B3T_VEC_ASSIGN = 2 };
+enum { B3T_VEC_F32 = 1, B3T_VEC_ASSIGN = 2, B3T_VEC_LOWER_M = 4, B3T_VEC_UPPER_M = 8 };
 
 /* Low-precision formats of the Q tiles. */
 enum b3t_fmt { B3T_FMT_BF16 = 0, B3T_FMT_E4M3 = 1 };
@@ -346,11 +355,42 @@ B3T_API int b3t_cholesky_mx_submit(b3t_ctx *ctx, float *const *W, double *const 
 B3T_API int b3t_chol_solve_submit(b3t_ctx *ctx, double *const *L, double *Y, int32_t T, int32_t b,
                                   int32_t nrhs, int64_t part_stride, int32_t flags);
 
-/* Elements (f64) of the residual work area b3t_ir_solve needs. */
+/* U_k <- L_kk^{-T} for the T diagonal tiles of a tiled Cholesky factor
+ * (TRTRI tasks, one per tile, 32-row items).  L: T(T+1)/2 f64 tile pointers
+ * (packed order); U: T f64 tile pointers (b x b each, caller-owned); both
+ * registered here if they are not already.  Returns 0 or -EINVAL (shape,
+ * b not a multiple of 64). */
+B3T_API int b3t_chol_inv_submit(b3t_ctx *ctx, double *const *L, double *const *U, int32_t T, int32_t b);
+
+/* Y <- (L L^T)^{-1} Y with the inverted diagonal tiles U (from
+ * b3t_chol_inv_submit, which must have been submitted earlier on this
+ * context; the dependency on it is derived from the U registrations):
+ *   forward, k ascending:   Z_k = U_k^T Y_k (GEMV_LT, assign, lower M);
+ *                           Y_i -= L_ik Z_k for i > k (GEMV_L)
+ *   backward, k descending: Y_k = U_k Z_k (GEMV_L, assign, upper M);
+ *                           Z_i -= L_ki^T Y_k for i < k (GEMV_LT)
+ * Y, Z: device f64 block vectors of T parts part_stride elements apart
+ * (>= b*nrhs); Z is scratch.  Every step splits into 64-row items, so no
+ * task runs a row-by-row substitution.  flags: B3T_VEC_F32. */
+B3T_API int b3t_chol_solve_inv_submit(b3t_ctx *ctx, double *const *L, double *const *U, double *Y,
+                                      double *Z, int32_t T, int32_t b, int32_t nrhs, int64_t part_stride,
+                                      int32_t flags);
+
+/* Elements (f64) of the work area b3t_ir_solve and b3t_ir_step_submit need:
+ * the residual parts (b*nrhs values plus per-item norm partials each), a
+ * scratch block vector and the T inverted diagonal tiles of the factor, each
+ * region 256-byte aligned.  0 for invalid arguments. */
 B3T_API size_t b3t_ir_work_elems(int32_t T, int32_t b, int32_t nrhs);
 
+/* Forget the registrations the refinement helpers made inside the work area
+ * R (residual parts, scratch vector, inverted tiles), so that the memory can
+ * be freed and reused.  Waits for pending tasks (outside stream mode); in
+ * stream mode returns -EBUSY while a batch still uses them. */
+B3T_API int b3t_ir_release(b3t_ctx *ctx, double *R, int32_t T, int32_t b, int32_t nrhs);
+
 /* Iterative refinement, each step a task graph run by the executor:
- *   x_0 = 0, r_0 = b;  repeat  d = (L L^T)^{-1} r (solve tasks),
+ *   x_0 = 0, r_0 = b, U_k = L_kk^{-T} (TRTRI);  repeat  d = (L L^T)^{-1} r
+ *   (solve tasks with the inverted diagonal tiles),
  *   x += d (AXPY), r = b - A x in FP64 (RESID), eta (NRM)
  * until eta <= tol (returns 0), max_iter steps (-ERANGE) or no progress
  * (eta above 0.9 x its previous value: -ERANGE).  A_packed: the original

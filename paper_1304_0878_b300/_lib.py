@@ -22,7 +22,8 @@ POTRF_MX, TRSM_MX, SYRK_MX, GEMM_MX, QUANT = 6, 7, 8, 9, 10
 FMT_BF16, FMT_E4M3 = 0, 1
 PRIO_UPWARD, PRIO_DEPTH = 0, 1
 TRSV_L, GEMV_L, TRSV_LT, GEMV_LT, AXPY, RESID, NRM = 11, 12, 13, 14, 15, 16, 17
-VEC_F32, VEC_ASSIGN = 1, 2
+VEC_F32, VEC_ASSIGN, VEC_LOWER_M, VEC_UPPER_M = 1, 2, 4, 8
+POTRF_D, PANEL_TRSM, PANEL_UPD, CVT, TRTRI = 18, 19, 20, 21, 22
 
 
 class B3TError(RuntimeError):
@@ -78,6 +79,10 @@ _SIGS = {
     "b3t_stream_close": (ctypes.c_int, [_vp]),
     "b3t_chol_solve_submit": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), _vp, _i32, _i32, _i32, _i64, _i32]),
     "b3t_ir_work_elems": (_sz, [_i32, _i32, _i32]),
+    "b3t_chol_inv_submit": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i32, _i32]),
+    "b3t_chol_solve_inv_submit": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp, _vp, _i32,
+                                                 _i32, _i32, _i64, _i32]),
+    "b3t_ir_release": (ctypes.c_int, [_vp, _vp, _i32, _i32, _i32]),
     "b3t_ir_step_submit": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_vp), _vp, _vp, _vp, _vp, _i32, _i32,
                                           _i32, _i32, _i32]),
     "b3t_ir_solve": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_vp), _vp, _vp, _vp, _vp, _i32, _i32, _i32,
@@ -285,6 +290,17 @@ class Context:
     def chol_solve_submit(self, L_ptrs, Y_ptr, T, b, nrhs, part_stride, flags=0):
         _check(lib().b3t_chol_solve_submit(self._h, _ptrs(L_ptrs), _vp(int(Y_ptr)), T, b, nrhs,
                                            part_stride, flags), "b3t_chol_solve_submit")
+
+    def chol_inv_submit(self, L_ptrs, U_ptrs, T, b):
+        _check(lib().b3t_chol_inv_submit(self._h, _ptrs(L_ptrs), _ptrs(U_ptrs), T, b), "b3t_chol_inv_submit")
+
+    def chol_solve_inv_submit(self, L_ptrs, U_ptrs, Y_ptr, Z_ptr, T, b, nrhs, part_stride, flags=0):
+        _check(lib().b3t_chol_solve_inv_submit(self._h, _ptrs(L_ptrs), _ptrs(U_ptrs), _vp(int(Y_ptr)),
+                                               _vp(int(Z_ptr)), T, b, nrhs, part_stride, flags),
+               "b3t_chol_solve_inv_submit")
+
+    def ir_release(self, R_ptr, T, b, nrhs):
+        _check(lib().b3t_ir_release(self._h, _vp(int(R_ptr)), T, b, nrhs), "b3t_ir_release")
 
     def ir_solve(self, A_ptr, L_ptrs, B_ptr, X_ptr, R_ptr, eta_ptr, T, b, nrhs, flags=0, tol=1e-12,
                  max_iter=30):

@@ -35,6 +35,9 @@ struct VecArgs {
     int32_t b;        // rows per block (tile size)
 };
 constexpr int32_t kVecF32 = 1, kVecAssign = 2;
+// GEMV with a triangular matrix M: only the 64-column blocks that can hold
+// nonzeros are visited (lower: q <= r, upper: q >= r)
+constexpr int32_t kVecLowerM = 4, kVecUpperM = 8;
 
 struct PanelArgs {
     int32_t b, pw, kk, jj, col0;
@@ -51,8 +54,8 @@ enum : int32_t {
     kNoop = 0, kScalF32 = 1, kPotrf = 2, kTrsm = 3, kSyrk = 4, kGemm = 5,
     kPotrfMx = 6, kTrsmMx = 7, kSyrkMx = 8, kGemmMx = 9, kQuant = 10,
     kTrsvL = 11, kGemvL = 12, kTrsvLT = 13, kGemvLT = 14, kAxpy = 15, kResid = 16, kNrm = 17,
-    kPotrfD = 18, kPanelTrsm = 19, kPanelUpd = 20, kCvt = 21,
-    kNumKinds = 22
+    kPotrfD = 18, kPanelTrsm = 19, kPanelUpd = 20, kCvt = 21, kTrtri = 22,
+    kNumKinds = 23
 };
 
 // One task as the device sees it: 64 bytes.

@@ -497,6 +497,7 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
             break;
         }
         case kTrsmMx: trsm_mx_item(rec, it, (double *)smem); break;
+        case kTrtri: trtri_item(rec, it, (double *)smem); break;
         case kPotrfD: {
             const int info = potrf_d_item(rec, (double *)smem, &s_info);
             if (info) st = rec.aux + info;

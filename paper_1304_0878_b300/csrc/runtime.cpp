@@ -121,12 +121,13 @@ const KindSig kSigs[kNumKinds] = {
     /* PANEL_TR */ {1, {B3T_RW}, {8}, sizeof(PanelArgs), false},
     /* PANEL_UP */ {2, {B3T_R, B3T_RW}, {8, 8}, sizeof(PanelArgs), false},
     /* CVT      */ {2, {B3T_R, B3T_W}, {4, 8}, 0, true},
+    /* TRTRI    */ {2, {B3T_R, B3T_W}, {8, 8}, 0, true},
 };
 
 const char *kKindNames[kNumKinds] = {"noop", "scal_f32", "potrf", "trsm", "syrk", "gemm",
                                      "potrf_mx", "trsm_mx", "syrk_mx", "gemm_mx", "quant",
                                      "trsv_l", "gemv_l", "trsv_lt", "gemv_lt", "axpy", "resid", "nrm",
-                                     "potrf_d", "panel_trsm", "panel_upd", "cvt"};
+                                     "potrf_d", "panel_trsm", "panel_upd", "cvt", "trtri"};
 bool is_panel(int kind) { return kind >= kPotrfD && kind <= kPanelUpd; }
 bool is_vec(int kind) { return kind >= kTrsvL && kind <= kNrm; }
 
@@ -137,7 +138,7 @@ int64_t items_of(int kind, int64_t n) {
     switch (kind) {
     case kScalF32: return std::max<int64_t>(1, (n + kScalChunk - 1) / kScalChunk);
     case kPotrf: case kPotrfMx: case kQuant: case kNoop: case kCvt: return 1;
-    case kTrsm: case kTrsmMx: return n / kTrsmRows;
+    case kTrsm: case kTrsmMx: case kTrtri: return n / kTrsmRows;
     case kSyrk: { int64_t m = n / kGemmBlk; return m * (m + 1) / 2; }
     case kGemm: { int64_t m = n / kGemmBlk; return m * m; }
     case kSyrkMx: { int64_t m = n / kMxBlk; return m * (m + 1) / 2; }
@@ -172,6 +173,7 @@ float cost_of(int kind, int64_t n, int nrhs = 1, int T = 1, bool f32 = false) {
     case kResid: return (float)(2.0 * b * b * T * nrhs / 3.7);
     case kNrm: return 5000.0f;
     case kCvt: return (float)(12.0 * b * b / 20.0);
+    case kTrtri: return (float)(b * b * b / fp64);    // the first item's share dominates
     }
     return 1000.0f;
 }
@@ -540,7 +542,7 @@ int submit_impl(b3t_ctx *c, b3t_codelet cl, const b3t_handle *handles, const uin
         const int fmt = has_fmt(C.kind) ? r.aux : 0;
         if (fmt != B3T_FMT_BF16 && fmt != B3T_FMT_E4M3) return -EINVAL;
         if (b <= 0 || b % kGemmBlk || b > 4096) return -EINVAL;
-        if (C.kind >= kPotrfMx && b % kMxBlk) return -EINVAL;
+        if (((C.kind >= kPotrfMx && C.kind <= kQuant) || C.kind == kCvt) && b % kMxBlk) return -EINVAL;
         for (int i = 0; i < nbuffers; ++i) {
             const Handle &H = c->handles[handles[i]];
             if (H.ld != b || r.buf[i] % 16) return -EINVAL;
@@ -586,7 +588,7 @@ int submit_impl(b3t_ctx *c, b3t_codelet cl, const b3t_handle *handles, const uin
     if (is_vec(C.kind)) {
         VecArgs v;
         std::memcpy(&v, scalars, sizeof(v));
-        if (v.nrhs < 1 || v.nrhs > kMaxRhs || v.flags < 0 || v.flags > 3 || v.T < 1 || v.T > 65535 ||
+        if (v.nrhs < 1 || v.nrhs > kMaxRhs || v.flags < 0 || v.flags > 15 || v.T < 1 || v.T > 65535 ||
             v.i < 0 || v.i >= v.T || v.b < 64 || v.b > 4096 || v.b % 64)
             return -EINVAL;
         const size_t b = (size_t)v.b, blk = b * v.nrhs, T = (size_t)v.T;
@@ -1417,32 +1419,144 @@ int b3t_chol_solve_submit(b3t_ctx *c, double *const *L, double *Y, int32_t T, in
     return rc;
 }
 
+// U_k <- L_kk^{-T} for every diagonal tile (TRTRI tasks).
+static int submit_inv(b3t_ctx *c, const std::vector<b3t_handle> &hl, const std::vector<b3t_handle> &hu,
+                      int32_t T) {
+    b3t_codelet ci;
+    int rc = kind_codelet(c, kTrtri, &ci);
+    if (rc) return rc;
+    for (int32_t k = 0; k < T; ++k) {
+        const b3t_handle h2[2] = {hl[tidx(k, k, T)], hu[k]};
+        if ((rc = submit_impl(c, ci, h2, nullptr, 2, nullptr, 0))) return rc;
+    }
+    return 0;
+}
+
+// Solve with inverted diagonal tiles (U_k = L_kk^{-T}).  Forward, k
+// ascending: Z_k = L_kk^{-1} Y_k, then Y_i -= L_ik Z_k below; backward, k
+// descending: Y_k = L_kk^{-T} Z_k, then Z_i -= L_ki^T Y_k above.  The
+// solution ends in Y.  Each diagonal step is a triangular multiply split
+// into 64-row items instead of a substitution that runs row after row.
+static int submit_solve_inv(b3t_ctx *c, const std::vector<b3t_handle> &hl, const std::vector<b3t_handle> &hu,
+                            const std::vector<b3t_handle> &hy, const std::vector<b3t_handle> &hz, int32_t T,
+                            int32_t b, int32_t nrhs, int32_t flags) {
+    b3t_codelet gl, glt;
+    int rc;
+    if ((rc = kind_codelet(c, kGemvL, &gl)) || (rc = kind_codelet(c, kGemvLT, &glt))) return rc;
+    const int32_t f32 = flags & kVecF32;
+    const VecArgs v{nrhs, f32, 0, T, b};
+    const VecArgs vf{nrhs, f32 | kVecAssign | kVecLowerM, 0, T, b};   // M = U_k^T = L_kk^{-1}
+    const VecArgs vb{nrhs, f32 | kVecAssign | kVecUpperM, 0, T, b};   // M = U_k = L_kk^{-T}
+    for (int32_t k = 0; k < T; ++k) {
+        const b3t_handle h3[3] = {hu[k], hy[k], hz[k]};
+        if ((rc = submit_impl(c, glt, h3, nullptr, 3, &vf, sizeof(vf)))) return rc;
+        for (int32_t i = k + 1; i < T; ++i) {
+            const b3t_handle g3[3] = {hl[tidx(i, k, T)], hz[k], hy[i]};
+            if ((rc = submit_impl(c, gl, g3, nullptr, 3, &v, sizeof(v)))) return rc;
+        }
+    }
+    for (int32_t k = T - 1; k >= 0; --k) {
+        const b3t_handle h3[3] = {hu[k], hz[k], hy[k]};
+        if ((rc = submit_impl(c, gl, h3, nullptr, 3, &vb, sizeof(vb)))) return rc;
+        for (int32_t i = 0; i < k; ++i) {
+            const b3t_handle g3[3] = {hl[tidx(k, i, T)], hy[k], hz[i]};
+            if ((rc = submit_impl(c, glt, g3, nullptr, 3, &v, sizeof(v)))) return rc;
+        }
+    }
+    return 0;
+}
+
+int b3t_chol_inv_submit(b3t_ctx *c, double *const *L, double *const *U, int32_t T, int32_t b) {
+    if (!c || !L || !U || T <= 0 || b <= 0 || b % 64) return -EINVAL;
+    std::vector<b3t_handle> hl, hu;
+    int rc = reg_tiles(c, (void *const *)L, (int64_t)T * (T + 1) / 2, (size_t)b * b, 8, b, hl);
+    if (!rc) rc = reg_tiles(c, (void *const *)U, T, (size_t)b * b, 8, b, hu);
+    if (!rc) rc = submit_inv(c, hl, hu, T);
+    return rc;
+}
+
+int b3t_chol_solve_inv_submit(b3t_ctx *c, double *const *L, double *const *U, double *Y, double *Z, int32_t T,
+                              int32_t b, int32_t nrhs, int64_t part_stride, int32_t flags) {
+    if (!c || !L || !U || !Y || !Z || T <= 0 || b <= 0 || b % 64 || nrhs < 1 || nrhs > kMaxRhs ||
+        part_stride < (int64_t)b * nrhs)
+        return -EINVAL;
+    std::vector<b3t_handle> hl, hu, hy, hz;
+    b3t_handle hyp, hzp;
+    int rc = reg_tiles(c, (void *const *)L, (int64_t)T * (T + 1) / 2, (size_t)b * b, 8, b, hl);
+    if (!rc) rc = reg_tiles(c, (void *const *)U, T, (size_t)b * b, 8, b, hu);
+    if (!rc) rc = reg_parted(c, Y, T, (size_t)part_stride, &hyp, hy);
+    if (!rc) rc = reg_parted(c, Z, T, (size_t)part_stride, &hzp, hz);
+    if (!rc) rc = submit_solve_inv(c, hl, hu, hy, hz, T, b, nrhs, flags);
+    return rc;
+}
+
+// Refinement workspace: [T residual parts] [Z: T parts of b x nrhs]
+// [U: T tiles of b x b], each region starting on a 256-byte boundary.
+static size_t round32(size_t n) { return (n + 31) / 32 * 32; }
+static size_t ir_z_off(int32_t T, int32_t b, int32_t nrhs) {
+    return round32((size_t)T * (size_t)resid_part_elems(b, nrhs));
+}
+static size_t ir_u_off(int32_t T, int32_t b, int32_t nrhs) {
+    return ir_z_off(T, b, nrhs) + round32((size_t)T * b * nrhs);
+}
+
 size_t b3t_ir_work_elems(int32_t T, int32_t b, int32_t nrhs) {
     if (T <= 0 || b <= 0 || b % 64 || nrhs < 1 || nrhs > kMaxRhs) return 0;
-    return (size_t)T * (size_t)resid_part_elems(b, nrhs);
+    return ir_u_off(T, b, nrhs) + (size_t)T * b * b;
 }
 
 // Registration shared by the refinement helpers.
 struct IrHandles {
-    std::vector<b3t_handle> hl, hx, hr;
-    b3t_handle ha, hxp, hrp, hbp, he;
+    std::vector<b3t_handle> hl, hx, hr, hz, hu;
+    b3t_handle ha, hxp, hrp, hbp, he, hzp;
 };
+
+static std::vector<double *> ir_u_tiles(double *R, int32_t T, int32_t b, int32_t nrhs) {
+    std::vector<double *> u(T);
+    for (int32_t k = 0; k < T; ++k) u[k] = R + ir_u_off(T, b, nrhs) + (size_t)k * b * b;
+    return u;
+}
 
 static int ir_register(b3t_ctx *c, const double *A, double *const *L, const double *B, double *X, double *R,
                        double *eta, int32_t T, int32_t b, int32_t nrhs, IrHandles &H) {
     const int64_t nt = (int64_t)T * (T + 1) / 2;
     const size_t blk = (size_t)b * nrhs, PR = (size_t)resid_part_elems(b, nrhs);
+    const std::vector<double *> u = ir_u_tiles(R, T, b, nrhs);
     int rc = reg_tiles(c, (void *const *)L, nt, (size_t)b * b, 8, b, H.hl);
     if (!rc) rc = reg_vec(c, A, (size_t)nt * b * b, &H.ha);
     if (!rc) rc = reg_parted(c, X, T, blk, &H.hxp, H.hx);
     if (!rc) rc = reg_vec(c, B, (size_t)T * blk, &H.hbp);
     if (!rc) rc = reg_parted(c, R, T, PR, &H.hrp, H.hr);
+    if (!rc) rc = reg_parted(c, R + ir_z_off(T, b, nrhs), T, blk, &H.hzp, H.hz);
+    if (!rc) rc = reg_tiles(c, (void *const *)u.data(), T, (size_t)b * b, 8, b, H.hu);
     if (!rc) rc = reg_vec(c, eta, (size_t)nrhs + 1, &H.he);
     return rc;
 }
 
-// One refinement step: [first: r = b]; d = (L L^T)^{-1} r; x (+)= d;
-// r = b - A x; eta.
+int b3t_ir_release(b3t_ctx *c, double *R, int32_t T, int32_t b, int32_t nrhs) {
+    if (!c || !R || T <= 0 || b <= 0 || b % 64 || nrhs < 1 || nrhs > kMaxRhs) return -EINVAL;
+    const std::vector<double *> u = ir_u_tiles(R, T, b, nrhs);
+    void *const regions[2] = {R, R + ir_z_off(T, b, nrhs)};
+    if (c->st.open) {
+        b3t_handle h;
+        for (void *p : regions)
+            if (b3t_data_lookup(c, p, &h) == 0 && stream_handle_busy(c, h)) return -EBUSY;
+        for (double *p : u)
+            if (b3t_data_lookup(c, p, &h) == 0 && stream_handle_busy(c, h)) return -EBUSY;
+    } else if (!c->capturing) {
+        const int rc = wait_impl(c, 0);
+        if (rc) return rc;
+    }
+    b3t_handle h;
+    for (void *p : regions)
+        if (b3t_data_lookup(c, p, &h) == 0) drop_handle(c, h);
+    for (double *p : u)
+        if (b3t_data_lookup(c, p, &h) == 0) drop_handle(c, h);
+    return 0;
+}
+
+// One refinement step: [first: r = b, U_k = L_kk^{-T}]; d = (L L^T)^{-1} r
+// (with the inverted diagonal tiles); x (+)= d; r = b - A x; eta.
 static int ir_step(b3t_ctx *c, IrHandles &H, int32_t T, int32_t b, int32_t nrhs, int32_t flags, bool first) {
     b3t_codelet cres, cax, cnrm;
     int rc;
@@ -1459,7 +1573,8 @@ static int ir_step(b3t_ctx *c, IrHandles &H, int32_t T, int32_t b, int32_t nrhs,
         return 0;
     };
     if (first && (rc = resid(kVecAssign))) return rc;          // r_0 = b (x_0 = 0)
-    if ((rc = submit_solve(c, H.hl, H.hr, T, b, nrhs, flags))) return rc;
+    if (first && (rc = submit_inv(c, H.hl, H.hu, T))) return rc;   // U_k = L_kk^{-T}, kept for later steps
+    if ((rc = submit_solve_inv(c, H.hl, H.hu, H.hr, H.hz, T, b, nrhs, flags))) return rc;
     for (int32_t i = 0; i < T; ++i) {
         VecArgs v{nrhs, first ? kVecAssign : 0, i, T, b};
         const b3t_handle h2[2] = {H.hx[i], H.hr[i]};

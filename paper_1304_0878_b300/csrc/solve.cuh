@@ -6,6 +6,8 @@
 //   GEMV_L  : Y_i <- Y_i - L_ik Y_k           item = 64 rows of Y_i
 //   TRSV_LT : Y_k <- L_kk^{-T} Y_k            item = one right-hand side
 //   GEMV_LT : Y_i <- Y_i - L_ki^T Y_k         item = 64 rows of Y_i
+//             (flags: assign Y_i <- M Y_k instead; M lower or upper
+//             triangular, so that blocks of zeros are skipped)
 //   AXPY    : X_i <- X_i + D_i (or X_i = D_i) one item
 //   RESID   : R_i <- B_i - (A X)_i, FP64, with A symmetric and only its lower
 //             tiles stored; also per-item maxima |R|, |X_i| and the largest
@@ -112,10 +114,14 @@ __device__ __forceinline__ void gemv_body(const TaskRec &t, int item, unsigned c
     const int r = tid & 63, g = tid >> 6, r0 = item * 64;
     Tc *Ys = (Tc *)smem;                 // [nrhs][64]
     Tc *Lc = Ys + 64 * 32;               // [64][65]: Lc[r*65 + q] = M(r0 + r, q0 + q)
+    const int fl = vk_flags(t);
+    // a triangular M has nonzeros only in the blocks q0 <= r0 (lower) or
+    // q0 >= r0 (upper)
+    const int qa = (fl & kVecUpperM) ? r0 : 0, qb = (fl & kVecLowerM) ? r0 + 64 : b;
     Tc acc[NM];
 #pragma unroll
     for (int m = 0; m < NM; ++m) acc[m] = 0;
-    for (int q0 = 0; q0 < b; q0 += 64) {
+    for (int q0 = qa; q0 < qb; q0 += 64) {
         for (int e = tid; e < 64 * nrhs; e += kThreads) {
             const int q = e & 63, jj = e >> 6;
             Ys[jj * 64 + q] = (Tc)Yk[(size_t)jj * b + q0 + q];
@@ -145,12 +151,13 @@ __device__ __forceinline__ void gemv_body(const TaskRec &t, int item, unsigned c
         }
         __syncthreads();
     }
+    const bool assign = fl & kVecAssign;
 #pragma unroll
     for (int m = 0; m < NM; ++m) {
         const int jj = g + 4 * m;
         if (jj < nrhs) {
             double *p = Yi + (size_t)jj * b + r0 + r;
-            *p = *p - (double)acc[m];
+            *p = assign ? (double)acc[m] : *p - (double)acc[m];
         }
     }
 }

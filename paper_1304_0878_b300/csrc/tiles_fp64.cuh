@@ -97,10 +97,14 @@ __device__ __forceinline__ void syrk_item(const TaskRec &t, int item, double *sm
 // Ain is the input (f64, or f32 for the mixed-precision panel), X the f64
 // output (may alias Ain when Tin is double), L the n x n lower factor; all
 // column-major with leading dimension ld.
-template <typename Tin>
+// kIdent: the input rows are rows r0.. of the identity (Ain is not read), so
+// X rows are rows of L^{-T}: columns before the 64-block holding r0 are zero
+// and are written as zeros without being computed.
+template <typename Tin, bool kIdent = false>
 __device__ __forceinline__ void trsm_rows(const double *L, const Tin *Ain, double *X, int r0, int n, int ld,
                                           double *smem) {
     const int b = ld;
+    const int cs = kIdent ? (r0 / 64) * 64 : 0;     // first column block that can be nonzero
     constexpr int RB = kTrsmRows;           // 32 rows
     double *Lcb = smem;                     // [64][65]  Lcb[c*65 + q] = L(c0+c, c0+q)
     double *Acc = Lcb + 64 * 65;            // [64][33]  Acc[c*33 + r]
@@ -108,12 +112,20 @@ __device__ __forceinline__ void trsm_rows(const double *L, const Tin *Ain, doubl
     double *Ls = Xs + kKc * 33;             // [kKc][64] Ls[p*64 + c] = L(c0+c, k0+p)
     const int tid = threadIdx.x;
     const int tr = tid & 31, tw = tid >> 5;     // row, column group
-    for (int c0 = 0; c0 < n; c0 += 64) {
+    if (kIdent) {
+        for (int c0 = 0; c0 < cs; c0 += 64) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) X[(size_t)(r0 + tr) + (size_t)(c0 + tw + 8 * j) * b] = 0.0;
+        }
+    }
+    for (int c0 = cs; c0 < n; c0 += 64) {
         double acc[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-            acc[j] = (double)Ain[(size_t)(r0 + tr) + (size_t)(c0 + tw + 8 * j) * b];
-        for (int k0 = 0; k0 < c0; k0 += kKc) {
+        for (int j = 0; j < 8; ++j) {
+            if (kIdent) acc[j] = (r0 + tr == c0 + tw + 8 * j) ? 1.0 : 0.0;
+            else acc[j] = (double)Ain[(size_t)(r0 + tr) + (size_t)(c0 + tw + 8 * j) * b];
+        }
+        for (int k0 = cs; k0 < c0; k0 += kKc) {
 #pragma unroll
             for (int q = 0; q < (RB * kKc) / kThreads; ++q) {
                 const int e = tid + q * kThreads;
@@ -163,6 +175,13 @@ __device__ __forceinline__ void trsm_rows(const double *L, const Tin *Ain, doubl
 __device__ __forceinline__ void trsm_item(const TaskRec &t, int item, double *smem) {
     double *A = (double *)t.buf[1];
     trsm_rows<double>((const double *)t.buf[0], A, A, item * kTrsmRows, (int)t.n, (int)t.n, smem);
+}
+
+// TRTRI: U_k <- L_kk^{-T} (upper triangular, the strict lower part zero),
+// 32 rows of U_k (= 32 columns of L_kk^{-1}) per item.
+__device__ __forceinline__ void trtri_item(const TaskRec &t, int item, double *smem) {
+    trsm_rows<double, true>((const double *)t.buf[0], (const double *)nullptr, (double *)t.buf[1],
+                            item * kTrsmRows, (int)t.n, (int)t.n, smem);
 }
 
 __device__ __forceinline__ void trsm_mx_item(const TaskRec &t, int item, double *smem) {

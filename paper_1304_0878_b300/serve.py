@@ -32,6 +32,7 @@ import torch
 
 from . import tiles as dt
 from . import tune
+from . import _lib
 
 U64 = 8
 
@@ -41,7 +42,7 @@ def footprint(Np, nrhs, b, prec):
     T = Np // b
     tile = T * (T + 1) // 2 * b * b
     vec = T * b * nrhs * 8
-    work = T * (b * nrhs + (b // 32) * (2 * nrhs + 1)) * 8
+    work = _lib.ir_work_elems(T, b, nrhs) * 8             # residual parts, scratch, inverted tiles
     if prec == "fp64":
         mats = tile * 16                                   # A + factor
     else:
@@ -157,7 +158,8 @@ def release(ctx, req, keep_x=False, stream=None):
             req.x = req.bufs["X"].to("cpu", non_blocking=False)
     for p in req.ptrs.values():
         ctx.tiles_unregister(p, req.T)
-    for k in ("A", "B", "X", "R", "eta"):
+    ctx.ir_release(req.bufs["R"].data_ptr(), req.T, req.b, req.nrhs)
+    for k in ("A", "B", "X", "eta"):
         try:
             h = ctx.data_lookup(req.bufs[k].data_ptr())
             ctx.data_unregister(h)

@@ -46,6 +46,37 @@ def test_chol_solve_against_substitution(orc, gctx, nrhs, f32):
     assert err <= (1e-5 if f32 else 1e-13), err
 
 
+@pytest.mark.parametrize("nrhs", [1, 7, 16, 32])
+@pytest.mark.parametrize("f32", [False, True])
+def test_chol_solve_with_inverted_diagonal(orc, gctx, nrhs, f32):
+    # TRTRI: U_k = L_kk^{-T}, checked against forward substitution on the
+    # identity; then the inverse-based solve against substitution
+    N, b = 640, 128
+    T = N // b
+    A = synth.spd_host(N, seed=nrhs + 3, shift=1.0)
+    L = sla.cholesky(A, lower=True)
+    Bm = synth.rhs(N, nrhs, seed=4)
+    Lt = torch.from_numpy(och.to_tiles(L, b)).cuda()
+    U = torch.full((T, b, b), float("nan"), dtype=torch.float64, device="cuda")
+    Y = parts_from(Bm, b)
+    Z = torch.zeros_like(Y)
+    gctx.chol_inv_submit(dt.tile_ptrs(Lt), dt.tile_ptrs(U), T, b)
+    gctx.chol_solve_inv_submit(dt.tile_ptrs(Lt), dt.tile_ptrs(U), Y.data_ptr(), Z.data_ptr(), T, b, nrhs,
+                               b * nrhs, b3t.VEC_F32 if f32 else 0)
+    gctx.task_wait()
+    Uh = U.cpu().numpy()
+    for k in range(T):
+        Lkk = L[k * b:(k + 1) * b, k * b:(k + 1) * b]
+        Uk = Uh[k].T                                   # tile memory is column-major
+        Linv = oir.forward_sub(Lkk, np.eye(b))
+        assert np.all(np.tril(Uk, -1) == 0.0)
+        assert np.max(np.abs(Uk - Linv.T)) / np.max(np.abs(Linv)) <= 1e-13
+    got = dense_from(Y)
+    ref = oir.chol_solve(L, Bm)
+    err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+    assert err <= (1e-5 if f32 else 1e-12), err
+
+
 def test_residual_and_backward_error(orc, gctx):
     N, b, nrhs = 768, 256, 3
     T = N // b

@@ -227,3 +227,39 @@ def test_tiles_unregister_forgets_panel_parts(ctx):
     part1 = p + 256 * 128 * 8
     ctx.cholesky_submit([part1], 1, 128)
     assert ctx.dag_stats()[0] == 1
+
+
+@pytest.mark.parametrize("T", [1, 3, 6])
+def test_inverse_solve_edges(ctx, T):
+    # TRTRI per diagonal tile, then the solve with inverted diagonal tiles:
+    # forward Z_k = U_k^T Y_k, Y_i -= L_ik Z_k; backward Y_k = U_k Z_k,
+    # Z_i -= L_ki^T Y_k (Y and Z partitioned into T parts)
+    b, nrhs = 128, 4
+    L = [fake_ptr(i) for i in range(och.ntiles(T))]
+    U = [fake_ptr(1000 + k) for k in range(T)]
+    Y, Z = fake_ptr(2000), fake_ptr(3000)
+    ctx.chol_inv_submit(L, U, T, b)
+    ctx.chol_solve_inv_submit(L, U, Y, Z, T, b, nrhs, b * nrhs)
+    ti = lambda i, j: och.tile_index(i, j, T)    # noqa: E731
+    parts = {"Y": tuple(("Y", k) for k in range(T)), "Z": tuple(("Z", k) for k in range(T))}
+    acc = [[(ti(k, k), R), (("U", k), W)] for k in range(T)]
+    for k in range(T):
+        acc.append([(("U", k), R), (("Y", k), R), (("Z", k), RW)])
+        for i in range(k + 1, T):
+            acc.append([(ti(i, k), R), (("Z", k), R), (("Y", i), RW)])
+    for k in reversed(range(T)):
+        acc.append([(("U", k), R), (("Z", k), R), (("Y", k), RW)])
+        for i in range(k):
+            acc.append([(ti(k, i), R), (("Y", k), R), (("Z", i), RW)])
+    assert ctx.dag_stats()[0] == len(acc)
+    assert sorted(ctx.dag_edges()) == dag.derive_edges(acc, parts)
+
+
+def test_ir_work_elems_layout():
+    # residual parts, a scratch block vector and T inverted tiles, each
+    # region a multiple of 32 doubles from the start
+    T, b, nrhs = 5, 128, 3
+    part = b * nrhs + (b // 64) * (2 * nrhs + 1)
+    r32 = lambda n: (n + 31) // 32 * 32    # noqa: E731
+    assert b3t.ir_work_elems(T, b, nrhs) == r32(T * part) + r32(T * b * nrhs) + T * b * b
+    assert b3t.ir_work_elems(T, 100, nrhs) == 0
