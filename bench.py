@@ -636,12 +636,13 @@ def run_case(args):
         A = synth.spd_tiles_device(N, b, 3, 0.1, dev)
         X = torch.randn((T, nrhs, b), dtype=torch.float64, device=dev)
         B = torch.randn((T, nrhs, b), dtype=torch.float64, device=dev)
-        R = torch.zeros(b3t.ir_work_elems(T, b, nrhs), dtype=torch.float64, device=dev)
+        PR = b * nrhs + (b // 64) * (2 * nrhs + 1)     # residual part: values, then per-item maxima
+        R = torch.zeros(T * PR, dtype=torch.float64, device=dev)
         ha = ctx.data_register(A.data_ptr(), A.numel(), 8)
         hx = ctx.data_register(X.data_ptr(), X.numel(), 8)
         hb = ctx.data_register(B.data_ptr(), B.numel(), 8)
         hr = ctx.data_register(R.data_ptr(), R.numel(), 8)
-        pr = ctx.data_partition(hr, T, R.numel() // T)
+        pr = ctx.data_partition(hr, T, PR)
         cr = ctx.task_decl("resid", b3t.RESID, [1, 1, 1, 2], 20)
         ctx.graph_capture_begin()
         for i in range(T):

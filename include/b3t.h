@@ -158,12 +158,13 @@ typedef struct b3t_panel_args {
  *  B3T_AXPY     X_i (RW), D_i (R)                     X_i <- X_i + D_i
  *               (flags bit 1: X_i <- D_i)
  *  B3T_RESID    A (R, all T(T+1)/2 packed f64 tiles as one buffer), X (R,
- *               T parts), B (R, T parts), R_i (W, b3t_ir_work_elems / T
+ *               T parts), B (R, T parts), R_i (W, b*nrhs + (b/64)(2 nrhs + 1)
  *               elements): R_i <- B_i - (A X)_i in FP64 with A symmetric and
  *               only its lower tiles stored; after the b*nrhs values, R_i
  *               holds per 64-row item max|r_j|, max|x_j| and the largest
  *               row sum of |A| (flags bit 1: X taken as 0, R_i <- B_i)
- *  B3T_NRM      R (R, all parts), B (R), eta (W, nrhs + 1 f64):
+ *  B3T_NRM      R (R, the T residual parts back to back), B (R), eta (W,
+ *               nrhs + 1 f64):
  *               eta_j = max|r_j| / (||A||_inf max|x_j| + max|b_j|),
  *               eta[nrhs] = max_j eta_j (normwise backward error) */
 typedef struct b3t_vec_args {
@@ -354,6 +355,27 @@ B3T_API int b3t_cholesky_mx_submit(b3t_ctx *ctx, float *const *W, double *const 
  * it is not already.  flags: B3T_VEC_F32 for binary32 arithmetic. */
 B3T_API int b3t_chol_solve_submit(b3t_ctx *ctx, double *const *L, double *Y, int32_t T, int32_t b,
                                   int32_t nrhs, int64_t part_stride, int32_t flags);
+
+/* Tracing.  While it is on, every launch built (flushed, captured or opened
+ * in stream mode) records one b3t_trace_rec per finished work item: task id
+ * (index in its launch, or in the stream's task arena), item, SM, kind, and
+ * the item's start and end on the device clock (%globaltimer, ns).  Records
+ * beyond the capacity are counted but dropped.
+ *  b3t_trace_start  waits for pending work, (re)allocates room for capacity
+ *                   records (device memory, owned by the context, freed by
+ *                   b3t_shutdown), zeroes the count and turns tracing on.
+ *  b3t_trace_read   waits, copies min(count, capacity) records to host
+ *                   memory and sets *count to the number of items traced.
+ *  b3t_trace_stop   turns tracing off for launches built afterwards.
+ * -ENODEV on a host-only context, -ENOENT (read) before any start, -EBUSY
+ * while a stream is open. */
+typedef struct b3t_trace_rec {
+    int32_t task, item, sm, kind;
+    uint64_t t_start_ns, t_end_ns;
+} b3t_trace_rec;
+B3T_API int b3t_trace_start(b3t_ctx *ctx, int64_t capacity);
+B3T_API int b3t_trace_read(b3t_ctx *ctx, void *records, int64_t capacity, int64_t *count);
+B3T_API int b3t_trace_stop(b3t_ctx *ctx);
 
 /* U_k <- L_kk^{-T} for the T diagonal tiles of a tiled Cholesky factor
  * (TRTRI tasks, one per tile, 32-row items).  L: T(T+1)/2 f64 tile pointers

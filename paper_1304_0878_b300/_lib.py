@@ -83,6 +83,9 @@ _SIGS = {
     "b3t_chol_solve_inv_submit": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp, _vp, _i32,
                                                  _i32, _i32, _i64, _i32]),
     "b3t_ir_release": (ctypes.c_int, [_vp, _vp, _i32, _i32, _i32]),
+    "b3t_trace_start": (ctypes.c_int, [_vp, _i64]),
+    "b3t_trace_read": (ctypes.c_int, [_vp, _vp, _i64, ctypes.POINTER(_i64)]),
+    "b3t_trace_stop": (ctypes.c_int, [_vp]),
     "b3t_ir_step_submit": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_vp), _vp, _vp, _vp, _vp, _i32, _i32,
                                           _i32, _i32, _i32]),
     "b3t_ir_solve": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_vp), _vp, _vp, _vp, _vp, _i32, _i32, _i32,
@@ -298,6 +301,25 @@ class Context:
         _check(lib().b3t_chol_solve_inv_submit(self._h, _ptrs(L_ptrs), _ptrs(U_ptrs), _vp(int(Y_ptr)),
                                                _vp(int(Z_ptr)), T, b, nrhs, part_stride, flags),
                "b3t_chol_solve_inv_submit")
+
+    def trace_start(self, capacity=1 << 20):
+        _check(lib().b3t_trace_start(self._h, int(capacity)), "b3t_trace_start")
+        self._trace_cap = int(capacity)
+
+    def trace_read(self):
+        """The traced work items as a numpy structured array (task, item, sm,
+        kind, t_start_ns, t_end_ns)."""
+        import numpy as np
+        dt = np.dtype([("task", np.int32), ("item", np.int32), ("sm", np.int32), ("kind", np.int32),
+                       ("t_start_ns", np.uint64), ("t_end_ns", np.uint64)])
+        cap = getattr(self, "_trace_cap", 0)
+        buf = np.zeros(cap, dtype=dt)
+        n = _i64(0)
+        _check(lib().b3t_trace_read(self._h, _vp(buf.ctypes.data), cap, ctypes.byref(n)), "b3t_trace_read")
+        return buf[:min(n.value, cap)]
+
+    def trace_stop(self):
+        _check(lib().b3t_trace_stop(self._h), "b3t_trace_stop")
 
     def ir_release(self, R_ptr, T, b, nrhs):
         _check(lib().b3t_ir_release(self._h, _vp(int(R_ptr)), T, b, nrhs), "b3t_ir_release")

@@ -103,6 +103,13 @@ struct SubDesc {
     uint32_t batch;
 };
 
+// One traced work item (globaltimer ns on the CTA's SM).
+struct TraceRec {
+    int32_t task, item, sm, kind;
+    uint64_t t_start, t_end;
+};
+static_assert(sizeof(TraceRec) == 32, "TraceRec is 32 bytes");
+
 struct LaunchParams {
     const TaskRec *tasks;
     const int32_t *succ;         // CSR successor lists
@@ -130,6 +137,10 @@ struct LaunchParams {
     volatile int32_t *batch_done;   // host-mapped: 1 when a batch retired, 2 + info if a
                                     // POTRF of it met a non-positive pivot
     int64_t deadline_ns;
+    // tracing (null when off): one record per finished work item
+    TraceRec *trace;
+    unsigned long long *trace_n;
+    int64_t trace_cap;
 };
 
 // Init-kernel parameters: reset counters, rings and status for a launch.

@@ -462,6 +462,7 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
         __threadfence();   // acquire side for every thread of the CTA
         const int64_t t = (int64_t)(item >> 32);
         const int it = (int)(item & 0xffffffffu);
+        const uint64_t t_item = (p.trace && tid == 0) ? gtimer() : 0;
         if (p.debug && (t >= p.ntasks || it >= s_rec.nitems)) {
             if (tid == 0) set_error(p.ctl, EPROTO, (int)t, -1, 5);
             __syncthreads();
@@ -562,6 +563,14 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
                     nj = atomicAdd(&p.next_item[t], 1);
                     const int d = atomicAdd(&p.done_items[t], 1) + 1;
                     flag = d == rec.nitems;
+                }
+            }
+            if (p.trace && tid == 0) {
+                const unsigned long long k = atomicAdd(p.trace_n, 1ull);
+                if ((int64_t)k < p.trace_cap) {
+                    uint32_t sm;
+                    asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+                    p.trace[k] = TraceRec{(int32_t)t, it, (int32_t)sm, rec.kind, t_item, gtimer()};
                 }
             }
             flag = __shfl_sync(0xffffffffu, flag, 0);

@@ -211,6 +211,12 @@ struct b3t_ctx {
     int32_t err_task = -1, err_info = -1;
     std::vector<GraphRec> graphs;
     b3t_codelet kind_cl[kNumKinds];
+    // tracing: one record per finished work item of the launches built
+    // while it is on (device buffer; the count is the first 8 bytes)
+    TraceRec *trace = nullptr;
+    unsigned long long *trace_n = nullptr;
+    int64_t trace_cap = 0;
+    bool trace_on = false;
     // stream mode: one resident kernel fed with task graphs while it runs
     struct Stream {
         bool open = false;
@@ -399,6 +405,7 @@ int build_launch(b3t_ctx *c, Arena &a, InitParams &ip, LaunchParams &lp, int64_t
     lp.has_mx = has_mx ? 1 : 0;
     lp.timeout_ns = c->cfg.timeout_ns;
     lp.debug = c->cfg.debug_checks;
+    if (c->trace_on) { lp.trace = c->trace; lp.trace_n = c->trace_n; lp.trace_cap = c->trace_cap; }
     for (int l = 0; l < L; ++l) {
         ip.root_off[l] = rootoff[l]; ip.root_cnt[l] = rootcnt[l];
         lp.ring_off[l] = ringoff[l]; lp.ring_cap[l] = cap[l];
@@ -697,6 +704,7 @@ int b3t_shutdown(b3t_ctx *c) {
         g.arena.release();
     }
     c->arena.release();
+    if (c->trace_n) cudaFree(c->trace_n);
     if (c->staging) cudaFreeHost(c->staging);
     for (Ctl *m : c->mirrors) cudaFreeHost(m);
     cudaEventDestroy(c->ev0);
@@ -1047,6 +1055,7 @@ int b3t_stream_open(b3t_ctx *c, int64_t max_tasks, int64_t max_edges, int32_t ma
     for (int l = 0; l < L; ++l) { lp.ring_off[l] = (unsigned long long)l * nt; lp.ring_cap[l] = nt; }
     lp.ntasks = max_tasks; lp.nlevels = L; lp.has_mx = 1; lp.timeout_ns = c->cfg.timeout_ns;
     lp.debug = c->cfg.debug_checks; lp.stream_mode = 1;
+    if (c->trace_on) { lp.trace = c->trace; lp.trace_n = c->trace_n; lp.trace_cap = c->trace_cap; }
     lp.sctl = S.sctl; lp.subs = S.subs; lp.sroots = S.sroots; lp.task_batch = S.task_batch;
     lp.batch_left = S.batch_left; lp.batch_info = S.batch_info; lp.batch_done = S.done_d;
     lp.deadline_ns = deadline_ns;
@@ -1623,6 +1632,48 @@ int b3t_ir_solve(b3t_ctx *c, const double *A, double *const *L, const double *B,
         prev = e;
     }
     return -ERANGE;
+}
+
+int b3t_trace_start(b3t_ctx *c, int64_t capacity) {
+    if (!c || capacity < 1) return -EINVAL;
+    if (c->cfg.host_only) return -ENODEV;
+    if (c->st.open) return -EBUSY;
+    int rc = wait_impl(c, 0);
+    if (rc) return rc;
+    if (capacity > c->trace_cap) {
+        if (c->trace_n) cudaFree(c->trace_n);
+        c->trace_n = nullptr; c->trace = nullptr; c->trace_cap = 0;
+        void *m = nullptr;
+        // the count and the records in one allocation (records 256-byte aligned)
+        if ((rc = cuda_err(cudaMalloc(&m, 256 + (size_t)capacity * sizeof(TraceRec))))) return rc;
+        c->trace_n = (unsigned long long *)m;
+        c->trace = (TraceRec *)((char *)m + 256);
+        c->trace_cap = capacity;
+    }
+    if ((rc = cuda_err(cudaMemsetAsync(c->trace_n, 0, sizeof(unsigned long long), c->stream)))) return rc;
+    c->trace_on = true;
+    return 0;
+}
+
+int b3t_trace_read(b3t_ctx *c, void *records, int64_t capacity, int64_t *count) {
+    if (!c || !count || capacity < 0 || (capacity && !records)) return -EINVAL;
+    if (c->cfg.host_only) return -ENODEV;
+    if (!c->trace_n) return -ENOENT;
+    if (c->st.open) return -EBUSY;
+    int rc = wait_impl(c, 0);
+    if (rc) return rc;
+    unsigned long long n = 0;
+    if ((rc = cuda_err(cudaMemcpy(&n, c->trace_n, sizeof(n), cudaMemcpyDeviceToHost)))) return rc;
+    *count = (int64_t)n;
+    const int64_t k = std::min<int64_t>({(int64_t)n, capacity, c->trace_cap});
+    if (k > 0) rc = cuda_err(cudaMemcpy(records, c->trace, (size_t)k * sizeof(TraceRec), cudaMemcpyDeviceToHost));
+    return rc;
+}
+
+int b3t_trace_stop(b3t_ctx *c) {
+    if (!c) return -EINVAL;
+    c->trace_on = false;
+    return 0;
 }
 
 int b3t_tiles_unregister(b3t_ctx *c, void *const *tiles, int32_t T) {

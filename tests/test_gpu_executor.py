@@ -225,3 +225,21 @@ def test_noop_dags_and_partitions(orc, gctx):
     assert nt == 20 * 65
     gctx.task_wait()
     assert gctx.last_launch()["ntasks"] == nt
+
+
+def test_trace_records_every_item(gctx):
+    # one record per finished work item: every (task, item) exactly once,
+    # start <= end, kinds as submitted
+    T, b = 4, 128
+    A = torch.from_numpy(och.to_tiles(synth.spd_host(T * b, seed=11, shift=1.0), b)).cuda()
+    gctx.trace_start(1 << 14)
+    gctx.cholesky_submit(dt.tile_ptrs(A), T, b)
+    gctx.task_wait()
+    tr = gctx.trace_read()
+    gctx.trace_stop()
+    ntasks, nitems = gctx.last_launch()["ntasks"], gctx.last_launch()["nitems"]
+    assert len(tr) == nitems
+    pairs = set(zip(tr["task"].tolist(), tr["item"].tolist()))
+    assert len(pairs) == nitems and {t for t, _ in pairs} == set(range(ntasks))
+    assert np.all(tr["t_end_ns"] >= tr["t_start_ns"])
+    assert set(tr["kind"].tolist()) <= {b3t.POTRF, b3t.TRSM, b3t.SYRK, b3t.GEMM}

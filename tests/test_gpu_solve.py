@@ -86,13 +86,14 @@ def test_residual_and_backward_error(orc, gctx):
     X = np.linalg.solve(As, Bm) * (1.0 + 1e-3 * synth.gaussian((N, nrhs), 7))   # eta ~ 1e-3
     Ap = torch.from_numpy(och.to_tiles(A, b)).cuda()
     Xd, Bd = parts_from(X, b), parts_from(Bm, b)
-    R = torch.zeros(b3t.ir_work_elems(T, b, nrhs), dtype=torch.float64, device="cuda")
+    PR = b * nrhs + (b // 64) * (2 * nrhs + 1)     # residual part: values, then per-item maxima
+    R = torch.zeros(T * PR, dtype=torch.float64, device="cuda")
     eta = torch.zeros(nrhs + 1, dtype=torch.float64, device="cuda")
     ha = gctx.data_register(Ap.data_ptr(), Ap.numel(), 8)
     hx = gctx.data_register(Xd.data_ptr(), Xd.numel(), 8)
     hb = gctx.data_register(Bd.data_ptr(), Bd.numel(), 8)
     hr = gctx.data_register(R.data_ptr(), R.numel(), 8)
-    pr = gctx.data_partition(hr, T, R.numel() // T)
+    pr = gctx.data_partition(hr, T, PR)
     he = gctx.data_register(eta.data_ptr(), eta.numel(), 8)
     cres = gctx.task_decl("resid", b3t.RESID, [1, 1, 1, 2], 20)
     cnrm = gctx.task_decl("nrm", b3t.NRM, [1, 1, 2], 20)
@@ -100,7 +101,6 @@ def test_residual_and_backward_error(orc, gctx):
         gctx.task_submit(cres, [ha, hx, hb, pr[i]], b3t.vec_args(nrhs, 0, i, T, b))
     gctx.task_submit(cnrm, [hr, hb, he], b3t.vec_args(nrhs, 0, 0, T, b))
     gctx.task_wait()
-    PR = R.numel() // T
     Rv = R.view(T, PR)[:, : b * nrhs].reshape(T, nrhs, b)
     ref = Bm - As @ X
     assert np.max(np.abs(dense_from(Rv) - ref)) <= 1e-13 * np.max(np.abs(As)) * np.max(np.abs(X))
