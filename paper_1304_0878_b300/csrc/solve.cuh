@@ -3,9 +3,9 @@
 // Vectors with nrhs right-hand sides are split into T row blocks ("parts")
 // of b rows; part k holds Y_k(r, j) at j*b + r (column-major b x nrhs).
 //   TRSV_L  : Y_k <- L_kk^{-1} Y_k            item = one right-hand side
-//   GEMV_L  : Y_i <- Y_i - L_ik Y_k           item = 64 rows of Y_i
+//   GEMV_L  : Y_i <- Y_i - L_ik Y_k           item = 16 rows of Y_i
 //   TRSV_LT : Y_k <- L_kk^{-T} Y_k            item = one right-hand side
-//   GEMV_LT : Y_i <- Y_i - L_ki^T Y_k         item = 64 rows of Y_i
+//   GEMV_LT : Y_i <- Y_i - L_ki^T Y_k         item = 16 rows of Y_i
 //             (flags: assign Y_i <- M Y_k instead; M lower or upper
 //             triangular, so that blocks of zeros are skipped)
 //   AXPY    : X_i <- X_i + D_i (or X_i = D_i) one item
@@ -102,51 +102,72 @@ __device__ __forceinline__ void trsv_lt_item(const TaskRec &t, int j, unsigned c
 }
 
 // Y_i(r0+r, j) -= sum_q M(r, q) Y_k(q, j), M = L_ik (trans = false) or
-// L_ki^T (trans = true), 64 rows per item.  Thread (r, g) owns row r and the
-// right-hand sides g, g + 4, ...: NM of them, NM the smallest power of two
-// that covers nrhs (so no multiply-add is issued for an absent column).
+// L_ki^T (trans = true), kGemvRows = 16 rows per item (32 items per 512-row
+// part: the solve's critical path is a chain of these tasks, so short items
+// spread each step over many SMs).  Thread (r, g) owns row r and the
+// right-hand sides g, g + 16 (NM of them, 1 or 2).  The 16 x 64 block of M
+// and the 64 x nrhs block of Y_k are staged in shared memory per 64-column
+// step; the loads of the next step are in flight while a step is computed.
 template <typename Tc, bool trans, int NM>
 __device__ __forceinline__ void gemv_body(const TaskRec &t, int item, unsigned char *smem) {
     const double *L = (const double *)t.buf[0];
     const double *Yk = (const double *)t.buf[1];
     double *Yi = (double *)t.buf[2];
+    constexpr int RR = kGemvRows, G = kThreads / RR;
     const int b = (int)t.n, nrhs = vk_nrhs(t), tid = threadIdx.x;
-    const int r = tid & 63, g = tid >> 6, r0 = item * 64;
-    Tc *Ys = (Tc *)smem;                 // [nrhs][64]
-    Tc *Lc = Ys + 64 * 32;               // [64][65]: Lc[r*65 + q] = M(r0 + r, q0 + q)
+    const int r = tid % RR, g = tid / RR, r0 = item * RR;
+    Tc *Ys = (Tc *)smem;                 // [nrhs][65]: Ys[j*65 + q] = Y_k(q0 + q, j)
+    Tc *Lc = Ys + 65 * kMaxRhs;          // [RR][65]:   Lc[r*65 + q] = M(r0 + r, q0 + q)
     const int fl = vk_flags(t);
-    // a triangular M has nonzeros only in the blocks q0 <= r0 (lower) or
-    // q0 >= r0 (upper)
-    const int qa = (fl & kVecUpperM) ? r0 : 0, qb = (fl & kVecLowerM) ? r0 + 64 : b;
+    // a triangular M has nonzeros only in the 64-column blocks that reach
+    // q <= r (lower) or q >= r (upper) for the item's rows
+    const int qa = (fl & kVecUpperM) ? (r0 / 64) * 64 : 0;
+    const int qb = (fl & kVecLowerM) ? r0 + RR : b;
     Tc acc[NM];
 #pragma unroll
     for (int m = 0; m < NM; ++m) acc[m] = 0;
-    for (int q0 = qa; q0 < qb; q0 += 64) {
-        for (int e = tid; e < 64 * nrhs; e += kThreads) {
-            const int q = e & 63, jj = e >> 6;
-            Ys[jj * 64 + q] = (Tc)Yk[(size_t)jj * b + q0 + q];
+    // the next step's loads are issued before the current step is computed
+    double ly[8], lm[(RR * 64) / kThreads];
+    auto load = [&](int q0) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = tid + u * kThreads, q = e & 63, jj = e >> 6;
+            if (jj < nrhs) ly[u] = Yk[(size_t)jj * b + q0 + q];
         }
-        // the 64 x 64 block of M in shared memory: 16 independent coalesced
-        // loads per thread, so the block arrives in about one memory latency
-        if (trans) {
-            for (int e = tid; e < 64 * 64; e += kThreads) {
+#pragma unroll
+        for (int u = 0; u < (RR * 64) / kThreads; ++u) {
+            const int e = tid + u * kThreads;
+            if (trans) {
                 const int q = e & 63, rr = e >> 6;
-                Lc[rr * 65 + q] = (Tc)L[(size_t)(q0 + q) + (size_t)(r0 + rr) * b];
+                lm[u] = L[(size_t)(q0 + q) + (size_t)(r0 + rr) * b];
+            } else {
+                const int rr = e % RR, q = e / RR;
+                lm[u] = L[(size_t)(r0 + rr) + (size_t)(q0 + q) * b];
             }
-        } else {
-            for (int e = tid; e < 64 * 64; e += kThreads) {
-                const int rr = e & 63, q = e >> 6;
-                Lc[rr * 65 + q] = (Tc)L[(size_t)(r0 + rr) + (size_t)(q0 + q) * b];
-            }
+        }
+    };
+    if (qa < qb) load(qa);
+    for (int q0 = qa; q0 < qb; q0 += 64) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = tid + u * kThreads, q = e & 63, jj = e >> 6;
+            if (jj < nrhs) Ys[jj * 65 + q] = (Tc)ly[u];
+        }
+#pragma unroll
+        for (int u = 0; u < (RR * 64) / kThreads; ++u) {
+            const int e = tid + u * kThreads;
+            const int q = trans ? (e & 63) : (e / RR), rr = trans ? (e >> 6) : (e % RR);
+            Lc[rr * 65 + q] = (Tc)lm[u];
         }
         __syncthreads();
-#pragma unroll 4
+        if (q0 + 64 < qb) load(q0 + 64);
+#pragma unroll 8
         for (int q = 0; q < 64; ++q) {
             const Tc a = Lc[r * 65 + q];
 #pragma unroll
             for (int m = 0; m < NM; ++m) {
-                const int jj = g + 4 * m;
-                if (NM == 1 || jj < nrhs) acc[m] += a * Ys[jj * 64 + q];
+                const int jj = g + G * m;
+                if (jj < nrhs) acc[m] += a * Ys[jj * 65 + q];
             }
         }
         __syncthreads();
@@ -154,7 +175,7 @@ __device__ __forceinline__ void gemv_body(const TaskRec &t, int item, unsigned c
     const bool assign = fl & kVecAssign;
 #pragma unroll
     for (int m = 0; m < NM; ++m) {
-        const int jj = g + 4 * m;
+        const int jj = g + G * m;
         if (jj < nrhs) {
             double *p = Yi + (size_t)jj * b + r0 + r;
             *p = assign ? (double)acc[m] : *p - (double)acc[m];
@@ -164,11 +185,8 @@ __device__ __forceinline__ void gemv_body(const TaskRec &t, int item, unsigned c
 
 template <typename Tc, bool trans>
 __device__ __forceinline__ void gemv_item(const TaskRec &t, int item, unsigned char *smem) {
-    const int nm = (vk_nrhs(t) + 3) / 4;
-    if (nm <= 1) gemv_body<Tc, trans, 1>(t, item, smem);
-    else if (nm <= 2) gemv_body<Tc, trans, 2>(t, item, smem);
-    else if (nm <= 4) gemv_body<Tc, trans, 4>(t, item, smem);
-    else gemv_body<Tc, trans, 8>(t, item, smem);
+    if (vk_nrhs(t) <= kThreads / kGemvRows) gemv_body<Tc, trans, 1>(t, item, smem);
+    else gemv_body<Tc, trans, 2>(t, item, smem);
 }
 
 __device__ __forceinline__ void axpy_item(const TaskRec &t) {
