@@ -162,7 +162,9 @@ typedef struct b3t_panel_args {
  *               elements): R_i <- B_i - (A X)_i in FP64 with A symmetric and
  *               only its lower tiles stored; after the b*nrhs values, R_i
  *               holds per 64-row item max|r_j|, max|x_j| and the largest
- *               row sum of |A| (flags bit 1: X taken as 0, R_i <- B_i)
+ *               row sum of |A| (flags bit 1: X taken as 0, R_i <- B_i;
+ *               bit 4: keep the row-sum partials an earlier residual wrote,
+ *               for refinement steps after the first)
  *  B3T_NRM      R (R, the T residual parts back to back), B (R), eta (W,
  *               nrhs + 1 f64):
  *               eta_j = max|r_j| / (||A||_inf max|x_j| + max|b_j|),
@@ -170,7 +172,7 @@ typedef struct b3t_panel_args {
 typedef struct b3t_vec_args {
     int32_t nrhs, flags, i, T, b;
 } b3t_vec_args;
-enum { B3T_VEC_F32 = 1, B3T_VEC_ASSIGN = 2, B3T_VEC_LOWER_M = 4, B3T_VEC_UPPER_M = 8 };
+enum { B3T_VEC_F32 = 1, B3T_VEC_ASSIGN = 2, B3T_VEC_LOWER_M = 4, B3T_VEC_UPPER_M = 8, B3T_VEC_KEEP_NORM = 16 };
 
 /* Low-precision formats of the Q tiles. */
 enum b3t_fmt { B3T_FMT_BF16 = 0, B3T_FMT_E4M3 = 1 };

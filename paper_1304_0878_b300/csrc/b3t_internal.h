@@ -38,6 +38,9 @@ constexpr int32_t kVecF32 = 1, kVecAssign = 2;
 // GEMV with a triangular matrix M: only the 64-column blocks that can hold
 // nonzeros are visited (lower: q <= r, upper: q >= r)
 constexpr int32_t kVecLowerM = 4, kVecUpperM = 8;
+// RESID: leave the |A| row-sum partials from an earlier residual in place
+// (the norm of A does not change between refinement steps)
+constexpr int32_t kVecKeepNorm = 16;
 
 struct PanelArgs {
     int32_t b, pw, kk, jj, col0;

@@ -595,7 +595,7 @@ int submit_impl(b3t_ctx *c, b3t_codelet cl, const b3t_handle *handles, const uin
     if (is_vec(C.kind)) {
         VecArgs v;
         std::memcpy(&v, scalars, sizeof(v));
-        if (v.nrhs < 1 || v.nrhs > kMaxRhs || v.flags < 0 || v.flags > 15 || v.T < 1 || v.T > 65535 ||
+        if (v.nrhs < 1 || v.nrhs > kMaxRhs || v.flags < 0 || v.flags > 31 || v.T < 1 || v.T > 65535 ||
             v.i < 0 || v.i >= v.T || v.b < 64 || v.b > 4096 || v.b % 64)
             return -EINVAL;
         const size_t b = (size_t)v.b, blk = b * v.nrhs, T = (size_t)v.T;
@@ -1589,7 +1589,8 @@ static int ir_step(b3t_ctx *c, IrHandles &H, int32_t T, int32_t b, int32_t nrhs,
         const b3t_handle h2[2] = {H.hx[i], H.hr[i]};
         if ((rc = submit_impl(c, cax, h2, nullptr, 2, &v, sizeof(v)))) return rc;
     }
-    if ((rc = resid(0))) return rc;
+    // the |A| row sums are formed by the first step's residual and kept
+    if ((rc = resid(first ? 0 : kVecKeepNorm))) return rc;
     VecArgs v{nrhs, 0, 0, T, b};
     const b3t_handle h3[3] = {H.hrp, H.hbp, H.he};
     return submit_impl(c, cnrm, h3, nullptr, 3, &v, sizeof(v));

@@ -204,7 +204,8 @@ __device__ __forceinline__ int64_t ptile(int i, int j, int T) {
 // Thread (r, g) accumulates row r0 + r of A X for the right-hand sides
 // g, g + 4, ... (NM of them, the smallest power of two covering nrhs: no
 // multiply-add is issued for an absent column), and the threads of g = 0
-// also the row sum of |A| (one FP64 add per element of A, not four).
+// also the row sum of |A| (one FP64 add per element of A, not four), unless
+// the flags keep the row sums an earlier residual left in place.
 template <int NM>
 __device__ __forceinline__ void resid_body(const TaskRec &t, int item, unsigned char *smem) {
     const double *A = (const double *)t.buf[0];
@@ -212,7 +213,7 @@ __device__ __forceinline__ void resid_body(const TaskRec &t, int item, unsigned 
     const double *B = (const double *)t.buf[2];
     double *Ri = (double *)t.buf[3];
     const int b = (int)t.n, nrhs = vk_nrhs(t), T = vk_T(t), i = vk_i(t);
-    const bool xzero = vk_flags(t) & 2;
+    const bool xzero = vk_flags(t) & 2, keep_norm = vk_flags(t) & kVecKeepNorm;
     constexpr int RR = kResidRows;          // 64 rows per item
     const int tid = threadIdx.x, r = tid & (RR - 1), g = tid / RR, r0 = item * RR, nit = b / RR;
     double *As = (double *)smem;            // [64 columns][65]: As[c*65 + r]
@@ -246,7 +247,7 @@ __device__ __forceinline__ void resid_body(const TaskRec &t, int item, unsigned 
                     As[c * 65 + rr] = tile[off];
                 }
                 __syncthreads();
-                if (g == 0) {
+                if (g == 0 && !keep_norm) {
 #pragma unroll 2
                     for (int c = 0; c < 64; ++c) {
                         const double a = As[c * 65 + r];
@@ -298,7 +299,7 @@ __device__ __forceinline__ void resid_body(const TaskRec &t, int item, unsigned 
         }
         Rn[(size_t)item * nrhs + tid] = mr;
         Rn[(size_t)nit * nrhs + (size_t)item * nrhs + tid] = mx;
-    } else if (tid == 32) {
+    } else if (tid == 32 && !keep_norm) {
         double m = 0.0;
         for (int k = 0; k < RR; ++k) m = fmax(m, Rs[k]);
         Rn[(size_t)2 * nit * nrhs + item] = m;
