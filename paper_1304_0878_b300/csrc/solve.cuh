@@ -107,7 +107,8 @@ __device__ __forceinline__ void trsv_lt_item(const TaskRec &t, int j, unsigned c
 // spread each step over many SMs).  Thread (r, g) owns row r and the
 // right-hand sides g, g + 16 (NM of them, 1 or 2).  The 16 x 64 block of M
 // and the 64 x nrhs block of Y_k are staged in shared memory per 64-column
-// step; the loads of the next step are in flight while a step is computed.
+// step, all loads of a step issued before the first is used (prefetching
+// the next step into registers measured slower: it spills).
 template <typename Tc, bool trans, int NM>
 __device__ __forceinline__ void gemv_body(const TaskRec &t, int item, unsigned char *smem) {
     const double *L = (const double *)t.buf[0];
@@ -126,9 +127,8 @@ __device__ __forceinline__ void gemv_body(const TaskRec &t, int item, unsigned c
     Tc acc[NM];
 #pragma unroll
     for (int m = 0; m < NM; ++m) acc[m] = 0;
-    // the next step's loads are issued before the current step is computed
-    double ly[8], lm[(RR * 64) / kThreads];
-    auto load = [&](int q0) {
+    for (int q0 = qa; q0 < qb; q0 += 64) {
+        double ly[8], lm[(RR * 64) / kThreads];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int e = tid + u * kThreads, q = e & 63, jj = e >> 6;
@@ -145,9 +145,6 @@ __device__ __forceinline__ void gemv_body(const TaskRec &t, int item, unsigned c
                 lm[u] = L[(size_t)(r0 + rr) + (size_t)(q0 + q) * b];
             }
         }
-    };
-    if (qa < qb) load(qa);
-    for (int q0 = qa; q0 < qb; q0 += 64) {
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int e = tid + u * kThreads, q = e & 63, jj = e >> 6;
@@ -160,7 +157,6 @@ __device__ __forceinline__ void gemv_body(const TaskRec &t, int item, unsigned c
             Lc[rr * 65 + q] = (Tc)lm[u];
         }
         __syncthreads();
-        if (q0 + 64 < qb) load(q0 + 64);
 #pragma unroll 8
         for (int q = 0; q < 64; ++q) {
             const Tc a = Lc[r * 65 + q];
