@@ -288,6 +288,13 @@ __device__ __forceinline__ int mx_update_item(const TaskRec &t, int item, bool s
         }
         st.fills = G + issued;
         mma_commit(st.done);
+    } else {
+        // while thread 0 streams the operands, the other threads pull the
+        // item's W block (128 columns x 4 lines of 128 bytes) into L2
+        for (int l = tid - 1; l < 4 * kMxBlk; l += kThreads - 1) {
+            const float *p = W + (size_t)(bi * kMxBlk + (l & 3) * 32) + (size_t)(bj * kMxBlk + (l >> 2)) * b;
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+        }
     }
     __syncthreads();
     const bool ok = mbar_wait(st.done, st.items & 1, limit_ns);
