@@ -71,6 +71,12 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
+__device__ __forceinline__ void bulk_s2g_mx(void *dst, const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+
 // tcgen05 shared-memory matrix descriptor: K-major operand, 128-byte swizzle,
 // 8-row groups 1024 bytes apart.
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
@@ -141,7 +147,8 @@ struct MxState {
     uint64_t *full;       // [kMxStages]
     uint64_t *empty;      // [kMxStages]
     uint64_t *done;       // [1]
-    unsigned char *stage; // kMxStages x 32 KiB, 1024-aligned
+    uint64_t *wfull;      // [1] the item's W block has landed in shared memory
+    unsigned char *stage; // kMxStages x 32 KiB, 1024-aligned, then the W block (64 KiB)
     uint32_t tmem;        // accumulator base address
     uint32_t fills;       // stage fills issued so far (thread 0)
     uint32_t items;       // items completed so far (all threads)
@@ -242,6 +249,20 @@ __device__ __forceinline__ int mx_update_item(const TaskRec &t, int item, bool s
     const int nk = b * es / 128;
     const uint32_t idesc = mx_idesc(fmt == 0 ? 1u : 0u);
     const int tid = threadIdx.x;
+    // the item's 128 x 128 block of W (column-major, 128 columns of 512 bytes)
+    // is copied into shared memory while the operands stream in
+    float *Ws = (float *)(st.stage + kMxStages * 2 * kChunkBytes);
+    float *Wg = W + (size_t)bi * kMxBlk + (size_t)bj * kMxBlk * b;
+    if ((tid >> 5) == 1) {
+        const int lane = tid & 31;
+        if (lane == 0) {
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            mbar_expect_tx(st.wfull, kMxBlk * kMxBlk * 4);
+        }
+        __syncwarp();
+        for (int c = lane; c < kMxBlk; c += 32)
+            bulk_g2s(Ws + c * kMxBlk, Wg + (size_t)c * b, kMxBlk * 4, st.wfull);
+    }
     if (tid == 0) {
         *s_fail = 0;
         // make generic-proxy writes of the producer tasks visible to the bulk copies
@@ -288,19 +309,13 @@ __device__ __forceinline__ int mx_update_item(const TaskRec &t, int item, bool s
         }
         st.fills = G + issued;
         mma_commit(st.done);
-    } else {
-        // while thread 0 streams the operands, the other threads pull the
-        // item's W block (128 columns x 4 lines of 128 bytes) into L2
-        for (int l = tid - 1; l < 4 * kMxBlk; l += kThreads - 1) {
-            const float *p = W + (size_t)(bi * kMxBlk + (l & 3) * 32) + (size_t)(bj * kMxBlk + (l >> 2)) * b;
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-        }
     }
     __syncthreads();
     const bool ok = mbar_wait(st.done, st.items & 1, limit_ns);
+    const bool wok = mbar_wait(st.wfull, st.items & 1, limit_ns);
     st.items++;
     tc_fence_after();
-    if (*s_fail || !ok) return ETIMEDOUT;
+    if (*s_fail || !ok || !wok) return ETIMEDOUT;
     // epilogue: warp w reads TMEM lanes 32*(w%4).. and columns 64*(w/4)..
     const int warp = tid >> 5, lane = tid & 31;
     const int q = warp & 3, h = warp >> 2;
@@ -310,21 +325,33 @@ __device__ __forceinline__ int mx_update_item(const TaskRec &t, int item, bool s
         const int eb = *(const int *)(QB + (size_t)b * b * es);
         s = ldexpf(1.0f, ea + eb);
     }
-    const int gr = bi * kMxBlk + 32 * q + lane;
+    const int rr = 32 * q + lane, gr = bi * kMxBlk + rr;
 #pragma unroll 1
     for (int i = 0; i < 4; ++i) {
         float v[16];
         tmem_ld16(st.tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * 64 + 16 * i), v);
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
-            const int gc = bj * kMxBlk + h * 64 + 16 * i + c;
-            if (!syrk || gr >= gc) {
-                float *p = W + (size_t)gr + (size_t)gc * b;
+            const int cc = h * 64 + 16 * i + c;
+            if (!syrk || gr >= bj * kMxBlk + cc) {
+                float *p = Ws + cc * kMxBlk + rr;
                 *p = fmaf(-s, v[c], *p);
             }
         }
     }
     tc_fence_before();
+    // the updated block goes back with bulk stores (the upper part of a
+    // diagonal block is written back as it was read)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (warp == 1) {
+        for (int c = lane; c < kMxBlk; c += 32) bulk_s2g_mx(Wg + (size_t)c * b, Ws + c * kMxBlk, kMxBlk * 4);
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        __threadfence();
+    }
+    __syncthreads();
     return 0;
 }
 
