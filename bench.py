@@ -636,7 +636,7 @@ def run_case(args):
         A = synth.spd_tiles_device(N, b, 3, 0.1, dev)
         X = torch.randn((T, nrhs, b), dtype=torch.float64, device=dev)
         B = torch.randn((T, nrhs, b), dtype=torch.float64, device=dev)
-        PR = b * nrhs + (b // 64) * (2 * nrhs + 1)     # residual part: values, then per-item maxima
+        PR = b3t.resid_part_elems(b, nrhs)             # residual part: values, then per-item maxima
         R = torch.zeros(T * PR, dtype=torch.float64, device=dev)
         ha = ctx.data_register(A.data_ptr(), A.numel(), 8)
         hx = ctx.data_register(X.data_ptr(), X.numel(), 8)

@@ -8,7 +8,7 @@ submission order, and a wait.  The C-ABI library (include/b3t.h,
 libb3t.so) does all of it; this package only marshals arguments.
 """
 from ._lib import (Context, B3TError, Config, lib, strerror, q_bytes, header_symbols,  # noqa: F401
-                   ir_work_elems, vec_args, TRSV_L, GEMV_L, TRSV_LT, GEMV_LT, AXPY, RESID, NRM,
+                   ir_work_elems, resid_part_elems, vec_args, TRSV_L, GEMV_L, TRSV_LT, GEMV_LT, AXPY, RESID, NRM,
                    VEC_F32, VEC_ASSIGN, VEC_LOWER_M, VEC_UPPER_M, TRTRI,
                    pack_f32, pack_i32, R, W, RW, NOOP, SCAL_F32, POTRF, TRSM, SYRK, GEMM,
                    POTRF_MX, TRSM_MX, SYRK_MX, GEMM_MX, QUANT, FMT_BF16, FMT_E4M3,

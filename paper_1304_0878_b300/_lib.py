@@ -79,6 +79,7 @@ _SIGS = {
     "b3t_stream_close": (ctypes.c_int, [_vp]),
     "b3t_chol_solve_submit": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), _vp, _i32, _i32, _i32, _i64, _i32]),
     "b3t_ir_work_elems": (_sz, [_i32, _i32, _i32]),
+    "b3t_resid_part_elems": (_sz, [_i32, _i32]),
     "b3t_chol_inv_submit": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i32, _i32]),
     "b3t_chol_solve_inv_submit": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp, _vp, _i32,
                                                  _i32, _i32, _i64, _i32]),
@@ -138,6 +139,10 @@ def q_bytes(b, fmt):
 
 def ir_work_elems(T, b, nrhs):
     return int(lib().b3t_ir_work_elems(T, b, nrhs))
+
+
+def resid_part_elems(b, nrhs):
+    return int(lib().b3t_resid_part_elems(b, nrhs))
 
 
 def vec_args(nrhs, flags=0, i=0, T=1, b=64):

@@ -23,7 +23,7 @@ constexpr int kGemmBlk = 64;             // f64 GEMM / SYRK item: 64 x 64 of C
 constexpr int kTrsmRows = 32;            // f64 TRSM item: 32 rows of A_ik
 constexpr int kMxBlk = 128;              // MX GEMM / SYRK item: 128 x 128 of C
 constexpr int kGemvRows = 16;            // GEMV item: 16 rows of the updated part
-constexpr int kResidRows = 64;           // RESID item: 64 rows of the residual part
+constexpr int kResidRows = 16;           // RESID item: 16 rows of the residual part
 constexpr int kMaxRhs = 32;
 
 // Scalar blob of the vector kinds (TRSV / GEMV / AXPY / RESID / NRM).

@@ -1509,6 +1509,11 @@ static size_t ir_u_off(int32_t T, int32_t b, int32_t nrhs) {
     return ir_z_off(T, b, nrhs) + round32((size_t)T * b * nrhs);
 }
 
+size_t b3t_resid_part_elems(int32_t b, int32_t nrhs) {
+    if (b <= 0 || b % 64 || nrhs < 1 || nrhs > kMaxRhs) return 0;
+    return (size_t)resid_part_elems(b, nrhs);
+}
+
 size_t b3t_ir_work_elems(int32_t T, int32_t b, int32_t nrhs) {
     if (T <= 0 || b <= 0 || b % 64 || nrhs < 1 || nrhs > kMaxRhs) return 0;
     return ir_u_off(T, b, nrhs) + (size_t)T * b * b;

@@ -11,7 +11,7 @@
 //   AXPY    : X_i <- X_i + D_i (or X_i = D_i) one item
 //   RESID   : R_i <- B_i - (A X)_i, FP64, with A symmetric and only its lower
 //             tiles stored; also per-item maxima |R|, |X_i| and the largest
-//             row sum of |A| (for the backward error)   item = 64 rows
+//             row sum of |A| (for the backward error)   item = 16 rows
 //   NRM     : eta_j = max|r_j| / (||A||_inf max|x_j| + max|b_j|), one item
 // The solve bodies compute in Tc (double, or float for refinement
 // corrections) and read / write FP64 storage.
@@ -199,11 +199,12 @@ __device__ __forceinline__ int64_t ptile(int i, int j, int T) {
     return (int64_t)j * T - (int64_t)j * (j - 1) / 2 + (i - j);
 }
 
-// Thread (r, g) accumulates row r0 + r of A X for the right-hand sides
-// g, g + 4, ... (NM of them, the smallest power of two covering nrhs: no
-// multiply-add is issued for an absent column), and the threads of g = 0
-// also the row sum of |A| (one FP64 add per element of A, not four), unless
-// the flags keep the row sums an earlier residual left in place.
+// Thread (r, g) accumulates row r0 + r of A X (kResidRows = 16 rows per
+// item: 32 items per 512-row part, so that the items fill the grid in many
+// waves) for the right-hand sides g, g + 16 (NM of them, 1 or 2); it also
+// adds columns 4g..4g+3 of each 64-column step to the row sum of |A| (one
+// FP64 add per element of A, spread evenly over the warps), unless the flags
+// keep the row sums an earlier residual left in place.
 template <int NM>
 __device__ __forceinline__ void resid_body(const TaskRec &t, int item, unsigned char *smem) {
     const double *A = (const double *)t.buf[0];
@@ -212,10 +213,10 @@ __device__ __forceinline__ void resid_body(const TaskRec &t, int item, unsigned 
     double *Ri = (double *)t.buf[3];
     const int b = (int)t.n, nrhs = vk_nrhs(t), T = vk_T(t), i = vk_i(t);
     const bool xzero = vk_flags(t) & 2, keep_norm = vk_flags(t) & kVecKeepNorm;
-    constexpr int RR = kResidRows;          // 64 rows per item
-    const int tid = threadIdx.x, r = tid & (RR - 1), g = tid / RR, r0 = item * RR, nit = b / RR;
-    double *As = (double *)smem;            // [64 columns][65]: As[c*65 + r]
-    double *Xs = As + 64 * 65;              // [nrhs][64]
+    constexpr int RR = kResidRows, G = kThreads / RR;
+    const int tid = threadIdx.x, r = tid % RR, g = tid / RR, r0 = item * RR, nit = b / RR;
+    double *As = (double *)smem;            // [64 columns][RR + 1]: As[c*(RR+1) + r]
+    double *Xs = As + 64 * (RR + 1);        // [nrhs][65]
     double acc[NM];
 #pragma unroll
     for (int m = 0; m < NM; ++m) acc[m] = 0.0;
@@ -224,47 +225,54 @@ __device__ __forceinline__ void resid_body(const TaskRec &t, int item, unsigned 
         for (int J = 0; J < T; ++J) {
             const double *tile = A + (size_t)ptile(J > i ? J : i, J > i ? i : J, T) * b * b;
             for (int c0 = 0; c0 < b; c0 += 64) {
-                for (int e = tid; e < 64 * nrhs; e += kThreads) {
-                    const int c = e & 63, jj = e >> 6;
-                    Xs[jj * 64 + c] = X[(size_t)J * b * nrhs + (size_t)jj * b + c0 + c];
+                double lx[8], la[(64 * RR) / kThreads];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int e = tid + u * kThreads, c = e & 63, jj = e >> 6;
+                    if (jj < nrhs) lx[u] = X[(size_t)J * b * nrhs + (size_t)jj * b + c0 + c];
                 }
-                for (int e = tid; e < 64 * RR; e += kThreads) {
-                    int rr, c;
+#pragma unroll
+                for (int u = 0; u < (64 * RR) / kThreads; ++u) {
+                    const int e = tid + u * kThreads;
                     size_t off;
                     if (J < i) {            // tile (i, J): (r, c) at r + c*b
-                        rr = e & 63; c = e >> 6;
+                        const int rr = e % RR, c = e / RR;
                         off = (size_t)(r0 + rr) + (size_t)(c0 + c) * b;
                     } else if (J > i) {     // tile (J, i): A(i.., J..) = tile(c, r)
-                        c = e & 63; rr = e >> 6;
+                        const int c = e & 63, rr = e >> 6;
                         off = (size_t)(c0 + c) + (size_t)(r0 + rr) * b;
                     } else {                // diagonal tile: lower part, mirrored
-                        rr = e & 63; c = e >> 6;
+                        const int rr = e % RR, c = e / RR;
                         const int R = r0 + rr, C = c0 + c;
                         off = R >= C ? (size_t)R + (size_t)C * b : (size_t)C + (size_t)R * b;
                     }
-                    As[c * 65 + rr] = tile[off];
+                    la[u] = tile[off];
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int e = tid + u * kThreads, c = e & 63, jj = e >> 6;
+                    if (jj < nrhs) Xs[jj * 65 + c] = lx[u];
+                }
+#pragma unroll
+                for (int u = 0; u < (64 * RR) / kThreads; ++u) {
+                    const int e = tid + u * kThreads;
+                    const int rr = (J > i) ? (e >> 6) : (e % RR), c = (J > i) ? (e & 63) : (e / RR);
+                    As[c * (RR + 1) + rr] = la[u];
                 }
                 __syncthreads();
-                if (g == 0 && !keep_norm) {
-#pragma unroll 2
-                    for (int c = 0; c < 64; ++c) {
-                        const double a = As[c * 65 + r];
+                // row sums of |A|: group g adds columns 4g..4g+3 of its row
+                // (spread over every warp: no warp does more FP64 work)
+                if (!keep_norm) {
 #pragma unroll
-                        for (int m = 0; m < NM; ++m) {
-                            const int jj = 4 * m;
-                            if (jj < nrhs) acc[m] = fma(a, Xs[jj * 64 + c], acc[m]);
-                        }
-                        rs += fabs(a);
-                    }
-                } else {
-#pragma unroll 2
-                    for (int c = 0; c < 64; ++c) {
-                        const double a = As[c * 65 + r];
+                    for (int c = 4 * g; c < 4 * g + 4; ++c) rs += fabs(As[c * (RR + 1) + r]);
+                }
+#pragma unroll 4
+                for (int c = 0; c < 64; ++c) {
+                    const double a = As[c * (RR + 1) + r];
 #pragma unroll
-                        for (int m = 0; m < NM; ++m) {
-                            const int jj = g + 4 * m;
-                            if (jj < nrhs) acc[m] = fma(a, Xs[jj * 64 + c], acc[m]);
-                        }
+                    for (int m = 0; m < NM; ++m) {
+                        const int jj = g + G * m;
+                        if (jj < nrhs) acc[m] = fma(a, Xs[jj * 65 + c], acc[m]);
                     }
                 }
                 __syncthreads();
@@ -272,44 +280,45 @@ __device__ __forceinline__ void resid_body(const TaskRec &t, int item, unsigned 
         }
     }
     // residual, then per-column maxima of |r| and |x| and the largest |A| row sum
-    double *Ra = As;                        // reuse: [nrhs][64] |r|, then [nrhs][64] |x|
-    double *Xa = As + 64 * kMaxRhs;
+    double *Ra = As;                        // reuse: [nrhs][RR] |r|, then [nrhs][RR] |x|
+    double *Xa = As + RR * kMaxRhs;
 #pragma unroll
     for (int m = 0; m < NM; ++m) {
-        const int jj = g + 4 * m;
+        const int jj = g + G * m;
         if (jj < nrhs) {
             const size_t o = (size_t)jj * b + r0 + r;
             const double v = B[(size_t)i * b * nrhs + o] - acc[m];
             Ri[o] = v;
-            Ra[jj * 64 + r] = fabs(v);
-            Xa[jj * 64 + r] = xzero ? 0.0 : fabs(X[(size_t)i * b * nrhs + o]);
+            Ra[jj * RR + r] = fabs(v);
+            Xa[jj * RR + r] = xzero ? 0.0 : fabs(X[(size_t)i * b * nrhs + o]);
         }
     }
-    double *Rs = Xa + 64 * kMaxRhs;         // [64] row sums
-    if (g == 0) Rs[r] = rs;
+    double *Rs = Xa + RR * kMaxRhs;         // [G][RR] partial row sums
+    Rs[g * RR + r] = rs;
     __syncthreads();
     double *Rn = Ri + (size_t)b * nrhs;
     if (tid < nrhs) {
         double mr = 0.0, mx = 0.0;
         for (int k = 0; k < RR; ++k) {
-            mr = fmax(mr, Ra[tid * 64 + k]);
-            mx = fmax(mx, Xa[tid * 64 + k]);
+            mr = fmax(mr, Ra[tid * RR + k]);
+            mx = fmax(mx, Xa[tid * RR + k]);
         }
         Rn[(size_t)item * nrhs + tid] = mr;
         Rn[(size_t)nit * nrhs + (size_t)item * nrhs + tid] = mx;
     } else if (tid == 32 && !keep_norm) {
         double m = 0.0;
-        for (int k = 0; k < RR; ++k) m = fmax(m, Rs[k]);
+        for (int k = 0; k < RR; ++k) {
+            double rsum = 0.0;
+            for (int q = 0; q < G; ++q) rsum += Rs[q * RR + k];
+            m = fmax(m, rsum);
+        }
         Rn[(size_t)2 * nit * nrhs + item] = m;
     }
 }
 
 __device__ __forceinline__ void resid_item(const TaskRec &t, int item, unsigned char *smem) {
-    const int nm = (vk_nrhs(t) + 3) / 4;
-    if (nm <= 1) resid_body<1>(t, item, smem);
-    else if (nm <= 2) resid_body<2>(t, item, smem);
-    else if (nm <= 4) resid_body<4>(t, item, smem);
-    else resid_body<8>(t, item, smem);
+    if (vk_nrhs(t) <= kThreads / kResidRows) resid_body<1>(t, item, smem);
+    else resid_body<2>(t, item, smem);
 }
 
 __device__ __forceinline__ void nrm_item(const TaskRec &t, unsigned char *smem) {

@@ -86,7 +86,7 @@ def test_residual_and_backward_error(orc, gctx):
     X = np.linalg.solve(As, Bm) * (1.0 + 1e-3 * synth.gaussian((N, nrhs), 7))   # eta ~ 1e-3
     Ap = torch.from_numpy(och.to_tiles(A, b)).cuda()
     Xd, Bd = parts_from(X, b), parts_from(Bm, b)
-    PR = b * nrhs + (b // 64) * (2 * nrhs + 1)     # residual part: values, then per-item maxima
+    PR = b3t.resid_part_elems(b, nrhs)             # residual part: values, then per-item maxima
     R = torch.zeros(T * PR, dtype=torch.float64, device="cuda")
     eta = torch.zeros(nrhs + 1, dtype=torch.float64, device="cuda")
     ha = gctx.data_register(Ap.data_ptr(), Ap.numel(), 8)
