@@ -699,6 +699,7 @@ int b3t_shutdown(b3t_ctx *c) {
     if (c->st.open) b3t_stream_close(c);
     const int rc = wait_impl(c, 0);
     for (auto &g : c->graphs) {
+        if (!g.alive) continue;        // destroyed already (its arena released)
         if (g.exec) cudaGraphExecDestroy(g.exec);
         if (g.graph) cudaGraphDestroy(g.graph);
         g.arena.release();
@@ -949,8 +950,10 @@ int b3t_graph_destroy(b3t_ctx *c, b3t_graph gi) {
     if (!c || gi < 0 || gi >= (int32_t)c->graphs.size() || !c->graphs[gi].alive) return -EINVAL;
     const int rc = wait_impl(c, 0);
     GraphRec &g = c->graphs[gi];
-    cudaGraphExecDestroy(g.exec);
-    cudaGraphDestroy(g.graph);
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+    g.exec = nullptr;                  // b3t_shutdown must not destroy them again
+    g.graph = nullptr;
     g.arena.release();
     g.alive = false;
     return rc;
