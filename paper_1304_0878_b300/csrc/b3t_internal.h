@@ -113,6 +113,29 @@ struct TraceRec {
 };
 static_assert(sizeof(TraceRec) == 32, "TraceRec is 32 bytes");
 
+// Kernel variants.  The executor is compiled once per family set below; a
+// launch runs the smallest variant whose families cover its task kinds, so
+// that a DAG of simple tasks is not compiled together with (and does not
+// share registers with) the bodies it never runs.
+constexpr uint32_t kFamScal = 1, kFamF64 = 2, kFamSolve = 4, kFamMx = 8;
+constexpr uint32_t kVarScal = kFamScal, kVarF64 = kFamF64, kVarSolve = kFamSolve,
+                   kVarNoMx = kFamScal | kFamF64 | kFamSolve, kVarAll = kVarNoMx | kFamMx;
+B3T_HD constexpr uint32_t family_of(int kind) {
+    return kind == kScalF32 ? kFamScal
+         : (kind == kPotrf || kind == kTrsm || kind == kSyrk || kind == kGemm || kind == kPotrfD ||
+            kind == kPanelTrsm || kind == kPanelUpd) ? kFamF64
+         : ((kind >= kTrsvL && kind <= kNrm) || kind == kTrtri) ? kFamSolve
+         : (kind >= kPotrfMx && kind <= kQuant) || kind == kCvt ? kFamMx
+         : 0u;   // NOOP runs in every variant
+}
+B3T_HD constexpr uint32_t variant_of(uint32_t fams) {
+    return (fams & kFamMx) ? kVarAll
+         : (fams & ~kVarScal) == 0 ? kVarScal
+         : (fams & ~kVarF64) == 0 ? kVarF64
+         : (fams & ~kVarSolve) == 0 ? kVarSolve
+         : kVarNoMx;
+}
+
 struct LaunchParams {
     const TaskRec *tasks;
     const int32_t *succ;         // CSR successor lists
@@ -127,6 +150,7 @@ struct LaunchParams {
     int64_t ntasks;
     int32_t nlevels;
     int32_t has_mx;              // launch holds tcgen05 work: allocate TMEM
+    uint32_t variant;            // kernel variant (family set) the launch runs
     int64_t timeout_ns;
     int32_t debug;
     int32_t stream_mode;
@@ -175,7 +199,7 @@ B3T_HD inline unsigned long long pack_slot(int64_t task, int32_t nitems) {
 extern "C" {
 int b3t_internal_launch(const b3t::InitParams *ip, const b3t::LaunchParams *lp,
                         int nctas, size_t smem, void *stream, void *ev_start, void *ev_stop);
-int b3t_internal_occupancy(int *ctas_per_sm, size_t smem, int *num_sms, int has_mx);
+int b3t_internal_occupancy(int *ctas_per_sm, size_t smem, int *num_sms, uint32_t variant);
 int b3t_internal_launch_exec(const b3t::LaunchParams *lp, int nctas, size_t smem, void *stream, void *ev_start);
-size_t b3t_internal_smem_bytes(int has_mx);
+size_t b3t_internal_smem_bytes(uint32_t variant);
 }

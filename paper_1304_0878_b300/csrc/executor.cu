@@ -396,13 +396,15 @@ __device__ __forceinline__ void retire(const LaunchParams &p, int64_t t, const T
     }
 }
 
-// Two variants: kMx = true carries the tcgen05 tensor-memory path (launches
-// with SYRK_MX / GEMM_MX tasks, and stream mode); a kernel that allocates
-// tensor memory runs one CTA per SM.  kMx = false leaves it out, so that two
-// CTAs per SM fit (120 registers keep two 256-thread CTAs in the register
-// file).
-template <bool kMx>
+// One variant per family set (kVarScal, kVarF64, kVarSolve, kVarNoMx,
+// kVarAll): only the bodies of the variant's families are compiled in.  The
+// variant with the tcgen05 tensor-memory path (kVarAll: mixed-precision
+// launches and stream mode) runs one CTA per SM, as a kernel that allocates
+// tensor memory does; the others run two (120 registers keep two 256-thread
+// CTAs in the register file).
+template <uint32_t kVar>
 __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
+    constexpr bool kMx = (kVar & kFamMx) != 0;
     extern __shared__ __align__(1024) unsigned char dsmem[];
     // align the dynamic area to 1024 bytes (128-byte swizzled operands)
     unsigned char *smem = (unsigned char *)(((uintptr_t)dsmem + 1023) & ~(uintptr_t)1023);
@@ -437,7 +439,7 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
     // SCAL bulk-copy ring (the variant without the tensor-memory path)
     __shared__ __align__(8) uint64_t s_sbar[kSbStages];
     uint32_t sfills = 0;
-    if (!kMx) {
+    if ((kVar & kFamScal) && !kMx) {
         if (tid == 0) {
             for (int i = 0; i < kSbStages; ++i) mbar_init(&s_sbar[i], 1);
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -472,73 +474,89 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
         }
         const TaskRec rec = s_rec;
         int st = 0;
-        switch (rec.kind) {
-        case kScalF32:
-            if constexpr (!kMx) {
-                // each wait of the ring gives up after 50 ms (a 16 KiB copy
-                // takes microseconds) and the launch reports ETIMEDOUT
-                const int fc = scal_item_bulk(rec, it, s_sbar, smem, sfills, min(p.timeout_ns, (int64_t)50000000));
-                if (fc) {
-                    if (tid == 0) set_error(p.ctl, ETIMEDOUT, (int)t, fc, 20);
-                    st = -ETIMEDOUT;
+        constexpr bool kScal = (kVar & kFamScal) != 0, kF64 = (kVar & kFamF64) != 0,
+                       kSolve = (kVar & kFamSolve) != 0;
+        const uint32_t fam = family_of(rec.kind);
+        if (fam && !(fam & kVar)) {
+            st = -EPROTO;   // the runtime picks a variant that covers every kind of the launch
+        } else {
+            switch (rec.kind) {
+            case kScalF32:
+                if constexpr (kScal && !kMx) {
+                    // each wait of the ring gives up after 50 ms (a 16 KiB copy
+                    // takes microseconds) and the launch reports ETIMEDOUT
+                    const int fc = scal_item_bulk(rec, it, s_sbar, smem, sfills, min(p.timeout_ns, (int64_t)50000000));
+                    if (fc) {
+                        if (tid == 0) set_error(p.ctl, ETIMEDOUT, (int)t, fc, 20);
+                        st = -ETIMEDOUT;
+                    }
+                } else if constexpr (kScal) {
+                    scal_item(rec, it);
                 }
-            } else {
-                scal_item(rec, it);
+                break;
+            case kPotrf:
+                if constexpr (kF64) {
+                    const int info = potrf_tile((double *)rec.buf[0], (int)rec.n, (double *)smem, &s_info);
+                    if (info) st = rec.aux + info;
+                }
+                break;
+            case kTrsm: if constexpr (kF64) trsm_item(rec, it, (double *)smem); break;
+            case kSyrk: if constexpr (kF64) syrk_item(rec, it, (double *)smem); break;
+            case kGemm: if constexpr (kF64) gemm_item(rec, it, (double *)smem); break;
+            case kPotrfD:
+                if constexpr (kF64) {
+                    const int info = potrf_d_item(rec, (double *)smem, &s_info);
+                    if (info) st = rec.aux + info;
+                }
+                break;
+            case kPanelTrsm: if constexpr (kF64) panel_trsm_item(rec, it, (double *)smem); break;
+            case kPanelUpd: if constexpr (kF64) panel_upd_item(rec, it, (double *)smem); break;
+            case kPotrfMx:
+                if constexpr (kMx) {
+                    const int info = potrf_mx_item(rec, (double *)smem, &s_info);
+                    if (info) st = rec.aux + info;
+                }
+                break;
+            case kTrsmMx: if constexpr (kMx) trsm_mx_item(rec, it, (double *)smem); break;
+            case kCvt: if constexpr (kMx) cvt_item(rec); break;
+            case kQuant: if constexpr (kMx) quant_item(rec, s_red, &s_e); break;
+            case kSyrkMx:
+            case kGemmMx:
+                if constexpr (kMx) {
+                    if (!p.has_mx) { st = -EPROTO; break; }
+                    if (mx_update_item(rec, it, rec.kind == kSyrkMx, mx, p.timeout_ns, &s_fail)) st = -ETIMEDOUT;
+                }
+                break;
+            case kTrtri: if constexpr (kSolve) trtri_item(rec, it, (double *)smem); break;
+            case kTrsvL:
+                if constexpr (kSolve) {
+                    if (vk_flags(rec) & kVecF32) trsv_l_item<float>(rec, it, smem);
+                    else trsv_l_item<double>(rec, it, smem);
+                }
+                break;
+            case kTrsvLT:
+                if constexpr (kSolve) {
+                    if (vk_flags(rec) & kVecF32) trsv_lt_item<float>(rec, it, smem);
+                    else trsv_lt_item<double>(rec, it, smem);
+                }
+                break;
+            case kGemvL:
+                if constexpr (kSolve) {
+                    if (vk_flags(rec) & kVecF32) gemv_item<float, false>(rec, it, smem);
+                    else gemv_item<double, false>(rec, it, smem);
+                }
+                break;
+            case kGemvLT:
+                if constexpr (kSolve) {
+                    if (vk_flags(rec) & kVecF32) gemv_item<float, true>(rec, it, smem);
+                    else gemv_item<double, true>(rec, it, smem);
+                }
+                break;
+            case kAxpy: if constexpr (kSolve) axpy_item(rec); break;
+            case kResid: if constexpr (kSolve) resid_item(rec, it, smem); break;
+            case kNrm: if constexpr (kSolve) nrm_item(rec, smem); break;
+            default: break;   // NOOP
             }
-            break;
-        case kPotrf: {
-            const int info = potrf_tile((double *)rec.buf[0], (int)rec.n, (double *)smem, &s_info);
-            if (info) st = rec.aux + info;
-            break;
-        }
-        case kTrsm: trsm_item(rec, it, (double *)smem); break;
-        case kSyrk: syrk_item(rec, it, (double *)smem); break;
-        case kGemm: gemm_item(rec, it, (double *)smem); break;
-        case kPotrfMx: {
-            const int info = potrf_mx_item(rec, (double *)smem, &s_info);
-            if (info) st = rec.aux + info;
-            break;
-        }
-        case kTrsmMx: trsm_mx_item(rec, it, (double *)smem); break;
-        case kTrtri: trtri_item(rec, it, (double *)smem); break;
-        case kPotrfD: {
-            const int info = potrf_d_item(rec, (double *)smem, &s_info);
-            if (info) st = rec.aux + info;
-            break;
-        }
-        case kPanelTrsm: panel_trsm_item(rec, it, (double *)smem); break;
-        case kPanelUpd: panel_upd_item(rec, it, (double *)smem); break;
-        case kCvt: cvt_item(rec); break;
-        case kQuant: quant_item(rec, s_red, &s_e); break;
-        case kSyrkMx:
-        case kGemmMx:
-            if constexpr (kMx) {
-                if (!p.has_mx) { st = -EPROTO; break; }
-                if (mx_update_item(rec, it, rec.kind == kSyrkMx, mx, p.timeout_ns, &s_fail)) st = -ETIMEDOUT;
-            } else {
-                st = -EPROTO;
-            }
-            break;
-        case kTrsvL:
-            if (vk_flags(rec) & kVecF32) trsv_l_item<float>(rec, it, smem);
-            else trsv_l_item<double>(rec, it, smem);
-            break;
-        case kTrsvLT:
-            if (vk_flags(rec) & kVecF32) trsv_lt_item<float>(rec, it, smem);
-            else trsv_lt_item<double>(rec, it, smem);
-            break;
-        case kGemvL:
-            if (vk_flags(rec) & kVecF32) gemv_item<float, false>(rec, it, smem);
-            else gemv_item<double, false>(rec, it, smem);
-            break;
-        case kGemvLT:
-            if (vk_flags(rec) & kVecF32) gemv_item<float, true>(rec, it, smem);
-            else gemv_item<double, true>(rec, it, smem);
-            break;
-        case kAxpy: axpy_item(rec); break;
-        case kResid: resid_item(rec, it, smem); break;
-        case kNrm: nrm_item(rec, smem); break;
-        default: break;   // NOOP
         }
         __syncthreads();   // every thread is done with the item
         if (warp == 0) {
@@ -617,28 +635,45 @@ __global__ void init_kernel(const InitParams ip, const LaunchParams lp) {
 
 using namespace b3t;
 
-extern "C" size_t b3t_internal_smem_bytes(int has_mx) {
-    return (has_mx ? kSmemData : kSmemDataNoMx) + 1024;
+extern "C" size_t b3t_internal_smem_bytes(uint32_t variant) {
+    return ((variant & kFamMx) ? kSmemData : kSmemDataNoMx) + 1024;
 }
 
-template <bool kMx>
+template <uint32_t kVar>
 static int occupancy_of(int *ctas_per_sm, size_t smem) {
-    if (cudaFuncSetAttribute(exec_kernel<kMx>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(exec_kernel<kVar>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kSmemData + 1024)) != cudaSuccess ||
-        cudaFuncSetAttribute(exec_kernel<kMx>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) !=
+        cudaFuncSetAttribute(exec_kernel<kVar>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) !=
             cudaSuccess)
         return -EIO;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, exec_kernel<kMx>, kThreads, smem) ==
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, exec_kernel<kVar>, kThreads, smem) ==
                    cudaSuccess
                ? 0
                : -EIO;
 }
 
-extern "C" int b3t_internal_occupancy(int *ctas_per_sm, size_t smem, int *num_sms, int has_mx) {
+extern "C" int b3t_internal_occupancy(int *ctas_per_sm, size_t smem, int *num_sms, uint32_t variant) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -EIO;
-    return has_mx ? occupancy_of<true>(ctas_per_sm, smem) : occupancy_of<false>(ctas_per_sm, smem);
+    switch (variant) {
+    case kVarScal: return occupancy_of<kVarScal>(ctas_per_sm, smem);
+    case kVarF64: return occupancy_of<kVarF64>(ctas_per_sm, smem);
+    case kVarSolve: return occupancy_of<kVarSolve>(ctas_per_sm, smem);
+    case kVarNoMx: return occupancy_of<kVarNoMx>(ctas_per_sm, smem);
+    case kVarAll: return occupancy_of<kVarAll>(ctas_per_sm, smem);
+    }
+    return -EINVAL;
+}
+
+static void launch_exec(const LaunchParams *lp, int nctas, size_t smem, cudaStream_t s) {
+    switch (lp->variant) {
+    case kVarScal: exec_kernel<kVarScal><<<nctas, kThreads, smem, s>>>(*lp); break;
+    case kVarF64: exec_kernel<kVarF64><<<nctas, kThreads, smem, s>>>(*lp); break;
+    case kVarSolve: exec_kernel<kVarSolve><<<nctas, kThreads, smem, s>>>(*lp); break;
+    case kVarNoMx: exec_kernel<kVarNoMx><<<nctas, kThreads, smem, s>>>(*lp); break;
+    default: exec_kernel<kVarAll><<<nctas, kThreads, smem, s>>>(*lp); break;
+    }
 }
 
 extern "C" int b3t_internal_launch(const InitParams *ip, const LaunchParams *lp, int nctas, size_t smem,
@@ -649,8 +684,7 @@ extern "C" int b3t_internal_launch(const InitParams *ip, const LaunchParams *lp,
     ib = ib < 1 ? 1 : (ib > 4096 ? 4096 : ib);
     init_kernel<<<ib, 256, 0, s>>>(*ip, *lp);
     if (ev_start) cudaEventRecord((cudaEvent_t)ev_start, s);
-    if (lp->has_mx) exec_kernel<true><<<nctas, kThreads, smem, s>>>(*lp);
-    else exec_kernel<false><<<nctas, kThreads, smem, s>>>(*lp);
+    launch_exec(lp, nctas, smem, s);
     if (ev_stop) cudaEventRecord((cudaEvent_t)ev_stop, s);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? 0 : -EIO;
@@ -660,7 +694,6 @@ extern "C" int b3t_internal_launch_exec(const LaunchParams *lp, int nctas, size_
                                         void *ev_start) {
     cudaStream_t s = (cudaStream_t)stream;
     if (ev_start) cudaEventRecord((cudaEvent_t)ev_start, s);
-    if (lp->has_mx) exec_kernel<true><<<nctas, kThreads, smem, s>>>(*lp);
-    else exec_kernel<false><<<nctas, kThreads, smem, s>>>(*lp);
+    launch_exec(lp, nctas, smem, s);
     return cudaGetLastError() == cudaSuccess ? 0 : -EIO;
 }

@@ -325,6 +325,7 @@ int build_launch(b3t_ctx *c, Arena &a, InitParams &ip, LaunchParams &lp, int64_t
     unsigned long long cap[kMaxLevels] = {0}, rootcnt[kMaxLevels] = {0};
     int64_t nitems = 0;
     has_mx = false;
+    uint32_t fams = 0;
     for (int64_t t = 0; t < nt; ++t) {
         TaskRec &r = c->tasks[t].rec;
         r.succ_off = off[t];
@@ -340,6 +341,7 @@ int build_launch(b3t_ctx *c, Arena &a, InitParams &ip, LaunchParams &lp, int64_t
         if (indeg[t] == 0) rootcnt[lv] += 1;
         nitems += r.nitems;
         if (is_mx(r.kind)) has_mx = true;
+        fams |= family_of(r.kind);
     }
     unsigned long long ringoff[kMaxLevels] = {0}, rootoff[kMaxLevels] = {0};
     unsigned long long nslots = 0, nroots = 0;
@@ -403,6 +405,7 @@ int build_launch(b3t_ctx *c, Arena &a, InitParams &ip, LaunchParams &lp, int64_t
     lp.counters = a.counters; lp.done_items = a.done; lp.next_item = a.next;
     lp.slots = a.slots; lp.ctl = a.ctl; lp.ntasks = nt; lp.nlevels = L;
     lp.has_mx = has_mx ? 1 : 0;
+    lp.variant = variant_of(fams);
     lp.timeout_ns = c->cfg.timeout_ns;
     lp.debug = c->cfg.debug_checks;
     if (c->trace_on) { lp.trace = c->trace; lp.trace_n = c->trace_n; lp.trace_cap = c->trace_cap; }
@@ -414,10 +417,10 @@ int build_launch(b3t_ctx *c, Arena &a, InitParams &ip, LaunchParams &lp, int64_t
     return 0;
 }
 
-int grid_for(b3t_ctx *c, bool has_mx, int *nctas, size_t *smem, int free_sms = 0) {
-    *smem = b3t_internal_smem_bytes(has_mx ? 1 : 0);
+int grid_for(b3t_ctx *c, uint32_t variant, int *nctas, size_t *smem, int free_sms = 0) {
+    *smem = b3t_internal_smem_bytes(variant);
     int per_sm = 0, sms = 0;
-    int rc = b3t_internal_occupancy(&per_sm, *smem, &sms, has_mx ? 1 : 0);
+    int rc = b3t_internal_occupancy(&per_sm, *smem, &sms, variant);
     if (rc) return rc;
     if (c->cfg.ctas_per_sm > 0) per_sm = std::min(per_sm, c->cfg.ctas_per_sm);
     // B3T_CTAS_PER_SM overrides the occupancy query (1..4).  Claims never
@@ -460,7 +463,7 @@ int flush_impl(b3t_ctx *c) {
     int rc = build_launch(c, c->arena, ip, lp, nitems, has_mx);
     if (rc) { clear_batch(c); return rc; }
     int nctas; size_t smem;
-    if ((rc = grid_for(c, has_mx, &nctas, &smem))) { clear_batch(c); return rc; }
+    if ((rc = grid_for(c, lp.variant, &nctas, &smem))) { clear_batch(c); return rc; }
     rc = b3t_internal_launch(&ip, &lp, nctas, smem, c->stream, c->ev0, c->ev1);
     c->last_ntasks = (int64_t)c->tasks.size();
     c->last_nitems = nitems;
@@ -907,7 +910,7 @@ int b3t_graph_capture_end(b3t_ctx *c, b3t_graph *out) {
     int rc = build_launch(c, g.arena, ip, lp, nitems, has_mx);
     if (!rc) rc = cuda_err(cudaStreamSynchronize(c->stream));
     int nctas = 0; size_t smem = 0;
-    if (!rc) rc = grid_for(c, has_mx, &nctas, &smem);
+    if (!rc) rc = grid_for(c, lp.variant, &nctas, &smem);
     if (rc) { clear_batch(c); g.arena.release(); return rc; }
     cudaStream_t cs;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
@@ -1056,7 +1059,8 @@ int b3t_stream_open(b3t_ctx *c, int64_t max_tasks, int64_t max_edges, int32_t ma
     lp.tasks = S.tasks; lp.succ = S.succ; lp.level = S.level; lp.counters = S.counters;
     lp.done_items = S.done; lp.next_item = S.next; lp.slots = S.slots; lp.ctl = S.ctl;
     for (int l = 0; l < L; ++l) { lp.ring_off[l] = (unsigned long long)l * nt; lp.ring_cap[l] = nt; }
-    lp.ntasks = max_tasks; lp.nlevels = L; lp.has_mx = 1; lp.timeout_ns = c->cfg.timeout_ns;
+    lp.ntasks = max_tasks; lp.nlevels = L; lp.has_mx = 1; lp.variant = kVarAll;
+    lp.timeout_ns = c->cfg.timeout_ns;
     lp.debug = c->cfg.debug_checks; lp.stream_mode = 1;
     if (c->trace_on) { lp.trace = c->trace; lp.trace_n = c->trace_n; lp.trace_cap = c->trace_cap; }
     lp.sctl = S.sctl; lp.subs = S.subs; lp.sroots = S.sroots; lp.task_batch = S.task_batch;
@@ -1067,7 +1071,7 @@ int b3t_stream_open(b3t_ctx *c, int64_t max_tasks, int64_t max_edges, int32_t ma
     // could not start otherwise, and whoever waits for it would stall
     const int free_sms = c->cfg.stream_free_sms > 0 ? c->cfg.stream_free_sms : kStreamFreeSms;
     int nctas; size_t smem;
-    if ((rc = grid_for(c, true, &nctas, &smem, free_sms))) { stream_free(c); return rc; }
+    if ((rc = grid_for(c, kVarAll, &nctas, &smem, free_sms))) { stream_free(c); return rc; }
     if ((rc = b3t_internal_launch_exec(&lp, nctas, smem, c->stream, c->ev0))) { stream_free(c); return rc; }
     S.open = true;
     c->last_nctas = nctas;
