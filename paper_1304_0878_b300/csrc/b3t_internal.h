@@ -80,9 +80,10 @@ struct alignas(128) Ctl {
     int32_t err_task;            // task id that set it
     int32_t err_info;            // POTRF info (1-based global column)
     int32_t err_where;           // where it was raised (diagnostics)
-    unsigned long long retired;  // tasks retired in this launch
+    int32_t pad0[28];            // the error words alone on their line: every claim reads them
+    unsigned long long retired;  // tasks retired in this launch (every retirement adds 1)
     unsigned long long subs_consumed;   // stream mode: submissions taken in
-    int32_t pad0[24];
+    int32_t pad1[28];
     // per-level ring heads / tails, each on its own 128-byte line
     struct alignas(128) Level {
         unsigned long long head;
