@@ -133,6 +133,22 @@ def dist():
     return ws, rank, local
 
 
+def recorded_traffic(key):
+    """DRAM bytes (read + write) per launch that an ncu capture recorded for
+    this workload, or None when none exists or the kernel sources changed
+    since (paper_1304_0878_b300/ncu_traffic.json holds the source hash)."""
+    import paper_1304_0878_b300.build as pb
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1304_0878_b300", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)[key]
+    except (OSError, KeyError, ValueError):
+        return None
+    if rec.get("source_hash") != pb.source_hash():
+        return None
+    return rec["dram_bytes_read"] + rec["dram_bytes_write"]
+
+
 def max_over_ranks(ms, device=None):
     """Per-step time of the slowest rank (replicas run the same workload
     independently; the whole job is as slow as its slowest replica)."""
@@ -362,7 +378,7 @@ def run_ours(args):
                    "input_reset": "A tiles restored by a device copy inside each step",
                    "persistent_ctas": nctas},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": recorded_traffic("cholesky_fp64_n%d_b%d" % (N, b)),
                      "note": "FP64 DFMA pipe: 148 SMs x 4 flop/clk x 2032 MHz; achieved = "
                              "N^3/3 flops / persistent-kernel time"},
         "check": {"sampled_rel_residual": resid},

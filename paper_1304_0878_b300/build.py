@@ -31,6 +31,20 @@ def _inputs():
     return files
 
 
+def source_hash():
+    """SHA-256 of the library's sources (what a profile of its kernels was
+    taken on); a counter recorded for one hash is stale for any other."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(_inputs()):
+        if f == os.path.abspath(__file__):
+            continue
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode())
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def up_to_date():
     if not os.path.exists(LIB):
         return False
