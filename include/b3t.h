@@ -161,7 +161,7 @@ typedef struct b3t_panel_args {
  *               T parts), B (R, T parts), R_i (W, b3t_resid_part_elems
  *               elements): R_i <- B_i - (A X)_i in FP64 with A symmetric and
  *               only its lower tiles stored; after the b*nrhs values, R_i
- *               holds per 16-row item max|r_j|, max|x_j| and the largest
+ *               holds per 16-row item max|r_j|, max|x_j|, max|b_j| and the largest
  *               row sum of |A| (flags bit 1: X taken as 0, R_i <- B_i;
  *               bit 4: keep the row-sum partials an earlier residual wrote,
  *               for refinement steps after the first)
@@ -401,9 +401,9 @@ B3T_API int b3t_chol_solve_inv_submit(b3t_ctx *ctx, double *const *L, double *co
                                       int32_t flags);
 
 /* Elements (f64) of one RESID output part R_i: the b*nrhs residual values,
- * then per 16-row item max|r_j| and max|x_j| (nrhs each) and the largest
- * row sum of |A|.  NRM reads T such parts back to back.  0 for invalid
- * arguments. */
+ * then per 16-row item max|r_j|, max|x_j| and max|b_j| (nrhs each) and the
+ * largest row sum of |A|.  NRM reads T such parts back to back.  0 for
+ * invalid arguments. */
 B3T_API size_t b3t_resid_part_elems(int32_t b, int32_t nrhs);
 
 /* Elements (f64) of the work area b3t_ir_solve and b3t_ir_step_submit need:

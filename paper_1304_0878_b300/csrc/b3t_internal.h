@@ -49,8 +49,10 @@ constexpr int kPanelWidth = 128;          // panel width used by the Cholesky he
 
 // Elements of one part of the residual work area: b*nrhs values, then per
 // RESID item the maxima |r_j| and |x_j| and the largest row sum of |A|.
+// RESID output part: b*nrhs residual values, then per item max|r_j|,
+// max|x_j|, max|b_j| (nrhs each) and the largest |A| row sum
 B3T_HD constexpr int64_t resid_part_elems(int b, int nrhs) {
-    return (int64_t)b * nrhs + (int64_t)(b / kResidRows) * (2 * nrhs + 1);
+    return (int64_t)b * nrhs + (int64_t)(b / kResidRows) * (3 * nrhs + 1);
 }
 
 enum : int32_t {
@@ -152,6 +154,7 @@ struct LaunchParams {
     int32_t nlevels;
     int32_t has_mx;              // launch holds tcgen05 work: allocate TMEM
     uint32_t variant;            // kernel variant (family set) the launch runs
+    uint32_t fams;               // families of the launch's kinds (0: empty tasks only)
     int64_t timeout_ns;
     int32_t debug;
     int32_t stream_mode;

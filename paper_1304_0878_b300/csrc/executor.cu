@@ -653,6 +653,8 @@ __global__ void init_kernel(const InitParams ip, const LaunchParams lp) {
 using namespace b3t;
 
 extern "C" size_t b3t_internal_smem_bytes(uint32_t variant) {
+    // the vector variant needs only the SCAL ring, so three CTAs fit per SM
+    if (variant == kVarScal) return (size_t)kSbStages * kSbBytes + 1024;
     return ((variant & kFamMx) ? kSmemData : kSmemDataNoMx) + 1024;
 }
 

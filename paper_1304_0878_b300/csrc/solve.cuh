@@ -279,32 +279,37 @@ __device__ __forceinline__ void resid_body(const TaskRec &t, int item, unsigned 
             }
         }
     }
-    // residual, then per-column maxima of |r| and |x| and the largest |A| row sum
-    double *Ra = As;                        // reuse: [nrhs][RR] |r|, then [nrhs][RR] |x|
+    // residual, then per-column maxima of |r|, |x|, |b| and the largest |A| row sum
+    double *Ra = As;                        // reuse: [nrhs][RR] |r|, |x|, |b|
     double *Xa = As + RR * kMaxRhs;
+    double *Ba = Xa + RR * kMaxRhs;
 #pragma unroll
     for (int m = 0; m < NM; ++m) {
         const int jj = g + G * m;
         if (jj < nrhs) {
             const size_t o = (size_t)jj * b + r0 + r;
-            const double v = B[(size_t)i * b * nrhs + o] - acc[m];
+            const double bv = B[(size_t)i * b * nrhs + o];
+            const double v = bv - acc[m];
             Ri[o] = v;
             Ra[jj * RR + r] = fabs(v);
             Xa[jj * RR + r] = xzero ? 0.0 : fabs(X[(size_t)i * b * nrhs + o]);
+            Ba[jj * RR + r] = fabs(bv);
         }
     }
-    double *Rs = Xa + RR * kMaxRhs;         // [G][RR] partial row sums
+    double *Rs = Ba + RR * kMaxRhs;         // [G][RR] partial row sums
     Rs[g * RR + r] = rs;
     __syncthreads();
     double *Rn = Ri + (size_t)b * nrhs;
     if (tid < nrhs) {
-        double mr = 0.0, mx = 0.0;
+        double mr = 0.0, mx = 0.0, mb = 0.0;
         for (int k = 0; k < RR; ++k) {
             mr = fmax(mr, Ra[tid * RR + k]);
             mx = fmax(mx, Xa[tid * RR + k]);
+            mb = fmax(mb, Ba[tid * RR + k]);
         }
         Rn[(size_t)item * nrhs + tid] = mr;
         Rn[(size_t)nit * nrhs + (size_t)item * nrhs + tid] = mx;
+        Rn[(size_t)2 * nit * nrhs + (size_t)item * nrhs + tid] = mb;
     } else if (tid == 32 && !keep_norm) {
         double m = 0.0;
         for (int k = 0; k < RR; ++k) {
@@ -312,7 +317,7 @@ __device__ __forceinline__ void resid_body(const TaskRec &t, int item, unsigned 
             for (int q = 0; q < G; ++q) rsum += Rs[q * RR + k];
             m = fmax(m, rsum);
         }
-        Rn[(size_t)2 * nit * nrhs + item] = m;
+        Rn[(size_t)3 * nit * nrhs + item] = m;
     }
 }
 
@@ -331,21 +336,21 @@ __device__ __forceinline__ void nrm_item(const TaskRec &t, unsigned char *smem) 
     double *sm = (double *)smem;          // [4][8][32]: rmax, xmax, bmax, anorm partials
     double rm = 0.0, xm = 0.0, bm = 0.0, an = 0.0;
     const int jj = lane;
+    // every maximum comes from the RESID items' partials (B itself is not
+    // read again: its per-item maxima were recorded with the residual)
+    (void)B;
     if (jj < nrhs) {
         for (int k = warp; k < T * nit; k += 8) {
             const double *Rn = R + (size_t)(k / nit) * PR + (size_t)b * nrhs;
             const int it = k % nit;
             rm = fmax(rm, Rn[(size_t)it * nrhs + jj]);
             xm = fmax(xm, Rn[(size_t)nit * nrhs + (size_t)it * nrhs + jj]);
-        }
-        for (int k = warp; k < T * b; k += 8) {
-            const int part = k / b, row = k % b;
-            bm = fmax(bm, fabs(B[(size_t)part * b * nrhs + (size_t)jj * b + row]));
+            bm = fmax(bm, Rn[(size_t)2 * nit * nrhs + (size_t)it * nrhs + jj]);
         }
     }
     for (int k = tid; k < T * nit; k += kThreads) {
         const double *Rn = R + (size_t)(k / nit) * PR + (size_t)b * nrhs;
-        an = fmax(an, Rn[(size_t)2 * nit * nrhs + k % nit]);
+        an = fmax(an, Rn[(size_t)3 * nit * nrhs + k % nit]);
     }
     sm[0 * 256 + warp * 32 + lane] = rm;
     sm[1 * 256 + warp * 32 + lane] = xm;

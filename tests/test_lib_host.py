@@ -259,7 +259,7 @@ def test_ir_work_elems_layout():
     # residual parts, a scratch block vector and T inverted tiles, each
     # region a multiple of 32 doubles from the start
     T, b, nrhs = 5, 128, 3
-    part = b * nrhs + (b // 16) * (2 * nrhs + 1)      # 16-row residual items
+    part = b * nrhs + (b // 16) * (3 * nrhs + 1)      # 16-row residual items
     assert b3t.resid_part_elems(b, nrhs) == part
     r32 = lambda n: (n + 31) // 32 * 32    # noqa: E731
     assert b3t.ir_work_elems(T, b, nrhs) == r32(T * part) + r32(T * b * nrhs) + T * b * b
