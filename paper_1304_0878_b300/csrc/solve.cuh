@@ -181,9 +181,97 @@ __device__ __noinline__ void gemv_body(const TaskRec &t, int item, unsigned char
     }
 }
 
+// Binary32 GEMV with nrhs <= 16, one 16-row item: the warps split the
+// columns instead of taking turns on them.  Warp w owns the 64-column blocks
+// w, w + 8, ... of the item's range; it stages its block of M and of Y_k in
+// its own shared memory (no block-wide barrier per step), accumulates its
+// partial sums for all 16 x nrhs outputs (lane: row lane % 16, right-hand
+// sides lane / 16 + 2m), and one reduction over the warps ends the item.
+// Only the final sum order differs from gemv_body (binary32 either way).
+template <bool trans>
+__device__ __noinline__ void gemv_f32_split(const TaskRec &t, int item, unsigned char *smem) {
+    const double *L = (const double *)t.buf[0];
+    const double *Yk = (const double *)t.buf[1];
+    double *Yi = (double *)t.buf[2];
+    constexpr int RR = kGemvRows, NW = kThreads / 32, P = 65;
+    const int b = (int)t.n, nrhs = vk_nrhs(t), tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int r0 = item * RR, fl = vk_flags(t);
+    const int qa = (fl & kVecUpperM) ? (r0 / 64) * 64 : 0;
+    const int qb = (fl & kVecLowerM) ? r0 + RR : b;
+    float *Lw = (float *)smem + warp * (RR + 16) * P;   // [RR][P]: Lw[r*P + q] = M(r0 + r, q0 + q)
+    float *Yw = Lw + RR * P;                             // [16][P]: Yw[j*P + q] = Y_k(q0 + q, j)
+    const int r = lane & 15, jh = lane >> 4;
+    float acc[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) acc[m] = 0.f;
+    for (int q0 = qa + 64 * warp; q0 < qb; q0 += 64 * NW) {
+        // four rounds of 16 independent loads per lane (the block of M, then
+        // the block of Y_k), converted to binary32 into the warp's area
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            double v[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int e = lane + 32 * (u + 16 * h);
+                if (trans) {
+                    const int q = e & 63, rr = e >> 6;
+                    v[u] = L[(size_t)(q0 + q) + (size_t)(r0 + rr) * b];
+                } else {
+                    const int rr = e % RR, q = e / RR;
+                    v[u] = L[(size_t)(r0 + rr) + (size_t)(q0 + q) * b];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int e = lane + 32 * (u + 16 * h);
+                const int q = trans ? (e & 63) : (e / RR), rr = trans ? (e >> 6) : (e % RR);
+                Lw[rr * P + q] = (float)v[u];
+            }
+        }
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            double v[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int e = lane + 32 * (u + 16 * h), q = e & 63, jj = e >> 6;
+                v[u] = jj < nrhs ? Yk[(size_t)jj * b + q0 + q] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int e = lane + 32 * (u + 16 * h), q = e & 63, jj = e >> 6;
+                Yw[jj * P + q] = (float)v[u];
+            }
+        }
+        __syncwarp();
+#pragma unroll 8
+        for (int q = 0; q < 64; ++q) {
+            const float a = Lw[r * P + q];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) acc[m] = fmaf(a, Yw[(jh + 2 * m) * P + q], acc[m]);
+        }
+    }
+    __syncthreads();   // every warp is done with its staging area
+    float *Red = (float *)smem;                          // [NW][RR][16]
+#pragma unroll
+    for (int m = 0; m < 8; ++m) Red[(warp * RR + r) * 16 + jh + 2 * m] = acc[m];
+    __syncthreads();
+    {
+        const int rr = tid & 15, jj = tid >> 4;          // 256 threads: 16 rows x 16 rhs
+        float v = 0.f;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) v += Red[(w * RR + rr) * 16 + jj];
+        if (jj < nrhs) {
+            double *p = Yi + (size_t)jj * b + r0 + rr;
+            *p = (fl & kVecAssign) ? (double)v : *p - (double)v;
+        }
+    }
+    __syncthreads();   // the reduction area is the next item's staging area
+}
+
 template <typename Tc, bool trans>
 __device__ __forceinline__ void gemv_item(const TaskRec &t, int item, unsigned char *smem) {
-    if (vk_nrhs(t) <= kThreads / kGemvRows) gemv_body<Tc, trans, 1>(t, item, smem);
+    if (sizeof(Tc) == 4 && vk_nrhs(t) <= 16) gemv_f32_split<trans>(t, item, smem);
+    else if (vk_nrhs(t) <= kThreads / kGemvRows) gemv_body<Tc, trans, 1>(t, item, smem);
     else gemv_body<Tc, trans, 2>(t, item, smem);
 }
 
@@ -328,8 +416,7 @@ __device__ __forceinline__ void resid_item(const TaskRec &t, int item, unsigned 
 
 __device__ __forceinline__ void nrm_item(const TaskRec &t, unsigned char *smem) {
     const double *R = (const double *)t.buf[0];
-    const double *B = (const double *)t.buf[1];
-    double *eta = (double *)t.buf[2];
+    double *eta = (double *)t.buf[2];              // buf[1] (B) orders the task after B's writers
     const int b = (int)t.n, nrhs = vk_nrhs(t), T = vk_T(t), nit = b / kResidRows;
     const int64_t PR = resid_part_elems(b, nrhs);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -338,7 +425,6 @@ __device__ __forceinline__ void nrm_item(const TaskRec &t, unsigned char *smem) 
     const int jj = lane;
     // every maximum comes from the RESID items' partials (B itself is not
     // read again: its per-item maxima were recorded with the residual)
-    (void)B;
     if (jj < nrhs) {
         for (int k = warp; k < T * nit; k += 8) {
             const double *Rn = R + (size_t)(k / nit) * PR + (size_t)b * nrhs;
