@@ -394,7 +394,7 @@ B3T_API int b3t_chol_inv_submit(b3t_ctx *ctx, double *const *L, double *const *U
  *   backward, k descending: Y_k = U_k Z_k (GEMV_L, assign, upper M);
  *                           Z_i -= L_ki^T Y_k for i < k (GEMV_LT)
  * Y, Z: device f64 block vectors of T parts part_stride elements apart
- * (>= b*nrhs); Z is scratch.  Every step splits into 64-row items, so no
+ * (>= b*nrhs); Z is scratch.  Every step splits into 16-row items, so no
  * task runs a row-by-row substitution.  flags: B3T_VEC_F32. */
 B3T_API int b3t_chol_solve_inv_submit(b3t_ctx *ctx, double *const *L, double *const *U, double *Y,
                                       double *Z, int32_t T, int32_t b, int32_t nrhs, int64_t part_stride,
