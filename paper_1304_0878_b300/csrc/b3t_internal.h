@@ -22,6 +22,7 @@ constexpr int64_t kScalChunk = 1 << 16;  // f32 elements per SCAL item
 constexpr int kGemmBlk = 64;             // f64 GEMM / SYRK item: 64 x 64 of C
 constexpr int kTrsmRows = 32;            // f64 TRSM item: 32 rows of A_ik
 constexpr int kMxBlk = 128;              // MX GEMM / SYRK item: 128 x 128 of C
+constexpr int kCvtCols = 16;             // CVT item: 16 columns of the tile
 constexpr int kGemvRows = 16;            // GEMV item: 16 rows of the updated part
 constexpr int kResidRows = 16;           // RESID item: 16 rows of the residual part
 constexpr int kMaxRhs = 32;

@@ -218,14 +218,15 @@ __device__ __forceinline__ int potrf_mx_item(const TaskRec &t, double *smem, int
 }
 
 // CVT: L_kk = fp64(W_kk) on the lower triangle, 0 above.
-__device__ __forceinline__ void cvt_item(const TaskRec &t) {
+// CVT, kCvtCols columns per item (column-parallel: the conversion of a
+// diagonal tile sits on the factorisation's critical path).
+__device__ __forceinline__ void cvt_item(const TaskRec &t, int item) {
     const float *Wt = (const float *)t.buf[0];
     double *L = (double *)t.buf[1];
     const int b = (int)t.n;
-    for (size_t e = threadIdx.x; e < (size_t)b * b; e += kThreads) {
-        const int r = (int)(e % b), c = (int)(e / b);
-        L[e] = r >= c ? (double)Wt[e] : 0.0;
-    }
+    for (int c = item * kCvtCols; c < (item + 1) * kCvtCols; ++c)
+        for (int r = threadIdx.x; r < b; r += kThreads)
+            L[(size_t)r + (size_t)c * b] = r >= c ? (double)Wt[(size_t)r + (size_t)c * b] : 0.0;
 }
 
 // ------------------------------------------------------------- queue
@@ -535,8 +536,8 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
                 }
                 break;
             case kTrsmMx: if constexpr (kMx) trsm_mx_item(rec, it, (double *)smem); break;
-            case kCvt: if constexpr (kMx) cvt_item(rec); break;
-            case kQuant: if constexpr (kMx) quant_item(rec, s_red, &s_e); break;
+            case kCvt: if constexpr (kMx) cvt_item(rec, it); break;
+            case kQuant: if constexpr (kMx) quant_item(rec, it, s_red, &s_e); break;
             case kSyrkMx:
             case kGemmMx:
                 if constexpr (kMx) {

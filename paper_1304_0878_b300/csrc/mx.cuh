@@ -166,7 +166,12 @@ __device__ __forceinline__ int e4m3_scale_exp(double amax) {
 __device__ __forceinline__ int q_esize(int fmt) { return fmt == 0 ? 2 : 1; }
 
 // QUANT: L (f64 tile) -> Q (layout above).  One work item per tile.
-__device__ __forceinline__ void quant_item(const TaskRec &t, double *red, int *s_e) {
+// QUANT, one 16 KiB chunk of the Q layout per item (128 rows x 128 bytes of
+// K): chunk-parallel, so that a tile's quantisation is not one CTA's serial
+// pass on the factorisation's critical path.  For E4M3 every item forms the
+// tile's max|L| itself (the same value in every item, from an L2-resident
+// tile) so that no second pass or cross-item reduction is needed.
+__device__ __forceinline__ void quant_item(const TaskRec &t, int item, double *red, int *s_e) {
     const double *L = (const double *)t.buf[0];
     unsigned char *Q = (unsigned char *)t.buf[1];
     const int b = (int)t.n, fmt = t.aux, es = q_esize(fmt);
@@ -190,11 +195,11 @@ __device__ __forceinline__ void quant_item(const TaskRec &t, double *red, int *s
     const int G = 16 / es;                  // values per 16-byte group
     const int cpc = 128 / es;               // K values per chunk
     const int nk = b / cpc;
-    const size_t npairs = (size_t)b * (b / G);
-    for (size_t p = tid; p < npairs; p += kThreads) {
-        const int r = (int)(p % b), gg = (int)(p / b);
-        const int c0 = gg * G, kb = c0 / cpc, g = (c0 % cpc) / G;
-        const int rb = r >> 7, rr = r & 127;
+    const int rb = item / nk, kb = item % nk;
+    // 128 rows x 8 groups of the chunk: 1024 (row, group) pairs, 4 per thread
+    for (int p = tid; p < 128 * (cpc / G); p += kThreads) {
+        const int rr = p & 127, g = p >> 7;
+        const int r = rb * 128 + rr, c0 = kb * cpc + g * G;
         uint32_t w[4];
         if (fmt == 0) {
 #pragma unroll
@@ -222,7 +227,7 @@ __device__ __forceinline__ void quant_item(const TaskRec &t, double *red, int *s
         unsigned char *dst = Q + ((size_t)rb * nk + kb) * kChunkBytes + (size_t)rr * 128 + ((g ^ (rr & 7)) << 4);
         *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
     }
-    if (tid == 0) {
+    if (item == 0 && tid == 0) {
         int *tr = (int *)(Q + (size_t)b * b * es);
         tr[0] = e; tr[1] = 0; tr[2] = 0; tr[3] = 0;
     }

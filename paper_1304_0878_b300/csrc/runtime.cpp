@@ -137,7 +137,9 @@ bool has_fmt(int kind) { return kind == kSyrkMx || kind == kGemmMx || kind == kQ
 int64_t items_of(int kind, int64_t n) {
     switch (kind) {
     case kScalF32: return std::max<int64_t>(1, (n + kScalChunk - 1) / kScalChunk);
-    case kPotrf: case kPotrfMx: case kQuant: case kNoop: case kCvt: return 1;
+    case kPotrf: case kPotrfMx: case kNoop: return 1;
+    case kCvt: return n / kCvtCols;
+    case kQuant: return 1;   // set from the format at submit (one item per 16 KiB chunk)
     case kTrsm: case kTrsmMx: case kTrtri: return n / kTrsmRows;
     case kSyrk: { int64_t m = n / kGemmBlk; return m * (m + 1) / 2; }
     case kGemm: { int64_t m = n / kGemmBlk; return m * m; }
@@ -636,6 +638,8 @@ int submit_impl(b3t_ctx *c, b3t_codelet cl, const b3t_handle *handles, const uin
     }
     if (!is_panel(C.kind))
         r.nitems = (int32_t)(C.kind == kTrsvL || C.kind == kTrsvLT ? vnrhs : items_of(C.kind, r.n));
+    if (C.kind == kQuant)   // chunks of 128 rows x 128 bytes of K: (b/128) x (b*esize/128)
+        r.nitems = (int32_t)((r.n / 128) * (r.n * (r.aux == B3T_FMT_BF16 ? 2 : 1) / 128));
     const int32_t t = (int32_t)c->tasks.size();
     // expand partitioned parents to their parts; OR the modes of repeats
     std::vector<int32_t> leaves;

@@ -100,7 +100,10 @@ __device__ __forceinline__ void syrk_item(const TaskRec &t, int item, double *sm
 // kIdent: the input rows are rows r0.. of the identity (Ain is not read), so
 // X rows are rows of L^{-T}: columns before the 64-block holding r0 are zero
 // and are written as zeros without being computed.
-template <typename Tin, bool kIdent = false>
+// kPipe: the next K chunk is loaded into registers while the current one is
+// used (one memory latency per item instead of one per chunk; more
+// registers, so only the out-of-line mixed-precision TRSM uses it).
+template <typename Tin, bool kIdent = false, bool kPipe = false>
 __device__ __forceinline__ void trsm_rows(const double *L, const Tin *Ain, double *X, int r0, int n, int ld,
                                           double *smem) {
     const int b = ld;
@@ -125,20 +128,46 @@ __device__ __forceinline__ void trsm_rows(const double *L, const Tin *Ain, doubl
             if (kIdent) acc[j] = (r0 + tr == c0 + tw + 8 * j) ? 1.0 : 0.0;
             else acc[j] = (double)Ain[(size_t)(r0 + tr) + (size_t)(c0 + tw + 8 * j) * b];
         }
+        constexpr int NX = (RB * kKc) / kThreads, NL = (64 * kKc) / kThreads;
+        double xv[kPipe ? NX : 1], lv[kPipe ? NL : 1];
+        if (kPipe && cs < c0) {
+#pragma unroll
+            for (int q = 0; q < NX; ++q) {
+                const int e = tid + q * kThreads;
+                xv[q] = X[(size_t)(r0 + (e & 31)) + (size_t)(cs + (e >> 5)) * b];
+            }
+#pragma unroll
+            for (int q = 0; q < NL; ++q) {
+                const int e = tid + q * kThreads;
+                lv[q] = L[(size_t)(c0 + (e & 63)) + (size_t)(cs + (e >> 6)) * b];
+            }
+        }
         for (int k0 = cs; k0 < c0; k0 += kKc) {
 #pragma unroll
-            for (int q = 0; q < (RB * kKc) / kThreads; ++q) {
+            for (int q = 0; q < NX; ++q) {
                 const int e = tid + q * kThreads;
                 const int r = e & 31, p = e >> 5;
-                Xs[p * 33 + r] = X[(size_t)(r0 + r) + (size_t)(k0 + p) * b];
+                Xs[p * 33 + r] = kPipe ? xv[kPipe ? q : 0] : X[(size_t)(r0 + r) + (size_t)(k0 + p) * b];
             }
 #pragma unroll
-            for (int q = 0; q < (64 * kKc) / kThreads; ++q) {
+            for (int q = 0; q < NL; ++q) {
                 const int e = tid + q * kThreads;
                 const int c = e & 63, p = e >> 6;
-                Ls[p * 64 + c] = L[(size_t)(c0 + c) + (size_t)(k0 + p) * b];
+                Ls[p * 64 + c] = kPipe ? lv[kPipe ? q : 0] : L[(size_t)(c0 + c) + (size_t)(k0 + p) * b];
             }
             __syncthreads();
+            if (kPipe && k0 + kKc < c0) {
+#pragma unroll
+                for (int q = 0; q < NX; ++q) {
+                    const int e = tid + q * kThreads;
+                    xv[q] = X[(size_t)(r0 + (e & 31)) + (size_t)(k0 + kKc + (e >> 5)) * b];
+                }
+#pragma unroll
+                for (int q = 0; q < NL; ++q) {
+                    const int e = tid + q * kThreads;
+                    lv[q] = L[(size_t)(c0 + (e & 63)) + (size_t)(k0 + kKc + (e >> 6)) * b];
+                }
+            }
 #pragma unroll 8
             for (int p = 0; p < kKc; ++p) {
                 const double x = Xs[p * 33 + tr];
@@ -204,9 +233,11 @@ __device__ __forceinline__ void trtri_item(const TaskRec &t, int item, double *s
                             item * kTrsmRows, (int)t.n, (int)t.n, smem);
 }
 
-__device__ __forceinline__ void trsm_mx_item(const TaskRec &t, int item, double *smem) {
-    trsm_rows<float>((const double *)t.buf[0], (const float *)t.buf[1], (double *)t.buf[2],
-                     item * kTrsmRows, (int)t.n, (int)t.n, smem);
+// Out of line with the pipelined K loop: the mixed-precision launch runs one
+// CTA per SM, so a chunk's load latency is not hidden by a second CTA.
+__device__ __noinline__ void trsm_mx_item(const TaskRec &t, int item, double *smem) {
+    trsm_rows<float, false, true>((const double *)t.buf[0], (const float *)t.buf[1], (double *)t.buf[2],
+                                  item * kTrsmRows, (int)t.n, (int)t.n, smem);
 }
 
 // Cholesky of one n x n block in place (lower, leading dimension ld), one

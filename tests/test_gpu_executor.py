@@ -243,3 +243,47 @@ def test_trace_records_every_item(gctx):
     assert len(pairs) == nitems and {t for t, _ in pairs} == set(range(ntasks))
     assert np.all(tr["t_end_ns"] >= tr["t_start_ns"])
     assert set(tr["kind"].tolist()) <= {b3t.POTRF, b3t.TRSM, b3t.SYRK, b3t.GEMM}
+
+
+def test_kernel_variant_covers_mixed_launch(orc, gctx):
+    # one launch holding vector-scaling chains and a tiled Cholesky runs the
+    # variant compiled with both families; each part matches the oracle.  The
+    # grid shows the variant: three CTAs per SM for vector tasks alone, two
+    # for a launch with FP64 tile tasks or with empty tasks only.
+    import oracle
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n, nb = 1 << 16, 3
+    x = synth.vector_f32(nb * n, seed=3)
+    f = synth.chain_factors(nb, 4, seed=4)
+    xd = torch.from_numpy(x.copy()).cuda()
+    hs = [gctx.data_register(xd[i * n:(i + 1) * n].data_ptr(), n, 4) for i in range(nb)]
+    cl = gctx.task_decl("scale_vector", b3t.SCAL_F32, [RW], 4)
+    for k in range(4):
+        for i in range(nb):
+            gctx.task_submit(cl, [hs[i]], b3t.pack_f32(float(f[i, k])))
+    gctx.task_wait()
+    assert gctx.last_launch()["nctas"] == 3 * sms          # vector variant alone
+    N, b = 384, 128
+    A = synth.spd_host(N, seed=9, shift=1.0)
+    t = torch.from_numpy(och.to_tiles(A, b)).cuda()
+    for k in range(4):
+        for i in range(nb):
+            gctx.task_submit(cl, [hs[i]], b3t.pack_f32(float(f[i, k])))
+    gctx.cholesky_submit(dt.tile_ptrs(t), N // b, b)
+    gctx.task_wait()
+    assert gctx.last_launch()["nctas"] == 2 * sms          # vector + FP64 tiles
+    y = x.copy()
+    for _ in range(2):
+        for k in range(4):
+            for i in range(nb):
+                oracle.tiles.scal_f32(y[i * n:(i + 1) * n], f[i, k])
+    assert np.array_equal(xd.cpu().numpy().view(np.uint32), y.view(np.uint32))
+    L = np.tril(och.from_tiles(t.cpu().numpy(), N, b))
+    to = och.to_tiles(A, b)
+    assert och.run(to, N // b, b) == 0
+    Lo = np.tril(och.from_tiles(to, N, b))
+    assert np.max(np.abs(L - Lo)) / np.max(np.abs(Lo)) <= 1e-12
+    cn = gctx.task_decl("noop", b3t.NOOP, [RW])
+    gctx.task_submit(cn, [hs[0]])
+    gctx.task_wait()
+    assert gctx.last_launch()["nctas"] == 2 * sms          # empty tasks only
