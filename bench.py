@@ -486,7 +486,9 @@ def run_serving(dev, args):
                        "1-32 rhs, A = B B^T/N + I per request (seed 5)" % args.serve_requests}
     for prec in ("fp64", "bf16"):
         sstream = torch.cuda.Stream(device=dev)
-        ctx = b3t.Context(stream=sstream.cuda_stream, timeout_ns=60_000_000_000)
+        # an FP64-only stream runs the resident kernel without the tensor-memory
+        # path (two CTAs per SM)
+        ctx = b3t.Context(stream=sstream.cuda_stream, timeout_ns=60_000_000_000, stream_no_mx=prec == "fp64")
         reqs = sv.make_requests(args.serve_requests, 2000.0, 5, prec=prec)
         gen_s = sv.prepare(reqs)
         cont = sv.serve(ctx, reqs, prec=prec, budget_bytes=64 << 30, max_inflight=48, time_limit=300.0)

@@ -203,6 +203,11 @@ typedef struct b3t_config {
     int32_t stream_free_sms; /* stream mode: SMs the resident kernel leaves
                                free for other work issued meanwhile (input
                                generation, copies); 0 = 8 */
+    int32_t stream_no_mx;    /* stream mode: 1 runs the resident kernel
+                               without the tensor-memory path (two CTAs per
+                               SM instead of one, for FP64-only streams); a
+                               batch holding a mixed-precision kind is then
+                               refused (-EINVAL) */
 } b3t_config;
 
 enum { B3T_PRIO_UPWARD = 0, B3T_PRIO_DEPTH = 1 };

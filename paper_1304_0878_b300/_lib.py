@@ -36,7 +36,7 @@ class Config(ctypes.Structure):
     _fields_ = [("timeout_ns", ctypes.c_int64), ("ctas_per_sm", ctypes.c_int32),
                 ("prio_levels", ctypes.c_int32), ("debug_checks", ctypes.c_int32),
                 ("host_only", ctypes.c_int32), ("prio_policy", ctypes.c_int32),
-                ("stream_free_sms", ctypes.c_int32)]
+                ("stream_free_sms", ctypes.c_int32), ("stream_no_mx", ctypes.c_int32)]
 
 
 _lib = None
@@ -154,9 +154,9 @@ class Context:
     as ``torch.cuda.current_stream().cuda_stream``)."""
 
     def __init__(self, stream=0, timeout_ns=0, ctas_per_sm=0, prio_levels=0, debug=False,
-                 host_only=False, prio_policy=0):
+                 host_only=False, prio_policy=0, stream_free_sms=0, stream_no_mx=False):
         cfg = Config(timeout_ns, ctas_per_sm, prio_levels, 1 if debug else 0, 1 if host_only else 0,
-                     prio_policy)
+                     prio_policy, stream_free_sms, 1 if stream_no_mx else 0)
         h = _vp()
         _check(lib().b3t_init(ctypes.byref(h), ctypes.byref(cfg), _vp(stream or 0)), "b3t_init")
         self._h = h

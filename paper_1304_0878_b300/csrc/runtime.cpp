@@ -1067,7 +1067,9 @@ int b3t_stream_open(b3t_ctx *c, int64_t max_tasks, int64_t max_edges, int32_t ma
     lp.tasks = S.tasks; lp.succ = S.succ; lp.level = S.level; lp.counters = S.counters;
     lp.done_items = S.done; lp.next_item = S.next; lp.slots = S.slots; lp.ctl = S.ctl;
     for (int l = 0; l < L; ++l) { lp.ring_off[l] = (unsigned long long)l * nt; lp.ring_cap[l] = nt; }
-    lp.ntasks = max_tasks; lp.nlevels = L; lp.has_mx = 1; lp.variant = kVarAll; lp.fams = kVarAll;
+    const uint32_t svar = c->cfg.stream_no_mx ? kVarNoMx : kVarAll;
+    lp.ntasks = max_tasks; lp.nlevels = L; lp.has_mx = c->cfg.stream_no_mx ? 0 : 1;
+    lp.variant = svar; lp.fams = svar;
     lp.timeout_ns = c->cfg.timeout_ns;
     lp.debug = c->cfg.debug_checks; lp.stream_mode = 1;
     if (c->trace_on) { lp.trace = c->trace; lp.trace_n = c->trace_n; lp.trace_cap = c->trace_cap; }
@@ -1079,7 +1081,7 @@ int b3t_stream_open(b3t_ctx *c, int64_t max_tasks, int64_t max_edges, int32_t ma
     // could not start otherwise, and whoever waits for it would stall
     const int free_sms = c->cfg.stream_free_sms > 0 ? c->cfg.stream_free_sms : kStreamFreeSms;
     int nctas; size_t smem;
-    if ((rc = grid_for(c, kVarAll, &nctas, &smem, free_sms))) { stream_free(c); return rc; }
+    if ((rc = grid_for(c, svar, &nctas, &smem, free_sms))) { stream_free(c); return rc; }
     if ((rc = b3t_internal_launch_exec(&lp, nctas, smem, c->stream, c->ev0))) { stream_free(c); return rc; }
     S.open = true;
     c->last_nctas = nctas;
@@ -1092,6 +1094,9 @@ int b3t_stream_submit(b3t_ctx *c, int32_t *batch_id) {
     if (!S.open) return -EINVAL;
     const int64_t nt = (int64_t)c->tasks.size(), ne = (int64_t)c->edges.size();
     if (nt == 0) return -EINVAL;
+    if (c->cfg.stream_no_mx)   // the resident kernel was compiled without these kinds
+        for (const auto &tk : c->tasks)
+            if (family_of(tk.rec.kind) & kFamMx) return -EINVAL;
     if (S.ntasks + nt > S.max_tasks || S.nedges + ne > S.max_edges || S.nroots + nt > S.max_tasks ||
         S.nbatches >= S.max_batches)
         return -ENOMEM;

@@ -32,7 +32,9 @@ def test_serve_mix_equals_alone(orc, prec, tol, n, nmin, nmax, inflight):
     reqs = requests(n, 400.0, prec, nmin, nmax)
     sv.prepare(reqs)
     side = torch.cuda.Stream()
-    ctx = b3t.Context(stream=side.cuda_stream, timeout_ns=20_000_000_000)
+    # FP64 requests are served by the resident kernel without the
+    # tensor-memory path (two CTAs per SM)
+    ctx = b3t.Context(stream=side.cuda_stream, timeout_ns=20_000_000_000, stream_no_mx=prec == "fp64")
     st = sv.serve(ctx, reqs, prec=prec, budget_bytes=2 << 30, max_inflight=inflight, time_limit=120.0,
                   max_tasks=1 << 20, max_edges=1 << 22, keep_x=True)
     ctx.close()

@@ -136,3 +136,29 @@ def test_stream_busy_buffer_and_deadline(orc):
         ctx.stream_close()
     assert e.value.code == b3t._lib.ETIMEDOUT and time.time() - t0 < 30
     ctx.close()
+
+
+def test_stream_without_tensor_memory(orc):
+    # an FP64-only stream runs the resident kernel without the tensor-memory
+    # path (two CTAs per SM): factorisations in it equal the same work alone
+    sizes = [(512, 128), (768, 256), (384, 128)]
+    mats = [synth.spd_host(N, seed=60 + k, shift=1.0) for k, (N, b) in enumerate(sizes)]
+    alone = [factor_alone(A, b) for A, (N, b) in zip(mats, sizes)]
+    s = torch.cuda.Stream()
+    _streams.append(s)
+    ctx = b3t.Context(stream=s.cuda_stream, timeout_ns=20_000_000_000, stream_no_mx=True)
+    ctx.stream_open(1 << 16, 1 << 18, 16, 60_000_000_000)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert ctx.last_launch()["nctas"] == 2 * (sms - 8)     # 8 SMs left free
+    tiles, ids = [], []
+    for A, (N, b) in zip(mats, sizes):
+        t = torch.from_numpy(och.to_tiles(A, b)).cuda()
+        tiles.append(t)
+        ctx.cholesky_submit(dt.tile_ptrs(t), N // b, b)
+        ids.append(ctx.stream_submit())
+    infos = wait_batches(ctx, ids)
+    ctx.stream_close()
+    assert all(v == 0 for v in infos.values())
+    for t, ref in zip(tiles, alone):
+        assert np.array_equal(t.cpu().numpy(), ref)
+    ctx.close()
