@@ -251,7 +251,14 @@ __device__ __forceinline__ void push_roots(const LaunchParams &p, const SubDesc 
     __syncwarp();
 }
 
-__device__ __forceinline__ unsigned long long claim(const LaunchParams &p, uint64_t kstart, uint32_t &nclaims) {
+// Up to kBatch ready single-item tasks are taken with one CAS of the head
+// when the level holds more than twice as many of them as the grid has CTAs
+// (the head is the serialisation point of a DAG of short tasks); the extra
+// ones are kept in pend[] (shared, warp 0 only) and run next.
+constexpr int kBatch = 4;
+
+__device__ __forceinline__ unsigned long long claim(const LaunchParams &p, uint64_t kstart, uint32_t &nclaims,
+                                                    unsigned long long *pend, int *npend) {
     const int lane = threadIdx.x & 31;
     Ctl *ctl = p.ctl;
     const uint64_t t0 = gtimer();
@@ -287,6 +294,7 @@ __device__ __forceinline__ unsigned long long claim(const LaunchParams &p, uint6
         if (mask) {
             const int lv = 31 - __clz(mask);
             const unsigned long long hv = __shfl_sync(0xffffffffu, h, lv);
+            const unsigned long long tv = __shfl_sync(0xffffffffu, tl, lv);
             unsigned long long item = kEmpty;
             int got = 0;
             if (lane == 0) {
@@ -311,10 +319,22 @@ __device__ __forceinline__ unsigned long long claim(const LaunchParams &p, uint6
                         const int64_t t = (int64_t)(v >> 32);
                         const int n = (int)(v & 0xffffffffu);
                         if (n == 1) {
-                            // single-item task: taking the head slot is taking the task
-                            if (atomicCAS(&ctl->lvl[lv].head, hv, hv + 1) == hv) {
+                            // single-item task: taking the head slot is taking the task;
+                            // with many ready, the next filled single-item slots too
+                            int k = 1;
+                            unsigned long long more[kBatch - 1];
+                            if (tv - hv > 2ull * gridDim.x) {
+                                while (k < kBatch && hv + k < tv) {
+                                    const unsigned long long w = ld_acq(slot + k);
+                                    if (w == kEmpty || (int)(w & 0xffffffffu) != 1) break;
+                                    more[k - 1] = w;
+                                    ++k;
+                                }
+                            }
+                            if (atomicCAS(&ctl->lvl[lv].head, hv, hv + k) == hv) {
                                 item = (unsigned long long)t << 32;
                                 got = 1;
+                                for (int q = k - 1; q >= 1; --q) pend[(*npend)++] = (more[q - 1] >> 32) << 32;
                             } else {
                                 got = 3;   // lost the race for the head
                             }
@@ -465,14 +485,29 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
     }
     const uint64_t kstart = gtimer();
     __shared__ TaskRec s_rec;
-    // warp 0: an item of the previous task taken when that item finished
+    // warp 0: an item of the previous task taken when that item finished,
+    // and single-item tasks taken together with an earlier claim
     unsigned long long fi = kEmpty;
     uint32_t nclaims = 0;
+    __shared__ unsigned long long s_pend[kBatch];
+    __shared__ int s_npend;
+    if (tid == 0) s_npend = 0;
     for (;;) {
         if (warp == 0) {
             const int lane = tid & 31;
             const bool same = fi != kEmpty;
-            const unsigned long long it = same ? fi : claim(p, kstart, nclaims);
+            __syncwarp();
+            const int np = s_npend;
+            unsigned long long it;
+            if (same) {
+                it = fi;
+            } else if (np > 0) {
+                it = s_pend[np - 1];
+                __syncwarp();
+                if (lane == 0) s_npend = np - 1;
+            } else {
+                it = claim(p, kstart, nclaims, s_pend, &s_npend);
+            }
             const int64_t t = (int64_t)(it >> 32);
             if (!same && it != kEmpty && (!p.debug || t < p.ntasks) && lane < 4)
                 reinterpret_cast<uint4 *>(&s_rec)[lane] = __ldcg(reinterpret_cast<const uint4 *>(p.tasks + t) + lane);
