@@ -251,11 +251,11 @@ __device__ __forceinline__ void push_roots(const LaunchParams &p, const SubDesc 
     __syncwarp();
 }
 
-// Up to kBatch ready single-item tasks are taken with one CAS of the head
+// Up to kBatch (8) ready single-item tasks are taken with one CAS of the head
 // when the level holds more than twice as many of them as the grid has CTAs
 // (the head is the serialisation point of a DAG of short tasks); the extra
 // ones are kept in pend[] (shared, warp 0 only) and run next.
-constexpr int kBatch = 4;
+constexpr int kBatch = 8;
 
 __device__ __forceinline__ unsigned long long claim(const LaunchParams &p, uint64_t kstart, uint32_t &nclaims,
                                                     unsigned long long *pend, int *npend) {
