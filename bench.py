@@ -9,10 +9,13 @@ CUDA graph and replayed).  Metric: TFLOP/s = (N^3/3 + N^2/2 + N/6) / time.
 
 Secondary (same JSON line, "secondary"): vector-scaling chains (n = 2^28
 binary32, 256 blocks x 8 chained RW tasks) in task-level GB/s, scheduler
-throughput in tasks/s on empty-bodied DAGs, and the small Cholesky
-(N = 1024, tile 128, 120 tasks) in ms.
+throughput in tasks/s on empty-bodied DAGs (1000 chains; fan-out / fan-in;
+the Cholesky DAG at T = 64), the small Cholesky (N = 1024, tile 128, 120
+tasks) in ms, time to solution with mixed precision and refinement, and
+serving with continuous batching against the per-request path.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --case serve_sweep | trace_headline | empty_dags | <kind>
 
 --impl reference times the oracle (the sequential CPU executor) on the same
 workload, a bounded sample of it per step, on the host cores.
@@ -63,9 +66,13 @@ def parse():
     p.add_argument("--nrhs", type=int, default=16)
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--serve-requests", type=int, default=96)
+    p.add_argument("--prio", default="upward", choices=["upward", "depth"],
+                   help="ready-queue order of the profiling cases (--case)")
+    p.add_argument("--ctas-per-sm", type=int, default=0, help="grid of the profiling cases (0: occupancy)")
     p.add_argument("--case", default=None, choices=["mx_gemm_bf16", "mx_gemm_e4m3", "scal", "resid", "solve_f32",
-                                                    "solve_f64"],
-                   help="run a DAG of one task kind only (profiling case) and print its timing")
+                                                    "solve_f64", "empty_dags", "serve_sweep", "trace_headline"],
+                   help="run one profiling case (a DAG of one task kind), or one secondary measurement alone "
+                        "(empty_dags, serve_sweep, trace_headline), and print its result")
     return p.parse_args()
 
 
@@ -349,6 +356,8 @@ def run_ours(args):
         def get(i, j):
             return A0[tile_index(i, j, T)].cpu().numpy()
         cpu = oracle_sample(get, T, b, args.cpu_seconds)
+        if not args.no_secondary:
+            cpu["empty_dags"] = oracle_empty_dags(min(3.0, args.cpu_seconds / 5))
 
     secondary = {}
     if not args.no_secondary:
@@ -503,6 +512,140 @@ def run_serving(dev, args):
     return out
 
 
+EMPTY_DAGS = (("chains", "1000 chains x 1000 RW tasks, submitted level by level (1M tasks)"),
+              ("fan", "1000 rounds of one writer of a shared buffer and 999 readers of it that each "
+                      "update a buffer of their own (fan-out, then a 999-way fan-in; 1M tasks)"),
+              ("cholesky", "the tiled Cholesky DAG at T = 64 with empty bodies (45,760 tasks)"))
+
+
+def empty_dag(shape):
+    """An empty-bodied DAG for scheduler throughput: the codelets' access
+    modes, the number of buffers, the task count and a generator of
+    (codelet, buffers) in submission order (the runtime derives the edges)."""
+    R_, RW_ = 1, 3
+    if shape == "chains":
+        def gen():
+            for _ in range(1000):
+                for h in range(1000):
+                    yield 0, (h,)
+        return [[RW_]], 1000, 10 ** 6, gen
+    if shape == "fan":
+        def gen():
+            for _ in range(1000):
+                yield 0, (0,)
+                for i in range(1, 1000):
+                    yield 1, (0, i)
+        return [[RW_], [R_, RW_]], 1000, 10 ** 6, gen
+    T = 64
+
+    def ix(i, j):
+        return i * (i + 1) // 2 + j
+
+    def gen():
+        # POTRF(kk); TRSM(kk, ik); SYRK(ik, ii); GEMM(ik, jk, ij) in
+        # right-looking order (Section 5.2's tiled factorisation)
+        for k in range(T):
+            yield 0, (ix(k, k),)
+            for i in range(k + 1, T):
+                yield 1, (ix(k, k), ix(i, k))
+            for i in range(k + 1, T):
+                yield 1, (ix(i, k), ix(i, i))
+                for j in range(k + 1, i):
+                    yield 2, (ix(i, k), ix(j, k), ix(i, j))
+    return [[RW_], [R_, RW_], [R_, R_, RW_]], T * (T + 1) // 2, len_tasks(T), gen
+
+
+def run_empty_dags(dev, stream):
+    """Tasks/s of the persistent executor on the three empty-bodied DAGs
+    (device time of one launch; the host's submission time apart)."""
+    import torch
+    import paper_1304_0878_b300 as b3t
+    out = {}
+    for shape, desc in EMPTY_DAGS:
+        modes, nh, nt, gen = empty_dag(shape)
+        ctx = b3t.Context(stream=stream.cuda_stream, timeout_ns=60_000_000_000)
+        buf = torch.zeros(nh * 16, device=dev)
+        hs = [ctx.data_register(buf[i * 16:(i + 1) * 16].data_ptr(), 16, 4) for i in range(nh)]
+        cls = [ctx.task_decl("empty", b3t.NOOP, m) for m in modes]
+        t0 = time.perf_counter()
+        ctx.graph_capture_begin()
+        for c, bs in gen():
+            ctx.task_submit(cls[c], [hs[h] for h in bs])
+        ntasks, nedges = ctx.dag_stats()
+        g = ctx.graph_capture_end()
+        host_s = time.perf_counter() - t0
+        ts = []
+        for r in range(7):
+            ctx.graph_replay(g)
+            ctx.task_wait()
+            if r >= 2:
+                ts.append(ctx.last_launch()["kernel_ns"] / 1e9)
+        med = float(np.median(ts))
+        out[shape] = {"workload": desc, "tasks": ntasks, "edges": nedges, "ms": 1e3 * med,
+                      "tasks_per_s": ntasks / med, "host_submit_s": host_s,
+                      "host_submit_tasks_per_s": ntasks / host_s}
+        ctx.graph_destroy(g)
+        ctx.close()
+        del buf
+    return out
+
+
+def oracle_empty_dags(seconds):
+    """The oracle executor (each task run at submission, empty bodies) on a
+    bounded prefix of each empty-bodied DAG, one core: tasks/s."""
+    from oracle import executor as oex
+    out = {}
+    for shape, _ in EMPTY_DAGS:
+        modes, nh, nt, gen = empty_dag(shape)
+        ex = oex.Executor()
+        hs = [ex.data_register(np.zeros(16, np.float32)) for _ in range(nh)]
+        cls = [ex.task_decl("empty", oex.noop_body, m) for m in modes]
+        n = 0
+        t0 = time.perf_counter()
+        for c, bs in gen():
+            ex.task_submit(cls[c], [hs[h] for h in bs])
+            n += 1
+            if (n & 1023) == 0 and time.perf_counter() - t0 > seconds:
+                break
+        sec = time.perf_counter() - t0
+        out[shape] = {"tasks_per_s": n / sec, "cores": 1, "kind": "oracle",
+                      "sample": "first %d of %d tasks in %.2f s" % (n, nt, sec)}
+    return out
+
+
+SWEEP_RATES = {"fp64": (10.0, 20.0, 40.0, 80.0, 160.0, 2000.0), "bf16": (20.0, 40.0, 80.0, 160.0, 320.0, 2000.0)}
+
+
+def run_serve_sweep(dev, args):
+    """Continuous batching at a range of offered rates (the same requests:
+    the generator draws arrival gaps as unit exponentials over the rate, so
+    sizes and seeds do not depend on it).  The largest sustainable rate is
+    the highest offered rate whose p99 latency stays within twice the p99 at
+    the lowest rate of the sweep (the queue does not build up)."""
+    import torch
+    import paper_1304_0878_b300 as b3t
+    from paper_1304_0878_b300 import serve as sv
+    out = {"workload": "first %d requests of the seed-5 stream, N log-uniform [256, 8192], 1-32 rhs, "
+                       "at each offered rate" % args.serve_requests}
+    for prec, rates in SWEEP_RATES.items():
+        rows = []
+        for rate in rates:
+            sstream = torch.cuda.Stream(device=dev)
+            ctx = b3t.Context(stream=sstream.cuda_stream, timeout_ns=60_000_000_000, stream_no_mx=prec == "fp64")
+            reqs = sv.make_requests(args.serve_requests, rate, 5, prec=prec)
+            sv.prepare(reqs)
+            st = sv.serve(ctx, reqs, prec=prec, budget_bytes=64 << 30, max_inflight=48, time_limit=300.0)
+            ctx.close()
+            rows.append({"offered_per_s": rate, "solves_per_s": st["solves_per_s"], "p50_ms": st["p50_ms"],
+                         "p99_ms": st["p99_ms"], "failed": st["failed"], "max_eta": st["max_eta"]})
+            del reqs
+            torch.cuda.empty_cache()
+        slo = 2.0 * rows[0]["p99_ms"]
+        ok = [r["offered_per_s"] for r in rows if r["p99_ms"] <= slo and r["failed"] == 0]
+        out[prec] = {"rates": rows, "p99_bound_ms": slo, "max_sustainable_rate_per_s": max(ok) if ok else None}
+    return out
+
+
 def run_secondary(ctx, dev, stream):
     """Vector chains (config 2), tasks/s on empty-bodied DAGs, small Cholesky."""
     import torch
@@ -560,6 +703,8 @@ def run_secondary(ctx, dev, stream):
     ctx.graph_destroy(g)
     for h in hy:
         ctx.data_unregister(h)
+    del y
+    out["empty_dags"] = run_empty_dags(dev, stream)
     # small Cholesky, N = 1024, tile 128 (config 1): latency of one launch
     N1, b1 = 1024, 128
     A1 = dt.to_tiles(torch.from_numpy(synth.spd_host(N1, seed=0, shift=1.0)).to(dev), b1)
@@ -592,7 +737,9 @@ def run_case(args):
     import paper_1304_0878_b300.build as pb
     pb.build()
     dev = torch.device("cuda", 0)
-    ctx = b3t.Context(stream=torch.cuda.current_stream().cuda_stream, timeout_ns=60_000_000_000)
+    ctx = b3t.Context(stream=torch.cuda.current_stream().cuda_stream, timeout_ns=60_000_000_000,
+                      ctas_per_sm=args.ctas_per_sm,
+                      prio_policy=b3t.PRIO_DEPTH if args.prio == "depth" else b3t.PRIO_UPWARD)
     b = 512
     if args.case.startswith("mx_gemm"):
         # 64 independent GEMM_MX updates W_i -= Q_a Q_b^T (b = 512): 64 x 2 b^3 flop
@@ -676,14 +823,98 @@ def run_case(args):
     med = float(np.median(ts))
     scale = 1e12 if unit == "TFLOP/s" else 1e9
     print(json.dumps({"case": args.case, "kernel_ms": med * 1e3, "value": work / med / scale, "unit": unit,
-                      "nctas": ctx.last_launch()["nctas"]}))
+                      "nctas": ctx.last_launch()["nctas"], "prio": args.prio}))
     ctx.graph_destroy(g)
     ctx.close()
 
 
+KIND_NAMES = {0: "NOOP", 1: "SCAL", 2: "POTRF", 3: "TRSM", 4: "SYRK", 5: "GEMM", 18: "POTRF_D",
+              19: "PANEL_TRSM", 20: "PANEL_UPD"}
+
+
+def run_trace_headline(dev, args):
+    """One traced factorisation of the headline workload: how busy the CTAs
+    were, each task kind's share of the CTA time, and the longest chain of
+    task spans (first item's start to last item's end) through the DAG, its
+    critical path, against the launch's makespan."""
+    import torch
+    import synth
+    import paper_1304_0878_b300 as b3t
+    from paper_1304_0878_b300 import tiles as dt
+    N, b = args.n, args.b
+    T = N // b
+    ctx = b3t.Context(stream=torch.cuda.current_stream(dev).cuda_stream, timeout_ns=120_000_000_000)
+    t = synth.spd_tiles_device(N, b, 3, 0.1, dev)
+    ctx.trace_start(1 << 22)
+    ctx.cholesky_submit(dt.tile_ptrs(t), T, b)
+    ntasks, nedges = ctx.dag_stats()
+    ed = np.array(ctx.dag_edges(), dtype=np.int64).reshape(-1, 2)
+    ctx.task_wait()
+    tr = ctx.trace_read()
+    ctx.trace_stop()
+    ll = ctx.last_launch()
+    ctx.close()
+    assert len(tr) == ll["nitems"], "trace buffer too small"
+    out = {"workload": "FP64 Cholesky N=%d tile %d, one traced launch" % (N, b), "tasks": ntasks,
+           "edges": nedges, "items": int(len(tr)), "ctas": ll["nctas"], "traced_kernel_ms": ll["kernel_ns"] / 1e6}
+    out.update(trace_summary(tr, ntasks, ed, ll["nctas"]))
+    return out
+
+
+def trace_summary(tr, ntasks, ed, nctas):
+    """Makespan, CTA busy fraction, per-kind share of the CTA time, the
+    critical path (longest chain of task spans along the edges `ed`, which
+    point from earlier to later submissions) and the number of edges whose
+    successor started before its predecessor ended (0 for a legal run)."""
+    st = tr["t_start_ns"].astype(np.int64)
+    en = tr["t_end_ns"].astype(np.int64)
+    t0 = int(st.min())
+    makespan = int(en.max()) - t0
+    dur = en - st
+    kinds = {}
+    for k in np.unique(tr["kind"]):
+        m = tr["kind"] == k
+        kinds[KIND_NAMES.get(int(k), str(int(k)))] = {"items": int(m.sum()),
+                                                      "cta_time_share": float(dur[m].sum() / dur.sum()),
+                                                      "mean_item_us": float(dur[m].mean() / 1e3)}
+    ts = np.full(ntasks, np.iinfo(np.int64).max, dtype=np.int64)
+    te = np.zeros(ntasks, dtype=np.int64)
+    np.minimum.at(ts, tr["task"], st)
+    np.maximum.at(te, tr["task"], en)
+    span = te - ts
+    order = np.argsort(ed[:, 1], kind="stable")
+    preds, succ_of = ed[order, 0], ed[order, 1]
+    first = np.searchsorted(succ_of, np.arange(ntasks + 1))
+    cp = span.astype(np.float64)
+    for v in range(ntasks):
+        a, z = first[v], first[v + 1]
+        if z > a:
+            cp[v] += cp[preds[a:z]].max()
+    return {"makespan_ms": makespan / 1e6, "cta_busy_frac": float(dur.sum()) / (nctas * makespan),
+            "critical_path_ms": float(cp.max()) / 1e6, "critical_path_share": float(cp.max()) / makespan,
+            "edges_violated": int(np.sum(te[ed[:, 0]] > ts[ed[:, 1]])), "kinds": kinds}
+
+
+def run_part(args):
+    """One secondary measurement alone, printed as one JSON line."""
+    import torch
+    import paper_1304_0878_b300.build as pb
+    pb.build()
+    dev = torch.device("cuda", 0)
+    if args.case == "empty_dags":
+        res = run_empty_dags(dev, torch.cuda.current_stream(dev))
+    elif args.case == "trace_headline":
+        res = run_trace_headline(dev, args)
+    else:
+        res = run_serve_sweep(dev, args)
+    print(json.dumps({"case": args.case, "result": res}))
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.case:
+    if a.case in ("empty_dags", "serve_sweep", "trace_headline"):
+        run_part(a)
+    elif a.case:
         run_case(a)
     elif a.impl == "reference":
         run_reference(a)

@@ -58,6 +58,23 @@ def test_scal_chains_bit_exact(orc, gctx, nb, n, order):
     assert np.array_equal(y.view(np.uint32), z.view(np.uint32))
 
 
+@pytest.mark.parametrize("nb,n", [(8, 3 * (1 << 14) + 12), (4, (1 << 16) + 12), (1, 2 * (1 << 14) + 7)])
+def test_scal_chains_successor_first_bit_exact(orc, nb, n):
+    # under the successor-first order (a block's next task is claimed before
+    # other blocks' first tasks) with a ragged last item, and a single block
+    # with a tail of fewer than four elements (blocks start 16-byte aligned,
+    # as submission requires): still exactly the in-order binary32 multiplies
+    c = b3t.Context(stream=torch.cuda.current_stream().cuda_stream, timeout_ns=20_000_000_000,
+                    prio_policy=b3t.PRIO_DEPTH)
+    x = synth.vector_f32(nb * n, seed=21)
+    x[:5] = np.array([1e-38, -3e-39, 5e-45, -0.0, 3e38], dtype=np.float32)
+    f = synth.chain_factors(nb, 8, seed=22)
+    y = run_chain_device(c, x, f, "b")
+    c.close()
+    z = run_chain_oracle(x, f)
+    assert np.array_equal(y.view(np.uint32), z.view(np.uint32))
+
+
 def test_scal_full_size_config(orc, gctx):
     # n = 2^28, 256 blocks x 8 chained tasks: compared element-wise against
     # in-order binary32 multiplies on sampled blocks (the whole vector fits
@@ -287,3 +304,65 @@ def test_kernel_variant_covers_mixed_launch(orc, gctx):
     gctx.task_submit(cn, [hs[0]])
     gctx.task_wait()
     assert gctx.last_launch()["nctas"] == 2 * sms          # empty tasks only
+
+
+def _task_spans(tr, ntasks):
+    start = np.full(ntasks, np.iinfo(np.uint64).max, dtype=np.uint64)
+    end = np.zeros(ntasks, dtype=np.uint64)
+    np.minimum.at(start, tr["task"], tr["t_start_ns"])
+    np.maximum.at(end, tr["task"], tr["t_end_ns"])
+    return start, end
+
+
+@pytest.mark.parametrize("shape", ["random", "fan", "cholesky"])
+def test_execution_order_respects_every_edge(orc, gctx, shape):
+    # The order the persistent kernel ran the tasks in is one the DAG allows
+    # (Section 3: any order that keeps each access's predecessors first
+    # gives the sequential program's result).  From the trace (the device's
+    # global nanosecond timer): every task's first item started no earlier
+    # than the last item of each of its predecessors ended.  The edges are
+    # the oracle's, derived from the same accesses.
+    from oracle import dag
+    if shape == "cholesky":
+        T, b = 6, 128
+        A = torch.from_numpy(och.to_tiles(synth.spd_host(T * b, seed=13, shift=1.0), b)).cuda()
+        gctx.trace_start(1 << 16)
+        gctx.cholesky_submit(dt.tile_ptrs(A), T, b)
+        acc = och.accesses(T)
+    else:
+        if shape == "random":
+            nh = 12
+            acc = synth.random_accesses(3000, nhandles=nh, maxbuf=3, seed=77)
+        else:
+            # 20 rounds: one writer of buffer 0, then 63 readers of it that
+            # each update a buffer of their own
+            nh = 64
+            acc = [a for _ in range(20) for a in [[(0, RW)]] + [[(0, R), (i, RW)] for i in range(1, nh)]]
+        x = torch.zeros(nh * 64, device="cuda")
+        hs = [gctx.data_register(x[i * 64:(i + 1) * 64].data_ptr(), 64, 4) for i in range(nh)]
+        cls = {}
+        gctx.trace_start(1 << 16)
+        for a in acc:
+            modes = tuple(m for _, m in a)
+            if modes not in cls:
+                cls[modes] = gctx.task_decl("empty", b3t.NOOP, list(modes))
+            gctx.task_submit(cls[modes], [hs[h] for h, _ in a])
+    edges = dag.derive_edges(acc)
+    assert sorted(gctx.dag_edges()) == edges
+    gctx.task_wait()
+    tr = gctx.trace_read()
+    gctx.trace_stop()
+    ntasks = gctx.last_launch()["ntasks"]
+    assert ntasks == len(acc) and len(tr) == gctx.last_launch()["nitems"]
+    start, end = _task_spans(tr, ntasks)
+    e = np.array(edges, dtype=np.int64).reshape(-1, 2)
+    bad = np.nonzero(end[e[:, 0]] > start[e[:, 1]])[0]
+    assert bad.size == 0, [(tuple(e[k]), int(end[e[k, 0]]), int(start[e[k, 1]])) for k in bad[:5]]
+    if shape == "cholesky":
+        L = np.tril(och.from_tiles(A.cpu().numpy(), T * b, b))
+        Lo, info = och.dense_potrf(synth.spd_host(T * b, seed=13, shift=1.0))
+        assert info == 0
+        assert np.max(np.abs(L - np.tril(Lo))) / np.max(np.abs(Lo)) <= FP64_TOL
+    else:
+        for h in hs:
+            gctx.data_unregister(h)

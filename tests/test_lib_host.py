@@ -264,3 +264,51 @@ def test_ir_work_elems_layout():
     r32 = lambda n: (n + 31) // 32 * 32    # noqa: E731
     assert b3t.ir_work_elems(T, b, nrhs) == r32(T * part) + r32(T * b * nrhs) + T * b * b
     assert b3t.ir_work_elems(T, 100, nrhs) == 0
+
+
+def test_fan_out_fan_in_edges(ctx):
+    # one writer of buffer 0, then readers of it that each update a buffer
+    # of their own, repeated: each writer waits for every reader of the
+    # round before (write after read), each reader for the writer
+    nh, rounds = 17, 5
+    acc = [a for _ in range(rounds) for a in [[(0, RW)]] + [[(0, R), (i, RW)] for i in range(1, nh)]]
+    _submit_accesses(ctx, acc, nh)
+    ed = sorted(ctx.dag_edges())
+    assert ed == dag.derive_edges(acc)
+    assert ctx.dag_stats() == (rounds * nh, (rounds - 1) * (nh - 1) * 3 + (nh - 1))
+
+
+def test_bench_empty_dags_follow_the_oracle():
+    # the scheduler-throughput DAGs: the Cholesky-shaped one submits the
+    # oracle's accesses in the oracle's order; the others have the stated
+    # task and edge counts under the oracle's rule
+    import bench
+    for shape, _ in bench.EMPTY_DAGS:
+        modes, nh, nt, gen = bench.empty_dag(shape)
+        acc = [[(h, modes[c][k]) for k, h in enumerate(bs)] for c, bs in gen()]
+        assert len(acc) == nt and max(h for a in acc for h, _ in a) == nh - 1
+        if shape == "cholesky":
+            T = 64
+            ref = [[(i * (i + 1) // 2 + j, m) for (i, j), m in a] for _, a in och.task_list(T)]
+            assert acc == ref
+            assert len(dag.derive_edges(acc)) == 131040
+
+
+def test_bench_trace_summary():
+    # critical path = longest chain of task spans along the edges; busy
+    # fraction = item time over CTAs x makespan; a late successor is counted
+    import bench
+    rec = np.dtype([("task", np.int32), ("item", np.int32), ("sm", np.int32), ("kind", np.int32),
+                    ("t_start_ns", np.uint64), ("t_end_ns", np.uint64)])
+    tr = np.zeros(5, dtype=rec)
+    tr["task"] = [0, 1, 2, 2, 3]
+    tr["kind"] = [b3t.POTRF, b3t.TRSM, b3t.GEMM, b3t.GEMM, b3t.SYRK]
+    tr["t_start_ns"] = [0, 1000, 1000, 1500, 4000]
+    tr["t_end_ns"] = [1000, 2000, 3000, 3500, 5000]
+    ed = np.array([(0, 1), (0, 2), (1, 3), (2, 3)])
+    s = bench.trace_summary(tr, 4, ed, 2)
+    assert s["critical_path_ms"] == 4500 / 1e6 and s["makespan_ms"] == 5000 / 1e6
+    assert s["cta_busy_frac"] == 0.7 and s["edges_violated"] == 0
+    assert s["kinds"]["GEMM"]["items"] == 2 and s["kinds"]["GEMM"]["cta_time_share"] == 4000 / 7000
+    tr["t_start_ns"][4] = 3200          # task 3 starts before task 2 ends
+    assert bench.trace_summary(tr, 4, ed, 2)["edges_violated"] == 1
