@@ -358,6 +358,8 @@ def run_ours(args):
         cpu = oracle_sample(get, T, b, args.cpu_seconds)
         if not args.no_secondary:
             cpu["empty_dags"] = oracle_empty_dags(min(3.0, args.cpu_seconds / 5))
+        if not args.no_serve:
+            cpu["serving_scipy"] = scipy_serving_sample(min(10.0, args.cpu_seconds), args.serve_requests)
 
     secondary = {}
     if not args.no_secondary:
@@ -613,6 +615,37 @@ def oracle_empty_dags(seconds):
     return out
 
 
+def scipy_serving_sample(seconds, n_max=96):
+    """Library CPU baseline of the serving workload: the first requests of
+    the seed-5 stream solved one at a time on the host (scipy Cholesky
+    factor and solve, all host cores), until `seconds` of solve time.  Each
+    A is a diagonally dominant symmetric matrix of the request's size (the
+    factorisation's cost does not depend on the values); building it is not
+    timed."""
+    import scipy.linalg as sla
+    import synth
+    _, Ns, nrhs, seeds = synth.serve_requests(n_max, rate=2000.0, seed=5)
+    lat, total, done = [], 0.0, 0
+    for N, r, sd in zip(Ns, nrhs, seeds):
+        rng = np.random.default_rng(sd % (2 ** 62))
+        A = rng.random((int(N), int(N)))
+        A += A.T
+        A[np.diag_indices(int(N))] += 2.0 * N
+        Bm = rng.standard_normal((int(N), int(r)))
+        t0 = time.perf_counter()
+        c = sla.cho_factor(A, lower=True, check_finite=False)
+        sla.cho_solve(c, Bm, check_finite=False)
+        dt = time.perf_counter() - t0
+        lat.append(dt)
+        total += dt
+        done += 1
+        if total > seconds:
+            break
+    return {"solves_per_s": done / total, "p50_solve_ms": 1e3 * float(np.median(lat)),
+            "cores": len(os.sched_getaffinity(0)), "kind": "scipy (LAPACK) on the host, one request at a time",
+            "sample": "first %d of the %d served requests, %.1f s of factor + solve time" % (done, n_max, total)}
+
+
 SWEEP_RATES = {"fp64": (10.0, 20.0, 40.0, 80.0, 160.0, 2000.0), "bf16": (20.0, 40.0, 80.0, 160.0, 320.0, 2000.0)}
 
 
@@ -722,7 +755,8 @@ def run_secondary(ctx, dev, stream):
             ts.append(ctx.last_launch()["kernel_ns"] / 1e9)
     out["cholesky_small"] = {"workload": "FP64 N=1024 tile 128 (120 tasks)",
                              "ms": 1e3 * float(np.median(ts)),
-                             "TFLOPs": cholesky_flops(N1) / float(np.median(ts)) / 1e12}
+                             "TFLOPs": cholesky_flops(N1) / float(np.median(ts)) / 1e12,
+                             "tasks_per_s": len_tasks(N1 // b1) / float(np.median(ts))}
     ctx.graph_destroy(g)
     ctx.tiles_unregister(p1, N1 // b1)
     return out

@@ -312,3 +312,12 @@ def test_bench_trace_summary():
     assert s["kinds"]["GEMM"]["items"] == 2 and s["kinds"]["GEMM"]["cta_time_share"] == 4000 / 7000
     tr["t_start_ns"][4] = 3200          # task 3 starts before task 2 ends
     assert bench.trace_summary(tr, 4, ed, 2)["edges_violated"] == 1
+
+
+def test_bench_scipy_serving_sample():
+    # the serving workload's library CPU baseline stops after its time
+    # budget (here: after the first request) and reports what it sampled
+    import bench
+    r = bench.scipy_serving_sample(0.0, 4)
+    assert r["solves_per_s"] > 0 and r["cores"] >= 1
+    assert r["sample"].startswith("first 1 of the 4 served requests")
