@@ -1,0 +1,125 @@
+"""Host-side logic of the package on the CPU: the packed tile layout shared
+with the oracle, identity padding for ragged sizes, the tile autotuner's
+choice rule, the serving requests and their device footprint."""
+import json
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+import paper_1304_0878_b300 as b3t
+from paper_1304_0878_b300 import tiles as dt, batch as bt, tune, serve as sv
+from oracle import cholesky as och
+
+
+@pytest.mark.parametrize("N,b", [(256, 64), (384, 128), (512, 512)])
+def test_tile_layout_matches_the_oracle(N, b):
+    # the device helpers and the oracle pack the lower tiles identically:
+    # tile (i, j) at j*T - j(j-1)/2 + (i - j), each tile column-major
+    A = synth.spd_host(N, seed=N, shift=1.0)
+    t = dt.to_tiles(torch.from_numpy(A), b).numpy()
+    assert np.array_equal(t, och.to_tiles(A, b))
+    assert np.array_equal(dt.pack_lower(torch.from_numpy(A), b).numpy(), t)
+    T = N // b
+    for i in range(T):
+        for j in range(i + 1):
+            assert dt.tile_index(i, j, T) == och.tile_index(i, j, T)
+            assert np.array_equal(t[dt.tile_index(i, j, T)], A[i * b:(i + 1) * b, j * b:(j + 1) * b].T)
+    back = dt.from_tiles(torch.from_numpy(t), N, b).numpy()
+    L = np.zeros_like(A)
+    for i in range(T):
+        for j in range(i + 1):
+            L[i * b:(i + 1) * b, j * b:(j + 1) * b] = A[i * b:(i + 1) * b, j * b:(j + 1) * b]
+    assert np.array_equal(back, L)
+
+
+def test_tile_ptrs_step_by_tile():
+    t = torch.zeros((6, 4, 4), dtype=torch.float64)
+    p = dt.tile_ptrs(t)
+    assert p[0] == t.data_ptr() and all(q - r == 4 * 4 * 8 for r, q in zip(p, p[1:]))
+
+
+@pytest.mark.parametrize("N,b", [(77, 64), (300, 128), (513, 256), (512, 128)])
+def test_identity_padding(N, b):
+    # a ragged size is padded to diag(A, I); its Cholesky factor is diag(L, I)
+    A = torch.from_numpy(synth.spd_host(N, seed=3, shift=1.0))
+    t, Np = bt.padded_tiles(A, b)
+    assert Np == dt.pad_size(N, b) and Np % b == 0 and Np - N < b
+    C = dt.from_tiles(t, Np, b).numpy()
+    assert np.array_equal(np.tril(C[:N, :N]), np.tril(A.numpy()))
+    assert np.array_equal(C[N:, N:], np.eye(Np - N))
+    assert np.all(C[N:, :N] == 0)
+    # the oracle factors the padded matrix to diag(L, I)
+    Cs = np.tril(C) + np.tril(C, -1).T
+    L, info = och.dense_potrf(Cs)
+    assert info == 0
+    L = np.tril(L)
+    assert np.allclose(L[N:, N:], np.eye(Np - N)) and np.all(L[N:, :N] == 0)
+
+
+def test_tile_choice_rule(tmp_path):
+    table = {"fp64": {"256": {"best": 64}, "1024": {"best": 128}, "8192": {"best": 512}},
+             "bf16": {"1024": {"best": 128}, "8192": {"best": 256}}}
+    path = tmp_path / "table.json"
+    path.write_text(json.dumps(table))
+    try:
+        tune.load(str(path))
+        assert tune.choose_tile(1024, "fp64") == 128
+        assert tune.choose_tile(900, "fp64") == 128          # nearest tuned size in log scale
+        assert tune.choose_tile(300, "fp64") == 64
+        assert tune.choose_tile(8192, "fp64") == 512
+        assert tune.choose_tile(5000, "fp64") == 512          # log-nearest to 8192
+        assert tune.choose_tile(200, "fp64") == 64
+        assert tune.choose_tile(100, "bf16") == 128           # mixed tiles are at least 128
+        assert tune.choose_tile(6000, "bf16") == 256
+        # no more than one mostly padded tile: b halves while b >= 2N (down to 64)
+        table["fp64"]["256"]["best"] = 512
+        path.write_text(json.dumps(table))
+        tune.load(str(path))
+        assert tune.choose_tile(100, "fp64") == 128 and tune.choose_tile(256, "fp64") == 256
+        # no measurements for a precision: the rule of thumb
+        assert tune.choose_tile(3000, "e4m3") == tune.default_tile(3000, "e4m3") == 256
+    finally:
+        tune.load()
+
+
+def test_committed_tile_table_is_complete():
+    tab = tune.load()
+    for prec in ("fp64", "bf16"):
+        for n in tune.SIZES:
+            row = tab[prec][str(n)]
+            ms = {int(k): v for k, v in row["ms"].items()}
+            assert row["best"] == min(ms, key=ms.get)
+            assert set(ms) <= set(tune.TILES[prec])
+
+
+def test_serving_requests():
+    # the same requests at every rate (arrival gaps scale with 1/rate), sizes
+    # log-uniform in range, tiles from the tuner, footprint from the layout
+    a = sv.make_requests(64, 2000.0, seed=5)
+    c = sv.make_requests(64, 20.0, seed=5)
+    assert [(r.N, r.nrhs, r.seed) for r in a] == [(r.N, r.nrhs, r.seed) for r in c]
+    ta = np.array([r.arrival for r in a])
+    tc = np.array([r.arrival for r in c])
+    assert np.all(np.diff(ta) > 0) and np.allclose(tc, ta * 100.0, rtol=1e-12)
+    for r in a:
+        assert 256 <= r.N <= 8192 and 1 <= r.nrhs <= 32
+        assert r.b == tune.choose_tile(r.N, "fp64") and r.Np == dt.pad_size(r.N, r.b) and r.T * r.b == r.Np
+        assert r.bytes == sv.footprint(r.Np, r.nrhs, r.b, "fp64")
+    f = [r for r in sv.make_requests(8, 100.0, seed=5, prec="bf16", tile=256)]
+    assert all(r.b == 256 for r in f)
+
+
+def test_footprint_counts_every_buffer():
+    # fp64: A + factor tiles; mixed: A (FP64), W (binary32), L (FP64), Q
+    # (one byte per element for E4M3, two for bf16); two block vectors; the
+    # refinement work area; 4 KiB of slack
+    Np, nrhs, b = 1024, 8, 256
+    T = Np // b
+    nt = T * (T + 1) // 2 * b * b
+    base = 2 * T * b * nrhs * 8 + b3t.ir_work_elems(T, b, nrhs) * 8 + 4096
+    assert sv.footprint(Np, nrhs, b, "fp64") == nt * 16 + base
+    assert sv.footprint(Np, nrhs, b, "bf16") == nt * 22 + base
+    assert sv.footprint(Np, nrhs, b, "e4m3") == nt * 21 + base
+    assert sv.footprint(2 * Np, nrhs, b, "fp64") > 3 * sv.footprint(Np, nrhs, b, "fp64")
