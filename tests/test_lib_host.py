@@ -321,3 +321,32 @@ def test_bench_scipy_serving_sample():
     r = bench.scipy_serving_sample(0.0, 4)
     assert r["solves_per_s"] > 0 and r["cores"] >= 1
     assert r["sample"].startswith("first 1 of the 4 served requests")
+
+
+from hypothesis import given, settings, HealthCheck, strategies as st   # noqa: E402
+
+_acc = st.lists(st.lists(st.tuples(st.sampled_from([0, 1, 2, 10, 11, 12]), st.sampled_from([R, W, RW])),
+                         min_size=0, max_size=4), min_size=1, max_size=40)
+
+
+@settings(max_examples=200, deadline=None, suppress_health_check=[HealthCheck.function_scoped_fixture])
+@given(acc=_acc)
+def test_edges_match_oracle_property(acc):
+    # any task set, including buffers named twice by one task (modes OR-ed),
+    # tasks without buffers, and a partitioned buffer named both whole and by
+    # part: the library derives exactly the oracle's edges
+    c = b3t.Context(host_only=True)
+    try:
+        hs = [c.data_register(fake_ptr(i), 64, 4) for i in range(3)]
+        kids = c.data_partition(hs[0], 3, 16)
+        lib_of = {0: hs[0], 1: hs[1], 2: hs[2], 10: kids[0], 11: kids[1], 12: kids[2]}
+        cls = {}
+        for a in acc:
+            modes = tuple(m for _, m in a)
+            if modes not in cls:
+                cls[modes] = c.task_decl("t", b3t.NOOP, list(modes))
+            c.task_submit(cls[modes], [lib_of[h] for h, _ in a])
+        assert sorted(c.dag_edges()) == dag.derive_edges(acc, {0: (10, 11, 12)})
+        assert c.dag_stats()[0] == len(acc)
+    finally:
+        c.close()
