@@ -133,6 +133,26 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def provenance():
+    """What the line was measured on: host cores, the library sources'
+    hash, and the git revision when the tree is a checkout."""
+    out = {"host_cores": len(os.sched_getaffinity(0)), "source_hash": None, "git_rev": None}
+    try:
+        import paper_1304_0878_b300.build as pb
+        out["source_hash"] = pb.source_hash()
+    except Exception:
+        pass
+    try:
+        top = subprocess.check_output(["git", "-C", ROOT, "rev-parse", "--show-toplevel"],
+                                      stderr=subprocess.DEVNULL, text=True).strip()
+        if os.path.realpath(top) == os.path.realpath(ROOT):
+            out["git_rev"] = subprocess.check_output(["git", "-C", ROOT, "rev-parse", "HEAD"],
+                                                     stderr=subprocess.DEVNULL, text=True).strip()
+    except (OSError, subprocess.CalledProcessError):
+        pass
+    return out
+
+
 def dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -233,7 +253,8 @@ def run_reference(args):
                        "execution": "the oracle: sequential CPU executor, C tile routines, one host core; "
                                     "a bounded prefix of the submission order per step"},
             "cpu_baseline": {**vals[-1], "value": v},
-            "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "provenance": provenance()}
     print(json.dumps(line))
 
 
@@ -407,6 +428,7 @@ def run_ours(args):
         "e2e": e2e,
         "cpu_baseline": cpu,
         "secondary": secondary,
+        "provenance": provenance(),
     }
     print(json.dumps(line))
 
@@ -871,10 +893,6 @@ def run_case(args):
     ctx.close()
 
 
-KIND_NAMES = {0: "NOOP", 1: "SCAL", 2: "POTRF", 3: "TRSM", 4: "SYRK", 5: "GEMM", 18: "POTRF_D",
-              19: "PANEL_TRSM", 20: "PANEL_UPD"}
-
-
 def run_trace_headline(dev, args):
     """One traced factorisation of the headline workload: how busy the CTAs
     were, each task kind's share of the CTA time, and the longest chain of
@@ -900,42 +918,9 @@ def run_trace_headline(dev, args):
     assert len(tr) == ll["nitems"], "trace buffer too small"
     out = {"workload": "FP64 Cholesky N=%d tile %d, one traced launch" % (N, b), "tasks": ntasks,
            "edges": nedges, "items": int(len(tr)), "ctas": ll["nctas"], "traced_kernel_ms": ll["kernel_ns"] / 1e6}
-    out.update(trace_summary(tr, ntasks, ed, ll["nctas"]))
+    from paper_1304_0878_b300 import trace
+    out.update(trace.summary(tr, ntasks, ed, ll["nctas"]))
     return out
-
-
-def trace_summary(tr, ntasks, ed, nctas):
-    """Makespan, CTA busy fraction, per-kind share of the CTA time, the
-    critical path (longest chain of task spans along the edges `ed`, which
-    point from earlier to later submissions) and the number of edges whose
-    successor started before its predecessor ended (0 for a legal run)."""
-    st = tr["t_start_ns"].astype(np.int64)
-    en = tr["t_end_ns"].astype(np.int64)
-    t0 = int(st.min())
-    makespan = int(en.max()) - t0
-    dur = en - st
-    kinds = {}
-    for k in np.unique(tr["kind"]):
-        m = tr["kind"] == k
-        kinds[KIND_NAMES.get(int(k), str(int(k)))] = {"items": int(m.sum()),
-                                                      "cta_time_share": float(dur[m].sum() / dur.sum()),
-                                                      "mean_item_us": float(dur[m].mean() / 1e3)}
-    ts = np.full(ntasks, np.iinfo(np.int64).max, dtype=np.int64)
-    te = np.zeros(ntasks, dtype=np.int64)
-    np.minimum.at(ts, tr["task"], st)
-    np.maximum.at(te, tr["task"], en)
-    span = te - ts
-    order = np.argsort(ed[:, 1], kind="stable")
-    preds, succ_of = ed[order, 0], ed[order, 1]
-    first = np.searchsorted(succ_of, np.arange(ntasks + 1))
-    cp = span.astype(np.float64)
-    for v in range(ntasks):
-        a, z = first[v], first[v + 1]
-        if z > a:
-            cp[v] += cp[preds[a:z]].max()
-    return {"makespan_ms": makespan / 1e6, "cta_busy_frac": float(dur.sum()) / (nctas * makespan),
-            "critical_path_ms": float(cp.max()) / 1e6, "critical_path_share": float(cp.max()) / makespan,
-            "edges_violated": int(np.sum(te[ed[:, 0]] > ts[ed[:, 1]])), "kinds": kinds}
 
 
 def run_part(args):

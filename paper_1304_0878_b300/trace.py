@@ -1,0 +1,63 @@
+"""Analysis of an execution trace (Context.trace_start / trace_read): one
+record per finished work item with its task, item, SM, kind, and start and
+end on the device's global nanosecond timer.
+
+`summary` answers where a launch's time went: the makespan, how busy the
+CTAs were, each task kind's share of the CTA time, the critical path (the
+longest chain of task spans along the dependency edges), and whether any
+task started before one of its predecessors ended.
+"""
+import numpy as np
+
+from . import _lib
+
+KIND_NAMES = {getattr(_lib, n): n for n in (
+    "NOOP", "SCAL_F32", "POTRF", "TRSM", "SYRK", "GEMM", "POTRF_MX", "TRSM_MX", "SYRK_MX", "GEMM_MX", "QUANT",
+    "TRSV_L", "GEMV_L", "TRSV_LT", "GEMV_LT", "AXPY", "RESID", "NRM", "POTRF_D", "PANEL_TRSM", "PANEL_UPD",
+    "CVT", "TRTRI")}
+
+
+def task_spans(records, ntasks):
+    """Per task: first item's start and last item's end (ns)."""
+    st = records["t_start_ns"].astype(np.int64)
+    en = records["t_end_ns"].astype(np.int64)
+    ts = np.full(ntasks, np.iinfo(np.int64).max, dtype=np.int64)
+    te = np.zeros(ntasks, dtype=np.int64)
+    np.minimum.at(ts, records["task"], st)
+    np.maximum.at(te, records["task"], en)
+    return ts, te
+
+
+def summary(records, ntasks, edges, nctas):
+    """records: Context.trace_read() of one launch; edges: (pred, succ)
+    pairs of that launch (Context.dag_edges() before the wait), each from an
+    earlier to a later submission; nctas: the launch's grid.  Returns the
+    makespan, the CTA busy fraction (item time over CTAs x makespan), the
+    per-kind share of the CTA time, the critical path and its share of the
+    makespan, and the number of edges whose successor started before its
+    predecessor ended (0 for a legal run)."""
+    ed = np.asarray(edges, dtype=np.int64).reshape(-1, 2)
+    st = records["t_start_ns"].astype(np.int64)
+    en = records["t_end_ns"].astype(np.int64)
+    makespan = int(en.max()) - int(st.min())
+    dur = en - st
+    kinds = {}
+    for k in np.unique(records["kind"]):
+        m = records["kind"] == k
+        kinds[KIND_NAMES.get(int(k), str(int(k)))] = {"items": int(m.sum()),
+                                                      "cta_time_share": float(dur[m].sum() / dur.sum()),
+                                                      "mean_item_us": float(dur[m].mean() / 1e3)}
+    ts, te = task_spans(records, ntasks)
+    span = te - ts
+    # submission order is a topological order: one pass in task order
+    order = np.argsort(ed[:, 1], kind="stable")
+    preds, succ_of = ed[order, 0], ed[order, 1]
+    first = np.searchsorted(succ_of, np.arange(ntasks + 1))
+    cp = span.astype(np.float64)
+    for v in range(ntasks):
+        a, z = first[v], first[v + 1]
+        if z > a:
+            cp[v] += cp[preds[a:z]].max()
+    return {"makespan_ms": makespan / 1e6, "cta_busy_frac": float(dur.sum()) / (nctas * makespan),
+            "critical_path_ms": float(cp.max()) / 1e6, "critical_path_share": float(cp.max()) / makespan,
+            "edges_violated": int(np.sum(te[ed[:, 0]] > ts[ed[:, 1]])) if len(ed) else 0, "kinds": kinds}

@@ -306,14 +306,6 @@ def test_kernel_variant_covers_mixed_launch(orc, gctx):
     assert gctx.last_launch()["nctas"] == 2 * sms          # empty tasks only
 
 
-def _task_spans(tr, ntasks):
-    start = np.full(ntasks, np.iinfo(np.uint64).max, dtype=np.uint64)
-    end = np.zeros(ntasks, dtype=np.uint64)
-    np.minimum.at(start, tr["task"], tr["t_start_ns"])
-    np.maximum.at(end, tr["task"], tr["t_end_ns"])
-    return start, end
-
-
 @pytest.mark.parametrize("shape", ["random", "fan", "cholesky"])
 def test_execution_order_respects_every_edge(orc, gctx, shape):
     # The order the persistent kernel ran the tasks in is one the DAG allows
@@ -354,7 +346,8 @@ def test_execution_order_respects_every_edge(orc, gctx, shape):
     gctx.trace_stop()
     ntasks = gctx.last_launch()["ntasks"]
     assert ntasks == len(acc) and len(tr) == gctx.last_launch()["nitems"]
-    start, end = _task_spans(tr, ntasks)
+    from paper_1304_0878_b300 import trace
+    start, end = trace.task_spans(tr, ntasks)
     e = np.array(edges, dtype=np.int64).reshape(-1, 2)
     bad = np.nonzero(end[e[:, 0]] > start[e[:, 1]])[0]
     assert bad.size == 0, [(tuple(e[k]), int(end[e[k, 0]]), int(start[e[k, 1]])) for k in bad[:5]]

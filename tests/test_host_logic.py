@@ -123,3 +123,25 @@ def test_footprint_counts_every_buffer():
     assert sv.footprint(Np, nrhs, b, "bf16") == nt * 22 + base
     assert sv.footprint(Np, nrhs, b, "e4m3") == nt * 21 + base
     assert sv.footprint(2 * Np, nrhs, b, "fp64") > 3 * sv.footprint(Np, nrhs, b, "fp64")
+
+
+def test_trace_summary():
+    # critical path = longest chain of task spans along the edges; busy
+    # fraction = item time over CTAs x makespan; a late successor is counted
+    from paper_1304_0878_b300 import trace
+    rec = np.dtype([("task", np.int32), ("item", np.int32), ("sm", np.int32), ("kind", np.int32),
+                    ("t_start_ns", np.uint64), ("t_end_ns", np.uint64)])
+    tr = np.zeros(5, dtype=rec)
+    tr["task"] = [0, 1, 2, 2, 3]
+    tr["kind"] = [b3t.POTRF, b3t.TRSM, b3t.GEMM, b3t.GEMM, b3t.SYRK]
+    tr["t_start_ns"] = [0, 1000, 1000, 1500, 4000]
+    tr["t_end_ns"] = [1000, 2000, 3000, 3500, 5000]
+    ed = [(0, 1), (0, 2), (1, 3), (2, 3)]
+    s = trace.summary(tr, 4, ed, 2)
+    assert s["critical_path_ms"] == 4500 / 1e6 and s["makespan_ms"] == 5000 / 1e6
+    assert s["cta_busy_frac"] == 0.7 and s["edges_violated"] == 0
+    assert s["kinds"]["GEMM"]["items"] == 2 and s["kinds"]["GEMM"]["cta_time_share"] == 4000 / 7000
+    assert set(s["kinds"]) == {"POTRF", "TRSM", "GEMM", "SYRK"}
+    tr["t_start_ns"][4] = 3200          # task 3 starts before task 2 ends
+    assert trace.summary(tr, 4, ed, 2)["edges_violated"] == 1
+    assert trace.summary(tr[:1], 1, [], 1)["critical_path_ms"] == 1000 / 1e6    # no edges

@@ -294,26 +294,6 @@ def test_bench_empty_dags_follow_the_oracle():
             assert len(dag.derive_edges(acc)) == 131040
 
 
-def test_bench_trace_summary():
-    # critical path = longest chain of task spans along the edges; busy
-    # fraction = item time over CTAs x makespan; a late successor is counted
-    import bench
-    rec = np.dtype([("task", np.int32), ("item", np.int32), ("sm", np.int32), ("kind", np.int32),
-                    ("t_start_ns", np.uint64), ("t_end_ns", np.uint64)])
-    tr = np.zeros(5, dtype=rec)
-    tr["task"] = [0, 1, 2, 2, 3]
-    tr["kind"] = [b3t.POTRF, b3t.TRSM, b3t.GEMM, b3t.GEMM, b3t.SYRK]
-    tr["t_start_ns"] = [0, 1000, 1000, 1500, 4000]
-    tr["t_end_ns"] = [1000, 2000, 3000, 3500, 5000]
-    ed = np.array([(0, 1), (0, 2), (1, 3), (2, 3)])
-    s = bench.trace_summary(tr, 4, ed, 2)
-    assert s["critical_path_ms"] == 4500 / 1e6 and s["makespan_ms"] == 5000 / 1e6
-    assert s["cta_busy_frac"] == 0.7 and s["edges_violated"] == 0
-    assert s["kinds"]["GEMM"]["items"] == 2 and s["kinds"]["GEMM"]["cta_time_share"] == 4000 / 7000
-    tr["t_start_ns"][4] = 3200          # task 3 starts before task 2 ends
-    assert bench.trace_summary(tr, 4, ed, 2)["edges_violated"] == 1
-
-
 def test_bench_scipy_serving_sample():
     # the serving workload's library CPU baseline stops after its time
     # budget (here: after the first request) and reports what it sampled
