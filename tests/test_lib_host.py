@@ -330,3 +330,28 @@ def test_edges_match_oracle_property(acc):
         assert c.dag_stats()[0] == len(acc)
     finally:
         c.close()
+
+
+def test_bench_empty_dags_edge_counts(ctx):
+    # the library derives the closed-form edge counts of the 1M-task shapes:
+    # chains 1000 x 999; fan-out / fan-in: each writer after the first waits
+    # for the 999 readers before it, each reader for its round's writer and
+    # for its own buffer's previous reader
+    import bench
+    want = {"chains": 1000 * 999, "fan": 999 * 999 + 1000 * 999 + 999 * 999}
+    for shape, n_edges in want.items():
+        c = b3t.Context(host_only=True)
+        modes, nh, nt, gen = bench.empty_dag(shape)
+        hs = [c.data_register(fake_ptr(i), 16, 4) for i in range(nh)]
+        cls = [c.task_decl("empty", b3t.NOOP, m) for m in modes]
+        for k, bs in gen():
+            c.task_submit(cls[k], [hs[h] for h in bs])
+        assert c.dag_stats() == (nt, n_edges)
+        c.close()
+
+
+def test_bench_oracle_empty_dags_rates():
+    import bench
+    r = bench.oracle_empty_dags(0.0)
+    assert set(r) == {"chains", "fan", "cholesky"}
+    assert all(v["tasks_per_s"] > 0 and v["cores"] == 1 and v["kind"] == "oracle" for v in r.values())
