@@ -70,9 +70,9 @@ def parse():
                    help="ready-queue order of the profiling cases (--case)")
     p.add_argument("--ctas-per-sm", type=int, default=0, help="grid of the profiling cases (0: occupancy)")
     p.add_argument("--case", default=None, choices=["mx_gemm_bf16", "mx_gemm_e4m3", "scal", "resid", "solve_f32",
-                                                    "solve_f64", "empty_dags", "serve_sweep", "trace_headline"],
+                                                    "solve_f64", "empty_dags", "serve_sweep", "trace_headline", "batch"],
                    help="run one profiling case (a DAG of one task kind), or one secondary measurement alone "
-                        "(empty_dags, serve_sweep, trace_headline), and print its result")
+                        "(empty_dags, serve_sweep, trace_headline, batch), and print its result")
     return p.parse_args()
 
 
@@ -923,6 +923,49 @@ def run_trace_headline(dev, args):
     return out
 
 
+def run_batch(dev, args):
+    """Batching: 24 uneven FP64 factorisations (N log-uniform in [256, 4096],
+    the serving stream's sizes, seed 5; tiles from the tuner, ragged sizes
+    padded with identity) in ONE persistent launch, against one launch per
+    matrix.  Each way is timed end to end (padding into tiles included) on
+    the device with CUDA events, after one untimed pass."""
+    import torch
+    import synth
+    import paper_1304_0878_b300 as b3t
+    from paper_1304_0878_b300 import batch as bt
+    _, Ns, _, seeds = synth.serve_requests(24, rate=2000.0, seed=5, nmin=256, nmax=4096)
+    mats = []
+    for N, sd in zip(Ns, seeds):
+        g = torch.Generator(device=dev)
+        g.manual_seed(int(sd % (2 ** 62)))
+        Bm = torch.randn((int(N), int(N)), generator=g, device=dev, dtype=torch.float64)
+        mats.append(Bm @ Bm.T / int(N) + torch.eye(int(N), dtype=torch.float64, device=dev))
+    del Bm
+    stream = torch.cuda.current_stream(dev)
+    ctx = b3t.Context(stream=stream.cuda_stream, timeout_ns=60_000_000_000)
+    flops = float(sum(cholesky_flops(int(N)) for N in Ns))
+    res = {}
+    for name in ("one_launch", "launch_per_matrix"):
+        ts = []
+        for rep in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            if name == "one_launch":
+                bt.cholesky_many(ctx, mats)
+            else:
+                for A in mats:
+                    bt.cholesky_many(ctx, [A])
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(e0.elapsed_time(e1))
+        res[name] = {"ms": ts[-1], "TFLOPs": flops / (ts[-1] / 1e3) / 1e12}
+    ctx.close()
+    res["speedup"] = res["launch_per_matrix"]["ms"] / res["one_launch"]["ms"]
+    res["sizes"] = [int(N) for N in Ns]
+    return res
+
+
 def run_part(args):
     """One secondary measurement alone, printed as one JSON line."""
     import torch
@@ -933,6 +976,8 @@ def run_part(args):
         res = run_empty_dags(dev, torch.cuda.current_stream(dev))
     elif args.case == "trace_headline":
         res = run_trace_headline(dev, args)
+    elif args.case == "batch":
+        res = run_batch(dev, args)
     else:
         res = run_serve_sweep(dev, args)
     print(json.dumps({"case": args.case, "result": res}))
@@ -940,7 +985,7 @@ def run_part(args):
 
 if __name__ == "__main__":
     a = parse()
-    if a.case in ("empty_dags", "serve_sweep", "trace_headline"):
+    if a.case in ("empty_dags", "serve_sweep", "trace_headline", "batch"):
         run_part(a)
     elif a.case:
         run_case(a)
