@@ -145,3 +145,27 @@ def test_trace_summary():
     tr["t_start_ns"][4] = 3200          # task 3 starts before task 2 ends
     assert trace.summary(tr, 4, ed, 2)["edges_violated"] == 1
     assert trace.summary(tr[:1], 1, [], 1)["critical_path_ms"] == 1000 / 1e6    # no edges
+
+
+def test_reference_arm_line_on_the_host():
+    # the reference arm (the oracle, as it stands, on a bounded sample)
+    # prints one JSON line with the same metric and workload config as the
+    # device arm, its CPU baseline and a zero-copy e2e entry
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    out = subprocess.check_output([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                                   "--n", "1024", "--b", "256", "--steps", "1", "--warmup", "0",
+                                   "--cpu-seconds", "0.5"], cwd=root, env=env, text=True, timeout=300)
+    line = json.loads(out.strip().splitlines()[-1])
+    import bench
+    assert line["impl"] == "reference" and line["metric"] == "cholesky_fp64_tflops"
+    assert line["unit"] == "TFLOP/s" and line["higher_is_better"] is True and line["value"] > 0
+    cfg = bench.workload_config(1024, 256)
+    assert {k: line["config"][k] for k in cfg} == cfg
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"] == {"value": line["value"], "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
