@@ -355,3 +355,18 @@ def test_bench_oracle_empty_dags_rates():
     r = bench.oracle_empty_dags(0.0)
     assert set(r) == {"chains", "fan", "cholesky"}
     assert all(v["tasks_per_s"] > 0 and v["cores"] == 1 and v["kind"] == "oracle" for v in r.values())
+
+
+def test_c_abi_from_plain_c(tmp_path):
+    # include/b3t.h compiles as C99 with warnings as errors, and a C program
+    # linked against libb3t.so declares, registers, submits by pointer and
+    # reads the derived graph and the error codes (tests/c_abi_host.c)
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    libdir = os.path.dirname(b3t._lib.LIB_PATH)
+    exe = str(tmp_path / "c_abi_host")
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(root, "include"),
+                           os.path.join(root, "tests", "c_abi_host.c"), "-o", exe, "-L", libdir, "-lb3t",
+                           "-Wl,-rpath," + libdir])
+    out = subprocess.check_output([exe], text=True, timeout=60)
+    assert out.strip() == "c abi ok"
