@@ -44,7 +44,7 @@ def lib():
             "orc_trsm": (None, [dp, i, dp, i, i, i]),
             "orc_syrk": (None, [dp, i, i, i, dp, i]),
             "orc_gemm": (None, [dp, i, dp, i, dp, i, i, i, i]),
-            "orc_round_format": (d, [ctypes.c_float, i, i, d, i]),
+            "orc_round_format": (d, [d, i, i, d, i]),
             "orc_scale_exponent": (i, [d, d]),
             "orc_quantise": (None, [dp, i64, i, i, i, d, i, dp]),
             "orc_gemm_lowp": (None, [dp, i, dp, i, d, fp, i, i, i, i, i]),

@@ -111,18 +111,26 @@ void orc_gemm(const double *A, int lda, const double *B, int ldb, double *C,
 
 /* ------------------------------------------------------- low precision */
 
-/* Round a binary32 value to the nearest value of a binary format with
- * `p` significant bits (implicit bit included) and minimum normal exponent
- * `emin`, ties to even.  Values whose magnitude rounds above `maxval`
- * become +-maxval when `satfinite` is set, +-inf otherwise.  NaN stays NaN.
+/* Round a value to the nearest value of a binary format with `p`
+ * significant bits (implicit bit included) and minimum normal exponent
+ * `emin`, ties to even: ONE rounding, straight from FP64.  Values whose
+ * magnitude rounds above `maxval` become +-maxval when `satfinite` is set,
+ * +-inf otherwise.  NaN stays NaN.
  *   bfloat16 : p = 8, emin = -126, maxval = (2 - 2^-7) * 2^127
  *   E4M3     : p = 4, emin = -6,   maxval = 448 (no infinities; saturating)
- * The value is scaled by a power of two (exact) and rounded with rint(),
- * which rounds to nearest-even in the default rounding mode. */
-double orc_round_format(float xf, int p, int emin, double maxval, int satfinite)
+ * The quantum (spacing of the format's grid around x) is 2^(e - p + 1), e
+ * the exponent of x's leading bit clamped below at emin (the format's
+ * subnormals share the quantum of its smallest binade).  x / quantum is exact
+ * in FP64 (a power-of-two scaling of a finite double), rint() rounds it to
+ * the nearest integer with ties to even in the default rounding mode, and
+ * the product with the quantum is exact again. */
+double orc_round_format(double x, int p, int emin, double maxval, int satfinite)
 {
-    double x = (double)xf;
     if (x != x || x == 0.0) return x;
+    if (isinf(x)) {
+        if (satfinite) return x > 0 ? maxval : -maxval;
+        return x;
+    }
     int e2;
     frexp(x, &e2);             /* |x| = m 2^e2, m in [0.5, 1) */
     int e = e2 - 1;            /* exponent of the leading bit */
@@ -149,16 +157,15 @@ int orc_scale_exponent(double amax, double fmt_max)
     return e;
 }
 
-/* Quantise n FP64 values: q[i] = round_format(float(x[i] / s)), s = 2^e.
- * x/s is exact; the FP64 -> binary32 conversion rounds to nearest-even and
- * the binary32 -> format rounding is orc_round_format (two roundings, the
- * conversion chain the device uses).  q holds the format values as doubles. */
+/* Quantise n FP64 values: q[i] = round_format(x[i] / s), s = 2^e.  x / s is
+ * exact (a power-of-two scaling), so each value is rounded once, from FP64
+ * to the format.  q holds the format values as doubles. */
 void orc_quantise(const double *x, int64_t n, int e, int p, int emin,
                   double maxval, int satfinite, double *q)
 {
     for (int64_t i = 0; i < n; ++i) {
         double v = ldexp(x[i], -e);
-        q[i] = orc_round_format((float)v, p, emin, maxval, satfinite);
+        q[i] = orc_round_format(v, p, emin, maxval, satfinite);
     }
 }
 

@@ -65,11 +65,12 @@ def gemm(A, B, C):
 
 
 def round_format(x, fmt):
-    """Round binary32 value(s) to the format, ties to even (scalar helper)."""
+    """Round value(s) to the format, one rounding from FP64, ties to even
+    (binary32 inputs widen exactly)."""
     p, emin, mx, sat = FORMATS[fmt]
     f = lib().orc_round_format
-    xs = np.asarray(x, dtype=np.float32).ravel()
-    out = np.array([f(ctypes.c_float(v), p, emin, mx, sat) for v in xs])
+    xs = np.asarray(x, dtype=np.float64).ravel()
+    out = np.array([f(float(v), p, emin, mx, sat) for v in xs])
     return out.reshape(np.shape(x))
 
 
@@ -83,8 +84,9 @@ def scale_exponent(amax, fmt):
 
 
 def quantise(X, fmt):
-    """Return (Q, e): Q = round_format(fl32(X / 2^e)) as float64 values in
-    Fortran order, e the tile's scale exponent from max |X|."""
+    """Return (Q, e): Q = round_format(X / 2^e) (one rounding from FP64) as
+    float64 values in Fortran order, e the tile's scale exponent from
+    max |X|."""
     p, emin, mx, sat = FORMATS[fmt]
     X = np.asfortranarray(X, dtype=np.float64)
     e = scale_exponent(np.max(np.abs(X)) if X.size else 0.0, fmt)

@@ -1,11 +1,20 @@
 """Pins for the oracle's low-precision pieces: rounding to bfloat16 / E4M3,
 the power-of-two per-tile scale, the binary32-accumulated update and the
-mixed-precision factorisation."""
+mixed-precision factorisation.
+
+The quantisation of a panel tile is one rounding, q = RN_fmt(x / 2^e),
+straight from FP64.  It is pinned here against an independent exact
+computation in rational arithmetic (fractions.Fraction), including FP64
+values just off a midpoint of the format's grid, where rounding through
+binary32 first would land on the midpoint and then round the other way."""
+import math
+
 import numpy as np
 import pytest
 import torch
 
 import synth
+from fpgrid import chain_round, exact_round, grid_midpoints, ulp32
 from oracle import cholesky as ch, mixed, tiles as tl
 
 
@@ -88,3 +97,56 @@ def test_mixed_factor_is_low_precision(fmt, lo, hi):
     assert info == 0
     r = ch.rel_residual(np.tril(ch.from_tiles(Lt, N, b)), A)
     assert lo < r < hi
+
+
+# ---- quantisation pinned to its definition in exact arithmetic
+
+@pytest.mark.parametrize("fmt", ["bf16", "e4m3"])
+def test_quantise_is_one_rounding_from_fp64(fmt):
+    rng = np.random.default_rng(11)
+    p, emin, maxval, _ = tl.FORMATS[fmt]
+    # random FP64 values over the format's whole range and beyond it
+    mags = rng.uniform(-1, 1, 3000) * 2.0 ** rng.uniform(emin - p - 3, math.log2(maxval) + 2, 3000)
+    # values just off midpoints: below half a binary32 ulp, so binary32
+    # rounds them onto the midpoint and the chain breaks the tie instead
+    mids = grid_midpoints(fmt, rng, 600)
+    u = ulp32(mids)
+    crafted = np.concatenate([mids + u * 2.0 ** -8, mids - u * 2.0 ** -8, mids, -mids])
+    x = np.concatenate([mags, crafted, [0.0, -0.0, 2.0 ** (emin - p), 2.0 ** (emin - p) * 1.0000001,
+                                        maxval, -maxval]])
+    X = np.asfortranarray(x.reshape(1, -1))
+    ref = np.array([exact_round(float(v), fmt) for v in x])
+    if fmt == "e4m3":
+        # unit scale: the tile maximum would pick e > 0, so quantise with e = 0
+        got = np.array([tl.round_format(float(v), fmt) for v in x])
+    else:
+        got, e = tl.quantise(X, fmt)
+        assert e == 0
+        got = got.ravel()
+    assert np.array_equal(got, ref)
+    # the crafted values tell one rounding from the binary32 chain: a slip
+    # to double rounding would fail the comparison above on these
+    n = len(mids)
+    chain = chain_round(crafted[:2 * n], fmt)
+    assert np.sum(chain != ref[len(mags):len(mags) + 2 * n]) >= n // 2
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "e4m3"])
+def test_quantise_tile_against_exact(fmt):
+    # a whole tile with its scale: every element is RN_fmt(x / 2^e); the tile
+    # maximum is 448 * 2^3, so E4M3 takes e = 3, and the first 8 columns are
+    # grid midpoints (after the scale) nudged below half a binary32 ulp
+    rng = np.random.default_rng(12)
+    X = rng.standard_normal((64, 64))
+    X = np.asfortranarray(X / np.max(np.abs(X)) * 448.0 * 8.0 * 0.99)
+    X[5, 40] = 448.0 * 8.0
+    mids = grid_midpoints(fmt, rng, 64 * 8)
+    if fmt == "e4m3":
+        mids = mids * 8.0
+    X[:, :8] = (mids + ulp32(mids) * 2.0 ** -10).reshape(64, 8)
+    Q, e = tl.quantise(X, fmt)
+    assert e == (3 if fmt == "e4m3" else 0)
+    ref = np.array([exact_round(float(v) * 2.0 ** -e, fmt) for v in X.ravel(order="F")])
+    assert np.array_equal(Q.ravel(order="F"), ref)
+    chain = chain_round(X[:, :8].ravel(order="F") * 2.0 ** -e, fmt)
+    assert np.sum(chain != ref[:64 * 8]) >= 64
