@@ -82,11 +82,18 @@ enum { B3T_R = 1, B3T_W = 2, B3T_RW = 3 };
  *  B3T_POTRF_MX    W_kk (R, f32), L_kk (W, f64)               int32 col0
  *                  L_kk = chol(fp64(W_kk)); strict upper part of L_kk = 0
  *  B3T_TRSM_MX     L_kk (R), W_ik (R, f32), L_ik (W, f64)     none
- *                  L_ik = fp64(W_ik) L_kk^{-T}
+ *                  L_ik = fp64(W_ik) L_kk^{-T} (substitution, row blocks)
+ *  B3T_TRMM_MX     U_k (R, f64), W_ik (R, f32), L_ik (W, f64) none
+ *                  L_ik = fp64(W_ik) U_k with U_k = L_kk^{-T} from B3T_TRTRI
+ *                  (upper triangular, zeros below the diagonal): the same
+ *                  panel solve as a product, in independent 64 x 64 blocks,
+ *                  summed over p ascending with one FMA per term
  *  B3T_QUANT       L_ik (R, f64), Q_ik (W)                    int32 fmt
- *                  Q_ik = round_fmt(fl32(L_ik / 2^e)), e the tile's scale
- *                  exponent (0 for bf16; for E4M3 the smallest e with
- *                  max|L_ik| <= 448 * 2^e)
+ *                  Q_ik = RN_fmt(L_ik / 2^e): one rounding from FP64 to the
+ *                  format, to nearest, ties to even (E4M3 saturating at
+ *                  448); e is the tile's scale exponent (0 for bf16; for
+ *                  E4M3 the smallest e with max|L_ik| <= 448 * 2^e), so the
+ *                  division is exact
  *  B3T_SYRK_MX     Q_ik (R), W_ii (RW, f32)                   int32 fmt
  *                  W_ii <- fl32(W_ii - 2^(2e) Q_ik Q_ik^T), lower triangle
  *  B3T_GEMM_MX     Q_ik (R), Q_jk (R), W_ij (RW, f32)         int32 fmt
@@ -117,7 +124,8 @@ enum b3t_kind {
     B3T_PANEL_TRSM = 19,
     B3T_PANEL_UPD = 20,
     B3T_CVT = 21,
-    B3T_TRTRI = 22
+    B3T_TRTRI = 22,
+    B3T_TRMM_MX = 23
 };
 
 /* Diagonal tile split into column panels.  A b x b diagonal tile partitioned
@@ -282,7 +290,11 @@ B3T_API int b3t_task_flush(b3t_ctx *ctx);
 B3T_API int b3t_task_wait(b3t_ctx *ctx, int64_t timeout_ns);
 
 /* Make a buffer safe for host-side use (Section 3.4, acquire pragma): waits
- * for the tasks that write it (mode R) or also read it (mode W / RW). */
+ * for the tasks that write it (mode R) or also read it (mode W / RW).  It
+ * currently flushes and joins ALL pending and in-flight work of the context,
+ * a superset of those tasks (one persistent launch runs the whole batch, so
+ * a per-buffer wait would not return earlier).  -ENOENT for an unknown
+ * handle, -EINVAL for a mode outside 1..3, -EBUSY while capturing. */
 B3T_API int b3t_data_acquire(b3t_ctx *ctx, b3t_handle h, uint8_t mode);
 
 /* Wait for the tasks using the buffer, then forget the handle (Section 2).
@@ -316,6 +328,18 @@ B3T_API int b3t_graph_destroy(b3t_ctx *ctx, b3t_graph g);
 B3T_API int b3t_dag_stats(b3t_ctx *ctx, int64_t *ntasks, int64_t *nedges);
 B3T_API int b3t_dag_edges(b3t_ctx *ctx, int32_t *pred, int32_t *succ, int64_t cap,
                           int64_t *count);
+
+/* Scheduling priority of the pending batch's tasks, as the next flush will
+ * use it (Section 5.3: upward rank as a scheduling hint): rank[t] is, under
+ * B3T_PRIO_UPWARD, the longest path from task t to the end of the graph
+ * weighted by the library's per-kind cost estimate (ns on one CTA; t's own
+ * cost included), or, under B3T_PRIO_DEPTH, the number of tasks on the
+ * longest path from a source to t; level[t] in 0..prio_levels-1 is the ready
+ * queue level (higher is claimed first): floor(L * rank / (max rank *
+ * 1.000001)) for upward rank, min(L - 1, rank) for depth, 0 with one level.
+ * Writes at most cap entries of each (either pointer may be NULL); *count =
+ * number of pending tasks. */
+B3T_API int b3t_dag_levels(b3t_ctx *ctx, float *rank, int32_t *level, int64_t cap, int64_t *count);
 
 /* Launch statistics of the last launch (flush or replay): tasks, work
  * items, persistent CTAs, and the device time of the persistent kernel (or
@@ -353,6 +377,23 @@ B3T_API int b3t_cholesky_submit(b3t_ctx *ctx, double *const *tiles, int32_t T, i
 B3T_API int b3t_cholesky_mx_submit(b3t_ctx *ctx, float *const *W, double *const *L,
                                    void *const *Q, int32_t T, int32_t b, int32_t fmt,
                                    int32_t col0);
+
+/* Mixed precision with the panel solve as a product with the inverted
+ * diagonal tile (the trailing updates as in b3t_cholesky_mx_submit):
+ *   for k: POTRF_MX(W_kk, L_kk) (or CVT + the panel DAG for b >= 256);
+ *          TRTRI(L_kk, U_k) (k < T-1);
+ *          for i>k: TRMM_MX(U_k, W_ik, L_ik), QUANT(L_ik, Q_ik);
+ *          for i>k: SYRK_MX(Q_ik, W_ii); for k<j<i: GEMM_MX(Q_ik, Q_jk, W_ij)
+ * U: T pointers to b x b f64 tiles of caller-owned scratch (U_k = L_kk^{-T}
+ * on return, for k < T-1).  An explicit inverse rounds differently from
+ * substitution, and its error grows with the condition number of L_kk
+ * (about kappa(L_kk) times the FP64 unit roundoff, relative): on the
+ * well-conditioned diagonal tiles of A = B B^T / N + c I it agrees with
+ * B3T_TRSM_MX to ~1e-15; for ill-conditioned tiles use
+ * b3t_cholesky_mx_submit.  -EINVAL for a bad shape or format. */
+B3T_API int b3t_cholesky_mx_inv_submit(b3t_ctx *ctx, float *const *W, double *const *L,
+                                       void *const *Q, double *const *U, int32_t T, int32_t b,
+                                       int32_t fmt, int32_t col0);
 
 /* Solves with a tiled Cholesky factor: Y <- (L L^T)^{-1} Y, submitted as
  * TRSV_L / GEMV_L tasks (forward, k ascending) then TRSV_LT / GEMV_LT tasks

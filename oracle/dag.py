@@ -95,6 +95,38 @@ def critical_path(n, edges):
     return max(depth) if n else 0
 
 
+def upward_rank(n, edges, cost):
+    """Upward rank of every task (Section 5.3 names upward and downward ranks
+    as scheduling hints): the largest total cost over the paths that start at
+    the task and follow edges to the end of the graph, the task's own cost
+    included.  Written as that definition, by recursion over successors."""
+    succ = successors(n, edges)
+    memo = {}
+
+    def longest(t):
+        if t not in memo:
+            memo[t] = cost[t] + max((longest(s) for s in succ[t]), default=0.0)
+        return memo[t]
+
+    # every edge goes from an earlier to a later submission: evaluating from
+    # the last task backwards keeps the recursion shallow
+    for t in range(n - 1, -1, -1):
+        longest(t)
+    return [memo[t] for t in range(n)]
+
+
+def depth(n, edges):
+    """Edges on the longest path from a source to each task."""
+    d = [0] * n
+    pred = [[] for _ in range(n)]
+    for p, s in edges:
+        pred[s].append(p)
+    for t in range(n):
+        for p in pred[t]:
+            d[t] = max(d[t], d[p] + 1)
+    return d
+
+
 def topological_orders(n, edges):
     """All linear extensions (brute force; tiny n only)."""
     pos_pred = [set() for _ in range(n)]

@@ -23,7 +23,7 @@ FMT_BF16, FMT_E4M3 = 0, 1
 PRIO_UPWARD, PRIO_DEPTH = 0, 1
 TRSV_L, GEMV_L, TRSV_LT, GEMV_LT, AXPY, RESID, NRM = 11, 12, 13, 14, 15, 16, 17
 VEC_F32, VEC_ASSIGN, VEC_LOWER_M, VEC_UPPER_M, VEC_KEEP_NORM = 1, 2, 4, 8, 16
-POTRF_D, PANEL_TRSM, PANEL_UPD, CVT, TRTRI = 18, 19, 20, 21, 22
+POTRF_D, PANEL_TRSM, PANEL_UPD, CVT, TRTRI, TRMM_MX = 18, 19, 20, 21, 22, 23
 
 
 class B3TError(RuntimeError):
@@ -66,11 +66,15 @@ _SIGS = {
     "b3t_graph_destroy": (ctypes.c_int, [_vp, _i32]),
     "b3t_dag_stats": (ctypes.c_int, [_vp, _pi64, _pi64]),
     "b3t_dag_edges": (ctypes.c_int, [_vp, _pi32, _pi32, _i64, _pi64]),
+    "b3t_dag_levels": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float), _pi32, _i64, _pi64]),
     "b3t_last_launch": (ctypes.c_int, [_vp, _pi64, _pi64, _pi32, _pi64]),
     "b3t_debug_block_task": (ctypes.c_int, [_vp, _i64]),
     "b3t_cholesky_submit": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), _i32, _i32, _i32]),
     "b3t_cholesky_mx_submit": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                               ctypes.POINTER(_vp), _i32, _i32, _i32, _i32]),
+    "b3t_cholesky_mx_inv_submit": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                                  ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i32, _i32, _i32,
+                                                  _i32]),
     "b3t_tiles_unregister": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), _i32]),
     "b3t_scal_chains_noalloc": (ctypes.c_int, [_vp, _i64, _i32, _i32, _vp, _i64, _vp]),
     "b3t_stream_open": (ctypes.c_int, [_vp, _i64, _i64, _i32, _i64]),
@@ -259,6 +263,13 @@ class Context:
         _check(lib().b3t_dag_edges(self._h, p, s, ne, ctypes.byref(cnt)), "b3t_dag_edges")
         return [(p[i], s[i]) for i in range(cnt.value)]
 
+    def dag_levels(self):
+        """(rank, level) per pending task, as the next flush will use them."""
+        nt, _ = self.dag_stats()
+        rk, lv, cnt = (ctypes.c_float * max(nt, 1))(), (_i32 * max(nt, 1))(), _i64()
+        _check(lib().b3t_dag_levels(self._h, rk, lv, nt, ctypes.byref(cnt)), "b3t_dag_levels")
+        return [rk[i] for i in range(cnt.value)], [lv[i] for i in range(cnt.value)]
+
     def last_launch(self):
         nt, ni, nc, ns = _i64(), _i64(), _i32(), _i64()
         _check(lib().b3t_last_launch(self._h, ctypes.byref(nt), ctypes.byref(ni), ctypes.byref(nc),
@@ -277,6 +288,10 @@ class Context:
                                             T, b, fmt, col0), "b3t_cholesky_mx_submit")
 
     # -- stream mode (continuous submission) --------------------------------------
+    def cholesky_mx_inv_submit(self, W_ptrs, L_ptrs, Q_ptrs, U_ptrs, T, b, fmt, col0=0):
+        _check(lib().b3t_cholesky_mx_inv_submit(self._h, _ptrs(W_ptrs), _ptrs(L_ptrs), _ptrs(Q_ptrs),
+                                                _ptrs(U_ptrs), T, b, fmt, col0), "b3t_cholesky_mx_inv_submit")
+
     def stream_open(self, max_tasks, max_edges, max_batches, deadline_ns):
         _check(lib().b3t_stream_open(self._h, max_tasks, max_edges, max_batches, deadline_ns),
                "b3t_stream_open")

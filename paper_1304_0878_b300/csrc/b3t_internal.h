@@ -60,8 +60,8 @@ enum : int32_t {
     kNoop = 0, kScalF32 = 1, kPotrf = 2, kTrsm = 3, kSyrk = 4, kGemm = 5,
     kPotrfMx = 6, kTrsmMx = 7, kSyrkMx = 8, kGemmMx = 9, kQuant = 10,
     kTrsvL = 11, kGemvL = 12, kTrsvLT = 13, kGemvLT = 14, kAxpy = 15, kResid = 16, kNrm = 17,
-    kPotrfD = 18, kPanelTrsm = 19, kPanelUpd = 20, kCvt = 21, kTrtri = 22,
-    kNumKinds = 23
+    kPotrfD = 18, kPanelTrsm = 19, kPanelUpd = 20, kCvt = 21, kTrtri = 22, kTrmmMx = 23,
+    kNumKinds = 24
 };
 
 // One task as the device sees it: 64 bytes.
@@ -129,7 +129,7 @@ B3T_HD constexpr uint32_t family_of(int kind) {
          : (kind == kPotrf || kind == kTrsm || kind == kSyrk || kind == kGemm || kind == kPotrfD ||
             kind == kPanelTrsm || kind == kPanelUpd) ? kFamF64
          : ((kind >= kTrsvL && kind <= kNrm) || kind == kTrtri) ? kFamSolve
-         : (kind >= kPotrfMx && kind <= kQuant) || kind == kCvt ? kFamMx
+         : (kind >= kPotrfMx && kind <= kQuant) || kind == kCvt || kind == kTrmmMx ? kFamMx
          : 0u;   // NOOP runs in every variant
 }
 B3T_HD constexpr uint32_t variant_of(uint32_t fams) {

@@ -123,8 +123,10 @@ __device__ __forceinline__ void scal_item(const TaskRec &t, int item) {
 // memory stages (global -> shared with an mbarrier, multiply in place,
 // shared -> global).  Thread 0 issues every copy.  Every wait is bounded;
 // the first that gives up stops the item (no further copies) after the
-// fills already issued are drained, again with a bound.  Returns 0 or the
-// 1-based chunk whose wait gave up.
+// fills already issued are drained, again with a bound (drain_ns).  Returns
+// 0 or the 1-based chunk whose wait gave up; the caller then takes no
+// further item on this CTA (the ring's phases are no longer known), so
+// nothing touches the shared area again.
 constexpr int kSbStages = 4;
 constexpr uint32_t kSbBytes = 16384;
 
@@ -136,7 +138,7 @@ __device__ __forceinline__ void bulk_s2g_commit(void *dst, const void *src, uint
 }
 
 __device__ __forceinline__ int scal_item_bulk(const TaskRec &t, int item, uint64_t *full, unsigned char *stage,
-                                              uint32_t &fills, int64_t limit_ns) {
+                                              uint32_t &fills, int64_t limit_ns, int64_t drain_ns) {
     float *x = (float *)t.buf[0];
     const float f = __uint_as_float(t.scal);
     const int64_t start = (int64_t)item * kScalChunk;
@@ -187,7 +189,7 @@ __device__ __forceinline__ int scal_item_bulk(const TaskRec &t, int item, uint64
     if (failed) {
         for (int d = c; d < issued; ++d) {
             const uint32_t g = G + d;
-            mbar_wait(&full[g % kSbStages], (g / kSbStages) & 1, limit_ns);
+            mbar_wait(&full[g % kSbStages], (g / kSbStages) & 1, drain_ns);
         }
     }
     fills = G + issued;
@@ -538,7 +540,8 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
                 if constexpr (kScal && !kMx) {
                     // each wait of the ring gives up after 50 ms (a 16 KiB copy
                     // takes microseconds) and the launch reports ETIMEDOUT
-                    const int fc = scal_item_bulk(rec, it, s_sbar, smem, sfills, min(p.timeout_ns, (int64_t)50000000));
+                    const int fc = scal_item_bulk(rec, it, s_sbar, smem, sfills, min(p.timeout_ns, (int64_t)50000000),
+                                                  p.timeout_ns);
                     if (fc) {
                         if (tid == 0) set_error(p.ctl, ETIMEDOUT, (int)t, fc, 20);
                         st = -ETIMEDOUT;
@@ -571,6 +574,7 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
                 }
                 break;
             case kTrsmMx: if constexpr (kMx) trsm_mx_item(rec, it, (double *)smem); break;
+            case kTrmmMx: if constexpr (kMx) trmm_mx_item(rec, it, (double *)smem); break;
             case kCvt: if constexpr (kMx) cvt_item(rec, it); break;
             case kQuant: if constexpr (kMx) quant_item(rec, it, s_red, &s_e); break;
             case kSyrkMx:
@@ -611,6 +615,10 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
             default: break;   // NOOP
             }
         }
+        // generic-proxy writes of this body to the dynamic shared area are
+        // ordered before any bulk copy (async proxy) a later item issues into
+        // the same bytes; the barrier below hands them to the issuing thread
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();   // every thread is done with the item
         if (warp == 0) {
             // warp 0 alone finishes the item; the other warps go on to the
@@ -651,6 +659,12 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
             if (flag) retire(p, t, rec);
             fi = (nj >= 0 && nj < rec.nitems) ? (((unsigned long long)t << 32) | (uint32_t)nj) : kEmpty;
         }
+        // a bulk-copy or tensor-core pipeline whose bounded wait gave up
+        // leaves its mbarrier phases unknown (and, after a failed drain,
+        // copies possibly still landing in shared memory): the CTA takes no
+        // further item, neither its pending ones nor a claim (st is the same
+        // in every thread: the pipeline bodies return a block-wide result)
+        if (st == -ETIMEDOUT) break;
     }
 
     if (kMx && p.has_mx) {

@@ -165,6 +165,37 @@ __device__ __forceinline__ int e4m3_scale_exp(double amax) {
 
 __device__ __forceinline__ int q_esize(int fmt) { return fmt == 0 ? 2 : 1; }
 
+// FP64 -> bfloat16, one rounding to nearest even (the PTX conversion from
+// .f64 to .bf16 rounds once; overflow gives infinity).
+__device__ __forceinline__ uint32_t bf16_bits_rn(double x) {
+    unsigned short h;
+    asm("cvt.rn.bf16.f64 %0, %1;" : "=h"(h) : "d"(x));
+    return h;
+}
+
+// FP64 -> the nearest value of the E4M3 grid (4 significant bits, smallest
+// normal 2^-6, so a quantum of 2^-9 below it), ties to even, as a binary32
+// holding that value exactly.  One rounding, done on the FP64 significand:
+// with m the 53-bit significand and k the bits to drop (49 in the normal
+// range, more below 2^-6), RN-even is (m + 2^(k-1) - 1 + bit_k(m)) >> k.
+// Magnitudes above 448 are left to the saturating conversion that follows;
+// the tile's scale keeps them out (max |x / 2^e| <= 448).
+__device__ __forceinline__ float e4m3_round_f64(double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long sgn = u & 0x8000000000000000ull, a = u ^ sgn;
+    if (a >= 0x7ff0000000000000ull) return (float)x;           // inf / NaN: left to the conversion
+    const int E = (int)(a >> 52);
+    const int ex = E - 1023;
+    const int k = 49 + max(0, -6 - ex);
+    if (E == 0 || k >= 54) return sgn ? -0.0f : 0.0f;          // below half the smallest subnormal
+    const unsigned long long m = (a & 0x000fffffffffffffull) | 0x0010000000000000ull;
+    const unsigned long long r = (m + (1ull << (k - 1)) - 1ull + ((m >> k) & 1ull)) >> k;
+    // r * 2^(ex - 52 + k); the exponent is >= -9, so the power of two is a
+    // normal double and the product is exact
+    const double y = (double)r * __longlong_as_double((long long)(1023 + ex - 52 + k) << 52);
+    return (float)(sgn ? -y : y);
+}
+
 // QUANT: L (f64 tile) -> Q (layout above).  One work item per tile.
 // QUANT, one 16 KiB chunk of the Q layout per item (128 rows x 128 bytes of
 // K): chunk-parallel, so that a tile's quantisation is not one CTA's serial
@@ -204,10 +235,9 @@ __device__ __forceinline__ void quant_item(const TaskRec &t, int item, double *r
         if (fmt == 0) {
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const float lo = (float)L[(size_t)r + (size_t)(c0 + 2 * j) * b];
-                const float hi = (float)L[(size_t)r + (size_t)(c0 + 2 * j + 1) * b];
-                __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-                w[j] = *reinterpret_cast<uint32_t *>(&h);
+                const uint32_t lo = bf16_bits_rn(L[(size_t)r + (size_t)(c0 + 2 * j) * b]);
+                const uint32_t hi = bf16_bits_rn(L[(size_t)r + (size_t)(c0 + 2 * j + 1) * b]);
+                w[j] = lo | (hi << 16);
             }
         } else {
 #pragma unroll
@@ -215,9 +245,10 @@ __device__ __forceinline__ void quant_item(const TaskRec &t, int item, double *r
                 uint32_t word = 0;
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
+                    // the rounded values are on the E4M3 grid: the conversion is exact
                     float2 f;
-                    f.x = (float)ldexp(L[(size_t)r + (size_t)(c0 + 4 * j + 2 * h) * b], -e);
-                    f.y = (float)ldexp(L[(size_t)r + (size_t)(c0 + 4 * j + 2 * h + 1) * b], -e);
+                    f.x = e4m3_round_f64(ldexp(L[(size_t)r + (size_t)(c0 + 4 * j + 2 * h) * b], -e));
+                    f.y = e4m3_round_f64(ldexp(L[(size_t)r + (size_t)(c0 + 4 * j + 2 * h + 1) * b], -e));
                     const __nv_fp8x2_storage_t q = __nv_cvt_float2_to_fp8x2(f, __NV_SATFINITE, __NV_E4M3);
                     word |= (uint32_t)q << (16 * h);
                 }
@@ -320,7 +351,8 @@ __device__ __forceinline__ int mx_update_item(const TaskRec &t, int item, bool s
     const bool wok = mbar_wait(st.wfull, st.items & 1, limit_ns);
     st.items++;
     tc_fence_after();
-    if (*s_fail || !ok || !wok) return ETIMEDOUT;
+    // every thread takes the same branch: each one's waits may end differently
+    if (__syncthreads_or(*s_fail || !ok || !wok)) return ETIMEDOUT;
     // epilogue: warp w reads TMEM lanes 32*(w%4).. and columns 64*(w/4)..
     const int warp = tid >> 5, lane = tid & 31;
     const int q = warp & 3, h = warp >> 2;

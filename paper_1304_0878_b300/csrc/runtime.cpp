@@ -122,12 +122,13 @@ const KindSig kSigs[kNumKinds] = {
     /* PANEL_UP */ {2, {B3T_R, B3T_RW}, {8, 8}, sizeof(PanelArgs), false},
     /* CVT      */ {2, {B3T_R, B3T_W}, {4, 8}, 0, true},
     /* TRTRI    */ {2, {B3T_R, B3T_W}, {8, 8}, 0, true},
+    /* TRMM_MX  */ {3, {B3T_R, B3T_R, B3T_W}, {8, 4, 8}, 0, true},
 };
 
 const char *kKindNames[kNumKinds] = {"noop", "scal_f32", "potrf", "trsm", "syrk", "gemm",
                                      "potrf_mx", "trsm_mx", "syrk_mx", "gemm_mx", "quant",
                                      "trsv_l", "gemv_l", "trsv_lt", "gemv_lt", "axpy", "resid", "nrm",
-                                     "potrf_d", "panel_trsm", "panel_upd", "cvt", "trtri"};
+                                     "potrf_d", "panel_trsm", "panel_upd", "cvt", "trtri", "trmm_mx"};
 bool is_panel(int kind) { return kind >= kPotrfD && kind <= kPanelUpd; }
 bool is_vec(int kind) { return kind >= kTrsvL && kind <= kNrm; }
 
@@ -142,7 +143,7 @@ int64_t items_of(int kind, int64_t n) {
     case kQuant: return 1;   // set from the format at submit (one item per 16 KiB chunk)
     case kTrsm: case kTrsmMx: case kTrtri: return n / kTrsmRows;
     case kSyrk: { int64_t m = n / kGemmBlk; return m * (m + 1) / 2; }
-    case kGemm: { int64_t m = n / kGemmBlk; return m * m; }
+    case kGemm: case kTrmmMx: { int64_t m = n / kGemmBlk; return m * m; }
     case kSyrkMx: { int64_t m = n / kMxBlk; return m * (m + 1) / 2; }
     case kGemmMx: { int64_t m = n / kMxBlk; return m * m; }
     case kGemvL: case kGemvLT: return n / kGemvRows;
@@ -163,7 +164,7 @@ float cost_of(int kind, int64_t n, int nrhs = 1, int T = 1, bool f32 = false) {
     switch (kind) {
     case kScalF32: return (float)(8.0 * b / 20.0);
     case kPotrf: case kPotrfMx: return (float)(b * b * b / 3.0 / fp64);
-    case kTrsm: case kTrsmMx: return (float)(b * b * b / fp64);
+    case kTrsm: case kTrsmMx: case kTrmmMx: return (float)(b * b * b / fp64);
     case kSyrk: return (float)(b * b * b / fp64);
     case kGemm: return (float)(2.0 * b * b * b / fp64);
     case kSyrkMx: return (float)(b * b * b / mx + 4.0 * b * b / 20.0);
@@ -285,6 +286,15 @@ void derive(b3t_ctx *c, int32_t t, const int32_t *leaves, const uint8_t *modes, 
     preds.erase(std::unique(preds.begin(), preds.end()), preds.end());
 }
 
+// Priority of every task of the pending batch (higher level = claimed first):
+//   upward rank (default): the longest cost-weighted path from the task to
+//   the end of the graph, the task's own cost included, bucketed linearly
+//   into L levels (Section 5.3's scheduling hint);
+//   depth: the longest path from a source, in tasks (successor first).
+// off/succ: CSR successor lists of the batch (successors are later tasks).
+void compute_levels(const b3t_ctx *c, const std::vector<int32_t> &off, const int32_t *succ,
+                    std::vector<float> &rank, std::vector<int32_t> &level);
+
 // Build the task table, CSR graph, ready rings and root lists of the pending
 // batch into arena `a` (uploaded through the pinned staging buffer on the
 // context's stream) and fill the launch parameters.
@@ -304,26 +314,9 @@ int build_launch(b3t_ctx *c, Arena &a, InitParams &ip, LaunchParams &lp, int64_t
         for (auto &e : c->edges) succ_lv[pos[e.first]++] = e.second;
     }
     for (int64_t t = 0; t < nt && t < (int64_t)c->extra_deps.size(); ++t) indeg[t] += c->extra_deps[t];
-    // priority level of each task (higher level = claimed first):
-    //   upward rank: longest cost-weighted path to the end of the graph,
-    //   bucketed linearly (Section 5.3's scheduling hint);
-    //   depth: longest path from a source, in tasks (successor first).
-    std::vector<float> rank(nt, 0.f);
-    float maxr = 0.f;
-    if (c->cfg.prio_policy == B3T_PRIO_DEPTH) {
-        for (int64_t t = 0; t < nt; ++t) {
-            for (int32_t k = off[t]; k < off[t + 1]; ++k)
-                rank[succ_lv[k]] = std::max(rank[succ_lv[k]], rank[t] + 1.f);
-            maxr = std::max(maxr, rank[t]);
-        }
-    } else {
-        for (int64_t t = nt - 1; t >= 0; --t) {
-            float m = 0.f;
-            for (int32_t k = off[t]; k < off[t + 1]; ++k) m = std::max(m, rank[succ_lv[k]]);
-            rank[t] = c->tasks[t].cost + m;
-            maxr = std::max(maxr, rank[t]);
-        }
-    }
+    std::vector<float> rank;
+    std::vector<int32_t> level;
+    compute_levels(c, off, succ_lv.data(), rank, level);
     unsigned long long cap[kMaxLevels] = {0}, rootcnt[kMaxLevels] = {0};
     int64_t nitems = 0;
     has_mx = false;
@@ -332,12 +325,7 @@ int build_launch(b3t_ctx *c, Arena &a, InitParams &ip, LaunchParams &lp, int64_t
         TaskRec &r = c->tasks[t].rec;
         r.succ_off = off[t];
         r.nsucc = off[t + 1] - off[t];
-        int lv = 0;
-        if (L > 1 && maxr > 0.f) {
-            lv = c->cfg.prio_policy == B3T_PRIO_DEPTH
-                     ? std::min(L - 1, (int)rank[t])
-                     : std::min(L - 1, (int)((double)L * rank[t] / (maxr * 1.000001)));
-        }
+        const int lv = level[t];
         succ_lv[ne_pad + t] = lv;
         cap[lv] += 1;
         if (indeg[t] == 0) rootcnt[lv] += 1;
@@ -418,6 +406,33 @@ int build_launch(b3t_ctx *c, Arena &a, InitParams &ip, LaunchParams &lp, int64_t
     }
     nitems_out = nitems;
     return 0;
+}
+
+void compute_levels(const b3t_ctx *c, const std::vector<int32_t> &off, const int32_t *succ,
+                    std::vector<float> &rank, std::vector<int32_t> &level) {
+    const int64_t nt = (int64_t)c->tasks.size();
+    const int L = c->cfg.prio_levels;
+    rank.assign(nt, 0.f);
+    level.assign(nt, 0);
+    float maxr = 0.f;
+    if (c->cfg.prio_policy == B3T_PRIO_DEPTH) {
+        for (int64_t t = 0; t < nt; ++t) {
+            for (int32_t k = off[t]; k < off[t + 1]; ++k) rank[succ[k]] = std::max(rank[succ[k]], rank[t] + 1.f);
+            maxr = std::max(maxr, rank[t]);
+        }
+    } else {
+        for (int64_t t = nt - 1; t >= 0; --t) {
+            float m = 0.f;
+            for (int32_t k = off[t]; k < off[t + 1]; ++k) m = std::max(m, rank[succ[k]]);
+            rank[t] = c->tasks[t].cost + m;
+            maxr = std::max(maxr, rank[t]);
+        }
+    }
+    if (L <= 1 || !(maxr > 0.f)) return;
+    for (int64_t t = 0; t < nt; ++t)
+        level[t] = c->cfg.prio_policy == B3T_PRIO_DEPTH
+                       ? std::min(L - 1, (int)rank[t])
+                       : std::min(L - 1, (int)((double)L * rank[t] / (maxr * 1.000001)));
 }
 
 int grid_for(b3t_ctx *c, uint32_t variant, int *nctas, size_t *smem, int free_sms = 0, uint32_t fams = ~0u) {
@@ -558,7 +573,8 @@ int submit_impl(b3t_ctx *c, b3t_codelet cl, const b3t_handle *handles, const uin
         const int fmt = has_fmt(C.kind) ? r.aux : 0;
         if (fmt != B3T_FMT_BF16 && fmt != B3T_FMT_E4M3) return -EINVAL;
         if (b <= 0 || b % kGemmBlk || b > 4096) return -EINVAL;
-        if (((C.kind >= kPotrfMx && C.kind <= kQuant) || C.kind == kCvt) && b % kMxBlk) return -EINVAL;
+        if (((C.kind >= kPotrfMx && C.kind <= kQuant) || C.kind == kCvt || C.kind == kTrmmMx) && b % kMxBlk)
+            return -EINVAL;
         for (int i = 0; i < nbuffers; ++i) {
             const Handle &H = c->handles[handles[i]];
             if (H.ld != b || r.buf[i] % 16) return -EINVAL;
@@ -988,6 +1004,28 @@ int b3t_dag_edges(b3t_ctx *c, int32_t *pred, int32_t *succ, int64_t cap, int64_t
     return 0;
 }
 
+int b3t_dag_levels(b3t_ctx *c, float *rank, int32_t *level, int64_t cap, int64_t *count) {
+    if (!c) return -EINVAL;
+    const int64_t nt = (int64_t)c->tasks.size();
+    if (count) *count = nt;
+    std::vector<int32_t> off(nt + 1, 0);
+    for (auto &e : c->edges) off[e.first + 1]++;
+    for (int64_t t = 0; t < nt; ++t) off[t + 1] += off[t];
+    std::vector<int32_t> succ(std::max<size_t>(c->edges.size(), 1));
+    {
+        std::vector<int32_t> pos(off.begin(), off.end() - 1);
+        for (auto &e : c->edges) succ[pos[e.first]++] = e.second;
+    }
+    std::vector<float> rk;
+    std::vector<int32_t> lv;
+    compute_levels(c, off, succ.data(), rk, lv);
+    for (int64_t t = 0; t < nt && t < cap; ++t) {
+        if (rank) rank[t] = rk[t];
+        if (level) level[t] = lv[t];
+    }
+    return 0;
+}
+
 int b3t_last_launch(b3t_ctx *c, int64_t *ntasks, int64_t *nitems, int32_t *nctas, int64_t *kernel_ns) {
     if (!c) return -EINVAL;
     if (ntasks) *ntasks = c->last_ntasks;
@@ -1367,6 +1405,69 @@ int b3t_cholesky_mx_submit(b3t_ctx *c, float *const *W, double *const *L, void *
         for (int32_t i = k + 1; i < T; ++i) {
             const b3t_handle ht[3] = {hl[tidx(k, k, T)], hw[tidx(i, k, T)], hl[tidx(i, k, T)]};
             if ((rc = submit_impl(c, ct, ht, nullptr, 3, nullptr, 0))) return rc;
+            const b3t_handle hqq[2] = {hl[tidx(i, k, T)], hq[tidx(i, k, T)]};
+            if ((rc = submit_impl(c, cq, hqq, nullptr, 2, &fmt, 4))) return rc;
+        }
+        for (int32_t i = k + 1; i < T; ++i) {
+            const b3t_handle hs[2] = {hq[tidx(i, k, T)], hw[tidx(i, i, T)]};
+            if ((rc = submit_impl(c, cs, hs, nullptr, 2, &fmt, 4))) return rc;
+            for (int32_t j = k + 1; j < i; ++j) {
+                const b3t_handle hg[3] = {hq[tidx(i, k, T)], hq[tidx(j, k, T)], hw[tidx(i, j, T)]};
+                if ((rc = submit_impl(c, cg, hg, nullptr, 3, &fmt, 4))) return rc;
+            }
+        }
+    }
+    return 0;
+}
+
+// Mixed precision with the panel solve as a product: per step k, after the
+// diagonal factor, TRTRI(L_kk -> U_k) and, for every i > k,
+// TRMM_MX(U_k, W_ik -> L_ik) and QUANT(L_ik -> Q_ik); the updates as in
+// b3t_cholesky_mx_submit.
+int b3t_cholesky_mx_inv_submit(b3t_ctx *c, float *const *W, double *const *L, void *const *Q,
+                               double *const *U, int32_t T, int32_t b, int32_t fmt, int32_t col0) {
+    if (!c || !W || !L || !Q || !U || T <= 0 || b <= 0 || b % kMxBlk) return -EINVAL;
+    if (fmt != B3T_FMT_BF16 && fmt != B3T_FMT_E4M3) return -EINVAL;
+    const int64_t nt = (int64_t)T * (T + 1) / 2;
+    std::vector<b3t_handle> hw, hl, hq, hu;
+    int rc = reg_tiles(c, (void *const *)W, nt, (size_t)b * b, 4, b, hw);
+    if (!rc) rc = reg_tiles(c, (void *const *)L, nt, (size_t)b * b, 8, b, hl);
+    if (!rc) rc = reg_tiles(c, (void *const *)U, T, (size_t)b * b, 8, b, hu);
+    if (rc) return rc;
+    hq.assign(nt, -1);
+    for (int32_t j = 0; j < T; ++j)
+        for (int32_t i = j + 1; i < T; ++i) {
+            const int64_t t = tidx(i, j, T);
+            rc = b3t_data_lookup(c, Q[t], &hq[t]);
+            if (rc == -ENOENT) rc = b3t_data_register(c, Q[t], q_bytes(b, fmt), 1, b, &hq[t]);
+            if (rc) return rc;
+        }
+    b3t_codelet cp, ci, cm, cq, cs, cg, cc;
+    if ((rc = kind_codelet(c, kPotrfMx, &cp)) || (rc = kind_codelet(c, kTrtri, &ci)) ||
+        (rc = kind_codelet(c, kTrmmMx, &cm)) || (rc = kind_codelet(c, kQuant, &cq)) ||
+        (rc = kind_codelet(c, kSyrkMx, &cs)) || (rc = kind_codelet(c, kGemmMx, &cg)) ||
+        (rc = kind_codelet(c, kCvt, &cc)))
+        return rc;
+    const bool panels = use_panels(b);
+    std::vector<std::vector<b3t_handle>> dparts(panels ? T : 0);
+    for (int32_t k = 0; panels && k < T; ++k)
+        if ((rc = panel_parts(c, hl[tidx(k, k, T)], b, kPanelWidth, dparts[k]))) return rc;
+    for (int32_t k = 0; k < T; ++k) {
+        const int32_t c0 = col0 + k * b;
+        const b3t_handle hp[2] = {hw[tidx(k, k, T)], hl[tidx(k, k, T)]};
+        if (panels) {
+            if ((rc = submit_impl(c, cc, hp, nullptr, 2, nullptr, 0))) return rc;
+            if ((rc = submit_panel_potrf(c, dparts[k], b, kPanelWidth, c0))) return rc;
+        } else if ((rc = submit_impl(c, cp, hp, nullptr, 2, &c0, 4))) {
+            return rc;
+        }
+        if (k + 1 < T) {
+            const b3t_handle hi[2] = {hl[tidx(k, k, T)], hu[k]};
+            if ((rc = submit_impl(c, ci, hi, nullptr, 2, nullptr, 0))) return rc;
+        }
+        for (int32_t i = k + 1; i < T; ++i) {
+            const b3t_handle ht[3] = {hu[k], hw[tidx(i, k, T)], hl[tidx(i, k, T)]};
+            if ((rc = submit_impl(c, cm, ht, nullptr, 3, nullptr, 0))) return rc;
             const b3t_handle hqq[2] = {hl[tidx(i, k, T)], hq[tidx(i, k, T)]};
             if ((rc = submit_impl(c, cq, hqq, nullptr, 2, &fmt, 4))) return rc;
         }

@@ -240,6 +240,78 @@ __device__ __noinline__ void trsm_mx_item(const TaskRec &t, int item, double *sm
                                   item * kTrsmRows, (int)t.n, (int)t.n, smem);
 }
 
+// TRMM_MX: L_ik <- fp64(W_ik) U_k with U_k = L_kk^{-T} (upper triangular,
+// zero below the diagonal, from TRTRI), one 64 x 64 block of L_ik per item:
+//   L(rows bi, cols bj) = sum_{p < 64 (bj + 1)} fp64(W(rows bi, p)) U(p, cols bj),
+// p ascending, one FMA per term.  Unlike the substitution (TRSM_MX), every
+// block is independent, so a tile's panel solve spreads over (b/64)^2 CTAs
+// and runs at the DFMA rate of a plain product.  The mixed-precision launch
+// runs one CTA per SM, so the next K chunk is loaded into registers while
+// the current one is used.
+__device__ __noinline__ void trmm_mx_item(const TaskRec &t, int item, double *smem) {
+    const int b = (int)t.n, m = b / kGemmBlk;
+    const int bi = item / m, bj = item % m;
+    const double *U = (const double *)t.buf[0];
+    const float *Wt = (const float *)t.buf[1];
+    double *L = (double *)t.buf[2];
+    double *As = smem;                   // [kKc][64]  As[p*64 + r] = W(64 bi + r, k0 + p)
+    double *Bs = smem + kKc * 64;        // [kKc][65]  Bs[p*65 + c] = U(k0 + p, 64 bj + c)
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int K = (bj + 1) * 64;
+    constexpr int NQ = (kKc * 64) / kThreads;   // 8 elements of each operand per thread and chunk
+    const float *Wb = Wt + (size_t)bi * 64;
+    const double *Ub = U + (size_t)bj * 64 * b;
+    float av[NQ];
+    double bv[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const int e = tid + q * kThreads;
+        av[q] = Wb[(size_t)(e & 63) + (size_t)(e >> 6) * b];
+        bv[q] = Ub[(size_t)(e & 31) + (size_t)(e >> 5) * b];
+    }
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int k0 = 0; k0 < K; k0 += kKc) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int e = tid + q * kThreads;
+            As[(e >> 6) * 64 + (e & 63)] = (double)av[q];
+            Bs[(e & 31) * 65 + (e >> 5)] = bv[q];
+        }
+        __syncthreads();
+        if (k0 + kKc < K) {
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const int e = tid + q * kThreads;
+                av[q] = Wb[(size_t)(e & 63) + (size_t)(k0 + kKc + (e >> 6)) * b];
+                bv[q] = Ub[(size_t)(k0 + kKc + (e & 31)) + (size_t)(e >> 5) * b];
+            }
+        }
+#pragma unroll 8
+        for (int p = 0; p < kKc; ++p) {
+            double a[4], bb[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[p * 64 + tx + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bb[j] = Bs[p * 65 + ty + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            L[(size_t)(bi * 64 + tx + 16 * i) + (size_t)(bj * 64 + ty + 16 * j) * b] = acc[i][j];
+}
+
 // Cholesky of one n x n block in place (lower, leading dimension ld), one
 // CTA, left-looking over panels of 32 columns.  Returns 0 or the 1-based
 // column (within the block) of the first pivot that is <= 0 or NaN.

@@ -359,3 +359,30 @@ def test_execution_order_respects_every_edge(orc, gctx, shape):
     else:
         for h in hs:
             gctx.data_unregister(h)
+
+
+def test_acquire_makes_the_writers_result_visible(orc, gctx):
+    # Section 3.4 (acquire): after acquire(h, R) returns, the host may read
+    # the buffer.  A chain of 64 SCAL tasks per block keeps the device busy
+    # for milliseconds; acquire is the only wait: right after it the
+    # context's stream has nothing left to run, and the values are the
+    # oracle's, bit for bit.
+    nb, n, nk = 8, 1 << 18, 64
+    x = synth.vector_f32(nb * n, seed=41)
+    f = synth.chain_factors(nb, nk, seed=42)
+    xd = torch.from_numpy(x.copy()).cuda()
+    torch.cuda.synchronize()
+    hs = [gctx.data_register(xd[i * n:(i + 1) * n].data_ptr(), n, 4) for i in range(nb)]
+    cl = gctx.task_decl("scale_vector", b3t.SCAL_F32, [RW], 4)
+    for k in range(nk):
+        for i in range(nb):
+            gctx.task_submit(cl, [hs[i]], b3t.pack_f32(float(f[i, k])))
+    gctx.task_flush()
+    gctx.data_acquire(hs[3], R)
+    assert torch.cuda.current_stream().query()
+    y = run_chain_oracle(x, f)
+    got = xd[3 * n:4 * n].cpu().numpy()
+    assert np.array_equal(got.view(np.uint32), y[3 * n:4 * n].view(np.uint32))
+    gctx.data_acquire(hs[5], RW)
+    for h in hs:
+        gctx.data_unregister(h)

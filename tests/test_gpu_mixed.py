@@ -1,7 +1,9 @@
 """Mixed-precision tasks against the oracle (GPU): quantisation bit-exact
-(both sides round FP64 -> binary32 -> format the same way), tensor-core
-updates exact when every product and partial sum is representable, and
-within the binary32 accumulation bound otherwise."""
+(both sides round once, FP64 -> format, ties to even; crafted tiles hold
+values just off the format's midpoints, where a rounding through binary32
+would break the tie the other way), tensor-core updates exact when every
+product and partial sum is representable, and within the binary32
+accumulation bound otherwise."""
 import numpy as np
 import pytest
 import torch
@@ -10,6 +12,7 @@ import synth
 import paper_1304_0878_b300 as b3t
 from paper_1304_0878_b300 import tiles as dt
 from oracle import cholesky as och, mixed as omx, tiles as otl
+from fpgrid import chain_round, grid_midpoints, ulp32
 from qlayout import decode
 
 pytestmark = [pytest.mark.gpu,
@@ -47,6 +50,33 @@ def test_quant_bit_exact(orc, gctx, fmt, b):
     qo, eo = otl.quantise(Lm, fmt)
     assert e == eo
     assert np.array_equal(vals, qo)
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "e4m3"])
+def test_quant_one_rounding_crafted(orc, gctx, fmt):
+    # tile maximum 448 * 2^3 (E4M3 scale e = 3); a quarter of the tile are
+    # format midpoints (after the scale) nudged by less than half a binary32
+    # ulp, up or down, and their negatives
+    b = 128
+    rng = np.random.default_rng(7)
+    Lm = rng.standard_normal((b, b))
+    Lm = Lm / np.max(np.abs(Lm)) * 448.0 * 8.0 * 0.99
+    Lm[3, 100] = 448.0 * 8.0
+    n = b * 32
+    mids = grid_midpoints(fmt, rng, n)
+    if fmt == "e4m3":
+        mids = mids * 8.0
+    sign = np.where(rng.random(n) < 0.5, -1.0, 1.0)
+    side = np.where(rng.random(n) < 0.5, -1.0, 1.0)
+    Lm[:, :32] = (sign * (mids + side * ulp32(mids) * 2.0 ** -9)).reshape(b, 32, order="F")
+    Q, hq = quantise_dev(gctx, Lm, fmt, b)
+    vals, e = decode(Q.cpu().numpy(), b, FMTS[fmt])
+    qo, eo = otl.quantise(Lm, fmt)
+    assert e == eo == (3 if fmt == "e4m3" else 0)
+    assert np.array_equal(vals, qo)
+    # the crafted block separates one rounding from the binary32 chain
+    chain = chain_round(Lm[:, :32].ravel(order="F") * 2.0 ** -e, fmt)
+    assert np.sum(chain != qo[:, :32].ravel(order="F")) >= n // 8
 
 
 def mx_update_dev(ctx, QA_m, QB_m, W0, fmt, b, syrk):
@@ -139,6 +169,96 @@ def test_mixed_factor_matches_mixed_oracle(orc, gctx, fmt):
     Lo = np.tril(och.from_tiles(Lt, N, b))
     r_dev, r_orc = och.rel_residual(L, A), och.rel_residual(Lo, A)
     # same low-precision factor up to binary32 accumulation order
+    assert r_dev <= 2.0 * r_orc + 1e-6
+    tol = 1e-3 if fmt == "bf16" else 5e-2
+    assert np.max(np.abs(L - Lo)) / np.max(np.abs(Lo)) <= tol
+
+
+# ---- the panel solve as a product with the inverted diagonal tile
+
+def trmm_dev(ctx, Lkk, Wik, b):
+    """TRTRI(L_kk -> U) then TRMM_MX(U, W_ik -> L_ik) on the device."""
+    L = dev_tile(Lkk)
+    Wd = dev_tile(Wik, torch.float32)
+    U = torch.full((b, b), float("nan"), dtype=torch.float64, device="cuda")
+    X = torch.full((b, b), float("nan"), dtype=torch.float64, device="cuda")
+    hl = ctx.data_register(L.data_ptr(), b * b, 8, b)
+    hu = ctx.data_register(U.data_ptr(), b * b, 8, b)
+    hw = ctx.data_register(Wd.data_ptr(), b * b, 4, b)
+    hx = ctx.data_register(X.data_ptr(), b * b, 8, b)
+    ci = ctx.task_decl("trtri", b3t.TRTRI, [R, W])
+    cm = ctx.task_decl("trmm_mx", b3t.TRMM_MX, [R, R, W])
+    ctx.task_submit(ci, [hl, hu])
+    ctx.task_submit(cm, [hu, hw, hx])
+    ctx.task_wait()
+    for h in (hl, hu, hw, hx):
+        ctx.data_unregister(h)
+    return X.cpu().numpy().T
+
+
+@pytest.mark.parametrize("b", [128, 256, 512])
+def test_trmm_mx_matches_substitution(orc, gctx, b):
+    # L_ik = fp64(W_ik) L_kk^{-T}: the oracle substitutes row by row
+    # (oracle.tiles.trsm); the device multiplies by U = L_kk^{-T}.  Both are
+    # FP64; an explicit inverse rounds differently, so the bound is relative
+    rng = np.random.default_rng(b + 1)
+    A = synth.spd_host(b, seed=b, shift=1.0)
+    Lkk = np.asfortranarray(np.tril(A))
+    assert otl.potrf(Lkk) == 0
+    Lkk = np.asfortranarray(np.tril(Lkk))
+    Wik = (rng.standard_normal((b, b)) * 0.5).astype(np.float32)
+    got = trmm_dev(gctx, Lkk, Wik, b)
+    ref = np.asfortranarray(Wik.astype(np.float64))
+    otl.trsm(Lkk, ref)
+    err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+    assert err <= 1e-12, err
+
+
+def factor_mx_inv_dev(ctx, A, b, fmt):
+    N = A.shape[0]
+    T = N // b
+    At = torch.from_numpy(och.to_tiles(A, b)).cuda()
+    Wt = At.float()
+    Lt = torch.zeros_like(At)
+    Qt = dt.q_tiles(T, b, FMTS[fmt], "cuda")
+    Ut = torch.zeros((T, b, b), dtype=torch.float64, device="cuda")
+    wp, lp, qp, up = dt.tile_ptrs(Wt), dt.tile_ptrs(Lt), dt.tile_ptrs(Qt), dt.tile_ptrs(Ut)
+    ctx.cholesky_mx_inv_submit(wp, lp, qp, up, T, b, FMTS[fmt])
+    ctx.task_wait()
+    for p, n in ((wp, T), (lp, T), (qp, T)):
+        ctx.tiles_unregister(p, n)
+    for p in up:
+        ctx.data_unregister(ctx.data_lookup(p))
+    return np.tril(och.from_tiles(Lt.cpu().numpy(), N, b))
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "e4m3"])
+@pytest.mark.parametrize("N,b", [(512, 128), (768, 256)])
+def test_mixed_inv_factor_on_integer_matrix(orc, gctx, fmt, N, b):
+    # integer L0: the diagonal factors are exact, the panel tiles carry only
+    # the inverse's FP64 rounding, which the quantisation rounds away (the
+    # low-precision operands, hence every update, stay exact).  An explicit
+    # inverse is only as accurate as the diagonal tile is well conditioned:
+    # random integer triangles with small diagonals have inverses of 1e15 and
+    # more, so this L0 has entries in [-1, 1] and diagonal 8 (max |L_kk^-1|
+    # about 0.2); products and partial sums stay exact in binary32
+    A, L0 = synth.integer_spd(N, seed=N + 7, lo=-1, hi=1, dlo=8, dhi=8)
+    L = factor_mx_inv_dev(gctx, A, b, fmt)
+    assert np.max(np.abs(L - L0)) / np.max(np.abs(L0)) <= 1e-13
+    T = N // b
+    for k in range(T):
+        blk = slice(k * b, (k + 1) * b)
+        assert np.array_equal(L[blk, blk], L0[blk, blk])
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "e4m3"])
+def test_mixed_inv_factor_matches_mixed_oracle(orc, gctx, fmt):
+    N, b = 1024, 128
+    A = synth.spd_host(N, seed=0, shift=1.0)
+    L = factor_mx_inv_dev(gctx, A, b, fmt)
+    Lt, info = omx.factor(och.to_tiles(A, b), N // b, b, fmt)
+    Lo = np.tril(och.from_tiles(Lt, N, b))
+    r_dev, r_orc = och.rel_residual(L, A), och.rel_residual(Lo, A)
     assert r_dev <= 2.0 * r_orc + 1e-6
     tol = 1e-3 if fmt == "bf16" else 5e-2
     assert np.max(np.abs(L - Lo)) / np.max(np.abs(Lo)) <= tol

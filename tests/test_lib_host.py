@@ -176,6 +176,21 @@ def test_error_codes(ctx):
     assert e.value.code == E.ENOENT
 
 
+def test_acquire_errors(ctx):
+    # Section 3.4 (acquire): an unknown handle and a mode outside R/W/RW are
+    # errors; with nothing pending, acquiring a registered buffer returns at once
+    E = b3t._lib
+    h = ctx.data_register(fake_ptr(5), 64, 4)
+    with pytest.raises(b3t.B3TError) as e:
+        ctx.data_acquire(h + 100, R)
+    assert e.value.code == E.ENOENT
+    for bad in (0, 4):
+        with pytest.raises(b3t.B3TError) as e:
+            ctx.data_acquire(h, bad)
+        assert e.value.code == E.EINVAL
+    ctx.data_acquire(h, RW)
+
+
 def test_q_bytes():
     assert b3t.q_bytes(512, b3t.FMT_BF16) == 512 * 512 * 2 + 16
     assert b3t.q_bytes(256, b3t.FMT_E4M3) == 256 * 256 + 16
@@ -370,3 +385,98 @@ def test_c_abi_from_plain_c(tmp_path):
                            "-Wl,-rpath," + libdir])
     out = subprocess.check_output([exe], text=True, timeout=60)
     assert out.strip() == "c abi ok"
+
+
+# ---- scheduling priorities (Section 5.3: upward rank as a hint)
+
+NOOP_COST = 1000.0   # the library's cost estimate of an empty task (ns)
+
+
+def _levels_from_rank(rank, L=8):
+    m = max(rank)
+    return [min(L - 1, int(L * r / (m * 1.000001))) for r in rank]
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_upward_rank_is_longest_path(seed):
+    rng = np.random.default_rng(700 + seed)
+    n, nh = int(rng.integers(20, 120)), int(rng.integers(3, 12))
+    acc = [[(int(h), int(rng.choice([R, W, RW])))
+            for h in rng.choice(nh, size=int(rng.integers(1, 4)), replace=False)] for _ in range(n)]
+    with b3t.Context(host_only=True) as c:
+        _submit_accesses(c, acc, nh)
+        rank, level = c.dag_levels()
+    edges = dag.derive_edges(acc)
+    ref = dag.upward_rank(n, edges, [NOOP_COST] * n)
+    assert rank == ref
+    assert level == _levels_from_rank(ref)
+    # with one level, the queue is FIFO (every task on level 0)
+    with b3t.Context(host_only=True, prio_levels=1) as c:
+        _submit_accesses(c, acc, nh)
+        assert c.dag_levels()[1] == [0] * n
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_depth_policy_is_longest_path_from_sources(seed):
+    rng = np.random.default_rng(800 + seed)
+    n, nh = 60, 6
+    acc = [[(int(h), int(rng.choice([R, W, RW])))
+            for h in rng.choice(nh, size=int(rng.integers(1, 3)), replace=False)] for _ in range(n)]
+    with b3t.Context(host_only=True, prio_policy=1) as c:
+        _submit_accesses(c, acc, nh)
+        rank, level = c.dag_levels()
+    d = dag.depth(n, dag.derive_edges(acc))
+    assert rank == [float(x) for x in d]
+    assert level == [min(7, x) for x in d]
+
+
+@pytest.mark.parametrize("T,cp", [(8, 22), (64, 190)])
+def test_cholesky_upward_rank_follows_the_critical_path(T, cp):
+    # tile kinds cost differently; the rank must still be the longest path of
+    # per-task costs: rank(t) - max over successors is one constant per kind,
+    # the ranks drop along every edge, POTRF(0) holds the largest, and
+    # following the largest-ranked successor from it walks a path whose costs
+    # add up to that rank.  With equal costs (the same accesses as empty
+    # tasks) that walk is the closed-form critical path of 3T - 2 tasks.
+    b = 128
+    with b3t.Context(host_only=True) as c:
+        nt = T * (T + 1) // 2
+        tiles = [fake_ptr(i) for i in range(nt)]
+        c.cholesky_submit(tiles, T, b)
+        rank, level = c.dag_levels()
+        edges = c.dag_edges()
+        n = c.dag_stats()[0]
+    acc_kinds = [k for k, _ in och.task_list(T)]
+    assert len(acc_kinds) == n
+    succ = dag.successors(n, edges)
+    own = {}
+    for t in range(n):
+        m = max((rank[s] for s in succ[t]), default=0.0)
+        assert all(rank[t] > rank[s] for s in succ[t])
+        own.setdefault(acc_kinds[t], []).append(rank[t] - m)
+    # one cost per kind (the ranks are binary32: differences agree to ~1e-5)
+    for k, v in own.items():
+        assert max(v) - min(v) <= 2e-5 * max(rank), (k, min(v), max(v))
+    kc = {k: float(np.mean(v)) for k, v in own.items()}
+    cost = [kc[k] for k in acc_kinds]
+    ref = dag.upward_rank(n, edges, cost)
+    assert np.allclose(rank, ref, rtol=1e-5)
+    assert int(np.argmax(rank)) == 0
+    t, total = 0, cost[0]
+    while succ[t]:
+        t = max(succ[t], key=lambda s: rank[s])
+        total += cost[t]
+    assert total == pytest.approx(rank[0], rel=1e-5)
+    assert level[0] == 7 and all(level[p] >= level[s] for p, s in edges)
+    # equal costs: the same access pattern as empty tasks
+    acc = och.accesses(T)
+    tid = {tile: i for i, tile in enumerate(sorted({h for a in acc for h, _ in a}))}
+    with b3t.Context(host_only=True) as c:
+        _submit_accesses(c, [[(tid[h], m) for h, m in a] for a in acc], len(tid))
+        rank_u, _ = c.dag_levels()
+    t, steps = 0, 1
+    while succ[t]:
+        t = max(succ[t], key=lambda s: rank_u[s])
+        steps += 1
+    assert rank_u[0] == NOOP_COST * cp
+    assert steps == cp == dag.critical_path(n, edges)
