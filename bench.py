@@ -65,11 +65,19 @@ def parse():
     p.add_argument("--no-mixed", action="store_true")
     p.add_argument("--nrhs", type=int, default=16)
     p.add_argument("--no-serve", action="store_true")
-    p.add_argument("--serve-requests", type=int, default=96)
+    p.add_argument("--mx-trsm", default="inv", choices=["inv", "subst", "both"],
+                   help="mixed panel solve: product with the inverted diagonal tile (TRTRI + TRMM_MX) "
+                        "or row substitution (TRSM_MX)")
+    p.add_argument("--serve-requests", type=int, default=2000,
+                   help="requests served with continuous batching, per precision (serving sweep: per rate)")
+    p.add_argument("--serve-distinct", type=int, default=128,
+                   help="distinct client inputs (the first requests of the stream), cycled over the run")
+    p.add_argument("--serve-plain-requests", type=int, default=256,
+                   help="requests of the same stream served by the per-request path")
     p.add_argument("--prio", default="upward", choices=["upward", "depth"],
                    help="ready-queue order of the profiling cases (--case)")
     p.add_argument("--ctas-per-sm", type=int, default=0, help="grid of the profiling cases (0: occupancy)")
-    p.add_argument("--case", default=None, choices=["mx_gemm_bf16", "mx_gemm_e4m3", "scal", "resid", "solve_f32",
+    p.add_argument("--case", default=None, choices=["mx_gemm_bf16", "mx_gemm_e4m3", "scal", "resid", "solve_f32", "trace_mixed",
                                                     "solve_f64", "empty_dags", "serve_sweep", "trace_headline", "batch"],
                    help="run one profiling case (a DAG of one task kind), or one secondary measurement alone "
                         "(empty_dags, serve_sweep, trace_headline, batch), and print its result")
@@ -484,11 +492,19 @@ def run_time_to_solution(ctx, A0, t, g64, N, b, dev, stream, args):
     # mixed precision + refinement
     W = torch.empty(A0.shape, dtype=torch.float32, device=dev)
     Lm = torch.zeros_like(A0)
-    for fmt, name in ((b3t.FMT_BF16, "bf16"), (b3t.FMT_E4M3, "e4m3")):
+    U = torch.zeros((T, b, b), dtype=torch.float64, device=dev)
+    up = dt.tile_ptrs(U)
+    variants = [(b3t.FMT_BF16, "bf16", args.mx_trsm != "subst"), (b3t.FMT_E4M3, "e4m3", args.mx_trsm != "subst")]
+    if args.mx_trsm == "both":
+        variants += [(b3t.FMT_BF16, "bf16_substitution", False), (b3t.FMT_E4M3, "e4m3_substitution", False)]
+    for fmt, name, inv in variants:
         Q = dt.q_tiles(T, b, fmt, dev)
         wp, lp, qp = dt.tile_ptrs(W), dt.tile_ptrs(Lm), dt.tile_ptrs(Q)
         ctx.graph_capture_begin()
-        ctx.cholesky_mx_submit(wp, lp, qp, T, b, fmt)
+        if inv:
+            ctx.cholesky_mx_inv_submit(wp, lp, qp, up, T, b, fmt)
+        else:
+            ctx.cholesky_mx_submit(wp, lp, qp, T, b, fmt)
         gm = ctx.graph_capture_end()
         Xm = torch.zeros_like(Bd)
         res = []
@@ -504,7 +520,8 @@ def run_time_to_solution(ctx, A0, t, g64, N, b, dev, stream, args):
             res.append((ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), rc, its, e[nrhs]))
         f_ms, s_ms, rc, its, em = res[-1]
         diff = float((Xm - X64).abs().max() / X64.abs().max())
-        out[name] = {"ms": f_ms + s_ms, "factor_ms": f_ms, "refine_ms": s_ms, "iterations": its, "eta": em,
+        out[name] = {"panel_solve": "TRTRI + TRMM_MX (inverted diagonal tile)" if inv else "TRSM_MX (substitution)",
+                     "ms": f_ms + s_ms, "factor_ms": f_ms, "refine_ms": s_ms, "iterations": its, "eta": em,
                      "converged": rc == 0, "max_rel_diff_vs_fp64_solution": diff,
                      "effective_TFLOPs": flops / ((f_ms + s_ms) / 1e3) / 1e12,
                      "speedup_vs_fp64": (out["fp64"]["ms"]) / (f_ms + s_ms)}
@@ -513,35 +530,47 @@ def run_time_to_solution(ctx, A0, t, g64, N, b, dev, stream, args):
         del Q
     ctx.tiles_unregister(dt.tile_ptrs(W), T)
     ctx.tiles_unregister(dt.tile_ptrs(Lm), T)
+    for p in up:
+        ctx.data_unregister(ctx.data_lookup(p))
     return out
 
 
 def run_serving(dev, args):
-    """Config 5 (bounded sample): the first requests of the seed-5 stream
+    """Config 5 (bounded window): the first requests of the seed-5 stream
     (Poisson 2000/s, N log-uniform in [256, 8192], 1..32 right-hand sides),
-    served with continuous batching (one resident executor) and, for
-    comparison, one at a time (plain per-request path)."""
+    served with continuous batching (one resident executor) and, on a prefix
+    of the same stream, one at a time (plain per-request path).  Each
+    request's A and B are uploaded from pinned host memory at admission and
+    its X downloaded at completion, both inside the latency."""
     import torch
     import paper_1304_0878_b300 as b3t
     from paper_1304_0878_b300 import serve as sv
-    out = {"workload": "first %d requests of 100k Poisson 2000/s, N log-uniform [256, 8192], "
-                       "1-32 rhs, A = B B^T/N + I per request (seed 5)" % args.serve_requests}
+    n, P, n_plain = args.serve_requests, args.serve_distinct, min(args.serve_plain_requests, args.serve_requests)
+    out = {"workload": "first %d requests of the 100k-request Poisson 2000/s stream (seed 5), N log-uniform "
+                       "[256, 8192], 1-32 rhs, A = B B^T/N + I; client inputs of the first %d requests held in "
+                       "pinned host memory and cycled (request i carries the inputs of request i mod %d); "
+                       "latency = arrival -> X in host memory, upload of A and B and download of X included; "
+                       "plain per-request path on the first %d requests" % (n, P, P, n_plain)}
     for prec in ("fp64", "bf16"):
+        pool = {}
         sstream = torch.cuda.Stream(device=dev)
         # an FP64-only stream runs the resident kernel without the tensor-memory
         # path (two CTAs per SM)
         ctx = b3t.Context(stream=sstream.cuda_stream, timeout_ns=60_000_000_000, stream_no_mx=prec == "fp64")
-        reqs = sv.make_requests(args.serve_requests, 2000.0, 5, prec=prec)
-        gen_s = sv.prepare(reqs)
-        cont = sv.serve(ctx, reqs, prec=prec, budget_bytes=64 << 30, max_inflight=48, time_limit=300.0)
+        reqs = sv.make_requests(n, 2000.0, 5, prec=prec, distinct=P)
+        gen_s, pinned = sv.prepare(reqs, pool=pool)
+        cont = sv.serve(ctx, reqs, prec=prec, budget_bytes=64 << 30, max_inflight=48, time_limit=600.0)
         cont["input_generation_s"] = gen_s
+        cont["pinned_input_bytes"] = pinned
         ctx.close()
         ctx2 = b3t.Context(stream=torch.cuda.current_stream(dev).cuda_stream, timeout_ns=60_000_000_000)
-        reqs2 = sv.make_requests(args.serve_requests, 2000.0, 5, prec=prec)
-        sv.prepare(reqs2)
-        plain = sv.serve_plain(ctx2, reqs2, prec=prec, time_limit=300.0)
+        reqs2 = sv.make_requests(n_plain, 2000.0, 5, prec=prec, distinct=P)
+        sv.prepare(reqs2, pool=pool)
+        plain = sv.serve_plain(ctx2, reqs2, prec=prec, time_limit=600.0)
         ctx2.close()
         out[prec] = {"continuous": cont, "plain": plain}
+        del reqs, reqs2, pool
+        torch.cuda.empty_cache()
     return out
 
 
@@ -689,16 +718,19 @@ def run_serve_sweep(dev, args):
     import torch
     import paper_1304_0878_b300 as b3t
     from paper_1304_0878_b300 import serve as sv
+    n = min(args.serve_requests, 500) if args.serve_requests == 2000 else args.serve_requests
     out = {"workload": "first %d requests of the seed-5 stream, N log-uniform [256, 8192], 1-32 rhs, "
-                       "at each offered rate" % args.serve_requests}
+                       "at each offered rate; client inputs of the first %d requests cycled, uploads and "
+                       "downloads inside the latency" % (n, args.serve_distinct)}
     for prec, rates in SWEEP_RATES.items():
         rows = []
+        pool = {}
         for rate in rates:
             sstream = torch.cuda.Stream(device=dev)
             ctx = b3t.Context(stream=sstream.cuda_stream, timeout_ns=60_000_000_000, stream_no_mx=prec == "fp64")
-            reqs = sv.make_requests(args.serve_requests, rate, 5, prec=prec)
-            sv.prepare(reqs)
-            st = sv.serve(ctx, reqs, prec=prec, budget_bytes=64 << 30, max_inflight=48, time_limit=300.0)
+            reqs = sv.make_requests(n, rate, 5, prec=prec, distinct=args.serve_distinct)
+            sv.prepare(reqs, pool=pool)
+            st = sv.serve(ctx, reqs, prec=prec, budget_bytes=64 << 30, max_inflight=48, time_limit=600.0)
             ctx.close()
             rows.append({"offered_per_s": rate, "solves_per_s": st["solves_per_s"], "p50_ms": st["p50_ms"],
                          "p99_ms": st["p99_ms"], "failed": st["failed"], "max_eta": st["max_eta"]})
@@ -923,6 +955,56 @@ def run_trace_headline(dev, args):
     return out
 
 
+def run_trace_mixed(dev, args):
+    """One traced mixed-precision factorisation (bf16 updates, FP64 panel),
+    N = --n, tile --b, the panel solve by --mx-trsm: CTA busy fraction, the
+    per-kind share of CTA time and the critical path."""
+    import torch
+    import synth
+    import paper_1304_0878_b300 as b3t
+    from paper_1304_0878_b300 import tiles as dt
+    N, b = args.n, args.b
+    T = N // b
+    ctx = b3t.Context(stream=torch.cuda.current_stream(dev).cuda_stream, timeout_ns=120_000_000_000)
+    A0 = synth.spd_tiles_device(N, b, 3, 0.1, dev)
+    W = A0.float()
+    del A0
+    Lm = torch.zeros(W.shape, dtype=torch.float64, device=dev)
+    Q = dt.q_tiles(T, b, b3t.FMT_BF16, dev)
+    U = torch.zeros((T, b, b), dtype=torch.float64, device=dev)
+    ctx.trace_start(1 << 23)
+    if args.mx_trsm == "subst":
+        ctx.cholesky_mx_submit(dt.tile_ptrs(W), dt.tile_ptrs(Lm), dt.tile_ptrs(Q), T, b, b3t.FMT_BF16)
+    else:
+        ctx.cholesky_mx_inv_submit(dt.tile_ptrs(W), dt.tile_ptrs(Lm), dt.tile_ptrs(Q), dt.tile_ptrs(U), T, b,
+                                   b3t.FMT_BF16)
+    ntasks, nedges = ctx.dag_stats()
+    ed = np.array(ctx.dag_edges(), dtype=np.int64).reshape(-1, 2)
+    ctx.task_wait()
+    tr = ctx.trace_read()
+    ctx.trace_stop()
+    ll = ctx.last_launch()
+    ctx.close()
+    assert len(tr) == ll["nitems"], "trace buffer too small"
+    out = {"workload": "mixed bf16 Cholesky N=%d tile %d (%s), one traced launch" % (N, b, args.mx_trsm),
+           "tasks": ntasks, "edges": nedges, "items": int(len(tr)), "ctas": ll["nctas"],
+           "traced_kernel_ms": ll["kernel_ns"] / 1e6}
+    from paper_1304_0878_b300 import trace
+    out.update(trace.summary(tr, ntasks, ed, ll["nctas"]))
+    # busy fraction over time: tenths of the makespan
+    st = tr["t_start_ns"].astype(np.int64)
+    en = tr["t_end_ns"].astype(np.int64)
+    t0, t1 = int(st.min()), int(en.max())
+    edges_t = np.linspace(t0, t1, 11)
+    busy = []
+    for i in range(10):
+        lo, hi = edges_t[i], edges_t[i + 1]
+        ov = np.clip(np.minimum(en, hi) - np.maximum(st, lo), 0, None)
+        busy.append(round(float(ov.sum()) / (ll["nctas"] * (hi - lo)), 3))
+    out["busy_by_tenth"] = busy
+    return out
+
+
 def run_batch(dev, args):
     """Batching: 24 uneven FP64 factorisations (N log-uniform in [256, 4096],
     the serving stream's sizes, seed 5; tiles from the tuner, ragged sizes
@@ -976,6 +1058,8 @@ def run_part(args):
         res = run_empty_dags(dev, torch.cuda.current_stream(dev))
     elif args.case == "trace_headline":
         res = run_trace_headline(dev, args)
+    elif args.case == "trace_mixed":
+        res = run_trace_mixed(dev, args)
     elif args.case == "batch":
         res = run_batch(dev, args)
     else:
@@ -985,7 +1069,7 @@ def run_part(args):
 
 if __name__ == "__main__":
     a = parse()
-    if a.case in ("empty_dags", "serve_sweep", "trace_headline", "batch"):
+    if a.case in ("empty_dags", "serve_sweep", "trace_headline", "trace_mixed", "batch"):
         run_part(a)
     elif a.case:
         run_case(a)

@@ -2,27 +2,34 @@
 
 Requests (N x N SPD matrix, nrhs right-hand sides) arrive as a Poisson
 process.  The loop admits them in arrival order while their device
-footprint fits an HBM budget and a slot is free, generates each request's
-matrix on the device (a side stream), and hands its work to ONE resident
-executor (stream mode): every request stage is a task graph submitted while
-the others run, so requests that arrive while others are on the GPU join
-them as slots and memory free up, and their tasks share the SMs.
+footprint fits an HBM budget and a slot is free, uploads each request's
+inputs from the client's (pinned) host memory on a side stream, and hands
+its work to ONE resident executor (stream mode): every request stage is a
+task graph submitted while the others run, so requests that arrive while
+others are on the GPU join them as slots and memory free up, and their
+tasks share the SMs.
 
 Stages per request:
   * fp64: factorisation + one solve step (x = (L L^T)^{-1} b, residual, eta);
   * bf16 / e4m3: mixed-precision factorisation + first refinement step, then
     one refinement step per stage until eta <= tol (FP64 residual).
 Factors stay on the device until the request completes.  Latency is
-measured from arrival to the completion of the last stage.
+measured from arrival to the moment the solution is back in host memory:
+it includes the upload of A and B (host -> device) at admission and the
+download of X (device -> host) at the end.
 
 `serve_plain` is the per-request path for comparison: one request at a time,
-one launch per stage, no overlap.
+one launch per stage, no overlap, with the same uploads and downloads.
 
-Request inputs (the matrix and right-hand sides, as a client would send
-them) are built on the device before serving starts (`prepare`, timed
-separately): that step uses library GEMMs, which may be persistent kernels
-that need the whole GPU and so cannot run next to the resident executor.
-Admission then only allocates the working buffers and copies into them.
+Client inputs.  A request's matrix and right-hand sides live in pinned host
+memory, as a client would hold them: packed lower FP64 tiles of the padded
+matrix diag(A, I) and T parts of b x nrhs.  They are built before serving
+(`prepare`, timed separately) on the device, where building them uses library
+GEMMs, then copied to the host.  Host memory bounds how many distinct inputs
+can be held, so a run of n requests uses the first P requests of the stream
+as the input sources: request i arrives at the i-th arrival time of the
+stream and carries the size, right-hand-side count and contents of request
+i mod P.
 """
 import math
 import time
@@ -53,15 +60,19 @@ def footprint(Np, nrhs, b, prec):
 class Request:
     __slots__ = ("rid", "arrival", "N", "nrhs", "seed", "b", "Np", "T", "state", "bufs", "ptrs",
                  "batch", "gen_ev", "t_admit", "t_ready", "t_done", "iters", "eta", "info", "bytes", "x",
-                 "inputs")
+                 "inputs", "src", "host", "slot")
 
-    def __init__(self, rid, arrival, N, nrhs, seed):
+    def __init__(self, rid, arrival, N, nrhs, seed, src=None):
         self.rid, self.arrival, self.N, self.nrhs, self.seed = rid, arrival, int(N), int(nrhs), int(seed)
+        self.src = rid if src is None else src
         self.state = "queued"
         self.iters = 0
         self.eta = float("nan")
         self.info = 0
         self.batch = -1
+        self.host = None
+        self.slot = None
+        self.x = None
 
 
 def make_inputs(req, device, stream):
@@ -96,12 +107,18 @@ def make_inputs(req, device, stream):
 
 
 def generate(req, prec, device, stream):
-    """Admission: the request's working buffers, filled from its inputs with
-    elementwise copies on `stream` (safe next to the resident executor)."""
+    """Admission: the client's inputs are uploaded from pinned host memory
+    (host -> device copies on `stream`), then the request's working buffers
+    are filled from them with elementwise copies (safe next to the resident
+    executor)."""
     import paper_1304_0878_b300 as b3t
     T, b, nrhs = req.T, req.b, req.nrhs
-    A, rhs = req.inputs
+    A_h, rhs_h = req.host
     with torch.cuda.stream(stream):
+        A = torch.empty(A_h.shape, dtype=A_h.dtype, device=device)
+        A.copy_(A_h, non_blocking=True)
+        rhs = torch.empty(rhs_h.shape, dtype=rhs_h.dtype, device=device)
+        rhs.copy_(rhs_h, non_blocking=True)
         X = torch.zeros_like(rhs)
         R = torch.zeros(b3t.ir_work_elems(T, b, nrhs), dtype=torch.float64, device=device)
         eta = torch.zeros(nrhs + 1, dtype=torch.float64, device=device)
@@ -120,14 +137,30 @@ def generate(req, prec, device, stream):
     req.ptrs = {k: dt.tile_ptrs(v) for k, v in bufs.items() if k in ("F", "W", "L", "Q")}
 
 
-def prepare(reqs, device="cuda"):
-    """Build every request's inputs (before serving); returns seconds."""
+def prepare(reqs, device="cuda", pool=None):
+    """Build the client inputs of every distinct source of `reqs` on the
+    device and keep them in pinned host memory (before serving); returns
+    (seconds, pinned bytes of the sources built).  `pool` (a dict, source ->
+    host tensors) is reused and filled, so that runs over the same stream
+    share one set of client inputs."""
     t0 = time.perf_counter()
     s = torch.cuda.current_stream(device)
+    pool = {} if pool is None else pool
+    nbytes = 0
     for r in reqs:
-        make_inputs(r, device, s)
+        if r.src not in pool:
+            make_inputs(r, device, s)
+            A, rhs = r.inputs
+            A_h = torch.empty(A.shape, dtype=A.dtype, pin_memory=True)
+            rhs_h = torch.empty(rhs.shape, dtype=rhs.dtype, pin_memory=True)
+            A_h.copy_(A)
+            rhs_h.copy_(rhs)
+            pool[r.src] = (A_h, rhs_h)
+            nbytes += A_h.numel() * 8 + rhs_h.numel() * 8
+            r.inputs = None
+        r.host = pool[r.src]
     torch.cuda.synchronize(device)
-    return time.perf_counter() - t0
+    return time.perf_counter() - t0, nbytes
 
 
 def submit_stage(ctx, req, prec, first, tol):
@@ -150,12 +183,21 @@ def submit_stage(ctx, req, prec, first, tol):
                        bf["eta"].data_ptr(), T, b, nrhs, flags, first)
 
 
-def release(ctx, req, keep_x=False, stream=None):
-    """Forget the request's registrations (its batches are done); keep_x
-    copies the solution (T parts of b x nrhs) to the host first."""
+def download(req, slot, stream, keep_x=False):
+    """The solution back to the client: X (T parts of b x nrhs) into pinned
+    host memory `slot` (device -> host on `stream`), waited for; keep_x also
+    keeps a copy of it on the request."""
+    X = req.bufs["X"]
+    n = X.numel()
+    with torch.cuda.stream(stream):
+        slot[:n].copy_(X.view(-1), non_blocking=True)
+    stream.synchronize()
     if keep_x:
-        with torch.cuda.stream(stream or torch.cuda.current_stream()):
-            req.x = req.bufs["X"].to("cpu", non_blocking=False)
+        req.x = slot[:n].clone().view(X.shape)
+
+
+def release(ctx, req):
+    """Forget the request's registrations (its batches are done)."""
     for p in req.ptrs.values():
         ctx.tiles_unregister(p, req.T)
     ctx.ir_release(req.bufs["R"].data_ptr(), req.T, req.b, req.nrhs)
@@ -170,14 +212,18 @@ def release(ctx, req, keep_x=False, stream=None):
     req.inputs = None
 
 
-def make_requests(n, rate, seed, nmin=256, nmax=8192, rmax=32, prec="fp64", tile=None):
+def make_requests(n, rate, seed, nmin=256, nmax=8192, rmax=32, prec="fp64", tile=None, distinct=None):
     """n requests (Poisson arrivals at `rate` per second); the tile size is
-    the tuner's choice for each N unless `tile` fixes it."""
+    the tuner's choice for each N unless `tile` fixes it.  With `distinct`
+    = P < n, request i takes the size, right-hand sides and seed of request
+    i mod P of the stream (the input sources) and its own arrival time."""
     import synth
     arr, Ns, nrhs, seeds = synth.serve_requests(n, rate=rate, seed=seed, nmin=nmin, nmax=nmax, rmax=rmax)
+    P = n if distinct is None else max(1, min(n, distinct))
     out = []
     for i in range(n):
-        r = Request(i, float(arr[i]), Ns[i], nrhs[i], seeds[i] % (2 ** 62))
+        j = i % P
+        r = Request(i, float(arr[i]), Ns[j], nrhs[j], seeds[j] % (2 ** 62), src=j)
         r.b = tile or tune.choose_tile(r.N, prec)
         r.Np = dt.pad_size(r.N, r.b)
         r.T = r.Np // r.b
@@ -186,12 +232,42 @@ def make_requests(n, rate, seed, nmin=256, nmax=8192, rmax=32, prec="fp64", tile
     return out
 
 
+def _timeline(samples, t_end, bins=24):
+    """Queue length and admission over time: per time bin, requests that
+    arrived, were admitted and completed, and the largest queue seen."""
+    if not samples:
+        return []
+    w = max(t_end, 1e-6) / bins
+    out = []
+    k = 0
+    prev = (0, 0, 0)
+    for i in range(bins):
+        hi = (i + 1) * w
+        mq = 0
+        last = None
+        while k < len(samples) and samples[k][0] <= hi:
+            mq = max(mq, samples[k][1])
+            last = samples[k]
+            k += 1
+        if last is None:
+            continue
+        arrived, admitted, completed = last[3], last[4], last[5]
+        out.append({"t_s": round(hi, 3), "arrived": arrived - prev[0], "admitted": admitted - prev[1],
+                    "completed": completed - prev[2], "max_queue": mq, "in_flight": last[2]})
+        prev = (arrived, admitted, completed)
+    return out
+
+
 def _stats(reqs, t_first, t_last, prec, mode):
     lat = np.array([r.t_done - r.arrival for r in reqs]) * 1e3
     qd = np.array([r.t_admit - r.arrival for r in reqs]) * 1e3
     ok = [r for r in reqs if r.info == 0]
+    h2d = sum(r.host[0].numel() * 8 + r.host[1].numel() * 8 for r in reqs)
+    d2h = sum(r.host[1].numel() * 8 for r in reqs)
     return {
         "mode": mode, "precision": prec, "requests": len(reqs),
+        "distinct_inputs": len({r.src for r in reqs}),
+        "h2d_bytes": h2d, "d2h_bytes": d2h,
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
         "mean_ms": float(lat.mean()), "admission_wait_p50_ms": float(np.percentile(qd, 50)),
         "solves_per_s": len(reqs) / max(t_last - t_first, 1e-9),
@@ -205,14 +281,14 @@ def _stats(reqs, t_first, t_last, prec, mode):
 def warm_up(prec, device, gen_stream, side, host, reserve_bytes):
     """Initialise, before the resident kernel starts, everything that is set up
     lazily on first use and may synchronise the whole device: cuBLAS handles
-    and workspaces of the generation stream, the random generator, and the
-    caching allocator's pools (one large reservation, freed into torch's
-    cache so that later allocations on that stream reuse it)."""
+    and workspaces of the generation stream, the random generator, pinned
+    staging, and the caching allocator's pools (one large reservation, freed
+    into torch's cache so that later allocations on that stream reuse it)."""
     r = Request(-1, 0.0, 300, 2, 1)
     r.b = tune.choose_tile(r.N, prec)
     r.Np = dt.pad_size(r.N, r.b)
     r.T = r.Np // r.b
-    make_inputs(r, device, gen_stream)
+    prepare([r], device)
     generate(r, prec, device, gen_stream)
     gen_stream.synchronize()
     with torch.cuda.stream(side):
@@ -226,23 +302,33 @@ def warm_up(prec, device, gen_stream, side, host, reserve_bytes):
     torch.cuda.synchronize(device)
 
 
+def _result_slots(reqs, k):
+    """k pinned host buffers, each large enough for any request's X."""
+    n = max(r.Np * r.nrhs for r in reqs)
+    return [torch.empty(n, dtype=torch.float64, pin_memory=True) for _ in range(k)]
+
+
 def serve(ctx, reqs, prec="fp64", budget_bytes=48 << 30, max_inflight=64, tol=1e-12, max_iter=30,
           device="cuda", time_limit=600.0, max_tasks=1 << 22, max_edges=1 << 24, keep_x=False):
     """Continuous batching with the resident executor.  Arrival times in
-    `reqs` are seconds from the start of the run; the requests' inputs must
-    have been built (prepare).  `ctx` must be bound to a stream of its own:
-    the resident kernel occupies it for the whole run (admission copies and
-    read-backs use other streams)."""
+    `reqs` are seconds from the start of the run; the requests' client inputs
+    must be in host memory (prepare).  `ctx` must be bound to a stream of its
+    own: the resident kernel occupies it for the whole run (uploads,
+    admission copies and read-backs use other streams)."""
     gen_stream = torch.cuda.Stream(device=device)
     side = torch.cuda.Stream(device=device)
     host = torch.empty(64, dtype=torch.float64, pin_memory=True)
     warm_up(prec, device, gen_stream, side, host, budget_bytes)
+    free_slots = _result_slots(reqs, max_inflight)
     nb = sum(1 for _ in reqs) * (max_iter + 1) + 16
     # from here until stream_close nothing may synchronise the whole device
     ctx.stream_open(max_tasks, max_edges, nb, int(time_limit * 1e9))
     pending = list(reqs)            # not yet arrived (arrival order)
     queue, gen, run, done = [], [], [], []
     used = 0
+    samples = []
+    t_sample = -1.0
+    admitted = 0
     t0 = time.perf_counter()
     pi = 0
     try:
@@ -257,8 +343,10 @@ def serve(ctx, reqs, prec="fp64", budget_bytes=48 << 30, max_inflight=64, tol=1e
                 r = queue.pop(0)
                 r.t_admit = time.perf_counter() - t0
                 used += r.bytes
+                r.slot = free_slots.pop()
                 generate(r, prec, device, gen_stream)
                 gen.append(r)
+                admitted += 1
             for r in list(gen):
                 if r.gen_ev.query():
                     submit_stage(ctx, r, prec, True, tol)
@@ -281,27 +369,38 @@ def serve(ctx, reqs, prec="fp64", budget_bytes=48 << 30, max_inflight=64, tol=1e
                     r.batch = ctx.stream_submit()
                     r.iters += 1
                     continue
+                download(r, r.slot, side, keep_x)
                 r.t_done = time.perf_counter() - t0
                 run.remove(r)
-                release(ctx, r, keep_x, side)
+                release(ctx, r)
+                free_slots.append(r.slot)
+                r.slot = None
                 used -= r.bytes
                 done.append(r)
+            if now - t_sample >= 0.02:
+                samples.append((now, len(queue), len(gen) + len(run), pi, admitted, len(done)))
+                t_sample = now
             if not gen and not run and not queue and pi < len(pending):
                 time.sleep(max(0.0, min(pending[pi].arrival - (time.perf_counter() - t0), 0.001)))
     finally:
         ctx.stream_close()
     t_first = min(r.arrival for r in reqs)
     t_last = max(r.t_done for r in done)
-    return _stats(done, t_first, t_last, prec, "continuous")
+    st = _stats(done, t_first, t_last, prec, "continuous")
+    samples.append((t_last, 0, 0, pi, admitted, len(done)))
+    st["max_queue"] = max(x[1] for x in samples)
+    st["timeline"] = _timeline(samples, t_last)
+    return st
 
 
 def serve_plain(ctx, reqs, prec="fp64", tol=1e-12, max_iter=30, device="cuda", time_limit=600.0,
                 keep_x=False):
     """Per-request path: requests one at a time in arrival order, one launch
-    per stage, nothing overlapped."""
+    per stage, nothing overlapped (uploads and downloads as in serve)."""
     stream = torch.cuda.current_stream(device)
     done = []
     host = torch.empty(64, dtype=torch.float64, pin_memory=True)
+    slot = _result_slots(reqs, 1)[0]
     t0 = time.perf_counter()
     for r in reqs:
         now = time.perf_counter() - t0
@@ -329,8 +428,9 @@ def serve_plain(ctx, reqs, prec="fp64", tol=1e-12, max_iter=30, device="cuda", t
             first = False
             if prec == "fp64" or r.eta <= tol or r.iters >= max_iter:
                 break
+        download(r, slot, stream, keep_x)
         r.t_done = time.perf_counter() - t0
-        release(ctx, r, keep_x)
+        release(ctx, r)
         done.append(r)
     t_first = min(r.arrival for r in reqs)
     t_last = max(r.t_done for r in done)

@@ -1,8 +1,13 @@
-"""Serving with continuous batching (GPU): every request completes with an
-FP64-level backward error, and each request's solution computed in the mix
-(stream mode, overlapping with other requests) is bit-for-bit the solution
-of the same request served alone (one request at a time)."""
+"""Serving with continuous batching (GPU): every served solution is checked
+against the oracle (its sequential tiled Cholesky and substitutions on the
+request's own matrix and right-hand sides, as the client uploaded them), the
+backward error is recomputed on the host, and each request's solution
+computed in the mix (stream mode, overlapping with other requests) is
+bit-for-bit the solution of the same request served alone (one request at a
+time)."""
 import copy
+import multiprocessing as mp
+from concurrent.futures import ProcessPoolExecutor
 
 import numpy as np
 import pytest
@@ -11,8 +16,9 @@ import torch
 import paper_1304_0878_b300 as b3t
 from paper_1304_0878_b300 import serve as sv
 from paper_1304_0878_b300 import batch as bt
+import serve_oracle
 import synth
-from oracle import cholesky as och
+from oracle import cholesky as och, ir as oir
 
 pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not torch.cuda.is_available(), reason="no CUDA device")]
@@ -31,6 +37,11 @@ def requests(n, rate, prec, nmin=200, nmax=1536):
 def test_serve_mix_equals_alone(orc, prec, tol, n, nmin, nmax, inflight):
     reqs = requests(n, 400.0, prec, nmin, nmax)
     sv.prepare(reqs)
+    # the oracle's solutions, computed on the host cores while the GPU serves
+    # (worker processes started with spawn: they never touch CUDA)
+    pool = ProcessPoolExecutor(max_workers=min(n, 8), mp_context=mp.get_context("spawn"))
+    futs = [pool.submit(serve_oracle.solve, (r.host[0].numpy().copy(), r.host[1].numpy().copy(), r.Np, r.b))
+            for r in reqs]
     side = torch.cuda.Stream()
     # FP64 requests are served by the resident kernel without the
     # tensor-memory path (two CTAs per SM)
@@ -48,6 +59,18 @@ def test_serve_mix_equals_alone(orc, prec, tol, n, nmin, nmax, inflight):
     for r, a in zip(reqs, alone):
         assert r.N == a.N and r.iters == a.iters
         assert torch.equal(r.x, a.x)
+    # against the oracle: FP64 to the oracle's own rounding level; mixed
+    # precision refined to eta <= 1e-12 agrees to about kappa(A) * 1e-12
+    # (kappa <= 5 for A = B B^T / N + I), and the backward error recomputed
+    # on the host from the uploaded A and B and the downloaded X meets the
+    # target (the FP64 residual of an N <= 3584 system adds at most ~1e-13)
+    xtol = 1e-13 if prec == "fp64" else 1e-10
+    for r, f in zip(reqs, futs):
+        Xo, A, Bm = f.result()
+        X = serve_oracle.dense_rhs(r.x.numpy())
+        assert np.max(np.abs(X - Xo)) / np.max(np.abs(Xo)) <= xtol
+        assert oir.backward_error(A, X, Bm) <= 2e-12
+    pool.shutdown()
 
 
 def test_batch_uneven_sizes_one_launch(orc):

@@ -111,6 +111,46 @@ def test_serving_requests():
     assert all(r.b == 256 for r in f)
 
 
+def test_serving_requests_cycle_distinct_sources():
+    # n requests over P input sources: request i keeps the i-th arrival of the
+    # stream and takes size, right-hand sides and seed of request i mod P
+    full = sv.make_requests(40, 2000.0, seed=5)
+    cyc = sv.make_requests(40, 2000.0, seed=5, distinct=8)
+    assert [r.arrival for r in cyc] == [r.arrival for r in full]
+    for i, r in enumerate(cyc):
+        s = full[i % 8]
+        assert (r.src, r.N, r.nrhs, r.seed, r.b, r.bytes) == (i % 8, s.N, s.nrhs, s.seed, s.b, s.bytes)
+    assert [r.src for r in full] == list(range(40))
+
+
+def test_serving_timeline_bins():
+    # samples: (t, queue, in flight, arrived, admitted, completed), counts
+    # cumulative; bins report increments and the largest queue in the bin
+    samples = [(0.1, 3, 1, 4, 1, 0), (0.4, 5, 2, 8, 3, 1), (0.6, 1, 2, 9, 7, 5), (1.0, 0, 0, 9, 9, 9)]
+    tl = sv._timeline(samples, 1.0, bins=2)
+    assert tl == [{"t_s": 0.5, "arrived": 8, "admitted": 3, "completed": 1, "max_queue": 5, "in_flight": 2},
+                  {"t_s": 1.0, "arrived": 1, "admitted": 6, "completed": 8, "max_queue": 1, "in_flight": 0}]
+
+
+def test_serve_oracle_helper_solves_the_padded_system():
+    # the test helper that checks served solutions: packed tiles of diag(A, I)
+    # and right-hand-side parts in, the oracle's X with A X = B out
+    import serve_oracle
+    from oracle import cholesky as och
+    N, b, nrhs = 200, 64, 3
+    Np = dt.pad_size(N, b)
+    A = np.eye(Np)
+    A[:N, :N] = synth.spd_host(N, seed=3, shift=1.0)
+    Bm = np.zeros((Np, nrhs))
+    Bm[:N] = synth.rhs(N, nrhs, seed=4)
+    parts = np.ascontiguousarray(Bm.reshape(Np // b, b, nrhs).transpose(0, 2, 1))
+    assert np.array_equal(serve_oracle.dense_rhs(parts), Bm)
+    X, A2, B2 = serve_oracle.solve((och.to_tiles(A, b), parts, Np, b))
+    assert np.array_equal(A2, A) and np.array_equal(B2, Bm)
+    assert np.max(np.abs(A @ X - Bm)) <= 1e-12 * np.max(np.abs(Bm))
+    assert np.all(X[N:] == 0.0)
+
+
 def test_footprint_counts_every_buffer():
     # fp64: A + factor tiles; mixed: A (FP64), W (binary32), L (FP64), Q
     # (one byte per element for E4M3, two for bf16); two block vectors; the
