@@ -35,7 +35,7 @@ namespace b3t {
 // dynamic shared memory per CTA: tensor-core stages and the W block need
 // 160 KB; without them the largest body (FP64 TRSM) needs 75 KB, which
 // leaves room for two CTAs
-constexpr size_t kSmemData = 164 * 1024;   // 3 x 32 KiB operand stages + the 64 KiB W block + slack
+constexpr size_t kSmemData = 164 * 1024;   // kMxStages (5) x 32 KiB operand stages + slack
 constexpr size_t kSmemDataNoMx = 76 * 1024;
 
 __device__ __forceinline__ unsigned long long ld_acq(const unsigned long long *p) {
@@ -449,7 +449,7 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
     unsigned char *smem = (unsigned char *)(((uintptr_t)dsmem + 1023) & ~(uintptr_t)1023);
     __shared__ unsigned long long s_item;
     __shared__ int s_info, s_fail, s_e;
-    __shared__ __align__(8) uint64_t s_bars[2 * kMxStages + 2];
+    __shared__ __align__(8) uint64_t s_bars[2 * kMxStages + 1];
     __shared__ uint32_t s_tmem;
     __shared__ double s_red[kThreads / 32];
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -458,14 +458,13 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
     mx.full = s_bars;
     mx.empty = s_bars + kMxStages;
     mx.done = s_bars + 2 * kMxStages;
-    mx.wfull = s_bars + 2 * kMxStages + 1;
     mx.stage = smem;
     mx.fills = 0;
     mx.items = 0;
     mx.tmem = 0;
     if (kMx && p.has_mx) {
         if (tid == 0) {
-            for (int i = 0; i < 2 * kMxStages + 2; ++i) mbar_init(&s_bars[i], 1);
+            for (int i = 0; i < 2 * kMxStages + 1; ++i) mbar_init(&s_bars[i], 1);
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
         if (warp == 0) tmem_alloc(&s_tmem, kTmemCols);

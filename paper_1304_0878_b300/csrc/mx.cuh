@@ -14,9 +14,10 @@
 //   W <- fl32(W - 2^(ea+eb) * QA QB^T),
 // QA = rows 128*bi.. of the first operand, QB = rows 128*bj.. of the second.
 // One thread issues bulk copies (cp.async.bulk, completion on an mbarrier)
-// into a 3-stage ring and the MMAs (M = 128, N = 128, 4 per 128-byte K
-// chunk); the accumulator lives in tensor memory (128 columns) and all eight
-// warps read it back for the epilogue.
+// into a kMxStages ring and the MMAs (M = 128, N = 128, 4 per 128-byte K
+// chunk); the accumulator lives in tensor memory (128 columns), starts from
+// the W block (all eight warps write it there) and is read back by all eight
+// warps for the epilogue.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
@@ -24,7 +25,7 @@
 
 namespace b3t {
 
-constexpr int kMxStages = 3;
+constexpr int kMxStages = 5;
 constexpr uint32_t kChunkBytes = 16384;
 constexpr uint32_t kTmemCols = 128;
 
@@ -147,10 +148,9 @@ struct MxState {
     uint64_t *full;       // [kMxStages]
     uint64_t *empty;      // [kMxStages]
     uint64_t *done;       // [1]
-    uint64_t *wfull;      // [1] the item's W block has landed in shared memory
-    unsigned char *stage; // kMxStages x 32 KiB, 1024-aligned, then the W block (64 KiB)
+    unsigned char *stage; // kMxStages x 32 KiB, 1024-aligned
     uint32_t tmem;        // accumulator base address
-    uint32_t fills;       // stage fills issued so far (thread 0)
+    uint32_t fills;       // stage fills issued so far (kept by thread 0 only)
     uint32_t items;       // items completed so far (all threads)
 };
 
@@ -264,8 +264,33 @@ __device__ __forceinline__ void quant_item(const TaskRec &t, int item, double *r
     }
 }
 
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float *v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+        "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+        "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+        "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+        "r"(__float_as_uint(v[15]))
+        : "memory");
+}
+
 // SYRK_MX (syrk = true, lower blocks only) / GEMM_MX update of one 128 x 128
-// block.  Returns 0, or ETIMEDOUT when a pipeline wait ran out.
+// block.  The accumulator starts from the W block itself:
+//   D = -W / s + QA QB^T   (tensor cores, binary32 accumulation),
+//   W <- -s D,
+// with s = 2^(ea+eb): dividing by a power of two and negating are exact and
+// round-to-nearest is symmetric, so this is W - s QA QB^T with the block's
+// old value as the first term of the sum.  Every thread owns one row of the
+// block (TMEM lane) and 64 of its columns: it loads them from global memory
+// (a warp reads 32 consecutive floats of a column: coalesced), writes them
+// into tensor memory (tcgen05.st), and after the MMAs reads the result back
+// (tcgen05.ld) and stores it, so the W block never passes through shared
+// memory.  Thread 0 streams the operand chunks through the kMxStages ring
+// (bulk copies) and issues the MMAs.  Returns 0, or ETIMEDOUT when a
+// pipeline wait ran out (block-wide).
 __device__ __forceinline__ int mx_update_item(const TaskRec &t, int item, bool syrk, MxState &st,
                                               int64_t limit_ns, int *s_fail) {
     const int b = (int)t.n, fmt = t.aux, es = q_esize(fmt);
@@ -284,29 +309,49 @@ __device__ __forceinline__ int mx_update_item(const TaskRec &t, int item, bool s
     }
     const int nk = b * es / 128;
     const uint32_t idesc = mx_idesc(fmt == 0 ? 1u : 0u);
-    const int tid = threadIdx.x;
-    // the item's 128 x 128 block of W (column-major, 128 columns of 512 bytes)
-    // is copied into shared memory while the operands stream in
-    float *Ws = (float *)(st.stage + kMxStages * 2 * kChunkBytes);
-    float *Wg = W + (size_t)bi * kMxBlk + (size_t)bj * kMxBlk * b;
-    if ((tid >> 5) == 1) {
-        const int lane = tid & 31;
-        if (lane == 0) {
-            asm volatile("fence.proxy.async.global;" ::: "memory");
-            mbar_expect_tx(st.wfull, kMxBlk * kMxBlk * 4);
-        }
-        __syncwarp();
-        for (int c = lane; c < kMxBlk; c += 32)
-            bulk_g2s(Ws + c * kMxBlk, Wg + (size_t)c * b, kMxBlk * 4, st.wfull);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, h = warp >> 2;
+    const int rr = 32 * q + lane;                            // row of the block = TMEM lane
+    int es_sum = 0;
+    if (fmt == 1) {
+        es_sum = *(const int *)(QA + (size_t)b * b * es) + *(const int *)(QB + (size_t)b * b * es);
     }
+    const uint32_t G = st.fills;
+    uint32_t issued = 0;
     if (tid == 0) {
         *s_fail = 0;
         // make generic-proxy writes of the producer tasks visible to the bulk copies
         asm volatile("fence.proxy.async.global;" ::: "memory");
+        // the first chunks start loading while the W block goes into tensor memory
+        while ((int)issued < nk && (int)issued < kMxStages) {
+            const uint32_t g = G + issued, slot = g % kMxStages;
+            if (g >= (uint32_t)kMxStages && !mbar_wait(&st.empty[slot], ((g / kMxStages) - 1) & 1, limit_ns)) {
+                *s_fail = 1;
+                break;
+            }
+            unsigned char *sa = st.stage + slot * 2 * kChunkBytes;
+            mbar_expect_tx(&st.full[slot], 2 * kChunkBytes);
+            bulk_g2s(sa, QA + ((size_t)bi * nk + issued) * kChunkBytes, kChunkBytes, &st.full[slot]);
+            bulk_g2s(sa + kChunkBytes, QB + ((size_t)bj * nk + issued) * kChunkBytes, kChunkBytes, &st.full[slot]);
+            ++issued;
+        }
+    }
+    // D = -W / s: row rr, columns 64 h .. 64 h + 63 of the block
+    float *Wg = W + (size_t)(bi * kMxBlk + rr) + (size_t)(bj * kMxBlk + 64 * h) * b;
+    const uint32_t tl = st.tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(64 * h);
+#pragma unroll 1
+    for (int i = 0; i < 4; ++i) {
+        float v[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[c] = -ldexpf(Wg[(size_t)(16 * i + c) * b], -es_sum);
+        tmem_st16(tl + 16 * i, v);
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
         tc_fence_after();
-        uint32_t issued = 0;
-        const uint32_t G = st.fills;
-        bool fail = false;
+        bool fail = *s_fail != 0;
         for (int kk = 0; kk < nk && !fail; ++kk) {
             while ((int)issued < nk && (int)issued < kk + kMxStages) {
                 const uint32_t g = G + issued, slot = g % kMxStages;
@@ -329,9 +374,10 @@ __device__ __forceinline__ int mx_update_item(const TaskRec &t, int item, bool s
             const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + kChunkBytes);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                // advance 32 bytes of K per MMA inside the swizzle atom
-                if (fmt == 0) mma_bf16(st.tmem, ad + 2 * i, bd + 2 * i, idesc, (kk | i) ? 1u : 0u);
-                else mma_e4m3(st.tmem, ad + 2 * i, bd + 2 * i, idesc, (kk | i) ? 1u : 0u);
+                // advance 32 bytes of K per MMA inside the swizzle atom; every
+                // MMA accumulates (the accumulator holds -W / s)
+                if (fmt == 0) mma_bf16(st.tmem, ad + 2 * i, bd + 2 * i, idesc, 1u);
+                else mma_e4m3(st.tmem, ad + 2 * i, bd + 2 * i, idesc, 1u);
             }
             mma_commit(&st.empty[slot]);
         }
@@ -348,46 +394,24 @@ __device__ __forceinline__ int mx_update_item(const TaskRec &t, int item, bool s
     }
     __syncthreads();
     const bool ok = mbar_wait(st.done, st.items & 1, limit_ns);
-    const bool wok = mbar_wait(st.wfull, st.items & 1, limit_ns);
     st.items++;
     tc_fence_after();
-    // every thread takes the same branch: each one's waits may end differently
-    if (__syncthreads_or(*s_fail || !ok || !wok)) return ETIMEDOUT;
-    // epilogue: warp w reads TMEM lanes 32*(w%4).. and columns 64*(w/4)..
-    const int warp = tid >> 5, lane = tid & 31;
-    const int q = warp & 3, h = warp >> 2;
-    float s = 1.0f;
-    if (fmt == 1) {
-        const int ea = *(const int *)(QA + (size_t)b * b * es);
-        const int eb = *(const int *)(QB + (size_t)b * b * es);
-        s = ldexpf(1.0f, ea + eb);
-    }
-    const int rr = 32 * q + lane, gr = bi * kMxBlk + rr;
+    // every thread takes the same branch: each one's wait may end differently
+    if (__syncthreads_or(*s_fail || !ok)) return ETIMEDOUT;
+    // epilogue: W <- -s D, row rr, the thread's 64 columns (SYRK: the upper
+    // part of a diagonal block is left as it was)
+    const int gr = bi * kMxBlk + rr;
 #pragma unroll 1
     for (int i = 0; i < 4; ++i) {
         float v[16];
-        tmem_ld16(st.tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * 64 + 16 * i), v);
+        tmem_ld16(tl + 16 * i, v);
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
-            const int cc = h * 64 + 16 * i + c;
-            if (!syrk || gr >= bj * kMxBlk + cc) {
-                float *p = Ws + cc * kMxBlk + rr;
-                *p = fmaf(-s, v[c], *p);
-            }
+            const int gc = bj * kMxBlk + 64 * h + 16 * i + c;
+            if (!syrk || gr >= gc) Wg[(size_t)(16 * i + c) * b] = -ldexpf(v[c], es_sum);
         }
     }
     tc_fence_before();
-    // the updated block goes back with bulk stores (the upper part of a
-    // diagonal block is written back as it was read)
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (warp == 1) {
-        for (int c = lane; c < kMxBlk; c += 32) bulk_s2g_mx(Wg + (size_t)c * b, Ws + c * kMxBlk, kMxBlk * 4);
-        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-        asm volatile("fence.proxy.async.global;" ::: "memory");
-        __threadfence();
-    }
     __syncthreads();
     return 0;
 }

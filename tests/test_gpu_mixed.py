@@ -235,20 +235,26 @@ def factor_mx_inv_dev(ctx, A, b, fmt):
 @pytest.mark.parametrize("fmt", ["bf16", "e4m3"])
 @pytest.mark.parametrize("N,b", [(512, 128), (768, 256)])
 def test_mixed_inv_factor_on_integer_matrix(orc, gctx, fmt, N, b):
-    # integer L0: the diagonal factors are exact, the panel tiles carry only
-    # the inverse's FP64 rounding, which the quantisation rounds away (the
-    # low-precision operands, hence every update, stay exact).  An explicit
-    # inverse is only as accurate as the diagonal tile is well conditioned:
-    # random integer triangles with small diagonals have inverses of 1e15 and
-    # more, so this L0 has entries in [-1, 1] and diagonal 8 (max |L_kk^-1|
-    # about 0.2); products and partial sums stay exact in binary32
+    # integer L0: the panel tiles carry the inverse's FP64 rounding (an
+    # explicit inverse is only as accurate as the diagonal tile is well
+    # conditioned: random integer triangles with small diagonals have inverses
+    # of 1e15 and more, so this L0 has entries in [-1, 1] and diagonal 8, max
+    # |L_kk^-1| about 0.2).  Entries that are 0 in L0 come out as residues of
+    # up to ~1e-14: E4M3 (smallest step 2^-9 times the tile scale) rounds them
+    # to 0, so its operands and updates, hence the diagonal factors, are
+    # exact; bf16 keeps them (binary32's exponent range), and whether they
+    # survive the binary32 sums depends on the summation order, so there the
+    # diagonal blocks meet the same relative bound as the rest
     A, L0 = synth.integer_spd(N, seed=N + 7, lo=-1, hi=1, dlo=8, dhi=8)
     L = factor_mx_inv_dev(gctx, A, b, fmt)
     assert np.max(np.abs(L - L0)) / np.max(np.abs(L0)) <= 1e-13
     T = N // b
     for k in range(T):
         blk = slice(k * b, (k + 1) * b)
-        assert np.array_equal(L[blk, blk], L0[blk, blk])
+        if fmt == "e4m3":
+            assert np.array_equal(L[blk, blk], L0[blk, blk])
+        else:
+            assert np.max(np.abs(L[blk, blk] - L0[blk, blk])) <= 1e-13 * np.max(np.abs(L0))
 
 
 @pytest.mark.parametrize("fmt", ["bf16", "e4m3"])
