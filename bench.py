@@ -65,6 +65,7 @@ def parse():
     p.add_argument("--no-mixed", action="store_true")
     p.add_argument("--nrhs", type=int, default=16)
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--no-scipy", action="store_true", help="skip the LAPACK CPU baselines (scipy, all host cores)")
     p.add_argument("--mx-trsm", default="inv", choices=["inv", "subst", "both"],
                    help="mixed panel solve: product with the inverted diagonal tile (TRTRI + TRMM_MX) "
                         "or row substitution (TRSM_MX)")
@@ -171,9 +172,9 @@ def dist():
 def recorded_traffic(key):
     """DRAM bytes (read + write) per launch that an ncu capture recorded for
     this workload, or None when none exists or the kernel sources changed
-    since (paper_1304_0878_b300/ncu_traffic.json holds the source hash)."""
+    since (profiles/ncu_traffic.json holds the source hash)."""
     import paper_1304_0878_b300.build as pb
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1304_0878_b300", "ncu_traffic.json")
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)[key]
@@ -384,7 +385,9 @@ def run_ours(args):
         mse = e2.elapsed_time(e3) / ke
         nbytes = A0.numel() * A0.element_size()
         e2e = {"value": ws * flops / (mse / 1e3) / 1e12, "unit": "TFLOP/s",
-               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "ms_per_step": mse}
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "ms_per_step": mse,
+               "note": "per step: pinned host A -> device, replay of the captured DAG (task table built once, "
+                       "its host-side dependency derivation outside the timed region), L -> pinned host"}
         del hA, hL
 
     nctas = ctx.last_launch()["nctas"]
@@ -399,6 +402,8 @@ def run_ours(args):
             cpu["empty_dags"] = oracle_empty_dags(min(3.0, args.cpu_seconds / 5))
         if not args.no_serve:
             cpu["serving_scipy"] = scipy_serving_sample(min(10.0, args.cpu_seconds), args.serve_requests)
+        if not args.no_scipy:
+            cpu["library"] = scipy_baselines(A0.cpu().numpy(), N, b, args.nrhs)
 
     secondary = {}
     if not args.no_secondary:
@@ -438,7 +443,141 @@ def run_ours(args):
         "secondary": secondary,
         "provenance": provenance(),
     }
+    line["summary"] = summarise(line)
     print(json.dumps(line))
+
+
+def summarise(line):
+    """The figures a reader needs first, last on the line (a log tail keeps them)."""
+    sec = line.get("secondary") or {}
+    g = lambda d, *ks: _dig(d, ks)
+    out = {"cholesky_fp64_tflops": line["value"], "roofline_frac": line["roofline"]["frac"],
+           "e2e_tflops": g(line, "e2e", "value")}
+    for k in ("vector_chains", "vector_chains_depth_first"):
+        if k in sec:
+            out[k] = {"ms": sec[k]["ms"], "hbm_frac": sec[k]["hbm_frac"]}
+    ed = sec.get("empty_dags") or {}
+    tps = {k: v["tasks_per_s"] for k, v in ed.items()}
+    if "tasks_per_s" in sec:
+        tps["chains_100k"] = sec["tasks_per_s"]["value"]
+    if tps:
+        out["tasks_per_s"] = tps
+    for k in ("cholesky_small", "cholesky_small_fifo"):
+        if k in sec:
+            out[k + "_ms"] = sec[k]["ms"]
+    tts = sec.get("time_to_solution")
+    if tts:
+        out["time_to_solution"] = {"fp64_ms": tts["fp64"]["ms"]}
+        for p in ("bf16", "e4m3"):
+            if p in tts:
+                out["time_to_solution"][p] = {k: tts[p][k] for k in ("ms", "factor_ms", "speedup_vs_fp64", "eta",
+                                                                      "host_sampled_eta", "iterations")}
+    sv = sec.get("serving")
+    if sv:
+        out["serving"] = {}
+        for p in ("fp64", "bf16"):
+            if p in sv:
+                c, pl = sv[p]["continuous"], sv[p]["plain"]
+                out["serving"][p] = {"requests": c["requests"], "p50_ms": c["p50_ms"], "p99_ms": c["p99_ms"],
+                                     "solves_per_s": c["solves_per_s"], "max_queue": c.get("max_queue"),
+                                     "plain_requests": pl["requests"], "plain_solves_per_s": pl["solves_per_s"],
+                                     "plain_p99_ms": pl["p99_ms"]}
+    cpu = line.get("cpu_baseline") or {}
+    if cpu:
+        out["cpu"] = {"oracle_tflops_1core": cpu.get("value"),
+                      "scipy_cholesky_n32768_tflops": g(cpu, "library", "cholesky_n32768", "TFLOPs"),
+                      "scipy_cholesky_n1024_ms": g(cpu, "library", "cholesky_n1024", "ms"),
+                      "scipy_cores": g(cpu, "library", "cores")}
+    return out
+
+
+def _dig(d, ks):
+    for k in ks:
+        if not isinstance(d, dict) or k not in d:
+            return None
+        d = d[k]
+    return d
+
+
+def host_sym_row(tl, i, N, b):
+    """Row i of the symmetric A from its packed lower tiles on the host
+    (tl[t][c, r] = element (I*b + r, J*b + c) of tile t = (I, J))."""
+    from paper_1304_0878_b300.tiles import tile_index
+    T = N // b
+    I, r = divmod(i, b)
+    parts = [tl[tile_index(I, J, T)][:, r] for J in range(I + 1)]        # row r of tiles (I, J), J <= I
+    parts[-1] = np.concatenate([parts[-1][: r + 1], tl[tile_index(I, I, T)][r, r + 1:]])
+    parts += [tl[tile_index(J, I, T)][r, :] for J in range(I + 1, T)]    # column r of tiles (J, I), J > I
+    return np.concatenate(parts)
+
+
+def host_anorm(tl, N, b):
+    """Exact ||A||_inf of the symmetric A from its lower tiles, in FP64 on the host."""
+    from paper_1304_0878_b300.tiles import tile_index
+    T = N // b
+    rows = np.zeros(N)
+    for j in range(T):
+        for i in range(j, T):
+            F = np.abs(tl[tile_index(i, j, T)].T)                        # F[r, c] = A(i*b + r, j*b + c)
+            if i == j:
+                F = np.tril(F) + np.tril(F, -1).T
+                rows[i * b:(i + 1) * b] += F.sum(axis=1)
+            else:
+                rows[i * b:(i + 1) * b] += F.sum(axis=1)
+                rows[j * b:(j + 1) * b] += F.sum(axis=0)
+    return float(rows.max())
+
+
+def sampled_host_eta(tl, anorm, X, Bh, N, b, nsamp=32, seed=1):
+    """Normwise backward error of the device solution X (N x nrhs) on sampled
+    rows: |b_i - A_i X| / (||A||_inf max|x_j| + max|b_j|), the residual rows
+    formed in FP64 on the host from the stored A (the check the oracle's
+    backward_error makes, restricted to rows it can afford at this size)."""
+    rng = np.random.default_rng(seed)
+    xn = np.abs(X).max(axis=0)
+    bn = np.abs(Bh).max(axis=0)
+    worst = 0.0
+    for _ in range(nsamp):
+        i = int(rng.integers(0, N))
+        r = Bh[i] - host_sym_row(tl, i, N, b) @ X
+        worst = max(worst, float(np.max(np.abs(r) / (anorm * xn + bn))))
+    return worst
+
+
+def scipy_baselines(tl, N, b, nrhs):
+    """Library CPU baselines on all host cores (LAPACK through scipy): the
+    FP64 Cholesky of the N = 1024 matrix (seed 0), and of the N = 32768
+    matrix (the same bytes as the device's A, assembled from the tiles) with
+    the FP64 solve of the 16 right-hand sides (seed 4)."""
+    import scipy.linalg as sla
+    import synth
+    cores = len(os.sched_getaffinity(0))
+    out = {"kind": "scipy.linalg (LAPACK) FP64 on the host", "cores": cores}
+    A1 = synth.spd_host(1024, seed=0, shift=1.0)
+    ts = []
+    for _ in range(7):
+        t0 = time.perf_counter()
+        sla.cholesky(A1, lower=True, check_finite=False)
+        ts.append(time.perf_counter() - t0)
+    m1 = float(np.median(ts[2:]))
+    out["cholesky_n1024"] = {"ms": 1e3 * m1, "TFLOPs": cholesky_flops(1024) / m1 / 1e12}
+    from paper_1304_0878_b300.tiles import tile_index
+    T = N // b
+    A = np.zeros((N, N), order="F")
+    for j in range(T):
+        for i in range(j, T):
+            A[i * b:(i + 1) * b, j * b:(j + 1) * b] = tl[tile_index(i, j, T)].T
+    t0 = time.perf_counter()
+    c = sla.cho_factor(A, lower=True, overwrite_a=True, check_finite=False)
+    tf = time.perf_counter() - t0
+    Bh = synth.rhs(N, nrhs, seed=4)
+    t0 = time.perf_counter()
+    sla.cho_solve(c, Bh, check_finite=False)
+    tsv = time.perf_counter() - t0
+    out["cholesky_n%d" % N] = {"s": tf, "TFLOPs": cholesky_flops(N) / tf / 1e12}
+    out["solve_n%d" % N] = {"ms": 1e3 * tsv, "nrhs": nrhs, "time_to_solution_s": tf + tsv}
+    del A, c
+    return out
 
 
 def rhs_parts(N, b, nrhs, seed, dev):
@@ -460,9 +599,19 @@ def run_time_to_solution(ctx, A0, t, g64, N, b, dev, stream, args):
     import torch
     import paper_1304_0878_b300 as b3t
     from paper_1304_0878_b300 import tiles as dt
+    import synth
     T = N // b
     nrhs = args.nrhs
     Bd = rhs_parts(N, b, nrhs, 4, dev)
+    # per-result error against FP64, checked on the host: A's tiles, its exact
+    # infinity norm, and the right-hand sides
+    tl = A0.cpu().numpy()
+    anorm = host_anorm(tl, N, b)
+    Bh = synth.rhs(N, nrhs, seed=4)
+
+    def host_eta(X):
+        Xh = X.cpu().numpy().transpose(0, 2, 1).reshape(N, nrhs)
+        return sampled_host_eta(tl, anorm, Xh, Bh, N, b)
     R = torch.zeros(b3t.ir_work_elems(T, b, nrhs), dtype=torch.float64, device=dev)
     eta = torch.zeros(nrhs + 1, dtype=torch.float64, device=dev)
     flops = cholesky_flops(N)
@@ -488,6 +637,7 @@ def run_time_to_solution(ctx, A0, t, g64, N, b, dev, stream, args):
         res.append((ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), rc, its, e[nrhs]))
     f_ms, s_ms, rc, its, e64 = res[-1]
     out["fp64"] = {"ms": f_ms + s_ms, "factor_ms": f_ms, "solve_ms": s_ms, "eta": e64, "rc": rc,
+                   "host_sampled_eta": host_eta(X64),
                    "effective_TFLOPs": flops / ((f_ms + s_ms) / 1e3) / 1e12}
     # mixed precision + refinement
     W = torch.empty(A0.shape, dtype=torch.float32, device=dev)
@@ -522,6 +672,7 @@ def run_time_to_solution(ctx, A0, t, g64, N, b, dev, stream, args):
         diff = float((Xm - X64).abs().max() / X64.abs().max())
         out[name] = {"panel_solve": "TRTRI + TRMM_MX (inverted diagonal tile)" if inv else "TRSM_MX (substitution)",
                      "ms": f_ms + s_ms, "factor_ms": f_ms, "refine_ms": s_ms, "iterations": its, "eta": em,
+                     "host_sampled_eta": host_eta(Xm),
                      "converged": rc == 0, "max_rel_diff_vs_fp64_solution": diff,
                      "effective_TFLOPs": flops / ((f_ms + s_ms) / 1e3) / 1e12,
                      "speedup_vs_fp64": (out["fp64"]["ms"]) / (f_ms + s_ms)}
@@ -532,6 +683,8 @@ def run_time_to_solution(ctx, A0, t, g64, N, b, dev, stream, args):
     ctx.tiles_unregister(dt.tile_ptrs(Lm), T)
     for p in up:
         ctx.data_unregister(ctx.data_lookup(p))
+    out["host_check"] = ("host_sampled_eta: 32 sampled rows of b - A x formed in FP64 on the host from the "
+                         "stored A and B, with the exact ||A||_inf")
     return out
 
 
@@ -623,9 +776,13 @@ def run_empty_dags(dev, stream):
     import torch
     import paper_1304_0878_b300 as b3t
     out = {}
-    for shape, desc in EMPTY_DAGS:
+    runs = [(shape, desc, 0) for shape, desc in EMPTY_DAGS]
+    # the Cholesky shape again with one ready-queue level: FIFO order instead
+    # of upward-rank priorities (Section 5.3's hint)
+    runs.append(("cholesky", EMPTY_DAGS[2][1] + ", one ready-queue level (FIFO)", 1))
+    for shape, desc, levels in runs:
         modes, nh, nt, gen = empty_dag(shape)
-        ctx = b3t.Context(stream=stream.cuda_stream, timeout_ns=60_000_000_000)
+        ctx = b3t.Context(stream=stream.cuda_stream, timeout_ns=60_000_000_000, prio_levels=levels)
         buf = torch.zeros(nh * 16, device=dev)
         hs = [ctx.data_register(buf[i * 16:(i + 1) * 16].data_ptr(), 16, 4) for i in range(nh)]
         cls = [ctx.task_decl("empty", b3t.NOOP, m) for m in modes]
@@ -643,7 +800,8 @@ def run_empty_dags(dev, stream):
             if r >= 2:
                 ts.append(ctx.last_launch()["kernel_ns"] / 1e9)
         med = float(np.median(ts))
-        out[shape] = {"workload": desc, "tasks": ntasks, "edges": nedges, "ms": 1e3 * med,
+        out[shape + ("_fifo" if levels == 1 else "")] = {
+                      "workload": desc, "tasks": ntasks, "edges": nedges, "ms": 1e3 * med,
                       "tasks_per_s": ntasks / med, "host_submit_s": host_s,
                       "host_submit_tasks_per_s": ntasks / host_s}
         ctx.graph_destroy(g)
@@ -801,27 +959,33 @@ def run_secondary(ctx, dev, stream):
         ctx.data_unregister(h)
     del y
     out["empty_dags"] = run_empty_dags(dev, stream)
-    # small Cholesky, N = 1024, tile 128 (config 1): latency of one launch
+    # small Cholesky, N = 1024, tile 128 (config 1): latency of one launch,
+    # with upward-rank priorities and with one level (FIFO)
     N1, b1 = 1024, 128
     A1 = dt.to_tiles(torch.from_numpy(synth.spd_host(N1, seed=0, shift=1.0)).to(dev), b1)
     t1 = torch.empty_like(A1)
     p1 = dt.tile_ptrs(t1)
-    ctx.graph_capture_begin()
-    ctx.cholesky_submit(p1, N1 // b1, b1)
-    g = ctx.graph_capture_end()
-    ts = []
-    for r in range(8):
-        t1.copy_(A1)
-        ctx.graph_replay(g)
-        ctx.task_wait()
-        if r >= 3:
-            ts.append(ctx.last_launch()["kernel_ns"] / 1e9)
-    out["cholesky_small"] = {"workload": "FP64 N=1024 tile 128 (120 tasks)",
-                             "ms": 1e3 * float(np.median(ts)),
-                             "TFLOPs": cholesky_flops(N1) / float(np.median(ts)) / 1e12,
-                             "tasks_per_s": len_tasks(N1 // b1) / float(np.median(ts))}
-    ctx.graph_destroy(g)
-    ctx.tiles_unregister(p1, N1 // b1)
+    for name, levels in (("cholesky_small", 0), ("cholesky_small_fifo", 1)):
+        c1 = b3t.Context(stream=stream.cuda_stream, timeout_ns=60_000_000_000, prio_levels=levels)
+        c1.graph_capture_begin()
+        c1.cholesky_submit(p1, N1 // b1, b1)
+        ntasks = c1.dag_stats()[0]
+        g = c1.graph_capture_end()
+        ts = []
+        for r in range(13):
+            t1.copy_(A1)
+            c1.graph_replay(g)
+            c1.task_wait()
+            if r >= 3:
+                ts.append(c1.last_launch()["kernel_ns"] / 1e9)
+        med = float(np.median(ts))
+        out[name] = {"workload": "FP64 N=1024 tile 128 (120 tile tasks, %d device tasks)%s"
+                                 % (ntasks, ", one ready-queue level (FIFO)" if levels == 1 else ""),
+                     "ms": 1e3 * med, "TFLOPs": cholesky_flops(N1) / med / 1e12,
+                     "tasks_per_s": ntasks / med}
+        c1.graph_destroy(g)
+        c1.tiles_unregister(p1, N1 // b1)
+        c1.close()
     return out
 
 

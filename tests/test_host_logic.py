@@ -209,3 +209,46 @@ def test_reference_arm_line_on_the_host():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["e2e"] == {"value": line["value"], "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+
+
+def test_bench_host_checks_match_dense_definitions():
+    # the benchmark's per-result error: rows of the symmetric A gathered from
+    # packed lower tiles, the exact infinity norm, and the sampled normwise
+    # backward error, against the same quantities on the dense matrix
+    import bench
+    from oracle import ir as oir
+    N, b, nrhs = 256, 64, 3
+    A = synth.spd_host(N, seed=9, shift=1.0)
+    tl = och.to_tiles(A, b)
+    for i in range(0, N, 17):
+        assert np.array_equal(bench.host_sym_row(tl, i, N, b), A[i])
+    assert bench.host_anorm(tl, N, b) == pytest.approx(np.max(np.sum(np.abs(A), axis=1)), rel=1e-14)
+    rng = np.random.default_rng(2)
+    X = rng.standard_normal((N, nrhs))
+    Bh = A @ X + 1e-9 * rng.standard_normal((N, nrhs))
+    full = oir.backward_error(A, X, Bh)
+    got = bench.sampled_host_eta(tl, bench.host_anorm(tl, N, b), X, Bh, N, b, nsamp=N * 4)
+    assert got <= full * (1 + 1e-12) and got >= 0.5 * full
+
+
+def test_bench_summary_keeps_the_headline_figures():
+    import bench
+    line = {"value": 1.2, "roofline": {"frac": 0.98}, "e2e": {"value": 1.1},
+            "secondary": {"vector_chains": {"ms": 2.6, "hbm_frac": 0.99},
+                          "empty_dags": {"chains": {"tasks_per_s": 4.5e6}},
+                          "cholesky_small": {"ms": 5.0},
+                          "time_to_solution": {"fp64": {"ms": 10000.0},
+                                               "bf16": {"ms": 600.0, "factor_ms": 400.0, "speedup_vs_fp64": 16.0,
+                                                        "eta": 1e-14, "host_sampled_eta": 2e-14,
+                                                        "iterations": 5}},
+                          "serving": {"fp64": {"continuous": {"requests": 2000, "p50_ms": 1.0, "p99_ms": 2.0,
+                                                              "solves_per_s": 80.0, "max_queue": 5},
+                                               "plain": {"requests": 256, "solves_per_s": 40.0,
+                                                         "p99_ms": 9.0}}}},
+            "cpu_baseline": {"value": 1e-3, "library": {"cores": 16, "cholesky_n1024": {"ms": 3.0}}}}
+    sm = bench.summarise(line)
+    assert sm["cholesky_fp64_tflops"] == 1.2 and sm["vector_chains"]["hbm_frac"] == 0.99
+    assert sm["tasks_per_s"]["chains"] == 4.5e6 and sm["cholesky_small_ms"] == 5.0
+    assert sm["time_to_solution"]["bf16"]["host_sampled_eta"] == 2e-14
+    assert sm["serving"]["fp64"]["requests"] == 2000 and sm["serving"]["fp64"]["plain_requests"] == 256
+    assert sm["cpu"]["scipy_cores"] == 16 and sm["cpu"]["scipy_cholesky_n32768_tflops"] is None
