@@ -159,6 +159,7 @@ struct LaunchParams {
     int64_t timeout_ns;
     int32_t debug;
     int32_t stream_mode;
+    int32_t scal_stages;         // 16 KiB stages of the SCAL bulk-copy ring (fit the dynamic shared memory)
     // stream mode only
     const StreamCtl *sctl;
     const SubDesc *subs;
@@ -206,5 +207,6 @@ int b3t_internal_launch(const b3t::InitParams *ip, const b3t::LaunchParams *lp,
                         int nctas, size_t smem, void *stream, void *ev_start, void *ev_stop);
 int b3t_internal_occupancy(int *ctas_per_sm, size_t smem, int *num_sms, uint32_t variant);
 int b3t_internal_launch_exec(const b3t::LaunchParams *lp, int nctas, size_t smem, void *stream, void *ev_start);
-size_t b3t_internal_smem_bytes(uint32_t variant);
+size_t b3t_internal_smem_bytes(uint32_t variant, int32_t scal_stages);
+int32_t b3t_internal_scal_stages(uint32_t variant, size_t smem);
 }

@@ -119,16 +119,36 @@ __device__ __forceinline__ void scal_item(const TaskRec &t, int item) {
     }
 }
 
-// SCAL through bulk copies: 16 KiB chunks stream through a ring of 4 shared
+// SCAL through bulk copies: 16 KiB chunks stream through a ring of S shared
 // memory stages (global -> shared with an mbarrier, multiply in place,
-// shared -> global).  Thread 0 issues every copy.  Every wait is bounded;
-// the first that gives up stops the item (no further copies) after the
-// fills already issued are drained, again with a bound (drain_ns).  Returns
-// 0 or the 1-based chunk whose wait gave up; the caller then takes no
-// further item on this CTA (the ring's phases are no longer known), so
-// nothing touches the shared area again.
-constexpr int kSbStages = 4;
+// shared -> global).  Thread 0 issues every copy.  The loads of a CTA form one
+// sequence across items: load q goes into stage q % S and completes phase
+// q / S of that stage's mbarrier.  So that the ring does not drain at item
+// boundaries, the item reserves the next item of the same task at its start
+// (the same next-item counter the claims use) and, once the current item's
+// chunks are all issued, its loads continue with that item's chunks; the
+// executor runs the reserved item next.  A stage is refilled one chunk late:
+// after chunk c is stored, the stage of chunk c - 1 is refilled once its
+// store has read it (cp.async.bulk.wait_group.read 1), so the store just
+// issued never holds up a load.  An item ends when its own stores have
+// completed (wait_group 0); the next item's loads stay in flight.
+// Every wait is bounded; the first that gives up stops the item (no further
+// copies) after the loads already issued are drained, again with a bound
+// (drain_ns).  Returns 0 or the 1-based chunk whose wait gave up; the caller
+// then takes no further item on this CTA (the ring's phases are no longer
+// known), so nothing touches the shared area again.
+constexpr int kSbMaxStages = 12;
 constexpr uint32_t kSbBytes = 16384;
+
+struct ScalRing {
+    uint64_t *full;          // [S] mbarriers
+    unsigned char *stage;    // S x 16 KiB
+    uint32_t S;              // stages of this launch
+    uint32_t issued;         // loads issued so far (sequence number of the next one; thread 0's copy counts)
+    uint32_t consumed;       // chunks processed so far (sequence number of the next one)
+    int64_t nx_task;         // task and item whose first chunks are already loading
+    int32_t nx_item;
+};
 
 __device__ __forceinline__ void bulk_s2g_commit(void *dst, const void *src, uint32_t bytes) {
     asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
@@ -137,35 +157,53 @@ __device__ __forceinline__ void bulk_s2g_commit(void *dst, const void *src, uint
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
 
-__device__ __forceinline__ int scal_item_bulk(const TaskRec &t, int item, uint64_t *full, unsigned char *stage,
-                                              uint32_t &fills, int64_t limit_ns, int64_t drain_ns) {
+// bytes moved by bulk copies for item `it` of a SCAL task over n floats, and
+// the item's first element
+__device__ __forceinline__ uint32_t scal_bulk_bytes(int64_t n, int it, int64_t *start) {
+    *start = (int64_t)it * kScalChunk;
+    const int64_t end = min(n, *start + kScalChunk);
+    return (uint32_t)(((end - *start) & ~(int64_t)3) * 4);
+}
+
+__device__ __forceinline__ int scal_item_bulk(const TaskRec &t, int64_t task, int item, int next_item,
+                                              ScalRing &ring, int64_t limit_ns, int64_t drain_ns) {
     float *x = (float *)t.buf[0];
     const float f = __uint_as_float(t.scal);
-    const int64_t start = (int64_t)item * kScalChunk;
-    const int64_t end = min(t.n, start + kScalChunk);
-    const int64_t nvec = (end - start) & ~(int64_t)3;
-    const uint32_t bytes = (uint32_t)(nvec * 4);
+    int64_t start, start2 = 0;
+    const uint32_t bytes = scal_bulk_bytes(t.n, item, &start);
     const int nch = (int)((bytes + kSbBytes - 1) / kSbBytes);
+    uint32_t bytes2 = 0;
+    if (next_item >= 0) bytes2 = scal_bulk_bytes(t.n, next_item, &start2);
+    const int nch2 = (int)((bytes2 + kSbBytes - 1) / kSbBytes);
+    const int64_t end = min(t.n, start + kScalChunk);
     const int tid = threadIdx.x;
     char *gx = (char *)(x + start);
-    const uint32_t G = fills;
+    char *gx2 = (char *)(x + start2);
+    const uint32_t S = ring.S;
+    const uint32_t base = ring.consumed;            // sequence number of this item's chunk 0
+    if (!(ring.nx_task == task && ring.nx_item == item)) ring.issued = base;   // nothing of it loading yet
+    const uint32_t total = (uint32_t)(nch + nch2);  // chunks in the sequence this item may issue
+    // issue load q (sequence number) into stage q % S
+    auto issue = [&](uint32_t q) {
+        const uint32_t k = q - base;
+        const uint32_t sl = q % S;
+        const uint32_t nb = k < (uint32_t)nch ? min(kSbBytes, bytes - k * kSbBytes)
+                                              : min(kSbBytes, bytes2 - (k - nch) * kSbBytes);
+        const char *src = k < (uint32_t)nch ? gx + (size_t)k * kSbBytes : gx2 + (size_t)(k - nch) * kSbBytes;
+        mbar_expect_tx(&ring.full[sl], nb);
+        bulk_g2s(ring.stage + sl * kSbBytes, src, nb, &ring.full[sl]);
+    };
     if (tid == 0) {
         asm volatile("fence.proxy.async.global;" ::: "memory");
-        for (int c = 0; c < nch && c < kSbStages; ++c) {
-            const uint32_t s = (G + c) % kSbStages;
-            const uint32_t nb = min(kSbBytes, bytes - (uint32_t)c * kSbBytes);
-            mbar_expect_tx(&full[s], nb);
-            bulk_g2s(stage + s * kSbBytes, gx + (size_t)c * kSbBytes, nb, &full[s]);
-        }
+        while (ring.issued - base < total && ring.issued - base < S) issue(ring.issued++);
     }
-    int issued = min(nch, kSbStages);
     int failed = 0, c = 0;
     for (; c < nch; ++c) {
-        const uint32_t g = G + c, s = g % kSbStages;
+        const uint32_t q = base + c, sl = q % S;
         const uint32_t nb = min(kSbBytes, bytes - (uint32_t)c * kSbBytes);
-        const bool ok = mbar_wait(&full[s], (g / kSbStages) & 1, limit_ns);
+        const bool ok = mbar_wait(&ring.full[sl], (q / S) & 1, limit_ns);
         if (ok) {
-            float4 *v = reinterpret_cast<float4 *>(stage + s * kSbBytes);
+            float4 *v = reinterpret_cast<float4 *>(ring.stage + sl * kSbBytes);
             for (uint32_t i = tid; i < nb / 16; i += kThreads) v[i] = mul4(v[i], f);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         }
@@ -174,31 +212,31 @@ __device__ __forceinline__ int scal_item_bulk(const TaskRec &t, int item, uint64
             break;
         }
         if (tid == 0) {
-            bulk_s2g_commit(gx + (size_t)c * kSbBytes, stage + s * kSbBytes, nb);
-            if (c + kSbStages < nch) {
-                // the stage is refilled once the store has read it
-                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-                const int cn = c + kSbStages;
-                const uint32_t nb2 = min(kSbBytes, bytes - (uint32_t)cn * kSbBytes);
-                mbar_expect_tx(&full[s], nb2);
-                bulk_g2s(stage + s * kSbBytes, gx + (size_t)cn * kSbBytes, nb2, &full[s]);
+            bulk_s2g_commit(gx + (size_t)c * kSbBytes, ring.stage + sl * kSbBytes, nb);
+            // refill the stage of the previous chunk (q - 1) with load q - 1 + S
+            // once its store has read it; the store just issued may still be reading
+            const uint32_t target = q - 1 + S;
+            if (ring.issued <= target && ring.issued - base < total) {
+                asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                while (ring.issued <= target && ring.issued - base < total) issue(ring.issued++);
             }
         }
-        if (c + kSbStages < nch) ++issued;
     }
-    if (failed) {
-        for (int d = c; d < issued; ++d) {
-            const uint32_t g = G + d;
-            mbar_wait(&full[g % kSbStages], (g / kSbStages) & 1, drain_ns);
-        }
+    if (tid == 0 && failed) {
+        // loads already issued (this item's and the next one's) land before
+        // the CTA stops touching its shared memory
+        for (uint32_t q = base + c; q != ring.issued; ++q) mbar_wait(&ring.full[q % S], (q / S) & 1, drain_ns);
     }
-    fills = G + issued;
-    const int64_t tail = (end - start) - nvec;
+    ring.consumed = base + (uint32_t)nch;
+    ring.nx_task = task;
+    ring.nx_item = next_item;
+    const int64_t tail = (end - start) - (int64_t)(bytes / 4);
     if (!failed && tid < tail) {
-        float *p = x + start + nvec + tid;
+        float *p = x + start + bytes / 4 + tid;
         *p = __fmul_rn(*p, f);
     }
     if (tid == 0) {
+        // this item's stores are complete before its done count is published
         asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
         asm volatile("fence.proxy.async.global;" ::: "memory");
     }
@@ -474,12 +512,19 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
         mx.tmem = s_tmem;
     }
 
-    // SCAL bulk-copy ring (the variant without the tensor-memory path)
-    __shared__ __align__(8) uint64_t s_sbar[kSbStages];
-    uint32_t sfills = 0;
+    // SCAL bulk-copy ring (the variants without the tensor-memory path)
+    __shared__ __align__(8) uint64_t s_sbar[kSbMaxStages];
+    __shared__ int s_resv;      // next item of the same task reserved by a SCAL item, or -1
+    ScalRing ring;
+    ring.full = s_sbar;
+    ring.stage = smem;
+    ring.S = (uint32_t)min(max(p.scal_stages, 2), kSbMaxStages);
+    ring.issued = ring.consumed = 0;
+    ring.nx_task = -1;
+    ring.nx_item = -1;
     if ((kVar & kFamScal) && !kMx) {
         if (tid == 0) {
-            for (int i = 0; i < kSbStages; ++i) mbar_init(&s_sbar[i], 1);
+            for (uint32_t i = 0; i < ring.S; ++i) mbar_init(&s_sbar[i], 1);
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
         __syncthreads();
@@ -537,9 +582,14 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
             switch (rec.kind) {
             case kScalF32:
                 if constexpr (kScal && !kMx) {
+                    // reserve the task's next item so that its loads start
+                    // while this one drains (the executor runs it next)
+                    if (tid == 0) s_resv = rec.nitems > 1 ? atomicAdd(&p.next_item[t], 1) : -1;
+                    __syncthreads();
+                    const int nxt = s_resv < rec.nitems ? s_resv : -1;
                     // each wait of the ring gives up after 50 ms (a 16 KiB copy
                     // takes microseconds) and the launch reports ETIMEDOUT
-                    const int fc = scal_item_bulk(rec, it, s_sbar, smem, sfills, min(p.timeout_ns, (int64_t)50000000),
+                    const int fc = scal_item_bulk(rec, t, it, nxt, ring, min(p.timeout_ns, (int64_t)50000000),
                                                   p.timeout_ns);
                     if (fc) {
                         if (tid == 0) set_error(p.ctl, ETIMEDOUT, (int)t, fc, 20);
@@ -639,8 +689,10 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
                 } else {
                     __threadfence();
                     // the next item of the same task is asked for together
-                    // with the done count (the two round trips overlap)
-                    nj = atomicAdd(&p.next_item[t], 1);
+                    // with the done count (the two round trips overlap); a
+                    // SCAL item of the streaming variants reserved it already
+                    const bool resv = rec.kind == kScalF32 && (kVar & kFamScal) && !kMx;
+                    nj = resv ? s_resv : atomicAdd(&p.next_item[t], 1);
                     const int d = atomicAdd(&p.done_items[t], 1) + 1;
                     flag = d == rec.nitems;
                 }
@@ -701,16 +753,26 @@ __global__ void init_kernel(const InitParams ip, const LaunchParams lp) {
 
 using namespace b3t;
 
-extern "C" size_t b3t_internal_smem_bytes(uint32_t variant) {
-    // the vector variant needs only the SCAL ring, so three CTAs fit per SM
-    if (variant == kVarScal) return (size_t)kSbStages * kSbBytes + 1024;
+extern "C" size_t b3t_internal_smem_bytes(uint32_t variant, int32_t scal_stages) {
+    // the vector variant needs only the SCAL ring: scal_stages x 16 KiB (4
+    // stages let three CTAs share an SM, 12 fill one CTA per SM)
+    if (variant == kVarScal) return (size_t)min(max(scal_stages, 2), kSbMaxStages) * kSbBytes + 1024;
     return ((variant & kFamMx) ? kSmemData : kSmemDataNoMx) + 1024;
+}
+
+extern "C" int32_t b3t_internal_scal_stages(uint32_t variant, size_t smem) {
+    // stages of the SCAL ring that fit the launch's dynamic shared memory
+    if (variant & kFamMx) return 0;
+    const size_t n = (smem - 1024) / kSbBytes;
+    return (int32_t)(n > (size_t)kSbMaxStages ? kSbMaxStages : n);
 }
 
 template <uint32_t kVar>
 static int occupancy_of(int *ctas_per_sm, size_t smem) {
-    if (cudaFuncSetAttribute(exec_kernel<kVar>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(kSmemData + 1024)) != cudaSuccess ||
+    // the largest dynamic area a launch of this variant may ask for
+    const size_t most = kVar == kVarScal ? (size_t)kSbMaxStages * kSbBytes + 1024 : kSmemData + 1024;
+    if (cudaFuncSetAttribute(exec_kernel<kVar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most) !=
+            cudaSuccess ||
         cudaFuncSetAttribute(exec_kernel<kVar>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) !=
             cudaSuccess)
         return -EIO;

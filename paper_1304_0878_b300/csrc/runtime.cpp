@@ -436,7 +436,17 @@ void compute_levels(const b3t_ctx *c, const std::vector<int32_t> &off, const int
 }
 
 int grid_for(b3t_ctx *c, uint32_t variant, int *nctas, size_t *smem, int free_sms = 0, uint32_t fams = ~0u) {
-    *smem = b3t_internal_smem_bytes(variant);
+    // the vector variant's SCAL ring: 12 stages (one CTA per SM) for the
+    // successor-first order or an explicit one-CTA grid, where a block's
+    // chain stays in L2 and each CTA must keep many bytes in flight; 4
+    // stages (three CTAs per SM) for breadth-first streaming from HBM
+    int32_t stages = 4;
+    if (variant == kVarScal) {
+        int one = c->cfg.ctas_per_sm == 1 || (c->cfg.ctas_per_sm == 0 && c->cfg.prio_policy == B3T_PRIO_DEPTH);
+        if (const char *e = std::getenv("B3T_CTAS_PER_SM")) one = std::atoi(e) == 1;
+        stages = one ? 12 : 4;
+    }
+    *smem = b3t_internal_smem_bytes(variant, stages);
     int per_sm = 0, sms = 0;
     int rc = b3t_internal_occupancy(&per_sm, *smem, &sms, variant);
     if (rc) return rc;
@@ -485,6 +495,7 @@ int flush_impl(b3t_ctx *c) {
     if (rc) { clear_batch(c); return rc; }
     int nctas; size_t smem;
     if ((rc = grid_for(c, lp.variant, &nctas, &smem, 0, lp.fams))) { clear_batch(c); return rc; }
+    lp.scal_stages = b3t_internal_scal_stages(lp.variant, smem);
     rc = b3t_internal_launch(&ip, &lp, nctas, smem, c->stream, c->ev0, c->ev1);
     c->last_ntasks = (int64_t)c->tasks.size();
     c->last_nitems = nitems;
@@ -935,6 +946,7 @@ int b3t_graph_capture_end(b3t_ctx *c, b3t_graph *out) {
     if (!rc) rc = cuda_err(cudaStreamSynchronize(c->stream));
     int nctas = 0; size_t smem = 0;
     if (!rc) rc = grid_for(c, lp.variant, &nctas, &smem, 0, lp.fams);
+    lp.scal_stages = b3t_internal_scal_stages(lp.variant, smem);
     if (rc) { clear_batch(c); g.arena.release(); return rc; }
     cudaStream_t cs;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
@@ -1120,6 +1132,7 @@ int b3t_stream_open(b3t_ctx *c, int64_t max_tasks, int64_t max_edges, int32_t ma
     const int free_sms = c->cfg.stream_free_sms > 0 ? c->cfg.stream_free_sms : kStreamFreeSms;
     int nctas; size_t smem;
     if ((rc = grid_for(c, svar, &nctas, &smem, free_sms))) { stream_free(c); return rc; }
+    lp.scal_stages = b3t_internal_scal_stages(lp.variant, smem);
     if ((rc = b3t_internal_launch_exec(&lp, nctas, smem, c->stream, c->ev0))) { stream_free(c); return rc; }
     S.open = true;
     c->last_nctas = nctas;
@@ -1327,7 +1340,18 @@ static int submit_panel_potrf(b3t_ctx *c, const std::vector<b3t_handle> &P, int3
     return 0;
 }
 
-static bool use_panels(int32_t b) { return b >= 2 * kPanelWidth && b % kPanelWidth == 0; }
+// Panel width of the diagonal-tile DAG for tile size b, 0 for one POTRF task
+// per diagonal tile.  B3T_PANEL_WIDTH (64 or 128; 0 for none) overrides the
+// default, for measurements.
+static int32_t panel_width(int32_t b) {
+    int32_t pw = (b >= 2 * kPanelWidth && b % kPanelWidth == 0) ? kPanelWidth : 0;
+    if (const char *e = std::getenv("B3T_PANEL_WIDTH")) {
+        const int v = std::atoi(e);
+        if (v == 0) pw = 0;
+        else if ((v == 64 || v == 128) && b >= 2 * v && b % v == 0) pw = v;
+    }
+    return pw;
+}
 
 int b3t_cholesky_submit(b3t_ctx *c, double *const *tiles, int32_t T, int32_t b, int32_t col0) {
     if (!c || !tiles || T <= 0 || b <= 0 || b % kGemmBlk) return -EINVAL;
@@ -1339,15 +1363,16 @@ int b3t_cholesky_submit(b3t_ctx *c, double *const *tiles, int32_t T, int32_t b, 
     if ((rc = kind_codelet(c, kPotrf, &cp)) || (rc = kind_codelet(c, kTrsm, &ct)) ||
         (rc = kind_codelet(c, kSyrk, &cs)) || (rc = kind_codelet(c, kGemm, &cg)))
         return rc;
-    const bool panels = use_panels(b);
+    const int32_t pw = panel_width(b);
+    const bool panels = pw > 0;
     std::vector<std::vector<b3t_handle>> dparts(panels ? T : 0);
     for (int32_t k = 0; panels && k < T; ++k)
-        if ((rc = panel_parts(c, h[tidx(k, k, T)], b, kPanelWidth, dparts[k]))) return rc;
+        if ((rc = panel_parts(c, h[tidx(k, k, T)], b, pw, dparts[k]))) return rc;
     for (int32_t k = 0; k < T; ++k) {
         const int32_t c0 = col0 + k * b;
         const b3t_handle hp[1] = {h[tidx(k, k, T)]};
         if (panels) {
-            if ((rc = submit_panel_potrf(c, dparts[k], b, kPanelWidth, c0))) return rc;
+            if ((rc = submit_panel_potrf(c, dparts[k], b, pw, c0))) return rc;
         } else if ((rc = submit_impl(c, cp, hp, nullptr, 1, &c0, 4))) {
             return rc;
         }
@@ -1389,16 +1414,17 @@ int b3t_cholesky_mx_submit(b3t_ctx *c, float *const *W, double *const *L, void *
         (rc = kind_codelet(c, kQuant, &cq)) || (rc = kind_codelet(c, kSyrkMx, &cs)) ||
         (rc = kind_codelet(c, kGemmMx, &cg)) || (rc = kind_codelet(c, kCvt, &cc)))
         return rc;
-    const bool panels = use_panels(b);
+    const int32_t pw = panel_width(b);
+    const bool panels = pw > 0;
     std::vector<std::vector<b3t_handle>> dparts(panels ? T : 0);
     for (int32_t k = 0; panels && k < T; ++k)
-        if ((rc = panel_parts(c, hl[tidx(k, k, T)], b, kPanelWidth, dparts[k]))) return rc;
+        if ((rc = panel_parts(c, hl[tidx(k, k, T)], b, pw, dparts[k]))) return rc;
     for (int32_t k = 0; k < T; ++k) {
         const int32_t c0 = col0 + k * b;
         const b3t_handle hp[2] = {hw[tidx(k, k, T)], hl[tidx(k, k, T)]};
         if (panels) {
             if ((rc = submit_impl(c, cc, hp, nullptr, 2, nullptr, 0))) return rc;
-            if ((rc = submit_panel_potrf(c, dparts[k], b, kPanelWidth, c0))) return rc;
+            if ((rc = submit_panel_potrf(c, dparts[k], b, pw, c0))) return rc;
         } else if ((rc = submit_impl(c, cp, hp, nullptr, 2, &c0, 4))) {
             return rc;
         }
@@ -1448,16 +1474,17 @@ int b3t_cholesky_mx_inv_submit(b3t_ctx *c, float *const *W, double *const *L, vo
         (rc = kind_codelet(c, kSyrkMx, &cs)) || (rc = kind_codelet(c, kGemmMx, &cg)) ||
         (rc = kind_codelet(c, kCvt, &cc)))
         return rc;
-    const bool panels = use_panels(b);
+    const int32_t pw = panel_width(b);
+    const bool panels = pw > 0;
     std::vector<std::vector<b3t_handle>> dparts(panels ? T : 0);
     for (int32_t k = 0; panels && k < T; ++k)
-        if ((rc = panel_parts(c, hl[tidx(k, k, T)], b, kPanelWidth, dparts[k]))) return rc;
+        if ((rc = panel_parts(c, hl[tidx(k, k, T)], b, pw, dparts[k]))) return rc;
     for (int32_t k = 0; k < T; ++k) {
         const int32_t c0 = col0 + k * b;
         const b3t_handle hp[2] = {hw[tidx(k, k, T)], hl[tidx(k, k, T)]};
         if (panels) {
             if ((rc = submit_impl(c, cc, hp, nullptr, 2, nullptr, 0))) return rc;
-            if ((rc = submit_panel_potrf(c, dparts[k], b, kPanelWidth, c0))) return rc;
+            if ((rc = submit_panel_potrf(c, dparts[k], b, pw, c0))) return rc;
         } else if ((rc = submit_impl(c, cp, hp, nullptr, 2, &c0, 4))) {
             return rc;
         }

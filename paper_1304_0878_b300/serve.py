@@ -159,6 +159,9 @@ def prepare(reqs, device="cuda", pool=None):
             nbytes += A_h.numel() * 8 + rhs_h.numel() * 8
             r.inputs = None
         r.host = pool[r.src]
+        if r.host[0].shape[0] != r.T * (r.T + 1) // 2 or r.host[0].shape[1] != r.b or r.host[1].shape != (r.T, r.nrhs, r.b):
+            raise ValueError("client input of source %d does not fit request %d (pool built for another stream)"
+                             % (r.src, r.rid))
     torch.cuda.synchronize(device)
     return time.perf_counter() - t0, nbytes
 
@@ -302,6 +305,24 @@ def warm_up(prec, device, gen_stream, side, host, reserve_bytes):
     torch.cuda.synchronize(device)
 
 
+def stream_capacity(reqs, prec, iters):
+    """Upper bounds on the tasks and edges the stream executor's fixed
+    arenas must hold for `reqs` (stream mode does not reuse the slots of
+    retired batches): per request the factorisation (POTRF / TRSM (+ QUANT)
+    / SYRK / GEMM tasks, the diagonal-panel tasks) and `iters` solve or
+    refinement steps (each about T^2 + 4T + 4 vector tasks), with three edges
+    per task and a quarter of slack."""
+    tasks = 0
+    for r in reqs:
+        T = r.T
+        pan = (r.b // 64) ** 2 if r.b >= 256 else 1
+        fac = T * pan + T * (T - 1) + T * (T - 1) // 2 + T * (T - 1) * (T - 2) // 6 + 2 * T
+        step = T * T + 4 * T + 4
+        tasks += fac + iters * step
+    tasks = int(tasks * 1.25) + 4096
+    return tasks, 3 * tasks
+
+
 def _result_slots(reqs, k):
     """k pinned host buffers, each large enough for any request's X."""
     n = max(r.Np * r.nrhs for r in reqs)
@@ -309,12 +330,18 @@ def _result_slots(reqs, k):
 
 
 def serve(ctx, reqs, prec="fp64", budget_bytes=48 << 30, max_inflight=64, tol=1e-12, max_iter=30,
-          device="cuda", time_limit=600.0, max_tasks=1 << 22, max_edges=1 << 24, keep_x=False):
+          device="cuda", time_limit=600.0, max_tasks=None, max_edges=None, keep_x=False):
     """Continuous batching with the resident executor.  Arrival times in
     `reqs` are seconds from the start of the run; the requests' client inputs
     must be in host memory (prepare).  `ctx` must be bound to a stream of its
     own: the resident kernel occupies it for the whole run (uploads,
-    admission copies and read-backs use other streams)."""
+    admission copies and read-backs use other streams).  The stream's
+    arenas are sized by stream_capacity (12 refinement steps per mixed
+    request) unless max_tasks / max_edges are given."""
+    if max_tasks is None or max_edges is None:
+        mt, me = stream_capacity(reqs, prec, 1 if prec == "fp64" else 12)
+        max_tasks = max_tasks or mt
+        max_edges = max_edges or me
     gen_stream = torch.cuda.Stream(device=device)
     side = torch.cuda.Stream(device=device)
     host = torch.empty(64, dtype=torch.float64, pin_memory=True)

@@ -119,15 +119,19 @@ def random_accesses(ntasks, nhandles, maxbuf, seed):
     return out
 
 
-def serve_requests(n, rate=2000.0, seed=5, nmin=256, nmax=8192, rmin=1, rmax=32):
-    """n Cholesky-solve requests: arrival times (s) of a Poisson process of
-    the given rate, N log-uniform on [nmin, nmax], nrhs uniform on
-    {rmin..rmax}, and an independent seed per request."""
+def serve_requests(n, rate=2000.0, seed=5, nmin=256, nmax=8192, rmin=1, rmax=32, total=100000):
+    """The first n of a stream of `total` Cholesky-solve requests: arrival
+    times (s) of a Poisson process of the given rate, N log-uniform on
+    [nmin, nmax], nrhs uniform on {rmin..rmax}, and an independent seed per
+    request.  The whole stream is drawn (gaps, then sizes, then right-hand
+    side counts, each for `total` requests) and its prefix returned, so the
+    first k requests are the same whatever n >= k is asked for."""
+    m = max(n, total)
     root = np.random.SeedSequence(seed)
     rng = np.random.default_rng(root)
-    gaps = rng.exponential(1.0 / rate, n)
+    gaps = rng.exponential(1.0 / rate, m)[:n]
     arrival = np.cumsum(gaps)
-    N = np.floor(np.exp(rng.uniform(math.log(nmin), math.log(nmax), n))).astype(np.int64)
-    nrhs = rng.integers(rmin, rmax + 1, n)
+    N = np.floor(np.exp(rng.uniform(math.log(nmin), math.log(nmax), m))).astype(np.int64)[:n]
+    nrhs = rng.integers(rmin, rmax + 1, m)[:n]
     seeds = [int(s.generate_state(1)[0]) for s in root.spawn(n)]
     return arrival, N, nrhs, seeds

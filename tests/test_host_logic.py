@@ -111,6 +111,14 @@ def test_serving_requests():
     assert all(r.b == 256 for r in f)
 
 
+def test_serving_stream_prefix_is_stable():
+    # the first k requests of the stream do not depend on how many are drawn
+    a = synth.serve_requests(2000)
+    b = synth.serve_requests(256)
+    for x, y in zip(a, b):
+        assert np.array_equal(np.asarray(x)[:256], np.asarray(y))
+
+
 def test_serving_requests_cycle_distinct_sources():
     # n requests over P input sources: request i keeps the i-th arrival of the
     # stream and takes size, right-hand sides and seed of request i mod P
