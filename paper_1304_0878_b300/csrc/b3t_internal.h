@@ -14,6 +14,11 @@ namespace b3t {
 
 constexpr int kMaxBuffers = 4;
 constexpr int kMaxLevels = 8;
+// Each priority level's ready queue is split into nsub rings (task id mod
+// nsub), each with its own head and tail, so that claims contend on several
+// heads instead of one; a claiming warp reads every ring's head and tail in
+// one round trip (one lane per ring), so levels x nsub <= 32.
+constexpr int kMaxRings = 32;
 constexpr int kThreads = 256;            // threads per persistent CTA
 
 // Work-item decomposition of each kind (the host computes nitems, the
@@ -87,12 +92,12 @@ struct alignas(128) Ctl {
     unsigned long long retired;  // tasks retired in this launch (every retirement adds 1)
     unsigned long long subs_consumed;   // stream mode: submissions taken in
     int32_t pad1[28];
-    // per-level ring heads / tails, each on its own 128-byte line
+    // per-ring heads / tails (ring = level * nsub + sub), each on its own 128-byte line
     struct alignas(128) Level {
         unsigned long long head;
         unsigned long long tail;
         int32_t pad[28];
-    } lvl[kMaxLevels];
+    } lvl[kMaxRings];
 };
 
 // Stream mode (a resident kernel fed with new task graphs while it runs).
@@ -147,12 +152,13 @@ struct LaunchParams {
     int32_t *counters;           // remaining predecessors per task
     int32_t *done_items;         // finished items per task
     int32_t *next_item;          // next item to hand out, per task
-    unsigned long long *slots;   // ready rings (one slot per task), levels back to back
+    unsigned long long *slots;   // ready rings (one slot per task), rings back to back
     Ctl *ctl;
-    unsigned long long ring_off[kMaxLevels];   // first slot of each level
-    unsigned long long ring_cap[kMaxLevels];
+    unsigned long long ring_off[kMaxRings];   // first slot of each ring (ring = level * nsub + sub)
+    unsigned long long ring_cap[kMaxRings];
     int64_t ntasks;
     int32_t nlevels;
+    int32_t nsub;                // rings per level (task t of level l goes to ring l * nsub + t % nsub)
     int32_t has_mx;              // launch holds tcgen05 work: allocate TMEM
     uint32_t variant;            // kernel variant (family set) the launch runs
     uint32_t fams;               // families of the launch's kinds (0: empty tasks only)
@@ -184,12 +190,13 @@ struct InitParams {
     int32_t *next_item;
     unsigned long long *slots;
     unsigned long long nslots;
-    const unsigned long long *roots;      // root task slots, per level back to back
-    unsigned long long root_off[kMaxLevels];
-    unsigned long long root_cnt[kMaxLevels];
+    const unsigned long long *roots;      // root task slots, per ring back to back
+    unsigned long long root_off[kMaxRings];
+    unsigned long long root_cnt[kMaxRings];
     Ctl *ctl;
     int64_t ntasks;
     int32_t nlevels;
+    int32_t nrings;              // nlevels * nsub
 };
 
 constexpr unsigned long long kEmpty = ~0ull;

@@ -283,7 +283,7 @@ __device__ __forceinline__ void push_roots(const LaunchParams &p, const SubDesc 
     for (uint32_t k = lane; k < sd.nroots; k += 32) {
         const unsigned long long v = p.sroots[sd.root_off + k];
         const int64_t t = (int64_t)(v >> 32);
-        const int lv = p.level[t];
+        const int lv = p.level[t] * p.nsub + (int)(t % p.nsub);
         const unsigned long long pos = atomicAdd(&p.ctl->lvl[lv].tail, 1ull);
         if (p.debug && pos >= p.ring_cap[lv]) set_error(p.ctl, EPROTO, (int)t, -1, 7);
         else st_rel(p.slots + p.ring_off[lv] + pos, v);
@@ -320,19 +320,26 @@ __device__ __forceinline__ unsigned long long claim(const LaunchParams &p, uint6
             if (err) return kEmpty;
         }
         unsigned long long h = 0, tl = 0;
-        const bool mine = lane < p.nlevels;
+        const int nrings = p.nlevels * p.nsub;
+        const bool mine = lane < nrings;
         if (mine) {
             h = ld_rlx(&ctl->lvl[lane].head);
             tl = ld_rlx(&ctl->lvl[lane].tail);
-        } else if (lane == 31 && !lost && (check || spin > 0)) {
-            err = ld_rlx_i32(&ctl->error);
         }
+        if (lane == 31 && !lost && (check || spin > 0)) err = ld_rlx_i32(&ctl->error);
         err = __shfl_sync(0xffffffffu, err, 31);
         if (err) return kEmpty;
         lost = false;
         const unsigned mask = __ballot_sync(0xffffffffu, mine && h < tl);
         if (mask) {
-            const int lv = 31 - __clz(mask);
+            // the highest non-empty level; among its rings the CTA's own
+            // (blockIdx mod nsub) first, then the next ones in turn
+            const int top = (31 - __clz(mask)) / p.nsub;
+            const unsigned long long all = (1ull << p.nsub) - 1ull;     // nsub <= 32
+            const unsigned long long sub = ((unsigned long long)mask >> (top * p.nsub)) & all;
+            const int home = (int)(blockIdx.x % (unsigned)p.nsub);
+            const unsigned long long rot = ((sub >> home) | (sub << (p.nsub - home))) & all;
+            const int lv = top * p.nsub + (home + __ffsll((long long)rot) - 1) % p.nsub;
             const unsigned long long hv = __shfl_sync(0xffffffffu, h, lv);
             const unsigned long long tv = __shfl_sync(0xffffffffu, tl, lv);
             unsigned long long item = kEmpty;
@@ -363,7 +370,7 @@ __device__ __forceinline__ unsigned long long claim(const LaunchParams &p, uint6
                             // with many ready, the next filled single-item slots too
                             int k = 1;
                             unsigned long long more[kBatch - 1];
-                            if (tv - hv > 2ull * gridDim.x) {
+                            if (tv - hv > 2ull * gridDim.x / (unsigned)p.nsub) {
                                 while (k < kBatch && hv + k < tv) {
                                     const unsigned long long w = ld_acq(slot + k);
                                     if (w == kEmpty || (int)(w & 0xffffffffu) != 1) break;
@@ -450,7 +457,7 @@ __device__ __forceinline__ void retire(const LaunchParams &p, int64_t t, const T
             const int s = p.succ[rec.succ_off + k];
             const int prev = atomicSub(&p.counters[s], 1);
             if (prev == 1) {
-                const int lv = p.level[s];
+                const int lv = p.level[s] * p.nsub + s % p.nsub;
                 const unsigned long long pos = atomicAdd(&p.ctl->lvl[lv].tail, 1ull);
                 if (p.debug && pos >= p.ring_cap[lv]) set_error(p.ctl, EPROTO, s, -1, 4);
                 else st_rel(p.slots + p.ring_off[lv] + pos, pack_slot(s, p.tasks[s].nitems));
@@ -736,14 +743,14 @@ __global__ void init_kernel(const InitParams ip, const LaunchParams lp) {
     }
     for (int64_t i = gid; i < (int64_t)ip.nslots; i += stride) {
         int l = 0;
-        while (l + 1 < ip.nlevels && (unsigned long long)i >= lp.ring_off[l + 1]) ++l;
+        while (l + 1 < ip.nrings && (unsigned long long)i >= lp.ring_off[l + 1]) ++l;
         const unsigned long long k = (unsigned long long)i - lp.ring_off[l];
         ip.slots[i] = k < ip.root_cnt[l] ? ip.roots[ip.root_off[l] + k] : kEmpty;
     }
     if (gid == 0) {
-        for (int l = 0; l < kMaxLevels; ++l) {
+        for (int l = 0; l < kMaxRings; ++l) {
             ip.ctl->lvl[l].head = 0;
-            ip.ctl->lvl[l].tail = l < ip.nlevels ? ip.root_cnt[l] : 0;
+            ip.ctl->lvl[l].tail = l < ip.nrings ? ip.root_cnt[l] : 0;
         }
         ip.ctl->retired = 0;
     }

@@ -295,6 +295,19 @@ void derive(b3t_ctx *c, int32_t t, const int32_t *leaves, const uint8_t *modes, 
 void compute_levels(const b3t_ctx *c, const std::vector<int32_t> &off, const int32_t *succ,
                     std::vector<float> &rank, std::vector<int32_t> &level);
 
+// Rings per priority level of a launch: as many as the 32 lanes of the
+// claiming warp allow (4 with 8 levels, 32 with one); B3T_SUB_RINGS
+// overrides it (1 .. that number), for measurements.
+int sub_rings(const b3t_ctx *c) {
+    const int most = kMaxRings / std::max(1, c->cfg.prio_levels);
+    int n = most;
+    if (const char *e = std::getenv("B3T_SUB_RINGS")) {
+        const int v = std::atoi(e);
+        if (v >= 1 && v <= most) n = v;
+    }
+    return n;
+}
+
 // Build the task table, CSR graph, ready rings and root lists of the pending
 // batch into arena `a` (uploaded through the pinned staging buffer on the
 // context's stream) and fill the launch parameters.
@@ -317,7 +330,11 @@ int build_launch(b3t_ctx *c, Arena &a, InitParams &ip, LaunchParams &lp, int64_t
     std::vector<float> rank;
     std::vector<int32_t> level;
     compute_levels(c, off, succ_lv.data(), rank, level);
-    unsigned long long cap[kMaxLevels] = {0}, rootcnt[kMaxLevels] = {0};
+    // ring of task t: level * nsub + t % nsub (the device pushes successors
+    // by the same rule); capacities and roots are counted per ring
+    const int nsub = sub_rings(c);
+    const int NR = L * nsub;
+    unsigned long long cap[kMaxRings] = {0}, rootcnt[kMaxRings] = {0};
     int64_t nitems = 0;
     has_mx = false;
     uint32_t fams = 0;
@@ -327,24 +344,26 @@ int build_launch(b3t_ctx *c, Arena &a, InitParams &ip, LaunchParams &lp, int64_t
         r.nsucc = off[t + 1] - off[t];
         const int lv = level[t];
         succ_lv[ne_pad + t] = lv;
-        cap[lv] += 1;
-        if (indeg[t] == 0) rootcnt[lv] += 1;
+        const int ring = lv * nsub + (int)(t % nsub);
+        cap[ring] += 1;
+        if (indeg[t] == 0) rootcnt[ring] += 1;
         nitems += r.nitems;
         if (is_mx(r.kind)) has_mx = true;
         fams |= family_of(r.kind);
     }
-    unsigned long long ringoff[kMaxLevels] = {0}, rootoff[kMaxLevels] = {0};
+    unsigned long long ringoff[kMaxRings] = {0}, rootoff[kMaxRings] = {0};
     unsigned long long nslots = 0, nroots = 0;
-    for (int l = 0; l < L; ++l) {
+    for (int l = 0; l < NR; ++l) {
         ringoff[l] = nslots; nslots += cap[l];
         rootoff[l] = nroots; nroots += rootcnt[l];
     }
     std::vector<unsigned long long> roots(std::max<unsigned long long>(nroots, 1), kEmpty);
     {
-        unsigned long long fill[kMaxLevels];
-        for (int l = 0; l < L; ++l) fill[l] = rootoff[l];
+        unsigned long long fill[kMaxRings];
+        for (int l = 0; l < NR; ++l) fill[l] = rootoff[l];
         for (int64_t t = 0; t < nt; ++t)
-            if (indeg[t] == 0) roots[fill[succ_lv[ne_pad + t]]++] = pack_slot(t, c->tasks[t].rec.nitems);
+            if (indeg[t] == 0) roots[fill[succ_lv[ne_pad + t] * nsub + (int)(t % nsub)]++] =
+                                   pack_slot(t, c->tasks[t].rec.nitems);
     }
     int rc;
     if ((rc = grow(a.tasks, a.cap_tasks, nt))) return rc;
@@ -389,18 +408,18 @@ int build_launch(b3t_ctx *c, Arena &a, InitParams &ip, LaunchParams &lp, int64_t
     ip = InitParams{};
     ip.indeg = a.indeg; ip.counters = a.counters; ip.done_items = a.done; ip.next_item = a.next;
     ip.slots = a.slots; ip.nslots = nslots; ip.roots = a.roots; ip.ctl = a.ctl;
-    ip.ntasks = nt; ip.nlevels = L;
+    ip.ntasks = nt; ip.nlevels = L; ip.nrings = NR;
     lp = LaunchParams{};
     lp.tasks = a.tasks; lp.succ = a.succ; lp.level = a.succ + ne_pad;
     lp.counters = a.counters; lp.done_items = a.done; lp.next_item = a.next;
-    lp.slots = a.slots; lp.ctl = a.ctl; lp.ntasks = nt; lp.nlevels = L;
+    lp.slots = a.slots; lp.ctl = a.ctl; lp.ntasks = nt; lp.nlevels = L; lp.nsub = nsub;
     lp.has_mx = has_mx ? 1 : 0;
     lp.variant = variant_of(fams);
     lp.fams = fams;
     lp.timeout_ns = c->cfg.timeout_ns;
     lp.debug = c->cfg.debug_checks;
     if (c->trace_on) { lp.trace = c->trace; lp.trace_n = c->trace_n; lp.trace_cap = c->trace_cap; }
-    for (int l = 0; l < L; ++l) {
+    for (int l = 0; l < NR; ++l) {
         ip.root_off[l] = rootoff[l]; ip.root_cnt[l] = rootcnt[l];
         lp.ring_off[l] = ringoff[l]; lp.ring_cap[l] = cap[l];
     }
@@ -1116,7 +1135,9 @@ int b3t_stream_open(b3t_ctx *c, int64_t max_tasks, int64_t max_edges, int32_t ma
     LaunchParams lp{};
     lp.tasks = S.tasks; lp.succ = S.succ; lp.level = S.level; lp.counters = S.counters;
     lp.done_items = S.done; lp.next_item = S.next; lp.slots = S.slots; lp.ctl = S.ctl;
+    // one ring per level: a stream's rings are sized before its tasks are known
     for (int l = 0; l < L; ++l) { lp.ring_off[l] = (unsigned long long)l * nt; lp.ring_cap[l] = nt; }
+    lp.nsub = 1;
     const uint32_t svar = c->cfg.stream_no_mx ? kVarNoMx : kVarAll;
     lp.ntasks = max_tasks; lp.nlevels = L; lp.has_mx = c->cfg.stream_no_mx ? 0 : 1;
     lp.variant = svar; lp.fams = svar;
