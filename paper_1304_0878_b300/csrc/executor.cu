@@ -493,6 +493,7 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
     // align the dynamic area to 1024 bytes (128-byte swizzled operands)
     unsigned char *smem = (unsigned char *)(((uintptr_t)dsmem + 1023) & ~(uintptr_t)1023);
     __shared__ unsigned long long s_item;
+    __shared__ int s_fresh;
     __shared__ int s_info, s_fail, s_e;
     __shared__ __align__(8) uint64_t s_bars[2 * kMxStages + 1];
     __shared__ uint32_t s_tmem;
@@ -564,12 +565,16 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
             const int64_t t = (int64_t)(it >> 32);
             if (!same && it != kEmpty && (!p.debug || t < p.ntasks) && lane < 4)
                 reinterpret_cast<uint4 *>(&s_rec)[lane] = __ldcg(reinterpret_cast<const uint4 *>(p.tasks + t) + lane);
-            if (lane == 0) s_item = it;
+            if (lane == 0) { s_item = it; s_fresh = !same; }
         }
         __syncthreads();
         const unsigned long long item = s_item;
         if (item == kEmpty) break;
-        __threadfence();   // acquire side for every thread of the CTA
+        // acquire side for every thread of the CTA, when the item starts a
+        // task this CTA has not run yet: the next item of the same task reads
+        // the inputs the first one acquired (the release side is warp 0's
+        // fence after the CTA barrier that ends every item)
+        if (s_fresh) __threadfence();
         const int64_t t = (int64_t)(item >> 32);
         const int it = (int)(item & 0xffffffffu);
         const uint64_t t_item = (p.trace && tid == 0) ? gtimer() : 0;

@@ -133,6 +133,20 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
 __device__ __forceinline__ void tmem_alloc(uint32_t *dst_smem, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
                  "r"(ncols)
@@ -264,6 +278,24 @@ __device__ __forceinline__ void quant_item(const TaskRec &t, int item, double *r
     }
 }
 
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float *v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+        "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+        "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+        "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+        "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])),
+        "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])),
+        "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])),
+        "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])),
+        "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])),
+        "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+        : "memory");
+}
+
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float *v) {
     asm volatile(
         "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
@@ -340,11 +372,13 @@ __device__ __forceinline__ int mx_update_item(const TaskRec &t, int item, bool s
     float *Wg = W + (size_t)(bi * kMxBlk + rr) + (size_t)(bj * kMxBlk + 64 * h) * b;
     const uint32_t tl = st.tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(64 * h);
 #pragma unroll 1
-    for (int i = 0; i < 4; ++i) {
-        float v[16];
+    for (int i = 0; i < 2; ++i) {
+        float v[32];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) v[c] = -ldexpf(Wg[(size_t)(16 * i + c) * b], -es_sum);
-        tmem_st16(tl + 16 * i, v);
+        for (int c = 0; c < 32; ++c) v[c] = Wg[(size_t)(32 * i + c) * b];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) v[c] = -ldexpf(v[c], -es_sum);
+        tmem_st32(tl + 32 * i, v);
     }
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     tc_fence_before();
@@ -402,13 +436,13 @@ __device__ __forceinline__ int mx_update_item(const TaskRec &t, int item, bool s
     // part of a diagonal block is left as it was)
     const int gr = bi * kMxBlk + rr;
 #pragma unroll 1
-    for (int i = 0; i < 4; ++i) {
-        float v[16];
-        tmem_ld16(tl + 16 * i, v);
+    for (int i = 0; i < 2; ++i) {
+        float v[32];
+        tmem_ld32(tl + 32 * i, v);
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-            const int gc = bj * kMxBlk + 64 * h + 16 * i + c;
-            if (!syrk || gr >= gc) Wg[(size_t)(16 * i + c) * b] = -ldexpf(v[c], es_sum);
+        for (int c = 0; c < 32; ++c) {
+            const int gc = bj * kMxBlk + 64 * h + 32 * i + c;
+            if (!syrk || gr >= gc) Wg[(size_t)(32 * i + c) * b] = -ldexpf(v[c], es_sum);
         }
     }
     tc_fence_before();
