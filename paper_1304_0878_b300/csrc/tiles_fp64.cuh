@@ -312,6 +312,55 @@ __device__ __noinline__ void trmm_mx_item(const TaskRec &t, int item, double *sm
             L[(size_t)(bi * 64 + tx + 16 * i) + (size_t)(bj * 64 + ty + 16 * j) * b] = acc[i][j];
 }
 
+// Panel update of potrf_block for RB rows from rr0 (all valid):
+// A(rr0.., jb..jb+32) -= A(rr0.., 0..jb) A(jb..jb+32, 0..jb)^T on the lower
+// part.  RB = 64: thread (tr, tc) owns row tr and 8 columns; RB = 32: row tr
+// and 4 columns, so that a 32-row tail keeps all eight warps (and the FP64
+// units of all four SM sub-partitions) busy instead of half of them on rows
+// past the block.  The per-element FMA order (k ascending) is the same.
+template <int RB>
+__device__ __forceinline__ void potrf_panel_rows(double *A, int ld, int rr0, int jb, double *Lr, double *Lc) {
+    constexpr int PW = 32;
+    constexpr int NG = kThreads / RB;          // column groups
+    constexpr int NJ = PW / NG;                // columns per thread
+    const int tid = threadIdx.x;
+    const int tr = tid % RB, tc = tid / RB;
+    double acc[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) acc[j] = 0.0;
+    for (int k0 = 0; k0 < jb; k0 += kKc) {
+#pragma unroll
+        for (int q = 0; q < (RB * kKc) / kThreads; ++q) {
+            const int e = tid + q * kThreads;
+            const int r = e % RB, p = e / RB;
+            Lr[p * RB + r] = A[(size_t)(rr0 + r) + (size_t)(k0 + p) * ld];
+        }
+#pragma unroll
+        for (int q = 0; q < (PW * kKc) / kThreads; ++q) {
+            const int e = tid + q * kThreads;
+            const int c = e & 31, p = e >> 5;
+            Lc[p * 32 + c] = A[(size_t)(jb + c) + (size_t)(k0 + p) * ld];
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int p = 0; p < kKc; ++p) {
+            const double x = Lr[p * RB + tr];
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) acc[j] = fma(x, Lc[p * 32 + tc + NG * j], acc[j]);
+        }
+        __syncthreads();
+    }
+    const int gr = rr0 + tr;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const int gc = jb + tc + NG * j;
+        if (gr >= gc) {
+            double *p = A + (size_t)gr + (size_t)gc * ld;
+            *p = *p - acc[j];
+        }
+    }
+}
+
 // Cholesky of one n x n block in place (lower, leading dimension ld), one
 // CTA, left-looking over panels of 32 columns.  Returns 0 or the 1-based
 // column (within the block) of the first pivot that is <= 0 or NaN.
@@ -325,45 +374,12 @@ __device__ __forceinline__ int potrf_block(double *A, int n, int ld, double *sme
     if (tid == 0) *s_info = 0;
     __syncthreads();
     for (int jb = 0; jb < b; jb += PW) {
-        // (1) panel update: P = A(jb:, jb:jb+32) - A(jb:, :jb) A(jb:jb+32, :jb)^T
+        // (1) panel update: P = A(jb:, jb:jb+32) - A(jb:, :jb) A(jb:jb+32, :jb)^T,
+        // in blocks of 64 rows and a 32-row tail (b and jb are multiples of 32)
         if (jb > 0) {
-            const int tr = tid & 63, tc = tid >> 6;    // 64 rows x (4 x 8) columns
             for (int rr0 = jb; rr0 < b; rr0 += 64) {
-                double acc[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) acc[j] = 0.0;
-                for (int k0 = 0; k0 < jb; k0 += kKc) {
-#pragma unroll
-                    for (int q = 0; q < (64 * kKc) / kThreads; ++q) {
-                        const int e = tid + q * kThreads;
-                        const int r = e & 63, p = e >> 6;
-                        const int gr = rr0 + r;
-                        Lr[p * 64 + r] = gr < b ? A[(size_t)gr + (size_t)(k0 + p) * ld] : 0.0;
-                    }
-#pragma unroll
-                    for (int q = 0; q < (PW * kKc) / kThreads; ++q) {
-                        const int e = tid + q * kThreads;
-                        const int c = e & 31, p = e >> 5;
-                        Lc[p * 32 + c] = A[(size_t)(jb + c) + (size_t)(k0 + p) * ld];
-                    }
-                    __syncthreads();
-#pragma unroll 8
-                    for (int p = 0; p < kKc; ++p) {
-                        const double x = Lr[p * 64 + tr];
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) acc[j] = fma(x, Lc[p * 32 + tc + 4 * j], acc[j]);
-                    }
-                    __syncthreads();
-                }
-                const int gr = rr0 + tr;
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int gc = jb + tc + 4 * j;
-                    if (gr < b && gr >= gc) {
-                        double *p = A + (size_t)gr + (size_t)gc * ld;
-                        *p = *p - acc[j];
-                    }
-                }
+                if (b - rr0 >= 64) potrf_panel_rows<64>(A, ld, rr0, jb, Lr, Lc);
+                else potrf_panel_rows<32>(A, ld, rr0, jb, Lr, Lc);
             }
             __syncthreads();
         }
