@@ -17,8 +17,8 @@ constexpr int kMaxLevels = 8;
 // Each priority level's ready queue is split into nsub rings (task id mod
 // nsub), each with its own head and tail, so that claims contend on several
 // heads instead of one; a claiming warp reads every ring's head and tail in
-// one round trip (one lane per ring), so levels x nsub <= 32.
-constexpr int kMaxRings = 32;
+// one round trip (two rings per lane), so levels x nsub <= 64.
+constexpr int kMaxRings = 64;
 constexpr int kThreads = 256;            // threads per persistent CTA
 
 // Work-item decomposition of each kind (the host computes nitems, the

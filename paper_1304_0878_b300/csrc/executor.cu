@@ -319,29 +319,36 @@ __device__ __forceinline__ unsigned long long claim(const LaunchParams &p, uint6
             err = __shfl_sync(0xffffffffu, err, 0);
             if (err) return kEmpty;
         }
-        unsigned long long h = 0, tl = 0;
+        // lane l reads rings l and l + 32
+        unsigned long long h = 0, tl = 0, h2 = 0, tl2 = 0;
         const int nrings = p.nlevels * p.nsub;
-        const bool mine = lane < nrings;
+        const bool mine = lane < nrings, mine2 = lane + 32 < nrings;
         if (mine) {
             h = ld_rlx(&ctl->lvl[lane].head);
             tl = ld_rlx(&ctl->lvl[lane].tail);
+        }
+        if (mine2) {
+            h2 = ld_rlx(&ctl->lvl[lane + 32].head);
+            tl2 = ld_rlx(&ctl->lvl[lane + 32].tail);
         }
         if (lane == 31 && !lost && (check || spin > 0)) err = ld_rlx_i32(&ctl->error);
         err = __shfl_sync(0xffffffffu, err, 31);
         if (err) return kEmpty;
         lost = false;
-        const unsigned mask = __ballot_sync(0xffffffffu, mine && h < tl);
+        const unsigned long long mask = (unsigned long long)__ballot_sync(0xffffffffu, mine && h < tl) |
+                                        ((unsigned long long)__ballot_sync(0xffffffffu, mine2 && h2 < tl2) << 32);
         if (mask) {
             // the highest non-empty level; among its rings the CTA's own
             // (blockIdx mod nsub) first, then the next ones in turn
-            const int top = (31 - __clz(mask)) / p.nsub;
-            const unsigned long long all = (1ull << p.nsub) - 1ull;     // nsub <= 32
-            const unsigned long long sub = ((unsigned long long)mask >> (top * p.nsub)) & all;
-            const int home = (int)(blockIdx.x % (unsigned)p.nsub);
-            const unsigned long long rot = ((sub >> home) | (sub << (p.nsub - home))) & all;
-            const int lv = top * p.nsub + (home + __ffsll((long long)rot) - 1) % p.nsub;
-            const unsigned long long hv = __shfl_sync(0xffffffffu, h, lv);
-            const unsigned long long tv = __shfl_sync(0xffffffffu, tl, lv);
+            const int ns = p.nsub;                                       // 1..64
+            const int top = (63 - __clzll((long long)mask)) / ns;
+            const unsigned long long all = ns == 64 ? ~0ull : (1ull << ns) - 1ull;
+            const unsigned long long sub = (mask >> (top * ns)) & all;
+            const int home = (int)(blockIdx.x % (unsigned)ns);
+            const unsigned long long rot = home == 0 ? sub : ((sub >> home) | (sub << (ns - home))) & all;
+            const int lv = top * ns + (home + __ffsll((long long)rot) - 1) % ns;
+            const unsigned long long hv = __shfl_sync(0xffffffffu, lv < 32 ? h : h2, lv & 31);
+            const unsigned long long tv = __shfl_sync(0xffffffffu, lv < 32 ? tl : tl2, lv & 31);
             unsigned long long item = kEmpty;
             int got = 0;
             if (lane == 0) {

@@ -295,9 +295,9 @@ void derive(b3t_ctx *c, int32_t t, const int32_t *leaves, const uint8_t *modes, 
 void compute_levels(const b3t_ctx *c, const std::vector<int32_t> &off, const int32_t *succ,
                     std::vector<float> &rank, std::vector<int32_t> &level);
 
-// Rings per priority level of a launch: as many as the 32 lanes of the
-// claiming warp allow (4 with 8 levels, 32 with one); B3T_SUB_RINGS
-// overrides it (1 .. that number), for measurements.
+// Rings per priority level of a launch: as many as the claiming warp reads in
+// one round trip (64 rings: 8 per level with 8 levels, 64 with one);
+// B3T_SUB_RINGS overrides it (1 .. that number), for measurements.
 int sub_rings(const b3t_ctx *c) {
     const int most = kMaxRings / std::max(1, c->cfg.prio_levels);
     int n = most;
