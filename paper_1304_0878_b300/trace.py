@@ -33,9 +33,11 @@ def summary(records, ntasks, edges, nctas):
     pairs of that launch (Context.dag_edges() before the wait), each from an
     earlier to a later submission; nctas: the launch's grid.  Returns the
     makespan, the CTA busy fraction (item time over CTAs x makespan), the
-    per-kind share of the CTA time, the critical path and its share of the
-    makespan, and the number of edges whose successor started before its
-    predecessor ended (0 for a legal run)."""
+    per-kind share of the CTA time, the critical path (its length, share of
+    the makespan, task count, time per kind along it, and how long its tasks
+    waited after their predecessor on it ended), and the number of edges
+    whose successor started before its predecessor ended (0 for a legal
+    run)."""
     ed = np.asarray(edges, dtype=np.int64).reshape(-1, 2)
     st = records["t_start_ns"].astype(np.int64)
     en = records["t_end_ns"].astype(np.int64)
@@ -54,10 +56,28 @@ def summary(records, ntasks, edges, nctas):
     preds, succ_of = ed[order, 0], ed[order, 1]
     first = np.searchsorted(succ_of, np.arange(ntasks + 1))
     cp = span.astype(np.float64)
+    via = np.full(ntasks, -1, dtype=np.int64)      # predecessor on the longest chain
     for v in range(ntasks):
         a, z = first[v], first[v + 1]
         if z > a:
-            cp[v] += cp[preds[a:z]].max()
+            j = a + int(np.argmax(cp[preds[a:z]]))
+            cp[v] += cp[preds[j]]
+            via[v] = preds[j]
+    # the critical path itself: its tasks' spans per kind, and the time the
+    # path's tasks waited after their chain predecessor ended (queueing)
+    task_kind = np.full(ntasks, -1, dtype=np.int64)
+    task_kind[records["task"]] = records["kind"]
+    v = int(np.argmax(cp))
+    path_kinds, waits, ntask_path = {}, 0, 0
+    while v >= 0:
+        name = KIND_NAMES.get(int(task_kind[v]), str(int(task_kind[v])))
+        path_kinds[name] = path_kinds.get(name, 0.0) + float(span[v]) / 1e6
+        if via[v] >= 0:
+            waits += max(0, int(ts[v]) - int(te[via[v]]))
+        ntask_path += 1
+        v = int(via[v])
     return {"makespan_ms": makespan / 1e6, "cta_busy_frac": float(dur.sum()) / (nctas * makespan),
             "critical_path_ms": float(cp.max()) / 1e6, "critical_path_share": float(cp.max()) / makespan,
+            "critical_path_tasks": ntask_path, "critical_path_ms_by_kind": path_kinds,
+            "critical_path_wait_ms": waits / 1e6,
             "edges_violated": int(np.sum(te[ed[:, 0]] > ts[ed[:, 1]])) if len(ed) else 0, "kinds": kinds}

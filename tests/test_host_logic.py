@@ -190,6 +190,10 @@ def test_trace_summary():
     assert s["cta_busy_frac"] == 0.7 and s["edges_violated"] == 0
     assert s["kinds"]["GEMM"]["items"] == 2 and s["kinds"]["GEMM"]["cta_time_share"] == 4000 / 7000
     assert set(s["kinds"]) == {"POTRF", "TRSM", "GEMM", "SYRK"}
+    # the path is POTRF -> GEMM (task 2, span 1000..3500) -> SYRK; SYRK waited 500 ns
+    assert s["critical_path_tasks"] == 3
+    assert s["critical_path_ms_by_kind"] == {"POTRF": 1000 / 1e6, "GEMM": 2500 / 1e6, "SYRK": 1000 / 1e6}
+    assert s["critical_path_wait_ms"] == 500 / 1e6
     tr["t_start_ns"][4] = 3200          # task 3 starts before task 2 ends
     assert trace.summary(tr, 4, ed, 2)["edges_violated"] == 1
     assert trace.summary(tr[:1], 1, [], 1)["critical_path_ms"] == 1000 / 1e6    # no edges
