@@ -26,6 +26,15 @@ constexpr int kThreads = 256;            // threads per persistent CTA
 constexpr int64_t kScalChunk = 1 << 16;  // f32 elements per SCAL item
 constexpr int kGemmBlk = 64;             // f64 GEMM / SYRK item: 64 x 64 of C
 constexpr int kTrsmRows = 32;            // f64 TRSM item: 32 rows of A_ik
+#ifndef B3T_TRTRI_ROWS
+#define B3T_TRTRI_ROWS 8
+#endif
+#ifndef B3T_TRMM_ROWS
+#define B3T_TRMM_ROWS 32
+#endif
+constexpr int kTrtriRows = B3T_TRTRI_ROWS;   // TRTRI item: rows of U_k (8, 16 or 32)
+constexpr int kTrmmRows = B3T_TRMM_ROWS;     // TRMM_MX item: rows x 64 columns of L_ik (32 or 64)
+static_assert(kTrmmRows == 32 || kTrmmRows == 64, "TRMM_MX rows per item");
 constexpr int kMxBlk = 128;              // MX GEMM / SYRK item: 128 x 128 of C
 constexpr int kCvtCols = 16;             // CVT item: 16 columns of the tile
 constexpr int kGemvRows = 16;            // GEMV item: 16 rows of the updated part

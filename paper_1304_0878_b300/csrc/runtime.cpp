@@ -141,9 +141,11 @@ int64_t items_of(int kind, int64_t n) {
     case kPotrf: case kPotrfMx: case kNoop: return 1;
     case kCvt: return n / kCvtCols;
     case kQuant: return 1;   // set from the format at submit (one item per 16 KiB chunk)
-    case kTrsm: case kTrsmMx: case kTrtri: return n / kTrsmRows;
+    case kTrsm: case kTrsmMx: return n / kTrsmRows;
+    case kTrtri: return n / kTrtriRows;
     case kSyrk: { int64_t m = n / kGemmBlk; return m * (m + 1) / 2; }
-    case kGemm: case kTrmmMx: { int64_t m = n / kGemmBlk; return m * m; }
+    case kGemm: { int64_t m = n / kGemmBlk; return m * m; }
+    case kTrmmMx: return (n / kTrmmRows) * (n / kGemmBlk);
     case kSyrkMx: { int64_t m = n / kMxBlk; return m * (m + 1) / 2; }
     case kGemmMx: { int64_t m = n / kMxBlk; return m * m; }
     case kGemvL: case kGemvLT: return n / kGemvRows;

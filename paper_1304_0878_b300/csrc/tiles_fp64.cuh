@@ -103,30 +103,33 @@ __device__ __forceinline__ void syrk_item(const TaskRec &t, int item, double *sm
 // kPipe: the next K chunk is loaded into registers while the current one is
 // used (one memory latency per item instead of one per chunk; more
 // registers, so only the out-of-line mixed-precision TRSM uses it).
-template <typename Tin, bool kIdent = false, bool kPipe = false>
+template <typename Tin, bool kIdent = false, bool kPipe = false, int RB = kTrsmRows>
 __device__ __forceinline__ void trsm_rows(const double *L, const Tin *Ain, double *X, int r0, int n, int ld,
                                           double *smem) {
+    static_assert(RB == 8 || RB == 16 || RB == 32, "rows per item");
     const int b = ld;
     const int cs = kIdent ? (r0 / 64) * 64 : 0;     // first column block that can be nonzero
-    constexpr int RB = kTrsmRows;           // 32 rows
+    constexpr int RS = RB + 1;              // padded row stride of the row-major staging
+    constexpr int NG = kThreads / RB;       // column groups: thread (tr, tw) owns row tr
+    constexpr int NC = 64 / NG;             // and columns tw + NG j, j < NC, of a block
     double *Lcb = smem;                     // [64][65]  Lcb[c*65 + q] = L(c0+c, c0+q)
-    double *Acc = Lcb + 64 * 65;            // [64][33]  Acc[c*33 + r]
-    double *Xs = Acc + 64 * 33;             // [kKc][33] Xs[p*33 + r] = X(r0+r, k0+p)
-    double *Ls = Xs + kKc * 33;             // [kKc][64] Ls[p*64 + c] = L(c0+c, k0+p)
+    double *Acc = Lcb + 64 * 65;            // [64][RS]  Acc[c*RS + r]
+    double *Xs = Acc + 64 * RS;             // [kKc][RS] Xs[p*RS + r] = X(r0+r, k0+p)
+    double *Ls = Xs + kKc * RS;             // [kKc][64] Ls[p*64 + c] = L(c0+c, k0+p)
     const int tid = threadIdx.x;
-    const int tr = tid & 31, tw = tid >> 5;     // row, column group
+    const int tr = tid % RB, tw = tid / RB;
     if (kIdent) {
         for (int c0 = 0; c0 < cs; c0 += 64) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) X[(size_t)(r0 + tr) + (size_t)(c0 + tw + 8 * j) * b] = 0.0;
+            for (int j = 0; j < NC; ++j) X[(size_t)(r0 + tr) + (size_t)(c0 + tw + NG * j) * b] = 0.0;
         }
     }
     for (int c0 = cs; c0 < n; c0 += 64) {
-        double acc[8];
+        double acc[NC];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            if (kIdent) acc[j] = (r0 + tr == c0 + tw + 8 * j) ? 1.0 : 0.0;
-            else acc[j] = (double)Ain[(size_t)(r0 + tr) + (size_t)(c0 + tw + 8 * j) * b];
+        for (int j = 0; j < NC; ++j) {
+            if (kIdent) acc[j] = (r0 + tr == c0 + tw + NG * j) ? 1.0 : 0.0;
+            else acc[j] = (double)Ain[(size_t)(r0 + tr) + (size_t)(c0 + tw + NG * j) * b];
         }
         constexpr int NX = (RB * kKc) / kThreads, NL = (64 * kKc) / kThreads;
         double xv[kPipe ? NX : 1], lv[kPipe ? NL : 1];
@@ -134,7 +137,7 @@ __device__ __forceinline__ void trsm_rows(const double *L, const Tin *Ain, doubl
 #pragma unroll
             for (int q = 0; q < NX; ++q) {
                 const int e = tid + q * kThreads;
-                xv[q] = X[(size_t)(r0 + (e & 31)) + (size_t)(cs + (e >> 5)) * b];
+                xv[q] = X[(size_t)(r0 + e % RB) + (size_t)(cs + e / RB) * b];
             }
 #pragma unroll
             for (int q = 0; q < NL; ++q) {
@@ -146,8 +149,8 @@ __device__ __forceinline__ void trsm_rows(const double *L, const Tin *Ain, doubl
 #pragma unroll
             for (int q = 0; q < NX; ++q) {
                 const int e = tid + q * kThreads;
-                const int r = e & 31, p = e >> 5;
-                Xs[p * 33 + r] = kPipe ? xv[kPipe ? q : 0] : X[(size_t)(r0 + r) + (size_t)(k0 + p) * b];
+                const int r = e % RB, p = e / RB;
+                Xs[p * RS + r] = kPipe ? xv[kPipe ? q : 0] : X[(size_t)(r0 + r) + (size_t)(k0 + p) * b];
             }
 #pragma unroll
             for (int q = 0; q < NL; ++q) {
@@ -160,7 +163,7 @@ __device__ __forceinline__ void trsm_rows(const double *L, const Tin *Ain, doubl
 #pragma unroll
                 for (int q = 0; q < NX; ++q) {
                     const int e = tid + q * kThreads;
-                    xv[q] = X[(size_t)(r0 + (e & 31)) + (size_t)(k0 + kKc + (e >> 5)) * b];
+                    xv[q] = X[(size_t)(r0 + e % RB) + (size_t)(k0 + kKc + e / RB) * b];
                 }
 #pragma unroll
                 for (int q = 0; q < NL; ++q) {
@@ -170,14 +173,14 @@ __device__ __forceinline__ void trsm_rows(const double *L, const Tin *Ain, doubl
             }
 #pragma unroll 8
             for (int p = 0; p < kKc; ++p) {
-                const double x = Xs[p * 33 + tr];
+                const double x = Xs[p * RS + tr];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[j] = fma(-x, Ls[p * 64 + tw + 8 * j], acc[j]);
+                for (int j = 0; j < NC; ++j) acc[j] = fma(-x, Ls[p * 64 + tw + NG * j], acc[j]);
             }
             __syncthreads();
         }
 #pragma unroll
-        for (int j = 0; j < 8; ++j) Acc[(tw + 8 * j) * 33 + tr] = acc[j];
+        for (int j = 0; j < NC; ++j) Acc[(tw + NG * j) * RS + tr] = acc[j];
         for (int e = tid; e < 64 * 64; e += kThreads) {
             const int c = e & 63, q = e >> 6;           // element (c0+c, c0+q)
             if (c >= q) Lcb[c * 65 + q] = L[(size_t)(c0 + c) + (size_t)(c0 + q) * b];
@@ -193,7 +196,7 @@ __device__ __forceinline__ void trsm_rows(const double *L, const Tin *Ain, doubl
             if (tid < RB) {
                 double x[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) x[j] = Acc[(p0 + j) * 33 + tid];
+                for (int j = 0; j < 8; ++j) x[j] = Acc[(p0 + j) * RS + tid];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     x[j] = x[j] / Lcb[(p0 + j) * 65 + p0 + j];
@@ -201,22 +204,22 @@ __device__ __forceinline__ void trsm_rows(const double *L, const Tin *Ain, doubl
                     for (int jj = j + 1; jj < 8; ++jj) x[jj] = fma(-x[j], Lcb[(p0 + jj) * 65 + p0 + j], x[jj]);
                 }
 #pragma unroll
-                for (int j = 0; j < 8; ++j) Acc[(p0 + j) * 33 + tid] = x[j];
+                for (int j = 0; j < 8; ++j) Acc[(p0 + j) * RS + tid] = x[j];
             }
             __syncthreads();
             const int rem = 56 - p0;
             for (int e = tid; e < RB * rem; e += kThreads) {
-                const int r = e & 31, cc = p0 + 8 + (e >> 5);
-                double v = Acc[cc * 33 + r];
+                const int r = e % RB, cc = p0 + 8 + e / RB;
+                double v = Acc[cc * RS + r];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) v = fma(-Acc[(p0 + j) * 33 + r], Lcb[cc * 65 + p0 + j], v);
-                Acc[cc * 33 + r] = v;
+                for (int j = 0; j < 8; ++j) v = fma(-Acc[(p0 + j) * RS + r], Lcb[cc * 65 + p0 + j], v);
+                Acc[cc * RS + r] = v;
             }
             __syncthreads();
         }
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-            X[(size_t)(r0 + tr) + (size_t)(c0 + tw + 8 * j) * b] = Acc[(tw + 8 * j) * 33 + tr];
+        for (int j = 0; j < NC; ++j)
+            X[(size_t)(r0 + tr) + (size_t)(c0 + tw + NG * j) * b] = Acc[(tw + NG * j) * RS + tr];
         __syncthreads();
     }
 }
@@ -227,10 +230,15 @@ __device__ __forceinline__ void trsm_item(const TaskRec &t, int item, double *sm
 }
 
 // TRTRI: U_k <- L_kk^{-T} (upper triangular, the strict lower part zero),
-// 32 rows of U_k (= 32 columns of L_kk^{-1}) per item.
-__device__ __forceinline__ void trtri_item(const TaskRec &t, int item, double *smem) {
-    trsm_rows<double, true>((const double *)t.buf[0], (const double *)nullptr, (double *)t.buf[1],
-                            item * kTrsmRows, (int)t.n, (int)t.n, smem);
+// kTrtriRows rows of U_k (= columns of L_kk^{-1}) per item.  Row r of U_k
+// needs the columns from r to b, so the first item is the longest: it is the
+// step of the mixed factorisation that no other CTA can share, and short
+// items keep it short.  Out of line, with the pipelined K loop (one CTA per
+// SM in the mixed-precision launch).
+__device__ __noinline__ void trtri_item(const TaskRec &t, int item, double *smem) {
+    trsm_rows<double, true, true, kTrtriRows>((const double *)t.buf[0], (const double *)nullptr,
+                                              (double *)t.buf[1], item * kTrtriRows, (int)t.n, (int)t.n,
+                                              smem);
 }
 
 // Out of line with the pipelined K loop: the mixed-precision launch runs one
@@ -241,65 +249,82 @@ __device__ __noinline__ void trsm_mx_item(const TaskRec &t, int item, double *sm
 }
 
 // TRMM_MX: L_ik <- fp64(W_ik) U_k with U_k = L_kk^{-T} (upper triangular,
-// zero below the diagonal, from TRTRI), one 64 x 64 block of L_ik per item:
+// zero below the diagonal, from TRTRI), one kTrmmRows x 64 block of L_ik per
+// item:
 //   L(rows bi, cols bj) = sum_{p < 64 (bj + 1)} fp64(W(rows bi, p)) U(p, cols bj),
 // p ascending, one FMA per term.  Unlike the substitution (TRSM_MX), every
-// block is independent, so a tile's panel solve spreads over (b/64)^2 CTAs
-// and runs at the DFMA rate of a plain product.  The mixed-precision launch
-// runs one CTA per SM, so the next K chunk is loaded into registers while
-// the current one is used.
+// block is independent, so a tile's panel solve spreads over many CTAs and
+// runs at the DFMA rate of a plain product; the longest item (the last block
+// column, K = b) bounds the task's latency.  The mixed-precision launch runs
+// one CTA per SM, so the next K chunk is loaded into registers while the
+// current one is used.
 __device__ __noinline__ void trmm_mx_item(const TaskRec &t, int item, double *smem) {
+    constexpr int RM = kTrmmRows;
+    constexpr int NI = RM / 16;                 // rows per thread
     const int b = (int)t.n, m = b / kGemmBlk;
     const int bi = item / m, bj = item % m;
     const double *U = (const double *)t.buf[0];
     const float *Wt = (const float *)t.buf[1];
     double *L = (double *)t.buf[2];
-    double *As = smem;                   // [kKc][64]  As[p*64 + r] = W(64 bi + r, k0 + p)
-    double *Bs = smem + kKc * 64;        // [kKc][65]  Bs[p*65 + c] = U(k0 + p, 64 bj + c)
+    double *As = smem;                   // [kKc][RM]  As[p*RM + r] = W(RM bi + r, k0 + p)
+    double *Bs = smem + kKc * RM;        // [kKc][65]  Bs[p*65 + c] = U(k0 + p, 64 bj + c)
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     const int K = (bj + 1) * 64;
-    constexpr int NQ = (kKc * 64) / kThreads;   // 8 elements of each operand per thread and chunk
-    const float *Wb = Wt + (size_t)bi * 64;
+    constexpr int NA = (kKc * RM) / kThreads;   // elements of W per thread and chunk
+    constexpr int NQ = (kKc * 64) / kThreads;   // elements of U per thread and chunk
+    const float *Wb = Wt + (size_t)bi * RM;
     const double *Ub = U + (size_t)bj * 64 * b;
-    float av[NQ];
+    float av[NA];
     double bv[NQ];
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+        const int e = tid + q * kThreads;
+        av[q] = Wb[(size_t)(e % RM) + (size_t)(e / RM) * b];
+    }
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
         const int e = tid + q * kThreads;
-        av[q] = Wb[(size_t)(e & 63) + (size_t)(e >> 6) * b];
         bv[q] = Ub[(size_t)(e & 31) + (size_t)(e >> 5) * b];
     }
-    double acc[4][4];
+    double acc[NI][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < NI; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
     for (int k0 = 0; k0 < K; k0 += kKc) {
 #pragma unroll
+        for (int q = 0; q < NA; ++q) {
+            const int e = tid + q * kThreads;
+            As[(e / RM) * RM + e % RM] = (double)av[q];
+        }
+#pragma unroll
         for (int q = 0; q < NQ; ++q) {
             const int e = tid + q * kThreads;
-            As[(e >> 6) * 64 + (e & 63)] = (double)av[q];
             Bs[(e & 31) * 65 + (e >> 5)] = bv[q];
         }
         __syncthreads();
         if (k0 + kKc < K) {
 #pragma unroll
+            for (int q = 0; q < NA; ++q) {
+                const int e = tid + q * kThreads;
+                av[q] = Wb[(size_t)(e % RM) + (size_t)(k0 + kKc + e / RM) * b];
+            }
+#pragma unroll
             for (int q = 0; q < NQ; ++q) {
                 const int e = tid + q * kThreads;
-                av[q] = Wb[(size_t)(e & 63) + (size_t)(k0 + kKc + (e >> 6)) * b];
                 bv[q] = Ub[(size_t)(k0 + kKc + (e & 31)) + (size_t)(e >> 5) * b];
             }
         }
 #pragma unroll 8
         for (int p = 0; p < kKc; ++p) {
-            double a[4], bb[4];
+            double a[NI], bb[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[p * 64 + tx + 16 * i];
+            for (int i = 0; i < NI; ++i) a[i] = As[p * RM + tx + 16 * i];
 #pragma unroll
             for (int j = 0; j < 4; ++j) bb[j] = Bs[p * 65 + ty + 16 * j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < NI; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
         }
@@ -308,8 +333,8 @@ __device__ __noinline__ void trmm_mx_item(const TaskRec &t, int item, double *sm
 #pragma unroll
     for (int j = 0; j < 4; ++j)
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-            L[(size_t)(bi * 64 + tx + 16 * i) + (size_t)(bj * 64 + ty + 16 * j) * b] = acc[i][j];
+        for (int i = 0; i < NI; ++i)
+            L[(size_t)(bi * RM + tx + 16 * i) + (size_t)(bj * 64 + ty + 16 * j) * b] = acc[i][j];
 }
 
 // Panel update of potrf_block for RB rows from rr0 (all valid):
