@@ -46,10 +46,11 @@ def task_list(T):
     return out
 
 
-def factor(A_tiles, T, b, fmt):
+def factor(A_tiles, T, b, fmt, state=False):
     """Run the mixed task list in submission order on packed FP64 tiles of A
     (unchanged).  Returns (L tiles FP64, info); L tiles use the packed
-    layout of cholesky.to_tiles."""
+    layout of cholesky.to_tiles.  state=True also returns the updated
+    binary32 tiles W and the quantised panels {(i, k): (Q, e)}."""
     Wt = A_tiles.astype(np.float32)
     Lt = np.zeros_like(A_tiles)
     Q = {}
@@ -60,7 +61,7 @@ def factor(A_tiles, T, b, fmt):
             Lt[t] = np.tril(Wt[t].T.astype(np.float64)).T   # lower part only
             info = _t.potrf(Lt[t].T)
             if info:
-                return Lt, k * b + info
+                return (Lt, k * b + info, Wt, Q) if state else (Lt, k * b + info)
         elif kind == TRSM_MX:
             _, i, k = acc[1][0]
             t = tile_index(i, k, T)
@@ -79,4 +80,4 @@ def factor(A_tiles, T, b, fmt):
             qb, eb = Q[(j, k)]
             C = Wt[tile_index(i, j, T)].T
             _t.gemm_lowp(qa, qb, 2.0 ** (ea + eb), C)
-    return Lt, 0
+    return (Lt, 0, Wt, Q) if state else (Lt, 0)

@@ -168,10 +168,10 @@ def test_mixed_factor_matches_mixed_oracle(orc, gctx, fmt):
     Lt, info = omx.factor(och.to_tiles(A, b), N // b, b, fmt)
     Lo = np.tril(och.from_tiles(Lt, N, b))
     r_dev, r_orc = och.rel_residual(L, A), och.rel_residual(Lo, A)
-    # same low-precision factor up to binary32 accumulation order
-    assert r_dev <= 2.0 * r_orc + 1e-6
-    tol = 1e-3 if fmt == "bf16" else 5e-2
-    assert np.max(np.abs(L - Lo)) / np.max(np.abs(Lo)) <= tol
+    # the same low-precision factor up to the order of the binary32 sums: a
+    # residual of the same size (the element-level parity is
+    # test_mixed_factor_every_task_within_its_bound)
+    assert r_dev <= 2.0 * r_orc and r_orc <= 2.0 * r_dev
 
 
 # ---- the panel solve as a product with the inverted diagonal tile
@@ -265,6 +265,53 @@ def test_mixed_inv_factor_matches_mixed_oracle(orc, gctx, fmt):
     Lt, info = omx.factor(och.to_tiles(A, b), N // b, b, fmt)
     Lo = np.tril(och.from_tiles(Lt, N, b))
     r_dev, r_orc = och.rel_residual(L, A), och.rel_residual(Lo, A)
-    assert r_dev <= 2.0 * r_orc + 1e-6
-    tol = 1e-3 if fmt == "bf16" else 5e-2
-    assert np.max(np.abs(L - Lo)) / np.max(np.abs(Lo)) <= tol
+    assert r_dev <= 2.0 * r_orc and r_orc <= 2.0 * r_dev
+
+
+# ---- every task of the factorisation against its own rounding bound
+
+def factor_state_dev(ctx, A, b, fmt, inv):
+    """Run the mixed factorisation; return what it leaves on the device: W
+    and L tiles (packed), the decoded panel tiles {(i, k): (values, e)} and
+    the inverted diagonal tiles (product form) or None."""
+    N = A.shape[0]
+    T = N // b
+    At = torch.from_numpy(och.to_tiles(A, b)).cuda()
+    Wt = At.float()
+    Lt = torch.zeros_like(At)
+    Qt = dt.q_tiles(T, b, FMTS[fmt], "cuda")
+    Ut = torch.zeros((T, b, b), dtype=torch.float64, device="cuda")
+    wp, lp, qp, up = dt.tile_ptrs(Wt), dt.tile_ptrs(Lt), dt.tile_ptrs(Qt), dt.tile_ptrs(Ut)
+    if inv:
+        ctx.cholesky_mx_inv_submit(wp, lp, qp, up, T, b, FMTS[fmt])
+    else:
+        ctx.cholesky_mx_submit(wp, lp, qp, T, b, FMTS[fmt])
+    ctx.task_wait()
+    for p in (wp, lp, qp):
+        ctx.tiles_unregister(p, T)
+    if inv:
+        for p in up:
+            ctx.data_unregister(ctx.data_lookup(p))
+    Qh = Qt.cpu().numpy()
+    Q = {}
+    for k in range(T):
+        for i in range(k + 1, T):
+            Q[(i, k)] = decode(Qh[och.tile_index(i, k, T)], b, FMTS[fmt])
+    return Wt.cpu().numpy(), Lt.cpu().numpy(), Q, (Ut.cpu().numpy() if inv else None)
+
+
+@pytest.mark.parametrize("inv", [False, True])
+@pytest.mark.parametrize("fmt", ["bf16", "e4m3"])
+@pytest.mark.parametrize("N,b", [(1024, 128), (1024, 256)])
+def test_mixed_factor_every_task_within_its_bound(orc, gctx, fmt, inv, N, b):
+    # each task's output against that task's inputs as the device left them:
+    # QUANT bit for bit, the tensor-core updates within the binary32
+    # accumulation bound carried over a tile's updates, POTRF / TRSM / TRTRI /
+    # TRMM within the FP64 backward-error bounds (tests/mixed_steps.py); b =
+    # 256 takes the diagonal-panel DAG (CVT, POTRF_D, PANEL_TRSM, PANEL_UPD)
+    from mixed_steps import check_factor
+    A = synth.spd_host(N, seed=N + b, shift=1.0)
+    Wt, Lt, Q, Ut = factor_state_dev(gctx, A, b, fmt, inv)
+    r = check_factor(A, Wt, Lt, Q, N // b, b, fmt, Ut)
+    assert r["quant"] == 0.0, r
+    assert all(v <= 1.0 for v in r.values()), r
