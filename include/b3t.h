@@ -125,7 +125,10 @@ enum b3t_kind {
     B3T_PANEL_UPD = 20,
     B3T_CVT = 21,
     B3T_TRTRI = 22,
-    B3T_TRMM_MX = 23
+    B3T_TRMM_MX = 23,
+    B3T_SLICE_A = 24,
+    B3T_SLICE_X = 25,
+    B3T_RESID_SL = 26
 };
 
 /* Diagonal tile split into column panels.  A b x b diagonal tile partitioned
@@ -180,6 +183,45 @@ typedef struct b3t_panel_args {
 typedef struct b3t_vec_args {
     int32_t nrhs, flags, i, T, b;
 } b3t_vec_args;
+
+/* Sliced FP64 residual (the refinement's r = b - A x with the products on
+ * the tensor cores; the Ozaki scheme, Ozaki, Ogita, Oishi and Rump, Numer.
+ * Algorithms 59, 2012).  A value v of a block with scale exponent e (the
+ * smallest e = ilogb(max|block|) + 3, so |v| < 2^(e-2); 0 for a zero block)
+ * is V = trunc(v 2^(60-e)) written as twelve balanced base-32 digits d_s in
+ * [-16, 15], V = sum_s d_s 32^(11-s), each an exact E4M3 value ("slice" s).
+ * The product of an A tile and an X part keeps the slice pairs with
+ * s + t <= 11, each group m = s + t summed exactly in binary32 on the tensor
+ * cores, and adds it in FP64 with its scale 2^(eA + eX - 5 (m + 2)).  Per
+ * product term a*x the error is below 2^(eA + eX - 58.3); the FP64 sum
+ * takes two roundings per tile.  b a multiple of 128 (<= 4096), nrhs <= 16.
+ * Scalars: struct b3t_slice_args.
+ *  B3T_SLICE_A   A (R, all T(T+1)/2 packed f64 tiles), D_ij (W), D_ji (W):
+ *                the slices of the stored tile (i, j), j <= i, for its two
+ *                uses: D_ij for A_ij (rows of block i), D_ji for A_ij^T
+ *                (rows of block j); a diagonal tile passes the same part
+ *                twice and has the one symmetric use.  A part
+ *                (b3t_slice_a_part_bytes) holds, for 128-row block rb,
+ *                128-column block kc and slice s, a 16 KiB chunk at
+ *                ((rb * b/128 + kc) * 12 + s) * 16384 in the quantised tile
+ *                layout (row r at r*128, 16-byte group g at g ^ (r % 8));
+ *                then the b row sums of |A_use| (f64), then the int32
+ *                exponent (padded to 16 bytes).
+ *  B3T_SLICE_X   X_j (R, part of b*nrhs f64), E_j (W): the slices of the
+ *                part, right-hand sides as 16 rows (zero padded): chunk
+ *                (kc, t) of 16 x 128 bytes at (kc * 12 + t) * 2048 (same
+ *                swizzle), then 16 int32 exponents, then per 16-row group
+ *                and right-hand side max|x| (b/16 x 16 f64).
+ *  B3T_RESID_SL  D (R, the T x T parts of use (I, J) at (I*T + J) *
+ *                b3t_slice_a_part_bytes), E (R, T parts), B (R, T parts),
+ *                R_i (W, b3t_resid_part_elems f64): R_i <- B_i - (A X)_i,
+ *                with the per-16-row maxima of B3T_RESID (row sums of |A|
+ *                from the A slice parts); items of 128 rows. */
+typedef struct b3t_slice_args {
+    int32_t i, j, T, b, nrhs;
+} b3t_slice_args;
+B3T_API size_t b3t_slice_a_part_bytes(int32_t b);
+B3T_API size_t b3t_slice_x_part_bytes(int32_t b);
 enum { B3T_VEC_F32 = 1, B3T_VEC_ASSIGN = 2, B3T_VEC_LOWER_M = 4, B3T_VEC_UPPER_M = 8, B3T_VEC_KEEP_NORM = 16 };
 
 /* Low-precision formats of the Q tiles. */
@@ -478,6 +520,22 @@ B3T_API int b3t_ir_release(b3t_ctx *ctx, double *R, int32_t T, int32_t b, int32_
 B3T_API int b3t_ir_solve(b3t_ctx *ctx, const double *A_packed, double *const *L, const double *B,
                          double *X, double *R, double *eta, int32_t T, int32_t b, int32_t nrhs,
                          int32_t flags, double tol, int32_t max_iter, int32_t *iters, double *eta_out);
+
+/* Bytes of the slice area b3t_ir_solve_sliced needs: the T x T A slice
+ * parts, then (256-byte aligned) the T X slice parts.  0 for invalid
+ * arguments (b a multiple of 128 up to 4096, T <= 4096). */
+B3T_API size_t b3t_ir_slice_bytes(int32_t T, int32_t b);
+
+/* b3t_ir_solve with the sliced FP64 residual (B3T_RESID_SL) in place of
+ * B3T_RESID: the first step also slices every stored tile of A (SLICE_A),
+ * every step slices x (SLICE_X) before the residual.  S: device area of
+ * b3t_ir_slice_bytes(T, b) bytes, 256-byte aligned, owned by the caller; its
+ * registrations are dropped before returning.  nrhs <= 16, b a multiple of
+ * 128 (-EINVAL otherwise). */
+B3T_API int b3t_ir_solve_sliced(b3t_ctx *ctx, const double *A_packed, double *const *L, const double *B,
+                                double *X, double *R, void *S, double *eta, int32_t T, int32_t b,
+                                int32_t nrhs, int32_t flags, double tol, int32_t max_iter, int32_t *iters,
+                                double *eta_out);
 
 /* ---------------------------------------------------------------------
  * Stream mode: continuous submission into one resident persistent kernel.

@@ -24,6 +24,7 @@ PRIO_UPWARD, PRIO_DEPTH = 0, 1
 TRSV_L, GEMV_L, TRSV_LT, GEMV_LT, AXPY, RESID, NRM = 11, 12, 13, 14, 15, 16, 17
 VEC_F32, VEC_ASSIGN, VEC_LOWER_M, VEC_UPPER_M, VEC_KEEP_NORM = 1, 2, 4, 8, 16
 POTRF_D, PANEL_TRSM, PANEL_UPD, CVT, TRTRI, TRMM_MX = 18, 19, 20, 21, 22, 23
+SLICE_A, SLICE_X, RESID_SL = 24, 25, 26
 
 
 class B3TError(RuntimeError):
@@ -95,6 +96,12 @@ _SIGS = {
                                           _i32, _i32, _i32]),
     "b3t_ir_solve": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_vp), _vp, _vp, _vp, _vp, _i32, _i32, _i32,
                                     _i32, ctypes.c_double, _i32, _pi32, ctypes.POINTER(ctypes.c_double)]),
+    "b3t_ir_slice_bytes": (_sz, [_i32, _i32]),
+    "b3t_slice_a_part_bytes": (_sz, [_i32]),
+    "b3t_slice_x_part_bytes": (_sz, [_i32]),
+    "b3t_ir_solve_sliced": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_vp), _vp, _vp, _vp, _vp, _vp, _i32, _i32,
+                                           _i32, _i32, ctypes.c_double, _i32, _pi32,
+                                           ctypes.POINTER(ctypes.c_double)]),
 }
 
 
@@ -151,6 +158,22 @@ def resid_part_elems(b, nrhs):
 
 def vec_args(nrhs, flags=0, i=0, T=1, b=64):
     return struct.pack("<5i", nrhs, flags, i, T, b)
+
+
+def ir_slice_bytes(T, b):
+    return int(lib().b3t_ir_slice_bytes(T, b))
+
+
+def slice_a_part_bytes(b):
+    return int(lib().b3t_slice_a_part_bytes(b))
+
+
+def slice_x_part_bytes(b):
+    return int(lib().b3t_slice_x_part_bytes(b))
+
+
+def slice_args(i, j, T, b, nrhs):
+    return struct.pack("<5i", i, j, T, b, nrhs)
 
 
 class Context:
@@ -355,6 +378,19 @@ class Context:
                                 ctypes.byref(it), eta)
         if rc < 0 and rc != ERANGE:
             raise B3TError(rc, "b3t_ir_solve")
+        return rc, it.value, list(eta)
+
+    def ir_solve_sliced(self, A_ptr, L_ptrs, B_ptr, X_ptr, R_ptr, S_ptr, eta_ptr, T, b, nrhs, flags=0,
+                        tol=1e-12, max_iter=30):
+        """ir_solve with the sliced FP64 residual; S_ptr: ir_slice_bytes(T, b)
+        bytes of device memory.  Returns (return code, iterations, eta list)."""
+        it = _i32(0)
+        eta = (ctypes.c_double * (nrhs + 1))()
+        rc = lib().b3t_ir_solve_sliced(self._h, _vp(int(A_ptr)), _ptrs(L_ptrs), _vp(int(B_ptr)),
+                                       _vp(int(X_ptr)), _vp(int(R_ptr)), _vp(int(S_ptr)), _vp(int(eta_ptr)),
+                                       T, b, nrhs, flags, tol, max_iter, ctypes.byref(it), eta)
+        if rc < 0 and rc != ERANGE:
+            raise B3TError(rc, "b3t_ir_solve_sliced")
         return rc, it.value, list(eta)
 
     def ir_step_submit(self, A_ptr, L_ptrs, B_ptr, X_ptr, R_ptr, eta_ptr, T, b, nrhs, flags=0, first=True):

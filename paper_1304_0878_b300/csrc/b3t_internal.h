@@ -75,7 +75,39 @@ enum : int32_t {
     kPotrfMx = 6, kTrsmMx = 7, kSyrkMx = 8, kGemmMx = 9, kQuant = 10,
     kTrsvL = 11, kGemvL = 12, kTrsvLT = 13, kGemvLT = 14, kAxpy = 15, kResid = 16, kNrm = 17,
     kPotrfD = 18, kPanelTrsm = 19, kPanelUpd = 20, kCvt = 21, kTrtri = 22, kTrmmMx = 23,
-    kNumKinds = 24
+    kSliceA = 24, kSliceX = 25, kResidSl = 26,
+    kNumKinds = 27
+};
+
+// Sliced FP64 residual (the Ozaki scheme: exact products of integer digit
+// slices on the tensor cores).  A value v of a block with scale exponent e
+// (|v| < 2^(e-2)) is V = trunc(v 2^(60-e)), written in kSlDigits balanced
+// base-32 digits d_s in [-16, 15], V = sum_s d_s 32^(11-s); every digit is an
+// E4M3 integer.  Pairs of slices (s, t) with s + t <= kSlDigits - 1 are
+// multiplied and each group m = s + t is summed in one binary32 accumulator:
+// at most 12 pairs x b products of magnitude <= 256, so every partial sum is
+// an integer below 2^24 (b <= 4096) and the sums are exact.
+constexpr int kSlDigits = 12;
+constexpr int kSlGroups = 12;             // m = s + t = 0 .. 11
+constexpr int kSlRows = 128;              // RESID_SL item: 128 rows of R_i
+constexpr int kSlNp = 16;                 // B operand rows: right-hand sides, padded to 16
+constexpr uint32_t kSlChunk = 16384;      // A slice chunk: 128 rows x 128 bytes of K
+constexpr uint32_t kSlXChunk = kSlNp * 128;   // X slice chunk: 16 rows x 128 bytes of K
+// A slice part (one use-tile (I, J) of the symmetric matrix): chunks
+// (rb, kc, s) at ((rb * nk + kc) * 12 + s) * 16 KiB, nk = b / 128; then b f64
+// row sums of |A_IJ|; then the int32 scale exponent, padded to 16 bytes.
+B3T_HD constexpr int64_t sl_a_part_bytes(int b) {
+    return (int64_t)kSlDigits * b * b + 8 * (int64_t)b + 16;
+}
+// X slice part (part J): chunks (kc, t) at (kc * 12 + t) * 2 KiB; then 16
+// int32 exponents (one per right-hand side); then per 16-row group and
+// right-hand side max|x| (b / 16 x 16 f64).
+B3T_HD constexpr int64_t sl_x_part_bytes(int b) {
+    return (int64_t)kSlDigits * (b / 128) * kSlXChunk + 64 + (int64_t)(b / 16) * kSlNp * 8;
+}
+
+struct SliceArgs {
+    int32_t i, j, T, b, nrhs;
 };
 
 // One task as the device sees it: 64 bytes.
@@ -142,8 +174,8 @@ B3T_HD constexpr uint32_t family_of(int kind) {
     return kind == kScalF32 ? kFamScal
          : (kind == kPotrf || kind == kTrsm || kind == kSyrk || kind == kGemm || kind == kPotrfD ||
             kind == kPanelTrsm || kind == kPanelUpd) ? kFamF64
-         : ((kind >= kTrsvL && kind <= kNrm) || kind == kTrtri) ? kFamSolve
-         : (kind >= kPotrfMx && kind <= kQuant) || kind == kCvt || kind == kTrmmMx ? kFamMx
+         : ((kind >= kTrsvL && kind <= kNrm) || kind == kTrtri || kind == kSliceA || kind == kSliceX) ? kFamSolve
+         : (kind >= kPotrfMx && kind <= kQuant) || kind == kCvt || kind == kTrmmMx || kind == kResidSl ? kFamMx
          : 0u;   // NOOP runs in every variant
 }
 B3T_HD constexpr uint32_t variant_of(uint32_t fams) {

@@ -29,6 +29,7 @@
 #include "mx.cuh"
 #include "solve.cuh"
 #include "tiles_fp64.cuh"
+#include "sliced.cuh"
 
 namespace b3t {
 
@@ -515,9 +516,25 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
     mx.fills = 0;
     mx.items = 0;
     mx.tmem = 0;
+    // RESID_SL pipeline (its own barriers: the phases of the MX ring above
+    // are tracked separately, only the stage bytes are shared)
+    __shared__ __align__(8) uint64_t s_slbars[kSlBars];
+    SlState sl;
+    sl.full = s_slbars;
+    sl.empty = s_slbars + kSlStages;
+    sl.xfull = s_slbars + 2 * kSlStages;
+    sl.xempty = sl.xfull + 2;
+    sl.done = sl.xempty + 2;
+    sl.tfree = sl.done + 2;
+    sl.drain = sl.tfree + 2;
+    sl.fa = sl.fx = sl.nj = 0;
     if (kMx && p.has_mx) {
         if (tid == 0) {
             for (int i = 0; i < 2 * kMxStages + 1; ++i) mbar_init(&s_bars[i], 1);
+            for (int i = 0; i < kSlBars; ++i) mbar_init(&s_slbars[i], 1);
+            // each of the four epilogue warps frees an accumulator buffer
+            mbar_init(&sl.tfree[0], 4);
+            mbar_init(&sl.tfree[1], 4);
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
         if (warp == 0) tmem_alloc(&s_tmem, kTmemCols);
@@ -653,6 +670,19 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
                 }
                 break;
             case kTrtri: if constexpr (kSolve) trtri_item(rec, it, (double *)smem); break;
+            case kSliceA: if constexpr (kSolve) slice_a_item(rec, s_red, &s_e); break;
+            case kSliceX: if constexpr (kSolve) slice_x_item(rec, (int *)s_red); break;
+            case kResidSl:
+                if constexpr (kMx) {
+                    if (!p.has_mx) { st = -EPROTO; break; }
+                    // a chunk copy or a tile's MMAs take microseconds: each wait of
+                    // the pipeline gives up after 200 ms and the launch reports ETIMEDOUT
+                    if (resid_sl_item(rec, it, sl, smem, mx.tmem, min(p.timeout_ns, (int64_t)200000000), &s_fail)) {
+                        if (tid == 0) set_error(p.ctl, ETIMEDOUT, (int)t, 0, 30);
+                        st = -ETIMEDOUT;
+                    }
+                }
+                break;
             case kTrsvL:
                 if constexpr (kSolve) {
                     if (vk_flags(rec) & kVecF32) trsv_l_item<float>(rec, it, smem);

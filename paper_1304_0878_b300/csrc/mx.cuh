@@ -27,7 +27,9 @@ namespace b3t {
 
 constexpr int kMxStages = 5;
 constexpr uint32_t kChunkBytes = 16384;
-constexpr uint32_t kTmemCols = 128;
+// 128 columns for the MX update's accumulator, 2 x 192 for RESID_SL's group
+// accumulators (the MX launch runs one CTA per SM)
+constexpr uint32_t kTmemCols = 512;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);

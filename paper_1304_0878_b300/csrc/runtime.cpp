@@ -123,16 +123,21 @@ const KindSig kSigs[kNumKinds] = {
     /* CVT      */ {2, {B3T_R, B3T_W}, {4, 8}, 0, true},
     /* TRTRI    */ {2, {B3T_R, B3T_W}, {8, 8}, 0, true},
     /* TRMM_MX  */ {3, {B3T_R, B3T_R, B3T_W}, {8, 4, 8}, 0, true},
+    /* SLICE_A  */ {3, {B3T_R, B3T_W, B3T_W}, {8, 1, 1}, sizeof(SliceArgs), false},
+    /* SLICE_X  */ {2, {B3T_R, B3T_W}, {8, 1}, sizeof(SliceArgs), false},
+    /* RESID_SL */ {4, {B3T_R, B3T_R, B3T_R, B3T_W}, {1, 1, 8, 8}, sizeof(SliceArgs), false},
 };
 
 const char *kKindNames[kNumKinds] = {"noop", "scal_f32", "potrf", "trsm", "syrk", "gemm",
                                      "potrf_mx", "trsm_mx", "syrk_mx", "gemm_mx", "quant",
                                      "trsv_l", "gemv_l", "trsv_lt", "gemv_lt", "axpy", "resid", "nrm",
-                                     "potrf_d", "panel_trsm", "panel_upd", "cvt", "trtri", "trmm_mx"};
+                                     "potrf_d", "panel_trsm", "panel_upd", "cvt", "trtri", "trmm_mx",
+                                     "slice_a", "slice_x", "resid_sl"};
 bool is_panel(int kind) { return kind >= kPotrfD && kind <= kPanelUpd; }
 bool is_vec(int kind) { return kind >= kTrsvL && kind <= kNrm; }
 
-bool is_mx(int kind) { return kind == kSyrkMx || kind == kGemmMx; }
+bool is_mx(int kind) { return kind == kSyrkMx || kind == kGemmMx || kind == kResidSl; }
+bool is_slice(int kind) { return kind >= kSliceA && kind <= kResidSl; }
 bool has_fmt(int kind) { return kind == kSyrkMx || kind == kGemmMx || kind == kQuant; }
 
 int64_t items_of(int kind, int64_t n) {
@@ -151,6 +156,8 @@ int64_t items_of(int kind, int64_t n) {
     case kGemvL: case kGemvLT: return n / kGemvRows;
     case kResid: return n / kResidRows;
     case kAxpy: case kNrm: return 1;
+    case kSliceA: case kSliceX: return 1;
+    case kResidSl: return n / kSlRows;
     }
     return 1;
 }
@@ -179,6 +186,9 @@ float cost_of(int kind, int64_t n, int nrhs = 1, int T = 1, bool f32 = false) {
     case kNrm: return 5000.0f;
     case kCvt: return (float)(12.0 * b * b / 20.0);
     case kTrtri: return (float)(b * b * b / fp64);    // the first item's share dominates
+    case kSliceA: return (float)(2.0 * b * b / 4.0 + b * b / fp64);
+    case kSliceX: return (float)(16.0 * b / 4.0 + 2000.0);
+    case kResidSl: return (float)(T * b * 50.0);
     }
     return 1000.0f;
 }
@@ -649,6 +659,33 @@ int submit_impl(b3t_ctx *c, b3t_codelet cl, const b3t_handle *handles, const uin
     }
     int vnrhs = 1, vT = 1;
     bool vf32 = false;
+    if (is_slice(C.kind)) {
+        SliceArgs a;
+        std::memcpy(&a, scalars, sizeof(a));
+        const Handle *Hs[kMaxBuffers];
+        for (int i = 0; i < nbuffers; ++i) Hs[i] = &c->handles[handles[i]];
+        auto bytes = [&](int i) { return Hs[i]->nelems * Hs[i]->elemsize; };
+        bool ok = a.T >= 1 && a.T <= 4096 && a.b >= 128 && a.b <= 4096 && a.b % 128 == 0 && a.i >= 0 &&
+                  a.i < a.T && a.j >= 0 && a.j < a.T;
+        for (int i = 0; ok && i < nbuffers; ++i) ok = r.buf[i] % 16 == 0;
+        const size_t T = ok ? (size_t)a.T : 0, b = ok ? (size_t)a.b : 0;
+        const size_t PB = ok ? (size_t)sl_a_part_bytes(a.b) : 0, XB = ok ? (size_t)sl_x_part_bytes(a.b) : 0;
+        if (ok && C.kind == kSliceA)
+            ok = a.j <= a.i && Hs[0]->elemsize == 8 && Hs[0]->nelems >= T * (T + 1) / 2 * b * b &&
+                 bytes(1) >= PB && bytes(2) >= PB && (a.i == a.j) == (handles[1] == handles[2]);
+        if (ok && C.kind == kSliceX)
+            ok = a.nrhs >= 1 && a.nrhs <= kSlNp && Hs[0]->elemsize == 8 && Hs[0]->nelems >= b * a.nrhs &&
+                 bytes(1) >= XB;
+        if (ok && C.kind == kResidSl)
+            ok = a.nrhs >= 1 && a.nrhs <= kSlNp && bytes(0) >= T * T * PB && bytes(1) >= T * XB &&
+                 Hs[2]->elemsize == 8 && Hs[2]->nelems >= T * b * a.nrhs && Hs[3]->elemsize == 8 &&
+                 Hs[3]->nelems >= (size_t)resid_part_elems(a.b, a.nrhs);
+        if (!ok) return -EINVAL;
+        r.n = a.b;
+        r.aux = a.i | (a.j << 16);
+        r.scal = (uint32_t)a.T | ((uint32_t)(C.kind == kSliceA ? 0 : a.nrhs) << 16);
+        vT = a.T;
+    }
     if (is_vec(C.kind)) {
         VecArgs v;
         std::memcpy(&v, scalars, sizeof(v));
@@ -1694,7 +1731,55 @@ size_t b3t_ir_work_elems(int32_t T, int32_t b, int32_t nrhs) {
 struct IrHandles {
     std::vector<b3t_handle> hl, hx, hr, hz, hu;
     b3t_handle ha, hxp, hrp, hbp, he, hzp;
+    // sliced residual: the T x T A slice parts and the T X slice parts
+    std::vector<b3t_handle> has, hxs;
+    b3t_handle hasp = -1, hxsp = -1;
 };
+
+// Slice area of the sliced refinement: [T*T A slice parts][T X slice parts],
+// the second region 256-byte aligned.
+static size_t sl_x_off(int32_t T, int32_t b) {
+    const size_t n = (size_t)T * T * (size_t)sl_a_part_bytes(b);
+    return (n + 255) / 256 * 256;
+}
+
+size_t b3t_ir_slice_bytes(int32_t T, int32_t b) {
+    if (T <= 0 || T > 4096 || b < 128 || b > 4096 || b % 128) return 0;
+    return sl_x_off(T, b) + (size_t)T * (size_t)sl_x_part_bytes(b);
+}
+
+size_t b3t_slice_a_part_bytes(int32_t b) {
+    return (b < 128 || b > 4096 || b % 128) ? 0 : (size_t)sl_a_part_bytes(b);
+}
+
+size_t b3t_slice_x_part_bytes(int32_t b) {
+    return (b < 128 || b > 4096 || b % 128) ? 0 : (size_t)sl_x_part_bytes(b);
+}
+
+// Register ptr as nparts byte parts of part_bytes (reusing an existing
+// registration of the same shape).
+static int reg_byte_parts(b3t_ctx *c, void *ptr, int32_t nparts, size_t part_bytes, b3t_handle *parent,
+                          std::vector<b3t_handle> &parts) {
+    int rc = b3t_data_lookup(c, ptr, parent);
+    if (rc == -ENOENT) rc = b3t_data_register(c, ptr, (size_t)nparts * part_bytes, 1, 0, parent);
+    if (rc) return rc;
+    Handle &H = c->handles[*parent];
+    if (H.elemsize != 1) return -EINVAL;
+    if (H.parts.empty()) {
+        if (H.nelems < (size_t)nparts * part_bytes) return -EINVAL;
+        parts.resize(nparts);
+        return b3t_data_partition(c, *parent, nparts, part_bytes, parts.data());
+    }
+    if ((int32_t)H.parts.size() != nparts || c->handles[H.parts[0]].nelems != part_bytes) return -EINVAL;
+    parts = H.parts;
+    return 0;
+}
+
+static int ir_register_slices(b3t_ctx *c, unsigned char *S, int32_t T, int32_t b, IrHandles &H) {
+    int rc = reg_byte_parts(c, S, T * T, (size_t)sl_a_part_bytes(b), &H.hasp, H.has);
+    if (!rc) rc = reg_byte_parts(c, S + sl_x_off(T, b), T, (size_t)sl_x_part_bytes(b), &H.hxsp, H.hxs);
+    return rc;
+}
 
 static std::vector<double *> ir_u_tiles(double *R, int32_t T, int32_t b, int32_t nrhs) {
     std::vector<double *> u(T);
@@ -1742,12 +1827,16 @@ int b3t_ir_release(b3t_ctx *c, double *R, int32_t T, int32_t b, int32_t nrhs) {
 
 // One refinement step: [first: r = b, U_k = L_kk^{-T}]; d = (L L^T)^{-1} r
 // (with the inverted diagonal tiles); x (+)= d; r = b - A x; eta.
+// With slices (H.hasp >= 0) the residual r = b - A x is RESID_SL: the first
+// step slices every stored tile of A (SLICE_A), every step slices x
+// (SLICE_X) and forms r on the tensor cores.
 static int ir_step(b3t_ctx *c, IrHandles &H, int32_t T, int32_t b, int32_t nrhs, int32_t flags, bool first) {
     b3t_codelet cres, cax, cnrm;
     int rc;
     if ((rc = kind_codelet(c, kResid, &cres)) || (rc = kind_codelet(c, kAxpy, &cax)) ||
         (rc = kind_codelet(c, kNrm, &cnrm)))
         return rc;
+    const bool sliced = H.hasp >= 0;
     auto resid = [&](int32_t fl) -> int {
         for (int32_t i = 0; i < T; ++i) {
             VecArgs v{nrhs, fl, i, T, b};
@@ -1759,14 +1848,39 @@ static int ir_step(b3t_ctx *c, IrHandles &H, int32_t T, int32_t b, int32_t nrhs,
     };
     if (first && (rc = resid(kVecAssign))) return rc;          // r_0 = b (x_0 = 0)
     if (first && (rc = submit_inv(c, H.hl, H.hu, T))) return rc;   // U_k = L_kk^{-T}, kept for later steps
+    if (first && sliced) {                                     // slices of A, kept for later steps
+        b3t_codelet csa;
+        if ((rc = kind_codelet(c, kSliceA, &csa))) return rc;
+        for (int32_t j = 0; j < T; ++j)
+            for (int32_t i = j; i < T; ++i) {
+                const SliceArgs a{i, j, T, b, nrhs};
+                const b3t_handle h3[3] = {H.ha, H.has[(size_t)i * T + j], H.has[(size_t)j * T + i]};
+                if ((rc = submit_impl(c, csa, h3, nullptr, 3, &a, sizeof(a)))) return rc;
+            }
+    }
     if ((rc = submit_solve_inv(c, H.hl, H.hu, H.hr, H.hz, T, b, nrhs, flags))) return rc;
     for (int32_t i = 0; i < T; ++i) {
         VecArgs v{nrhs, first ? kVecAssign : 0, i, T, b};
         const b3t_handle h2[2] = {H.hx[i], H.hr[i]};
         if ((rc = submit_impl(c, cax, h2, nullptr, 2, &v, sizeof(v)))) return rc;
     }
-    // the |A| row sums are formed by the first step's residual and kept
-    if ((rc = resid(first ? 0 : kVecKeepNorm))) return rc;
+    if (sliced) {
+        b3t_codelet csx, crs;
+        if ((rc = kind_codelet(c, kSliceX, &csx)) || (rc = kind_codelet(c, kResidSl, &crs))) return rc;
+        for (int32_t j = 0; j < T; ++j) {
+            const SliceArgs a{j, 0, T, b, nrhs};
+            const b3t_handle h2[2] = {H.hx[j], H.hxs[j]};
+            if ((rc = submit_impl(c, csx, h2, nullptr, 2, &a, sizeof(a)))) return rc;
+        }
+        for (int32_t i = 0; i < T; ++i) {
+            const SliceArgs a{i, 0, T, b, nrhs};
+            const b3t_handle h4[4] = {H.hasp, H.hxsp, H.hbp, H.hr[i]};
+            if ((rc = submit_impl(c, crs, h4, nullptr, 4, &a, sizeof(a)))) return rc;
+        }
+    } else if ((rc = resid(first ? 0 : kVecKeepNorm))) {
+        // the |A| row sums are formed by the first step's residual and kept
+        return rc;
+    }
     VecArgs v{nrhs, 0, 0, T, b};
     const b3t_handle h3[3] = {H.hrp, H.hbp, H.he};
     return submit_impl(c, cnrm, h3, nullptr, 3, &v, sizeof(v));
@@ -1781,6 +1895,9 @@ int b3t_ir_step_submit(b3t_ctx *c, const double *A, double *const *L, const doub
     return rc ? rc : ir_step(c, H, T, b, nrhs, flags, first != 0);
 }
 
+static int ir_loop(b3t_ctx *c, IrHandles &H, double *eta, int32_t T, int32_t b, int32_t nrhs, int32_t flags,
+                   double tol, int32_t max_iter, int32_t *iters, double *eta_out);
+
 int b3t_ir_solve(b3t_ctx *c, const double *A, double *const *L, const double *B, double *X, double *R,
                  double *eta, int32_t T, int32_t b, int32_t nrhs, int32_t flags, double tol, int32_t max_iter,
                  int32_t *iters, double *eta_out) {
@@ -1792,6 +1909,31 @@ int b3t_ir_solve(b3t_ctx *c, const double *A, double *const *L, const double *B,
     IrHandles H;
     int rc = ir_register(c, A, L, B, X, R, eta, T, b, nrhs, H);
     if (rc) return rc;
+    return ir_loop(c, H, eta, T, b, nrhs, flags, tol, max_iter, iters, eta_out);
+}
+
+int b3t_ir_solve_sliced(b3t_ctx *c, const double *A, double *const *L, const double *B, double *X, double *R,
+                        void *S, double *eta, int32_t T, int32_t b, int32_t nrhs, int32_t flags, double tol,
+                        int32_t max_iter, int32_t *iters, double *eta_out) {
+    if (!c || !A || !L || !B || !X || !R || !S || !eta || T <= 0 || T > 4096 || b < 128 || b > 4096 ||
+        b % 128 || nrhs < 1 || nrhs > kSlNp || max_iter < 1 || c->capturing || (uintptr_t)S % 256)
+        return -EINVAL;
+    if (c->cfg.host_only) return -ENODEV;
+    if (c->st.open) return -EBUSY;
+    IrHandles H;
+    int rc = ir_register(c, A, L, B, X, R, eta, T, b, nrhs, H);
+    if (!rc) rc = ir_register_slices(c, (unsigned char *)S, T, b, H);
+    if (!rc) rc = ir_loop(c, H, eta, T, b, nrhs, flags, tol, max_iter, iters, eta_out);
+    // the slices are the call's own: forget them once every task is done
+    const int rw = wait_impl(c, 0);
+    if (H.hasp >= 0) drop_handle(c, H.hasp);
+    if (H.hxsp >= 0) drop_handle(c, H.hxsp);
+    return rc ? rc : rw;
+}
+
+static int ir_loop(b3t_ctx *c, IrHandles &H, double *eta, int32_t T, int32_t b, int32_t nrhs, int32_t flags,
+                   double tol, int32_t max_iter, int32_t *iters, double *eta_out) {
+    int rc;
     std::vector<double> host(nrhs + 1, 0.0);
     double prev = 0.0;
     for (int32_t it = 1; it <= max_iter; ++it) {

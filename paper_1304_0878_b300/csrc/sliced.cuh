@@ -1,0 +1,437 @@
+// Sliced FP64 residual: R_i = B_i - (A X)_i with the products on the tcgen05
+// tensor cores (the Ozaki scheme: Ozaki, Ogita, Oishi and Rump, "Error-free
+// transformations of matrix multiplication by using fast routines of matrix
+// multiplication and its applications", Numer. Algorithms 59, 2012).
+//
+// Every value of a block with scale exponent e (|v| < 2^(e-2): the tile of A,
+// or one right-hand side of a part of X) becomes the integer
+// V = trunc(v 2^(60-e)), |V| < 2^58, written in twelve balanced base-32
+// digits d_s in [-16, 15] (V = sum_s d_s 32^(11-s)); every digit is an exact
+// E4M3 value, so slice s of a block is an E4M3 matrix.  The product of a tile
+// and a part is
+//   sum_{s,t} 2^(eA + eX - 5 (s + t + 2)) A_s X_t,
+// of which the pairs with m = s + t <= 11 are kept.  One MMA chain per group
+// m sums its pairs' products (integers of magnitude <= 256) in a binary32
+// accumulator: at most 12 pairs x b terms, below 2^24, so the sums are exact.
+// The twelve group sums of a tile are combined in 64-bit integers,
+//   H = sum_{m<6} G_m 32^(5-m),  L = sum_{m>=6} G_m 32^(11-m)  (|H|, |L| < 2^50),
+// and added to the FP64 accumulator as H 2^(eA+eX-35) + L 2^(eA+eX-65): two
+// roundings per tile, the only ones besides the final B - AX.  Error per
+// product term (the truncation of both values and the dropped pairs):
+// below 2^(eA+eX-58.3).
+//
+//   SLICE_A   one stored lower tile (i, j) -> the slices of its uses: A_ij
+//             (rows of block i, K = its columns) and A_ij^T (rows of block
+//             j); a diagonal tile has the one symmetric use.  Also the row
+//             sums of |A_IJ| per use (for ||A||_inf) and the scale exponent.
+//   SLICE_X   part J of X -> its slices (16 right-hand sides, zero padded),
+//             one exponent per right-hand side, max|x| per 16-row group.
+//   RESID_SL  128 rows of R_i: thread 0 streams A slice chunks (16 KiB,
+//             bulk copies into a kSlStages ring) and the X slices of each
+//             K-chunk (24 KiB, two slots) and issues the MMAs (M = 128,
+//             N = 16, K = 32) into twelve group accumulators per tile, in
+//             two tensor-memory buffers; warps 4-7 read a finished tile's
+//             groups (one row per thread), combine them and accumulate in
+//             FP64 while the next tile's MMAs run.  Then R_i = B_i - acc and
+//             the per-16-row maxima that NRM reads (the RESID part layout).
+#pragma once
+#include <cuda_fp8.h>
+#include "b3t_internal.h"
+#include "mx.cuh"
+#include "solve.cuh"
+
+namespace b3t {
+
+// record packing: n = b, aux = i | j << 16, scal = T | nrhs << 16
+__device__ __forceinline__ int sl_i(const TaskRec &t) { return t.aux & 0xffff; }
+__device__ __forceinline__ int sl_j(const TaskRec &t) { return (t.aux >> 16) & 0xffff; }
+__device__ __forceinline__ int sl_T(const TaskRec &t) { return (int)(t.scal & 0xffff); }
+__device__ __forceinline__ int sl_nrhs(const TaskRec &t) { return (int)(t.scal >> 16); }
+
+constexpr int kSlStages = 7;                         // A chunk ring
+constexpr uint32_t kSlXSet = kSlDigits * kSlXChunk;  // X slices of one K-chunk (24 KiB)
+constexpr uint32_t kSlXOff = 0;                      // two X slots
+constexpr uint32_t kSlAOff = 2 * kSlXSet;            // then the A ring (7 x 16 KiB)
+static_assert(kSlAOff + kSlStages * kSlChunk <= 160 * 1024, "RESID_SL stages fit the MX data area");
+// 16 (32^12 - 1) / 31: adds 16 to every base-32 digit, so that the balanced
+// digits of V are the plain digits of V + kSlBias, minus 16
+constexpr unsigned long long kSlBias = 595056260442243600ull;
+
+// Scale exponent of a block with max |v| = amax: |v| < 2^(e-2); 0 if amax = 0.
+__device__ __forceinline__ int sl_exp(double amax) {
+    if (!(amax > 0.0)) return 0;
+    return ilogb(amax) + 3;
+}
+
+// V + kSlBias for one value (V = trunc(v 2^(60-e)) from the significand;
+// zeros and subnormals give V = 0).
+__device__ __forceinline__ unsigned long long sl_u(double v, int e) {
+    const long long bits = __double_as_longlong(v);
+    const int E = (int)((bits >> 52) & 0x7ff);
+    long long V = 0;
+    if (E != 0) {
+        const long long m = (bits & 0x000fffffffffffffll) | 0x0010000000000000ll;
+        int sh = E - 1015 - e;                   // <= 5 when |v| < 2^(e-2)
+        if (sh > 5) sh = 5;
+        if (sh >= 0) V = m << sh;
+        else if (sh > -64) V = m >> (-sh);
+        if (bits < 0) V = -V;
+    }
+    return (unsigned long long)(V + (long long)kSlBias);
+}
+
+// Four digits (shift sh picks the slice) -> four E4M3 bytes, K ascending.
+__device__ __forceinline__ uint32_t sl_pack4(const unsigned long long *u, int sh) {
+    float2 a, c;
+    a.x = (float)((int)((u[0] >> sh) & 31ull) - 16);
+    a.y = (float)((int)((u[1] >> sh) & 31ull) - 16);
+    c.x = (float)((int)((u[2] >> sh) & 31ull) - 16);
+    c.y = (float)((int)((u[3] >> sh) & 31ull) - 16);
+    const uint32_t lo = __nv_cvt_float2_to_fp8x2(a, __NV_SATFINITE, __NV_E4M3);
+    const uint32_t hi = __nv_cvt_float2_to_fp8x2(c, __NV_SATFINITE, __NV_E4M3);
+    return lo | (hi << 16);
+}
+
+// Store the twelve slices of 16 values (one 16-byte group of a chunk row).
+__device__ __forceinline__ void sl_store16(unsigned char *dst, size_t slice_stride, const unsigned long long *u) {
+#pragma unroll
+    for (int s = 0; s < kSlDigits; ++s) {
+        const int sh = 5 * (kSlDigits - 1 - s);
+        uint4 w;
+        w.x = sl_pack4(u, sh);
+        w.y = sl_pack4(u + 4, sh);
+        w.z = sl_pack4(u + 8, sh);
+        w.w = sl_pack4(u + 12, sh);
+        *reinterpret_cast<uint4 *>(dst + (size_t)s * slice_stride) = w;
+    }
+}
+
+// 2^k as a double (k may be below the normal range).
+__device__ __forceinline__ double sl_pow2(int k) {
+    if (k >= -1022 && k <= 1023) return __longlong_as_double((long long)(k + 1023) << 52);
+    return ldexp(1.0, k);
+}
+
+__device__ __noinline__ void slice_a_item(const TaskRec &t, double *red, int *s_e) {
+    const int b = (int)t.n, T = sl_T(t), i = sl_i(t), j = sl_j(t);
+    const double *A = (const double *)t.buf[0] + (size_t)ptile(i, j, T) * b * b;
+    unsigned char *D = (unsigned char *)t.buf[1];     // use (i, j)
+    unsigned char *Dt = (unsigned char *)t.buf[2];    // use (j, i); D itself on the diagonal
+    const bool diag = i == j;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nk = b / 128;
+    const size_t sbytes = (size_t)kSlDigits * b * b;
+    double *Pd = (double *)(D + sbytes), *Pt = (double *)(Dt + sbytes);
+    // element (r, c) of the use (i, j): the stored tile, or on the diagonal
+    // the symmetric tile from its lower triangle
+    auto at = [&](int r, int c) -> double {
+        return (!diag || r >= c) ? A[(size_t)r + (size_t)c * b] : A[(size_t)c + (size_t)r * b];
+    };
+    // row sums of |A_ij| (c ascending) and the tile's maximum
+    double mx = 0.0;
+    for (int r = tid; r < b; r += kThreads) {
+        double s = 0.0;
+        for (int c = 0; c < b; ++c) {
+            const double a = fabs(at(r, c));
+            s += a;
+            mx = fmax(mx, a);
+        }
+        Pd[r] = s;
+    }
+    // column sums of |A_ij| = row sums of the use (j, i): a warp per column,
+    // lane partials over rows lane, lane + 32, ..., then a fixed shuffle tree
+    if (!diag) {
+        for (int c = warp; c < b; c += kThreads / 32) {
+            double s = 0.0;
+            for (int r = lane; r < b; r += 32) s += fabs(A[(size_t)r + (size_t)c * b]);
+#pragma unroll
+            for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) Pt[c] = s;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) red[warp] = mx;
+    __syncthreads();
+    if (tid == 0) {
+        double m = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) m = fmax(m, red[w]);
+        *s_e = sl_exp(m);
+    }
+    __syncthreads();
+    const int e = *s_e;
+    // use (i, j): unit = (row r, 16-column group g16), consecutive threads on
+    // consecutive rows (coalesced reads of the column-major tile)
+    for (int u0 = tid; u0 < b * (b / 16); u0 += kThreads) {
+        const int r = u0 % b, g16 = u0 / b;
+        unsigned long long u[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) u[k] = sl_u(at(r, 16 * g16 + k), e);
+        const int rb = r >> 7, rr = r & 127, kc = g16 >> 3, g = g16 & 7;
+        sl_store16(D + (size_t)(rb * nk + kc) * kSlDigits * kSlChunk + (size_t)rr * 128 + ((g ^ (rr & 7)) << 4),
+                   kSlChunk, u);
+    }
+    // use (j, i): row c of A_ij^T is column c of the tile; unit = (c, 16-row
+    // group), a thread reads 16 consecutive doubles
+    if (!diag) {
+        for (int u0 = tid; u0 < b * (b / 16); u0 += kThreads) {
+            const int c = u0 / (b / 16), g16 = u0 % (b / 16);
+            unsigned long long u[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) u[k] = sl_u(A[(size_t)(16 * g16 + k) + (size_t)c * b], e);
+            const int rb = c >> 7, rr = c & 127, kc = g16 >> 3, g = g16 & 7;
+            sl_store16(Dt + (size_t)(rb * nk + kc) * kSlDigits * kSlChunk + (size_t)rr * 128 + ((g ^ (rr & 7)) << 4),
+                       kSlChunk, u);
+        }
+    }
+    if (tid == 0) {
+        int *ed = (int *)(D + sbytes + 8 * (size_t)b);
+        ed[0] = e; ed[1] = 0; ed[2] = 0; ed[3] = 0;
+        if (!diag) {
+            int *et = (int *)(Dt + sbytes + 8 * (size_t)b);
+            et[0] = e; et[1] = 0; et[2] = 0; et[3] = 0;
+        }
+    }
+}
+
+__device__ __noinline__ void slice_x_item(const TaskRec &t, int *s_ex) {
+    const int b = (int)t.n, nrhs = sl_nrhs(t);
+    const double *X = (const double *)t.buf[0];
+    unsigned char *D = (unsigned char *)t.buf[1];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const size_t sbytes = (size_t)kSlDigits * (b / 128) * kSlXChunk;
+    int *ex = (int *)(D + sbytes);
+    double *xm = (double *)(D + sbytes + 64);         // [b / 16][kSlNp]
+    // a warp per right-hand side: max |x| per 16-row group and over the part
+    for (int c = warp; c < kSlNp; c += kThreads / 32) {
+        double m = 0.0;
+        for (int r0 = 0; r0 < b; r0 += 32) {
+            double v = c < nrhs ? fabs(X[(size_t)c * b + r0 + lane]) : 0.0;
+#pragma unroll
+            for (int o = 8; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+            if ((lane & 15) == 0) xm[(size_t)((r0 + lane) >> 4) * kSlNp + c] = v;
+            m = fmax(m, v);
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) s_ex[c] = sl_exp(m);
+    }
+    __syncthreads();
+    // unit = (right-hand side n, 16-row group): 16 consecutive doubles
+    for (int u0 = tid; u0 < kSlNp * (b / 16); u0 += kThreads) {
+        const int n = u0 / (b / 16), g16 = u0 % (b / 16);
+        const int e = s_ex[n];
+        unsigned long long u[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) u[k] = n < nrhs ? sl_u(X[(size_t)n * b + 16 * g16 + k], e) : kSlBias;
+        const int kc = g16 >> 3, g = g16 & 7;
+        sl_store16(D + (size_t)kc * kSlDigits * kSlXChunk + (size_t)n * 128 + ((g ^ (n & 7)) << 4), kSlXChunk, u);
+    }
+    if (tid < kSlNp) ex[tid] = s_ex[tid];
+}
+
+// Instruction descriptor: f32 accumulate, E4M3 A and B, K-major, M = 128, N = 16.
+__host__ __device__ constexpr uint32_t sl_idesc() {
+    return (1u << 4) | ((uint32_t)kSlNp >> 3 << 17) | ((128u >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Per-CTA pipeline state of RESID_SL, persistent across items.
+struct SlState {
+    uint64_t *full, *empty;     // [kSlStages] A chunk ring
+    uint64_t *xfull, *xempty;   // [2] X slots
+    uint64_t *done, *tfree;     // [2] accumulator buffers: MMAs finished / read out
+    uint64_t *drain;            // [1] after a failed wait: every MMA issued has finished
+    uint32_t fa, fx;            // A / X fills so far (thread 0)
+    uint32_t nj;                // tiles accumulated so far (every thread)
+};
+constexpr int kSlBars = 2 * kSlStages + 2 + 2 + 2 + 2 + 1;
+
+// Returns 0, or ETIMEDOUT when a pipeline wait ran out (block-wide).
+__device__ __noinline__ int resid_sl_item(const TaskRec &t, int item, SlState &st, unsigned char *smem,
+                                             uint32_t tmem, int64_t limit_ns, int *s_fail) {
+    const int b = (int)t.n, T = sl_T(t), nrhs = sl_nrhs(t), i = sl_i(t), rb = item;
+    const int nk = b / 128;
+    const size_t PB = (size_t)sl_a_part_bytes(b), XB = (size_t)sl_x_part_bytes(b);
+    const size_t a_sbytes = (size_t)kSlDigits * b * b, x_sbytes = (size_t)kSlDigits * nk * kSlXChunk;
+    const unsigned char *AS = (const unsigned char *)t.buf[0];
+    const unsigned char *XS = (const unsigned char *)t.buf[1];
+    const double *B = (const double *)t.buf[2];
+    double *Rp = (double *)t.buf[3];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t Q = (uint32_t)T * nk * kSlDigits;    // steps: (J, kc, s)
+    if (tid == 0) *s_fail = 0;
+    __syncthreads();
+    bool ok = true;
+    if (tid == 0) {
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        uint32_t issued = 0, consumed = 0, xissued = 0, xconsumed = 0;
+        // fill of step q: first, for s = 0, the X slices of (J, kc)
+        auto issue = [&](uint32_t q) -> bool {
+            const uint32_t s = q % kSlDigits, jk = q / kSlDigits, J = jk / nk, kc = jk % nk;
+            if (s == 0) {
+                const uint32_t gx = st.fx + jk, xs = gx & 1;
+                if (gx >= 2 && !mbar_wait(&st.xempty[xs], ((gx >> 1) - 1) & 1, limit_ns)) return false;
+                mbar_expect_tx(&st.xfull[xs], kSlXSet);
+                bulk_g2s(smem + kSlXOff + xs * kSlXSet, XS + (size_t)J * XB + (size_t)kc * kSlXSet, kSlXSet,
+                         &st.xfull[xs]);
+                ++xissued;
+            }
+            const uint32_t ga = st.fa + q, slot = ga % kSlStages;
+            if (ga >= (uint32_t)kSlStages && !mbar_wait(&st.empty[slot], ((ga / kSlStages) - 1) & 1, limit_ns))
+                return false;
+            mbar_expect_tx(&st.full[slot], kSlChunk);
+            bulk_g2s(smem + kSlAOff + slot * kSlChunk,
+                     AS + ((size_t)i * T + J) * PB + ((size_t)(rb * nk + kc) * kSlDigits + s) * kSlChunk, kSlChunk,
+                     &st.full[slot]);
+            return true;
+        };
+        const uint32_t idesc = sl_idesc();
+        for (uint32_t J = 0; J < (uint32_t)T && ok; ++J) {
+            const uint32_t jt = st.nj + J, buf = jt & 1;
+            // the buffer is free once the epilogue of tile jt - 2 has read it
+            if (jt >= 2 && !mbar_wait(&st.tfree[buf], ((jt >> 1) - 1) & 1, limit_ns)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t dbase = tmem + buf * (kSlGroups * kSlNp);
+            for (uint32_t kc = 0; kc < (uint32_t)nk && ok; ++kc) {
+                for (uint32_t s = 0; s < (uint32_t)kSlDigits; ++s) {
+                    const uint32_t q = (J * nk + kc) * kSlDigits + s;
+                    // fills run kSlStages - 1 steps ahead: refilling a slot waits
+                    // for the MMAs of two steps back, not of the previous one
+                    while (issued < Q && issued < q + kSlStages - 1) {
+                        if (!issue(issued)) { ok = false; break; }
+                        ++issued;
+                    }
+                    if (!ok) break;
+                    const uint32_t ga = st.fa + q, slot = ga % kSlStages;
+                    const uint32_t gx = st.fx + J * nk + kc, xs = gx & 1;
+                    if (s == 0) {
+                        if (!mbar_wait(&st.xfull[xs], (gx >> 1) & 1, limit_ns)) { ok = false; break; }
+                        ++xconsumed;
+                    }
+                    if (!mbar_wait(&st.full[slot], (ga / kSlStages) & 1, limit_ns)) { ok = false; break; }
+                    ++consumed;
+                    tc_fence_after();
+                    const uint64_t ad = sw128_desc(smem_u32(smem + kSlAOff + slot * kSlChunk));
+                    const uint32_t sx = smem_u32(smem + kSlXOff + xs * kSlXSet);
+                    for (uint32_t tt = 0; tt + s < (uint32_t)kSlGroups; ++tt) {
+                        const uint64_t bd = sw128_desc(sx + tt * kSlXChunk);
+                        const uint32_t d = dbase + (s + tt) * kSlNp;
+#pragma unroll
+                        for (uint32_t k4 = 0; k4 < 4; ++k4)
+                            mma_e4m3(d, ad + 2 * k4, bd + 2 * k4, idesc, (kc | s | k4) ? 1u : 0u);
+                    }
+                    mma_commit(&st.empty[slot]);
+                    if (s == kSlDigits - 1) mma_commit(&st.xempty[xs]);
+                }
+            }
+            if (ok) mma_commit(&st.done[buf]);
+        }
+        if (!ok) {
+            *s_fail = 1;
+            // copies in flight land, and every MMA issued finishes, before the
+            // shared and tensor memory are given up
+            for (uint32_t q = consumed; q < issued; ++q) {
+                const uint32_t ga = st.fa + q;
+                mbar_wait(&st.full[ga % kSlStages], (ga / kSlStages) & 1, limit_ns);
+            }
+            for (uint32_t x = xconsumed; x < xissued; ++x) {
+                const uint32_t gx = st.fx + x;
+                mbar_wait(&st.xfull[gx & 1], (gx >> 1) & 1, limit_ns);
+            }
+            mma_commit(st.drain);
+            mbar_wait(st.drain, 0, limit_ns);
+        }
+        st.fa += issued;
+        st.fx += xissued;
+    } else if (warp >= 4) {
+        const int q = warp & 3, row = 32 * q + lane;        // TMEM lane = row of the item
+        const int gr = rb * kSlRows + row;                   // row within part i
+        double acc[kSlNp];
+#pragma unroll
+        for (int c = 0; c < kSlNp; ++c) acc[c] = 0.0;
+        for (int J = 0; J < T; ++J) {
+            const uint32_t jt = st.nj + J, buf = jt & 1;
+            const int ea = *(const int *)(AS + ((size_t)i * T + J) * PB + a_sbytes + 8 * (size_t)b);
+            const int *ex = (const int *)(XS + (size_t)J * XB + x_sbytes);
+            if (ok && !mbar_wait(&st.done[buf], (jt >> 1) & 1, limit_ns)) ok = false;
+            if (ok) {
+                tc_fence_after();
+                const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16) + buf * (kSlGroups * kSlNp);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    long long Hs[8], Ls[8];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) { Hs[c] = 0; Ls[c] = 0; }
+#pragma unroll
+                    for (int m = 0; m < kSlGroups; ++m) {
+                        float v[8];
+                        tmem_ld8(tb + m * kSlNp + 8 * h, v);
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            const long long g = (long long)__float2int_rz(v[c]);
+                            if (m < 6) Hs[c] += g << (5 * (5 - m));
+                            else Ls[c] += g << (5 * (11 - m));
+                        }
+                    }
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const int e = ea + ex[8 * h + c];
+                        acc[8 * h + c] = fma((double)Hs[c], sl_pow2(e - 35), acc[8 * h + c]);
+                        acc[8 * h + c] = fma((double)Ls[c], sl_pow2(e - 65), acc[8 * h + c]);
+                    }
+                }
+                tc_fence_before();
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&st.tfree[buf]);
+        }
+        // R_i = B_i - acc and the per-16-row maxima of the RESID part layout
+        const double *Bi = B + (size_t)i * b * nrhs;
+        double *Rn = Rp + (size_t)b * nrhs;
+        const int nit = b / kResidRows, it16 = gr >> 4;
+        double rs = 0.0;
+        for (int J = 0; J < T; ++J) rs += ((const double *)(AS + ((size_t)i * T + J) * PB + a_sbytes))[gr];
+        const double *xmax = (const double *)(XS + (size_t)i * XB + x_sbytes + 64);
+#pragma unroll
+        for (int c = 0; c < kSlNp; ++c) {
+            if (c < nrhs) {
+                const double bv = Bi[(size_t)c * b + gr];
+                const double r = bv - acc[c];
+                Rp[(size_t)c * b + gr] = r;
+                double mr = fabs(r), mb = fabs(bv);
+#pragma unroll
+                for (int o = 8; o; o >>= 1) {
+                    mr = fmax(mr, __shfl_xor_sync(0xffffffffu, mr, o));
+                    mb = fmax(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+                }
+                if ((lane & 15) == 0) {
+                    Rn[(size_t)it16 * nrhs + c] = mr;
+                    Rn[(size_t)nit * nrhs + (size_t)it16 * nrhs + c] = xmax[(size_t)it16 * kSlNp + c];
+                    Rn[(size_t)2 * nit * nrhs + (size_t)it16 * nrhs + c] = mb;
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 8; o; o >>= 1) rs = fmax(rs, __shfl_xor_sync(0xffffffffu, rs, o));
+        if ((lane & 15) == 0) Rn[(size_t)3 * nit * nrhs + it16] = rs;
+    }
+    st.nj += (uint32_t)T;
+    if (__syncthreads_or(*s_fail || !ok)) return ETIMEDOUT;
+    return 0;
+}
+
+}  // namespace b3t

@@ -1,0 +1,221 @@
+"""The sliced FP64 residual on the device (GPU): the slices SLICE_A and
+SLICE_X write are the host restatement's digits bit for bit (every value's
+integer V, the scale exponents, the row sums of |A| and the max|x| the norm
+uses); RESID_SL's residual and its per-16-row maxima equal the host
+restatement of the same arithmetic (tests/sliced_ref.py) bit for bit and lie
+within the a-priori bound of the exact residual; the sliced refinement
+reaches the same backward error as the FP64 one."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+import paper_1304_0878_b300 as b3t
+from paper_1304_0878_b300 import tiles as dt
+from oracle import cholesky as och
+import sliced_ref as sr
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="no CUDA device")]
+R, W = 1, 2
+
+
+def e4m3_ints(raw):
+    v = torch.from_numpy(np.ascontiguousarray(raw)).view(torch.float8_e4m3fn).to(torch.float32).numpy()
+    return v.astype(np.int64)
+
+
+def decode_a_part(p, b):
+    """A slice part -> (digits (12, b, b), row sums (b), exponent)."""
+    nk = b // 128
+    vals = e4m3_ints(p[:12 * b * b]).reshape(nk, nk, 12, 128, 8, 16)
+    rows = np.arange(128)
+    out = np.empty((12, b, b), dtype=np.int64)
+    for g in range(8):
+        grp = vals[:, :, :, rows, g ^ (rows % 8), :]          # (nk, nk, 12, 128, 16)
+        for rb in range(nk):
+            for kc in range(nk):
+                out[:, rb * 128:(rb + 1) * 128, kc * 128 + 16 * g:kc * 128 + 16 * g + 16] = grp[rb, kc]
+    o = 12 * b * b
+    P = p[o:o + 8 * b].view(np.float64)
+    e = int(p[o + 8 * b:o + 8 * b + 4].view(np.int32)[0])
+    return out, P, e
+
+
+def decode_x_part(p, b):
+    """X slice part -> (digits (12, 16, b), exponents (16), max|x| (b/16, 16))."""
+    nk = b // 128
+    vals = e4m3_ints(p[:12 * nk * 2048]).reshape(nk, 12, 16, 8, 16)
+    rows = np.arange(16)
+    out = np.empty((12, 16, b), dtype=np.int64)
+    for g in range(8):
+        grp = vals[:, :, rows, g ^ (rows % 8), :]            # (nk, 12, 16, 16)
+        for kc in range(nk):
+            out[:, :, kc * 128 + 16 * g:kc * 128 + 16 * g + 16] = grp[kc]
+    o = 12 * nk * 2048
+    ex = p[o:o + 64].view(np.int32).astype(np.int64)
+    xm = p[o + 64:o + 64 + (b // 16) * 16 * 8].view(np.float64).reshape(b // 16, 16)
+    return out, ex, xm
+
+
+def parts_from(M, b):
+    N, nrhs = M.shape
+    T = N // b
+    return torch.from_numpy(np.ascontiguousarray(M.reshape(T, b, nrhs).transpose(0, 2, 1))).cuda()
+
+
+def run_sliced(ctx, A, X, Bm, b, nrhs):
+    """SLICE_A on every stored tile, SLICE_X on every part, RESID_SL per part;
+    returns (R parts host (T, PR), AS bytes, XS bytes)."""
+    N = A.shape[0]
+    T = N // b
+    PB, XB, PR = b3t.slice_a_part_bytes(b), b3t.slice_x_part_bytes(b), b3t.resid_part_elems(b, nrhs)
+    Ap = torch.from_numpy(och.to_tiles(A, b)).cuda()
+    AS = torch.zeros(T * T * PB, dtype=torch.uint8, device="cuda")
+    XS = torch.zeros(T * XB, dtype=torch.uint8, device="cuda")
+    Xd, Bd = parts_from(X, b), parts_from(Bm, b)
+    Rd = torch.full((T, PR), float("nan"), dtype=torch.float64, device="cuda")
+    hA = ctx.data_register(Ap.data_ptr(), Ap.numel(), 8)
+    hAS = ctx.data_register(AS.data_ptr(), AS.numel(), 1)
+    pAS = ctx.data_partition(hAS, T * T, PB)
+    hXS = ctx.data_register(XS.data_ptr(), XS.numel(), 1)
+    pXS = ctx.data_partition(hXS, T, XB)
+    hX = ctx.data_register(Xd.data_ptr(), Xd.numel(), 8)
+    pX = ctx.data_partition(hX, T, b * nrhs)
+    hB = ctx.data_register(Bd.data_ptr(), Bd.numel(), 8)
+    hR = ctx.data_register(Rd.data_ptr(), Rd.numel(), 8)
+    pR = ctx.data_partition(hR, T, PR)
+    ca = ctx.task_decl("slice_a", b3t.SLICE_A, [R, W, W], 20)
+    cx = ctx.task_decl("slice_x", b3t.SLICE_X, [R, W], 20)
+    cr = ctx.task_decl("resid_sl", b3t.RESID_SL, [R, R, R, W], 20)
+    for j in range(T):
+        for i in range(j, T):
+            ctx.task_submit(ca, [hA, pAS[i * T + j], pAS[j * T + i]], b3t.slice_args(i, j, T, b, 0))
+    for J in range(T):
+        ctx.task_submit(cx, [pX[J], pXS[J]], b3t.slice_args(J, 0, T, b, nrhs))
+    for i in range(T):
+        ctx.task_submit(cr, [hAS, hXS, hB, pR[i]], b3t.slice_args(i, 0, T, b, nrhs))
+    ctx.task_wait()
+    for h in (hA, hAS, hXS, hX, hB, hR):
+        ctx.data_unregister(h)
+    return Rd.cpu().numpy(), AS.cpu().numpy(), XS.cpu().numpy()
+
+
+CASES = [(512, 128, 16), (768, 256, 5), (512, 128, 1)]
+
+
+@pytest.fixture(scope="module", params=CASES, ids=lambda c: "N%d_b%d_r%d" % c)
+def sliced_run(request):
+    N, b, nrhs = request.param
+    A = synth.spd_host(N, seed=N + nrhs, shift=0.1)
+    X = synth.rhs(N, nrhs, seed=7) * 0.5
+    X[5, 0] = 0.0
+    Bm = A @ X + 1e-4 * synth.rhs(N, nrhs, seed=8)
+    torch.cuda.set_device(0)
+    ctx = b3t.Context(stream=torch.cuda.current_stream().cuda_stream, timeout_ns=20_000_000_000)
+    try:
+        out = run_sliced(ctx, A, X, Bm, b, nrhs)
+    finally:
+        ctx.close()
+    return (N, b, nrhs, A, X, Bm) + out
+
+
+def test_a_slices_bit_exact(orc, sliced_run):
+    N, b, nrhs, A, X, Bm, Rh, AS, XS = sliced_run
+    T = N // b
+    PB = b3t.slice_a_part_bytes(b)
+    for I in range(T):
+        for J in range(T):
+            D, P, e = decode_a_part(AS[(I * T + J) * PB:(I * T + J + 1) * PB], b)
+            Au = sr.use_tile(A, I, J, b)
+            e0 = sr.scale_exp(float(np.max(np.abs(Au))))
+            assert e == e0, (I, J)
+            assert D.min() >= -16 and D.max() <= 15
+            assert np.array_equal(sr.from_digits(D), sr.to_int(Au, e0)), (I, J)
+            assert np.array_equal(P, sr.row_sums_of_use(A, I, J, b)), (I, J)
+
+
+def test_x_slices_bit_exact(orc, sliced_run):
+    N, b, nrhs, A, X, Bm, Rh, AS, XS = sliced_run
+    T = N // b
+    XB = b3t.slice_x_part_bytes(b)
+    for J in range(T):
+        D, ex, xm = decode_x_part(XS[J * XB:(J + 1) * XB], b)
+        Xj = np.zeros((b, 16))
+        Xj[:, :nrhs] = X[J * b:(J + 1) * b]
+        e0 = sr.x_exps(Xj, nrhs)
+        assert np.array_equal(ex, e0)
+        assert np.array_equal(sr.from_digits(D), sr.to_int(Xj, e0[None, :]).T)
+        want = np.max(np.abs(Xj).reshape(b // 16, 16, 16), axis=1)
+        assert np.array_equal(xm, want)
+
+
+def test_residual_bit_exact_and_within_bound(orc, sliced_run):
+    N, b, nrhs, A, X, Bm, Rh, AS, XS = sliced_run
+    T = N // b
+    PR = b3t.resid_part_elems(b, nrhs)
+    Rref, eA, eX = sr.resid_sliced(A, X, Bm, b, nrhs)
+    got = Rh[:, :b * nrhs].reshape(T, nrhs, b).transpose(0, 2, 1).reshape(N, nrhs)
+    assert np.array_equal(got, Rref)
+    # the per-16-row maxima NRM reads
+    nit = b // 16
+    for i in range(T):
+        Rn = Rh[i, b * nrhs:PR]
+        blk = slice(i * b, (i + 1) * b)
+        r16 = np.abs(Rref[blk]).reshape(nit, 16, nrhs).max(axis=1)
+        x16 = np.abs(X[blk]).reshape(nit, 16, nrhs).max(axis=1)
+        b16 = np.abs(Bm[blk]).reshape(nit, 16, nrhs).max(axis=1)
+        assert np.array_equal(Rn[:nit * nrhs].reshape(nit, nrhs), r16)
+        assert np.array_equal(Rn[nit * nrhs:2 * nit * nrhs].reshape(nit, nrhs), x16)
+        assert np.array_equal(Rn[2 * nit * nrhs:3 * nit * nrhs].reshape(nit, nrhs), b16)
+        rs = np.zeros(b)
+        for J in range(T):
+            rs = rs + sr.row_sums_of_use(A, i, J, b)
+        assert np.array_equal(Rn[3 * nit * nrhs:], rs.reshape(nit, 16).max(axis=1))
+    rows = list(range(0, N, 29)) + [N - 1]
+    Rex = sr.exact_resid_rows(A, X, Bm, rows, b)
+    assert np.all(np.abs(got[rows] - Rex) <= sr.resid_bound(eA, eX, rows, Rex, b, T, nrhs))
+
+
+@pytest.mark.parametrize("fmt", [b3t.FMT_BF16, b3t.FMT_E4M3])
+def test_sliced_refinement_matches_fp64_refinement(orc, gctx, fmt):
+    # the mixed factor refined with the FP64 residual and with the sliced
+    # one: both reach eta <= 1e-12 in the same number of steps (+-1), and the
+    # exact residual of the sliced solution meets the target
+    N, b, nrhs = 1024, 128, 16
+    T = N // b
+    A = synth.spd_host(N, seed=9, shift=0.1)
+    Bm = synth.rhs(N, nrhs, seed=4)
+    At = torch.from_numpy(och.to_tiles(A, b)).cuda()
+    Wt = At.float()
+    Lt = torch.zeros_like(At)
+    Qt = dt.q_tiles(T, b, fmt, "cuda")
+    Ut = torch.zeros((T, b, b), dtype=torch.float64, device="cuda")
+    wp, lp, qp, up = dt.tile_ptrs(Wt), dt.tile_ptrs(Lt), dt.tile_ptrs(Qt), dt.tile_ptrs(Ut)
+    gctx.cholesky_mx_inv_submit(wp, lp, qp, up, T, b, fmt)
+    gctx.task_wait()
+    Bd = parts_from(Bm, b)
+    Rw = torch.zeros(b3t.ir_work_elems(T, b, nrhs), dtype=torch.float64, device="cuda")
+    S = torch.empty(b3t.ir_slice_bytes(T, b) + 256, dtype=torch.uint8, device="cuda")
+    s_ptr = (S.data_ptr() + 255) // 256 * 256
+    eta = torch.zeros(nrhs + 1, dtype=torch.float64, device="cuda")
+    X64 = torch.zeros_like(Bd)
+    Xsl = torch.zeros_like(Bd)
+    rc1, it1, e1 = gctx.ir_solve(At.data_ptr(), lp, Bd.data_ptr(), X64.data_ptr(), Rw.data_ptr(), eta.data_ptr(),
+                                 T, b, nrhs, b3t.VEC_F32, 1e-12, 30)
+    rc2, it2, e2 = gctx.ir_solve_sliced(At.data_ptr(), lp, Bd.data_ptr(), Xsl.data_ptr(), Rw.data_ptr(), s_ptr,
+                                        eta.data_ptr(), T, b, nrhs, b3t.VEC_F32, 1e-12, 30)
+    assert rc1 == 0 and rc2 == 0, (rc1, rc2, e1[-1], e2[-1])
+    assert abs(it1 - it2) <= 1
+    assert e2[-1] <= 1e-12
+    Xh = Xsl.cpu().numpy().transpose(0, 2, 1).reshape(N, nrhs)
+    rows = list(range(0, N, 61))
+    Rex = sr.exact_resid_rows(A, Xh, Bm, rows, b)
+    anorm = np.max(np.sum(np.abs(A), axis=1))
+    eta_h = np.max(np.abs(Rex), axis=0) / (anorm * np.max(np.abs(Xh), axis=0) + np.max(np.abs(Bm), axis=0))
+    assert np.max(eta_h) <= 1e-12
+    gctx.ir_release(Rw.data_ptr(), T, b, nrhs)
+    for p in (wp, lp, qp):
+        gctx.tiles_unregister(p, T)
+    for p in up:
+        gctx.data_unregister(gctx.data_lookup(p))
