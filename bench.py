@@ -66,6 +66,8 @@ def parse():
     p.add_argument("--nrhs", type=int, default=16)
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-scipy", action="store_true", help="skip the LAPACK CPU baselines (scipy, all host cores)")
+    p.add_argument("--no-sliced-resid", action="store_true",
+                   help="time to solution: skip the refinement with the sliced FP64 residual (tensor cores)")
     p.add_argument("--mx-trsm", default="inv", choices=["inv", "subst", "both"],
                    help="mixed panel solve: product with the inverted diagonal tile (TRTRI + TRMM_MX) "
                         "or row substitution (TRSM_MX)")
@@ -78,7 +80,7 @@ def parse():
     p.add_argument("--prio", default="upward", choices=["upward", "depth"],
                    help="ready-queue order of the profiling cases (--case)")
     p.add_argument("--ctas-per-sm", type=int, default=0, help="grid of the profiling cases (0: occupancy)")
-    p.add_argument("--case", default=None, choices=["mx_gemm_bf16", "mx_gemm_e4m3", "scal", "resid", "solve_f32", "trace_mixed",
+    p.add_argument("--case", default=None, choices=["mx_gemm_bf16", "mx_gemm_e4m3", "scal", "resid", "resid_sl", "solve_f32", "trace_mixed",
                                                     "solve_f64", "empty_dags", "serve_sweep", "trace_headline", "batch"],
                    help="run one profiling case (a DAG of one task kind), or one secondary measurement alone "
                         "(empty_dags, serve_sweep, trace_headline, batch), and print its result")
@@ -472,6 +474,10 @@ def summarise(line):
             if p in tts:
                 out["time_to_solution"][p] = {k: tts[p][k] for k in ("ms", "factor_ms", "speedup_vs_fp64", "eta",
                                                                       "host_sampled_eta", "iterations")}
+                if "sliced_residual" in tts[p]:
+                    out["time_to_solution"][p]["sliced_residual"] = {
+                        k: tts[p]["sliced_residual"][k] for k in ("ms", "speedup_vs_fp64", "eta", "host_sampled_eta",
+                                                                   "iterations")}
     sv = sec.get("serving")
     if sv:
         out["serving"] = {}
@@ -614,6 +620,9 @@ def run_time_to_solution(ctx, A0, t, g64, N, b, dev, stream, args):
         return sampled_host_eta(tl, anorm, Xh, Bh, N, b)
     R = torch.zeros(b3t.ir_work_elems(T, b, nrhs), dtype=torch.float64, device=dev)
     eta = torch.zeros(nrhs + 1, dtype=torch.float64, device=dev)
+    sliced = not args.no_sliced_resid and b % 128 == 0 and nrhs <= 16
+    S = torch.empty(b3t.ir_slice_bytes(T, b) + 256, dtype=torch.uint8, device=dev) if sliced else None
+    s_ptr = (S.data_ptr() + 255) // 256 * 256 if sliced else 0
     flops = cholesky_flops(N)
     out = {"workload": "N=%d tile %d, %d right-hand sides N(0,1) seed 4, target eta <= 1e-12" % (N, b, nrhs)}
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
@@ -670,12 +679,34 @@ def run_time_to_solution(ctx, A0, t, g64, N, b, dev, stream, args):
             res.append((ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), rc, its, e[nrhs]))
         f_ms, s_ms, rc, its, em = res[-1]
         diff = float((Xm - X64).abs().max() / X64.abs().max())
+        sl = None
+        if sliced:
+            # the same factor refined with the sliced FP64 residual (SLICE_A
+            # once, then SLICE_X + RESID_SL every step, on the tensor cores)
+            Xs = torch.zeros_like(Bd)
+            sres = []
+            for rep in range(2):
+                Xs.zero_()
+                ev[2].record(stream)
+                rc2, its2, e2 = ctx.ir_solve_sliced(A0.data_ptr(), lp, Bd.data_ptr(), Xs.data_ptr(), R.data_ptr(),
+                                                    s_ptr, eta.data_ptr(), T, b, nrhs, b3t.VEC_F32, 1e-12, 30)
+                ev[3].record(stream)
+                torch.cuda.synchronize()
+                sres.append((ev[2].elapsed_time(ev[3]), rc2, its2, e2[nrhs]))
+            r_ms, rc2, its2, e2m = sres[-1]
+            sl = {"ms": f_ms + r_ms, "refine_ms": r_ms, "iterations": its2, "eta": e2m, "converged": rc2 == 0,
+                  "host_sampled_eta": host_eta(Xs),
+                  "max_rel_diff_vs_fp64_solution": float((Xs - X64).abs().max() / X64.abs().max()),
+                  "speedup_vs_fp64": out["fp64"]["ms"] / (f_ms + r_ms)}
+            del Xs
         out[name] = {"panel_solve": "TRTRI + TRMM_MX (inverted diagonal tile)" if inv else "TRSM_MX (substitution)",
                      "ms": f_ms + s_ms, "factor_ms": f_ms, "refine_ms": s_ms, "iterations": its, "eta": em,
                      "host_sampled_eta": host_eta(Xm),
                      "converged": rc == 0, "max_rel_diff_vs_fp64_solution": diff,
                      "effective_TFLOPs": flops / ((f_ms + s_ms) / 1e3) / 1e12,
                      "speedup_vs_fp64": (out["fp64"]["ms"]) / (f_ms + s_ms)}
+        if sl is not None:
+            out[name]["sliced_residual"] = sl
         ctx.graph_destroy(gm)
         ctx.tiles_unregister(qp, T)
         del Q
@@ -1056,6 +1087,8 @@ def run_case(args):
                                   b * nrhs, flags)
         g = ctx.graph_capture_end()
         work, unit = 2.0 * N * N * nrhs, "TFLOP/s"
+    elif args.case == "resid_sl":
+        return run_resid_sliced(ctx, dev, args)
     else:  # resid: one refinement residual over N = 16384, 16 rhs (FP64)
         N, nrhs = 16384, 16
         T = N // b
@@ -1086,6 +1119,79 @@ def run_case(args):
     print(json.dumps({"case": args.case, "kernel_ms": med * 1e3, "value": work / med / scale, "unit": unit,
                       "nctas": ctx.last_launch()["nctas"], "prio": args.prio}))
     ctx.graph_destroy(g)
+    ctx.close()
+
+
+def run_resid_sliced(ctx, dev, args):
+    """The refinement residual at N = 32768, tile 512, 16 rhs: the sliced
+    FP64 residual (SLICE_X + RESID_SL, one launch per step; SLICE_A once per
+    solve) against the FP64 RESID on the same inputs.  Kernel times of the
+    persistent launches (CUDA events), inputs larger than L2."""
+    import torch
+    import synth
+    import paper_1304_0878_b300 as b3t
+    N, b, nrhs = 32768, 512, 16
+    T = N // b
+    A = synth.spd_tiles_device(N, b, 3, 0.1, dev)
+    X = torch.randn((T, nrhs, b), dtype=torch.float64, device=dev)
+    B = torch.randn((T, nrhs, b), dtype=torch.float64, device=dev)
+    PR = b3t.resid_part_elems(b, nrhs)
+    PB, XB = b3t.slice_a_part_bytes(b), b3t.slice_x_part_bytes(b)
+    R = torch.zeros(T * PR, dtype=torch.float64, device=dev)
+    AS = torch.empty(T * T * PB, dtype=torch.uint8, device=dev)
+    XS = torch.empty(T * XB, dtype=torch.uint8, device=dev)
+    ha = ctx.data_register(A.data_ptr(), A.numel(), 8)
+    hx = ctx.data_register(X.data_ptr(), X.numel(), 8)
+    px = ctx.data_partition(hx, T, b * nrhs)
+    hb = ctx.data_register(B.data_ptr(), B.numel(), 8)
+    hr = ctx.data_register(R.data_ptr(), R.numel(), 8)
+    pr = ctx.data_partition(hr, T, PR)
+    has = ctx.data_register(AS.data_ptr(), AS.numel(), 1)
+    pas = ctx.data_partition(has, T * T, PB)
+    hxs = ctx.data_register(XS.data_ptr(), XS.numel(), 1)
+    pxs = ctx.data_partition(hxs, T, XB)
+    ca = ctx.task_decl("slice_a", b3t.SLICE_A, [1, 2, 2], 20)
+    cx = ctx.task_decl("slice_x", b3t.SLICE_X, [1, 2], 20)
+    cs = ctx.task_decl("resid_sl", b3t.RESID_SL, [1, 1, 1, 2], 20)
+    cr = ctx.task_decl("resid", b3t.RESID, [1, 1, 1, 2], 20)
+    graphs = {}
+    ctx.graph_capture_begin()
+    for j in range(T):
+        for i in range(j, T):
+            ctx.task_submit(ca, [ha, pas[i * T + j], pas[j * T + i]], b3t.slice_args(i, j, T, b, 0))
+    graphs["slice_a"] = ctx.graph_capture_end()
+    ctx.graph_capture_begin()
+    for J in range(T):
+        ctx.task_submit(cx, [px[J], pxs[J]], b3t.slice_args(J, 0, T, b, nrhs))
+    for i in range(T):
+        ctx.task_submit(cs, [has, hxs, hb, pr[i]], b3t.slice_args(i, 0, T, b, nrhs))
+    graphs["sliced_step"] = ctx.graph_capture_end()
+    ctx.graph_capture_begin()
+    for i in range(T):
+        ctx.task_submit(cr, [ha, hx, hb, pr[i]], b3t.vec_args(nrhs, 0, i, T, b))
+    graphs["fp64_resid"] = ctx.graph_capture_end()
+    ms = {}
+    for name in ("slice_a", "sliced_step", "fp64_resid"):
+        ts = []
+        for r in range(args.warmup + args.steps):
+            ctx.graph_replay(graphs[name])
+            ctx.task_wait()
+            if r >= args.warmup:
+                ts.append(ctx.last_launch()["kernel_ns"] / 1e6)
+        ms[name] = float(np.median(ts))
+        ctx.graph_destroy(graphs[name])
+    flops = 2.0 * N * N * nrhs
+    slice_bytes = T * T * (PB - 8 * b - 16)
+    hbm, src = hbm_peak()
+    out = {"case": "resid_sl", "workload": "r = b - A x, N=%d tile %d, %d rhs" % (N, b, nrhs),
+           "fp64_resid_ms": ms["fp64_resid"], "fp64_resid_TFLOPs": flops / ms["fp64_resid"] / 1e9,
+           "sliced_step_ms": ms["sliced_step"], "sliced_effective_TFLOPs": flops / ms["sliced_step"] / 1e9,
+           "slice_a_ms": ms["slice_a"], "speedup_per_step": ms["fp64_resid"] / ms["sliced_step"],
+           "slice_bytes_per_step": slice_bytes,
+           "roofline": {"bound": "hbm", "achieved": slice_bytes / ms["sliced_step"] / 1e6, "peak": hbm,
+                        "unit": "GB/s", "frac": slice_bytes / ms["sliced_step"] / 1e6 / hbm, "peak_source": src},
+           "nctas": ctx.last_launch()["nctas"]}
+    print(json.dumps(out))
     ctx.close()
 
 

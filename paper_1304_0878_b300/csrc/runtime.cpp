@@ -729,12 +729,27 @@ int submit_impl(b3t_ctx *c, b3t_codelet cl, const b3t_handle *handles, const uin
     // expand partitioned parents to their parts; OR the modes of repeats
     std::vector<int32_t> leaves;
     std::vector<uint8_t> lmodes;
+    size_t nleaves = 0;
+    for (int i = 0; i < nbuffers; ++i) {
+        const Handle &H = c->handles[handles[i]];
+        nleaves += H.parts.empty() ? 1 : H.parts.size();
+    }
+    // repeats are found by a scan for a few leaves, by a hash map for a
+    // partitioned parent's many parts (the first occurrence keeps its place)
+    std::unordered_map<int32_t, size_t> seen;
+    const bool many = nleaves > 32;
     for (int i = 0; i < nbuffers; ++i) {
         const Handle &H = c->handles[handles[i]];
         const uint8_t m = C.modes[i];
         auto add = [&](int32_t leaf) {
-            for (size_t k = 0; k < leaves.size(); ++k)
-                if (leaves[k] == leaf) { lmodes[k] |= m; return; }
+            if (many) {
+                auto it = seen.find(leaf);
+                if (it != seen.end()) { lmodes[it->second] |= m; return; }
+                seen.emplace(leaf, leaves.size());
+            } else {
+                for (size_t k = 0; k < leaves.size(); ++k)
+                    if (leaves[k] == leaf) { lmodes[k] |= m; return; }
+            }
             leaves.push_back(leaf);
             lmodes.push_back(m);
         };
@@ -1731,8 +1746,8 @@ size_t b3t_ir_work_elems(int32_t T, int32_t b, int32_t nrhs) {
 struct IrHandles {
     std::vector<b3t_handle> hl, hx, hr, hz, hu;
     b3t_handle ha, hxp, hrp, hbp, he, hzp;
-    // sliced residual: the T x T A slice parts and the T X slice parts
-    std::vector<b3t_handle> has, hxs;
+    // sliced residual: the A slice area (one buffer) and the T X slice parts
+    std::vector<b3t_handle> hxs;
     b3t_handle hasp = -1, hxsp = -1;
 };
 
@@ -1775,8 +1790,28 @@ static int reg_byte_parts(b3t_ctx *c, void *ptr, int32_t nparts, size_t part_byt
     return 0;
 }
 
+// Slices of A, once per solve, in a launch of their own: SLICE_A per stored
+// tile into the T x T use parts.  The finished slice area is then
+// registered again as one plain buffer, so that the residual tasks of every
+// step name one buffer instead of T x T parts (nothing writes it during the
+// refinement); the X slices keep their T parts.
 static int ir_register_slices(b3t_ctx *c, unsigned char *S, int32_t T, int32_t b, IrHandles &H) {
-    int rc = reg_byte_parts(c, S, T * T, (size_t)sl_a_part_bytes(b), &H.hasp, H.has);
+    b3t_handle hp = -1;
+    std::vector<b3t_handle> parts;
+    int rc = reg_byte_parts(c, S, T * T, (size_t)sl_a_part_bytes(b), &hp, parts);
+    b3t_codelet csa;
+    if (!rc) rc = kind_codelet(c, kSliceA, &csa);
+    for (int32_t j = 0; !rc && j < T; ++j)
+        for (int32_t i = j; !rc && i < T; ++i) {
+            const SliceArgs a{i, j, T, b, 0};
+            const b3t_handle h3[3] = {H.ha, parts[(size_t)i * T + j], parts[(size_t)j * T + i]};
+            rc = submit_impl(c, csa, h3, nullptr, 3, &a, sizeof(a));
+        }
+    const int rw = rc ? 0 : wait_impl(c, 0);
+    if (rc) wait_impl(c, 0);
+    if (hp >= 0 && c->handles[hp].alive) drop_handle(c, hp);
+    if (rc || rw) return rc ? rc : rw;
+    rc = b3t_data_register(c, S, (size_t)T * T * (size_t)sl_a_part_bytes(b), 1, 0, &H.hasp);
     if (!rc) rc = reg_byte_parts(c, S + sl_x_off(T, b), T, (size_t)sl_x_part_bytes(b), &H.hxsp, H.hxs);
     return rc;
 }
@@ -1827,9 +1862,8 @@ int b3t_ir_release(b3t_ctx *c, double *R, int32_t T, int32_t b, int32_t nrhs) {
 
 // One refinement step: [first: r = b, U_k = L_kk^{-T}]; d = (L L^T)^{-1} r
 // (with the inverted diagonal tiles); x (+)= d; r = b - A x; eta.
-// With slices (H.hasp >= 0) the residual r = b - A x is RESID_SL: the first
-// step slices every stored tile of A (SLICE_A), every step slices x
-// (SLICE_X) and forms r on the tensor cores.
+// With slices (H.hasp >= 0, A sliced beforehand) the residual r = b - A x is
+// RESID_SL: every step slices x (SLICE_X) and forms r on the tensor cores.
 static int ir_step(b3t_ctx *c, IrHandles &H, int32_t T, int32_t b, int32_t nrhs, int32_t flags, bool first) {
     b3t_codelet cres, cax, cnrm;
     int rc;
@@ -1848,16 +1882,7 @@ static int ir_step(b3t_ctx *c, IrHandles &H, int32_t T, int32_t b, int32_t nrhs,
     };
     if (first && (rc = resid(kVecAssign))) return rc;          // r_0 = b (x_0 = 0)
     if (first && (rc = submit_inv(c, H.hl, H.hu, T))) return rc;   // U_k = L_kk^{-T}, kept for later steps
-    if (first && sliced) {                                     // slices of A, kept for later steps
-        b3t_codelet csa;
-        if ((rc = kind_codelet(c, kSliceA, &csa))) return rc;
-        for (int32_t j = 0; j < T; ++j)
-            for (int32_t i = j; i < T; ++i) {
-                const SliceArgs a{i, j, T, b, nrhs};
-                const b3t_handle h3[3] = {H.ha, H.has[(size_t)i * T + j], H.has[(size_t)j * T + i]};
-                if ((rc = submit_impl(c, csa, h3, nullptr, 3, &a, sizeof(a)))) return rc;
-            }
-    }
+
     if ((rc = submit_solve_inv(c, H.hl, H.hu, H.hr, H.hz, T, b, nrhs, flags))) return rc;
     for (int32_t i = 0; i < T; ++i) {
         VecArgs v{nrhs, first ? kVecAssign : 0, i, T, b};
@@ -1865,6 +1890,9 @@ static int ir_step(b3t_ctx *c, IrHandles &H, int32_t T, int32_t b, int32_t nrhs,
         if ((rc = submit_impl(c, cax, h2, nullptr, 2, &v, sizeof(v)))) return rc;
     }
     if (sliced) {
+        // the solves in a launch of their own (the vector variant, more CTAs
+        // per SM), then the slicing and the tensor-core residual
+        if (!c->capturing && (rc = flush_impl(c))) return rc;
         b3t_codelet csx, crs;
         if ((rc = kind_codelet(c, kSliceX, &csx)) || (rc = kind_codelet(c, kResidSl, &crs))) return rc;
         for (int32_t j = 0; j < T; ++j) {

@@ -29,7 +29,8 @@
 //   RESID_SL  128 rows of R_i: thread 0 streams A slice chunks (16 KiB,
 //             bulk copies into a kSlStages ring) and the X slices of each
 //             K-chunk (24 KiB, two slots) and issues the MMAs (M = 128,
-//             N = 16, K = 32) into twelve group accumulators per tile, in
+//             K = 32; per A slice s one MMA of N = 16 (12 - s) against the
+//             stacked X slices) into twelve group accumulators per tile, in
 //             two tensor-memory buffers; warps 4-7 read a finished tile's
 //             groups (one row per thread), combine them and accumulate in
 //             FP64 while the next tile's MMAs run.  Then R_i = B_i - acc and
@@ -230,9 +231,9 @@ __device__ __noinline__ void slice_x_item(const TaskRec &t, int *s_ex) {
     if (tid < kSlNp) ex[tid] = s_ex[tid];
 }
 
-// Instruction descriptor: f32 accumulate, E4M3 A and B, K-major, M = 128, N = 16.
-__host__ __device__ constexpr uint32_t sl_idesc() {
-    return (1u << 4) | ((uint32_t)kSlNp >> 3 << 17) | ((128u >> 4) << 24);
+// Instruction descriptor: f32 accumulate, E4M3 A and B, K-major, M = 128, N = n.
+__host__ __device__ constexpr uint32_t sl_idesc(uint32_t n) {
+    return (1u << 4) | ((n >> 3) << 17) | ((128u >> 4) << 24);
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
@@ -299,7 +300,6 @@ __device__ __noinline__ int resid_sl_item(const TaskRec &t, int item, SlState &s
                      &st.full[slot]);
             return true;
         };
-        const uint32_t idesc = sl_idesc();
         for (uint32_t J = 0; J < (uint32_t)T && ok; ++J) {
             const uint32_t jt = st.nj + J, buf = jt & 1;
             // the buffer is free once the epilogue of tile jt - 2 has read it
@@ -325,15 +325,16 @@ __device__ __noinline__ int resid_sl_item(const TaskRec &t, int item, SlState &s
                     if (!mbar_wait(&st.full[slot], (ga / kSlStages) & 1, limit_ns)) { ok = false; break; }
                     ++consumed;
                     tc_fence_after();
+                    // one MMA per K step for all pairs (s, t), t = 0 .. 11 - s: the
+                    // X set is [t][16 rows][128 bytes], i.e. one K-major operand of
+                    // 192 rows, and group m = s + t sits at columns 16 m, so the
+                    // first 16 (12 - s) rows land on the groups s .. 11
                     const uint64_t ad = sw128_desc(smem_u32(smem + kSlAOff + slot * kSlChunk));
-                    const uint32_t sx = smem_u32(smem + kSlXOff + xs * kSlXSet);
-                    for (uint32_t tt = 0; tt + s < (uint32_t)kSlGroups; ++tt) {
-                        const uint64_t bd = sw128_desc(sx + tt * kSlXChunk);
-                        const uint32_t d = dbase + (s + tt) * kSlNp;
+                    const uint64_t bd = sw128_desc(smem_u32(smem + kSlXOff + xs * kSlXSet));
+                    const uint32_t idesc = sl_idesc((uint32_t)kSlNp * (kSlGroups - s));
 #pragma unroll
-                        for (uint32_t k4 = 0; k4 < 4; ++k4)
-                            mma_e4m3(d, ad + 2 * k4, bd + 2 * k4, idesc, (kc | s | k4) ? 1u : 0u);
-                    }
+                    for (uint32_t k4 = 0; k4 < 4; ++k4)
+                        mma_e4m3(dbase + s * kSlNp, ad + 2 * k4, bd + 2 * k4, idesc, (kc | s | k4) ? 1u : 0u);
                     mma_commit(&st.empty[slot]);
                     if (s == kSlDigits - 1) mma_commit(&st.xempty[xs]);
                 }
