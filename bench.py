@@ -68,9 +68,10 @@ def parse():
     p.add_argument("--no-scipy", action="store_true", help="skip the LAPACK CPU baselines (scipy, all host cores)")
     p.add_argument("--no-sliced-resid", action="store_true",
                    help="time to solution: skip the refinement with the sliced FP64 residual (tensor cores)")
-    p.add_argument("--mx-trsm", default="inv", choices=["inv", "subst", "both"],
-                   help="mixed panel solve: product with the inverted diagonal tile (TRTRI + TRMM_MX) "
-                        "or row substitution (TRSM_MX)")
+    p.add_argument("--mx-trsm", default="inv,sliced",
+                   help="mixed panel solves to time, comma-separated: inv (TRTRI + TRMM_MX, FP64 DFMA), "
+                        "sliced (TRTRI + TRMM_SL, the product on the tensor cores), subst (TRSM_MX); "
+                        "both = inv,subst.  The traced case (--case trace_mixed) takes the first")
     p.add_argument("--serve-requests", type=int, default=2000,
                    help="requests served with continuous batching, per precision (serving sweep: per rate)")
     p.add_argument("--serve-distinct", type=int, default=128,
@@ -470,7 +471,7 @@ def summarise(line):
     tts = sec.get("time_to_solution")
     if tts:
         out["time_to_solution"] = {"fp64_ms": tts["fp64"]["ms"]}
-        for p in ("bf16", "e4m3"):
+        for p in ("bf16", "e4m3", "bf16_sliced_panel", "e4m3_sliced_panel"):
             if p in tts:
                 out["time_to_solution"][p] = {k: tts[p][k] for k in ("ms", "factor_ms", "speedup_vs_fp64", "eta",
                                                                       "host_sampled_eta", "iterations")}
@@ -595,6 +596,14 @@ def rhs_parts(N, b, nrhs, seed, dev):
     return torch.from_numpy(np.ascontiguousarray(B.reshape(T, b, nrhs).transpose(0, 2, 1))).to(dev)
 
 
+def mx_modes(args):
+    m = args.mx_trsm.replace("both", "inv,subst").split(",")
+    for x in m:
+        if x not in ("inv", "sliced", "subst"):
+            raise SystemExit("--mx-trsm: unknown panel solve %r" % x)
+    return list(dict.fromkeys(m))
+
+
 def run_time_to_solution(ctx, A0, t, g64, N, b, dev, stream, args):
     """Config 4: 16 right-hand sides to backward error <= 1e-12.
     FP64: FP64 factorisation (graph g64 on tiles t) + one FP64 solve step.
@@ -653,15 +662,21 @@ def run_time_to_solution(ctx, A0, t, g64, N, b, dev, stream, args):
     Lm = torch.zeros_like(A0)
     U = torch.zeros((T, b, b), dtype=torch.float64, device=dev)
     up = dt.tile_ptrs(U)
-    variants = [(b3t.FMT_BF16, "bf16", args.mx_trsm != "subst"), (b3t.FMT_E4M3, "e4m3", args.mx_trsm != "subst")]
-    if args.mx_trsm == "both":
-        variants += [(b3t.FMT_BF16, "bf16_substitution", False), (b3t.FMT_E4M3, "e4m3_substitution", False)]
-    for fmt, name, inv in variants:
+    modes = mx_modes(args)
+    suffix = {"inv": "", "sliced": "_sliced_panel", "subst": "_substitution"}
+    variants = [(fmt, nm + suffix[m], m) for m in modes for fmt, nm in ((b3t.FMT_BF16, "bf16"), (b3t.FMT_E4M3, "e4m3"))]
+    WS = US = None
+    if "sliced" in modes:
+        WS = torch.zeros((T * (T + 1) // 2, b3t.slice_w_bytes(b)), dtype=torch.uint8, device=dev)
+        US = torch.zeros((T, b3t.slice_u_bytes(b)), dtype=torch.uint8, device=dev)
+    for fmt, name, mode in variants:
         Q = dt.q_tiles(T, b, fmt, dev)
         wp, lp, qp = dt.tile_ptrs(W), dt.tile_ptrs(Lm), dt.tile_ptrs(Q)
         ctx.graph_capture_begin()
-        if inv:
+        if mode == "inv":
             ctx.cholesky_mx_inv_submit(wp, lp, qp, up, T, b, fmt)
+        elif mode == "sliced":
+            ctx.cholesky_mx_sliced_submit(wp, lp, qp, up, dt.tile_ptrs(WS), dt.tile_ptrs(US), T, b, fmt)
         else:
             ctx.cholesky_mx_submit(wp, lp, qp, T, b, fmt)
         gm = ctx.graph_capture_end()
@@ -699,7 +714,10 @@ def run_time_to_solution(ctx, A0, t, g64, N, b, dev, stream, args):
                   "max_rel_diff_vs_fp64_solution": float((Xs - X64).abs().max() / X64.abs().max()),
                   "speedup_vs_fp64": out["fp64"]["ms"] / (f_ms + r_ms)}
             del Xs
-        out[name] = {"panel_solve": "TRTRI + TRMM_MX (inverted diagonal tile)" if inv else "TRSM_MX (substitution)",
+        panel = {"inv": "TRTRI + TRMM_MX (inverted diagonal tile, FP64 DFMA)",
+                 "sliced": "TRTRI + TRMM_SL (inverted diagonal tile, the product sliced onto the tensor cores)",
+                 "subst": "TRSM_MX (substitution)"}[mode]
+        out[name] = {"panel_solve": panel,
                      "ms": f_ms + s_ms, "factor_ms": f_ms, "refine_ms": s_ms, "iterations": its, "eta": em,
                      "host_sampled_eta": host_eta(Xm),
                      "converged": rc == 0, "max_rel_diff_vs_fp64_solution": diff,
@@ -1242,9 +1260,16 @@ def run_trace_mixed(dev, args):
     Lm = torch.zeros(W.shape, dtype=torch.float64, device=dev)
     Q = dt.q_tiles(T, b, b3t.FMT_BF16, dev)
     U = torch.zeros((T, b, b), dtype=torch.float64, device=dev)
+    mode = mx_modes(args)[0]
+    if mode == "sliced":
+        WS = torch.zeros((T * (T + 1) // 2, b3t.slice_w_bytes(b)), dtype=torch.uint8, device=dev)
+        US = torch.zeros((T, b3t.slice_u_bytes(b)), dtype=torch.uint8, device=dev)
     ctx.trace_start(1 << 23)
-    if args.mx_trsm == "subst":
+    if mode == "subst":
         ctx.cholesky_mx_submit(dt.tile_ptrs(W), dt.tile_ptrs(Lm), dt.tile_ptrs(Q), T, b, b3t.FMT_BF16)
+    elif mode == "sliced":
+        ctx.cholesky_mx_sliced_submit(dt.tile_ptrs(W), dt.tile_ptrs(Lm), dt.tile_ptrs(Q), dt.tile_ptrs(U),
+                                      dt.tile_ptrs(WS), dt.tile_ptrs(US), T, b, b3t.FMT_BF16)
     else:
         ctx.cholesky_mx_inv_submit(dt.tile_ptrs(W), dt.tile_ptrs(Lm), dt.tile_ptrs(Q), dt.tile_ptrs(U), T, b,
                                    b3t.FMT_BF16)
@@ -1256,7 +1281,7 @@ def run_trace_mixed(dev, args):
     ll = ctx.last_launch()
     ctx.close()
     assert len(tr) == ll["nitems"], "trace buffer too small"
-    out = {"workload": "mixed bf16 Cholesky N=%d tile %d (%s), one traced launch" % (N, b, args.mx_trsm),
+    out = {"workload": "mixed bf16 Cholesky N=%d tile %d (%s), one traced launch" % (N, b, mode),
            "tasks": ntasks, "edges": nedges, "items": int(len(tr)), "ctas": ll["nctas"],
            "traced_kernel_ms": ll["kernel_ns"] / 1e6}
     from paper_1304_0878_b300 import trace

@@ -128,7 +128,10 @@ enum b3t_kind {
     B3T_TRMM_MX = 23,
     B3T_SLICE_A = 24,
     B3T_SLICE_X = 25,
-    B3T_RESID_SL = 26
+    B3T_RESID_SL = 26,
+    B3T_SLICE_W = 27,
+    B3T_SLICE_U = 28,
+    B3T_TRMM_SL = 29
 };
 
 /* Diagonal tile split into column panels.  A b x b diagonal tile partitioned
@@ -222,6 +225,27 @@ typedef struct b3t_slice_args {
 } b3t_slice_args;
 B3T_API size_t b3t_slice_a_part_bytes(int32_t b);
 B3T_API size_t b3t_slice_x_part_bytes(int32_t b);
+
+/* Sliced panel product of the mixed factorisation, L_ik = fp64(W_ik) U_k
+ * (the product of B3T_TRMM_MX) with the slices of both operands on the
+ * tensor cores: row r of W_ik is sliced with its own exponent eW[r] (K = the
+ * columns), column c of U_k with eU[c] (K = the rows); the kept pairs' group
+ * sums are combined as for B3T_RESID_SL and each element of L_ik is
+ * H 2^(eW+eU-35) + L 2^(eW+eU-65) with one rounding.  Per product term the
+ * error is below 2^(eW[r]+eU[c]-58.3).  No scalars; b = the tile's leading
+ * dimension (a multiple of 128, <= 4096).
+ *  B3T_SLICE_W  W_ik (R, f32 tile), WS_ik (W, b3t_slice_w_bytes): chunks
+ *               (rb, kc, s) of 128 rows x 128 bytes of K at
+ *               ((rb * b/128 + kc) * 12 + s) * 16384 (quantised-tile swizzle),
+ *               then b int32 row exponents; items of 128 rows.
+ *  B3T_SLICE_U  U_k (R, f64 tile), US_k (W, b3t_slice_u_bytes): per
+ *               32-column block cb and K chunk kc, twelve chunks of 32 rows
+ *               (columns of U) x 128 bytes at ((cb * b/128 + kc) * 12 + t) *
+ *               4096, then b int32 column exponents; items of 32 columns.
+ *  B3T_TRMM_SL  US_k (R), WS_ik (R), L_ik (W, f64 tile): items of 128 x 32;
+ *               U_k must be zero below its diagonal (B3T_TRTRI's output). */
+B3T_API size_t b3t_slice_w_bytes(int32_t b);
+B3T_API size_t b3t_slice_u_bytes(int32_t b);
 enum { B3T_VEC_F32 = 1, B3T_VEC_ASSIGN = 2, B3T_VEC_LOWER_M = 4, B3T_VEC_UPPER_M = 8, B3T_VEC_KEEP_NORM = 16 };
 
 /* Low-precision formats of the Q tiles. */
@@ -436,6 +460,18 @@ B3T_API int b3t_cholesky_mx_submit(b3t_ctx *ctx, float *const *W, double *const 
 B3T_API int b3t_cholesky_mx_inv_submit(b3t_ctx *ctx, float *const *W, double *const *L,
                                        void *const *Q, double *const *U, int32_t T, int32_t b,
                                        int32_t fmt, int32_t col0);
+
+/* b3t_cholesky_mx_inv_submit with the panel product sliced onto the tensor
+ * cores: per step k, TRTRI(L_kk -> U_k), SLICE_U(U_k -> US_k), and for every
+ * i > k SLICE_W(W_ik -> WS_ik), TRMM_SL(US_k, WS_ik -> L_ik), QUANT(L_ik ->
+ * Q_ik); the updates as in b3t_cholesky_mx_submit.  WS: T(T+1)/2 pointers
+ * in the packed order (the diagonal entries are not used) to
+ * b3t_slice_w_bytes(b) bytes each; US: T pointers to b3t_slice_u_bytes(b)
+ * bytes (the last one is not used).  b a multiple of 128 (-EINVAL
+ * otherwise). */
+B3T_API int b3t_cholesky_mx_sliced_submit(b3t_ctx *ctx, float *const *W, double *const *L, void *const *Q,
+                                          double *const *U, void *const *WS, void *const *US, int32_t T,
+                                          int32_t b, int32_t fmt, int32_t col0);
 
 /* Solves with a tiled Cholesky factor: Y <- (L L^T)^{-1} Y, submitted as
  * TRSV_L / GEMV_L tasks (forward, k ascending) then TRSV_LT / GEMV_LT tasks

@@ -24,7 +24,7 @@ PRIO_UPWARD, PRIO_DEPTH = 0, 1
 TRSV_L, GEMV_L, TRSV_LT, GEMV_LT, AXPY, RESID, NRM = 11, 12, 13, 14, 15, 16, 17
 VEC_F32, VEC_ASSIGN, VEC_LOWER_M, VEC_UPPER_M, VEC_KEEP_NORM = 1, 2, 4, 8, 16
 POTRF_D, PANEL_TRSM, PANEL_UPD, CVT, TRTRI, TRMM_MX = 18, 19, 20, 21, 22, 23
-SLICE_A, SLICE_X, RESID_SL = 24, 25, 26
+SLICE_A, SLICE_X, RESID_SL, SLICE_W, SLICE_U, TRMM_SL = 24, 25, 26, 27, 28, 29
 
 
 class B3TError(RuntimeError):
@@ -99,6 +99,12 @@ _SIGS = {
     "b3t_ir_slice_bytes": (_sz, [_i32, _i32]),
     "b3t_slice_a_part_bytes": (_sz, [_i32]),
     "b3t_slice_x_part_bytes": (_sz, [_i32]),
+    "b3t_slice_w_bytes": (_sz, [_i32]),
+    "b3t_slice_u_bytes": (_sz, [_i32]),
+    "b3t_cholesky_mx_sliced_submit": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                                     ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                                     ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i32, _i32, _i32,
+                                                     _i32]),
     "b3t_ir_solve_sliced": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_vp), _vp, _vp, _vp, _vp, _vp, _i32, _i32,
                                            _i32, _i32, ctypes.c_double, _i32, _pi32,
                                            ctypes.POINTER(ctypes.c_double)]),
@@ -170,6 +176,14 @@ def slice_a_part_bytes(b):
 
 def slice_x_part_bytes(b):
     return int(lib().b3t_slice_x_part_bytes(b))
+
+
+def slice_w_bytes(b):
+    return int(lib().b3t_slice_w_bytes(b))
+
+
+def slice_u_bytes(b):
+    return int(lib().b3t_slice_u_bytes(b))
 
 
 def slice_args(i, j, T, b, nrhs):
@@ -314,6 +328,11 @@ class Context:
     def cholesky_mx_inv_submit(self, W_ptrs, L_ptrs, Q_ptrs, U_ptrs, T, b, fmt, col0=0):
         _check(lib().b3t_cholesky_mx_inv_submit(self._h, _ptrs(W_ptrs), _ptrs(L_ptrs), _ptrs(Q_ptrs),
                                                 _ptrs(U_ptrs), T, b, fmt, col0), "b3t_cholesky_mx_inv_submit")
+
+    def cholesky_mx_sliced_submit(self, W_ptrs, L_ptrs, Q_ptrs, U_ptrs, WS_ptrs, US_ptrs, T, b, fmt, col0=0):
+        _check(lib().b3t_cholesky_mx_sliced_submit(self._h, _ptrs(W_ptrs), _ptrs(L_ptrs), _ptrs(Q_ptrs),
+                                                   _ptrs(U_ptrs), _ptrs(WS_ptrs), _ptrs(US_ptrs), T, b, fmt,
+                                                   col0), "b3t_cholesky_mx_sliced_submit")
 
     def stream_open(self, max_tasks, max_edges, max_batches, deadline_ns):
         _check(lib().b3t_stream_open(self._h, max_tasks, max_edges, max_batches, deadline_ns),

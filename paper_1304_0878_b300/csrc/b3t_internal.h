@@ -75,8 +75,8 @@ enum : int32_t {
     kPotrfMx = 6, kTrsmMx = 7, kSyrkMx = 8, kGemmMx = 9, kQuant = 10,
     kTrsvL = 11, kGemvL = 12, kTrsvLT = 13, kGemvLT = 14, kAxpy = 15, kResid = 16, kNrm = 17,
     kPotrfD = 18, kPanelTrsm = 19, kPanelUpd = 20, kCvt = 21, kTrtri = 22, kTrmmMx = 23,
-    kSliceA = 24, kSliceX = 25, kResidSl = 26,
-    kNumKinds = 27
+    kSliceA = 24, kSliceX = 25, kResidSl = 26, kSliceW = 27, kSliceU = 28, kTrmmSl = 29,
+    kNumKinds = 30
 };
 
 // Sliced FP64 residual (the Ozaki scheme: exact products of integer digit
@@ -109,6 +109,16 @@ B3T_HD constexpr int64_t sl_x_part_bytes(int b) {
 struct SliceArgs {
     int32_t i, j, T, b, nrhs;
 };
+
+// Sliced panel product of the mixed factorisation, L_ik = fp64(W_ik) U_k:
+// W_ik sliced with one exponent per row (K = its columns), U_k with one
+// exponent per column (K = its rows).  W slices: chunks (rb, kc, s) at
+// ((rb * nk + kc) * 12 + s) * 16 KiB (128 rows x 128 bytes of K); U slices:
+// for 32-column block cb, chunk set (cb, kc) of twelve 32 x 128-byte chunks
+// at ((cb * nk + kc) * 12 + t) * 4 KiB.  Then b int32 exponents.
+constexpr int kTsCols = 32;               // TRMM_SL item: 128 rows x 32 columns of L_ik
+B3T_HD constexpr int64_t sl_w_bytes(int b) { return (int64_t)kSlDigits * b * b + 4 * (int64_t)b; }
+B3T_HD constexpr int64_t sl_u_bytes(int b) { return (int64_t)kSlDigits * b * b + 4 * (int64_t)b; }
 
 // One task as the device sees it: 64 bytes.
 struct alignas(16) TaskRec {
@@ -175,6 +185,7 @@ B3T_HD constexpr uint32_t family_of(int kind) {
          : (kind == kPotrf || kind == kTrsm || kind == kSyrk || kind == kGemm || kind == kPotrfD ||
             kind == kPanelTrsm || kind == kPanelUpd) ? kFamF64
          : ((kind >= kTrsvL && kind <= kNrm) || kind == kTrtri || kind == kSliceA || kind == kSliceX) ? kFamSolve
+         : (kind == kSliceW || kind == kSliceU || kind == kTrmmSl) ? kFamMx
          : (kind >= kPotrfMx && kind <= kQuant) || kind == kCvt || kind == kTrmmMx || kind == kResidSl ? kFamMx
          : 0u;   // NOOP runs in every variant
 }

@@ -528,10 +528,21 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
     sl.tfree = sl.done + 2;
     sl.drain = sl.tfree + 2;
     sl.fa = sl.fx = sl.nj = 0;
+    // TRMM_SL pipeline (its own barriers as well)
+    __shared__ __align__(8) uint64_t s_tsbars[kTsBars];
+    TsState ts;
+    ts.full = s_tsbars;
+    ts.empty = s_tsbars + kTsStages;
+    ts.bfull = s_tsbars + 2 * kTsStages;
+    ts.bempty = ts.bfull + 2;
+    ts.done = ts.bempty + 2;
+    ts.drain = ts.done + 1;
+    ts.fa = ts.fb = ts.nd = 0;
     if (kMx && p.has_mx) {
         if (tid == 0) {
             for (int i = 0; i < 2 * kMxStages + 1; ++i) mbar_init(&s_bars[i], 1);
             for (int i = 0; i < kSlBars; ++i) mbar_init(&s_slbars[i], 1);
+            for (int i = 0; i < kTsBars; ++i) mbar_init(&s_tsbars[i], 1);
             // each of the four epilogue warps frees an accumulator buffer
             mbar_init(&sl.tfree[0], 4);
             mbar_init(&sl.tfree[1], 4);
@@ -670,6 +681,17 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
                 }
                 break;
             case kTrtri: if constexpr (kSolve) trtri_item(rec, it, (double *)smem); break;
+            case kSliceW: if constexpr (kMx) slice_w_item(rec, it, smem); break;
+            case kSliceU: if constexpr (kMx) slice_u_item(rec, it, smem); break;
+            case kTrmmSl:
+                if constexpr (kMx) {
+                    if (!p.has_mx) { st = -EPROTO; break; }
+                    if (trmm_sl_item(rec, it, ts, smem, mx.tmem, min(p.timeout_ns, (int64_t)200000000), &s_fail)) {
+                        if (tid == 0) set_error(p.ctl, ETIMEDOUT, (int)t, 0, 31);
+                        st = -ETIMEDOUT;
+                    }
+                }
+                break;
             case kSliceA: if constexpr (kSolve) slice_a_item(rec, s_red, &s_e); break;
             case kSliceX: if constexpr (kSolve) slice_x_item(rec, (int *)s_red); break;
             case kResidSl:

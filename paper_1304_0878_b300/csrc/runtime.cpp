@@ -126,17 +126,20 @@ const KindSig kSigs[kNumKinds] = {
     /* SLICE_A  */ {3, {B3T_R, B3T_W, B3T_W}, {8, 1, 1}, sizeof(SliceArgs), false},
     /* SLICE_X  */ {2, {B3T_R, B3T_W}, {8, 1}, sizeof(SliceArgs), false},
     /* RESID_SL */ {4, {B3T_R, B3T_R, B3T_R, B3T_W}, {1, 1, 8, 8}, sizeof(SliceArgs), false},
+    /* SLICE_W  */ {2, {B3T_R, B3T_W}, {4, 1}, 0, false},
+    /* SLICE_U  */ {2, {B3T_R, B3T_W}, {8, 1}, 0, false},
+    /* TRMM_SL  */ {3, {B3T_R, B3T_R, B3T_W}, {1, 1, 8}, 0, false},
 };
 
 const char *kKindNames[kNumKinds] = {"noop", "scal_f32", "potrf", "trsm", "syrk", "gemm",
                                      "potrf_mx", "trsm_mx", "syrk_mx", "gemm_mx", "quant",
                                      "trsv_l", "gemv_l", "trsv_lt", "gemv_lt", "axpy", "resid", "nrm",
                                      "potrf_d", "panel_trsm", "panel_upd", "cvt", "trtri", "trmm_mx",
-                                     "slice_a", "slice_x", "resid_sl"};
+                                     "slice_a", "slice_x", "resid_sl", "slice_w", "slice_u", "trmm_sl"};
 bool is_panel(int kind) { return kind >= kPotrfD && kind <= kPanelUpd; }
 bool is_vec(int kind) { return kind >= kTrsvL && kind <= kNrm; }
 
-bool is_mx(int kind) { return kind == kSyrkMx || kind == kGemmMx || kind == kResidSl; }
+bool is_mx(int kind) { return kind == kSyrkMx || kind == kGemmMx || kind == kResidSl || kind == kTrmmSl; }
 bool is_slice(int kind) { return kind >= kSliceA && kind <= kResidSl; }
 bool has_fmt(int kind) { return kind == kSyrkMx || kind == kGemmMx || kind == kQuant; }
 
@@ -158,6 +161,9 @@ int64_t items_of(int kind, int64_t n) {
     case kAxpy: case kNrm: return 1;
     case kSliceA: case kSliceX: return 1;
     case kResidSl: return n / kSlRows;
+    case kSliceW: return n / 128;
+    case kSliceU: return n / kTsCols;
+    case kTrmmSl: return (n / 128) * (n / kTsCols);
     }
     return 1;
 }
@@ -189,6 +195,8 @@ float cost_of(int kind, int64_t n, int nrhs = 1, int T = 1, bool f32 = false) {
     case kSliceA: return (float)(2.0 * b * b / 4.0 + b * b / fp64);
     case kSliceX: return (float)(16.0 * b / 4.0 + 2000.0);
     case kResidSl: return (float)(T * b * 50.0);
+    case kSliceW: case kSliceU: return (float)(b * b / 20.0 + 5000.0);
+    case kTrmmSl: return (float)(b * 60.0 + 5000.0);
     }
     return 1000.0f;
 }
@@ -626,6 +634,26 @@ int submit_impl(b3t_ctx *c, b3t_codelet cl, const b3t_handle *handles, const uin
                 return -EINVAL;
             }
         }
+        r.n = b;
+    }
+    if (C.kind == kSliceW || C.kind == kSliceU || C.kind == kTrmmSl) {
+        // b from the FP32 / FP64 tile operand's leading dimension
+        const Handle &Ht = c->handles[handles[C.kind == kTrmmSl ? 2 : 0]];
+        const int64_t b = Ht.ld;
+        bool ok = b >= 128 && b <= 4096 && b % 128 == 0;
+        for (int i = 0; ok && i < nbuffers; ++i) ok = r.buf[i] % 16 == 0;
+        if (ok) {
+            const size_t tb = (size_t)b * b;
+            const Handle &H0 = c->handles[handles[0]], &H1 = c->handles[handles[1]];
+            if (C.kind == kSliceW)
+                ok = H0.elemsize == 4 && H0.nelems >= tb && H1.elemsize == 1 && H1.nelems >= (size_t)sl_w_bytes((int)b);
+            else if (C.kind == kSliceU)
+                ok = H0.elemsize == 8 && H0.nelems >= tb && H1.elemsize == 1 && H1.nelems >= (size_t)sl_u_bytes((int)b);
+            else
+                ok = H0.elemsize == 1 && H0.nelems >= (size_t)sl_u_bytes((int)b) && H1.elemsize == 1 &&
+                     H1.nelems >= (size_t)sl_w_bytes((int)b) && Ht.elemsize == 8 && Ht.nelems >= tb;
+        }
+        if (!ok) return -EINVAL;
         r.n = b;
     }
     float pcost = -1.f;
@@ -1583,6 +1611,96 @@ int b3t_cholesky_mx_inv_submit(b3t_ctx *c, float *const *W, double *const *L, vo
         }
     }
     return 0;
+}
+
+// Mixed precision with the panel product on the tensor cores: per step k,
+// after the diagonal factor, TRTRI(L_kk -> U_k) and SLICE_U(U_k -> US_k); for
+// every i > k SLICE_W(W_ik -> WS_ik) (W_ik is final once step k - 1 has
+// updated it), TRMM_SL(US_k, WS_ik -> L_ik) and QUANT(L_ik -> Q_ik); the
+// updates as in b3t_cholesky_mx_submit.
+static int reg_bytes(b3t_ctx *c, void *p, size_t bytes, b3t_handle *h) {
+    int rc = b3t_data_lookup(c, p, h);
+    if (rc == -ENOENT) rc = b3t_data_register(c, p, bytes, 1, 0, h);
+    if (rc) return rc;
+    return c->handles[*h].elemsize == 1 && c->handles[*h].nelems >= bytes ? 0 : -EINVAL;
+}
+
+int b3t_cholesky_mx_sliced_submit(b3t_ctx *c, float *const *W, double *const *L, void *const *Q,
+                                  double *const *U, void *const *WS, void *const *US, int32_t T, int32_t b,
+                                  int32_t fmt, int32_t col0) {
+    if (!c || !W || !L || !Q || !U || !WS || !US || T <= 0 || b < 128 || b > 4096 || b % kMxBlk) return -EINVAL;
+    if (fmt != B3T_FMT_BF16 && fmt != B3T_FMT_E4M3) return -EINVAL;
+    const int64_t nt = (int64_t)T * (T + 1) / 2;
+    std::vector<b3t_handle> hw, hl, hq, hu, hws(nt, -1), hus(T, -1);
+    int rc = reg_tiles(c, (void *const *)W, nt, (size_t)b * b, 4, b, hw);
+    if (!rc) rc = reg_tiles(c, (void *const *)L, nt, (size_t)b * b, 8, b, hl);
+    if (!rc) rc = reg_tiles(c, (void *const *)U, T, (size_t)b * b, 8, b, hu);
+    if (rc) return rc;
+    hq.assign(nt, -1);
+    for (int32_t j = 0; j < T; ++j)
+        for (int32_t i = j + 1; i < T; ++i) {
+            const int64_t t = tidx(i, j, T);
+            rc = b3t_data_lookup(c, Q[t], &hq[t]);
+            if (rc == -ENOENT) rc = b3t_data_register(c, Q[t], q_bytes(b, fmt), 1, b, &hq[t]);
+            if (!rc) rc = reg_bytes(c, WS[t], (size_t)sl_w_bytes(b), &hws[t]);
+            if (rc) return rc;
+        }
+    for (int32_t k = 0; k + 1 < T; ++k)
+        if ((rc = reg_bytes(c, US[k], (size_t)sl_u_bytes(b), &hus[k]))) return rc;
+    b3t_codelet cp, ci, csu, csw, cm, cq, cs, cg, cc;
+    if ((rc = kind_codelet(c, kPotrfMx, &cp)) || (rc = kind_codelet(c, kTrtri, &ci)) ||
+        (rc = kind_codelet(c, kSliceU, &csu)) || (rc = kind_codelet(c, kSliceW, &csw)) ||
+        (rc = kind_codelet(c, kTrmmSl, &cm)) || (rc = kind_codelet(c, kQuant, &cq)) ||
+        (rc = kind_codelet(c, kSyrkMx, &cs)) || (rc = kind_codelet(c, kGemmMx, &cg)) ||
+        (rc = kind_codelet(c, kCvt, &cc)))
+        return rc;
+    const int32_t pw = panel_width(b);
+    const bool panels = pw > 0;
+    std::vector<std::vector<b3t_handle>> dparts(panels ? T : 0);
+    for (int32_t k = 0; panels && k < T; ++k)
+        if ((rc = panel_parts(c, hl[tidx(k, k, T)], b, pw, dparts[k]))) return rc;
+    for (int32_t k = 0; k < T; ++k) {
+        const int32_t c0 = col0 + k * b;
+        const b3t_handle hp[2] = {hw[tidx(k, k, T)], hl[tidx(k, k, T)]};
+        if (panels) {
+            if ((rc = submit_impl(c, cc, hp, nullptr, 2, nullptr, 0))) return rc;
+            if ((rc = submit_panel_potrf(c, dparts[k], b, pw, c0))) return rc;
+        } else if ((rc = submit_impl(c, cp, hp, nullptr, 2, &c0, 4))) {
+            return rc;
+        }
+        if (k + 1 < T) {
+            const b3t_handle hi[2] = {hl[tidx(k, k, T)], hu[k]};
+            if ((rc = submit_impl(c, ci, hi, nullptr, 2, nullptr, 0))) return rc;
+            const b3t_handle hsu[2] = {hu[k], hus[k]};
+            if ((rc = submit_impl(c, csu, hsu, nullptr, 2, nullptr, 0))) return rc;
+        }
+        for (int32_t i = k + 1; i < T; ++i) {
+            const int64_t t = tidx(i, k, T);
+            const b3t_handle hsw[2] = {hw[t], hws[t]};
+            if ((rc = submit_impl(c, csw, hsw, nullptr, 2, nullptr, 0))) return rc;
+            const b3t_handle ht[3] = {hus[k], hws[t], hl[t]};
+            if ((rc = submit_impl(c, cm, ht, nullptr, 3, nullptr, 0))) return rc;
+            const b3t_handle hqq[2] = {hl[t], hq[t]};
+            if ((rc = submit_impl(c, cq, hqq, nullptr, 2, &fmt, 4))) return rc;
+        }
+        for (int32_t i = k + 1; i < T; ++i) {
+            const b3t_handle hs2[2] = {hq[tidx(i, k, T)], hw[tidx(i, i, T)]};
+            if ((rc = submit_impl(c, cs, hs2, nullptr, 2, &fmt, 4))) return rc;
+            for (int32_t j = k + 1; j < i; ++j) {
+                const b3t_handle hg[3] = {hq[tidx(i, k, T)], hq[tidx(j, k, T)], hw[tidx(i, j, T)]};
+                if ((rc = submit_impl(c, cg, hg, nullptr, 3, &fmt, 4))) return rc;
+            }
+        }
+    }
+    return 0;
+}
+
+size_t b3t_slice_w_bytes(int32_t b) {
+    return (b < 128 || b > 4096 || b % 128) ? 0 : (size_t)sl_w_bytes(b);
+}
+
+size_t b3t_slice_u_bytes(int32_t b) {
+    return (b < 128 || b > 4096 || b % 128) ? 0 : (size_t)sl_u_bytes(b);
 }
 
 // Register ptr as a vector of nparts parts of part_elems f64 (reusing an

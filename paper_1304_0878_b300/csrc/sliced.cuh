@@ -435,4 +435,238 @@ __device__ __noinline__ int resid_sl_item(const TaskRec &t, int item, SlState &s
     return 0;
 }
 
+// ---------------------------------------------------------------------
+// Sliced panel product of the mixed factorisation: L_ik = fp64(W_ik) U_k
+// (U_k = L_kk^{-T}, upper triangular), the product of TRMM_MX with the
+// slices of both operands on the tensor cores.  Row r of W_ik has the scale
+// exponent eW[r] (its maximum), column c of U_k the exponent eU[c]; with the
+// group sums G_m of the kept pairs (s + t <= 11),
+//   L(r, c) = H 2^(eW[r]+eU[c]-35) + L 2^(eW[r]+eU[c]-65)   (one rounding),
+// H and L combined from G_m as in RESID_SL.  Per product term the error is
+// below 2^(eW+eU-58.3), as for the residual.
+//   SLICE_W   128 rows of W_ik per item: row exponents, then the slices
+//             (chunks (rb, kc, s) of 128 rows x 128 bytes of K).
+//   SLICE_U   32 columns of U_k per item: column exponents, then the
+//             slices as chunk sets (cb, kc) of 12 x (32 rows x 128 bytes).
+//   TRMM_SL   a 128 x 32 block of L_ik per item.  Thread 0 streams the W
+//             chunks of the block's rows (16 KiB, 4-stage ring) and the U
+//             chunk set of each K chunk (48 KiB, two slots), and issues per
+//             W slice s the MMAs against the stacked U slices: group m =
+//             s + t at TMEM columns 32 m, N = 32 (12 - s) (two MMAs, 256 and
+//             32 (4 - s) columns, for s < 4).  U_k is zero below the
+//             diagonal, so the K range stops at the block's last column.
+//             All eight warps then combine the groups and write L.
+
+constexpr int kTsStages = 4;
+constexpr uint32_t kTsBChunk = kTsCols * 128;            // 4 KiB: 32 rows x 128 bytes
+constexpr uint32_t kTsBSet = kSlDigits * kTsBChunk;      // 48 KiB: the 12 U slices of a K chunk
+constexpr uint32_t kTsBOff = 0;                          // two U slots
+constexpr uint32_t kTsAOff = 2 * kTsBSet;                // then the W ring (4 x 16 KiB)
+static_assert(kTsAOff + kTsStages * kSlChunk <= 160 * 1024, "TRMM_SL stages fit the MX data area");
+
+__device__ __noinline__ void slice_w_item(const TaskRec &t, int item, unsigned char *smem) {
+    const int b = (int)t.n, nk = b / 128, rb = item;
+    const float *W = (const float *)t.buf[0];
+    unsigned char *D = (unsigned char *)t.buf[1];
+    int *eW = (int *)(D + (size_t)kSlDigits * b * b);
+    float *hm = (float *)smem;                 // [2][128] maxima over half a row
+    int *re = (int *)(smem + 1024);            // [128] row exponents
+    const int tid = threadIdx.x;
+    {
+        const int rr = tid & 127, h = tid >> 7, r = rb * 128 + rr;
+        float m = 0.0f;
+        for (int c = h * (b / 2); c < (h + 1) * (b / 2); ++c) m = fmaxf(m, fabsf(W[(size_t)r + (size_t)c * b]));
+        hm[h * 128 + rr] = m;
+    }
+    __syncthreads();
+    if (tid < 128) {
+        const int e = sl_exp((double)fmaxf(hm[tid], hm[128 + tid]));
+        re[tid] = e;
+        eW[rb * 128 + tid] = e;
+    }
+    __syncthreads();
+    for (int u0 = tid; u0 < 128 * (b / 16); u0 += kThreads) {
+        const int rr = u0 & 127, g16 = u0 >> 7, r = rb * 128 + rr;
+        const int e = re[rr];
+        unsigned long long u[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) u[k] = sl_u((double)W[(size_t)r + (size_t)(16 * g16 + k) * b], e);
+        const int kc = g16 >> 3, g = g16 & 7;
+        sl_store16(D + (size_t)(rb * nk + kc) * kSlDigits * kSlChunk + (size_t)rr * 128 + ((g ^ (rr & 7)) << 4),
+                   kSlChunk, u);
+    }
+}
+
+__device__ __noinline__ void slice_u_item(const TaskRec &t, int item, unsigned char *smem) {
+    const int b = (int)t.n, nk = b / 128, cb = item, c0 = cb * kTsCols;
+    const double *U = (const double *)t.buf[0];
+    unsigned char *D = (unsigned char *)t.buf[1];
+    int *eU = (int *)(D + (size_t)kSlDigits * b * b);
+    int *ce = (int *)smem;                     // [32] column exponents
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int cc = warp; cc < kTsCols; cc += kThreads / 32) {
+        double m = 0.0;
+        for (int p = lane; p < b; p += 32) m = fmax(m, fabs(U[(size_t)p + (size_t)(c0 + cc) * b]));
+#pragma unroll
+        for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) {
+            const int e = sl_exp(m);
+            ce[cc] = e;
+            eU[c0 + cc] = e;
+        }
+    }
+    __syncthreads();
+    for (int u0 = tid; u0 < kTsCols * (b / 16); u0 += kThreads) {
+        const int cc = u0 / (b / 16), g16 = u0 % (b / 16);
+        const int e = ce[cc];
+        unsigned long long u[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) u[k] = sl_u(U[(size_t)(16 * g16 + k) + (size_t)(c0 + cc) * b], e);
+        const int kc = g16 >> 3, g = g16 & 7;
+        sl_store16(D + (size_t)(cb * nk + kc) * kSlDigits * kTsBChunk + (size_t)cc * 128 + ((g ^ (cc & 7)) << 4),
+                   kTsBChunk, u);
+    }
+}
+
+// Per-CTA pipeline state of TRMM_SL, persistent across items.
+struct TsState {
+    uint64_t *full, *empty;     // [kTsStages] W chunk ring
+    uint64_t *bfull, *bempty;   // [2] U chunk sets
+    uint64_t *done;             // [1] the item's MMAs have finished
+    uint64_t *drain;            // [1] after a failed wait
+    uint32_t fa, fb;            // W / U fills so far (thread 0)
+    uint32_t nd;                // items completed so far (every thread)
+};
+constexpr int kTsBars = 2 * kTsStages + 2 + 2 + 1 + 1;
+
+// Returns 0, or ETIMEDOUT when a pipeline wait ran out (block-wide).
+__device__ __noinline__ int trmm_sl_item(const TaskRec &t, int item, TsState &st, unsigned char *smem,
+                                         uint32_t tmem, int64_t limit_ns, int *s_fail) {
+    const int b = (int)t.n, nk = b / 128, ncb = b / kTsCols;
+    const int rb = item / ncb, cb = item % ncb, c0 = cb * kTsCols;
+    const unsigned char *US = (const unsigned char *)t.buf[0];
+    const unsigned char *WS = (const unsigned char *)t.buf[1];
+    double *L = (double *)t.buf[2];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t nks = (uint32_t)cb + 1;                 // K steps of 32: rows p < c0 + 32 of U_k
+    const uint32_t nkc = (nks + 3) / 4;                    // K chunks of 128
+    const uint32_t Q = nkc * kSlDigits;                    // steps (kc, s)
+    if (tid == 0) *s_fail = 0;
+    __syncthreads();
+    if (tid == 0) {
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        bool ok = true;
+        uint32_t issued = 0, consumed = 0, bissued = 0, bconsumed = 0;
+        auto issue = [&](uint32_t q) -> bool {
+            const uint32_t s = q % kSlDigits, kc = q / kSlDigits;
+            if (s == 0) {
+                const uint32_t gb = st.fb + kc, bs = gb & 1;
+                if (gb >= 2 && !mbar_wait(&st.bempty[bs], ((gb >> 1) - 1) & 1, limit_ns)) return false;
+                mbar_expect_tx(&st.bfull[bs], kTsBSet);
+                bulk_g2s(smem + kTsBOff + bs * kTsBSet, US + (size_t)(cb * nk + kc) * kTsBSet, kTsBSet,
+                         &st.bfull[bs]);
+                ++bissued;
+            }
+            const uint32_t ga = st.fa + q, slot = ga % kTsStages;
+            if (ga >= (uint32_t)kTsStages && !mbar_wait(&st.empty[slot], ((ga / kTsStages) - 1) & 1, limit_ns))
+                return false;
+            mbar_expect_tx(&st.full[slot], kSlChunk);
+            bulk_g2s(smem + kTsAOff + slot * kSlChunk, WS + ((size_t)(rb * nk + kc) * kSlDigits + s) * kSlChunk,
+                     kSlChunk, &st.full[slot]);
+            return true;
+        };
+        for (uint32_t kc = 0; kc < nkc && ok; ++kc) {
+            const uint32_t ksteps = min(4u, nks - 4 * kc);
+            for (uint32_t s = 0; s < (uint32_t)kSlDigits; ++s) {
+                const uint32_t q = kc * kSlDigits + s;
+                while (issued < Q && issued < q + kTsStages - 1) {
+                    if (!issue(issued)) { ok = false; break; }
+                    ++issued;
+                }
+                if (!ok) break;
+                const uint32_t ga = st.fa + q, slot = ga % kTsStages;
+                const uint32_t gb = st.fb + kc, bs = gb & 1;
+                if (s == 0) {
+                    if (!mbar_wait(&st.bfull[bs], (gb >> 1) & 1, limit_ns)) { ok = false; break; }
+                    ++bconsumed;
+                }
+                if (!mbar_wait(&st.full[slot], (ga / kTsStages) & 1, limit_ns)) { ok = false; break; }
+                ++consumed;
+                tc_fence_after();
+                const uint64_t ad = sw128_desc(smem_u32(smem + kTsAOff + slot * kSlChunk));
+                const uint64_t bd = sw128_desc(smem_u32(smem + kTsBOff + bs * kTsBSet));
+                for (uint32_t k4 = 0; k4 < ksteps; ++k4) {
+                    const uint32_t acc = (kc | s | k4) ? 1u : 0u;
+                    if (s < 4) {
+                        // U slices t = 0..7 (256 rows), then t = 8..11-s from row 256
+                        mma_e4m3(tmem + kTsCols * s, ad + 2 * k4, bd + 2 * k4, sl_idesc(256), acc);
+                        mma_e4m3(tmem + kTsCols * (s + 8), ad + 2 * k4, bd + ((256u * 128u) >> 4) + 2 * k4,
+                                 sl_idesc(kTsCols * (4 - s)), acc);
+                    } else {
+                        mma_e4m3(tmem + kTsCols * s, ad + 2 * k4, bd + 2 * k4, sl_idesc(kTsCols * (12 - s)), acc);
+                    }
+                }
+                mma_commit(&st.empty[slot]);
+                if (s == kSlDigits - 1) mma_commit(&st.bempty[bs]);
+            }
+        }
+        if (!ok) {
+            *s_fail = 1;
+            for (uint32_t q = consumed; q < issued; ++q) {
+                const uint32_t ga = st.fa + q;
+                mbar_wait(&st.full[ga % kTsStages], (ga / kTsStages) & 1, limit_ns);
+            }
+            for (uint32_t x = bconsumed; x < bissued; ++x) {
+                const uint32_t gb = st.fb + x;
+                mbar_wait(&st.bfull[gb & 1], (gb >> 1) & 1, limit_ns);
+            }
+            mma_commit(st.drain);
+            mbar_wait(st.drain, 0, limit_ns);
+        } else {
+            mma_commit(st.done);
+        }
+        st.fa += issued;
+        st.fb += bissued;
+    }
+    __syncthreads();
+    bool ok = *s_fail == 0;
+    if (ok && !mbar_wait(st.done, st.nd & 1, limit_ns)) ok = false;
+    if (ok) st.nd++;
+    if (__syncthreads_or(!ok)) return ETIMEDOUT;
+    tc_fence_after();
+    // epilogue: warp w reads TMEM lanes 32 (w & 3).. (its rows) and 16 of the
+    // block's 32 columns (w >> 2)
+    const int q = warp & 3, h = warp >> 2, rr = 32 * q + lane, r = rb * 128 + rr;
+    const int ew = *(const int *)(WS + (size_t)kSlDigits * b * b + 4 * (size_t)r);
+    const int *eU = (const int *)(US + (size_t)kSlDigits * b * b);
+    const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16) + 16 * h;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        long long Hs[8], Ls[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) { Hs[c] = 0; Ls[c] = 0; }
+#pragma unroll
+        for (int m = 0; m < kSlGroups; ++m) {
+            float v[8];
+            tmem_ld8(tb + kTsCols * m + 8 * half, v);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const long long g = (long long)__float2int_rz(v[c]);
+                if (m < 6) Hs[c] += g << (5 * (5 - m));
+                else Ls[c] += g << (5 * (11 - m));
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int cc = 16 * h + 8 * half + c;
+            const int e = ew + eU[c0 + cc];
+            const double v = fma((double)Ls[c], sl_pow2(e - 65), (double)Hs[c] * sl_pow2(e - 35));
+            L[(size_t)r + (size_t)(c0 + cc) * b] = v;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    return 0;
+}
+
 }  // namespace b3t

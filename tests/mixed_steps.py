@@ -19,6 +19,8 @@ Cholesky, Section 3.5 for inner products and matrix products):
   TRSM     |L_ik L_kk^T - fp64(W_ik)| <= gamma_b(2^-53) |L_ik||L_kk^T|
   TRTRI    |U_k L_kk^T - I| <= gamma_b(2^-53) |U_k||L_kk^T|, U_k upper
   TRMM     |L_ik - fp64(W_ik) U_k| <= gamma_b(2^-53) |W_ik||U_k|
+  TRMM_SL  |L_ik - fp64(W_ik) U_k| <= b 2^(eW[r]+eU[c]-58.3) + 2u|L_ik|
+           (the product from slices: row exponents of W, column ones of U)
 
 Residuals are formed in numpy's extended precision and the rounding of that
 evaluation is added to each bound.  Each check returns the largest ratio of
@@ -128,6 +130,21 @@ def trtri_ratio(U, Lkk):
     return _ratio(err, bnd)
 
 
+def trmm_sliced_ratio(W32, X, U):
+    """TRMM_SL: X = fp64(W) U from the slices (row exponents eW of W,
+    column exponents eU of U): per term the truncation bound
+    2^(eW[r]+eU[c]-58.3) (tests/sliced_ref.py), b terms, one rounding."""
+    import sliced_ref as sr
+    n = U.shape[0]
+    Wd = np.asarray(W32, dtype=np.float64)
+    eW, eU = sr.row_exps(Wd), sr.col_exps(U)
+    R, Rabs = _product(Wd, U)
+    err = _ld(X) - R
+    scale = np.ldexp(1.0, (eW[:, None] + eU[None, :]).astype(np.int64))
+    bnd = _ld(n * sr.term_error() * scale) + (2 * U64 + gamma(n, ULD)) * (np.abs(R) + Rabs * ULD)
+    return _ratio(err, bnd)
+
+
 def trmm_ratio(W32, X, U):
     """TRMM: X = fp64(W) U as a product."""
     n = U.shape[0]
@@ -137,14 +154,15 @@ def trmm_ratio(W32, X, U):
     return _ratio(err, bnd)
 
 
-def check_factor(A, Wt, Lt, Q, T, b, fmt, Ut=None):
+def check_factor(A, Wt, Lt, Q, T, b, fmt, Ut=None, sliced=False):
     """Every task of the factorisation against its bound.
 
     A: the input (N x N FP64, lower used); Wt, Lt: packed tiles in the
     layout of oracle.cholesky.to_tiles (binary32 and FP64); Q: {(i, k):
     (values [r, c], e)} for i > k; Ut: (T, b, b) inverted diagonal tiles
-    (element (r, c) at [k][c, r]) for the product form, else None.
-    Returns {check name: worst ratio} (quant: 0 equal, inf not)."""
+    (element (r, c) at [k][c, r]) for the product form, else None;
+    sliced: the product formed from slices (TRMM_SL), checked against its
+    own bound.  Returns {check name: worst ratio} (quant: 0 equal, inf not)."""
     F = lambda t: t.T                                  # tile -> [r, c]
     A32 = {}
     for j in range(T):
@@ -172,6 +190,8 @@ def check_factor(A, Wt, Lt, Q, T, b, fmt, Ut=None):
         for i in range(k + 1, T):
             if Ut is None:
                 r = trsm_ratio(W[(i, k)], L[(i, k)], L[(k, k)])
+            elif sliced:
+                r = trmm_sliced_ratio(W[(i, k)], L[(i, k)], F(Ut[k]))
             else:
                 r = trmm_ratio(W[(i, k)], L[(i, k)], F(Ut[k]))
             out["panel"] = max(out["panel"], r)

@@ -197,3 +197,42 @@ def resid_bound(eA, eX, rows, Rex, b, T, nrhs):
             sc += np.ldexp(1.0, eA[i, J] + eX[J, :nrhs])
         out[k] = sc * b * (term_error() + acc_terms * gamma(2 * T)) + 3.0 * U64 * np.abs(Rex[k])
     return out
+
+
+def row_exps(M):
+    return np.array([scale_exp(float(np.max(np.abs(M[r])))) for r in range(M.shape[0])], dtype=np.int64)
+
+
+def col_exps(M):
+    return row_exps(M.T)
+
+
+def trmm_sliced(W32, U):
+    """L = fp64(W) U the sliced way (B3T_TRMM_SL): W rows with their own
+    exponents, U columns with theirs; one rounding per element.  Returns
+    (L, eW, eU)."""
+    Wd = np.asarray(W32, dtype=np.float64)
+    eW, eU = row_exps(Wd), col_exps(U)
+    G = group_sums(digits(to_int(Wd, eW[:, None])), digits(to_int(U, eU[None, :])))
+    H = np.zeros(G.shape[1:], dtype=np.int64)
+    L = np.zeros(G.shape[1:], dtype=np.int64)
+    for m in range(DIGITS):
+        if m < 6:
+            H += G[m] << (5 * (5 - m))
+        else:
+            L += G[m] << (5 * (11 - m))
+    sc = eW[:, None] + eU[None, :]
+    return np.ldexp(H.astype(np.float64), sc - 35) + np.ldexp(L.astype(np.float64), sc - 65), eW, eU
+
+
+def exact_product_entries(A, B, entries):
+    """(A B)[r, c], correctly rounded, for the given (r, c) pairs."""
+    out = []
+    for r, c in entries:
+        a, x = A[r], B[:, c]
+        ah, al = _split(a)
+        xh, xl = _split(x)
+        p = a * x
+        e = ((ah * xh - p) + ah * xl + al * xh) + al * xl
+        out.append(math.fsum(list(p) + list(e)))
+    return np.array(out)

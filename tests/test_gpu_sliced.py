@@ -219,3 +219,135 @@ def test_sliced_refinement_matches_fp64_refinement(orc, gctx, fmt):
         gctx.tiles_unregister(p, T)
     for p in up:
         gctx.data_unregister(gctx.data_lookup(p))
+
+
+# ---- the sliced panel product of the mixed factorisation
+
+def decode_w(p, b):
+    """W slices -> (digits (12, b rows, b K), row exponents (b))."""
+    nk = b // 128
+    vals = e4m3_ints(p[:12 * b * b]).reshape(nk, nk, 12, 128, 8, 16)
+    rows = np.arange(128)
+    out = np.empty((12, b, b), dtype=np.int64)
+    for g in range(8):
+        grp = vals[:, :, :, rows, g ^ (rows % 8), :]
+        for rb in range(nk):
+            for kc in range(nk):
+                out[:, rb * 128:(rb + 1) * 128, kc * 128 + 16 * g:kc * 128 + 16 * g + 16] = grp[rb, kc]
+    return out, p[12 * b * b:12 * b * b + 4 * b].view(np.int32).astype(np.int64)
+
+
+def decode_u(p, b):
+    """U slices -> (digits (12, b K, b columns), column exponents (b))."""
+    nk, ncb = b // 128, b // 32
+    vals = e4m3_ints(p[:12 * b * b]).reshape(ncb, nk, 12, 32, 8, 16)
+    rows = np.arange(32)
+    out = np.empty((12, b, b), dtype=np.int64)
+    for g in range(8):
+        grp = vals[:, :, :, rows, g ^ (rows % 8), :]       # (ncb, nk, 12, 32, 16): [.., column, K]
+        for cb in range(ncb):
+            for kc in range(nk):
+                out[:, kc * 128 + 16 * g:kc * 128 + 16 * g + 16, cb * 32:(cb + 1) * 32] = \
+                    grp[cb, kc].transpose(0, 2, 1)
+    return out, p[12 * b * b:12 * b * b + 4 * b].view(np.int32).astype(np.int64)
+
+
+def dev_tile(M, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(M.T)).to(dtype).cuda()
+
+
+def sliced_panel_dev(ctx, Lkk, Wik, b):
+    """TRTRI(L_kk -> U), SLICE_U, SLICE_W, TRMM_SL on the device; returns
+    (U, L_ik, WS bytes, US bytes) on the host."""
+    L = dev_tile(Lkk)
+    Wd = dev_tile(Wik, torch.float32)
+    U = torch.full((b, b), float("nan"), dtype=torch.float64, device="cuda")
+    X = torch.full((b, b), float("nan"), dtype=torch.float64, device="cuda")
+    WS = torch.zeros(b3t.slice_w_bytes(b), dtype=torch.uint8, device="cuda")
+    US = torch.zeros(b3t.slice_u_bytes(b), dtype=torch.uint8, device="cuda")
+    hl = ctx.data_register(L.data_ptr(), b * b, 8, b)
+    hu = ctx.data_register(U.data_ptr(), b * b, 8, b)
+    hw = ctx.data_register(Wd.data_ptr(), b * b, 4, b)
+    hx = ctx.data_register(X.data_ptr(), b * b, 8, b)
+    hws = ctx.data_register(WS.data_ptr(), WS.numel(), 1)
+    hus = ctx.data_register(US.data_ptr(), US.numel(), 1)
+    ci = ctx.task_decl("trtri", b3t.TRTRI, [R, W])
+    cu = ctx.task_decl("slice_u", b3t.SLICE_U, [R, W])
+    cw = ctx.task_decl("slice_w", b3t.SLICE_W, [R, W])
+    cm = ctx.task_decl("trmm_sl", b3t.TRMM_SL, [R, R, W])
+    ctx.task_submit(ci, [hl, hu])
+    ctx.task_submit(cu, [hu, hus])
+    ctx.task_submit(cw, [hw, hws])
+    ctx.task_submit(cm, [hus, hws, hx])
+    ctx.task_wait()
+    for h in (hl, hu, hw, hx, hws, hus):
+        ctx.data_unregister(h)
+    return U.cpu().numpy().T, X.cpu().numpy().T, WS.cpu().numpy(), US.cpu().numpy()
+
+
+@pytest.mark.parametrize("b", [128, 256, 512])
+def test_sliced_panel_product_bit_exact_and_within_bound(orc, gctx, b):
+    from oracle import tiles as otl
+    rng = np.random.default_rng(b + 3)
+    A = synth.spd_host(b, seed=b, shift=1.0)
+    Lkk = np.asfortranarray(np.tril(A))
+    assert otl.potrf(Lkk) == 0
+    Lkk = np.tril(Lkk)
+    Wik = (rng.standard_normal((b, b)) * 10.0 ** rng.integers(-2, 3, (b, 1))).astype(np.float32)
+    Wik[3, :] = 0.0
+    U, X, WS, US = sliced_panel_dev(gctx, Lkk, Wik, b)
+    Xref, eW, eU = sr.trmm_sliced(Wik, U)
+    # the slices, then the product, bit for bit
+    DW, eWd = decode_w(WS, b)
+    DU, eUd = decode_u(US, b)
+    assert np.array_equal(eWd, eW) and np.array_equal(eUd, eU)
+    assert np.array_equal(sr.from_digits(DW), sr.to_int(Wik.astype(np.float64), eW[:, None]))
+    assert np.array_equal(sr.from_digits(DU), sr.to_int(U, eU[None, :]))
+    assert np.array_equal(X, Xref)
+    # against the exact product: b terms of the truncation bound plus one rounding
+    ent = [(int(r), int(c)) for r, c in zip(rng.integers(0, b, 64), rng.integers(0, b, 64))] + [(b - 1, b - 1)]
+    ex = sr.exact_product_entries(Wik.astype(np.float64), U, ent)
+    got = np.array([X[r, c] for r, c in ent])
+    bound = np.array([b * sr.term_error() * 2.0 ** float(eW[r] + eU[c]) for r, c in ent]) + 2 * sr.U64 * np.abs(ex)
+    assert np.all(np.abs(got - ex) <= bound)
+
+
+def factor_sliced_dev(ctx, A, b, fmt):
+    N = A.shape[0]
+    T = N // b
+    At = torch.from_numpy(och.to_tiles(A, b)).cuda()
+    Wt = At.float()
+    Lt = torch.zeros_like(At)
+    Qt = dt.q_tiles(T, b, fmt, "cuda")
+    Ut = torch.zeros((T, b, b), dtype=torch.float64, device="cuda")
+    nt = T * (T + 1) // 2
+    WSt = torch.zeros((nt, b3t.slice_w_bytes(b)), dtype=torch.uint8, device="cuda")
+    USt = torch.zeros((T, b3t.slice_u_bytes(b)), dtype=torch.uint8, device="cuda")
+    wp, lp, qp, up = dt.tile_ptrs(Wt), dt.tile_ptrs(Lt), dt.tile_ptrs(Qt), dt.tile_ptrs(Ut)
+    ctx.cholesky_mx_sliced_submit(wp, lp, qp, up, dt.tile_ptrs(WSt), dt.tile_ptrs(USt), T, b, fmt)
+    ctx.task_wait()
+    for p in (wp, lp, qp):
+        ctx.tiles_unregister(p, T)
+    for p in up[:-1] + dt.tile_ptrs(USt)[:-1]:
+        ctx.data_unregister(ctx.data_lookup(p))
+    ctx.data_unregister(ctx.data_lookup(up[-1]))
+    for j in range(T):
+        for i in range(j + 1, T):
+            ctx.data_unregister(ctx.data_lookup(dt.tile_ptrs(WSt)[och.tile_index(i, j, T)]))
+    return Wt, Lt, Qt, Ut
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "e4m3"])
+@pytest.mark.parametrize("N,b", [(1024, 128), (1024, 256)])
+def test_sliced_factor_every_task_within_its_bound(orc, gctx, fmt, N, b):
+    from mixed_steps import check_factor
+    from qlayout import decode
+    FM = {"bf16": b3t.FMT_BF16, "e4m3": b3t.FMT_E4M3}[fmt]
+    A = synth.spd_host(N, seed=N + b + 1, shift=1.0)
+    Wt, Lt, Qt, Ut = factor_sliced_dev(gctx, A, b, FM)
+    T = N // b
+    Qh = Qt.cpu().numpy()
+    Q = {(i, k): decode(Qh[och.tile_index(i, k, T)], b, FM) for k in range(T) for i in range(k + 1, T)}
+    r = check_factor(A, Wt.cpu().numpy(), Lt.cpu().numpy(), Q, T, b, fmt, Ut.cpu().numpy(), sliced=True)
+    assert r["quant"] == 0.0, r
+    assert all(v <= 1.0 for v in r.values()), r

@@ -7,8 +7,8 @@ import numpy as np
 import pytest
 
 import synth
-from mixed_steps import (check_factor, potrf_ratio, trmm_ratio, trsm_ratio, trtri_ratio,
-                         update_ratio)
+from mixed_steps import (check_factor, potrf_ratio, trmm_ratio, trmm_sliced_ratio, trsm_ratio,
+                         trtri_ratio, update_ratio)
 from oracle import cholesky as och, ir as oir, mixed as omx, tiles as otl
 from oracle.cholesky import tile_index
 
@@ -112,3 +112,17 @@ def test_inverse_and_product_checks(state):
     X2 = X.copy()
     X2[7, 90] *= 1.0 + 1e-12
     assert trmm_ratio(Wik, X2, U) > 1.0
+
+
+def test_sliced_product_check(state):
+    # the host restatement of TRMM_SL passes its bound; a perturbation of
+    # 1e-11 relative does not
+    import sliced_ref as sr
+    fmt, A, Lt, Wt, Q = state
+    Lkk, Wik = np.tril(_tile(Lt, 0, 0)), _tile(Wt, 1, 0)
+    U = np.triu(oir.forward_sub(Lkk, np.eye(B)).T)
+    X, _, _ = sr.trmm_sliced(Wik, U)
+    assert trmm_sliced_ratio(Wik, X, U) <= 1.0
+    X2 = X.copy()
+    X2[7, 90] *= 1.0 + 1e-11
+    assert trmm_sliced_ratio(Wik, X2, U) > 1.0
