@@ -51,6 +51,16 @@ def hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def bf16_peak():
+    """Measured dense bf16 burst throughput (TFLOP/s) and its source."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 1800.0, "fallback"
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -81,7 +91,7 @@ def parse():
     p.add_argument("--prio", default="upward", choices=["upward", "depth"],
                    help="ready-queue order of the profiling cases (--case)")
     p.add_argument("--ctas-per-sm", type=int, default=0, help="grid of the profiling cases (0: occupancy)")
-    p.add_argument("--case", default=None, choices=["mx_gemm_bf16", "mx_gemm_e4m3", "scal", "resid", "resid_sl", "solve_f32", "trace_mixed",
+    p.add_argument("--case", default=None, choices=["mx_gemm_bf16", "mx_gemm_e4m3", "scal", "resid", "resid_sl", "trmm_sl", "solve_f32", "trace_mixed",
                                                     "solve_f64", "empty_dags", "serve_sweep", "trace_headline", "batch"],
                    help="run one profiling case (a DAG of one task kind), or one secondary measurement alone "
                         "(empty_dags, serve_sweep, trace_headline, batch), and print its result")
@@ -1107,6 +1117,8 @@ def run_case(args):
         work, unit = 2.0 * N * N * nrhs, "TFLOP/s"
     elif args.case == "resid_sl":
         return run_resid_sliced(ctx, dev, args)
+    elif args.case == "trmm_sl":
+        return run_trmm_sliced(ctx, dev, args)
     else:  # resid: one refinement residual over N = 16384, 16 rhs (FP64)
         N, nrhs = 16384, 16
         T = N // b
@@ -1148,7 +1160,7 @@ def run_resid_sliced(ctx, dev, args):
     import torch
     import synth
     import paper_1304_0878_b300 as b3t
-    N, b, nrhs = 32768, 512, 16
+    N, b, nrhs = (args.n if args.n != 32768 else 32768), 512, 16
     T = N // b
     A = synth.spd_tiles_device(N, b, 3, 0.1, dev)
     X = torch.randn((T, nrhs, b), dtype=torch.float64, device=dev)
@@ -1209,6 +1221,69 @@ def run_resid_sliced(ctx, dev, args):
            "roofline": {"bound": "hbm", "achieved": slice_bytes / ms["sliced_step"] / 1e6, "peak": hbm,
                         "unit": "GB/s", "frac": slice_bytes / ms["sliced_step"] / 1e6 / hbm, "peak_source": src},
            "nctas": ctx.last_launch()["nctas"]}
+    print(json.dumps(out))
+    ctx.close()
+
+
+def run_trmm_sliced(ctx, dev, args):
+    """64 panel products L_i = fp64(W_i) U (b = 512) in one launch: TRMM_SL
+    from slices (SLICE_W / SLICE_U once, untimed) against TRMM_MX (FP64
+    DFMA) on the same inputs.  Work: b^3 FP64-equivalent flop per product
+    (U triangular); the tensor-core flops of the kept slice pairs for the
+    roofline (E4M3 peak = the measured bf16 peak x 2)."""
+    import torch
+    import paper_1304_0878_b300 as b3t
+    from paper_1304_0878_b300 import tiles as dt
+    b, n = 512, 64
+    U = torch.triu(torch.randn((b, b), dtype=torch.float64, device=dev)).T.contiguous()   # tile: upper
+    W = torch.randn((n, b, b), dtype=torch.float32, device=dev)
+    L = torch.zeros((n, b, b), dtype=torch.float64, device=dev)
+    WS = torch.empty((n, b3t.slice_w_bytes(b)), dtype=torch.uint8, device=dev)
+    US = torch.empty(b3t.slice_u_bytes(b), dtype=torch.uint8, device=dev)
+    hu = ctx.data_register(U.data_ptr(), b * b, 8, b)
+    hus = ctx.data_register(US.data_ptr(), US.numel(), 1)
+    hw = [ctx.data_register(p, b * b, 4, b) for p in dt.tile_ptrs(W)]
+    hl = [ctx.data_register(p, b * b, 8, b) for p in dt.tile_ptrs(L)]
+    hws = [ctx.data_register(p, WS.shape[1], 1) for p in dt.tile_ptrs(WS)]
+    cu = ctx.task_decl("slice_u", b3t.SLICE_U, [1, 2])
+    cw = ctx.task_decl("slice_w", b3t.SLICE_W, [1, 2])
+    cm = ctx.task_decl("trmm_sl", b3t.TRMM_SL, [1, 1, 2])
+    cf = ctx.task_decl("trmm_mx", b3t.TRMM_MX, [1, 1, 2])
+    ctx.task_submit(cu, [hu, hus])
+    for i in range(n):
+        ctx.task_submit(cw, [hw[i], hws[i]])
+    ctx.task_wait()
+    graphs = {}
+    ctx.graph_capture_begin()
+    for i in range(n):
+        ctx.task_submit(cm, [hus, hws[i], hl[i]])
+    graphs["trmm_sl"] = ctx.graph_capture_end()
+    ctx.graph_capture_begin()
+    for i in range(n):
+        ctx.task_submit(cf, [hu, hw[i], hl[i]])
+    graphs["trmm_mx"] = ctx.graph_capture_end()
+    ms = {}
+    for name, g in graphs.items():
+        ts = []
+        for r in range(args.warmup + args.steps):
+            ctx.graph_replay(g)
+            ctx.task_wait()
+            if r >= args.warmup:
+                ts.append(ctx.last_launch()["kernel_ns"] / 1e6)
+        ms[name] = float(np.median(ts))
+        ctx.graph_destroy(g)
+    fp64_flops = n * float(b) ** 3
+    # tensor work: per 128 x 32 block, K = 32 (cb + 1), 78 kept pairs of E4M3 products
+    kc = sum(32 * (cb + 1) for cb in range(b // 32)) * (b // 128)
+    tensor_flops = n * 78 * 2.0 * 128 * 32 * kc
+    peak = 2.0 * bf16_peak()[0]
+    out = {"case": "trmm_sl", "workload": "%d panel products L = fp64(W) U, b = %d, U upper triangular" % (n, b),
+           "trmm_sl_ms": ms["trmm_sl"], "trmm_mx_fp64_ms": ms["trmm_mx"], "speedup": ms["trmm_mx"] / ms["trmm_sl"],
+           "fp64_equivalent_TFLOPs": fp64_flops / ms["trmm_sl"] / 1e9,
+           "fp64_dfma_TFLOPs": fp64_flops / ms["trmm_mx"] / 1e9,
+           "roofline": {"bound": "tensor", "achieved": tensor_flops / ms["trmm_sl"] / 1e9, "peak": peak,
+                        "unit": "TFLOP/s", "frac": tensor_flops / ms["trmm_sl"] / 1e9 / peak,
+                        "peak_source": "measured bf16 burst x 2 (E4M3)"}}
     print(json.dumps(out))
     ctx.close()
 

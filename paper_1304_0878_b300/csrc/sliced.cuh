@@ -107,6 +107,20 @@ __device__ __forceinline__ void sl_store16(unsigned char *dst, size_t slice_stri
     }
 }
 
+// Hint: bring bytes of global memory into L2 ahead of their bulk copy (no
+// completion to wait for; the copy that follows finds them in L2).
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
+// Chunks whose L2 prefetch runs ahead of the shared-memory ring: the ring
+// keeps ~100 KB in flight per SM, which at HBM's loaded latency caps a CTA
+// near 20 GB/s; the prefetches raise the bytes in flight without shared memory.
+#ifndef B3T_SL_PREFETCH
+#define B3T_SL_PREFETCH 12
+#endif
+constexpr uint32_t kSlPrefetch = B3T_SL_PREFETCH;
+
 // 2^k as a double (k may be below the normal range).
 __device__ __forceinline__ double sl_pow2(int k) {
     if (k >= -1022 && k <= 1023) return __longlong_as_double((long long)(k + 1023) << 52);
@@ -280,6 +294,10 @@ __device__ __noinline__ int resid_sl_item(const TaskRec &t, int item, SlState &s
     if (tid == 0) {
         asm volatile("fence.proxy.async.global;" ::: "memory");
         uint32_t issued = 0, consumed = 0, xissued = 0, xconsumed = 0;
+        auto a_src = [&](uint32_t q) -> const unsigned char * {
+            const uint32_t s = q % kSlDigits, jk = q / kSlDigits, J = jk / nk, kc = jk % nk;
+            return AS + ((size_t)i * T + J) * PB + ((size_t)(rb * nk + kc) * kSlDigits + s) * kSlChunk;
+        };
         // fill of step q: first, for s = 0, the X slices of (J, kc)
         auto issue = [&](uint32_t q) -> bool {
             const uint32_t s = q % kSlDigits, jk = q / kSlDigits, J = jk / nk, kc = jk % nk;
@@ -295,11 +313,11 @@ __device__ __noinline__ int resid_sl_item(const TaskRec &t, int item, SlState &s
             if (ga >= (uint32_t)kSlStages && !mbar_wait(&st.empty[slot], ((ga / kSlStages) - 1) & 1, limit_ns))
                 return false;
             mbar_expect_tx(&st.full[slot], kSlChunk);
-            bulk_g2s(smem + kSlAOff + slot * kSlChunk,
-                     AS + ((size_t)i * T + J) * PB + ((size_t)(rb * nk + kc) * kSlDigits + s) * kSlChunk, kSlChunk,
-                     &st.full[slot]);
+            bulk_g2s(smem + kSlAOff + slot * kSlChunk, a_src(q), kSlChunk, &st.full[slot]);
+            if (kSlPrefetch && q + kSlPrefetch < Q) bulk_prefetch_l2(a_src(q + kSlPrefetch), kSlChunk);
             return true;
         };
+        for (uint32_t q = 0; q < kSlPrefetch && q < Q; ++q) bulk_prefetch_l2(a_src(q), kSlChunk);
         for (uint32_t J = 0; J < (uint32_t)T && ok; ++J) {
             const uint32_t jt = st.nj + J, buf = jt & 1;
             // the buffer is free once the epilogue of tile jt - 2 has read it
@@ -557,6 +575,9 @@ __device__ __noinline__ int trmm_sl_item(const TaskRec &t, int item, TsState &st
         asm volatile("fence.proxy.async.global;" ::: "memory");
         bool ok = true;
         uint32_t issued = 0, consumed = 0, bissued = 0, bconsumed = 0;
+        auto w_src = [&](uint32_t q) -> const unsigned char * {
+            return WS + ((size_t)(rb * nk + q / kSlDigits) * kSlDigits + q % kSlDigits) * kSlChunk;
+        };
         auto issue = [&](uint32_t q) -> bool {
             const uint32_t s = q % kSlDigits, kc = q / kSlDigits;
             if (s == 0) {
@@ -571,10 +592,11 @@ __device__ __noinline__ int trmm_sl_item(const TaskRec &t, int item, TsState &st
             if (ga >= (uint32_t)kTsStages && !mbar_wait(&st.empty[slot], ((ga / kTsStages) - 1) & 1, limit_ns))
                 return false;
             mbar_expect_tx(&st.full[slot], kSlChunk);
-            bulk_g2s(smem + kTsAOff + slot * kSlChunk, WS + ((size_t)(rb * nk + kc) * kSlDigits + s) * kSlChunk,
-                     kSlChunk, &st.full[slot]);
+            bulk_g2s(smem + kTsAOff + slot * kSlChunk, w_src(q), kSlChunk, &st.full[slot]);
+            if (kSlPrefetch && q + kSlPrefetch < Q) bulk_prefetch_l2(w_src(q + kSlPrefetch), kSlChunk);
             return true;
         };
+        for (uint32_t q = 0; q < kSlPrefetch && q < Q; ++q) bulk_prefetch_l2(w_src(q), kSlChunk);
         for (uint32_t kc = 0; kc < nkc && ok; ++kc) {
             const uint32_t ksteps = min(4u, nks - 4 * kc);
             for (uint32_t s = 0; s < (uint32_t)kSlDigits; ++s) {
