@@ -737,9 +737,11 @@ def run_time_to_solution(ctx, A0, t, g64, N, b, dev, stream, args):
             out[name]["sliced_residual"] = sl
         ctx.graph_destroy(gm)
         ctx.tiles_unregister(qp, T)
+        # the panel forms partition the diagonal tiles differently (64- or
+        # 128-wide panels): the next variant registers the tiles anew
+        ctx.tiles_unregister(wp, T)
+        ctx.tiles_unregister(lp, T)
         del Q
-    ctx.tiles_unregister(dt.tile_ptrs(W), T)
-    ctx.tiles_unregister(dt.tile_ptrs(Lm), T)
     for p in up:
         ctx.data_unregister(ctx.data_lookup(p))
     out["host_check"] = ("host_sampled_eta: 32 sampled rows of b - A x formed in FP64 on the host from the "

@@ -13,7 +13,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libb3t.so")
 
 SOURCES = ["executor.cu", "runtime.cpp", "noalloc.cu"]
-HEADERS = ["b3t_internal.h", "tiles_fp64.cuh", "mx.cuh", "solve.cuh"]
+HEADERS = ["b3t_internal.h", "tiles_fp64.cuh", "mx.cuh", "solve.cuh", "sliced.cuh"]
 
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = [

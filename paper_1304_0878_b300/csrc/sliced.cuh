@@ -28,7 +28,7 @@
 //             one exponent per right-hand side, max|x| per 16-row group.
 //   RESID_SL  128 rows of R_i: thread 0 streams A slice chunks (16 KiB,
 //             bulk copies into a kSlStages ring) and the X slices of each
-//             K-chunk (24 KiB, two slots) and issues the MMAs (M = 128,
+//             K-chunk (24 KiB, two slots); thread 32 issues the MMAs (M = 128,
 //             K = 32; per A slice s one MMA of N = 16 (12 - s) against the
 //             stacked X slices) into twelve group accumulators per tile, in
 //             two tensor-memory buffers; warps 4-7 read a finished tile's
@@ -106,20 +106,6 @@ __device__ __forceinline__ void sl_store16(unsigned char *dst, size_t slice_stri
         *reinterpret_cast<uint4 *>(dst + (size_t)s * slice_stride) = w;
     }
 }
-
-// Hint: bring bytes of global memory into L2 ahead of their bulk copy (no
-// completion to wait for; the copy that follows finds them in L2).
-__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
-
-// Chunks whose L2 prefetch runs ahead of the shared-memory ring: the ring
-// keeps ~100 KB in flight per SM, which at HBM's loaded latency caps a CTA
-// near 20 GB/s; the prefetches raise the bytes in flight without shared memory.
-#ifndef B3T_SL_PREFETCH
-#define B3T_SL_PREFETCH 12
-#endif
-constexpr uint32_t kSlPrefetch = B3T_SL_PREFETCH;
 
 // 2^k as a double (k may be below the normal range).
 __device__ __forceinline__ double sl_pow2(int k) {
@@ -292,32 +278,49 @@ __device__ __noinline__ int resid_sl_item(const TaskRec &t, int item, SlState &s
     __syncthreads();
     bool ok = true;
     if (tid == 0) {
+        // producer: the A chunks of every step into the ring, the X set of
+        // each (J, kc) into its slot, as soon as the slot is free
         asm volatile("fence.proxy.async.global;" ::: "memory");
-        uint32_t issued = 0, consumed = 0, xissued = 0, xconsumed = 0;
+        uint32_t issued = 0, xissued = 0;
         auto a_src = [&](uint32_t q) -> const unsigned char * {
             const uint32_t s = q % kSlDigits, jk = q / kSlDigits, J = jk / nk, kc = jk % nk;
             return AS + ((size_t)i * T + J) * PB + ((size_t)(rb * nk + kc) * kSlDigits + s) * kSlChunk;
         };
-        // fill of step q: first, for s = 0, the X slices of (J, kc)
-        auto issue = [&](uint32_t q) -> bool {
+        for (uint32_t q = 0; q < Q && ok; ++q) {
             const uint32_t s = q % kSlDigits, jk = q / kSlDigits, J = jk / nk, kc = jk % nk;
             if (s == 0) {
                 const uint32_t gx = st.fx + jk, xs = gx & 1;
-                if (gx >= 2 && !mbar_wait(&st.xempty[xs], ((gx >> 1) - 1) & 1, limit_ns)) return false;
+                if (gx >= 2 && !mbar_wait(&st.xempty[xs], ((gx >> 1) - 1) & 1, limit_ns)) { ok = false; break; }
                 mbar_expect_tx(&st.xfull[xs], kSlXSet);
                 bulk_g2s(smem + kSlXOff + xs * kSlXSet, XS + (size_t)J * XB + (size_t)kc * kSlXSet, kSlXSet,
                          &st.xfull[xs]);
                 ++xissued;
             }
             const uint32_t ga = st.fa + q, slot = ga % kSlStages;
-            if (ga >= (uint32_t)kSlStages && !mbar_wait(&st.empty[slot], ((ga / kSlStages) - 1) & 1, limit_ns))
-                return false;
+            if (ga >= (uint32_t)kSlStages && !mbar_wait(&st.empty[slot], ((ga / kSlStages) - 1) & 1, limit_ns)) {
+                ok = false;
+                break;
+            }
             mbar_expect_tx(&st.full[slot], kSlChunk);
             bulk_g2s(smem + kSlAOff + slot * kSlChunk, a_src(q), kSlChunk, &st.full[slot]);
-            if (kSlPrefetch && q + kSlPrefetch < Q) bulk_prefetch_l2(a_src(q + kSlPrefetch), kSlChunk);
-            return true;
-        };
-        for (uint32_t q = 0; q < kSlPrefetch && q < Q; ++q) bulk_prefetch_l2(a_src(q), kSlChunk);
+            ++issued;
+        }
+        if (!ok) {
+            *s_fail = 1;
+            // the copies in flight land before shared memory is given up: the
+            // latest fill of each slot
+            for (uint32_t q = issued > (uint32_t)kSlStages ? issued - kSlStages : 0; q < issued; ++q) {
+                const uint32_t ga = st.fa + q;
+                mbar_wait(&st.full[ga % kSlStages], (ga / kSlStages) & 1, limit_ns);
+            }
+            for (uint32_t x = xissued > 2 ? xissued - 2 : 0; x < xissued; ++x) {
+                const uint32_t gx = st.fx + x;
+                mbar_wait(&st.xfull[gx & 1], (gx >> 1) & 1, limit_ns);
+            }
+        }
+    } else if (tid == 32) {
+        // MMA issuer: per step, once its chunks have landed, one MMA per K
+        // step over the stacked X slices
         for (uint32_t J = 0; J < (uint32_t)T && ok; ++J) {
             const uint32_t jt = st.nj + J, buf = jt & 1;
             // the buffer is free once the epilogue of tile jt - 2 has read it
@@ -327,23 +330,12 @@ __device__ __noinline__ int resid_sl_item(const TaskRec &t, int item, SlState &s
             for (uint32_t kc = 0; kc < (uint32_t)nk && ok; ++kc) {
                 for (uint32_t s = 0; s < (uint32_t)kSlDigits; ++s) {
                     const uint32_t q = (J * nk + kc) * kSlDigits + s;
-                    // fills run kSlStages - 1 steps ahead: refilling a slot waits
-                    // for the MMAs of two steps back, not of the previous one
-                    while (issued < Q && issued < q + kSlStages - 1) {
-                        if (!issue(issued)) { ok = false; break; }
-                        ++issued;
-                    }
-                    if (!ok) break;
                     const uint32_t ga = st.fa + q, slot = ga % kSlStages;
                     const uint32_t gx = st.fx + J * nk + kc, xs = gx & 1;
-                    if (s == 0) {
-                        if (!mbar_wait(&st.xfull[xs], (gx >> 1) & 1, limit_ns)) { ok = false; break; }
-                        ++xconsumed;
-                    }
+                    if (s == 0 && !mbar_wait(&st.xfull[xs], (gx >> 1) & 1, limit_ns)) { ok = false; break; }
                     if (!mbar_wait(&st.full[slot], (ga / kSlStages) & 1, limit_ns)) { ok = false; break; }
-                    ++consumed;
                     tc_fence_after();
-                    // one MMA per K step for all pairs (s, t), t = 0 .. 11 - s: the
+                    // all pairs (s, t), t = 0 .. 11 - s, in one MMA per K step: the
                     // X set is [t][16 rows][128 bytes], i.e. one K-major operand of
                     // 192 rows, and group m = s + t sits at columns 16 m, so the
                     // first 16 (12 - s) rows land on the groups s .. 11
@@ -361,21 +353,10 @@ __device__ __noinline__ int resid_sl_item(const TaskRec &t, int item, SlState &s
         }
         if (!ok) {
             *s_fail = 1;
-            // copies in flight land, and every MMA issued finishes, before the
-            // shared and tensor memory are given up
-            for (uint32_t q = consumed; q < issued; ++q) {
-                const uint32_t ga = st.fa + q;
-                mbar_wait(&st.full[ga % kSlStages], (ga / kSlStages) & 1, limit_ns);
-            }
-            for (uint32_t x = xconsumed; x < xissued; ++x) {
-                const uint32_t gx = st.fx + x;
-                mbar_wait(&st.xfull[gx & 1], (gx >> 1) & 1, limit_ns);
-            }
+            // every MMA issued finishes before tensor memory is given up
             mma_commit(st.drain);
             mbar_wait(st.drain, 0, limit_ns);
         }
-        st.fa += issued;
-        st.fx += xissued;
     } else if (warp >= 4) {
         const int q = warp & 3, row = 32 * q + lane;        // TMEM lane = row of the item
         const int gr = rb * kSlRows + row;                   // row within part i
@@ -448,6 +429,8 @@ __device__ __noinline__ int resid_sl_item(const TaskRec &t, int item, SlState &s
         for (int o = 8; o; o >>= 1) rs = fmax(rs, __shfl_xor_sync(0xffffffffu, rs, o));
         if ((lane & 15) == 0) Rn[(size_t)3 * nit * nrhs + it16] = rs;
     }
+    st.fa += Q;
+    st.fx += (uint32_t)T * nk;
     st.nj += (uint32_t)T;
     if (__syncthreads_or(*s_fail || !ok)) return ETIMEDOUT;
     return 0;
@@ -468,8 +451,8 @@ __device__ __noinline__ int resid_sl_item(const TaskRec &t, int item, SlState &s
 //             slices as chunk sets (cb, kc) of 12 x (32 rows x 128 bytes).
 //   TRMM_SL   a 128 x 32 block of L_ik per item.  Thread 0 streams the W
 //             chunks of the block's rows (16 KiB, 4-stage ring) and the U
-//             chunk set of each K chunk (48 KiB, two slots), and issues per
-//             W slice s the MMAs against the stacked U slices: group m =
+//             chunk set of each K chunk (48 KiB, two slots); thread 32
+//             issues per W slice s the MMAs against the stacked U slices: group m =
 //             s + t at TMEM columns 32 m, N = 32 (12 - s) (two MMAs, 256 and
 //             32 (4 - s) columns, for s < 4).  U_k is zero below the
 //             diagonal, so the K range stops at the block's last column.
@@ -572,48 +555,55 @@ __device__ __noinline__ int trmm_sl_item(const TaskRec &t, int item, TsState &st
     if (tid == 0) *s_fail = 0;
     __syncthreads();
     if (tid == 0) {
+        // producer: the W chunks of the block's rows and the U chunk set of
+        // each K chunk, as soon as their slots are free
         asm volatile("fence.proxy.async.global;" ::: "memory");
         bool ok = true;
-        uint32_t issued = 0, consumed = 0, bissued = 0, bconsumed = 0;
+        uint32_t issued = 0, bissued = 0;
         auto w_src = [&](uint32_t q) -> const unsigned char * {
             return WS + ((size_t)(rb * nk + q / kSlDigits) * kSlDigits + q % kSlDigits) * kSlChunk;
         };
-        auto issue = [&](uint32_t q) -> bool {
+        for (uint32_t q = 0; q < Q && ok; ++q) {
             const uint32_t s = q % kSlDigits, kc = q / kSlDigits;
             if (s == 0) {
                 const uint32_t gb = st.fb + kc, bs = gb & 1;
-                if (gb >= 2 && !mbar_wait(&st.bempty[bs], ((gb >> 1) - 1) & 1, limit_ns)) return false;
+                if (gb >= 2 && !mbar_wait(&st.bempty[bs], ((gb >> 1) - 1) & 1, limit_ns)) { ok = false; break; }
                 mbar_expect_tx(&st.bfull[bs], kTsBSet);
                 bulk_g2s(smem + kTsBOff + bs * kTsBSet, US + (size_t)(cb * nk + kc) * kTsBSet, kTsBSet,
                          &st.bfull[bs]);
                 ++bissued;
             }
             const uint32_t ga = st.fa + q, slot = ga % kTsStages;
-            if (ga >= (uint32_t)kTsStages && !mbar_wait(&st.empty[slot], ((ga / kTsStages) - 1) & 1, limit_ns))
-                return false;
+            if (ga >= (uint32_t)kTsStages && !mbar_wait(&st.empty[slot], ((ga / kTsStages) - 1) & 1, limit_ns)) {
+                ok = false;
+                break;
+            }
             mbar_expect_tx(&st.full[slot], kSlChunk);
             bulk_g2s(smem + kTsAOff + slot * kSlChunk, w_src(q), kSlChunk, &st.full[slot]);
-            if (kSlPrefetch && q + kSlPrefetch < Q) bulk_prefetch_l2(w_src(q + kSlPrefetch), kSlChunk);
-            return true;
-        };
-        for (uint32_t q = 0; q < kSlPrefetch && q < Q; ++q) bulk_prefetch_l2(w_src(q), kSlChunk);
+            ++issued;
+        }
+        if (!ok) {
+            *s_fail = 1;
+            for (uint32_t q = issued > (uint32_t)kTsStages ? issued - kTsStages : 0; q < issued; ++q) {
+                const uint32_t ga = st.fa + q;
+                mbar_wait(&st.full[ga % kTsStages], (ga / kTsStages) & 1, limit_ns);
+            }
+            for (uint32_t x = bissued > 2 ? bissued - 2 : 0; x < bissued; ++x) {
+                const uint32_t gb = st.fb + x;
+                mbar_wait(&st.bfull[gb & 1], (gb >> 1) & 1, limit_ns);
+            }
+        }
+    } else if (tid == 32) {
+        // MMA issuer
+        bool ok = true;
         for (uint32_t kc = 0; kc < nkc && ok; ++kc) {
             const uint32_t ksteps = min(4u, nks - 4 * kc);
             for (uint32_t s = 0; s < (uint32_t)kSlDigits; ++s) {
                 const uint32_t q = kc * kSlDigits + s;
-                while (issued < Q && issued < q + kTsStages - 1) {
-                    if (!issue(issued)) { ok = false; break; }
-                    ++issued;
-                }
-                if (!ok) break;
                 const uint32_t ga = st.fa + q, slot = ga % kTsStages;
                 const uint32_t gb = st.fb + kc, bs = gb & 1;
-                if (s == 0) {
-                    if (!mbar_wait(&st.bfull[bs], (gb >> 1) & 1, limit_ns)) { ok = false; break; }
-                    ++bconsumed;
-                }
+                if (s == 0 && !mbar_wait(&st.bfull[bs], (gb >> 1) & 1, limit_ns)) { ok = false; break; }
                 if (!mbar_wait(&st.full[slot], (ga / kTsStages) & 1, limit_ns)) { ok = false; break; }
-                ++consumed;
                 tc_fence_after();
                 const uint64_t ad = sw128_desc(smem_u32(smem + kTsAOff + slot * kSlChunk));
                 const uint64_t bd = sw128_desc(smem_u32(smem + kTsBOff + bs * kTsBSet));
@@ -634,22 +624,14 @@ __device__ __noinline__ int trmm_sl_item(const TaskRec &t, int item, TsState &st
         }
         if (!ok) {
             *s_fail = 1;
-            for (uint32_t q = consumed; q < issued; ++q) {
-                const uint32_t ga = st.fa + q;
-                mbar_wait(&st.full[ga % kTsStages], (ga / kTsStages) & 1, limit_ns);
-            }
-            for (uint32_t x = bconsumed; x < bissued; ++x) {
-                const uint32_t gb = st.fb + x;
-                mbar_wait(&st.bfull[gb & 1], (gb >> 1) & 1, limit_ns);
-            }
             mma_commit(st.drain);
             mbar_wait(st.drain, 0, limit_ns);
         } else {
             mma_commit(st.done);
         }
-        st.fa += issued;
-        st.fb += bissued;
     }
+    st.fa += Q;
+    st.fb += nkc;
     __syncthreads();
     bool ok = *s_fail == 0;
     if (ok && !mbar_wait(st.done, st.nd & 1, limit_ns)) ok = false;
