@@ -131,7 +131,8 @@ enum b3t_kind {
     B3T_RESID_SL = 26,
     B3T_SLICE_W = 27,
     B3T_SLICE_U = 28,
-    B3T_TRMM_SL = 29
+    B3T_TRMM_SL = 29,
+    B3T_TRTRI_COL = 30
 };
 
 /* Diagonal tile split into column panels.  A b x b diagonal tile partitioned
@@ -147,6 +148,15 @@ enum b3t_kind {
  *                  P_jj(r, :) -= P_kk(r, :) P_kk(jj*pw.., :)^T for rows
  *                  r >= jj*pw (lower part on the diagonal block)
  *  Scalars: struct b3t_panel_args; col0 offsets POTRF info like B3T_POTRF.
+ *  B3T_TRTRI_COL   P_cb (R, panel part cb of L_kk, pw = 64), V_{cb-1} (R),
+ *                  V_cb (W): column block cb (columns 64 cb ..) of U_k =
+ *                  L_kk^{-T}, V_j being U_k's column blocks (a partition of
+ *                  the U tile into b x 64 parts; cb = 0 names V_0 twice).  The
+ *                  block needs the columns before it and rows 64 cb .. of
+ *                  L_kk, final once panel cb is factored, so the blocks follow
+ *                  the panel DAG instead of the whole diagonal factor; the
+ *                  same per-element operations as B3T_TRTRI.  Scalars: struct
+ *                  b3t_panel_args with kk = cb.
  *  B3T_CVT         W_kk (R, f32 tile), L_kk (W, f64 tile): L = fp64(W) on the
  *                  lower triangle, 0 above; no scalars.
  *  B3T_TRTRI       L_kk (R, f64 tile), U_k (W, f64 tile): U_k = L_kk^{-T}

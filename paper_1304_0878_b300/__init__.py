@@ -11,7 +11,7 @@ from ._lib import (Context, B3TError, Config, lib, strerror, q_bytes, header_sym
                    ir_work_elems, resid_part_elems, vec_args, TRSV_L, GEMV_L, TRSV_LT, GEMV_LT, AXPY, RESID, NRM,
                    VEC_F32, VEC_ASSIGN, VEC_LOWER_M, VEC_UPPER_M, TRTRI, TRMM_MX,
                    SLICE_A, SLICE_X, RESID_SL, SLICE_W, SLICE_U, TRMM_SL, ir_slice_bytes, slice_a_part_bytes,
-                   slice_x_part_bytes, slice_w_bytes, slice_u_bytes, slice_args,
+                   slice_x_part_bytes, slice_w_bytes, slice_u_bytes, slice_args, TRTRI_COL,
                    pack_f32, pack_i32, R, W, RW, NOOP, SCAL_F32, POTRF, TRSM, SYRK, GEMM,
                    POTRF_MX, TRSM_MX, SYRK_MX, GEMM_MX, QUANT, FMT_BF16, FMT_E4M3,
                    PRIO_UPWARD, PRIO_DEPTH)

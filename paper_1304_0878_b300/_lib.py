@@ -25,6 +25,7 @@ TRSV_L, GEMV_L, TRSV_LT, GEMV_LT, AXPY, RESID, NRM = 11, 12, 13, 14, 15, 16, 17
 VEC_F32, VEC_ASSIGN, VEC_LOWER_M, VEC_UPPER_M, VEC_KEEP_NORM = 1, 2, 4, 8, 16
 POTRF_D, PANEL_TRSM, PANEL_UPD, CVT, TRTRI, TRMM_MX = 18, 19, 20, 21, 22, 23
 SLICE_A, SLICE_X, RESID_SL, SLICE_W, SLICE_U, TRMM_SL = 24, 25, 26, 27, 28, 29
+TRTRI_COL = 30
 
 
 class B3TError(RuntimeError):

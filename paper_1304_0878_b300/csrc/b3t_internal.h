@@ -61,6 +61,8 @@ struct PanelArgs {
     int32_t b, pw, kk, jj, col0;
 };
 constexpr int kPanelWidth = 128;          // panel width used by the Cholesky helpers
+constexpr int kPanelTrsmRows = 16;        // PANEL_TRSM item: rows below the diagonal block
+constexpr int kPanelUpdRows = 32;         // PANEL_UPD item: rows x 64 columns
 
 // Elements of one part of the residual work area: b*nrhs values, then per
 // RESID item the maxima |r_j| and |x_j| and the largest row sum of |A|.
@@ -75,8 +77,8 @@ enum : int32_t {
     kPotrfMx = 6, kTrsmMx = 7, kSyrkMx = 8, kGemmMx = 9, kQuant = 10,
     kTrsvL = 11, kGemvL = 12, kTrsvLT = 13, kGemvLT = 14, kAxpy = 15, kResid = 16, kNrm = 17,
     kPotrfD = 18, kPanelTrsm = 19, kPanelUpd = 20, kCvt = 21, kTrtri = 22, kTrmmMx = 23,
-    kSliceA = 24, kSliceX = 25, kResidSl = 26, kSliceW = 27, kSliceU = 28, kTrmmSl = 29,
-    kNumKinds = 30
+    kSliceA = 24, kSliceX = 25, kResidSl = 26, kSliceW = 27, kSliceU = 28, kTrmmSl = 29, kTrtriCol = 30,
+    kNumKinds = 31
 };
 
 // Sliced FP64 residual (the Ozaki scheme: exact products of integer digit
@@ -184,7 +186,8 @@ B3T_HD constexpr uint32_t family_of(int kind) {
     return kind == kScalF32 ? kFamScal
          : (kind == kPotrf || kind == kTrsm || kind == kSyrk || kind == kGemm || kind == kPotrfD ||
             kind == kPanelTrsm || kind == kPanelUpd) ? kFamF64
-         : ((kind >= kTrsvL && kind <= kNrm) || kind == kTrtri || kind == kSliceA || kind == kSliceX) ? kFamSolve
+         : ((kind >= kTrsvL && kind <= kNrm) || kind == kTrtri || kind == kTrtriCol || kind == kSliceA ||
+            kind == kSliceX) ? kFamSolve
          : (kind == kSliceW || kind == kSliceU || kind == kTrmmSl) ? kFamMx
          : (kind >= kPotrfMx && kind <= kQuant) || kind == kCvt || kind == kTrmmMx || kind == kResidSl ? kFamMx
          : 0u;   // NOOP runs in every variant

@@ -681,6 +681,7 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
                 }
                 break;
             case kTrtri: if constexpr (kSolve) trtri_item(rec, it, (double *)smem); break;
+            case kTrtriCol: if constexpr (kSolve) trtri_col_item(rec, it, (double *)smem); break;
             case kSliceW: if constexpr (kMx) slice_w_item(rec, it, smem); break;
             case kSliceU: if constexpr (kMx) slice_u_item(rec, it, smem); break;
             case kTrmmSl:

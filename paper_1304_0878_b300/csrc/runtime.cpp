@@ -129,14 +129,16 @@ const KindSig kSigs[kNumKinds] = {
     /* SLICE_W  */ {2, {B3T_R, B3T_W}, {4, 1}, 0, false},
     /* SLICE_U  */ {2, {B3T_R, B3T_W}, {8, 1}, 0, false},
     /* TRMM_SL  */ {3, {B3T_R, B3T_R, B3T_W}, {1, 1, 8}, 0, false},
+    /* TRTRI_CO */ {3, {B3T_R, B3T_R, B3T_W}, {8, 8, 8}, sizeof(PanelArgs), false},
 };
 
 const char *kKindNames[kNumKinds] = {"noop", "scal_f32", "potrf", "trsm", "syrk", "gemm",
                                      "potrf_mx", "trsm_mx", "syrk_mx", "gemm_mx", "quant",
                                      "trsv_l", "gemv_l", "trsv_lt", "gemv_lt", "axpy", "resid", "nrm",
                                      "potrf_d", "panel_trsm", "panel_upd", "cvt", "trtri", "trmm_mx",
-                                     "slice_a", "slice_x", "resid_sl", "slice_w", "slice_u", "trmm_sl"};
-bool is_panel(int kind) { return kind >= kPotrfD && kind <= kPanelUpd; }
+                                     "slice_a", "slice_x", "resid_sl", "slice_w", "slice_u", "trmm_sl",
+                                     "trtri_col"};
+bool is_panel(int kind) { return (kind >= kPotrfD && kind <= kPanelUpd) || kind == kTrtriCol; }
 bool is_vec(int kind) { return kind >= kTrsvL && kind <= kNrm; }
 
 bool is_mx(int kind) { return kind == kSyrkMx || kind == kGemmMx || kind == kResidSl || kind == kTrmmSl; }
@@ -664,6 +666,7 @@ int submit_impl(b3t_ctx *c, b3t_codelet cl, const b3t_handle *handles, const uin
         bool ok = (a.pw == 64 || a.pw == 128) && a.b >= a.pw && a.b <= 4096 && a.b % a.pw == 0 &&
                   a.kk >= 0 && a.kk < np && a.col0 >= 0;
         if (C.kind == kPanelTrsm) ok = ok && a.kk < np - 1;
+        if (C.kind == kTrtriCol) ok = ok && a.pw == 64;
         if (C.kind == kPanelUpd) ok = ok && a.jj > a.kk && a.jj < np;
         for (int i = 0; ok && i < nbuffers; ++i) {
             const Handle &H = c->handles[handles[i]];
@@ -676,12 +679,16 @@ int submit_impl(b3t_ctx *c, b3t_codelet cl, const b3t_handle *handles, const uin
         const double bb = a.b, pw = a.pw;
         if (C.kind == kPotrfD) { r.nitems = 1; pcost = (float)(pw * pw * pw / 3.0 / 3.7 + 20000.0); }
         if (C.kind == kPanelTrsm) {
-            r.nitems = (a.b - (a.kk + 1) * a.pw) / kTrsmRows;
-            pcost = (float)(kTrsmRows * pw * pw / 3.7 + 5000.0);
+            r.nitems = (a.b - (a.kk + 1) * a.pw) / kPanelTrsmRows;
+            pcost = (float)(kPanelTrsmRows * pw * pw / 3.7 + 5000.0);
         }
         if (C.kind == kPanelUpd) {
-            r.nitems = ((a.b - a.jj * a.pw) / 64) * (a.pw / 64);
-            pcost = (float)(2.0 * 64 * 64 * pw / 3.7 + 5000.0);
+            r.nitems = ((a.b - a.jj * a.pw) / kPanelUpdRows) * (a.pw / 64);
+            pcost = (float)(2.0 * kPanelUpdRows * 64 * pw / 3.7 + 5000.0);
+        }
+        if (C.kind == kTrtriCol) {
+            r.nitems = a.b / kTrtriRows;
+            pcost = (float)(kTrtriRows * 64.0 * (a.kk + 1) * 64.0 / 3.7 + 5000.0);
         }
         (void)bb;
     }
@@ -1647,8 +1654,9 @@ int b3t_cholesky_mx_sliced_submit(b3t_ctx *c, float *const *W, double *const *L,
         }
     for (int32_t k = 0; k + 1 < T; ++k)
         if ((rc = reg_bytes(c, US[k], (size_t)sl_u_bytes(b), &hus[k]))) return rc;
-    b3t_codelet cp, ci, csu, csw, cm, cq, cs, cg, cc;
+    b3t_codelet cp, ci, ctc, csu, csw, cm, cq, cs, cg, cc;
     if ((rc = kind_codelet(c, kPotrfMx, &cp)) || (rc = kind_codelet(c, kTrtri, &ci)) ||
+        (rc = kind_codelet(c, kTrtriCol, &ctc)) ||
         (rc = kind_codelet(c, kSliceU, &csu)) || (rc = kind_codelet(c, kSliceW, &csw)) ||
         (rc = kind_codelet(c, kTrmmSl, &cm)) || (rc = kind_codelet(c, kQuant, &cq)) ||
         (rc = kind_codelet(c, kSyrkMx, &cs)) || (rc = kind_codelet(c, kGemmMx, &cg)) ||
@@ -1672,8 +1680,21 @@ int b3t_cholesky_mx_sliced_submit(b3t_ctx *c, float *const *W, double *const *L,
             return rc;
         }
         if (k + 1 < T) {
-            const b3t_handle hi[2] = {hl[tidx(k, k, T)], hu[k]};
-            if ((rc = submit_impl(c, ci, hi, nullptr, 2, nullptr, 0))) return rc;
+            if (pw == 64) {
+                // U_k column block by column block, each as soon as its rows of
+                // L_kk are final (after panel cb of the diagonal DAG), so that
+                // only the last block follows the diagonal factor
+                std::vector<b3t_handle> up;
+                if ((rc = panel_parts(c, hu[k], b, pw, up))) return rc;
+                for (int32_t cb = 0; cb < b / pw; ++cb) {
+                    PanelArgs a{b, pw, cb, 0, 0};
+                    const b3t_handle h3[3] = {dparts[k][cb], up[cb > 0 ? cb - 1 : 0], up[cb]};
+                    if ((rc = submit_impl(c, ctc, h3, nullptr, 3, &a, sizeof(a)))) return rc;
+                }
+            } else {
+                const b3t_handle hi[2] = {hl[tidx(k, k, T)], hu[k]};
+                if ((rc = submit_impl(c, ci, hi, nullptr, 2, nullptr, 0))) return rc;
+            }
             const b3t_handle hsu[2] = {hu[k], hus[k]};
             if ((rc = submit_impl(c, csu, hsu, nullptr, 2, nullptr, 0))) return rc;
         }

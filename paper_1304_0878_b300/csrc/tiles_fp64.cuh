@@ -21,37 +21,50 @@ constexpr int kKc = 32;            // K chunk staged in shared memory
 // C(crow0.., ccol0..) (64 x 64 block) -= A(arow0.., 0..K) * B(brow0.., 0..K)^T,
 // all column-major with leading dimension ld.  lower_only: write only the
 // entries with row - lower_shift >= column.
-__device__ __forceinline__ void gemm64_f64(const double *A, int arow0, const double *B, int brow0,
-                                           double *C, int crow0, int ccol0, int K, int ld, bool lower_only,
-                                           int lower_shift, double *smem) {
+// C(crow0.., ccol0..) (RM x 64 block) -= A(arow0.., 0..K) * B(brow0.., 0..K)^T,
+// all column-major with leading dimension ld.  lower_only: write only the
+// entries with row - lower_shift >= column.  Thread (tx, ty) owns rows
+// tx + 16 i (i < RM / 16) and columns ty + 16 j (j < 4); p ascending, one
+// FMA per term.
+template <int RM = 64>
+__device__ __forceinline__ void gemm_rows_f64(const double *A, int arow0, const double *B, int brow0,
+                                              double *C, int crow0, int ccol0, int K, int ld, bool lower_only,
+                                              int lower_shift, double *smem) {
+    static_assert(RM == 16 || RM == 32 || RM == 64, "rows per block");
+    constexpr int NI = RM / 16;
     const int b = ld;
-    double *As = smem;                   // [kKc][64]
-    double *Bs = smem + kKc * 64;        // [kKc][64]
+    double *As = smem;                   // [kKc][RM]
+    double *Bs = smem + kKc * RM;        // [kKc][64]
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
-    double acc[4][4];
+    double acc[NI][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < NI; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
     for (int k0 = 0; k0 < K; k0 += kKc) {
 #pragma unroll
+        for (int q = 0; q < (kKc * RM) / kThreads; ++q) {
+            const int e = tid + q * kThreads;
+            const int r = e % RM, p = e / RM;
+            As[p * RM + r] = A[(size_t)(arow0 + r) + (size_t)(k0 + p) * b];
+        }
+#pragma unroll
         for (int q = 0; q < (kKc * 64) / kThreads; ++q) {
             const int e = tid + q * kThreads;
             const int r = e & 63, p = e >> 6;
-            As[p * 64 + r] = A[(size_t)(arow0 + r) + (size_t)(k0 + p) * b];
             Bs[p * 64 + r] = B[(size_t)(brow0 + r) + (size_t)(k0 + p) * b];
         }
         __syncthreads();
 #pragma unroll 8
         for (int p = 0; p < kKc; ++p) {
-            double a[4], bb[4];
+            double a[NI], bb[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[p * 64 + tx + 16 * i];
+            for (int i = 0; i < NI; ++i) a[i] = As[p * RM + tx + 16 * i];
 #pragma unroll
             for (int j = 0; j < 4; ++j) bb[j] = Bs[p * 64 + ty + 16 * j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < NI; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
         }
@@ -60,13 +73,19 @@ __device__ __forceinline__ void gemm64_f64(const double *A, int arow0, const dou
 #pragma unroll
     for (int j = 0; j < 4; ++j)
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < NI; ++i) {
             const int r = crow0 + tx + 16 * i, c = ccol0 + ty + 16 * j;
             if (!lower_only || r - lower_shift >= c) {
                 double *p = C + (size_t)r + (size_t)c * b;
                 *p = *p - acc[i][j];
             }
         }
+}
+
+__device__ __forceinline__ void gemm64_f64(const double *A, int arow0, const double *B, int brow0,
+                                           double *C, int crow0, int ccol0, int K, int ld, bool lower_only,
+                                           int lower_shift, double *smem) {
+    gemm_rows_f64<64>(A, arow0, B, brow0, C, crow0, ccol0, K, ld, lower_only, lower_shift, smem);
 }
 
 __device__ __forceinline__ void gemm_item(const TaskRec &t, int item, double *smem) {
@@ -103,12 +122,16 @@ __device__ __forceinline__ void syrk_item(const TaskRec &t, int item, double *sm
 // kPipe: the next K chunk is loaded into registers while the current one is
 // used (one memory latency per item instead of one per chunk; more
 // registers, so only the out-of-line mixed-precision TRSM uses it).
+// Columns c_lo .. c_hi - 1 (64-column blocks) of rows r0 .. r0 + RB - 1; the
+// columns before c_lo must be final in X already (the column-block TRTRI).
 template <typename Tin, bool kIdent = false, bool kPipe = false, int RB = kTrsmRows>
 __device__ __forceinline__ void trsm_rows(const double *L, const Tin *Ain, double *X, int r0, int n, int ld,
-                                          double *smem) {
+                                          double *smem, int c_lo = 0, int c_hi = -1) {
     static_assert(RB == 8 || RB == 16 || RB == 32, "rows per item");
     const int b = ld;
-    const int cs = kIdent ? (r0 / 64) * 64 : 0;     // first column block that can be nonzero
+    if (c_hi < 0) c_hi = n;
+    const int cz = kIdent ? (r0 / 64) * 64 : 0;     // first column block that can be nonzero
+    const int cs = cz > c_lo ? cz : c_lo;
     constexpr int RS = RB + 1;              // padded row stride of the row-major staging
     constexpr int NG = kThreads / RB;       // column groups: thread (tr, tw) owns row tr
     constexpr int NC = 64 / NG;             // and columns tw + NG j, j < NC, of a block
@@ -119,12 +142,12 @@ __device__ __forceinline__ void trsm_rows(const double *L, const Tin *Ain, doubl
     const int tid = threadIdx.x;
     const int tr = tid % RB, tw = tid / RB;
     if (kIdent) {
-        for (int c0 = 0; c0 < cs; c0 += 64) {
+        for (int c0 = c_lo; c0 < cz && c0 < c_hi; c0 += 64) {
 #pragma unroll
             for (int j = 0; j < NC; ++j) X[(size_t)(r0 + tr) + (size_t)(c0 + tw + NG * j) * b] = 0.0;
         }
     }
-    for (int c0 = cs; c0 < n; c0 += 64) {
+    for (int c0 = cs; c0 < c_hi; c0 += 64) {
         double acc[NC];
 #pragma unroll
         for (int j = 0; j < NC; ++j) {
@@ -133,19 +156,21 @@ __device__ __forceinline__ void trsm_rows(const double *L, const Tin *Ain, doubl
         }
         constexpr int NX = (RB * kKc) / kThreads, NL = (64 * kKc) / kThreads;
         double xv[kPipe ? NX : 1], lv[kPipe ? NL : 1];
-        if (kPipe && cs < c0) {
+        if (kPipe && cz < c0) {
 #pragma unroll
             for (int q = 0; q < NX; ++q) {
                 const int e = tid + q * kThreads;
-                xv[q] = X[(size_t)(r0 + e % RB) + (size_t)(cs + e / RB) * b];
+                xv[q] = X[(size_t)(r0 + e % RB) + (size_t)(cz + e / RB) * b];
             }
 #pragma unroll
             for (int q = 0; q < NL; ++q) {
                 const int e = tid + q * kThreads;
-                lv[q] = L[(size_t)(c0 + (e & 63)) + (size_t)(cs + (e >> 6)) * b];
+                lv[q] = L[(size_t)(c0 + (e & 63)) + (size_t)(cz + (e >> 6)) * b];
             }
         }
-        for (int k0 = cs; k0 < c0; k0 += kKc) {
+        // the sum runs over every column block that can be nonzero, also
+        // those computed before c_lo
+        for (int k0 = cz; k0 < c0; k0 += kKc) {
 #pragma unroll
             for (int q = 0; q < NX; ++q) {
                 const int e = tid + q * kThreads;
@@ -386,6 +411,31 @@ __device__ __forceinline__ void potrf_panel_rows(double *A, int ld, int rr0, int
     }
 }
 
+// Step (3) of potrf_block: rows jb + 32.. of the 32 columns from jb, solved
+// against the factored 32 x 32 block Dg, one row per thread.  Right-looking:
+// once x[c] is final it is subtracted from every later column, so each x[c']
+// takes the terms q = 0, 1, .. in the same order as a left-looking sum (the
+// same roundings), but a row's dependent chain is one division and one FMA
+// per column instead of c FMAs and a division (on B300 a dependent FP64 FMA
+// takes 64 cycles whatever the number of active lanes).  Out of line: its 32
+// live values stay out of the caller's register budget.
+__device__ __noinline__ void potrf_rows_below(double *A, int b, int ld, int jb, const double *Dg) {
+    constexpr int PW = 32;
+    for (int i = jb + PW + (int)threadIdx.x; i < b; i += kThreads) {
+        double x[PW];
+#pragma unroll
+        for (int c = 0; c < PW; ++c) x[c] = A[(size_t)i + (size_t)(jb + c) * ld];
+#pragma unroll
+        for (int c = 0; c < PW; ++c) {
+            x[c] = x[c] / Dg[c * 33 + c];
+#pragma unroll
+            for (int c2 = c + 1; c2 < PW; ++c2) x[c2] = fma(-x[c], Dg[c2 * 33 + c], x[c2]);
+        }
+#pragma unroll
+        for (int c = 0; c < PW; ++c) A[(size_t)i + (size_t)(jb + c) * ld] = x[c];
+    }
+}
+
 // Cholesky of one n x n block in place (lower, leading dimension ld), one
 // CTA, left-looking over panels of 32 columns.  Returns 0 or the 1-based
 // column (within the block) of the first pivot that is <= 0 or NaN.
@@ -435,20 +485,7 @@ __device__ __forceinline__ int potrf_block(double *A, int n, int ld, double *sme
             if (i >= k) A[(size_t)(jb + i) + (size_t)(jb + k) * ld] = Dg[i * 33 + k];
         }
         // (3) rows below the block: X Dg^T = P, one row per thread
-        for (int i = jb + PW + tid; i < b; i += kThreads) {
-            double x[PW];
-#pragma unroll
-            for (int c = 0; c < PW; ++c) x[c] = A[(size_t)i + (size_t)(jb + c) * ld];
-#pragma unroll
-            for (int c = 0; c < PW; ++c) {
-                double s = x[c];
-#pragma unroll
-                for (int q = 0; q < c; ++q) s = fma(-x[q], Dg[c * 33 + q], s);
-                x[c] = s / Dg[c * 33 + c];
-            }
-#pragma unroll
-            for (int c = 0; c < PW; ++c) A[(size_t)i + (size_t)(jb + c) * ld] = x[c];
-        }
+        potrf_rows_below(A, b, ld, jb, Dg);
         __syncthreads();
     }
     return 0;
@@ -466,6 +503,20 @@ __device__ __forceinline__ int pn_jj(const TaskRec &t) { return (int)((t.scal >>
 __device__ __forceinline__ int pn_pw(const TaskRec &t) { return (int)(t.scal >> 16); }
 
 // POTRF of the diagonal block of panel kk (rows kk*pw.., pw x pw)
+// TRTRI of one 64-column block cb of U_k = L_kk^{-T}: rows r0 .. r0 + 7 of
+// columns 64 cb .. 64 cb + 63, from the columns before it (earlier TRTRI_COL
+// tasks) and rows 64 cb .. 64 cb + 63 of L_kk, which are final once panel cb
+// of the diagonal factor is done; rows below the block get zeros.  The same
+// per-element operations as TRTRI.  Record: buf[0] = panel part cb of L_kk,
+// buf[2] = column block cb of U_k (the tiles' bases are 64 cb columns before).
+__device__ __noinline__ void trtri_col_item(const TaskRec &t, int item, double *smem) {
+    const int b = (int)t.n, cb = pn_kk(t), c0 = cb * 64;
+    const double *L = (const double *)t.buf[0] - (size_t)c0 * b;
+    double *U = (double *)t.buf[2] - (size_t)c0 * b;
+    trsm_rows<double, true, true, kTrtriRows>(L, (const double *)nullptr, U, item * kTrtriRows, b, b, smem, c0,
+                                              c0 + 64);
+}
+
 __device__ __forceinline__ int potrf_d_item(const TaskRec &t, double *smem, int *s_info) {
     const int b = (int)t.n, kk = pn_kk(t), pw = pn_pw(t);
     double *P = (double *)t.buf[0];
@@ -473,23 +524,28 @@ __device__ __forceinline__ int potrf_d_item(const TaskRec &t, double *smem, int 
     return info ? kk * pw + info : 0;
 }
 
-// rows below the diagonal block of panel kk: X L_d^T = P, 32 rows per item
+// rows below the diagonal block of panel kk: X L_d^T = P, kPanelTrsmRows
+// rows per item (the next panel's update waits for every item: short items
+// keep the diagonal chain short)
 __device__ __forceinline__ void panel_trsm_item(const TaskRec &t, int item, double *smem) {
     const int b = (int)t.n, kk = pn_kk(t), pw = pn_pw(t);
     double *P = (double *)t.buf[0];
-    trsm_rows<double>(P + (size_t)kk * pw, P, P, (kk + 1) * pw + item * kTrsmRows, pw, b, smem);
+    trsm_rows<double, false, false, kPanelTrsmRows>(P + (size_t)kk * pw, P, P,
+                                                    (kk + 1) * pw + item * kPanelTrsmRows, pw, b, smem);
 }
 
 // panel jj -= panel kk(rows jj*pw.., :) panel kk(jj*pw..jj*pw+pw, :)^T, rows
-// from jj*pw (lower part on the diagonal block); 64 x 64 blocks per item
+// from jj*pw (lower part on the diagonal block); blocks of kPanelUpdRows x 64
+// per item (the update of the next panel is on the diagonal chain)
 __device__ __forceinline__ void panel_upd_item(const TaskRec &t, int item, double *smem) {
     const int b = (int)t.n, jj = pn_jj(t), pw = pn_pw(t);
     const double *Pk = (const double *)t.buf[0];
     double *Pj = (double *)t.buf[1];
     const int nc = pw / 64;
     const int bi = item / nc, bj = item % nc;
-    const int row0 = jj * pw + bi * 64;
-    gemm64_f64(Pk, row0, Pk, jj * pw + bj * 64, Pj, row0, bj * 64, pw, b, bi * 64 < pw, jj * pw, smem);
+    const int row0 = jj * pw + bi * kPanelUpdRows;
+    gemm_rows_f64<kPanelUpdRows>(Pk, row0, Pk, jj * pw + bj * 64, Pj, row0, bj * 64, pw, b,
+                                 bi * kPanelUpdRows < pw, jj * pw, smem);
 }
 
 }  // namespace b3t

@@ -15,7 +15,7 @@ KIND_NAMES = {getattr(_lib, n): n for n in (
     "NOOP", "SCAL_F32", "POTRF", "TRSM", "SYRK", "GEMM", "POTRF_MX", "TRSM_MX", "SYRK_MX", "GEMM_MX", "QUANT",
     "TRSV_L", "GEMV_L", "TRSV_LT", "GEMV_LT", "AXPY", "RESID", "NRM", "POTRF_D", "PANEL_TRSM", "PANEL_UPD",
     "CVT", "TRTRI", "TRMM_MX", "SLICE_A", "SLICE_X", "RESID_SL",
-    "SLICE_W", "SLICE_U", "TRMM_SL")}
+    "SLICE_W", "SLICE_U", "TRMM_SL", "TRTRI_COL")}
 
 
 def task_spans(records, ntasks):

@@ -351,3 +351,36 @@ def test_sliced_factor_every_task_within_its_bound(orc, gctx, fmt, N, b):
     r = check_factor(A, Wt.cpu().numpy(), Lt.cpu().numpy(), Q, T, b, fmt, Ut.cpu().numpy(), sliced=True)
     assert r["quant"] == 0.0, r
     assert all(v <= 1.0 for v in r.values()), r
+
+
+@pytest.mark.parametrize("b", [128, 256, 512])
+def test_trtri_by_column_blocks_equals_trtri(orc, gctx, b):
+    # U_k = L_kk^{-T} one 64-column block at a time (TRTRI_COL, each block
+    # from the blocks before it) is TRTRI's result bit for bit
+    from oracle import tiles as otl
+    A = synth.spd_host(b, seed=b + 11, shift=1.0)
+    Lkk = np.asfortranarray(np.tril(A))
+    assert otl.potrf(Lkk) == 0
+    L = dev_tile(np.tril(Lkk))
+    U1 = torch.full((b, b), float("nan"), dtype=torch.float64, device="cuda")
+    U2 = torch.full((b, b), float("nan"), dtype=torch.float64, device="cuda")
+    hl = gctx.data_register(L.data_ptr(), b * b, 8, b)
+    h1 = gctx.data_register(U1.data_ptr(), b * b, 8, b)
+    h2 = gctx.data_register(U2.data_ptr(), b * b, 8, b)
+    ci = gctx.task_decl("trtri", b3t.TRTRI, [R, W])
+    gctx.task_submit(ci, [hl, h1])
+    gctx.task_wait()
+    pl = gctx.data_partition(hl, b // 64, b * 64)
+    pu = gctx.data_partition(h2, b // 64, b * 64)
+    cc = gctx.task_decl("trtri_col", b3t.TRTRI_COL, [R, R, W], 20)
+    for cb in range(b // 64):
+        gctx.task_submit(cc, [pl[cb], pu[cb - 1 if cb else 0], pu[cb]], struct_panel(b, 64, cb))
+    gctx.task_wait()
+    for h in (hl, h1, h2):
+        gctx.data_unregister(h)
+    assert np.array_equal(U1.cpu().numpy(), U2.cpu().numpy())
+
+
+def struct_panel(b, pw, kk, jj=0, col0=0):
+    import struct
+    return struct.pack("<5i", b, pw, kk, jj, col0)
