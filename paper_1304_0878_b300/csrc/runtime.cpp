@@ -2006,12 +2006,14 @@ int b3t_ir_release(b3t_ctx *c, double *R, int32_t T, int32_t b, int32_t nrhs) {
 // (with the inverted diagonal tiles); x (+)= d; r = b - A x; eta.
 // With slices (H.hasp >= 0, A sliced beforehand) the residual r = b - A x is
 // RESID_SL: every step slices x (SLICE_X) and forms r on the tensor cores.
-static int ir_step(b3t_ctx *c, IrHandles &H, int32_t T, int32_t b, int32_t nrhs, int32_t flags, bool first) {
-    b3t_codelet cres, cax, cnrm;
+static int ir_step_resid(b3t_ctx *c, IrHandles &H, int32_t T, int32_t b, int32_t nrhs, bool first);
+
+// part 0: the whole step; 1: only its first half (the solves and AXPY).
+static int ir_step(b3t_ctx *c, IrHandles &H, int32_t T, int32_t b, int32_t nrhs, int32_t flags, bool first,
+                   int part = 0) {
+    b3t_codelet cres, cax;
     int rc;
-    if ((rc = kind_codelet(c, kResid, &cres)) || (rc = kind_codelet(c, kAxpy, &cax)) ||
-        (rc = kind_codelet(c, kNrm, &cnrm)))
-        return rc;
+    if ((rc = kind_codelet(c, kResid, &cres)) || (rc = kind_codelet(c, kAxpy, &cax))) return rc;
     const bool sliced = H.hasp >= 0;
     auto resid = [&](int32_t fl) -> int {
         for (int32_t i = 0; i < T; ++i) {
@@ -2031,10 +2033,23 @@ static int ir_step(b3t_ctx *c, IrHandles &H, int32_t T, int32_t b, int32_t nrhs,
         const b3t_handle h2[2] = {H.hx[i], H.hr[i]};
         if ((rc = submit_impl(c, cax, h2, nullptr, 2, &v, sizeof(v)))) return rc;
     }
-    if (sliced) {
+    if (part == 1) return 0;
+    if (sliced && part == 0) {
         // the solves in a launch of their own (the vector variant, more CTAs
         // per SM), then the slicing and the tensor-core residual
         if (!c->capturing && (rc = flush_impl(c))) return rc;
+    }
+    return ir_step_resid(c, H, T, b, nrhs, first);
+}
+
+// The second half of a refinement step: r = b - A x (RESID, or SLICE_X and
+// RESID_SL with slices) and eta (NRM).
+static int ir_step_resid(b3t_ctx *c, IrHandles &H, int32_t T, int32_t b, int32_t nrhs, bool first) {
+    b3t_codelet cres, cnrm;
+    int rc;
+    if ((rc = kind_codelet(c, kResid, &cres)) || (rc = kind_codelet(c, kNrm, &cnrm))) return rc;
+    const bool sliced = H.hasp >= 0;
+    if (sliced) {
         b3t_codelet csx, crs;
         if ((rc = kind_codelet(c, kSliceX, &csx)) || (rc = kind_codelet(c, kResidSl, &crs))) return rc;
         for (int32_t j = 0; j < T; ++j) {
@@ -2047,9 +2062,13 @@ static int ir_step(b3t_ctx *c, IrHandles &H, int32_t T, int32_t b, int32_t nrhs,
             const b3t_handle h4[4] = {H.hasp, H.hxsp, H.hbp, H.hr[i]};
             if ((rc = submit_impl(c, crs, h4, nullptr, 4, &a, sizeof(a)))) return rc;
         }
-    } else if ((rc = resid(first ? 0 : kVecKeepNorm))) {
+    } else {
         // the |A| row sums are formed by the first step's residual and kept
-        return rc;
+        for (int32_t i = 0; i < T; ++i) {
+            VecArgs v{nrhs, first ? 0 : kVecKeepNorm, i, T, b};
+            const b3t_handle h4[4] = {H.ha, H.hxp, H.hbp, H.hr[i]};
+            if ((rc = submit_impl(c, cres, h4, nullptr, 4, &v, sizeof(v)))) return rc;
+        }
     }
     VecArgs v{nrhs, 0, 0, T, b};
     const b3t_handle h3[3] = {H.hrp, H.hbp, H.he};
@@ -2101,13 +2120,45 @@ int b3t_ir_solve_sliced(b3t_ctx *c, const double *A, double *const *L, const dou
     return rc ? rc : rw;
 }
 
+// Steps after the first are the same task graph every time: they are
+// captured once (two graphs with slices, whose halves run in launches of
+// their own, else one) and replayed, so the host derives and uploads their
+// dependencies once per solve instead of once per step.
+struct IrGraphs {
+    b3t_ctx *c;
+    b3t_graph g[2] = {-1, -1};
+    ~IrGraphs() {
+        for (b3t_graph x : g)
+            if (x >= 0) b3t_graph_destroy(c, x);
+    }
+};
+
 static int ir_loop(b3t_ctx *c, IrHandles &H, double *eta, int32_t T, int32_t b, int32_t nrhs, int32_t flags,
                    double tol, int32_t max_iter, int32_t *iters, double *eta_out) {
     int rc;
     std::vector<double> host(nrhs + 1, 0.0);
     double prev = 0.0;
+    IrGraphs G{c};
+    const bool sliced = H.hasp >= 0;
     for (int32_t it = 1; it <= max_iter; ++it) {
-        if ((rc = ir_step(c, H, T, b, nrhs, flags, it == 1))) return rc;
+        if (it == 1) {
+            if ((rc = ir_step(c, H, T, b, nrhs, flags, true))) return rc;
+        } else {
+            if (G.g[0] < 0) {
+                if ((rc = b3t_graph_capture_begin(c))) return rc;
+                rc = ir_step(c, H, T, b, nrhs, flags, false, sliced ? 1 : 0);
+                const int re = b3t_graph_capture_end(c, &G.g[0]);
+                if (rc || re) return rc ? rc : re;
+                if (sliced) {
+                    if ((rc = b3t_graph_capture_begin(c))) return rc;
+                    rc = ir_step_resid(c, H, T, b, nrhs, false);
+                    const int re2 = b3t_graph_capture_end(c, &G.g[1]);
+                    if (rc || re2) return rc ? rc : re2;
+                }
+            }
+            for (b3t_graph x : G.g)
+                if (x >= 0 && (rc = b3t_graph_replay(c, x))) return rc;
+        }
         if ((rc = wait_impl(c, 0))) return rc;
         if ((rc = cuda_err(cudaMemcpyAsync(host.data(), eta, (nrhs + 1) * sizeof(double),
                                            cudaMemcpyDeviceToHost, c->stream))) ||
