@@ -36,6 +36,7 @@ constexpr int kTrtriRows = B3T_TRTRI_ROWS;   // TRTRI item: rows of U_k (8, 16 o
 constexpr int kTrmmRows = B3T_TRMM_ROWS;     // TRMM_MX item: rows x 64 columns of L_ik (32 or 64)
 static_assert(kTrmmRows == 32 || kTrmmRows == 64, "TRMM_MX rows per item");
 constexpr int kMxBlk = 128;              // MX GEMM / SYRK item: 128 x 128 of C
+constexpr int kMxWideBlk = 256;          // GEMM_MX item when b is a multiple of 256: 256 x 256
 constexpr int kCvtCols = 16;             // CVT item: 16 columns of the tile
 constexpr int kGemvRows = 16;            // GEMV item: 16 rows of the updated part
 constexpr int kResidRows = 16;           // RESID item: 16 rows of the residual part
@@ -62,7 +63,7 @@ struct PanelArgs {
 };
 constexpr int kPanelWidth = 128;          // panel width used by the Cholesky helpers
 constexpr int kPanelTrsmRows = 16;        // PANEL_TRSM item: rows below the diagonal block
-constexpr int kPanelUpdRows = 32;         // PANEL_UPD item: rows x 64 columns
+constexpr int kPanelUpdRows = 16;         // PANEL_UPD item: rows x 64 columns
 
 // Elements of one part of the residual work area: b*nrhs values, then per
 // RESID item the maxima |r_j| and |x_j| and the largest row sum of |A|.

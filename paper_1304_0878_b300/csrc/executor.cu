@@ -677,7 +677,10 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
             case kGemmMx:
                 if constexpr (kMx) {
                     if (!p.has_mx) { st = -EPROTO; break; }
-                    if (mx_update_item(rec, it, rec.kind == kSyrkMx, mx, p.timeout_ns, &s_fail)) st = -ETIMEDOUT;
+                    const bool wide = rec.kind == kGemmMx && rec.n % kMxWide == 0;
+                    if (wide ? mx_gemm_wide_item(rec, it, mx, p.timeout_ns, &s_fail)
+                             : mx_update_item(rec, it, rec.kind == kSyrkMx, mx, p.timeout_ns, &s_fail))
+                        st = -ETIMEDOUT;
                 }
                 break;
             case kTrtri: if constexpr (kSolve) trtri_item(rec, it, (double *)smem); break;

@@ -452,4 +452,160 @@ __device__ __forceinline__ int mx_update_item(const TaskRec &t, int item, bool s
     return 0;
 }
 
+// GEMM_MX on 256 x 256 blocks (b a multiple of 256; 4 items per 512-wide
+// tile): the same update as mx_update_item, with two accumulators of
+// M = 128, N = 256 (tensor-memory columns 0..255 for rows 0..127 of the
+// block, 256..511 for rows 128..255) that share every B chunk, so an item
+// moves 1 MiB (operands 512 KiB, W 256 KiB in and out) for four 128 x 128
+// blocks instead of 1.5 MiB, and pays the per-item claim once for four.
+// A K-chunk takes two ring slots (the two A chunks, then the two B chunks,
+// 32 KiB each); thread 0 issues a chunk's MMAs before topping up the ring,
+// so the slots it refills belong to chunks whose MMAs were issued one chunk
+// earlier.  Thread (q, h) owns row 128 h + 32 q + lane of the block (TMEM
+// lane 32 q + lane of accumulator h) and its 256 columns, loaded two 32-column
+// batches ahead of the tensor-memory stores.  Per element the arithmetic is
+// that of mx_update_item.  Returns 0, or ETIMEDOUT when a pipeline wait ran
+// out (block-wide).
+constexpr int kMxWide = kMxWideBlk;
+
+__device__ __forceinline__ void mx_wide_fill(MxState &st, uint32_t g, int s, const unsigned char *QA,
+                                             const unsigned char *QB, int bi, int bj, int nk) {
+    const uint32_t slot = g % kMxStages;
+    unsigned char *sa = st.stage + slot * 2 * kChunkBytes;
+    const int kk = s >> 1;
+    const unsigned char *Q = (s & 1) ? QB : QA;
+    const int rb = 2 * ((s & 1) ? bj : bi);
+    mbar_expect_tx(&st.full[slot], 2 * kChunkBytes);
+    bulk_g2s(sa, Q + ((size_t)rb * nk + kk) * kChunkBytes, kChunkBytes, &st.full[slot]);
+    bulk_g2s(sa + kChunkBytes, Q + ((size_t)(rb + 1) * nk + kk) * kChunkBytes, kChunkBytes, &st.full[slot]);
+}
+
+__device__ __noinline__ int mx_gemm_wide_item(const TaskRec &t, int item, MxState &st, int64_t limit_ns,
+                                              int *s_fail) {
+    const int b = (int)t.n, fmt = t.aux, es = q_esize(fmt);
+    const unsigned char *QA = (const unsigned char *)t.buf[0];
+    const unsigned char *QB = (const unsigned char *)t.buf[1];
+    float *W = (float *)t.buf[2];
+    const int m = b / kMxWide;
+    const int bi = item / m, bj = item % m;
+    const int nk = b * es / 128;
+    const int nfill = 2 * nk;
+    constexpr uint32_t idesc = (mx_idesc(1u) & ~(0x3Fu << 17)) | ((uint32_t)(kMxWide >> 3) << 17);
+    constexpr uint32_t idesc8 = (mx_idesc(0u) & ~(0x3Fu << 17)) | ((uint32_t)(kMxWide >> 3) << 17);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, h = warp >> 2;
+    int es_sum = 0;
+    if (fmt == 1) {
+        es_sum = *(const int *)(QA + (size_t)b * b * es) + *(const int *)(QB + (size_t)b * b * es);
+    }
+    const uint32_t G = st.fills;
+    int issued = 0;
+    if (tid == 0) {
+        *s_fail = 0;
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        while (issued < nfill && issued < kMxStages) {
+            const uint32_t g = G + issued;
+            if (g >= (uint32_t)kMxStages &&
+                !mbar_wait(&st.empty[g % kMxStages], ((g / kMxStages) - 1) & 1, limit_ns)) {
+                *s_fail = 1;
+                break;
+            }
+            mx_wide_fill(st, g, issued, QA, QB, bi, bj, nk);
+            ++issued;
+        }
+    }
+    // D = -W / s: row 128 h + 32 q + lane of the block, its 256 columns
+    const int rr = 128 * h + 32 * q + lane;
+    float *Wg = W + (size_t)(bi * kMxWide + rr) + (size_t)(bj * kMxWide) * b;
+    const uint32_t tl = st.tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(kMxWide * h);
+    {
+        float va[32], vb[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) va[c] = Wg[(size_t)c * b];
+#pragma unroll 1
+        for (int i = 0; i < kMxWide / 32; i += 2) {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) vb[c] = Wg[(size_t)(32 * (i + 1) + c) * b];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) va[c] = -ldexpf(va[c], -es_sum);
+            tmem_st32(tl + 32 * i, va);
+            if (i + 2 < kMxWide / 32) {
+#pragma unroll
+                for (int c = 0; c < 32; ++c) va[c] = Wg[(size_t)(32 * (i + 2) + c) * b];
+            }
+#pragma unroll
+            for (int c = 0; c < 32; ++c) vb[c] = -ldexpf(vb[c], -es_sum);
+            tmem_st32(tl + 32 * (i + 1), vb);
+        }
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+        tc_fence_after();
+        bool fail = *s_fail != 0;
+        for (int kk = 0; kk < nk && !fail; ++kk) {
+            const uint32_t ga = G + 2 * kk, gb = ga + 1;
+            if (!mbar_wait(&st.full[ga % kMxStages], (ga / kMxStages) & 1, limit_ns) ||
+                !mbar_wait(&st.full[gb % kMxStages], (gb / kMxStages) & 1, limit_ns)) {
+                fail = true;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(st.stage + (ga % kMxStages) * 2 * kChunkBytes);
+            const uint32_t sb = smem_u32(st.stage + (gb % kMxStages) * 2 * kChunkBytes);
+            const uint64_t a0 = sw128_desc(sa), a1 = sw128_desc(sa + kChunkBytes), bd = sw128_desc(sb);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (fmt == 0) {
+                    mma_bf16(st.tmem, a0 + 2 * i, bd + 2 * i, idesc, 1u);
+                    mma_bf16(st.tmem + kMxWide, a1 + 2 * i, bd + 2 * i, idesc, 1u);
+                } else {
+                    mma_e4m3(st.tmem, a0 + 2 * i, bd + 2 * i, idesc8, 1u);
+                    mma_e4m3(st.tmem + kMxWide, a1 + 2 * i, bd + 2 * i, idesc8, 1u);
+                }
+            }
+            mma_commit(&st.empty[ga % kMxStages]);
+            mma_commit(&st.empty[gb % kMxStages]);
+            // fills up to 2 kk + 4: their slots held chunk kk - 1, whose MMAs
+            // were issued one chunk ago (and the next chunk's two fills are
+            // among them)
+            while (issued < nfill && issued < 2 * kk + kMxStages) {
+                const uint32_t g = G + issued;
+                if (g >= (uint32_t)kMxStages &&
+                    !mbar_wait(&st.empty[g % kMxStages], ((g / kMxStages) - 1) & 1, limit_ns)) {
+                    fail = true;
+                    break;
+                }
+                mx_wide_fill(st, g, issued, QA, QB, bi, bj, nk);
+                ++issued;
+            }
+        }
+        if (fail) {
+            *s_fail = 1;
+            for (int k2 = 0; k2 < issued; ++k2) {
+                const uint32_t g = G + k2;
+                mbar_wait(&st.full[g % kMxStages], (g / kMxStages) & 1, limit_ns);
+            }
+        }
+        st.fills = G + issued;
+        mma_commit(st.done);
+    }
+    __syncthreads();
+    const bool ok = mbar_wait(st.done, st.items & 1, limit_ns);
+    st.items++;
+    tc_fence_after();
+    if (__syncthreads_or(*s_fail || !ok)) return ETIMEDOUT;
+#pragma unroll 1
+    for (int i = 0; i < kMxWide / 32; ++i) {
+        float v[32];
+        tmem_ld32(tl + 32 * i, v);
+#pragma unroll
+        for (int c = 0; c < 32; ++c) Wg[(size_t)(32 * i + c) * b] = -ldexpf(v[c], es_sum);
+    }
+    tc_fence_before();
+    __syncthreads();
+    return 0;
+}
+
 }  // namespace b3t

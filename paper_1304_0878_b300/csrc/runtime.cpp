@@ -157,7 +157,7 @@ int64_t items_of(int kind, int64_t n) {
     case kGemm: { int64_t m = n / kGemmBlk; return m * m; }
     case kTrmmMx: return (n / kTrmmRows) * (n / kGemmBlk);
     case kSyrkMx: { int64_t m = n / kMxBlk; return m * (m + 1) / 2; }
-    case kGemmMx: { int64_t m = n / kMxBlk; return m * m; }
+    case kGemmMx: { int64_t m = n % kMxWideBlk == 0 ? n / kMxWideBlk : n / kMxBlk; return m * m; }
     case kGemvL: case kGemvLT: return n / kGemvRows;
     case kResid: return n / kResidRows;
     case kAxpy: case kNrm: return 1;

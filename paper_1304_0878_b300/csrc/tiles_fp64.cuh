@@ -491,6 +491,136 @@ __device__ __forceinline__ int potrf_block(double *A, int n, int ld, double *sme
     return 0;
 }
 
+// Named barriers (ids 1..15; 0 is __syncthreads): sync waits for `count`
+// threads, arrive counts the caller without waiting.  The fence before the
+// arrival publishes the caller's shared-memory stores to the waiting threads.
+// Ids are immediates, so that the kernel reserves only the barriers it uses.
+template <int kId, int kCount>
+__device__ __forceinline__ void nbar_sync() {
+    asm volatile("bar.sync %0, %1;" ::"n"(kId), "n"(kCount) : "memory");
+}
+template <int kId, int kCount>
+__device__ __forceinline__ void nbar_arrive() {
+    __threadfence_block();
+    asm volatile("bar.arrive %0, %1;" ::"n"(kId), "n"(kCount) : "memory");
+}
+// phase parity p selects barrier kId + p
+template <int kId, int kCount>
+__device__ __forceinline__ void nbar_sync2(int p) {
+    if (p) nbar_sync<kId + 1, kCount>();
+    else nbar_sync<kId, kCount>();
+}
+template <int kId, int kCount>
+__device__ __forceinline__ void nbar_arrive2(int p) {
+    if (p) nbar_arrive<kId + 1, kCount>();
+    else nbar_arrive<kId, kCount>();
+}
+
+// Cholesky of one 64 x 64 block (lower, leading dimension ld) in shared
+// memory, right-looking column by column: column j is scaled (a square root,
+// then one division per row) and its contribution
+// A(i, k) -= L(i, j) L(k, j) is applied to every later column, for
+// j = 0, 1, .. in order, so every element takes its terms in ascending j with
+// one rounding each.  On B300 an FP64 instruction issues once per 64 cycles
+// per SM sub-partition, so the column chain (square root, division, and the
+// update of the next column) runs alone on warps 0 and 1 (one row per
+// thread), while warps 2, 3, 6 and 7 (the other two sub-partitions) apply
+// column j to columns j + 2 .. 63 one column behind:
+//   chain, column j:  (1) s = sqrt(d_j), L(i, j) = A(i, j) / s;
+//                     (2) L_j ready -> update warps;
+//                     (3) once the update warps have applied column j - 1 to
+//                         column j + 1 (T_{j-1}): A(i, j + 1) -= L(i, j)
+//                         L(j + 1, j) for i > j + 1, and d_{j+1} =
+//                         A(j+1, j+1) - L(j+1, j)^2 the same way in every
+//                         chain thread (no barrier before its square root);
+//   update, column j: wait L_j; column j + 2; arrive T_j; columns j + 3 ..;
+//                     barrier among the update warps.
+// L_j and T_j alternate between two barrier ids each: neither side can run
+// two columns ahead of the other, so an id is never reused before its
+// previous phase completed.  Warps 4 and 5 wait at the final barrier.  A
+// pivot that is <= 0 or NaN is recorded (1-based column) and the loops run to
+// the end on NaNs, so every warp takes the same barriers.
+__device__ __noinline__ int potrf64_pipelined(double *A, int ld, double *S, int *s_info) {
+    constexpr int n = 64, SP = 65;               // S[c * SP + r] = A(r, c)
+    constexpr int kChain = 64, kUpd = 128, kBoth = kChain + kUpd;
+    // L(j, j) goes to Dg: every chain thread reads the updated A(j, j) while
+    // forming d_j, so that element is not written again inside the loop
+    double *Dg = S + n * SP;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int e = tid; e < n * n; e += kThreads) {
+        const int r = e & 63, c = e >> 6;
+        if (r >= c) S[c * SP + r] = A[(size_t)r + (size_t)c * ld];
+    }
+    if (tid == 0) *s_info = 0;
+    __syncthreads();
+    if (warp < 2) {
+        const int i = tid;
+        int info = 0;
+        double d = S[0];
+        for (int j = 0; j < n; ++j) {
+            if (!(d > 0.0) && info == 0) info = j + 1;
+            const double s = sqrt(d);
+            double l = 0.0;
+            if (i == j) {
+                Dg[j] = s;
+                l = s;
+            } else if (i > j) {
+                l = S[j * SP + i] / s;
+                S[j * SP + i] = l;
+            }
+            nbar_sync<5, kChain>();
+            if (j + 2 < n) nbar_arrive2<1, kBoth>(j & 1);
+            if (j + 1 < n) {
+                if (j >= 1) nbar_sync2<3, kBoth>((j - 1) & 1);
+                const double lj1 = S[j * SP + j + 1];
+                d = fma(-lj1, lj1, S[(j + 1) * SP + j + 1]);
+                if (i > j + 1) S[(j + 1) * SP + i] = fma(-l, lj1, S[(j + 1) * SP + i]);
+            }
+        }
+        if (tid == 0) *s_info = info;
+    } else if (warp != 4 && warp != 5) {
+        // columns of parity g on sub-partition 2 + g (warps 2, 6: even;
+        // 3, 7: odd); rows 0..31 on warps 2, 3 and 32..63 on warps 6, 7, so
+        // that the late columns (rows near 63 only) still use both
+        const int g = warp & 1, i = (warp >= 6 ? 32 : 0) + lane;
+        for (int j = 0; j + 2 < n; ++j) {
+            nbar_sync2<1, kBoth>(j & 1);
+            const double li = S[j * SP + i];
+            if (((j + 2) & 1) == g && i >= j + 2)
+                S[(j + 2) * SP + i] = fma(-li, S[j * SP + j + 2], S[(j + 2) * SP + i]);
+            nbar_arrive2<3, kBoth>(j & 1);
+            // four columns of this parity at a time, loads before the FMAs
+            // (independent elements: one memory latency per group); rows
+            // 0..31 hold no element of the columns from 32
+            const int kend = warp >= 6 ? n : 32;
+            for (int k = j + 3 + (((j + 3) & 1) != g); k < kend; k += 8) {
+                double a[4], lk[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int kq = k + 2 * q;
+                    const bool v = kq < kend && i >= kq;
+                    lk[q] = v ? S[j * SP + kq] : 0.0;
+                    a[q] = v ? S[kq * SP + i] : 0.0;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int kq = k + 2 * q;
+                    if (kq < kend && i >= kq) S[kq * SP + i] = fma(-li, lk[q], a[q]);
+                }
+            }
+            nbar_sync<6, kUpd>();
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < n * n; e += kThreads) {
+        const int r = e & 63, c = e >> 6;
+        if (r >= c) A[(size_t)r + (size_t)c * ld] = r == c ? Dg[c] : S[c * SP + r];
+    }
+    const int info = *s_info;
+    __syncthreads();
+    return info;
+}
+
 __device__ __forceinline__ int potrf_tile(double *A, int b, double *smem, int *s_info) {
     return potrf_block(A, b, b, smem, s_info);
 }
@@ -520,7 +650,8 @@ __device__ __noinline__ void trtri_col_item(const TaskRec &t, int item, double *
 __device__ __forceinline__ int potrf_d_item(const TaskRec &t, double *smem, int *s_info) {
     const int b = (int)t.n, kk = pn_kk(t), pw = pn_pw(t);
     double *P = (double *)t.buf[0];
-    const int info = potrf_block(P + (size_t)kk * pw, pw, b, smem, s_info);
+    const int info = pw == 64 ? potrf64_pipelined(P + (size_t)kk * pw, b, smem, s_info)
+                              : potrf_block(P + (size_t)kk * pw, pw, b, smem, s_info);
     return info ? kk * pw + info : 0;
 }
 

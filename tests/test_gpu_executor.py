@@ -136,6 +136,30 @@ def test_cholesky_other_tiles(orc, gctx, N, b):
     assert och.rel_residual(L, A) <= 1e-12
 
 
+@pytest.mark.parametrize("N,b", [(512, 128), (1024, 256)])
+def test_cholesky_64_wide_panels(orc, gctx, monkeypatch, N, b):
+    # diagonal tiles as 64-wide column panels: the 64 x 64 POTRF_D blocks
+    # take the pipelined right-looking factorisation (a chain of two warps,
+    # the trailing columns on four more)
+    monkeypatch.setenv("B3T_PANEL_WIDTH", "64")
+    A, L0 = synth.integer_spd(N, seed=N + b + 64)
+    assert np.array_equal(factor_device(gctx, A, b), L0)
+    A = synth.spd_host(N, seed=5, shift=0.1)
+    L = factor_device(gctx, A, b)
+    Lo = factor_oracle(A, b)
+    assert np.max(np.abs(L - Lo)) / np.max(np.abs(Lo)) <= FP64_TOL
+    assert och.rel_residual(L, A) <= 1e-12
+    outs = [factor_device(gctx, A, b) for _ in range(2)]
+    assert np.array_equal(outs[0], L) and np.array_equal(outs[1], L)
+    # a pivot that fails inside a 64-wide panel is reported at its column
+    A[300, 300] = -10.0
+    with pytest.raises(b3t.B3TError) as e:
+        factor_device(gctx, A, b, col0=0)
+    assert e.value.code == b3t._lib.EDOM
+    t = och.to_tiles(A, b)
+    assert och.run(t, N // b, b) == gctx.last_error()[1] == 301
+
+
 def test_cholesky_deterministic(orc, gctx):
     A = synth.spd_host(768, seed=8, shift=1.0)
     outs = [factor_device(gctx, A, 128) for _ in range(3)]
