@@ -91,6 +91,8 @@ def parse():
     p.add_argument("--prio", default="upward", choices=["upward", "depth"],
                    help="ready-queue order of the profiling cases (--case)")
     p.add_argument("--ctas-per-sm", type=int, default=0, help="grid of the profiling cases (0: occupancy)")
+    p.add_argument("--item-chains", action="store_true",
+                   help="profiling cases: run vector-scaling chains item by item (b3t_config.item_chains)")
     p.add_argument("--case", default=None, choices=["mx_gemm_bf16", "mx_gemm_e4m3", "scal", "resid", "resid_sl", "trmm_sl", "solve_f32", "trace_mixed",
                                                     "solve_f64", "empty_dags", "serve_sweep", "trace_headline", "batch"],
                    help="run one profiling case (a DAG of one task kind), or one secondary measurement alone "
@@ -469,6 +471,9 @@ def summarise(line):
     for k in ("vector_chains", "vector_chains_depth_first"):
         if k in sec:
             out[k] = {"ms": sec[k]["ms"], "hbm_frac": sec[k]["hbm_frac"]}
+    if "vector_chains_item_chains" in sec:
+        v = sec["vector_chains_item_chains"]
+        out["vector_chains_item_chains"] = {"ms": v["ms"], "floor_ms": v["floor_ms"], "hbm_frac": v["hbm_frac"]}
     ed = sec.get("empty_dags") or {}
     tps = {k: v["tasks_per_s"] for k, v in ed.items()}
     if "tasks_per_s" in sec:
@@ -975,8 +980,14 @@ def run_secondary(ctx, dev, stream):
     x = torch.from_numpy(synth.vector_f32(nb * n, seed=1)).to(dev)
     f = synth.chain_factors(nb, nk, seed=2)
     tbytes = 8.0 * nb * nk * n
-    for name, pol in (("vector_chains", b3t.PRIO_UPWARD), ("vector_chains_depth_first", b3t.PRIO_DEPTH)):
-        c2 = b3t.Context(stream=stream.cuda_stream, timeout_ns=60_000_000_000, prio_policy=pol)
+    # item chains: a block's 8 tasks run item by item on one CTA (one load,
+    # 8 multiplies, one store per chunk): the floor is 2 GiB of HBM traffic
+    floor_bytes = 8.0 * nb * n
+    for name, pol, chained in (("vector_chains", b3t.PRIO_UPWARD, False),
+                               ("vector_chains_depth_first", b3t.PRIO_DEPTH, False),
+                               ("vector_chains_item_chains", b3t.PRIO_UPWARD, True)):
+        c2 = b3t.Context(stream=stream.cuda_stream, timeout_ns=60_000_000_000, prio_policy=pol,
+                         item_chains=chained)
         hs = [c2.data_register(x[i * n:(i + 1) * n].data_ptr(), n, 4) for i in range(nb)]
         cl = c2.task_decl("scale_vector", b3t.SCAL_F32, [b3t.RW], 4)
         c2.graph_capture_begin()
@@ -995,6 +1006,12 @@ def run_secondary(ctx, dev, stream):
                      "ms": 1e3 * med, "task_level_GBps": tbytes / med / 1e9, "task_bytes": tbytes,
                      "hbm_frac": tbytes / med / 1e9 / hbm_peak()[0], "hbm_peak_GBps": hbm_peak()[0],
                      "hbm_peak_source": hbm_peak()[1]}
+        if chained:
+            # each element read and written once: the HBM floor of the DAG
+            out[name].update({"execution": "item chains (each block's 8 tasks item by item on one CTA)",
+                              "floor_bytes": floor_bytes,
+                              "floor_ms": 1e3 * floor_bytes / (hbm_peak()[0] * 1e9),
+                              "hbm_frac": floor_bytes / med / 1e9 / hbm_peak()[0]})
         c2.graph_destroy(g)
         c2.close()
     del x
@@ -1061,7 +1078,8 @@ def run_case(args):
     dev = torch.device("cuda", 0)
     ctx = b3t.Context(stream=torch.cuda.current_stream().cuda_stream, timeout_ns=60_000_000_000,
                       ctas_per_sm=args.ctas_per_sm,
-                      prio_policy=b3t.PRIO_DEPTH if args.prio == "depth" else b3t.PRIO_UPWARD)
+                      prio_policy=b3t.PRIO_DEPTH if args.prio == "depth" else b3t.PRIO_UPWARD,
+                      item_chains=args.item_chains)
     b = 512
     if args.case.startswith("mx_gemm"):
         # 64 independent GEMM_MX updates W_i -= Q_a Q_b^T (b = 512): 64 x 2 b^3 flop

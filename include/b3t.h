@@ -292,6 +292,24 @@ typedef struct b3t_config {
                                SM instead of one, for FP64-only streams); a
                                batch holding a mixed-precision kind is then
                                refused (-EINVAL) */
+    int32_t item_chains;     /* 1: successor-first at item granularity for
+                               vector-scaling chains (Section 2's scheduler
+                               with a partial view of the graph).  A
+                               B3T_SCAL_F32 task whose only successor is a
+                               B3T_SCAL_F32 task on the same buffer, with no
+                               other predecessor, passes item i of that
+                               successor to the CTA running its own item i:
+                               the item reads exactly what item i of the
+                               task wrote, so the CTA applies both factors,
+                               in submission order and each rounded, to the
+                               chunk it holds, and stores it once.  Up to 32
+                               tasks form one chain.  Results are bit for bit
+                               those of task-by-task execution; every task
+                               still retires, and edges leaving a chain are
+                               released when its last task retires.  Applies
+                               to launches without mixed-precision kinds
+                               (not to stream mode).  0 (default): task by
+                               task. */
 } b3t_config;
 
 enum { B3T_PRIO_UPWARD = 0, B3T_PRIO_DEPTH = 1 };
@@ -416,6 +434,13 @@ B3T_API int b3t_dag_edges(b3t_ctx *ctx, int32_t *pred, int32_t *succ, int64_t ca
  * Writes at most cap entries of each (either pointer may be NULL); *count =
  * number of pending tasks. */
 B3T_API int b3t_dag_levels(b3t_ctx *ctx, float *rank, int32_t *level, int64_t cap, int64_t *count);
+
+/* Item chains of the pending batch, as the next flush will form them (see
+ * b3t_config.item_chains): aux[t] = k > 0 if task t heads a chain of k
+ * absorbed B3T_SCAL_F32 tasks, -1 if t is absorbed, 0 otherwise (always 0
+ * with item_chains off or when the batch holds a mixed-precision kind).
+ * Writes at most cap entries; *count = number of pending tasks. */
+B3T_API int b3t_dag_item_chains(b3t_ctx *ctx, int32_t *aux, int64_t cap, int64_t *count);
 
 /* Launch statistics of the last launch (flush or replay): tasks, work
  * items, persistent CTAs, and the device time of the persistent kernel (or

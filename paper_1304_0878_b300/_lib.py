@@ -38,7 +38,8 @@ class Config(ctypes.Structure):
     _fields_ = [("timeout_ns", ctypes.c_int64), ("ctas_per_sm", ctypes.c_int32),
                 ("prio_levels", ctypes.c_int32), ("debug_checks", ctypes.c_int32),
                 ("host_only", ctypes.c_int32), ("prio_policy", ctypes.c_int32),
-                ("stream_free_sms", ctypes.c_int32), ("stream_no_mx", ctypes.c_int32)]
+                ("stream_free_sms", ctypes.c_int32), ("stream_no_mx", ctypes.c_int32),
+                ("item_chains", ctypes.c_int32)]
 
 
 _lib = None
@@ -69,6 +70,7 @@ _SIGS = {
     "b3t_dag_stats": (ctypes.c_int, [_vp, _pi64, _pi64]),
     "b3t_dag_edges": (ctypes.c_int, [_vp, _pi32, _pi32, _i64, _pi64]),
     "b3t_dag_levels": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float), _pi32, _i64, _pi64]),
+    "b3t_dag_item_chains": (ctypes.c_int, [_vp, _pi32, _i64, _pi64]),
     "b3t_last_launch": (ctypes.c_int, [_vp, _pi64, _pi64, _pi32, _pi64]),
     "b3t_debug_block_task": (ctypes.c_int, [_vp, _i64]),
     "b3t_cholesky_submit": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), _i32, _i32, _i32]),
@@ -196,9 +198,9 @@ class Context:
     as ``torch.cuda.current_stream().cuda_stream``)."""
 
     def __init__(self, stream=0, timeout_ns=0, ctas_per_sm=0, prio_levels=0, debug=False,
-                 host_only=False, prio_policy=0, stream_free_sms=0, stream_no_mx=False):
+                 host_only=False, prio_policy=0, stream_free_sms=0, stream_no_mx=False, item_chains=False):
         cfg = Config(timeout_ns, ctas_per_sm, prio_levels, 1 if debug else 0, 1 if host_only else 0,
-                     prio_policy, stream_free_sms, 1 if stream_no_mx else 0)
+                     prio_policy, stream_free_sms, 1 if stream_no_mx else 0, 1 if item_chains else 0)
         h = _vp()
         _check(lib().b3t_init(ctypes.byref(h), ctypes.byref(cfg), _vp(stream or 0)), "b3t_init")
         self._h = h
@@ -307,6 +309,14 @@ class Context:
         rk, lv, cnt = (ctypes.c_float * max(nt, 1))(), (_i32 * max(nt, 1))(), _i64()
         _check(lib().b3t_dag_levels(self._h, rk, lv, nt, ctypes.byref(cnt)), "b3t_dag_levels")
         return [rk[i] for i in range(cnt.value)], [lv[i] for i in range(cnt.value)]
+
+    def dag_item_chains(self):
+        """Per pending task: k > 0 heads an item chain of k absorbed SCAL
+        tasks, -1 absorbed, 0 neither (as the next flush will form them)."""
+        nt, _ = self.dag_stats()
+        aux, cnt = (_i32 * max(nt, 1))(), _i64()
+        _check(lib().b3t_dag_item_chains(self._h, aux, nt, ctypes.byref(cnt)), "b3t_dag_item_chains")
+        return [aux[i] for i in range(cnt.value)]
 
     def last_launch(self):
         nt, ni, nc, ns = _i64(), _i64(), _i32(), _i64()

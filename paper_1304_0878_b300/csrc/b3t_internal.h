@@ -24,8 +24,16 @@ constexpr int kThreads = 256;            // threads per persistent CTA
 // Work-item decomposition of each kind (the host computes nitems, the
 // device maps item -> sub-block with the same constants).
 constexpr int64_t kScalChunk = 1 << 16;  // f32 elements per SCAL item
+constexpr int kMaxChain = 32;            // SCAL tasks absorbed by one item-chain head
 constexpr int kGemmBlk = 64;             // f64 GEMM / SYRK item: 64 x 64 of C
 constexpr int kTrsmRows = 32;            // f64 TRSM item: 32 rows of A_ik
+// Tiles of at most kSmallTile rows (a factorisation of a few thousand rows,
+// bound by its critical path) split finer: TRSM items of kSmallTrsmRows
+// rows, SYRK / GEMM items of kSmallGemmRows x 64, so that one task's work
+// spreads over more SMs (one SM does ~8 GFLOP/s of FP64)
+constexpr int kSmallTile = 128;
+constexpr int kSmallTrsmRows = 8;
+constexpr int kSmallGemmRows = 16;
 #ifndef B3T_TRTRI_ROWS
 #define B3T_TRTRI_ROWS 8
 #endif
@@ -131,7 +139,9 @@ struct alignas(16) TaskRec {
     int32_t nitems;              // work items the task is split into
     int32_t succ_off;            // first successor in the CSR array
     int32_t nsucc;
-    int32_t aux;                 // POTRF: global column offset; MX: format
+    int32_t aux;                 // POTRF: global column offset; MX: format; SCAL: item
+                                 // chain (k > 0: head of k absorbed tasks, buf[1] = their
+                                 // ids then their factor bits; -1: absorbed; 0: neither)
     uint32_t scal;               // SCAL: float factor bits
 };
 static_assert(sizeof(TaskRec) == 64, "TaskRec is 64 bytes");

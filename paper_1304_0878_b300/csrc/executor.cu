@@ -166,8 +166,11 @@ __device__ __forceinline__ uint32_t scal_bulk_bytes(int64_t n, int it, int64_t *
     return (uint32_t)(((end - *start) & ~(int64_t)3) * 4);
 }
 
+// fch / nf: factor bits of the task's item-chain members (nf = 0 for a
+// task alone), applied after the task's own factor, each rounded.
 __device__ __forceinline__ int scal_item_bulk(const TaskRec &t, int64_t task, int item, int next_item,
-                                              ScalRing &ring, int64_t limit_ns, int64_t drain_ns) {
+                                              ScalRing &ring, int64_t limit_ns, int64_t drain_ns,
+                                              const uint32_t *fch, int nf) {
     float *x = (float *)t.buf[0];
     const float f = __uint_as_float(t.scal);
     int64_t start, start2 = 0;
@@ -205,7 +208,15 @@ __device__ __forceinline__ int scal_item_bulk(const TaskRec &t, int64_t task, in
         const bool ok = mbar_wait(&ring.full[sl], (q / S) & 1, limit_ns);
         if (ok) {
             float4 *v = reinterpret_cast<float4 *>(ring.stage + sl * kSbBytes);
-            for (uint32_t i = tid; i < nb / 16; i += kThreads) v[i] = mul4(v[i], f);
+            if (nf == 0) {
+                for (uint32_t i = tid; i < nb / 16; i += kThreads) v[i] = mul4(v[i], f);
+            } else {
+                for (uint32_t i = tid; i < nb / 16; i += kThreads) {
+                    float4 a = mul4(v[i], f);
+                    for (int j = 0; j < nf; ++j) a = mul4(a, __uint_as_float(fch[j]));
+                    v[i] = a;
+                }
+            }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         }
         if (__syncthreads_or(!ok)) {
@@ -234,7 +245,9 @@ __device__ __forceinline__ int scal_item_bulk(const TaskRec &t, int64_t task, in
     const int64_t tail = (end - start) - (int64_t)(bytes / 4);
     if (!failed && tid < tail) {
         float *p = x + start + bytes / 4 + tid;
-        *p = __fmul_rn(*p, f);
+        float y = __fmul_rn(*p, f);
+        for (int j = 0; j < nf; ++j) y = __fmul_rn(y, __uint_as_float(fch[j]));
+        *p = y;
     }
     if (tid == 0) {
         // this item's stores are complete before its done count is published
@@ -455,13 +468,15 @@ __device__ __forceinline__ unsigned long long claim(const LaunchParams &p, uint6
 }
 
 // Warp 0 retires task t: successors' counters (one lane per successor),
-// one ready-ring slot per successor that became ready, retired count.
-__device__ __forceinline__ void retire(const LaunchParams &p, int64_t t, const TaskRec &rec) {
+// one ready-ring slot per successor that became ready, retired count.  A task
+// whose one successor it absorbed into an item chain releases none (nsucc
+// given as 0).
+__device__ __forceinline__ void retire(const LaunchParams &p, int64_t t, const TaskRec &rec, int nsucc) {
     const int lane = threadIdx.x & 31;
     __threadfence();
-    for (int base = 0; base < rec.nsucc; base += 32) {
+    for (int base = 0; base < nsucc; base += 32) {
         const int k = base + lane;
-        if (k < rec.nsucc) {
+        if (k < nsucc) {
             const int s = p.succ[rec.succ_off + k];
             const int prev = atomicSub(&p.counters[s], 1);
             if (prev == 1) {
@@ -558,6 +573,11 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
     // SCAL bulk-copy ring (the variants without the tensor-memory path)
     __shared__ __align__(8) uint64_t s_sbar[kSbMaxStages];
     __shared__ int s_resv;      // next item of the same task reserved by a SCAL item, or -1
+    // item chain of the SCAL task last run here: its id, members and factors
+    __shared__ int64_t s_cht;
+    __shared__ int32_t s_chid[kMaxChain];
+    __shared__ uint32_t s_chf[kMaxChain];
+    if (tid == 0) s_cht = -1;
     ScalRing ring;
     ring.full = s_sbar;
     ring.stage = smem;
@@ -621,7 +641,7 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
         const TaskRec rec = s_rec;
         int st = 0;
         constexpr bool kScal = (kVar & kFamScal) != 0, kF64 = (kVar & kFamF64) != 0,
-                       kSolve = (kVar & kFamSolve) != 0;
+                       kSolve = (kVar & kFamSolve) != 0, kScalRing = kScal && !kMx;
         const uint32_t fam = family_of(rec.kind);
         if (fam && !(fam & kVar)) {
             st = -EPROTO;   // the runtime picks a variant that covers every kind of the launch
@@ -632,12 +652,21 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
                     // reserve the task's next item so that its loads start
                     // while this one drains (the executor runs it next)
                     if (tid == 0) s_resv = rec.nitems > 1 ? atomicAdd(&p.next_item[t], 1) : -1;
+                    // head of an item chain: its members' ids and factors,
+                    // read once per run of the task's items on this CTA
+                    const int nf = rec.aux > 0 ? min(rec.aux, kMaxChain) : 0;
+                    if (nf && s_cht != t && tid < nf) {
+                        const int32_t *ch = (const int32_t *)rec.buf[1];
+                        s_chid[tid] = __ldcg(ch + tid);
+                        s_chf[tid] = (uint32_t)__ldcg(ch + rec.aux + tid);
+                    }
                     __syncthreads();
+                    if (tid == 0) s_cht = nf ? t : -1;
                     const int nxt = s_resv < rec.nitems ? s_resv : -1;
                     // each wait of the ring gives up after 50 ms (a 16 KiB copy
                     // takes microseconds) and the launch reports ETIMEDOUT
                     const int fc = scal_item_bulk(rec, t, it, nxt, ring, min(p.timeout_ns, (int64_t)50000000),
-                                                  p.timeout_ns);
+                                                  p.timeout_ns, s_chf, nf);
                     if (fc) {
                         if (tid == 0) set_error(p.ctl, ETIMEDOUT, (int)t, fc, 20);
                         st = -ETIMEDOUT;
@@ -782,7 +811,42 @@ __global__ void __maxnreg__(120) exec_kernel(const LaunchParams p) {
             }
             flag = __shfl_sync(0xffffffffu, flag, 0);
             nj = __shfl_sync(0xffffffffu, nj, 0);
-            if (flag) retire(p, t, rec);
+            const bool chain = kScalRing && rec.kind == kScalF32 && rec.aux > 0;
+            if (flag) retire(p, t, rec, chain ? 0 : rec.nsucc);
+            if (chain && st == 0) {
+                // the item was also item `it` of every chain member: count it
+                // done for each (lane j for member j); members that finished
+                // retire in chain order, the last one with its successors
+                const int lane = tid & 31, k = rec.aux;
+                uint32_t fin = 0;
+                __threadfence();   // the chunk's stores before each member's done count
+                for (int j0 = 0; j0 < k; j0 += 32) {
+                    const int j = j0 + lane;
+                    const bool last = j < k && atomicAdd(&p.done_items[s_chid[j]], 1) + 1 == rec.nitems;
+                    fin = __ballot_sync(0xffffffffu, last);
+                    for (uint32_t m = fin; m; m &= m - 1) {
+                        const int jj = j0 + __ffs(m) - 1;
+                        const int64_t mt = s_chid[jj];
+                        TaskRec mr = rec;
+                        if (jj == k - 1) {
+                            mr.succ_off = __ldcg(&p.tasks[mt].succ_off);
+                            mr.nsucc = __ldcg(&p.tasks[mt].nsucc);
+                        }
+                        retire(p, mt, mr, jj == k - 1 ? mr.nsucc : 0);
+                    }
+                }
+                if (p.trace && lane == 0) {
+                    const uint64_t t_end = gtimer();
+                    for (int j = 0; j < k; ++j) {
+                        const unsigned long long q = atomicAdd(p.trace_n, 1ull);
+                        if ((int64_t)q < p.trace_cap) {
+                            uint32_t sm;
+                            asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+                            p.trace[q] = TraceRec{s_chid[j], it, (int32_t)sm, rec.kind, t_item, t_end};
+                        }
+                    }
+                }
+            }
             fi = (nj >= 0 && nj < rec.nitems) ? (((unsigned long long)t << 32) | (uint32_t)nj) : kEmpty;
         }
         // a bulk-copy or tensor-core pipeline whose bounded wait gave up

@@ -151,10 +151,17 @@ int64_t items_of(int kind, int64_t n) {
     case kPotrf: case kPotrfMx: case kNoop: return 1;
     case kCvt: return n / kCvtCols;
     case kQuant: return 1;   // set from the format at submit (one item per 16 KiB chunk)
-    case kTrsm: case kTrsmMx: return n / kTrsmRows;
+    case kTrsm: return n <= kSmallTile ? n / kSmallTrsmRows : n / kTrsmRows;
+    case kTrsmMx: return n / kTrsmRows;
     case kTrtri: return n / kTrtriRows;
-    case kSyrk: { int64_t m = n / kGemmBlk; return m * (m + 1) / 2; }
-    case kGemm: { int64_t m = n / kGemmBlk; return m * m; }
+    case kSyrk: {
+        int64_t m = n / kGemmBlk;
+        return n <= kSmallTile ? (n / kSmallGemmRows) * m : m * (m + 1) / 2;
+    }
+    case kGemm: {
+        int64_t m = n / kGemmBlk;
+        return n <= kSmallTile ? (n / kSmallGemmRows) * m : m * m;
+    }
     case kTrmmMx: return (n / kTrmmRows) * (n / kGemmBlk);
     case kSyrkMx: { int64_t m = n / kMxBlk; return m * (m + 1) / 2; }
     case kGemmMx: { int64_t m = n % kMxWideBlk == 0 ? n / kMxWideBlk : n / kMxBlk; return m * m; }
@@ -330,6 +337,65 @@ int sub_rings(const b3t_ctx *c) {
     return n;
 }
 
+// Item chains (config item_chains; Section 2's scheduler that sees only part
+// of the graph, applied at item granularity): a SCAL task t whose only
+// successor s is a SCAL task on the same buffer and length, s having no
+// other predecessor, is linked to s; item i of s reads exactly what item i of
+// t wrote.  A maximal run of links becomes one chain of up to kMaxChain
+// absorbed members after its head: the CTA that runs item i of the head
+// applies every member's factor to the chunk, in order, before storing it.
+// Members are never queued (their one predecessor's retirement releases
+// nothing); each retires when its last item is done, and the last member
+// releases the chain's outgoing edges.  chain_aux[t]: k members (head), -1
+// (member), 0; chain_at[head]: offset in succ_lv of the members' ids, then
+// of their factor bits (appended to succ_lv).
+static void find_item_chains(const b3t_ctx *c, const std::vector<int32_t> &off, const int32_t *succ,
+                             const std::vector<int32_t> &indeg, std::vector<int32_t> &chain_aux,
+                             std::vector<int32_t> &chain_at, std::vector<int32_t> &succ_lv) {
+    const int64_t nt = (int64_t)c->tasks.size();
+    std::vector<int32_t> nxt(nt, -1);
+    std::vector<char> linked(nt, 0);
+    bool any = false;
+    for (int64_t t = 0; t < nt; ++t) {
+        const TaskRec &r = c->tasks[t].rec;
+        if (r.kind != kScalF32 || off[t + 1] - off[t] != 1) continue;
+        const int32_t sx = succ[off[t]];
+        const TaskRec &q = c->tasks[sx].rec;
+        if (q.kind != kScalF32 || indeg[sx] != 1 || q.buf[0] != r.buf[0] || q.n != r.n || q.nitems != r.nitems)
+            continue;
+        nxt[t] = sx;
+        linked[sx] = 1;
+        any = true;
+    }
+    if (!any) return;
+    chain_aux.assign(nt, 0);
+    chain_at.assign(nt, 0);
+    std::vector<int32_t> mem;
+    for (int64_t t = 0; t < nt; ++t) {
+        if (nxt[t] < 0 || linked[t]) continue;
+        // t heads a run of links; cut it into chains of at most kMaxChain members
+        int32_t h = (int32_t)t;
+        while (h >= 0 && nxt[h] >= 0) {
+            mem.clear();
+            int32_t m = nxt[h];
+            while (m >= 0 && (int)mem.size() < kMaxChain) {
+                mem.push_back(m);
+                m = nxt[m];
+            }
+            chain_aux[h] = (int32_t)mem.size();
+            chain_at[h] = (int32_t)succ_lv.size();
+            for (int32_t x : mem) {
+                chain_aux[x] = -1;
+                succ_lv.push_back(x);
+            }
+            for (int32_t x : mem) succ_lv.push_back((int32_t)c->tasks[x].rec.scal);
+            // a cut run continues with the next task as a new head, released
+            // by the last member like any successor
+            h = m;
+        }
+    }
+}
+
 // Build the task table, CSR graph, ready rings and root lists of the pending
 // batch into arena `a` (uploaded through the pinned staging buffer on the
 // context's stream) and fill the launch parameters.
@@ -343,12 +409,18 @@ int build_launch(b3t_ctx *c, Arena &a, InitParams &ip, LaunchParams &lp, int64_t
     for (int64_t t = 0; t < nt; ++t) off[t + 1] += off[t];
     const int64_t ne_pad = std::max<int64_t>(ne, 1);
     // device layout of the succ buffer: [successors (ne_pad)] [level (nt)]
+    // [item chains: per head, its members' ids then their factor bits]
     std::vector<int32_t> succ_lv(ne_pad + nt, 0);
     {
         std::vector<int32_t> pos(off.begin(), off.end() - 1);
         for (auto &e : c->edges) succ_lv[pos[e.first]++] = e.second;
     }
     for (int64_t t = 0; t < nt && t < (int64_t)c->extra_deps.size(); ++t) indeg[t] += c->extra_deps[t];
+    uint32_t fams0 = 0;
+    for (int64_t t = 0; t < nt; ++t) fams0 |= family_of(c->tasks[t].rec.kind);
+    std::vector<int32_t> chain_aux, chain_at;
+    if (c->cfg.item_chains && !(variant_of(fams0) & kFamMx))
+        find_item_chains(c, off, succ_lv.data(), indeg, chain_aux, chain_at, succ_lv);
     std::vector<float> rank;
     std::vector<int32_t> level;
     compute_levels(c, off, succ_lv.data(), rank, level);
@@ -418,6 +490,14 @@ int build_launch(b3t_ctx *c, Arena &a, InitParams &ip, LaunchParams &lp, int64_t
     }
     char *s = (char *)c->staging;
     for (int64_t t = 0; t < nt; ++t) std::memcpy(s + o_t + t * sizeof(TaskRec), &c->tasks[t].rec, sizeof(TaskRec));
+    // item chains: the head's aux counts its members, buf[1] points at their
+    // ids (then their factor bits) in the uploaded succ buffer; members get -1
+    for (int64_t t = 0; t < (int64_t)chain_aux.size(); ++t) {
+        if (!chain_aux[t]) continue;
+        TaskRec *r = reinterpret_cast<TaskRec *>(s + o_t + t * sizeof(TaskRec));
+        r->aux = chain_aux[t];
+        if (chain_aux[t] > 0) r->buf[1] = (uint64_t)(uintptr_t)(a.succ + chain_at[t]);
+    }
     std::memcpy(s + o_s, succ_lv.data(), succ_lv.size() * 4);
     std::memcpy(s + o_i, indeg.data(), nt * 4);
     std::memcpy(s + o_r, roots.data(), roots.size() * 8);
@@ -1146,6 +1226,27 @@ int b3t_dag_levels(b3t_ctx *c, float *rank, int32_t *level, int64_t cap, int64_t
     return 0;
 }
 
+int b3t_dag_item_chains(b3t_ctx *c, int32_t *aux, int64_t cap, int64_t *count) {
+    if (!c) return -EINVAL;
+    const int64_t nt = (int64_t)c->tasks.size();
+    if (count) *count = nt;
+    std::vector<int32_t> off(nt + 1, 0), indeg(nt, 0);
+    for (auto &e : c->edges) { off[e.first + 1]++; indeg[e.second]++; }
+    for (int64_t t = 0; t < nt; ++t) off[t + 1] += off[t];
+    for (int64_t t = 0; t < nt && t < (int64_t)c->extra_deps.size(); ++t) indeg[t] += c->extra_deps[t];
+    std::vector<int32_t> succ(std::max<size_t>(c->edges.size(), 1));
+    {
+        std::vector<int32_t> pos(off.begin(), off.end() - 1);
+        for (auto &e : c->edges) succ[pos[e.first]++] = e.second;
+    }
+    uint32_t fams = 0;
+    for (int64_t t = 0; t < nt; ++t) fams |= family_of(c->tasks[t].rec.kind);
+    std::vector<int32_t> ch_aux, ch_at, data = succ;
+    if (c->cfg.item_chains && !(variant_of(fams) & kFamMx)) find_item_chains(c, off, succ.data(), indeg, ch_aux, ch_at, data);
+    for (int64_t t = 0; t < nt && t < cap; ++t) aux[t] = ch_aux.empty() ? 0 : ch_aux[t];
+    return 0;
+}
+
 int b3t_last_launch(b3t_ctx *c, int64_t *ntasks, int64_t *nitems, int32_t *nctas, int64_t *kernel_ns) {
     if (!c) return -EINVAL;
     if (ntasks) *ntasks = c->last_ntasks;
@@ -1473,7 +1574,9 @@ int b3t_cholesky_submit(b3t_ctx *c, double *const *tiles, int32_t T, int32_t b, 
     if ((rc = kind_codelet(c, kPotrf, &cp)) || (rc = kind_codelet(c, kTrsm, &ct)) ||
         (rc = kind_codelet(c, kSyrk, &cs)) || (rc = kind_codelet(c, kGemm, &cg)))
         return rc;
-    const int32_t pw = panel_width(b);
+    // tiles below two 128-wide panels take 64-wide ones (a pipelined
+    // 64 x 64 POTRF, its panel solve and update instead of one CTA's whole tile)
+    const int32_t pw = b < 2 * kPanelWidth ? panel_width(b, 64) : panel_width(b);
     const bool panels = pw > 0;
     std::vector<std::vector<b3t_handle>> dparts(panels ? T : 0);
     for (int32_t k = 0; panels && k < T; ++k)

@@ -18,6 +18,22 @@ namespace b3t {
 
 constexpr int kKc = 32;            // K chunk staged in shared memory
 
+// a / d from r = 1 / d (one IEEE division per divisor, shared by every
+// quotient with that divisor): q = RN(a r), the exact remainder
+// e = a - q d by one FMA, then the correction RN(q + e r), which by
+// Markstein's theorem (P. Markstein, IBM J. Res. Dev. 34(1), 1990; Muller et
+// al., Handbook of Floating-Point Arithmetic, division with an FMA) is the
+// correctly rounded quotient, bit for bit what a / d gives, for finite d != 0
+// and no underflow.  A zero quotient keeps the sign of q (a / d would give
+// -0 for a = -0).  On sm_103 a dependent FP64 operation takes ~64 cycles and a
+// division ~640, so a substitution chain of k divisions by known pivots is
+// k x 3 operations long instead of k divisions.
+__device__ __forceinline__ double div_rcp(double a, double d, double r) {
+    const double q = __dmul_rn(a, r);
+    const double q1 = fma(fma(-q, d, a), r, q);
+    return (__double_as_longlong(q) << 1) == 0 ? q : q1;
+}
+
 // C(crow0.., ccol0..) (64 x 64 block) -= A(arow0.., 0..K) * B(brow0.., 0..K)^T,
 // all column-major with leading dimension ld.  lower_only: write only the
 // entries with row - lower_shift >= column.
@@ -91,6 +107,12 @@ __device__ __forceinline__ void gemm64_f64(const double *A, int arow0, const dou
 __device__ __forceinline__ void gemm_item(const TaskRec &t, int item, double *smem) {
     const int b = (int)t.n, m = b / kGemmBlk;
     const int bi = item / m, bj = item % m;
+    if (b <= kSmallTile) {   // kSmallGemmRows x 64 blocks (the same FMAs per element)
+        gemm_rows_f64<kSmallGemmRows>((const double *)t.buf[0], bi * kSmallGemmRows, (const double *)t.buf[1],
+                                      bj * 64, (double *)t.buf[2], bi * kSmallGemmRows, bj * 64, b, b, false, 0,
+                                      smem);
+        return;
+    }
     gemm64_f64((const double *)t.buf[0], bi * 64, (const double *)t.buf[1], bj * 64,
                (double *)t.buf[2], bi * 64, bj * 64, b, b, false, 0, smem);
 }
@@ -106,6 +128,15 @@ __device__ __forceinline__ void tri_index(int item, int &bi, int &bj) {
 
 __device__ __forceinline__ void syrk_item(const TaskRec &t, int item, double *smem) {
     const int b = (int)t.n;
+    if (b <= kSmallTile) {
+        // kSmallGemmRows x 64 blocks; those wholly above the diagonal are empty
+        const int m = b / kGemmBlk, bi = item / m, bj = item % m;
+        if (bi * kSmallGemmRows + kSmallGemmRows - 1 < bj * 64) return;
+        const double *A = (const double *)t.buf[0];
+        gemm_rows_f64<kSmallGemmRows>(A, bi * kSmallGemmRows, A, bj * 64, (double *)t.buf[1], bi * kSmallGemmRows,
+                                      bj * 64, b, b, true, 0, smem);
+        return;
+    }
     int bi, bj;
     tri_index(item, bi, bj);
     const double *A = (const double *)t.buf[0];
@@ -210,6 +241,9 @@ __device__ __forceinline__ void trsm_rows(const double *L, const Tin *Ain, doubl
             const int c = e & 63, q = e >> 6;           // element (c0+c, c0+q)
             if (c >= q) Lcb[c * 65 + q] = L[(size_t)(c0 + c) + (size_t)(c0 + q) * b];
         }
+        // 1 / L(c, c) in the padding slot of row c (every solve of the block
+        // divides by these 64 pivots)
+        if (tid < 64) Lcb[tid * 65 + 64] = 1.0 / L[(size_t)(c0 + tid) + (size_t)(c0 + tid) * b];
         __syncthreads();
         // small triangular solve, right-looking over the 64 columns in panels
         // of 8: warp 0 solves a panel (lane = row, the 8 columns in
@@ -224,7 +258,7 @@ __device__ __forceinline__ void trsm_rows(const double *L, const Tin *Ain, doubl
                 for (int j = 0; j < 8; ++j) x[j] = Acc[(p0 + j) * RS + tid];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    x[j] = x[j] / Lcb[(p0 + j) * 65 + p0 + j];
+                    x[j] = div_rcp(x[j], Lcb[(p0 + j) * 65 + p0 + j], Lcb[(p0 + j) * 65 + 64]);
 #pragma unroll
                     for (int jj = j + 1; jj < 8; ++jj) x[jj] = fma(-x[j], Lcb[(p0 + jj) * 65 + p0 + j], x[jj]);
                 }
@@ -251,7 +285,11 @@ __device__ __forceinline__ void trsm_rows(const double *L, const Tin *Ain, doubl
 
 __device__ __forceinline__ void trsm_item(const TaskRec &t, int item, double *smem) {
     double *A = (double *)t.buf[1];
-    trsm_rows<double>((const double *)t.buf[0], A, A, item * kTrsmRows, (int)t.n, (int)t.n, smem);
+    if (t.n <= kSmallTile)
+        trsm_rows<double, false, false, kSmallTrsmRows>((const double *)t.buf[0], A, A, item * kSmallTrsmRows,
+                                                        (int)t.n, (int)t.n, smem);
+    else
+        trsm_rows<double>((const double *)t.buf[0], A, A, item * kTrsmRows, (int)t.n, (int)t.n, smem);
 }
 
 // TRTRI: U_k <- L_kk^{-T} (upper triangular, the strict lower part zero),
@@ -412,7 +450,8 @@ __device__ __forceinline__ void potrf_panel_rows(double *A, int ld, int rr0, int
 }
 
 // Step (3) of potrf_block: rows jb + 32.. of the 32 columns from jb, solved
-// against the factored 32 x 32 block Dg, one row per thread.  Right-looking:
+// against the factored 32 x 32 block Dg (with 1 / Dg(c, c) in the padding
+// slot Dg[c * 33 + 32]), one row per thread.  Right-looking:
 // once x[c] is final it is subtracted from every later column, so each x[c']
 // takes the terms q = 0, 1, .. in the same order as a left-looking sum (the
 // same roundings), but a row's dependent chain is one division and one FMA
@@ -427,7 +466,7 @@ __device__ __noinline__ void potrf_rows_below(double *A, int b, int ld, int jb, 
         for (int c = 0; c < PW; ++c) x[c] = A[(size_t)i + (size_t)(jb + c) * ld];
 #pragma unroll
         for (int c = 0; c < PW; ++c) {
-            x[c] = x[c] / Dg[c * 33 + c];
+            x[c] = div_rcp(x[c], Dg[c * 33 + c], Dg[c * 33 + 32]);
 #pragma unroll
             for (int c2 = c + 1; c2 < PW; ++c2) x[c2] = fma(-x[c], Dg[c2 * 33 + c], x[c2]);
         }
@@ -484,8 +523,13 @@ __device__ __forceinline__ int potrf_block(double *A, int n, int ld, double *sme
             const int i = e & 31, k = e >> 5;
             if (i >= k) A[(size_t)(jb + i) + (size_t)(jb + k) * ld] = Dg[i * 33 + k];
         }
-        // (3) rows below the block: X Dg^T = P, one row per thread
-        potrf_rows_below(A, b, ld, jb, Dg);
+        // (3) rows below the block: X Dg^T = P, one row per thread, dividing
+        // by the 32 pivots through their reciprocals (padding slot of row c)
+        if (jb + PW < b) {
+            if (tid < PW) Dg[tid * 33 + 32] = 1.0 / Dg[tid * 33 + tid];
+            __syncthreads();
+            potrf_rows_below(A, b, ld, jb, Dg);
+        }
         __syncthreads();
     }
     return 0;
@@ -535,6 +579,11 @@ __device__ __forceinline__ void nbar_arrive2(int p) {
 //                         chain thread (no barrier before its square root);
 //   update, column j: wait L_j; column j + 2; arrive T_j; columns j + 3 ..;
 //                     barrier among the update warps.
+// The update warps walk the trailing elements of columns j + 3 .. 63 as one
+// packed range (the lower triangle stored column by column, an index table
+// in shared memory), 128 elements per pass, so that every FP64 instruction
+// they issue carries 32 useful lanes: an SM sub-partition issues one FP64
+// warp instruction per 64 cycles whatever the number of active lanes.
 // L_j and T_j alternate between two barrier ids each: neither side can run
 // two columns ahead of the other, so an id is never reused before its
 // previous phase completed.  Warps 4 and 5 wait at the final barrier.  A
@@ -546,10 +595,16 @@ __device__ __noinline__ int potrf64_pipelined(double *A, int ld, double *S, int 
     // L(j, j) goes to Dg: every chain thread reads the updated A(j, j) while
     // forming d_j, so that element is not written again inside the loop
     double *Dg = S + n * SP;
+    // packed lower triangle, column by column: element (r, c) at
+    // off(c) + r - c with off(c) = 64 c - c (c - 1) / 2; tab[e] = r | c << 8
+    unsigned short *tab = reinterpret_cast<unsigned short *>(Dg + n);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int e = tid; e < n * n; e += kThreads) {
         const int r = e & 63, c = e >> 6;
-        if (r >= c) S[c * SP + r] = A[(size_t)r + (size_t)c * ld];
+        if (r >= c) {
+            S[c * SP + r] = A[(size_t)r + (size_t)c * ld];
+            tab[c * n - c * (c - 1) / 2 + r - c] = (unsigned short)(r | c << 8);
+        }
     }
     if (tid == 0) *s_info = 0;
     __syncthreads();
@@ -579,34 +634,34 @@ __device__ __noinline__ int potrf64_pipelined(double *A, int ld, double *S, int 
         }
         if (tid == 0) *s_info = info;
     } else if (warp != 4 && warp != 5) {
-        // columns of parity g on sub-partition 2 + g (warps 2, 6: even;
-        // 3, 7: odd); rows 0..31 on warps 2, 3 and 32..63 on warps 6, 7, so
-        // that the late columns (rows near 63 only) still use both
-        const int g = warp & 1, i = (warp >= 6 ? 32 : 0) + lane;
+        // u = 0..127 over warps 2, 3, 6, 7 (sub-partitions 2, 3, 2, 3): each
+        // pass of 128 elements gives every warp 32 of them
+        const int u = ((warp & 1) | (warp >= 6 ? 2 : 0)) * 32 + lane;
         for (int j = 0; j + 2 < n; ++j) {
             nbar_sync2<1, kBoth>(j & 1);
-            const double li = S[j * SP + i];
-            if (((j + 2) & 1) == g && i >= j + 2)
-                S[(j + 2) * SP + i] = fma(-li, S[j * SP + j + 2], S[(j + 2) * SP + i]);
+            // column j + 2 first (rows j + 2 .., needed by the chain's next step)
+            const int i2 = j + 2 + u;
+            if (i2 < n) S[(j + 2) * SP + i2] = fma(-S[j * SP + i2], S[j * SP + j + 2], S[(j + 2) * SP + i2]);
             nbar_arrive2<3, kBoth>(j & 1);
-            // four columns of this parity at a time, loads before the FMAs
-            // (independent elements: one memory latency per group); rows
-            // 0..31 hold no element of the columns from 32
-            const int kend = warp >= 6 ? n : 32;
-            for (int k = j + 3 + (((j + 3) & 1) != g); k < kend; k += 8) {
-                double a[4], lk[4];
+            // columns j + 3 .. 63, four elements per thread at a time, loads
+            // before the FMAs (one shared-memory latency per group)
+            const int c3 = j + 3;
+            for (int e0 = c3 * n - c3 * (c3 - 1) / 2 + u; e0 < n * (n + 1) / 2; e0 += 4 * kUpd) {
+                double a[4], li[4], lk[4];
+                int pos[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const int kq = k + 2 * q;
-                    const bool v = kq < kend && i >= kq;
-                    lk[q] = v ? S[j * SP + kq] : 0.0;
-                    a[q] = v ? S[kq * SP + i] : 0.0;
+                    const int e = e0 + q * kUpd;
+                    const bool v = e < n * (n + 1) / 2;
+                    const int rc = v ? tab[e] : 0, r = rc & 255, c = rc >> 8;
+                    pos[q] = v ? c * SP + r : -1;
+                    li[q] = v ? S[j * SP + r] : 0.0;
+                    lk[q] = v ? S[j * SP + c] : 0.0;
+                    a[q] = v ? S[c * SP + r] : 0.0;
                 }
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int kq = k + 2 * q;
-                    if (kq < kend && i >= kq) S[kq * SP + i] = fma(-li, lk[q], a[q]);
-                }
+                for (int q = 0; q < 4; ++q)
+                    if (pos[q] >= 0) S[pos[q]] = fma(-li[q], lk[q], a[q]);
             }
             nbar_sync<6, kUpd>();
         }

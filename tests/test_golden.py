@@ -44,7 +44,7 @@ def test_cholesky_dag_golden_closed_forms_and_library():
     assert all(p < s for p, s in edges) and len(set(edges)) == len(edges)
     # the C ABI derives the stored edges for the same submission
     c = b3t.Context(host_only=True)
-    c.cholesky_submit([0x10000000 + (i << 20) for i in range(T * (T + 1) // 2)], T, 128)
+    c.cholesky_submit([0x10000000 + (i << 20) for i in range(T * (T + 1) // 2)], T, 64)   # one task per tile
     assert sorted(c.dag_edges()) == edges
     c.close()
 

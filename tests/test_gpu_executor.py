@@ -116,15 +116,21 @@ def test_cholesky_integer_exact(orc, gctx, N, b):
     assert np.array_equal(L, L0)
 
 
-def test_cholesky_config1_parity(orc, gctx):
-    # N = 1024, tile 128 (8 x 8 tiles, 120 tasks), A = B B^T / N + I, seed 0
+@pytest.mark.parametrize("panels", [True, False])
+def test_cholesky_config1_parity(orc, gctx, monkeypatch, panels):
+    # N = 1024, tile 128 (8 x 8 tiles, 120 tile tasks), A = B B^T / N + I,
+    # seed 0.  By default each diagonal POTRF runs as a DAG of 64-wide
+    # panels (POTRF_D, PANEL_TRSM, PANEL_UPD, POTRF_D: 144 device tasks);
+    # with the panels off, one POTRF task per diagonal tile (120)
+    if not panels:
+        monkeypatch.setenv("B3T_PANEL_WIDTH", "0")
     A = synth.spd_host(1024, seed=0, shift=1.0)
     L = factor_device(gctx, A, 128)
     Lo = factor_oracle(A, 128)
     assert np.max(np.abs(L - Lo)) / np.max(np.abs(Lo)) <= FP64_TOL
     assert och.rel_residual(L, A) <= 1e-12
     st = gctx.last_launch()
-    assert st["ntasks"] == 120
+    assert st["ntasks"] == (144 if panels else 120)
 
 
 @pytest.mark.parametrize("N,b", [(320, 64), (1536, 512)])
@@ -283,7 +289,8 @@ def test_trace_records_every_item(gctx):
     pairs = set(zip(tr["task"].tolist(), tr["item"].tolist()))
     assert len(pairs) == nitems and {t for t, _ in pairs} == set(range(ntasks))
     assert np.all(tr["t_end_ns"] >= tr["t_start_ns"])
-    assert set(tr["kind"].tolist()) <= {b3t.POTRF, b3t.TRSM, b3t.SYRK, b3t.GEMM}
+    assert set(tr["kind"].tolist()) <= {b3t.POTRF, b3t.TRSM, b3t.SYRK, b3t.GEMM, b3t.POTRF_D, b3t.PANEL_TRSM,
+                                        b3t.PANEL_UPD}
 
 
 def test_kernel_variant_covers_mixed_launch(orc, gctx):
@@ -340,7 +347,7 @@ def test_execution_order_respects_every_edge(orc, gctx, shape):
     # the oracle's, derived from the same accesses.
     from oracle import dag
     if shape == "cholesky":
-        T, b = 6, 128
+        T, b = 6, 64      # one task per tile (from b = 128 the diagonal POTRF is a panel DAG)
         A = torch.from_numpy(och.to_tiles(synth.spd_host(T * b, seed=13, shift=1.0), b)).cuda()
         gctx.trace_start(1 << 16)
         gctx.cholesky_submit(dt.tile_ptrs(A), T, b)
@@ -410,3 +417,111 @@ def test_acquire_makes_the_writers_result_visible(orc, gctx):
     gctx.data_acquire(hs[5], RW)
     for h in hs:
         gctx.data_unregister(h)
+
+
+# ---- item chains: successor first at item granularity (Section 2)
+def run_chain_items(x, f, n, extra=None, trace=False):
+    """Chains of scaling tasks (block-major submission) with item chains on;
+    extra(ctx, hs) may submit more tasks in between.  Returns the result and
+    the context's chain layout (and the trace when asked)."""
+    nb, nk = f.shape
+    c = b3t.Context(stream=torch.cuda.current_stream().cuda_stream, timeout_ns=20_000_000_000, item_chains=True)
+    if trace:
+        c.trace_start(1 << 16)      # before the submissions (a start waits for pending work)
+    xd = torch.from_numpy(x.copy()).cuda()
+    hs = [c.data_register(xd[i * n:(i + 1) * n].data_ptr(), n, 4) for i in range(nb)]
+    cl = c.task_decl("scale_vector", b3t.SCAL_F32, [RW], 4)
+    for k in range(nk):
+        for i in range(nb):
+            c.task_submit(cl, [hs[i]], b3t.pack_f32(float(f[i, k])))
+            if extra:
+                extra(c, hs, k, i)
+    aux = c.dag_item_chains()
+    ed = c.dag_edges()
+    c.task_wait()
+    tr = c.trace_read() if trace else None
+    ll = c.last_launch()
+    if trace:
+        c.trace_stop()
+    c.close()
+    return xd.cpu().numpy(), aux, ed, tr, ll
+
+
+@pytest.mark.parametrize("nb,n,nk", [(16, 3 * (1 << 16) + 12, 8), (3, 1000, 8), (4, (1 << 16) + 4, 40)])
+def test_item_chains_bit_exact(orc, nb, n, nk):
+    # each chunk takes every factor of its chain in order, one rounding each:
+    # the oracle's in-order binary32 multiplies, bit for bit; a ragged last
+    # item, tasks of one item, and runs of 40 cut into chains of 32 and 7
+    x = synth.vector_f32(nb * n, seed=41)
+    x[:7] = np.array([1e-38, -3e-39, 5e-45, 0.0, -0.0, 3e38, -1.0], dtype=np.float32)
+    f = synth.chain_factors(nb, nk, seed=42)
+    y, aux, _, _, _ = run_chain_items(x, f, n)
+    heads = [a for a in aux if a > 0]
+    assert len(heads) == nb * ((nk - 1 + 32) // 33 if nk > 33 else 1)
+    assert sum(heads) + len(heads) == nb * nk
+    z = run_chain_oracle(x, f)
+    assert np.array_equal(y.view(np.uint32), z.view(np.uint32))
+
+
+def test_item_chains_tail_of_a_single_block(orc):
+    # one block whose length is not a multiple of four (elements after the
+    # last full 16 bytes are scaled by the threads, not the bulk copies)
+    n = 2 * (1 << 16) + 7
+    x = synth.vector_f32(n, seed=43)
+    f = synth.chain_factors(1, 8, seed=44)
+    y, aux, _, _, _ = run_chain_items(x, f, n)
+    assert aux[0] == 7
+    assert np.array_equal(y.view(np.uint32), run_chain_oracle(x, f).view(np.uint32))
+
+
+def test_item_chains_break_at_readers_and_release_successors(orc):
+    # an empty task reading block 1 after step 3 ends that block's chain
+    # (the reader must see the step-3 result) and a new chain starts after
+    # it; every reader and the tasks after the chains run after them
+    nb, n, nk = 4, (1 << 16) + 4, 8
+    x = synth.vector_f32(nb * n, seed=45)
+    f = synth.chain_factors(nb, nk, seed=46)
+    cr = {}
+
+    def extra(c, hs, k, i):
+        if i == 1 and k == 3:
+            if "r" not in cr:
+                cr["r"] = c.task_decl("reader", b3t.NOOP, [R])
+            c.task_submit(cr["r"], [hs[1]])
+    y, aux, ed, tr, ll = run_chain_items(x, f, n, extra, trace=True)
+    assert sum(1 for a in aux if a > 0) == nb + 1
+    assert np.array_equal(y.view(np.uint32), run_chain_oracle(x, f).view(np.uint32))
+    # the trace holds every (task, item) once; the edges that no chain
+    # absorbed are respected task by task, the absorbed ones item by item
+    assert len(tr) == ll["nitems"]
+    pairs = set(zip(tr["task"].tolist(), tr["item"].tolist()))
+    assert len(pairs) == ll["nitems"]
+    member = {i for i, a in enumerate(aux) if a == -1}
+    st = {}
+    for t, it, s0, e0 in zip(tr["task"].tolist(), tr["item"].tolist(), tr["t_start_ns"].tolist(),
+                             tr["t_end_ns"].tolist()):
+        st[(t, it)] = (s0, e0)
+    ntask = len(aux)
+    ts = [min(v[0] for k, v in st.items() if k[0] == t) for t in range(ntask)]
+    te = [max(v[1] for k, v in st.items() if k[0] == t) for t in range(ntask)]
+    for p, s in ed:
+        if s in member:
+            items = [k[1] for k in st if k[0] == s]
+            assert all(st[(s, it)][0] >= st[(p, it)][0] for it in items)
+        else:
+            assert te[p] <= ts[s], (p, s)
+
+
+def test_item_chains_full_size_config(orc):
+    # n = 2^28, 256 blocks x 8 chained tasks with item chains: sampled blocks
+    # against in-order binary32 multiplies
+    nb, nk, n = 256, 8, 1 << 20
+    x = synth.vector_f32(nb * n, seed=1)
+    f = synth.chain_factors(nb, nk, seed=2)
+    y, aux, _, _, _ = run_chain_items(x, f, n)
+    assert aux[:nb] == [7] * nb
+    for i in [0, 1, 77, 128, 255]:
+        z = x[i * n:(i + 1) * n].copy()
+        for k in range(nk):
+            otl.scal_f32(z, f[i, k])
+        assert np.array_equal(y[i * n:(i + 1) * n].view(np.uint32), z.view(np.uint32))

@@ -91,7 +91,7 @@ def test_edges_match_oracle_with_partitions(ctx):
 
 @pytest.mark.parametrize("T", [1, 2, 8, 64])
 def test_cholesky_submission_edges(ctx, T):
-    b = 128
+    b = 64      # one POTRF task per diagonal tile (b >= 128 splits it into panels)
     ptrs = [fake_ptr(i) for i in range(och.ntiles(T))]
     ctx.cholesky_submit(ptrs, T, b)
     nt, ne = ctx.dag_stats()
@@ -202,13 +202,14 @@ def test_strerror():
     assert "positive definite" in b3t.strerror(b3t._lib.EDOM)
 
 
-@pytest.mark.parametrize("T,b", [(1, 256), (3, 512), (4, 256)])
+@pytest.mark.parametrize("T,b", [(1, 256), (3, 512), (4, 256), (3, 128), (2, 192)])
 def test_cholesky_panel_dag_edges(ctx, T, b):
     # b >= 256: each diagonal tile is partitioned into b/128 column panels
-    # and POTRF becomes POTRF_D / PANEL_TRSM / PANEL_UPD tasks on the parts
+    # (b = 128 and 192: 64-column panels) and POTRF becomes POTRF_D /
+    # PANEL_TRSM / PANEL_UPD tasks on the parts
     ptrs = [fake_ptr(i) for i in range(och.ntiles(T))]
     ctx.cholesky_submit(ptrs, T, b)
-    np_ = b // 128
+    np_ = b // (128 if b >= 256 else 64)
     parts = {och.tile_index(k, k, T): tuple(("P", k, kk) for kk in range(np_)) for k in range(T)}
     acc = []
     for k in range(T):
@@ -240,7 +241,7 @@ def test_tiles_unregister_forgets_panel_parts(ctx):
         ctx.tiles_unregister([p], 1)
     assert e.value.code == b3t._lib.ENODEV
     part1 = p + 256 * 128 * 8
-    ctx.cholesky_submit([part1], 1, 128)
+    ctx.cholesky_submit([part1], 1, 64)
     assert ctx.dag_stats()[0] == 1
 
 
@@ -438,7 +439,7 @@ def test_cholesky_upward_rank_follows_the_critical_path(T, cp):
     # following the largest-ranked successor from it walks a path whose costs
     # add up to that rank.  With equal costs (the same accesses as empty
     # tasks) that walk is the closed-form critical path of 3T - 2 tasks.
-    b = 128
+    b = 64
     with b3t.Context(host_only=True) as c:
         nt = T * (T + 1) // 2
         tiles = [fake_ptr(i) for i in range(nt)]
@@ -480,3 +481,90 @@ def test_cholesky_upward_rank_follows_the_critical_path(T, cp):
         steps += 1
     assert rank_u[0] == NOOP_COST * cp
     assert steps == cp == dag.critical_path(n, edges)
+
+
+# ---- item chains (successor first at item granularity, Section 2)
+def _chains_by_rule(kinds, bufs, edges, cap=32):
+    """Item chains restated from the edge list: t links to s when both are
+    vector-scaling tasks on one buffer, s is t's only successor and t is s's
+    only predecessor; maximal runs of links are cut into chains of at most
+    `cap` members after their head."""
+    n = len(kinds)
+    succ = [[] for _ in range(n)]
+    npred = [0] * n
+    for p, s in edges:
+        succ[p].append(s)
+        npred[s] += 1
+    nxt = [-1] * n
+    for t in range(n):
+        if kinds[t] == "scal" and len(succ[t]) == 1:
+            s = succ[t][0]
+            if kinds[s] == "scal" and npred[s] == 1 and bufs[s] == bufs[t]:
+                nxt[t] = s
+    linked = {s for s in nxt if s >= 0}
+    aux = [0] * n
+    for t in range(n):
+        if nxt[t] < 0 or t in linked:
+            continue
+        h = t
+        while h >= 0 and nxt[h] >= 0:
+            mem, m = [], nxt[h]
+            while m >= 0 and len(mem) < cap:
+                mem.append(m)
+                m = nxt[m]
+            aux[h] = len(mem)
+            for x in mem:
+                aux[x] = -1
+            h = m
+    return aux
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_item_chains_follow_the_rule(seed):
+    # random mixes of RW scaling tasks and R / W / RW empty tasks on four
+    # buffers, with long runs so that some chains are cut at 32 members
+    rng = np.random.default_rng(seed)
+    nb = 4
+    kinds, bufs, accesses = [], [], []
+    for _ in range(int(rng.integers(60, 160))):
+        h = int(rng.integers(nb))
+        r = rng.random()
+        if r < 0.8:
+            kinds.append("scal"); accesses.append([(h, RW)])
+        else:
+            kinds.append("noop"); accesses.append([(h, [R, W, RW][int(rng.integers(3))])])
+        bufs.append(h)
+    edges = dag.derive_edges(accesses)
+    with b3t.Context(host_only=True, item_chains=True) as c:
+        hs = [c.data_register(fake_ptr(i), 1 << 18, 4) for i in range(nb)]
+        cs = c.task_decl("scale_vector", b3t.SCAL_F32, [RW], 4)
+        cn = {m: c.task_decl("t", b3t.NOOP, [m]) for m in (R, W, RW)}
+        for k, acc in zip(kinds, accesses):
+            h, m = acc[0]
+            if k == "scal":
+                c.task_submit(cs, [hs[h]], b3t.pack_f32(1.5))
+            else:
+                c.task_submit(cn[m], [hs[h]])
+        assert sorted(c.dag_edges()) == sorted(edges)
+        got = c.dag_item_chains()
+    assert got == _chains_by_rule(kinds, bufs, edges)
+    # with item chains off nothing is chained
+    with b3t.Context(host_only=True) as c:
+        hs = [c.data_register(fake_ptr(i), 1 << 18, 4) for i in range(nb)]
+        cs = c.task_decl("scale_vector", b3t.SCAL_F32, [RW], 4)
+        for _ in range(5):
+            c.task_submit(cs, [hs[0]], b3t.pack_f32(2.0))
+        assert c.dag_item_chains() == [0] * 5
+
+
+def test_item_chains_of_the_vector_configuration():
+    # 256 blocks of 2^20 floats with 8 chained scaling tasks each form 256
+    # chains: every block's first task heads its 7 successors
+    with b3t.Context(host_only=True, item_chains=True) as c:
+        cs = c.task_decl("scale_vector", b3t.SCAL_F32, [RW], 4)
+        hs = [c.data_register(fake_ptr(i), 1 << 20, 4) for i in range(256)]
+        for k in range(8):
+            for h in hs:
+                c.task_submit(cs, [h], b3t.pack_f32(1.0))
+        aux = c.dag_item_chains()
+    assert aux[:256] == [7] * 256 and aux[256:] == [-1] * (7 * 256)
