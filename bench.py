@@ -88,8 +88,9 @@ def parse():
                    help="distinct client inputs (the first requests of the stream), cycled over the run")
     p.add_argument("--serve-plain-requests", type=int, default=256,
                    help="requests of the same stream served by the per-request path")
-    p.add_argument("--prio", default="upward", choices=["upward", "depth"],
-                   help="ready-queue order of the profiling cases (--case)")
+    p.add_argument("--prio", default="upward", choices=["upward", "depth", "critical"],
+                   help="ready-queue order (b3t_config.prio_policy) of the headline context, the time to solution "
+                        "and the profiling cases (--case); the vector chains and empty DAGs set their own")
     p.add_argument("--ctas-per-sm", type=int, default=0, help="grid of the profiling cases (0: occupancy)")
     p.add_argument("--item-chains", action="store_true",
                    help="profiling cases: run vector-scaling chains item by item (b3t_config.item_chains)")
@@ -98,6 +99,11 @@ def parse():
                    help="run one profiling case (a DAG of one task kind), or one secondary measurement alone "
                         "(empty_dags, serve_sweep, trace_headline, batch), and print its result")
     return p.parse_args()
+
+
+def prio_of(args):
+    import paper_1304_0878_b300 as b3t
+    return {"upward": b3t.PRIO_UPWARD, "depth": b3t.PRIO_DEPTH, "critical": b3t.PRIO_CRITICAL}[args.prio]
 
 
 def cholesky_flops(N):
@@ -332,7 +338,7 @@ def run_ours(args):
         tdist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    ctx = b3t.Context(stream=stream.cuda_stream, timeout_ns=120_000_000_000)
+    ctx = b3t.Context(stream=stream.cuda_stream, timeout_ns=120_000_000_000, prio_policy=prio_of(args))
     N, b = args.n, args.b
     T = N // b
     flops = cholesky_flops(N)
@@ -1078,7 +1084,7 @@ def run_case(args):
     dev = torch.device("cuda", 0)
     ctx = b3t.Context(stream=torch.cuda.current_stream().cuda_stream, timeout_ns=60_000_000_000,
                       ctas_per_sm=args.ctas_per_sm,
-                      prio_policy=b3t.PRIO_DEPTH if args.prio == "depth" else b3t.PRIO_UPWARD,
+                      prio_policy=prio_of(args),
                       item_chains=args.item_chains)
     b = 512
     if args.case.startswith("mx_gemm"):
@@ -1319,7 +1325,8 @@ def run_trace_headline(dev, args):
     from paper_1304_0878_b300 import tiles as dt
     N, b = args.n, args.b
     T = N // b
-    ctx = b3t.Context(stream=torch.cuda.current_stream(dev).cuda_stream, timeout_ns=120_000_000_000)
+    ctx = b3t.Context(stream=torch.cuda.current_stream(dev).cuda_stream, timeout_ns=120_000_000_000,
+                      prio_policy=prio_of(args))
     t = synth.spd_tiles_device(N, b, 3, 0.1, dev)
     ctx.trace_start(1 << 22)
     ctx.cholesky_submit(dt.tile_ptrs(t), T, b)
@@ -1348,7 +1355,8 @@ def run_trace_mixed(dev, args):
     from paper_1304_0878_b300 import tiles as dt
     N, b = args.n, args.b
     T = N // b
-    ctx = b3t.Context(stream=torch.cuda.current_stream(dev).cuda_stream, timeout_ns=120_000_000_000)
+    ctx = b3t.Context(stream=torch.cuda.current_stream(dev).cuda_stream, timeout_ns=120_000_000_000,
+                      prio_policy=prio_of(args))
     A0 = synth.spd_tiles_device(N, b, 3, 0.1, dev)
     W = A0.float()
     del A0

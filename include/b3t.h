@@ -283,7 +283,12 @@ typedef struct b3t_config {
                                longest remaining path first (upward rank,
                                Section 5.3); B3T_PRIO_DEPTH (1): deepest task
                                first, so a successor runs right after its
-                               predecessor while the data is in L2 */
+                               predecessor while the data is in L2;
+                               B3T_PRIO_CRITICAL (2): critical path first
+                               (Section 5.3's upward and downward ranks):
+                               the tasks whose upward plus downward rank is
+                               the graph's longest path take the top level,
+                               the others the levels below by upward rank */
     int32_t stream_free_sms; /* stream mode: SMs the resident kernel leaves
                                free for other work issued meanwhile (input
                                generation, copies); 0 = 8 */
@@ -312,7 +317,7 @@ typedef struct b3t_config {
                                task. */
 } b3t_config;
 
-enum { B3T_PRIO_UPWARD = 0, B3T_PRIO_DEPTH = 1 };
+enum { B3T_PRIO_UPWARD = 0, B3T_PRIO_DEPTH = 1, B3T_PRIO_CRITICAL = 2 };
 
 /* Create a context bound to the current CUDA device and to `cuda_stream`
  * (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream; NULL = the
@@ -425,12 +430,17 @@ B3T_API int b3t_dag_edges(b3t_ctx *ctx, int32_t *pred, int32_t *succ, int64_t ca
 
 /* Scheduling priority of the pending batch's tasks, as the next flush will
  * use it (Section 5.3: upward rank as a scheduling hint): rank[t] is, under
- * B3T_PRIO_UPWARD, the longest path from task t to the end of the graph
- * weighted by the library's per-kind cost estimate (ns on one CTA; t's own
- * cost included), or, under B3T_PRIO_DEPTH, the number of tasks on the
- * longest path from a source to t; level[t] in 0..prio_levels-1 is the ready
- * queue level (higher is claimed first): floor(L * rank / (max rank *
- * 1.000001)) for upward rank, min(L - 1, rank) for depth, 0 with one level.
+ * B3T_PRIO_UPWARD and B3T_PRIO_CRITICAL, the longest path from task t to the
+ * end of the graph weighted by the library's per-kind cost estimate (ns on
+ * one CTA; t's own cost included), or, under B3T_PRIO_DEPTH, the number of
+ * tasks on the longest path from a source to t; level[t] in
+ * 0..prio_levels-1 is the ready queue level (higher is claimed first):
+ * floor(L * rank / (max rank * 1.000001)) for upward rank, min(L - 1, rank)
+ * for depth; for critical, L - 1 if the longest path through t (its
+ * downward rank, the longest cost-weighted path from a source to t with t's
+ * cost excluded, plus its upward rank) is the graph's longest path, else
+ * min(L - 2, floor((L - 1) * rank / (max rank * 1.000001))); 0 with one
+ * level.
  * Writes at most cap entries of each (either pointer may be NULL); *count =
  * number of pending tasks. */
 B3T_API int b3t_dag_levels(b3t_ctx *ctx, float *rank, int32_t *level, int64_t cap, int64_t *count);

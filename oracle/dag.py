@@ -115,6 +115,26 @@ def upward_rank(n, edges, cost):
     return [memo[t] for t in range(n)]
 
 
+def downward_rank(n, edges, cost):
+    """Downward rank of every task (the other scheduling hint Section 5.3
+    names): the largest total cost over the paths from a task without
+    predecessors to the task, the task's own cost excluded.  Written as that
+    definition, by recursion over predecessors."""
+    pred = [[] for _ in range(n)]
+    for p, s in edges:
+        pred[s].append(p)
+    memo = {}
+
+    def longest(t):
+        if t not in memo:
+            memo[t] = max((longest(p) + cost[p] for p in pred[t]), default=0.0)
+        return memo[t]
+
+    for t in range(n):
+        longest(t)
+    return [memo[t] for t in range(n)]
+
+
 def depth(n, edges):
     """Edges on the longest path from a source to each task."""
     d = [0] * n

@@ -14,5 +14,5 @@ from ._lib import (Context, B3TError, Config, lib, strerror, q_bytes, header_sym
                    slice_x_part_bytes, slice_w_bytes, slice_u_bytes, slice_args, TRTRI_COL,
                    pack_f32, pack_i32, R, W, RW, NOOP, SCAL_F32, POTRF, TRSM, SYRK, GEMM,
                    POTRF_MX, TRSM_MX, SYRK_MX, GEMM_MX, QUANT, FMT_BF16, FMT_E4M3,
-                   PRIO_UPWARD, PRIO_DEPTH, POTRF_D, PANEL_TRSM, PANEL_UPD, CVT)
+                   PRIO_UPWARD, PRIO_DEPTH, PRIO_CRITICAL, POTRF_D, PANEL_TRSM, PANEL_UPD, CVT)
 from . import tiles  # noqa: F401

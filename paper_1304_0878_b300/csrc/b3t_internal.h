@@ -27,11 +27,14 @@ constexpr int64_t kScalChunk = 1 << 16;  // f32 elements per SCAL item
 constexpr int kMaxChain = 32;            // SCAL tasks absorbed by one item-chain head
 constexpr int kGemmBlk = 64;             // f64 GEMM / SYRK item: 64 x 64 of C
 constexpr int kTrsmRows = 32;            // f64 TRSM item: 32 rows of A_ik
-// Tiles of at most kSmallTile rows (a factorisation of a few thousand rows,
-// bound by its critical path) split finer: TRSM items of kSmallTrsmRows
-// rows, SYRK / GEMM items of kSmallGemmRows x 64, so that one task's work
-// spreads over more SMs (one SM does ~8 GFLOP/s of FP64)
+// In launches of at most kFineLaunchTasks tasks (a factorisation of a few
+// thousand rows, bound by its critical path), tiles of at most kSmallTile
+// rows split finer: TRSM items of kSmallTrsmRows rows, SYRK / GEMM items of
+// kSmallGemmRows x 64, so that one task's work spreads over more SMs (one SM
+// does ~8 GFLOP/s of FP64).  The device tells the splits apart by the
+// task's item count.
 constexpr int kSmallTile = 128;
+constexpr int64_t kFineLaunchTasks = 2048;
 constexpr int kSmallTrsmRows = 8;
 constexpr int kSmallGemmRows = 16;
 #ifndef B3T_TRTRI_ROWS

@@ -145,22 +145,25 @@ bool is_mx(int kind) { return kind == kSyrkMx || kind == kGemmMx || kind == kRes
 bool is_slice(int kind) { return kind >= kSliceA && kind <= kResidSl; }
 bool has_fmt(int kind) { return kind == kSyrkMx || kind == kGemmMx || kind == kQuant; }
 
-int64_t items_of(int kind, int64_t n) {
+// fine: the split of a small launch (see fine_items) for tiles of at most
+// kSmallTile rows; the device tells the two splits apart by the item count
+int64_t items_of(int kind, int64_t n, bool fine = false) {
+    fine = fine && n <= kSmallTile;
     switch (kind) {
     case kScalF32: return std::max<int64_t>(1, (n + kScalChunk - 1) / kScalChunk);
     case kPotrf: case kPotrfMx: case kNoop: return 1;
     case kCvt: return n / kCvtCols;
     case kQuant: return 1;   // set from the format at submit (one item per 16 KiB chunk)
-    case kTrsm: return n <= kSmallTile ? n / kSmallTrsmRows : n / kTrsmRows;
+    case kTrsm: return fine ? n / kSmallTrsmRows : n / kTrsmRows;
     case kTrsmMx: return n / kTrsmRows;
     case kTrtri: return n / kTrtriRows;
     case kSyrk: {
         int64_t m = n / kGemmBlk;
-        return n <= kSmallTile ? (n / kSmallGemmRows) * m : m * (m + 1) / 2;
+        return fine ? (n / kSmallGemmRows) * m : m * (m + 1) / 2;
     }
     case kGemm: {
         int64_t m = n / kGemmBlk;
-        return n <= kSmallTile ? (n / kSmallGemmRows) * m : m * m;
+        return fine ? (n / kSmallGemmRows) * m : m * m;
     }
     case kTrmmMx: return (n / kTrmmRows) * (n / kGemmBlk);
     case kSyrkMx: { int64_t m = n / kMxBlk; return m * (m + 1) / 2; }
@@ -402,6 +405,16 @@ static void find_item_chains(const b3t_ctx *c, const std::vector<int32_t> &off, 
 int build_launch(b3t_ctx *c, Arena &a, InitParams &ip, LaunchParams &lp, int64_t &nitems_out,
                  bool &has_mx) {
     const int64_t nt = (int64_t)c->tasks.size();
+    // a small launch (one factorisation of a few thousand rows, bound by its
+    // critical path) splits FP64 TRSM / SYRK / GEMM tasks on tiles of at
+    // most kSmallTile rows finer, so that one task spreads over more SMs;
+    // large launches (many factorisations, big T) keep the coarse split
+    const bool fine = nt <= kFineLaunchTasks;
+    for (auto &tk : c->tasks) {
+        TaskRec &r = tk.rec;
+        if ((r.kind == kTrsm || r.kind == kSyrk || r.kind == kGemm) && r.n <= kSmallTile)
+            r.nitems = (int32_t)items_of(r.kind, r.n, fine);
+    }
     const int64_t ne = (int64_t)c->edges.size();
     const int L = c->cfg.prio_levels;
     std::vector<int32_t> off(nt + 1, 0), indeg(nt, 0);
@@ -536,11 +549,33 @@ void compute_levels(const b3t_ctx *c, const std::vector<int32_t> &off, const int
     rank.assign(nt, 0.f);
     level.assign(nt, 0);
     float maxr = 0.f;
+    std::vector<char> crit;
     if (c->cfg.prio_policy == B3T_PRIO_DEPTH) {
         for (int64_t t = 0; t < nt; ++t) {
             for (int32_t k = off[t]; k < off[t + 1]; ++k) rank[succ[k]] = std::max(rank[succ[k]], rank[t] + 1.f);
             maxr = std::max(maxr, rank[t]);
         }
+    } else if (c->cfg.prio_policy == B3T_PRIO_CRITICAL) {
+        // upward rank (longest path from t to the end, t's cost included)
+        // and downward rank (longest path from a source to t, t's cost
+        // excluded) in double; their sum is the longest path through t, and
+        // the tasks whose sum is the graph's longest path (no slack) go on
+        // the top level
+        std::vector<double> up(nt, 0.0), down(nt, 0.0);
+        double longest = 0.0;
+        for (int64_t t = nt - 1; t >= 0; --t) {
+            double m = 0.0;
+            for (int32_t k = off[t]; k < off[t + 1]; ++k) m = std::max(m, up[succ[k]]);
+            up[t] = (double)c->tasks[t].cost + m;
+            rank[t] = (float)up[t];
+            maxr = std::max(maxr, rank[t]);
+            longest = std::max(longest, up[t]);
+        }
+        for (int64_t t = 0; t < nt; ++t)
+            for (int32_t k = off[t]; k < off[t + 1]; ++k)
+                down[succ[k]] = std::max(down[succ[k]], down[t] + (double)c->tasks[t].cost);
+        crit.assign(nt, 0);
+        for (int64_t t = 0; t < nt; ++t) crit[t] = down[t] + up[t] >= longest * (1.0 - 1e-9);
     } else {
         for (int64_t t = nt - 1; t >= 0; --t) {
             float m = 0.f;
@@ -553,6 +588,8 @@ void compute_levels(const b3t_ctx *c, const std::vector<int32_t> &off, const int
     for (int64_t t = 0; t < nt; ++t)
         level[t] = c->cfg.prio_policy == B3T_PRIO_DEPTH
                        ? std::min(L - 1, (int)rank[t])
+                   : !crit.empty()
+                       ? (crit[t] ? L - 1 : std::min(L - 2, (int)((double)(L - 1) * rank[t] / (maxr * 1.000001))))
                        : std::min(L - 1, (int)((double)L * rank[t] / (maxr * 1.000001)));
 }
 
@@ -904,7 +941,8 @@ int b3t_init(b3t_ctx **out, const b3t_config *cfg, void *cuda_stream) {
     if (cfg) c->cfg = *cfg;
     if (c->cfg.timeout_ns <= 0) c->cfg.timeout_ns = 10'000'000'000LL;
     if (c->cfg.prio_levels <= 0) c->cfg.prio_levels = kMaxLevels;
-    if (c->cfg.prio_policy != B3T_PRIO_DEPTH) c->cfg.prio_policy = B3T_PRIO_UPWARD;
+    if (c->cfg.prio_policy != B3T_PRIO_DEPTH && c->cfg.prio_policy != B3T_PRIO_CRITICAL)
+        c->cfg.prio_policy = B3T_PRIO_UPWARD;
     c->cfg.prio_levels = std::min(c->cfg.prio_levels, kMaxLevels);
     for (int k = 0; k < kNumKinds; ++k) c->kind_cl[k] = -1;
     if (host_only) { *out = c; return 0; }
@@ -1574,9 +1612,12 @@ int b3t_cholesky_submit(b3t_ctx *c, double *const *tiles, int32_t T, int32_t b, 
     if ((rc = kind_codelet(c, kPotrf, &cp)) || (rc = kind_codelet(c, kTrsm, &ct)) ||
         (rc = kind_codelet(c, kSyrk, &cs)) || (rc = kind_codelet(c, kGemm, &cg)))
         return rc;
-    // tiles below two 128-wide panels take 64-wide ones (a pipelined
-    // 64 x 64 POTRF, its panel solve and update instead of one CTA's whole tile)
-    const int32_t pw = b < 2 * kPanelWidth ? panel_width(b, 64) : panel_width(b);
+    // in a small factorisation (T <= 16) tiles below two 128-wide panels take
+    // 64-wide ones (a pipelined 64 x 64 POTRF, its panel solve and update
+    // instead of one CTA's whole tile); larger ones keep one POTRF task per
+    // tile.  The choice depends on the factorisation alone, so that a
+    // request's result is the same alone and in a stream of others
+    const int32_t pw = (b < 2 * kPanelWidth && T <= 16) ? panel_width(b, 64) : panel_width(b);
     const bool panels = pw > 0;
     std::vector<std::vector<b3t_handle>> dparts(panels ? T : 0);
     for (int32_t k = 0; panels && k < T; ++k)

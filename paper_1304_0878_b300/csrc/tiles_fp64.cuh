@@ -107,7 +107,7 @@ __device__ __forceinline__ void gemm64_f64(const double *A, int arow0, const dou
 __device__ __forceinline__ void gemm_item(const TaskRec &t, int item, double *smem) {
     const int b = (int)t.n, m = b / kGemmBlk;
     const int bi = item / m, bj = item % m;
-    if (b <= kSmallTile) {   // kSmallGemmRows x 64 blocks (the same FMAs per element)
+    if (b <= kSmallTile && t.nitems == (b / kSmallGemmRows) * m) {   // kSmallGemmRows x 64 blocks (the same FMAs per element)
         gemm_rows_f64<kSmallGemmRows>((const double *)t.buf[0], bi * kSmallGemmRows, (const double *)t.buf[1],
                                       bj * 64, (double *)t.buf[2], bi * kSmallGemmRows, bj * 64, b, b, false, 0,
                                       smem);
@@ -128,7 +128,7 @@ __device__ __forceinline__ void tri_index(int item, int &bi, int &bj) {
 
 __device__ __forceinline__ void syrk_item(const TaskRec &t, int item, double *smem) {
     const int b = (int)t.n;
-    if (b <= kSmallTile) {
+    if (b <= kSmallTile && t.nitems == (b / kSmallGemmRows) * (b / kGemmBlk)) {
         // kSmallGemmRows x 64 blocks; those wholly above the diagonal are empty
         const int m = b / kGemmBlk, bi = item / m, bj = item % m;
         if (bi * kSmallGemmRows + kSmallGemmRows - 1 < bj * 64) return;
@@ -285,7 +285,7 @@ __device__ __forceinline__ void trsm_rows(const double *L, const Tin *Ain, doubl
 
 __device__ __forceinline__ void trsm_item(const TaskRec &t, int item, double *smem) {
     double *A = (double *)t.buf[1];
-    if (t.n <= kSmallTile)
+    if (t.n <= kSmallTile && t.nitems == (int)t.n / kSmallTrsmRows)
         trsm_rows<double, false, false, kSmallTrsmRows>((const double *)t.buf[0], A, A, item * kSmallTrsmRows,
                                                         (int)t.n, (int)t.n, smem);
     else
@@ -677,7 +677,8 @@ __device__ __noinline__ int potrf64_pipelined(double *A, int ld, double *S, int 
 }
 
 __device__ __forceinline__ int potrf_tile(double *A, int b, double *smem, int *s_info) {
-    return potrf_block(A, b, b, smem, s_info);
+    // a 64 x 64 tile takes the pipelined right-looking factorisation
+    return b == 64 ? potrf64_pipelined(A, b, smem, s_info) : potrf_block(A, b, b, smem, s_info);
 }
 
 // ---- diagonal tile split into column panels (partition parts of the tile)

@@ -431,6 +431,53 @@ def test_depth_policy_is_longest_path_from_sources(seed):
     assert level == [min(7, x) for x in d]
 
 
+def _critical_levels(up, down, L=8):
+    longest = max(up)
+    return [L - 1 if d + u >= longest * (1 - 1e-9) else min(L - 2, int((L - 1) * u / (longest * 1.000001)))
+            for u, d in zip(up, down)]
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_critical_policy_puts_the_longest_paths_on_top(seed):
+    # critical path first (Section 5.3's upward and downward ranks): a task
+    # whose longest path through it is the graph's longest path takes the
+    # top level, the others the levels below by upward rank
+    rng = np.random.default_rng(1000 + seed)
+    n, nh = int(rng.integers(20, 120)), int(rng.integers(3, 12))
+    acc = [[(int(h), int(rng.choice([R, W, RW])))
+            for h in rng.choice(nh, size=int(rng.integers(1, 4)), replace=False)] for _ in range(n)]
+    with b3t.Context(host_only=True, prio_policy=b3t.PRIO_CRITICAL) as c:
+        _submit_accesses(c, acc, nh)
+        rank, level = c.dag_levels()
+    edges = dag.derive_edges(acc)
+    cost = [NOOP_COST] * n
+    up, down = dag.upward_rank(n, edges, cost), dag.downward_rank(n, edges, cost)
+    assert rank == up
+    assert level == _critical_levels(up, down)
+    top = [t for t in range(n) if level[t] == 7]
+    assert any(down[t] == 0 for t in top) and any(up[t] == NOOP_COST for t in top)
+
+
+def test_critical_policy_on_the_cholesky_dag():
+    # T = 8: the per-kind costs are read back from the ranks (rank minus the
+    # largest successor rank); the top level is exactly the tasks on a
+    # longest cost-weighted path
+    T, b = 8, 64
+    with b3t.Context(host_only=True, prio_policy=b3t.PRIO_CRITICAL) as c:
+        c.cholesky_submit([fake_ptr(i) for i in range(T * (T + 1) // 2)], T, b)
+        rank, level = c.dag_levels()
+        edges = c.dag_edges()
+        n = c.dag_stats()[0]
+    succ = [[] for _ in range(n)]
+    for p, s_ in edges:
+        succ[p].append(s_)
+    cost = [rank[t] - max((rank[s_] for s_ in succ[t]), default=0.0) for t in range(n)]
+    up, down = dag.upward_rank(n, edges, cost), dag.downward_rank(n, edges, cost)
+    assert np.allclose(rank, up, rtol=1e-6)
+    assert level == _critical_levels(up, down)
+    assert level[0] == 7 and level[n - 1] == 7      # POTRF(0) and the last POTRF
+
+
 @pytest.mark.parametrize("T,cp", [(8, 22), (64, 190)])
 def test_cholesky_upward_rank_follows_the_critical_path(T, cp):
     # tile kinds cost differently; the rank must still be the longest path of

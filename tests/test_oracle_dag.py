@@ -78,3 +78,39 @@ def test_cholesky_bruteforce_t2():
 def test_transitive_closure_small():
     e = [(0, 1), (1, 2), (0, 3)]
     assert dag.transitive_closure(4, e) == {(0, 1), (1, 2), (0, 2), (0, 3)}
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_ranks_by_path_enumeration(seed):
+    # upward and downward ranks (Section 5.3) against every path of small
+    # random DAGs enumerated one by one: the upward rank of v is the largest
+    # cost sum over paths starting at v, the downward rank the largest cost
+    # sum over paths ending at v with v's own cost left out
+    rng = np.random.default_rng(900 + seed)
+    n = 10
+    edges = sorted({(int(a), int(b)) for a, b in rng.integers(0, n, size=(18, 2)) if a < b})
+    cost = [float(c) for c in rng.integers(1, 9, size=n)]
+    adj = {v: [b for a, b in edges if a == v] for v in range(n)}
+    paths = []
+
+    def walk(p):
+        paths.append(p)
+        for s in adj[p[-1]]:
+            walk(p + [s])
+    for v in range(n):
+        walk([v])
+    up = [max(sum(cost[x] for x in p) for p in paths if p[0] == v) for v in range(n)]
+    down = [max(sum(cost[x] for x in p[:-1]) for p in paths if p[-1] == v) for v in range(n)]
+    assert dag.upward_rank(n, edges, cost) == up
+    assert dag.downward_rank(n, edges, cost) == down
+    # the longest path through v is the same from both ends
+    longest = max(sum(cost[x] for x in p) for p in paths)
+    assert max(u + d for u, d in zip(up, down)) == longest == max(up)
+
+
+def test_ranks_of_a_chain():
+    # closed form: a chain of n tasks with costs c_i
+    cost = [3.0, 1.0, 4.0, 1.0, 5.0]
+    edges = [(i, i + 1) for i in range(4)]
+    assert dag.upward_rank(5, edges, cost) == [14.0, 11.0, 10.0, 6.0, 5.0]
+    assert dag.downward_rank(5, edges, cost) == [0.0, 3.0, 4.0, 8.0, 9.0]
