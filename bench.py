@@ -88,7 +88,7 @@ def parse():
                    help="distinct client inputs (the first requests of the stream), cycled over the run")
     p.add_argument("--serve-plain-requests", type=int, default=256,
                    help="requests of the same stream served by the per-request path")
-    p.add_argument("--prio", default="upward", choices=["upward", "depth", "critical"],
+    p.add_argument("--prio", default="critical", choices=["critical", "upward", "depth"],
                    help="ready-queue order (b3t_config.prio_policy) of the headline context, the time to solution "
                         "and the profiling cases (--case); the vector chains and empty DAGs set their own")
     p.add_argument("--ctas-per-sm", type=int, default=0, help="grid of the profiling cases (0: occupancy)")

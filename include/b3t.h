@@ -279,16 +279,18 @@ typedef struct b3t_config {
                                submission and DAG inspection work, flush /
                                wait / replay return -ENODEV (for tools and
                                CPU-only tests of the dependency logic) */
-    int32_t prio_policy;    /* ready-queue order: B3T_PRIO_UPWARD (0, default):
-                               longest remaining path first (upward rank,
-                               Section 5.3); B3T_PRIO_DEPTH (1): deepest task
-                               first, so a successor runs right after its
-                               predecessor while the data is in L2;
-                               B3T_PRIO_CRITICAL (2): critical path first
-                               (Section 5.3's upward and downward ranks):
-                               the tasks whose upward plus downward rank is
-                               the graph's longest path take the top level,
-                               the others the levels below by upward rank */
+    int32_t prio_policy;    /* ready-queue order: B3T_PRIO_CRITICAL (0,
+                               default): critical path first (Section 5.3's
+                               upward and downward ranks): the tasks whose
+                               upward plus downward rank is the graph's
+                               longest path take the top level, the others
+                               the levels below by upward rank;
+                               B3T_PRIO_DEPTH (1): deepest task first, so a
+                               successor runs right after its predecessor
+                               while the data is in L2; B3T_PRIO_UPWARD (2):
+                               longest remaining path first (upward rank
+                               alone, over all levels).  Any other value is
+                               taken as the default */
     int32_t stream_free_sms; /* stream mode: SMs the resident kernel leaves
                                free for other work issued meanwhile (input
                                generation, copies); 0 = 8 */
@@ -317,7 +319,7 @@ typedef struct b3t_config {
                                task. */
 } b3t_config;
 
-enum { B3T_PRIO_UPWARD = 0, B3T_PRIO_DEPTH = 1, B3T_PRIO_CRITICAL = 2 };
+enum { B3T_PRIO_CRITICAL = 0, B3T_PRIO_DEPTH = 1, B3T_PRIO_UPWARD = 2 };
 
 /* Create a context bound to the current CUDA device and to `cuda_stream`
  * (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream; NULL = the

@@ -20,7 +20,7 @@ R, W, RW = 1, 2, 3
 NOOP, SCAL_F32, POTRF, TRSM, SYRK, GEMM = 0, 1, 2, 3, 4, 5
 POTRF_MX, TRSM_MX, SYRK_MX, GEMM_MX, QUANT = 6, 7, 8, 9, 10
 FMT_BF16, FMT_E4M3 = 0, 1
-PRIO_UPWARD, PRIO_DEPTH, PRIO_CRITICAL = 0, 1, 2
+PRIO_CRITICAL, PRIO_DEPTH, PRIO_UPWARD = 0, 1, 2
 TRSV_L, GEMV_L, TRSV_LT, GEMV_LT, AXPY, RESID, NRM = 11, 12, 13, 14, 15, 16, 17
 VEC_F32, VEC_ASSIGN, VEC_LOWER_M, VEC_UPPER_M, VEC_KEEP_NORM = 1, 2, 4, 8, 16
 POTRF_D, PANEL_TRSM, PANEL_UPD, CVT, TRTRI, TRMM_MX = 18, 19, 20, 21, 22, 23

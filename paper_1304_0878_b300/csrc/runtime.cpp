@@ -941,8 +941,8 @@ int b3t_init(b3t_ctx **out, const b3t_config *cfg, void *cuda_stream) {
     if (cfg) c->cfg = *cfg;
     if (c->cfg.timeout_ns <= 0) c->cfg.timeout_ns = 10'000'000'000LL;
     if (c->cfg.prio_levels <= 0) c->cfg.prio_levels = kMaxLevels;
-    if (c->cfg.prio_policy != B3T_PRIO_DEPTH && c->cfg.prio_policy != B3T_PRIO_CRITICAL)
-        c->cfg.prio_policy = B3T_PRIO_UPWARD;
+    if (c->cfg.prio_policy != B3T_PRIO_DEPTH && c->cfg.prio_policy != B3T_PRIO_UPWARD)
+        c->cfg.prio_policy = B3T_PRIO_CRITICAL;
     c->cfg.prio_levels = std::min(c->cfg.prio_levels, kMaxLevels);
     for (int k = 0; k < kNumKinds; ++k) c->kind_cl[k] = -1;
     if (host_only) { *out = c; return 0; }

@@ -404,7 +404,7 @@ def test_upward_rank_is_longest_path(seed):
     n, nh = int(rng.integers(20, 120)), int(rng.integers(3, 12))
     acc = [[(int(h), int(rng.choice([R, W, RW])))
             for h in rng.choice(nh, size=int(rng.integers(1, 4)), replace=False)] for _ in range(n)]
-    with b3t.Context(host_only=True) as c:
+    with b3t.Context(host_only=True, prio_policy=b3t.PRIO_UPWARD) as c:
         _submit_accesses(c, acc, nh)
         rank, level = c.dag_levels()
     edges = dag.derive_edges(acc)
@@ -449,6 +449,9 @@ def test_critical_policy_puts_the_longest_paths_on_top(seed):
     with b3t.Context(host_only=True, prio_policy=b3t.PRIO_CRITICAL) as c:
         _submit_accesses(c, acc, nh)
         rank, level = c.dag_levels()
+    with b3t.Context(host_only=True) as c:          # the default policy
+        _submit_accesses(c, acc, nh)
+        assert c.dag_levels() == (rank, level)
     edges = dag.derive_edges(acc)
     cost = [NOOP_COST] * n
     up, down = dag.upward_rank(n, edges, cost), dag.downward_rank(n, edges, cost)
@@ -487,7 +490,7 @@ def test_cholesky_upward_rank_follows_the_critical_path(T, cp):
     # add up to that rank.  With equal costs (the same accesses as empty
     # tasks) that walk is the closed-form critical path of 3T - 2 tasks.
     b = 64
-    with b3t.Context(host_only=True) as c:
+    with b3t.Context(host_only=True, prio_policy=b3t.PRIO_UPWARD) as c:
         nt = T * (T + 1) // 2
         tiles = [fake_ptr(i) for i in range(nt)]
         c.cholesky_submit(tiles, T, b)
