@@ -451,7 +451,7 @@ def run_ours(args):
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "l2": "inputs (%.2f GB of tiles) larger than L2" % (a_bytes / 1e9),
                    "input_reset": "A tiles restored by a device copy inside each step",
-                   "persistent_ctas": nctas},
+                   "persistent_ctas": nctas, "ready_queue": args.prio},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": recorded_traffic("cholesky_fp64_n%d_b%d" % (N, b)),
                      "note": "FP64 DFMA pipe: 148 SMs x 4 flop/clk x 2032 MHz; achieved = "

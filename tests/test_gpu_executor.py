@@ -525,3 +525,30 @@ def test_item_chains_full_size_config(orc):
         for k in range(nk):
             otl.scal_f32(z, f[i, k])
         assert np.array_equal(y[i * n:(i + 1) * n].view(np.uint32), z.view(np.uint32))
+
+
+def test_results_do_not_depend_on_the_queue_policy(orc):
+    # the ready-queue order (critical path first, upward-rank buckets, depth)
+    # changes when tasks run, never what they compute: the N = 1024
+    # factorisation is bitwise the same under each, and the vector chains
+    # too with item chains on or off
+    A = synth.spd_host(1024, seed=0, shift=1.0)
+    outs = []
+    for pol in (b3t.PRIO_CRITICAL, b3t.PRIO_UPWARD, b3t.PRIO_DEPTH):
+        c = b3t.Context(stream=torch.cuda.current_stream().cuda_stream, timeout_ns=20_000_000_000,
+                        prio_policy=pol)
+        outs.append(factor_device(c, A, 128))
+        c.close()
+    assert all(np.array_equal(o, outs[0]) for o in outs[1:])
+    nb, n = 6, (1 << 16) + 4
+    x = synth.vector_f32(nb * n, seed=47)
+    f = synth.chain_factors(nb, 8, seed=48)
+    ys = []
+    for pol in (b3t.PRIO_CRITICAL, b3t.PRIO_UPWARD, b3t.PRIO_DEPTH):
+        c = b3t.Context(stream=torch.cuda.current_stream().cuda_stream, timeout_ns=20_000_000_000,
+                        prio_policy=pol)
+        ys.append(run_chain_device(c, x, f, "b"))
+        c.close()
+    ys.append(run_chain_items(x, f, n)[0])
+    z = run_chain_oracle(x, f)
+    assert all(np.array_equal(y.view(np.uint32), z.view(np.uint32)) for y in ys)
