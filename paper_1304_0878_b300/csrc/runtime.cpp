@@ -319,9 +319,11 @@ void derive(b3t_ctx *c, int32_t t, const int32_t *leaves, const uint8_t *modes, 
 }
 
 // Priority of every task of the pending batch (higher level = claimed first):
-//   upward rank (default): the longest cost-weighted path from the task to
-//   the end of the graph, the task's own cost included, bucketed linearly
-//   into L levels (Section 5.3's scheduling hint);
+//   critical path first (default): the tasks whose downward plus upward rank
+//   is the graph's longest path on the top level, the others bucketed by
+//   upward rank below it (Section 5.3's scheduling hints);
+//   upward rank: the longest cost-weighted path from the task to the end of
+//   the graph, the task's own cost included, bucketed linearly into L levels;
 //   depth: the longest path from a source, in tasks (successor first).
 // off/succ: CSR successor lists of the batch (successors are later tasks).
 void compute_levels(const b3t_ctx *c, const std::vector<int32_t> &off, const int32_t *succ,
