@@ -89,3 +89,31 @@ def test_batch_uneven_sizes_one_launch(orc):
         Lo = np.tril(Lo)
         assert info == 0
         assert np.max(np.abs(L[:N, :N] - Lo)) / np.max(np.abs(Lo)) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", ["bf16", "e4m3"])
+def test_batch_mixed_precision_one_launch(orc, prec):
+    # cholesky_many in mixed precision: uneven sizes in one launch, tiles from
+    # the tuner, ragged sizes padded with identity.  Each factor is bitwise
+    # the one its matrix gets factored alone with the same tile (the order of
+    # every element's operations does not depend on the other requests), and
+    # its residual is that of the mixed oracle's factor of the padded matrix
+    # (the same low-precision factor up to the order of the binary32 sums)
+    from oracle import mixed as omx
+    sizes = [300, 1000, 513, 640]
+    mats = [synth.spd_host(N, seed=N + 1, shift=1.0) for N in sizes]
+    ctx = b3t.Context(stream=torch.cuda.current_stream().cuda_stream, timeout_ns=20_000_000_000)
+    out = bt.cholesky_many(ctx, [torch.from_numpy(A).cuda() for A in mats], prec=prec)
+    for A, (t, N, Np, b) in zip(mats, out):
+        L = np.tril(och.from_tiles(t.cpu().numpy(), Np, b))
+        assert np.array_equal(L[N:, N:], np.eye(Np - N)) and np.all(L[N:, :N] == 0)
+        (t1, _, _, _), = bt.cholesky_many(ctx, [torch.from_numpy(A).cuda()], prec=prec, tiles=[b])
+        assert np.array_equal(np.tril(och.from_tiles(t1.cpu().numpy(), Np, b)), L)
+        Ap = np.eye(Np)
+        Ap[:N, :N] = A
+        Lt, info = omx.factor(och.to_tiles(Ap, b), Np // b, b, prec)
+        assert info == 0
+        Lo = np.tril(och.from_tiles(Lt, Np, b))
+        r_dev, r_orc = och.rel_residual(L[:N, :N], A), och.rel_residual(Lo[:N, :N], A)
+        assert r_dev <= 2.0 * r_orc and r_orc <= 2.0 * r_dev
+    ctx.close()
