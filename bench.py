@@ -95,7 +95,8 @@ def parse():
     p.add_argument("--item-chains", action="store_true",
                    help="profiling cases: run vector-scaling chains item by item (b3t_config.item_chains)")
     p.add_argument("--case", default=None, choices=["mx_gemm_bf16", "mx_gemm_e4m3", "scal", "resid", "resid_sl", "trmm_sl", "solve_f32", "trace_mixed",
-                                                    "solve_f64", "empty_dags", "serve_sweep", "trace_headline", "batch"],
+                                                    "solve_f64", "empty_dags", "serve_sweep", "trace_headline", "batch",
+                                                    "trace_solve"],
                    help="run one profiling case (a DAG of one task kind), or one secondary measurement alone "
                         "(empty_dags, serve_sweep, trace_headline, batch), and print its result")
     return p.parse_args()
@@ -1446,6 +1447,55 @@ def run_batch(dev, args):
     return res
 
 
+def run_trace_solve(dev, args):
+    """The refinement's correction solve traced: forward and backward
+    substitution in binary32 with the inverted diagonal tiles of a sliced bf16
+    factor, N = --n, tile --b, 16 right-hand sides (two untraced runs, then one
+    traced): the critical path through the 2T dependent GEMV steps and the
+    time its tasks waited for a CTA."""
+    import torch
+    import synth
+    import paper_1304_0878_b300 as b3t
+    from paper_1304_0878_b300 import tiles as dt, trace
+    N, b, nrhs = args.n, args.b, 16
+    T = N // b
+    ctx = b3t.Context(stream=torch.cuda.current_stream(dev).cuda_stream, timeout_ns=120_000_000_000,
+                      prio_policy=prio_of(args))
+    A0 = synth.spd_tiles_device(N, b, 3, 0.1, dev)
+    W = A0.float()
+    del A0
+    L = torch.zeros(W.shape, dtype=torch.float64, device=dev)
+    Q = dt.q_tiles(T, b, b3t.FMT_BF16, dev)
+    U = torch.zeros((T, b, b), dtype=torch.float64, device=dev)
+    WS = torch.zeros((T * (T + 1) // 2, b3t.slice_w_bytes(b)), dtype=torch.uint8, device=dev)
+    US = torch.zeros((T, b3t.slice_u_bytes(b)), dtype=torch.uint8, device=dev)
+    ctx.cholesky_mx_sliced_submit(dt.tile_ptrs(W), dt.tile_ptrs(L), dt.tile_ptrs(Q), dt.tile_ptrs(U),
+                                  dt.tile_ptrs(WS), dt.tile_ptrs(US), T, b, b3t.FMT_BF16)
+    ctx.task_wait()
+    del W, WS, US, Q
+    Y = torch.randn((T, nrhs, b), dtype=torch.float64, device=dev)
+    Z = torch.zeros_like(Y)
+    out = {"workload": "binary32 forward + backward solve, N=%d tile %d, %d rhs, inverted diagonal tiles"
+                       % (N, b, nrhs)}
+    kms = []
+    for rep in range(3):
+        if rep == 2:
+            ctx.trace_start(1 << 20)
+        ctx.chol_solve_inv_submit(dt.tile_ptrs(L), dt.tile_ptrs(U), Y.data_ptr(), Z.data_ptr(), T, b, nrhs,
+                                  b * nrhs, b3t.VEC_F32)
+        ntasks, nedges = ctx.dag_stats()
+        ed = np.array(ctx.dag_edges(), dtype=np.int64).reshape(-1, 2)
+        ctx.task_wait()
+        kms.append(ctx.last_launch()["kernel_ns"] / 1e6)
+    tr = ctx.trace_read()
+    ctx.trace_stop()
+    ll = ctx.last_launch()
+    ctx.close()
+    out.update({"tasks": ntasks, "edges": nedges, "kernel_ms_untraced": kms[:2], "traced_kernel_ms": kms[2]})
+    out.update(trace.summary(tr, ntasks, ed, ll["nctas"]))
+    return out
+
+
 def run_part(args):
     """One secondary measurement alone, printed as one JSON line."""
     import torch
@@ -1460,6 +1510,8 @@ def run_part(args):
         res = run_trace_mixed(dev, args)
     elif args.case == "batch":
         res = run_batch(dev, args)
+    elif args.case == "trace_solve":
+        res = run_trace_solve(dev, args)
     else:
         res = run_serve_sweep(dev, args)
     print(json.dumps({"case": args.case, "result": res}))
@@ -1467,7 +1519,7 @@ def run_part(args):
 
 if __name__ == "__main__":
     a = parse()
-    if a.case in ("empty_dags", "serve_sweep", "trace_headline", "trace_mixed", "batch"):
+    if a.case in ("empty_dags", "serve_sweep", "trace_headline", "trace_mixed", "batch", "trace_solve"):
         run_part(a)
     elif a.case:
         run_case(a)
