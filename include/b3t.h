@@ -309,8 +309,9 @@ typedef struct b3t_config {
                                the item reads exactly what item i of the
                                task wrote, so the CTA applies both factors,
                                in submission order and each rounded, to the
-                               chunk it holds, and stores it once.  Up to 32
-                               tasks form one chain.  Results are bit for bit
+                               chunk it holds, and stores it once.  A chain
+                               is a head and up to 32 absorbed tasks after
+                               it.  Results are bit for bit
                                those of task-by-task execution; every task
                                still retires, and edges leaving a chain are
                                released when its last task retires.  Applies

@@ -145,8 +145,9 @@ bool is_mx(int kind) { return kind == kSyrkMx || kind == kGemmMx || kind == kRes
 bool is_slice(int kind) { return kind >= kSliceA && kind <= kResidSl; }
 bool has_fmt(int kind) { return kind == kSyrkMx || kind == kGemmMx || kind == kQuant; }
 
-// fine: the split of a small launch (see fine_items) for tiles of at most
-// kSmallTile rows; the device tells the two splits apart by the item count
+// fine: the split of a small launch (build_launch decides) for tiles of at
+// most kSmallTile rows; the device tells the two splits apart by the item
+// count
 int64_t items_of(int kind, int64_t n, bool fine = false) {
     fine = fine && n <= kSmallTile;
     switch (kind) {
