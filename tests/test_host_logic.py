@@ -247,6 +247,7 @@ def test_bench_summary_keeps_the_headline_figures():
     import bench
     line = {"value": 1.2, "roofline": {"frac": 0.98}, "e2e": {"value": 1.1},
             "secondary": {"vector_chains": {"ms": 2.6, "hbm_frac": 0.99},
+                          "vector_chains_item_chains": {"ms": 0.4, "floor_ms": 0.331, "hbm_frac": 0.83},
                           "empty_dags": {"chains": {"tasks_per_s": 4.5e6}},
                           "cholesky_small": {"ms": 5.0},
                           "time_to_solution": {"fp64": {"ms": 10000.0},
@@ -260,6 +261,7 @@ def test_bench_summary_keeps_the_headline_figures():
             "cpu_baseline": {"value": 1e-3, "library": {"cores": 16, "cholesky_n1024": {"ms": 3.0}}}}
     sm = bench.summarise(line)
     assert sm["cholesky_fp64_tflops"] == 1.2 and sm["vector_chains"]["hbm_frac"] == 0.99
+    assert sm["vector_chains_item_chains"] == {"ms": 0.4, "floor_ms": 0.331, "hbm_frac": 0.83}
     assert sm["tasks_per_s"]["chains"] == 4.5e6 and sm["cholesky_small_ms"] == 5.0
     assert sm["time_to_solution"]["bf16"]["host_sampled_eta"] == 2e-14
     assert sm["serving"]["fp64"]["requests"] == 2000 and sm["serving"]["fp64"]["plain_requests"] == 256
