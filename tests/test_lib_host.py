@@ -618,3 +618,21 @@ def test_item_chains_of_the_vector_configuration():
                 c.task_submit(cs, [h], b3t.pack_f32(1.0))
         aux = c.dag_item_chains()
     assert aux[:256] == [7] * 256 and aux[256:] == [-1] * (7 * 256)
+
+
+def test_item_chains_stay_off_beside_mixed_precision_kinds():
+    # the tensor-memory kernel variant runs SCAL items through registers, not
+    # the bulk-copy ring that applies a chain's factors: a batch that also
+    # holds a mixed-precision factorisation forms no item chains
+    T, b = 2, 128
+    nt = och.ntiles(T)
+    with b3t.Context(host_only=True, item_chains=True) as c:
+        hs = [c.data_register(fake_ptr(3000 + i), 1 << 18, 4) for i in range(2)]
+        cl = c.task_decl("scale_vector", b3t.SCAL_F32, [RW], 4)
+        for k in range(4):
+            for h in hs:
+                c.task_submit(cl, [h], b3t.pack_f32(2.0))
+        assert c.dag_item_chains()[:2] == [3, 3]
+        c.cholesky_mx_submit([fake_ptr(i) for i in range(nt)], [fake_ptr(100 + i) for i in range(nt)],
+                             [fake_ptr(200 + i) for i in range(nt)], T, b, b3t.FMT_BF16)
+        assert set(c.dag_item_chains()) == {0}
